@@ -1,0 +1,390 @@
+"""One shrinking-domain PM step in FP64 (oracle; test infrastructure only).
+
+Units: positions in cells of the n^3 mesh, measured from the mesh corner, so
+cell (i,j,k) has its centre at (i+0.5, j+0.5, k+0.5); conformal time in 1/H0;
+momentum p = a dx/dtau in cells*H0; potential in (cells*H0)^2.  With H0 = 1
+and the cell as length unit, Poisson's equation (Sec. 2.1, Eq. 3) reads
+    sum_nb(Phi) - 6 Phi = S(a) delta,    S(a) = 3 Om / (2 a),
+and the equations of motion (Sec. 2.1, Eqs. 1-2) are dx/dtau = p/a,
+dp/dtau = -a grad(Phi).  (The printed Eq. 2 has +a grad(Phi), which with the
+printed Poisson sign would make gravity repulsive; the attractive sign is
+taken.)
+
+Grid arrays are indexed [z, y, x] (x fastest); particle arrays are (N, 3) in
+(x, y, z) order.
+
+Step order follows Table 2 (usual-algorithm column for the static Poisson
+solve, plus the shrinking row of the right-hand column):
+  1. x += p dtau / (2 a_n)                       (Sec. 2.2, first DKD line)
+  2. CIC deposit of delta at t + dt/2            (Sec. 2.4 footnote: CIC)
+  3. solve Poisson for Phi(t + dt/2)             (Sec. 2.1, Eq. 3)
+  4. gradient + CIC gather (same weights as 2)   (Sec. 2.4 footnote)
+  5. p += -a_half grad(Phi) dtau                 (Sec. 2.2, second DKD line)
+  6. x += p dtau / (2 a_{n+1})                   (Sec. 2.2, third DKD line)
+  7. eliminate particles outside the lightcone   (Sec. 2.4, active cells and
+     particle pointers recomputed at the end of every step)
+
+Readings taken where the paper is silent (each also applies to the CUDA
+library, which implements them independently):
+* Domain shape: the implementation restricts loop bounds (Sec. 2.4), i.e. a
+  cube, centred on the observer at the box centre c = n/2.  Keep half-width
+  R = chi(a)/cell + buffer (1 cell).  Keep iff max_d |x_d - c| <= R.
+* Boundary conditions: periodic until the lightcone reaches the box border
+  (Sec. 3), read as R > n/2 - 1; afterwards open (Table 1) with Dirichlet
+  values from a monopole + dipole + quadrupole expansion of the source about
+  c at the centres of one ghost-cell layer.
+* Active mesh cube in the open phase: half-width m = ceil(R) + 1 cells, side
+  the smallest 2^j or 3*2^j >= 2m (multigrid-friendly), at most n.
+* Density contrast: delta = rho/rho_mean - 1 with the cosmic mean N/n^3;
+  the "-1" background is subtracted only on cells whose centre lies inside
+  the keep cube (the whole box in the periodic phase), so that cells of the
+  mesh cube outside the lightcone carry no spurious negative source.
+* Fixed-point CIC (not in the paper): on the float position u,
+  v = u - 0.5, i = floor(v), dq = floor(v*2^16) - i*2^16 in [0, 2^16);
+  per-axis weights (2^16 - dq, dq); the product (<= 2^48) is added to an
+  int64 cell count.  Each particle adds exactly 2^48 in total.
+* Gradient: centred difference (Phi_{i+1} - Phi_{i-1}) / 2 at the 8 CIC
+  nodes, gathered with the deposit's weights dq / 2^16.
+* A particle whose CIC nodes are not all inside the active cube (open phase)
+  is counted as escaped: it deposits nothing and feels no force.
+"""
+import math
+
+import numpy as np
+from scipy import fft as sfft
+
+Q16 = 65536
+MASS_UNIT = 2 ** 48
+
+
+# --------------------------------------------------------------------------
+# geometry of the active region (Sec. 2.4 and Sec. 3, readings above)
+# --------------------------------------------------------------------------
+
+def is_open(R, n):
+    """Open phase once the keep cube no longer wraps the box (Sec. 3)."""
+    return R <= n / 2 - 1
+
+
+def _mg_size(m):
+    """Smallest 2^j or 3*2^j that is >= m."""
+    sizes = sorted({2 ** j for j in range(40)} | {3 * 2 ** j for j in range(40)})
+    return next(x for x in sizes if x >= m)
+
+
+def active_cube(R, n):
+    """(lo, s, periodic) of the mesh cube worked on while the keep radius is R."""
+    if not is_open(R, n):
+        return 0, n, True
+    m = math.ceil(R) + 1
+    s = min(_mg_size(2 * m), n)
+    return n // 2 - s // 2, s, False
+
+
+def background_range(R, n, periodic):
+    """Index range [b0, b1] of cells whose centre is inside the keep cube."""
+    if periodic:
+        return 0, n - 1
+    c = n / 2
+    return math.ceil(c - R - 0.5), math.floor(c + R - 0.5)
+
+
+# --------------------------------------------------------------------------
+# CIC with fixed-point weights
+# --------------------------------------------------------------------------
+
+def cic_index(pos):
+    """Base node i and Q16 weight dq per axis.  Exact in FP64 for float32 or
+    float64 positions |u| < 2^36."""
+    v = np.asarray(pos, dtype=np.float64) - 0.5
+    i = np.floor(v)
+    dq = np.floor(v * Q16) - i * Q16
+    return i.astype(np.int64), dq.astype(np.int64)
+
+
+def _valid(i, lo, s):
+    return np.all((i >= lo) & (i + 1 <= lo + s - 1), axis=1)
+
+
+def deposit(pos, n, lo, s, periodic):
+    """Integer CIC mass counts rho[z,y,x] (int64), and the escaped count."""
+    i, dq = cic_index(pos)
+    rho = np.zeros((n, n, n), dtype=np.int64)
+    if periodic:
+        ok = np.ones(len(i), dtype=bool)
+    else:
+        ok = _valid(i, lo, s)
+    i, dq = i[ok], dq[ok]
+    w = [Q16 - dq, dq]
+    for cz in (0, 1):
+        for cy in (0, 1):
+            for cx in (0, 1):
+                ix, iy, iz = i[:, 0] + cx, i[:, 1] + cy, i[:, 2] + cz
+                if periodic:
+                    ix, iy, iz = ix % n, iy % n, iz % n
+                wt = w[cx][:, 0] * w[cy][:, 1] * w[cz][:, 2]
+                np.add.at(rho, (iz, iy, ix), wt)
+    return rho, int((~ok).sum())
+
+
+# --------------------------------------------------------------------------
+# source and boundary values (Sec. 2.1 Eq. 3; Table 1 open boundaries)
+# --------------------------------------------------------------------------
+
+def source_S(a, om):
+    """S(a) = 3 Om / (2a), the Poisson source factor in H0 = 1 units."""
+    return 1.5 * om / a
+
+
+def delta_cube(rho, n, lo, s, nbar, R, periodic):
+    """Density contrast on the active cube [z,y,x] (s^3, float64)."""
+    sub = rho[lo:lo + s, lo:lo + s, lo:lo + s].astype(np.float64)
+    d = sub / (MASS_UNIT * nbar)
+    b0, b1 = background_range(R, n, periodic)
+    idx = np.arange(lo, lo + s)
+    inside = (idx >= b0) & (idx <= b1)
+    mask = inside[:, None, None] & inside[None, :, None] & inside[None, None, :]
+    return d - mask.astype(np.float64)
+
+
+def multipoles(delta, lo, n):
+    """Monopole, dipole and traceless quadrupole of delta about the box centre.
+
+    Q0 = sum delta,  D_a = sum delta y_a,  Q_ab = sum delta (3 y_a y_b - y^2 d_ab)
+    with y the cell centre relative to c = n/2 (cell volume 1).
+    """
+    s = delta.shape[0]
+    y1 = np.arange(lo, lo + s) + 0.5 - n / 2
+    Z, Y, X = np.meshgrid(y1, y1, y1, indexing="ij")
+    comps = [X, Y, Z]
+    q0 = delta.sum()
+    dip = np.array([(delta * c).sum() for c in comps])
+    r2 = X * X + Y * Y + Z * Z
+    quad = np.zeros((3, 3))
+    for a in range(3):
+        for b in range(3):
+            t = 3 * comps[a] * comps[b] - (r2 if a == b else 0.0)
+            quad[a, b] = (delta * t).sum()
+    return q0, dip, quad
+
+
+def multipole_potential(points, S, q0, dip, quad):
+    """Phi at points (M,3) relative to c:  -(S/4pi)[Q0/r + D.r/r^3 + r.Q.r/(2 r^5)]."""
+    r2 = (points * points).sum(axis=1)
+    r = np.sqrt(r2)
+    dr = points @ dip
+    qr = np.einsum("ma,ab,mb->m", points, quad, points)
+    return -(S / (4 * math.pi)) * (q0 / r + dr / (r * r2) + 0.5 * qr / (r2 * r2 * r))
+
+
+def open_ghost_potential(f_cube, S, lo, n):
+    """Padded (s+2)^3 array whose ghost layer holds the Dirichlet values."""
+    s = f_cube.shape[0]
+    delta = f_cube / S
+    q0, dip, quad = multipoles(delta, lo, n)
+    g = np.zeros((s + 2,) * 3)
+    coords = np.arange(lo - 1, lo + s + 1) + 0.5 - n / 2
+    Z, Y, X = np.meshgrid(coords, coords, coords, indexing="ij")
+    ghost = np.ones((s + 2,) * 3, dtype=bool)
+    ghost[1:-1, 1:-1, 1:-1] = False
+    pts = np.stack([X[ghost], Y[ghost], Z[ghost]], axis=1)
+    g[ghost] = multipole_potential(pts, S, q0, dip, quad)
+    return g
+
+
+# --------------------------------------------------------------------------
+# Poisson solve: the exact discrete solution of the 7-point system
+# --------------------------------------------------------------------------
+
+def laplacian_eig_periodic(n):
+    k = np.arange(n)
+    lam1 = -4.0 * np.sin(np.pi * k / n) ** 2
+    return lam1[:, None, None] + lam1[None, :, None] + lam1[None, None, :]
+
+
+def solve_periodic(f):
+    """sum_nb - 6 Phi = f on a periodic n^3 grid; gauge mean(Phi) = 0.
+
+    The discrete Laplacian is diagonal in the DFT basis with eigenvalue
+    -4 sum_d sin^2(pi k_d / n); the k = 0 mode is set to zero."""
+    n = f.shape[0]
+    fk = np.fft.fftn(f)
+    lam = laplacian_eig_periodic(n)
+    lam[0, 0, 0] = 1.0
+    phik = fk / lam
+    phik[0, 0, 0] = 0.0
+    return np.real(np.fft.ifftn(phik))
+
+
+def laplacian_eig_dirichlet(s):
+    m = np.arange(1, s + 1)
+    lam1 = -4.0 * np.sin(np.pi * m / (2.0 * (s + 1))) ** 2
+    return lam1[:, None, None] + lam1[None, :, None] + lam1[None, None, :]
+
+
+def solve_open(f, ghost):
+    """sum_nb - 6 Phi = f on an s^3 cube with Dirichlet values at the ghost
+    cell centres (ghost: padded (s+2)^3 array, interior ignored).
+
+    Ghost neighbours move to the right-hand side; the remaining operator with
+    zero values one cell outside is diagonalised by the type-I DST."""
+    s = f.shape[0]
+    rhs = f.copy()
+    rhs[0, :, :] -= ghost[0, 1:-1, 1:-1]
+    rhs[-1, :, :] -= ghost[-1, 1:-1, 1:-1]
+    rhs[:, 0, :] -= ghost[1:-1, 0, 1:-1]
+    rhs[:, -1, :] -= ghost[1:-1, -1, 1:-1]
+    rhs[:, :, 0] -= ghost[1:-1, 1:-1, 0]
+    rhs[:, :, -1] -= ghost[1:-1, 1:-1, -1]
+    rh = sfft.dstn(rhs, type=1)
+    u = sfft.idstn(rh / laplacian_eig_dirichlet(s), type=1)
+    out = ghost.copy()
+    out[1:-1, 1:-1, 1:-1] = u
+    return out
+
+
+def apply_laplacian_padded(phi_pad):
+    """7-point operator on the interior of a padded array (h = 1)."""
+    p = phi_pad
+    c = p[1:-1, 1:-1, 1:-1]
+    return (p[2:, 1:-1, 1:-1] + p[:-2, 1:-1, 1:-1] + p[1:-1, 2:, 1:-1]
+            + p[1:-1, :-2, 1:-1] + p[1:-1, 1:-1, 2:] + p[1:-1, 1:-1, :-2]
+            - 6.0 * c)
+
+
+def apply_laplacian_periodic(phi):
+    return (sum(np.roll(phi, sh, axis=ax) for ax in range(3) for sh in (1, -1))
+            - 6.0 * phi)
+
+
+def solve_step_potential(rho, n, lo, s, periodic, nbar, R, a_half, om):
+    """Source and potential of one step.  Returns (f_cube, phi) where phi is
+    n^3 (periodic) or padded (s+2)^3 (open, ghosts included)."""
+    S = source_S(a_half, om)
+    f = S * delta_cube(rho, n, lo, s, nbar, R, periodic)
+    if periodic:
+        return f, solve_periodic(f)
+    return f, solve_open(f, open_ghost_potential(f, S, lo, n))
+
+
+# --------------------------------------------------------------------------
+# gradient + CIC gather (Sec. 2.4 footnote: same scheme as the deposit)
+# --------------------------------------------------------------------------
+
+def gather_force(phi, pos, n, lo, s, periodic):
+    """grad(Phi) interpolated to the particles; escaped particles get 0."""
+    i, dq = cic_index(pos)
+    N = len(i)
+    F = np.zeros((N, 3))
+    ok = np.ones(N, dtype=bool) if periodic else _valid(i, lo, s)
+    w = [(Q16 - dq) / Q16, dq / Q16]
+
+    if periodic:
+        def val(ix, iy, iz):
+            return phi[iz % n, iy % n, ix % n]
+        base = i
+    else:
+        def val(ix, iy, iz):
+            return phi[iz, iy, ix]
+        base = i - lo + 1  # padded local index
+        base = np.where(ok[:, None], base, 1)
+
+    for cz in (0, 1):
+        for cy in (0, 1):
+            for cx in (0, 1):
+                x, y, z = base[:, 0] + cx, base[:, 1] + cy, base[:, 2] + cz
+                wt = w[cx][:, 0] * w[cy][:, 1] * w[cz][:, 2]
+                gx = 0.5 * (val(x + 1, y, z) - val(x - 1, y, z))
+                gy = 0.5 * (val(x, y + 1, z) - val(x, y - 1, z))
+                gz = 0.5 * (val(x, y, z + 1) - val(x, y, z - 1))
+                F[:, 0] += wt * gx
+                F[:, 1] += wt * gy
+                F[:, 2] += wt * gz
+    F[~ok] = 0.0
+    return F, int((~ok).sum())
+
+
+# --------------------------------------------------------------------------
+# drift, kick, shrink
+# --------------------------------------------------------------------------
+
+def wrap(pos, n):
+    x = np.where(pos < 0, pos + n, pos)
+    return np.where(x >= n, x - n, x)
+
+
+def drift(pos, mom, coef, n, periodic):
+    """x += p * coef (FP64); periodic wrap in the periodic phase."""
+    x = pos + mom * coef
+    return wrap(x, n) if periodic else x
+
+
+def drift_fp32(pos32, mom32, coef, n, periodic):
+    """The same drift evaluated as the CUDA kernel documents it, in float32:
+    x' = fl(x + fl(p * fl(coef))), then the float32 wrap.  Used where a float
+    result decides an integer (the fixed-point CIC nodes)."""
+    c = np.float32(coef)
+    x = (pos32.astype(np.float32) + (mom32.astype(np.float32) * c)).astype(np.float32)
+    if periodic:
+        n32 = np.float32(n)
+        x = np.where(x < 0, (x + n32).astype(np.float32), x)
+        x = np.where(x >= n32, (x - n32).astype(np.float32), x)
+    return x.astype(np.float32)
+
+
+def keep_mask(pos, R, n):
+    """Keep iff max_d |x_d - c| <= R, compared in FP64 (Sec. 2.4)."""
+    d = np.abs(np.asarray(pos, dtype=np.float64) - n / 2)
+    return d.max(axis=1) <= R
+
+
+def shrink(arrays, keep):
+    """Order-preserving partition: (survivors..., leavers...) of each array."""
+    surv = [a[keep] for a in arrays]
+    leave = [a[~keep] for a in arrays]
+    return surv, leave
+
+
+# --------------------------------------------------------------------------
+# the whole step and the whole run
+# --------------------------------------------------------------------------
+
+def step(pos, mom, k, sched, n, om, nbar, want=False):
+    """Advance FP64 state (pos, mom) by step k.  Returns (pos, mom, info)."""
+    a0, a1 = sched["a"][k], sched["a"][k + 1]
+    dtau, ah = sched["dtau"][k], sched["a_half"][k]
+    R0 = sched["R"][k]
+    lo, s, periodic = active_cube(R0, n)
+    pos = drift(pos, mom, dtau / (2 * a0), n, periodic)
+    rho, esc = deposit(pos, n, lo, s, periodic)
+    f, phi = solve_step_potential(rho, n, lo, s, periodic, nbar, R0, ah, om)
+    F, _ = gather_force(phi, pos, n, lo, s, periodic)
+    mom = mom - ah * dtau * F
+    pos = drift(pos, mom, dtau / (2 * a1), n, periodic)
+    info = dict(lo=lo, s=s, periodic=periodic, escaped=esc)
+    if want:
+        info.update(rho=rho, f=f, phi=phi, F=F)
+    return pos, mom, info
+
+
+def run(pos, mom, ids, sched, n, om, nbar, steps=None):
+    """Whole run with shrinking.  Returns survivors, lightcone, per-step n_active."""
+    pos = np.asarray(pos, dtype=np.float64).copy()
+    mom = np.asarray(mom, dtype=np.float64).copy()
+    ids = np.asarray(ids).copy()
+    lc = [np.zeros((0, 3)), np.zeros((0, 3)), np.zeros(0, dtype=ids.dtype),
+          np.zeros(0)]
+    n_active = []
+    nsteps = len(sched["dtau"]) if steps is None else steps
+    for k in range(nsteps):
+        n_active.append(len(pos))
+        pos, mom, _ = step(pos, mom, k, sched, n, om, nbar)
+        R1 = sched["R"][k + 1]
+        if is_open(R1, n):
+            keep = keep_mask(pos, R1, n)
+            (pos, mom, ids), (lp, lm, li) = shrink([pos, mom, ids], keep)
+            lc = [np.concatenate([lc[0], lp]), np.concatenate([lc[1], lm]),
+                  np.concatenate([lc[2], li]),
+                  np.concatenate([lc[3], np.full(len(li), sched["a"][k + 1])])]
+    return dict(pos=pos, mom=mom, ids=ids, lc_pos=lc[0], lc_mom=lc[1],
+                lc_ids=lc[2], lc_a=lc[3], n_active=np.array(n_active))

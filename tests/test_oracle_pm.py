@@ -1,0 +1,353 @@
+"""Pins of the oracle's PM step against exact arithmetic, closed forms,
+brute force and conservation laws (no GPU)."""
+import itertools
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+from scipy.special import erf
+
+from oracle import cosmology as cz
+from oracle import pm
+from paper_1709_04703_gb300 import ics
+
+OM, OL = 0.3, 0.7
+
+
+# ---------------------------------------------------------------- deposit
+
+def _rational_cic(pos, n):
+    """CIC weights from exact rational arithmetic on the float32 value:
+    nodes at cell centres, weight 1 - |u - node| per axis, quantised down to
+    multiples of 2^-16 on the upper node."""
+    rho = {}
+    for p in pos:
+        axes = []
+        for u in p:
+            v = Fraction(float(u)) - Fraction(1, 2)
+            i = math.floor(v)
+            frac = v - i
+            dq = math.floor(frac * 65536)
+            axes.append(((i % n, 65536 - dq), ((i + 1) % n, dq)))
+        for (x, wx), (y, wy), (z, wz) in itertools.product(*axes):
+            rho[(z, y, x)] = rho.get((z, y, x), 0) + wx * wy * wz
+    return rho
+
+
+def test_deposit_matches_rational_brute_force():
+    n = 8
+    pos, _, _ = ics.random_particles(40, n, seed=3)
+    pos[0] = [0.5, 0.5, 0.5]          # exactly on a node
+    pos[1] = [1.0, 2.0, 3.0]          # on cell faces: equal split
+    pos[2] = [0.1, 7.9, 0.25]         # wraps in x and y
+    rho, esc = pm.deposit(pos, n, 0, n, True)
+    ref = _rational_cic(pos, n)
+    assert esc == 0
+    dense = np.zeros_like(rho)
+    for k, v in ref.items():
+        dense[k] = v
+    np.testing.assert_array_equal(rho, dense)
+
+
+def test_deposit_mass_is_exact():
+    n = 16
+    pos, _, _ = ics.random_particles(5000, n, seed=1)
+    rho, _ = pm.deposit(pos, n, 0, n, True)
+    assert int(rho.sum()) == 5000 * 2**48
+    one, _ = pm.deposit(np.array([[3.5, 4.5, 5.5]], np.float32), n, 0, n, True)
+    assert one[5, 4, 3] == 2**48 and int(one.sum()) == 2**48
+    corner, _ = pm.deposit(np.array([[4.0, 4.0, 4.0]], np.float32), n, 0, n, True)
+    np.testing.assert_array_equal(corner[3:5, 3:5, 3:5], np.full((2, 2, 2), 2**45))
+
+
+def test_deposit_open_counts_escapes():
+    n, lo, s = 32, 8, 16
+    pos = np.array([[16.0, 16.0, 16.0],     # inside
+                    [8.6, 16.0, 16.0],      # node 8 and 9: inside
+                    [8.4, 16.0, 16.0],      # node 7: outside
+                    [23.5, 23.5, 23.5],     # nodes 23, 24 -> 24 outside... 23.5-0.5=23 -> 23,24
+                    [23.4, 20.0, 20.0]],    # nodes 22, 23: inside
+                   np.float32)
+    rho, esc = pm.deposit(pos, n, lo, s, False)
+    assert esc == 2
+    assert int(rho.sum()) == 3 * 2**48
+    assert int(rho[:lo].sum()) == 0 and int(rho[lo + s:].sum()) == 0
+
+
+# ---------------------------------------------------------------- solve
+
+def test_periodic_single_mode_exact():
+    n = 16
+    x = np.arange(n)
+    m = (1, 3, 2)
+    f = (np.cos(2 * np.pi * m[0] * x / n)[None, None, :]
+         * np.cos(2 * np.pi * m[1] * x / n)[None, :, None]
+         * np.cos(2 * np.pi * m[2] * x / n)[:, None, None])
+    lam = -4 * sum(math.sin(math.pi * k / n) ** 2 for k in m)
+    np.testing.assert_allclose(pm.solve_periodic(f), f / lam, atol=1e-13)
+
+
+def _dense_open_solve(f, ghost):
+    s = f.shape[0]
+    N = s**3
+    A = np.zeros((N, N))
+    b = f.ravel().copy()
+    idx = lambda z, y, x: (z * s + y) * s + x
+    for z, y, x in itertools.product(range(s), repeat=3):
+        r = idx(z, y, x)
+        A[r, r] = -6.0
+        for dz, dy, dx in [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0),
+                           (0, 0, 1), (0, 0, -1)]:
+            zz, yy, xx = z + dz, y + dy, x + dx
+            if 0 <= zz < s and 0 <= yy < s and 0 <= xx < s:
+                A[r, idx(zz, yy, xx)] = 1.0
+            else:
+                b[r] -= ghost[zz + 1, yy + 1, xx + 1]
+    return np.linalg.solve(A, b).reshape(s, s, s)
+
+
+def test_open_solve_matches_dense_solve():
+    rng = np.random.default_rng(5)
+    s = 7
+    f = rng.standard_normal((s, s, s))
+    ghost = rng.standard_normal((s + 2,) * 3)
+    out = pm.solve_open(f, ghost)
+    np.testing.assert_allclose(out[1:-1, 1:-1, 1:-1], _dense_open_solve(f, ghost),
+                               rtol=1e-11, atol=1e-12)
+    # ghosts are left untouched
+    g = ghost.copy()
+    g[1:-1, 1:-1, 1:-1] = out[1:-1, 1:-1, 1:-1]
+    np.testing.assert_array_equal(out, g)
+
+
+def test_multipole_boundary_matches_direct_sum():
+    n, lo, s, S = 32, 0, 32, 2.0
+    delta = np.zeros((s, s, s))
+    delta[16, 16, 19] = 3.0      # off-centre: dipole and quadrupole matter
+    delta[14, 17, 15] = -1.0
+    delta[15, 15, 16] = 0.5
+    ghost = pm.open_ghost_potential(S * delta, S, lo, n)
+    coords = np.arange(lo - 1, lo + s + 1) + 0.5 - n / 2
+    src = np.argwhere(delta != 0)
+    err_max, scale = 0.0, 0.0
+    for (gz, gy, gx) in [(0, 5, 7), (20, 0, 33), (33, 33, 33), (10, 33, 1)]:
+        p = np.array([coords[gx], coords[gy], coords[gz]])
+        direct = 0.0
+        for (z, y, x) in src:
+            q = np.array([x, y, z]) + lo + 0.5 - n / 2
+            direct += -S / (4 * math.pi) * delta[z, y, x] / np.linalg.norm(p - q)
+        err_max = max(err_max, abs(ghost[gz, gy, gx] - direct))
+        scale = max(scale, abs(direct))
+    # octupole remainder ~ (source extent / distance)^3 ~ (3.5/16)^3
+    assert err_max < 2e-2 * scale
+
+
+def _gaussian_problem(s, om=OM, a=0.5):
+    n = s
+    sigma = s / 10.0
+    c = n / 2
+    g = np.arange(s) + 0.5 - c
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    r = np.sqrt(X**2 + Y**2 + Z**2)
+    A = 1.0
+    delta = A * np.exp(-r**2 / (2 * sigma**2))
+    S = pm.source_S(a, om)
+    f = S * delta
+    phi = pm.solve_open(f, pm.open_ghost_potential(f, S, 0, n))
+    exact = -(S / (4 * math.pi)) * A * (2 * math.pi * sigma**2) ** 1.5 * erf(
+        r / (math.sqrt(2) * sigma)) / r
+    return phi[1:-1, 1:-1, 1:-1], exact
+
+
+def test_gaussian_potential_converges_second_order():
+    errs = []
+    for s in (16, 32, 64):
+        phi, exact = _gaussian_problem(s)
+        errs.append(np.sqrt(np.mean((phi - exact) ** 2)) / np.sqrt(np.mean(exact**2)))
+    assert errs[2] < 5e-3
+    assert 3.0 < errs[0] / errs[1] < 5.0
+    assert 3.0 < errs[1] / errs[2] < 5.0
+
+
+def test_uniform_sphere_potential():
+    s = 64
+    c = s / 2
+    R = 10.0
+    g = np.arange(s) + 0.5 - c
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    r = np.sqrt(X**2 + Y**2 + Z**2)
+    d0 = 1.0
+    delta = np.where(r <= R, d0, 0.0)
+    S = 1.0
+    phi = pm.solve_open(S * delta, pm.open_ghost_potential(S * delta, S, 0, s))
+    phi = phi[1:-1, 1:-1, 1:-1]
+    M = delta.sum()                           # discrete mass of the sphere
+    Reff = (3 * M / (4 * math.pi)) ** (1 / 3)  # radius holding that mass
+    exact = np.where(r <= Reff, S * d0 * (r**2 - 3 * Reff**2) / 6,
+                     -S * d0 * Reff**3 / (3 * r))
+    far = r > 1.5 * R
+    inner = r < 0.5 * R
+    assert np.max(np.abs(phi[far] - exact[far]) / np.abs(exact[far])) < 3e-3
+    assert np.max(np.abs(phi[inner] - exact[inner]) / np.abs(exact[inner])) < 3e-2
+
+
+# ---------------------------------------------------------------- forces
+
+def _forces(pos, n, periodic, R=None, a=0.5, lo=None, s=None):
+    if periodic:
+        lo, s = 0, n
+        R = n
+    rho, _ = pm.deposit(pos, n, lo, s, periodic)
+    f, phi = pm.solve_step_potential(rho, n, lo, s, periodic, 1.0, R, a, OM)
+    F, esc = pm.gather_force(phi, pos, n, lo, s, periodic)
+    return F, esc
+
+
+def test_single_particle_feels_no_self_force():
+    n = 16
+    pos = np.array([[3.3, 7.8, 11.1]], np.float32)
+    F, _ = _forces(pos, n, True)
+    np.testing.assert_allclose(F, 0.0, atol=1e-13)
+
+
+def test_two_particles_antisymmetric_and_attractive_periodic():
+    n = 16
+    pos = np.array([[5.25, 8.0, 8.0], [10.75, 8.0, 8.0]], np.float32)
+    F, _ = _forces(pos, n, True)
+    np.testing.assert_allclose(F[0], -F[1], atol=1e-14)
+    # Phi has its well at each particle, so grad Phi at particle 0 points
+    # away from particle 1; the kick -a grad(Phi) dtau then attracts
+    assert F[0, 0] < 0 and F[1, 0] > 0
+
+
+def test_two_particle_inverse_square_law_open():
+    n = 64
+    S = pm.source_S(0.5, OM)
+    R, lo, s = 30.5, 0, 64
+    out = []
+    for d in (4.0, 6.0, 8.0, 12.0):
+        pos = np.array([[32.0 - d / 2 + 0.5, 32.5, 32.5],
+                        [32.0 + d / 2 + 0.5, 32.5, 32.5]], np.float32)
+        rho, _ = pm.deposit(pos, n, lo, s, False)
+        # no background: source of two unit masses only
+        f = S * rho[lo:lo + s, lo:lo + s, lo:lo + s].astype(np.float64) / 2**48
+        phi = pm.solve_open(f, pm.open_ghost_potential(f, S, lo, n))
+        F, _ = pm.gather_force(phi, pos, n, lo, s, False)
+        expected = S / (4 * math.pi * d * d)   # |grad Phi| of a unit mass
+        assert F[0, 0] < 0 and F[1, 0] > 0
+        out.append(-F[0, 0] / expected)
+    # discretisation error of the 7-point Green's function + centred
+    # gradient falls off as 1/d^2 relative to the inverse-square force
+    for d, x in zip((4.0, 6.0, 8.0, 12.0), out):
+        assert abs(x - 1) < 2.5 / d**2, out
+    assert abs(out[-1] - 1) < 0.02
+
+
+def test_lattice_feels_no_force_and_momentum_conserved():
+    n = 8
+    g = np.arange(n) + 0.5
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    lat = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1).astype(np.float32)
+    F, _ = _forces(lat, n, True)
+    np.testing.assert_allclose(F, 0.0, atol=1e-12)
+    pos, _, _ = ics.random_particles(300, n, seed=9)
+    F, _ = _forces(pos, n, True)
+    assert np.abs(F.sum(axis=0)).max() < 1e-11 * np.abs(F).sum()
+
+
+# ---------------------------------------------------------------- geometry + shrink
+
+def test_active_cube_rules():
+    assert pm.active_cube(200.0, 256) == (0, 256, True)
+    assert pm.is_open(127.0, 256) and not pm.is_open(127.01, 256)
+    lo, s, per = pm.active_cube(60.2, 256)       # m = 62 -> 2m = 124 -> 128
+    assert (lo, s, per) == (64, 128, False)
+    lo, s, per = pm.active_cube(40.0, 256)       # m = 41 -> 82 -> 96
+    assert (lo, s, per) == (80, 96, False)
+    lo, s, per = pm.active_cube(1.0, 32)         # m = 2 -> 4
+    assert (lo, s, per) == (14, 4, False)
+
+
+def test_shrink_is_stable_partition():
+    rng = np.random.default_rng(0)
+    n = 32
+    pos = rng.uniform(0, n, (1000, 3))
+    ids = np.arange(1000)
+    R = 9.3
+    keep = pm.keep_mask(pos, R, n)
+    (sp, si), (lp, li) = pm.shrink([pos, ids], keep)
+    ref_keep = [i for i in range(1000)
+                if max(abs(pos[i, d] - 16.0) for d in range(3)) <= R]
+    assert list(si) == ref_keep
+    assert list(li) == [i for i in range(1000) if i not in set(ref_keep)]
+    assert len(si) + len(li) == 1000
+
+
+def test_keep_boundary_is_inclusive():
+    pos = np.array([[16 + 9.5, 16.0, 16.0], [16 - 9.5, 16, 16],
+                    [np.nextafter(np.float32(25.5), np.float32(30)), 16, 16]],
+                   np.float32)
+    assert list(pm.keep_mask(pos, 9.5, 32)) == [True, True, False]
+
+
+# ---------------------------------------------------------------- dynamics
+
+def test_free_particle_drift_integrates_schedule():
+    n = 16
+    sched = cz.schedule(n, 100.0, OM, OL, 0.02, 0.1, 10)
+    pos = np.array([[3.0, 5.0, 7.0]])
+    mom = np.array([[0.01, -0.02, 0.005]])
+    out = pm.run(pos, mom, np.array([0]), sched, n, OM, 1.0 / n**3)
+    coef = sum(sched["dtau"][k] * (0.5 / sched["a"][k] + 0.5 / sched["a"][k + 1])
+               for k in range(10))
+    np.testing.assert_allclose(out["pos"], pos + mom * coef, rtol=1e-12)
+    np.testing.assert_allclose(out["mom"], mom, atol=1e-15)
+
+
+def test_momentum_conserved_and_mass_bookkept():
+    n = 16
+    pos, mom, ids = ics.zeldovich(n, -2.0, None, 4, 0.02)
+    sched = cz.schedule(n, 250.0, OM, OL, 0.02, 1.0, 8)
+    out = pm.run(pos, mom, ids, sched, n, OM, 1.0, steps=4)
+    p0 = mom.astype(np.float64).sum(axis=0)
+    assert np.abs(out["mom"].sum(axis=0) - p0).max() < 1e-12 * np.abs(out["mom"]).sum()
+    assert len(out["ids"]) + len(out["lc_ids"]) == n**3
+
+
+def _plane_wave_growth(n, steps, a0=0.02, a1=0.3, eps=1e-3):
+    g = np.arange(n) + 0.5
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    q = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    psi = eps * np.sin(2 * np.pi * q[:, 0] / n)
+    pos = q.copy()
+    pos[:, 0] += psi
+    mom = np.zeros_like(pos)
+    mom[:, 0] = a0**2 * cz.E(a0, OM, OL) * cz.growth_f(a0, OM, OL) * psi
+    sched = cz.schedule(n, 250.0, OM, OL, a0, a1, steps)
+    out = pm.run(pos, mom, np.arange(len(pos)), sched, n, OM, 1.0)
+    sel = np.abs(psi) > 0.5 * eps
+    growth = np.median((out["pos"][sel, 0] - q[sel, 0]) / psi[sel])
+    return 1 - growth / (cz.growth_D(a1, OM, OL) / cz.growth_D(a0, OM, OL))
+
+
+def test_zeldovich_plane_wave_growth_converges_to_linear_theory():
+    """A small plane-wave displacement grows like D(a) (Zel'dovich regime);
+    the PM deficit of the fundamental mode vanishes as h^2."""
+    d16 = _plane_wave_growth(16, 100)
+    d32 = _plane_wave_growth(32, 100)
+    assert 0 < d32 < 0.03
+    assert 3.0 < d16 / d32 < 5.0
+
+
+def test_shrinking_run_bookkeeping():
+    n = 16
+    pos, mom, ids = ics.zeldovich(n, -2.0, None, 2, 0.5)
+    # tiny box so that the lightcone crosses it mid-run
+    sched = cz.schedule(n, 4000.0, OM, OL, 0.5, 1.0, 6)
+    out = pm.run(pos, mom, ids, sched, n, OM, 1.0)
+    assert len(out["ids"]) + len(out["lc_ids"]) == n**3
+    assert np.all(np.diff(out["n_active"]) <= 0)
+    assert sorted(np.concatenate([out["ids"], out["lc_ids"]])) == list(range(n**3))
+    R = sched["R"][-1]
+    assert np.all(np.abs(out["pos"] - n / 2).max(axis=1) <= R)
