@@ -1,0 +1,323 @@
+#!/usr/bin/env python3
+"""Throughput of the shrinking-domain PM step on GB300.
+
+One "step" = one pass of the whole hot path (half drift + CIC deposit,
+source + boundary values, multigrid Poisson solve to rtol, gradient + gather +
+kick + drift, lightcone shrink) over the active particles of one simulation.
+The workload is 256^3 particles on a 256^3 mesh, 2000 Mpc/h, Zel'dovich ICs
+from P(k) ~ k^-1.5 exp(-k^2/2k_c^2) (seed 1), steps uniform in a from 0.01 to
+1 in 200 steps; --steps K times the first K of them (default: all 200, so the
+shrinking phase is inside the timed region).
+
+value  = sum over timed steps of the active particle count / device time
+e2e    = the same through the C ABI with host buffers: each step copies the
+         particles host->device, steps, and copies them back
+Multi-GPU: independent replicas (one per rank, no collective on the data
+path); value = all ranks' particle-steps / max rank time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "pm256"
+METRIC = "particle-steps/s, PM step at 256^3 (mixed FP32/double-float multigrid)"
+UNIT = "particle-steps/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _ics():
+    from paper_1709_04703_gb300 import ics
+    return ics.workload_ics(WORKLOAD), ics.WORKLOADS[WORKLOAD]
+
+
+def _new_sim(pos, mom, ids, cfg, rtol, precision):
+    from paper_1709_04703_gb300.sim import Sim
+    return Sim(pos, mom, ids, cfg["n"], cfg["box"], cfg["a_init"], cfg["a_final"],
+               cfg["steps"], rtol=rtol, precision=precision, max_vcycles=100)
+
+
+def cpu_baseline(budget_s=20.0, n_sample=128):
+    """The FP64 oracle, as it stands, on a replica of the workload at n_sample^3
+    (same box, spectrum and seed) stepping from a_init until budget_s of CPU
+    time; particle-steps/s = n_sample^3 * steps / time."""
+    from oracle import cosmology as cz
+    from oracle import pm as opm
+    from paper_1709_04703_gb300 import ics
+    cfg = ics.WORKLOADS[WORKLOAD]
+    n = n_sample
+    pos, mom, ids = ics.zeldovich(n, cfg["alpha"], cfg["cutoff"], cfg["seed"], cfg["a_init"])
+    sched = cz.schedule(n, cfg["box"], 0.3, 0.7, cfg["a_init"], cfg["a_final"], cfg["steps"])
+    x, p = pos.astype(np.float64), mom.astype(np.float64)
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        x, p, _ = opm.step(x, p, k, sched, n, 0.3, 1.0)
+        k += 1
+        if time.perf_counter() - t0 >= budget_s or k >= cfg["steps"]:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n**3 * k / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{k} oracle steps (numpy FP64, exact FFT Poisson solve) of a "
+                      f"{n}^3-particle replica of the 256^3 workload from a=0.01, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle as the reference arm, on the host cores."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    # bounded sample: a 32^3 replica per step keeps K+W steps to about a minute
+    from oracle import cosmology as cz
+    from oracle import pm as opm
+    from paper_1709_04703_gb300 import ics
+    cfg = ics.WORKLOADS[WORKLOAD]
+    n = 32 if args.steps + args.warmup > 60 else 64
+    pos, mom, ids = ics.zeldovich(n, cfg["alpha"], cfg["cutoff"], cfg["seed"], cfg["a_init"])
+    sched = cz.schedule(n, cfg["box"], 0.3, 0.7, cfg["a_init"], cfg["a_final"], cfg["steps"])
+    x, p = pos.astype(np.float64), mom.astype(np.float64)
+    ksteps = min(args.steps, cfg["steps"])
+    for k in range(args.warmup):
+        opm.step(x, p, k % cfg["steps"], sched, n, 0.3, 1.0)
+    t0 = time.perf_counter()
+    for k in range(ksteps):
+        x, p, _ = opm.step(x, p, k, sched, n, 0.3, 1.0)
+    dt = time.perf_counter() - t0
+    val = n**3 * ksteps / dt
+    sample = (f"oracle (numpy FP64) steps 0..{ksteps - 1} of the 256^3 schedule on a "
+              f"{n}^3-particle replica (same box, spectrum, seed)")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": ksteps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / max(ksteps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_mesh": 256, "n_particles": 256**3,
+                       "box_mpch": 2000.0, "sample_mesh": n},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_1709_04703_gb300 import _lib as L
+    from paper_1709_04703_gb300.sim import pack
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    (pos, mom, ids), cfg = _ics()
+    K = min(args.steps, cfg["steps"])
+    lib = L.load()
+
+    # warm-up: W steps on a throw-away context (same ICs)
+    sim = _new_sim(pos, mom, ids, cfg, args.rtol, args.precision)
+    sim.step(min(args.warmup, cfg["steps"]))
+    sim.close()
+    torch.cuda.synchronize()
+
+    # timed: K steps from the ICs, device-resident inputs
+    sim = _new_sim(pos, mom, ids, cfg, args.rtol, args.precision)
+    lib.pm_profile(sim._ctx, 1)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = lib.pm_launch_count()
+    ps0 = sim.stats()["particle_steps"]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        sim.step(K)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    st = sim.stats()
+    psteps = st["particle_steps"] - ps0
+    launches = lib.pm_launch_count() - l0
+    prof = {}
+    import ctypes as C
+    for c, name in enumerate(L.PROF_CLASSES):
+        t, g, b = C.c_double(), C.c_int64(), C.c_double()
+        lib.pm_profile_read(sim._ctx, c, C.byref(t), C.byref(g), C.byref(b))
+        prof[name] = {"ms": t.value, "groups": g.value, "bytes": b.value}
+    vstats = {"vcycles_total": st["vcycles_total"], "n_active_end": st["n_active"],
+              "n_lightcone": st["n_lightcone"], "escaped": st["escaped"]}
+    sim.close()
+
+    # end to end through the C ABI with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        sim = _new_sim(pos, mom, ids, cfg, args.rtol, args.precision)
+        p4, m4 = pack(pos, mom, ids)
+        hp = torch.from_numpy(p4).pin_memory()
+        hm = torch.from_numpy(m4).pin_memory()
+        n_act = len(pos)
+        h2d = d2h = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ps = 0
+        for _ in range(K):
+            L.check(lib.pm_set_particles(sim._ctx, C.c_void_p(hp.data_ptr()),
+                                         C.c_void_p(hm.data_ptr()), n_act, 1), sim._ctx)
+            h2d += 32 * n_act
+            ps += n_act
+            sim.step(1)
+            n_act = sim.get_particles_host(hp, hm)
+            d2h += 32 * n_act
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        sim.close()
+        e2e = {"value": ps / dt, "unit": UNIT, "h2d_bytes_per_step": h2d // K,
+               "d2h_bytes_per_step": d2h // K}
+
+    # aggregate over ranks: sum of particle-steps, max of time
+    tot_ps, max_ms = float(psteps), float(ms)
+    if ws > 1:
+        t = torch.tensor([tot_ps], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t)
+        m = torch.tensor([max_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(m, op=dist.ReduceOp.MAX)
+        tot_ps, max_ms = t.item(), m.item()
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return 0
+
+    peak, peak_kind = _peaks()
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
+    kernels = {k: {"ms": round(v["ms"], 3), "share": round(v["ms"] / max(1e-9, sum(
+        x["ms"] for x in prof.values())), 4), "GB/s": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1)
+        if v["ms"] > 0 else None} for k, v in prof.items()}
+    line = {
+        "metric": METRIC, "value": tot_ps / (max_ms * 1e-3), "unit": UNIT, "n_gpus": ws,
+        "steps": K, "warmup": args.warmup, "ms_per_step": max_ms / K,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+df32" if args.precision == "mixed" else "f32",
+        "data": "synthetic (seeded Zel'dovich ICs)",
+        "config": {"workload": WORKLOAD, "n_mesh": 256, "n_particles": 256**3,
+                   "box_mpch": 2000.0, "a": [cfg["a_init"], cfg["a_final"]],
+                   "schedule_steps": cfg["steps"], "rtol": args.rtol,
+                   "precision": args.precision, "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (particles 537 MB, mesh 134 MB)"},
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None},
+        "kernels": kernels,
+        "solver": vstats,
+        "clocks": clk.summary(),
+        "gpu_launches": int(launches),
+    }
+    if e2e is not None:
+        line["e2e"] = e2e
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_budget)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--rtol", type=float, default=1e-7)
+    ap.add_argument("--precision", choices=["mixed", "fp32"], default="mixed")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    from paper_1709_04703_gb300 import build
+    build.build()
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

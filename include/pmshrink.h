@@ -1,0 +1,236 @@
+/*
+ * pmshrink — shrinking-domain particle-mesh step on one GB300 (sm_103a).
+ *
+ * C ABI of the library libpmshrink.so.  The method is Llinares (2017),
+ * "The shrinking domain framework I" (arXiv:1709.04703):
+ *   - equations of motion dx/dtau = p/a, dp/dtau = -a grad(Phi)      Sec. 2.1, Eqs. 1-2
+ *   - Poisson's equation lap(Phi) = (3 H0^2 Om / 2a) delta           Sec. 2.1, Eq. 3
+ *   - synchronised (drift-kick-drift) leapfrog                        Sec. 2.2
+ *   - CIC mass assignment and force interpolation (same kernel)       Sec. 2.4
+ *   - active cells / particles restricted to the observer's past
+ *     lightcone, recomputed at the end of every step                 Sec. 2.4, Table 2
+ *   - periodic boundaries until the lightcone reaches the box edge,
+ *     open boundaries afterwards                                      Sec. 3, Table 1
+ *
+ * Units.  Positions are in cells of the n_mesh^3 mesh measured from the mesh
+ * corner (cell (i,j,k) is centred at (i+.5, j+.5, k+.5)); conformal time in
+ * 1/H0; momentum p = a dx/dtau in cells*H0; the potential in (cells*H0)^2.
+ * Grids are row-major [z][y][x].
+ *
+ * Particle records are float4:  pos4 = (x, y, z, id) with the int32 particle
+ * id stored bit-for-bit in .w;  mom4 = (px, py, pz, a_cross) where a_cross is
+ * only meaningful in lightcone records (expansion factor at which the particle
+ * left the domain).
+ *
+ * Errors.  Every call returns a pm_status; nothing throws or aborts.
+ * pm_last_error(ctx) gives a text description of the last failure of that
+ * context (pm_last_error(NULL) the last failure of a context-free call).
+ *
+ * Streams.  Calls that take a context are ordered on the CUDA stream given to
+ * pm_init; calls that return host scalars synchronise that stream.
+ */
+#ifndef PMSHRINK_H
+#define PMSHRINK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PM_OK = 0,
+  PM_EINVAL = 1,     /* bad argument or configuration */
+  PM_ENOMEM = 2,     /* device or pinned-host allocation failed */
+  PM_ECUDA = 3,      /* a CUDA call or kernel launch failed */
+  PM_ENOCONV = 4,    /* a Poisson solve did not reach rtol in max_vcycles */
+  PM_EOVERFLOW = 5,  /* a fixed-point cell count exceeded 2^62 */
+  PM_ETIMEOUT = 6    /* a bounded device-side wait gave up */
+} pm_status;
+
+enum { PM_MIXED = 0, PM_FP32_PLAIN = 1 };               /* pm_config.precision */
+enum { PM_GUESS_WARM = 0, PM_GUESS_ZERO = 1 };          /* pm_config.guess */
+enum { PM_BC_PAPER = 0, PM_BC_OPEN = 1, PM_BC_PERIODIC = 2 };  /* pm_config.bc */
+
+typedef struct {
+  int32_t n_mesh;        /* cells per side, of the form 2^j or 3*2^j, 4..1024 */
+  int64_t n_particles;   /* particle count N at the start of the run */
+  double box_mpch;       /* comoving side of the initial box, Mpc/h */
+  double omega_m;        /* flat background: omega_m + omega_l = 1 expected */
+  double omega_l;
+  double a_init;         /* first expansion factor */
+  double a_final;        /* last expansion factor */
+  int32_t n_steps;       /* steps uniform in a (Sec. 3) */
+  double rtol;           /* relative residual ||f - A Phi||_2 / ||f||_2 per solve */
+  int32_t max_vcycles;   /* V-cycles allowed per solve before PM_ENOCONV */
+  int32_t precision;     /* PM_MIXED: FP32 V-cycles inside a double-float
+                            defect-correction loop; PM_FP32_PLAIN: FP32 only */
+  int32_t guess;         /* PM_GUESS_WARM: previous step's Phi; PM_GUESS_ZERO */
+  int32_t bc;            /* PM_BC_PAPER: periodic until the lightcone reaches
+                            the box edge, open afterwards; PM_BC_OPEN /
+                            PM_BC_PERIODIC force one kind for the whole run */
+  int32_t shrink;        /* 1: drop particles that leave the keep cube (into
+                            the lightcone buffer); 0: keep everything */
+  double buffer_cells;   /* keep half-width R = chi(a)/cell + buffer_cells */
+  int32_t store_forces;  /* 1: keep grad(Phi) at each particle of the last step */
+} pm_config;
+
+/* Fill *cfg with defaults: 32^3 mesh and particles, 250 Mpc/h, Om=0.3,
+ * OL=0.7, a 0.02 -> 1 in 20 steps, rtol 1e-7, 50 V-cycles, mixed precision,
+ * warm start, paper boundary conditions, shrinking on, buffer 1 cell. */
+void pm_config_default(pm_config* cfg);
+
+typedef struct pm_ctx pm_ctx;
+
+/* Create a simulation context.  pos4/mom4 hold cfg->n_particles float4
+ * records (layout above); they are copied (host_mem = 1: host pointers,
+ * pinned or pageable; host_mem = 0: device pointers).  The context owns all
+ * device state it allocates; stream is a cudaStream_t (NULL = legacy default
+ * stream).  The step schedule (a_k, dtau_k, a_half_k, chi_k) is computed here
+ * on the host in FP64.  Errors: PM_EINVAL (n_mesh not 2^j / 3*2^j, N = 0,
+ * positions not representable), PM_ENOMEM, PM_ECUDA.  *out is NULL on error. */
+pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
+                  int32_t host_mem, void* stream, pm_ctx** out);
+
+/* Advance n_steps steps in the order of Table 2 (Sec. 2.4): half drift,
+ * CIC deposit, Poisson solve (Sec. 2.1, Eq. 3), gradient + CIC gather, kick,
+ * half drift, lightcone shrink (Sec. 2.4).  Stops early with PM_EINVAL past
+ * the last step of the schedule, PM_ENOCONV if a solve fails to converge,
+ * PM_EOVERFLOW on fixed-point overflow.  Synchronises the stream once per
+ * V-cycle (convergence test) and once per shrink (new active count). */
+pm_status pm_step(pm_ctx* ctx, int32_t n_steps);
+
+/* Drop particles outside the keep cube of expansion factor a (Sec. 2.4:
+ * max_d |x_d - c| > chi(a)/cell + buffer, c the box centre), appending them,
+ * in their current order, to the lightcone buffer with a_cross = a; the
+ * survivors keep their relative order.  A no-op while the keep cube still
+ * covers the periodic box.  Writes the new active count to *n_active_out
+ * (may be NULL).  Synchronises the stream. */
+pm_status pm_shrink(pm_ctx* ctx, double a, int64_t* n_active_out);
+
+/* Solve sum_nb(Phi) - 6 Phi = S(a) delta on the context's whole n^3 mesh
+ * (Sec. 2.1, Eq. 3; S = 3 Om / (2a), cell units) with bc = PM_BC_OPEN
+ * (Dirichlet values from the monopole+dipole+quadrupole expansion about the
+ * box centre at one layer of ghost-cell centres) or PM_BC_PERIODIC (zero-mean
+ * gauge on output).  delta_dev: n^3 doubles [z][y][x] (device).  phi_out_dev:
+ * n^3 floats (device), the FP32 rounding of the solution; phi64_out_dev
+ * (device, may be NULL): the same as doubles (hi + lo of the double-float
+ * state).  Starts from zero and iterates to the context's rtol with its
+ * precision setting; *vcycles_out and *resid_out (may be NULL) receive the
+ * V-cycles used and the final relative residual.  Does not touch the
+ * particles; overwrites the context's potential, which the next pm_step then
+ * takes as its warm start.  Errors: PM_EINVAL, PM_ENOCONV, PM_ECUDA. */
+pm_status pm_potential(pm_ctx* ctx, const double* delta_dev, double a, int32_t bc,
+                       float* phi_out_dev, double* phi64_out_dev,
+                       int32_t* vcycles_out, double* resid_out);
+
+/* Power spectrum of n particles (pos4_dev, device) with positions in cells of
+ * an n_mesh^3 periodic mesh of side box (Mpc/h): int64 fixed-point CIC
+ * density, R2C FFT, |delta_k|^2 L^3/Ng^6 divided by the squared CIC window
+ * prod_d sinc^2(k_d h/2), minus the shot noise L^3/n (Sec. 2.4: power
+ * spectrum with discreteness correction).  Linear bins of width
+ * k_f = 2 pi/L: bin b holds |k|/k_f in [b+.5, b+1.5).  Host outputs of n_bins
+ * entries: mean |k| (h/Mpc), mean P ((Mpc/h)^3), number of modes.  Allocates
+ * its own scratch; synchronises stream.  subtract_shot = 0 omits the L^3/n
+ * term (lattice-based particle sets). */
+pm_status pm_power_spectrum(const float* pos4_dev, int64_t n, double box,
+                            int32_t n_mesh, int32_t n_bins, int32_t subtract_shot,
+                            double* k_out, double* pk_out, double* modes_out,
+                            void* stream);
+
+/* Fixed-point CIC deposit of n particles into rho_dev (n_mesh^3 int64,
+ * device, accumulated into: clear it first) over the cube [lo, lo+side)^3
+ * (Sec. 2.4 footnote: CIC).  On the float position u per axis:
+ * i = floor(u - .5), dq = floor((u - .5) 2^16) - i 2^16; weights 2^16 - dq on
+ * node i and dq on node i+1; their product is added as an int64.  periodic=1
+ * wraps nodes mod n_mesh (then lo = 0, side = n_mesh); otherwise a particle
+ * with a node outside the cube deposits nothing and is counted in
+ * *escaped_out (host, may be NULL).  If mom4_dev is not NULL the particles
+ * are first drifted in place, x = fl(x + fl(p * drift_coef)) in float32
+ * (Sec. 2.2, first DKD line), wrapped into [0, n_mesh) when periodic.
+ * Synchronises stream only when escaped_out is not NULL. */
+pm_status pm_deposit(float* pos4_dev, const float* mom4_dev, int64_t n,
+                     float drift_coef, int32_t n_mesh, int32_t lo, int32_t side,
+                     int32_t periodic, int64_t* rho_dev, int64_t* escaped_out,
+                     void* stream);
+
+typedef struct {
+  int32_t step;          /* steps completed */
+  double a;              /* current expansion factor */
+  int64_t n_active;      /* particles inside the domain */
+  int64_t n_lightcone;   /* particles in the lightcone buffer */
+  int32_t cube_lo;       /* active mesh cube of the last step: [lo, lo+side)^3 */
+  int32_t cube_side;
+  int32_t periodic;      /* boundary kind of the last step */
+  int32_t vcycles_last;  /* V-cycles of the last solve */
+  int64_t vcycles_total; /* V-cycles since pm_init */
+  double resid_last;     /* final relative residual of the last solve */
+  int64_t escaped;       /* particle-steps skipped because a CIC node left the cube */
+  int64_t particle_steps;/* sum over completed steps of the active count */
+} pm_stats_t;
+
+pm_status pm_stats(pm_ctx* ctx, pm_stats_t* out);
+
+/* Copy the schedule (n_steps + 1 entries each, host arrays, any may be NULL):
+ * a_k, dtau_k (conformal step k -> k+1, last entry 0), a_half_k (a at the
+ * conformal midpoint of step k, last entry 0), chi_k (Mpc/h). */
+pm_status pm_schedule(pm_ctx* ctx, double* a, double* dtau, double* a_half,
+                      double* chi);
+
+/* Active particles (n_active float4 records each) to host (host_mem = 1) or
+ * device buffers; either pointer may be NULL.  Synchronises the stream. */
+pm_status pm_get_particles(pm_ctx* ctx, float* pos4, float* mom4,
+                           int32_t host_mem, int64_t* n_active_out);
+
+/* Replace the active particles by n records (n <= cfg.n_particles). */
+pm_status pm_set_particles(pm_ctx* ctx, const float* pos4, const float* mom4,
+                           int64_t n, int32_t host_mem);
+
+/* Lightcone records (pos4, mom4 with .w = a_cross). */
+pm_status pm_get_lightcone(pm_ctx* ctx, float* pos4, float* mom4,
+                           int32_t host_mem, int64_t* n_out);
+
+/* grad(Phi) at each active particle of the last step (float4, .w unused),
+ * in the particle order at the end of that step's kick, before the shrink.
+ * Needs cfg.store_forces = 1. */
+pm_status pm_get_forces(pm_ctx* ctx, float* f4, int32_t host_mem, int64_t* n_out);
+
+/* Copy the current potential on the active cube plus its ghost layer,
+ * (side+2)^3 doubles [z][y][x], to host (hi + lo of the double-float state). */
+pm_status pm_get_potential(pm_ctx* ctx, double* phi_host, int32_t* lo_out,
+                           int32_t* side_out);
+
+/* Per-kernel-class timing with CUDA events recorded on the context's stream
+ * around the launches of each class, read back at the step's existing sync
+ * points.  Classes: */
+enum {
+  PM_PROF_DEPOSIT = 0,  /* half drift + CIC deposit                         */
+  PM_PROF_SOURCE,       /* counts -> double-float source (+ moments)        */
+  PM_PROF_BOUNDARY,     /* open-boundary ghost layer                        */
+  PM_PROF_SMOOTH0,      /* RB-GS sweeps on the finest level                 */
+  PM_PROF_TRANSFER0,    /* finest-level residual+restriction, prolongation  */
+  PM_PROF_COARSE,       /* everything on levels >= 1                        */
+  PM_PROF_DEFECT,       /* double-float residual + norm                     */
+  PM_PROF_CORRECT,      /* Phi += e                                         */
+  PM_PROF_GATHER,       /* gradient + gather + kick + drift + keep flags    */
+  PM_PROF_COMPACT,      /* scan + stable scatter                            */
+  PM_PROF_N
+};
+/* enable = 1 starts (and zeroes) the counters, 0 stops them. */
+pm_status pm_profile(pm_ctx* ctx, int32_t enable);
+/* Accumulated device time (ms), timed launch groups, and algorithmic bytes
+ * (the minimal DRAM traffic of those launches) of one class. */
+pm_status pm_profile_read(pm_ctx* ctx, int32_t cls, double* ms, int64_t* groups,
+                          double* bytes);
+
+/* Kernel launches made by this library in this process so far. */
+int64_t pm_launch_count(void);
+
+const char* pm_last_error(const pm_ctx* ctx);
+void pm_destroy(pm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PMSHRINK_H */

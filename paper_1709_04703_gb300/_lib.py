@@ -1,0 +1,106 @@
+"""ctypes binding of libpmshrink.so (argument marshalling only).
+
+Every function here forwards to the C ABI declared in include/pmshrink.h;
+all arithmetic of the PM step runs in the library's CUDA kernels.  Loading
+fails loudly when the library has not been built: there is no CPU fallback.
+"""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpmshrink.so")
+
+PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_ENOCONV, PM_EOVERFLOW, PM_ETIMEOUT = range(7)
+PM_MIXED, PM_FP32_PLAIN = 0, 1
+PM_GUESS_WARM, PM_GUESS_ZERO = 0, 1
+PM_BC_PAPER, PM_BC_OPEN, PM_BC_PERIODIC = 0, 1, 2
+
+STATUS_NAMES = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ECUDA",
+                4: "PM_ENOCONV", 5: "PM_EOVERFLOW", 6: "PM_ETIMEOUT"}
+
+# every entry point declared in include/pmshrink.h
+EXPORTED = [
+    "pm_config_default", "pm_init", "pm_step", "pm_shrink", "pm_potential",
+    "pm_power_spectrum", "pm_deposit", "pm_stats", "pm_schedule",
+    "pm_get_particles", "pm_set_particles", "pm_get_lightcone", "pm_get_forces",
+    "pm_get_potential", "pm_profile", "pm_profile_read", "pm_launch_count", "pm_last_error",
+    "pm_destroy",
+]
+PROF_CLASSES = ["deposit", "source", "boundary", "smooth0", "transfer0", "coarse",
+                "defect", "correct", "gather", "compact"]
+
+
+class PmConfig(C.Structure):
+    _fields_ = [
+        ("n_mesh", C.c_int32), ("n_particles", C.c_int64), ("box_mpch", C.c_double),
+        ("omega_m", C.c_double), ("omega_l", C.c_double), ("a_init", C.c_double),
+        ("a_final", C.c_double), ("n_steps", C.c_int32), ("rtol", C.c_double),
+        ("max_vcycles", C.c_int32), ("precision", C.c_int32), ("guess", C.c_int32),
+        ("bc", C.c_int32), ("shrink", C.c_int32), ("buffer_cells", C.c_double),
+        ("store_forces", C.c_int32),
+    ]
+
+
+class PmStats(C.Structure):
+    _fields_ = [
+        ("step", C.c_int32), ("a", C.c_double), ("n_active", C.c_int64),
+        ("n_lightcone", C.c_int64), ("cube_lo", C.c_int32), ("cube_side", C.c_int32),
+        ("periodic", C.c_int32), ("vcycles_last", C.c_int32),
+        ("vcycles_total", C.c_int64), ("resid_last", C.c_double),
+        ("escaped", C.c_int64), ("particle_steps", C.c_int64),
+    ]
+
+
+class PmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load():
+    """Load the shared library once; raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it with "
+            "`python -m paper_1709_04703_gb300.build` (nvcc, sm_103a)")
+    lib = C.CDLL(LIB_PATH)
+    P, I32, I64, D, F = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_float
+    sig = {
+        "pm_config_default": (None, [C.POINTER(PmConfig)]),
+        "pm_init": (I32, [C.POINTER(PmConfig), P, P, I32, P, C.POINTER(P)]),
+        "pm_step": (I32, [P, I32]),
+        "pm_shrink": (I32, [P, D, C.POINTER(I64)]),
+        "pm_potential": (I32, [P, P, D, I32, P, P, C.POINTER(I32), C.POINTER(D)]),
+        "pm_power_spectrum": (I32, [P, I64, D, I32, I32, I32, P, P, P, P]),
+        "pm_deposit": (I32, [P, P, I64, F, I32, I32, I32, I32, P, C.POINTER(I64), P]),
+        "pm_stats": (I32, [P, C.POINTER(PmStats)]),
+        "pm_schedule": (I32, [P, P, P, P, P]),
+        "pm_get_particles": (I32, [P, P, P, I32, C.POINTER(I64)]),
+        "pm_set_particles": (I32, [P, P, P, I64, I32]),
+        "pm_get_lightcone": (I32, [P, P, P, I32, C.POINTER(I64)]),
+        "pm_get_forces": (I32, [P, P, I32, C.POINTER(I64)]),
+        "pm_get_potential": (I32, [P, P, C.POINTER(I32), C.POINTER(I32)]),
+        "pm_profile": (I32, [P, I32]),
+        "pm_profile_read": (I32, [P, I32, C.POINTER(D), C.POINTER(I64), C.POINTER(D)]),
+        "pm_launch_count": (I64, []),
+        "pm_last_error": (C.c_char_p, [P]),
+        "pm_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(code, ctx=None):
+    if code != PM_OK:
+        msg = load().pm_last_error(ctx)
+        raise PmError(code, msg.decode() if msg else "")

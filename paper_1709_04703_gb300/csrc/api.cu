@@ -1,0 +1,995 @@
+// C ABI of libpmshrink: context, step orchestration (Table 2 order), the
+// host-side FP64 schedule (conformal time, lightcone distance), and the
+// standalone solve / deposit / power-spectrum entry points.
+#include <cufft.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pm_kernels.cuh"
+
+using namespace pm;
+
+namespace {
+std::atomic<long long> g_launches{0};
+}  // namespace
+
+void pm::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+
+constexpr double C_OVER_H0 = 2997.92458;  // Mpc/h
+constexpr int SRC_GRID = 1216;            // 152 SMs x 8 blocks
+constexpr int COARSE_SWEEPS = 40;
+
+// ---------------------------------------------------------------------------
+// FP64 cosmology on the host.  tau(a) = int_0^a da'/(a'^2 E), H0 = 1, with
+// a' = u^2: tau = int_0^sqrt(a) 2 du / sqrt(om + ol u^6), a smooth integrand
+// integrated by composite 8-point Gauss-Legendre on 64 panels.
+// ---------------------------------------------------------------------------
+struct Quad {
+  double x[8], w[8];
+  Quad() {
+    const int m = 8;
+    for (int i = 0; i < m; ++i) {
+      double z = std::cos(M_PI * (i + 0.75) / (m + 0.5));
+      double dp = 0.0;
+      for (int it = 0; it < 100; ++it) {
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= m; ++k) {
+          double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+          p0 = p1;
+          p1 = p2;
+        }
+        dp = m * (z * p1 - p0) / (z * z - 1.0);
+        double dz = p1 / dp;
+        z -= dz;
+        if (std::fabs(dz) < 1e-16) break;
+      }
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= m; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = m * (z * p1 - p0) / (z * z - 1.0);
+      x[i] = z;
+      w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+  }
+};
+
+double tau_of_a(double a, double om, double ol) {
+  static const Quad q;
+  const int panels = 64;
+  double U = std::sqrt(a), hsz = U / panels, tot = 0.0;
+  for (int p = 0; p < panels; ++p) {
+    double c = (p + 0.5) * hsz, hw = 0.5 * hsz;
+    for (int i = 0; i < 8; ++i) {
+      double u = c + hw * q.x[i];
+      tot += hw * q.w[i] * 2.0 / std::sqrt(om + ol * u * u * u * u * u * u);
+    }
+  }
+  return tot;
+}
+
+double a_of_tau(double t, double om, double ol) {
+  double lo = 1e-12, hi = 4.0;
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (tau_of_a(mid, om, ol) < t) lo = mid; else hi = mid;
+    if (hi - lo <= 4e-16 * hi) break;
+  }
+  return 0.5 * (lo + hi);
+}
+
+bool mg_size_ok(int n) {
+  if (n < 4) return false;
+  while (n % 2 == 0) n /= 2;
+  return n == 1 || n == 3;
+}
+
+int mg_round_up(int m) {
+  int best = 1 << 30;
+  for (int p = 1; p < (1 << 29); p *= 2) {
+    if (p >= m) { best = std::min(best, p); break; }
+  }
+  for (int p = 3; p < (1 << 29); p *= 2) {
+    if (p >= m) { best = std::min(best, p); break; }
+  }
+  return best;
+}
+
+std::string g_err;  // last error of a context-free call
+
+}  // namespace
+
+struct pm_ctx {
+  pm_config cfg;
+  cudaStream_t st = nullptr;
+  int n = 0, P = 0;
+  long long N0 = 0;
+  std::vector<double> a, dtau, a_half, chi, R;
+  int step = 0;
+
+  float4 *pos = nullptr, *mom = nullptr, *pos2 = nullptr, *mom2 = nullptr;
+  float4 *lc_pos = nullptr, *lc_mom = nullptr, *forces = nullptr;
+  long long n_active = 0, n_lc = 0;
+  bool forces_valid = false;
+  long long forces_n = 0;
+  unsigned char* flags = nullptr;
+  unsigned int* block_keep = nullptr;
+  unsigned long long* keep_off = nullptr;
+
+  unsigned long long* rho = nullptr;
+  float *phi_hi = nullptr, *phi_lo = nullptr, *f_hi = nullptr, *f_lo = nullptr;
+  std::vector<float*> lu, lb;   // level arrays (compact padded); level 0 for e / r
+  std::vector<int> ls;          // level sides of the current cube
+
+  double* partial = nullptr;    // per-block FP64 partial sums
+  void* partial_m = nullptr;    // per-block int128 moments
+  unsigned int* counter = nullptr;
+  double* d_scal = nullptr;     // [0] ||f||^2, [1..10] moments, [11] ||r||^2, [12] sum phi
+  double* bgm = nullptr;        // background moments (10)
+  unsigned long long* d_cnt = nullptr;  // [0] n_keep, [1] escaped
+  int* d_overflow = nullptr;
+  double* h_scal = nullptr;     // pinned mirrors
+  unsigned long long* h_cnt = nullptr;
+
+  int lo = 0, s = 0, periodic = 1;
+  bool cube_valid = false;
+
+  // per-class event timing (pm_profile)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev;
+  int ev_next = 0;
+  struct Pend { int cls, e0, e1; double bytes; };
+  std::vector<Pend> pend;
+  double prof_ms[PM_PROF_N] = {0};
+  long long prof_groups[PM_PROF_N] = {0};
+  double prof_bytes[PM_PROF_N] = {0};
+
+  int vcycles_last = 0;
+  long long vcycles_total = 0;
+  double resid_last = 0.0;
+  long long particle_steps = 0;
+  std::string err;
+};
+
+namespace {
+
+pm_status fail(pm_ctx* c, pm_status code, const std::string& msg) {
+  if (c) c->err = msg; else g_err = msg;
+  return code;
+}
+
+#define CK(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return fail(ctx, PM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define CKL()                                                                      \
+  do {                                                                             \
+    cudaError_t e_ = cudaGetLastError();                                           \
+    if (e_ != cudaSuccess)                                                         \
+      return fail(ctx, PM_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+Grid full_view(const pm_ctx* c, float* base, int lo, int s) {
+  Grid g;
+  g.sy = c->P;
+  g.sz = c->P * c->P;
+  g.s = s;
+  g.base = base + (lo + 1) + (lo + 1) * g.sy + (lo + 1) * g.sz;
+  return g;
+}
+
+Grid compact_view(float* base, int s) {
+  Grid g;
+  g.sy = s + 2;
+  g.sz = (s + 2) * (s + 2);
+  g.s = s;
+  g.base = base + 1 + g.sy + g.sz;
+  return g;
+}
+
+bool is_open(const pm_ctx* c, double R) {
+  if (c->cfg.bc == PM_BC_OPEN) return true;
+  if (c->cfg.bc == PM_BC_PERIODIC) return false;
+  return R <= 0.5 * c->n - 1.0;
+}
+
+// Active mesh cube for keep half-width R (see pm_config.bc).
+void geometry(const pm_ctx* c, double R, int* lo, int* s, int* periodic) {
+  const int n = c->n;
+  if (!is_open(c, R)) { *lo = 0; *s = n; *periodic = 1; return; }
+  *periodic = 0;
+  if (R > 0.5 * n - 1.0) { *lo = 0; *s = n; return; }
+  int m = (int)std::ceil(R) + 1;
+  int side = std::min(mg_round_up(2 * m), n);
+  *s = side;
+  *lo = n / 2 - side / 2;
+}
+
+// Exact float bounds [klo, khi] with x in it  <=>  |(double)x - c| <= R.
+void keep_bounds(double c, double R, float* klo, float* khi) {
+  float l = (float)(c - R);
+  while ((double)l - c < -R) l = std::nextafter(l, INFINITY);
+  while ((double)std::nextafter(l, -INFINITY) - c >= -R) l = std::nextafter(l, -INFINITY);
+  float h = (float)(c + R);
+  while ((double)h - c > R) h = std::nextafter(h, -INFINITY);
+  while ((double)std::nextafter(h, INFINITY) - c <= R) h = std::nextafter(h, INFINITY);
+  *klo = l;
+  *khi = h;
+}
+
+pm_status set_cube(pm_ctx* ctx, int lo, int s, int periodic, double R) {
+  bool same = ctx->cube_valid && lo == ctx->lo && s == ctx->s && periodic == ctx->periodic;
+  ctx->lo = lo;
+  ctx->s = s;
+  ctx->periodic = periodic;
+  ctx->cube_valid = true;
+  // background moments over the cells whose centre is in the keep cube
+  const int n = ctx->n;
+  int b0 = 0, b1 = n - 1;
+  if (!periodic) {
+    double c = 0.5 * n;
+    b0 = std::max(lo, (int)std::ceil(c - R - 0.5));
+    b1 = std::min(lo + s - 1, (int)std::floor(c + R - 0.5));
+  }
+  double S1 = 0.0, S2 = 0.0;
+  long long L = b1 >= b0 ? b1 - b0 + 1 : 0;
+  for (int i = b0; i <= b1; ++i) {
+    double y = i + 0.5 - 0.5 * n;
+    S1 += y;
+    S2 += y * y;
+  }
+  double L2 = (double)L * L, L3 = L2 * L;
+  double h[10] = {L3, L2 * S1, L2 * S1, L2 * S1, L2 * S2, L2 * S2, L2 * S2,
+                  L * S1 * S1, L * S1 * S1, L * S1 * S1};
+  CK(cudaMemcpyAsync(ctx->bgm, h, sizeof(h), cudaMemcpyHostToDevice, ctx->st));
+  if (same) return PM_OK;
+  // multigrid level sides: halve while > 4
+  ctx->ls.clear();
+  int sl = s;
+  ctx->ls.push_back(sl);
+  while (sl > 4 && sl % 2 == 0) {
+    sl /= 2;
+    ctx->ls.push_back(sl);
+  }
+  if (sl > 8) return fail(ctx, PM_EINVAL, "cube side does not coarsen to <= 8");
+  for (size_t l = 0; l < ctx->ls.size(); ++l) {
+    size_t bytes = sizeof(float) * (size_t)(ctx->ls[l] + 2) * (ctx->ls[l] + 2) * (ctx->ls[l] + 2);
+    CK(cudaMemsetAsync(ctx->lu[l], 0, bytes, ctx->st));
+    CK(cudaMemsetAsync(ctx->lb[l], 0, bytes, ctx->st));
+  }
+  return PM_OK;
+}
+
+// Event pairs around launch groups; elapsed times are collected after the
+// next stream synchronisation.
+void prof_flush(pm_ctx* ctx) {
+  for (const auto& p : ctx->pend) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->ev[p.e0], ctx->ev[p.e1]) == cudaSuccess) {
+      ctx->prof_ms[p.cls] += ms;
+      ctx->prof_groups[p.cls] += 1;
+      ctx->prof_bytes[p.cls] += p.bytes;
+    }
+  }
+  ctx->pend.clear();
+  ctx->ev_next = 0;
+}
+
+int prof_begin(pm_ctx* ctx) {
+  if (!ctx->prof_on) return -1;
+  if (ctx->ev_next + 2 > (int)ctx->ev.size()) {
+    cudaStreamSynchronize(ctx->st);
+    prof_flush(ctx);
+  }
+  int e = ctx->ev_next++;
+  cudaEventRecord(ctx->ev[e], ctx->st);
+  return e;
+}
+
+void prof_end(pm_ctx* ctx, int cls, int e0, double bytes) {
+  if (e0 < 0) return;
+  int e1 = ctx->ev_next++;
+  cudaEventRecord(ctx->ev[e1], ctx->st);
+  ctx->pend.push_back({cls, e0, e1, bytes});
+}
+
+pm_status sync_read(pm_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->h_scal, ctx->d_scal, sizeof(double) * 16, cudaMemcpyDeviceToHost,
+                     ctx->st));
+  CK(cudaMemcpyAsync(ctx->h_cnt, ctx->d_cnt, sizeof(unsigned long long) * 4,
+                     cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (ctx->prof_on) prof_flush(ctx);
+  return PM_OK;
+}
+
+// V(2,2) cycle on level 0 grids (u0, b0) of the current cube.
+pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0) {
+  const int per = ctx->periodic;
+  const int L = (int)ctx->ls.size() - 1;
+  std::vector<Grid> U(L + 1), B(L + 1);
+  U[0] = u0;
+  B[0] = b0;
+  for (int l = 1; l <= L; ++l) {
+    U[l] = compact_view(ctx->lu[l], ctx->ls[l]);
+    B[l] = compact_view(ctx->lb[l], ctx->ls[l]);
+  }
+  const double c0 = (double)ctx->s * ctx->s * ctx->s;
+  // algorithmic bytes: a colour sweep reads u (4 B/cell) and half of b, writes
+  // half of u (8 B/cell per colour); residual+restriction reads u and b
+  // (8 B/fine cell) and writes the coarse b and u (1 B/fine cell);
+  // prolongation reads the coarse u (0.5) and updates the fine u (8).
+  float h2 = 1.0f;
+  int ec = -1;
+  for (int l = 0; l < L; ++l) {
+    int e = l == 0 ? prof_begin(ctx) : -1;
+    for (int sw = 0; sw < 2; ++sw) {
+      launch_rbgs(ctx->st, U[l], B[l], h2, 0, per);
+      launch_rbgs(ctx->st, U[l], B[l], h2, 1, per);
+    }
+    if (l == 0) {
+      prof_end(ctx, PM_PROF_SMOOTH0, e, 4 * 8.0 * c0);
+      e = prof_begin(ctx);
+    }
+    launch_resid_restrict(ctx->st, U[l], B[l], 1.0f / h2, U[l + 1], B[l + 1], per);
+    if (l == 0) {
+      prof_end(ctx, PM_PROF_TRANSFER0, e, 9.0 * c0);
+      ec = prof_begin(ctx);
+    }
+    h2 *= 4.0f;
+  }
+  if (L == 0) ec = prof_begin(ctx);
+  launch_coarse(ctx->st, U[L], B[L], h2, per, COARSE_SWEEPS);
+  for (int l = L - 1; l >= 0; --l) {
+    h2 *= 0.25f;
+    int e = -1;
+    if (l == 0) {
+      prof_end(ctx, PM_PROF_COARSE, ec, (L > 0 ? 8.0 / 7.0 * 81.0 * c0 / 8.0 : 0.0));
+      e = prof_begin(ctx);
+    }
+    launch_prolong(ctx->st, U[l + 1], U[l], per);
+    if (l == 0) {
+      prof_end(ctx, PM_PROF_TRANSFER0, e, 8.5 * c0);
+      e = prof_begin(ctx);
+    }
+    for (int sw = 0; sw < 2; ++sw) {
+      launch_rbgs(ctx->st, U[l], B[l], h2, 0, per);
+      launch_rbgs(ctx->st, U[l], B[l], h2, 1, per);
+    }
+    if (l == 0) prof_end(ctx, PM_PROF_SMOOTH0, e, 4 * 8.0 * c0);
+  }
+  if (L == 0) prof_end(ctx, PM_PROF_COARSE, ec, 0.0);
+  CKL();
+  return PM_OK;
+}
+
+// Iterate to rtol.  f2 = ||f||^2 already in d_scal[0] (read at first sync).
+pm_status solve(pm_ctx* ctx) {
+  const int lo = ctx->lo, s = ctx->s, per = ctx->periodic;
+  Grid ph = full_view(ctx, ctx->phi_hi, lo, s), pl = full_view(ctx, ctx->phi_lo, lo, s);
+  Grid fh = full_view(ctx, ctx->f_hi, lo, s), fl = full_view(ctx, ctx->f_lo, lo, s);
+  Grid e0 = compact_view(ctx->lu[0], s), r0 = compact_view(ctx->lb[0], s);
+  const bool mixed = ctx->cfg.precision == PM_MIXED;
+  if (ctx->cfg.guess == PM_GUESS_ZERO) {
+    launch_fill(ctx->st, ph, 0.0f, false);
+    launch_fill(ctx->st, pl, 0.0f, false);
+  }
+  int it = 0;
+  double rel = 0.0;
+  const double cells = (double)s * s * s;
+  for (;; ++it) {
+    int e = prof_begin(ctx);
+    launch_defect(ctx->st, ph, pl, fh, fl, r0, e0, per, mixed, ctx->partial, ctx->counter,
+                  ctx->d_scal + 11);
+    prof_end(ctx, PM_PROF_DEFECT, e, (mixed ? 24.0 : 16.0) * cells);
+    CKL();
+    pm_status st = sync_read(ctx);
+    if (st != PM_OK) return st;
+    double f2 = ctx->h_scal[0], r2 = ctx->h_scal[11];
+    rel = f2 > 0 ? std::sqrt(r2 / f2) : 0.0;
+    if (rel <= ctx->cfg.rtol || f2 == 0.0) break;
+    if (it >= ctx->cfg.max_vcycles) {
+      ctx->vcycles_last = it;
+      ctx->vcycles_total += it;
+      ctx->resid_last = rel;
+      char buf[160];
+      snprintf(buf, sizeof buf, "solve: relative residual %.3e after %d V-cycles (rtol %.1e)",
+               rel, it, ctx->cfg.rtol);
+      return fail(ctx, PM_ENOCONV, buf);
+    }
+    if (mixed) {
+      pm_status v = vcycle(ctx, e0, r0);
+      if (v != PM_OK) return v;
+      int ee = prof_begin(ctx);
+      launch_correct(ctx->st, ph, pl, e0);
+      prof_end(ctx, PM_PROF_CORRECT, ee, 20.0 * cells);
+    } else {
+      pm_status v = vcycle(ctx, ph, fh);
+      if (v != PM_OK) return v;
+    }
+  }
+  ctx->vcycles_last = it;
+  ctx->vcycles_total += it;
+  ctx->resid_last = rel;
+  return PM_OK;
+}
+
+pm_status shrink_to(pm_ctx* ctx, double R, double a_cross, bool flags_ready) {
+  const double c = 0.5 * ctx->n;
+  float klo, khi;
+  keep_bounds(c, R, &klo, &khi);
+  const long long N = ctx->n_active;
+  if (N == 0) return PM_OK;
+  const int nblk = gkd_blocks(N);
+  int e = prof_begin(ctx);
+  if (!flags_ready) launch_flag(ctx->st, ctx->pos, N, klo, khi, ctx->flags, ctx->block_keep);
+  launch_scan_blocks(ctx->st, ctx->block_keep, ctx->keep_off, nblk, ctx->d_cnt);
+  launch_scatter(ctx->st, ctx->pos, ctx->mom, N, ctx->flags, ctx->keep_off, ctx->pos2,
+                 ctx->mom2, ctx->lc_pos, ctx->lc_mom, ctx->n_lc, (float)a_cross);
+  // scatter: read the flag (1 B) and both records (32 B), write them (32 B)
+  prof_end(ctx, PM_PROF_COMPACT, e, 65.0 * N);
+  CKL();
+  pm_status st = sync_read(ctx);
+  if (st != PM_OK) return st;
+  long long keep = (long long)ctx->h_cnt[0];
+  std::swap(ctx->pos, ctx->pos2);
+  std::swap(ctx->mom, ctx->mom2);
+  ctx->n_lc += N - keep;
+  ctx->n_active = keep;
+  return PM_OK;
+}
+
+pm_status alloc(pm_ctx* ctx, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(ctx, PM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return PM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pm_config_default(pm_config* c) {
+  std::memset(c, 0, sizeof(*c));
+  c->n_mesh = 32;
+  c->n_particles = 32 * 32 * 32;
+  c->box_mpch = 250.0;
+  c->omega_m = 0.3;
+  c->omega_l = 0.7;
+  c->a_init = 0.02;
+  c->a_final = 1.0;
+  c->n_steps = 20;
+  c->rtol = 1e-7;
+  c->max_vcycles = 50;
+  c->precision = PM_MIXED;
+  c->guess = PM_GUESS_WARM;
+  c->bc = PM_BC_PAPER;
+  c->shrink = 1;
+  c->buffer_cells = 1.0;
+  c->store_forces = 0;
+}
+
+pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
+                  int32_t host_mem, void* stream, pm_ctx** out) {
+  pm_ctx* ctx = nullptr;
+  if (!out) return fail(nullptr, PM_EINVAL, "pm_init: out is NULL");
+  *out = nullptr;
+  if (!cfg || !pos4 || !mom4) return fail(nullptr, PM_EINVAL, "pm_init: NULL argument");
+  if (!mg_size_ok(cfg->n_mesh) || cfg->n_mesh > 1024)
+    return fail(nullptr, PM_EINVAL, "pm_init: n_mesh must be 2^j or 3*2^j in [4, 1024]");
+  if (cfg->n_particles <= 0 || cfg->n_particles >= (1LL << 31))
+    return fail(nullptr, PM_EINVAL, "pm_init: n_particles must be in [1, 2^31)");
+  if (cfg->n_steps <= 0 || !(cfg->a_init > 0) || !(cfg->a_final > cfg->a_init) ||
+      !(cfg->box_mpch > 0) || !(cfg->omega_m > 0) || cfg->omega_l < 0 || !(cfg->rtol > 0) ||
+      cfg->max_vcycles < 1)
+    return fail(nullptr, PM_EINVAL, "pm_init: invalid schedule, cosmology or tolerance");
+  if (cfg->precision != PM_MIXED && cfg->precision != PM_FP32_PLAIN)
+    return fail(nullptr, PM_EINVAL, "pm_init: unknown precision");
+  if (cfg->bc < PM_BC_PAPER || cfg->bc > PM_BC_PERIODIC)
+    return fail(nullptr, PM_EINVAL, "pm_init: unknown bc");
+
+  ctx = new pm_ctx();
+  ctx->cfg = *cfg;
+  ctx->st = (cudaStream_t)stream;
+  ctx->n = cfg->n_mesh;
+  ctx->P = cfg->n_mesh + 2;
+  ctx->N0 = cfg->n_particles;
+
+  // schedule (steps uniform in a, Sec. 3)
+  const int K = cfg->n_steps;
+  const double om = cfg->omega_m, ol = cfg->omega_l;
+  const double cell = cfg->box_mpch / cfg->n_mesh;
+  ctx->a.resize(K + 1);
+  ctx->dtau.assign(K + 1, 0.0);
+  ctx->a_half.assign(K + 1, 0.0);
+  ctx->chi.resize(K + 1);
+  ctx->R.resize(K + 1);
+  std::vector<double> t(K + 1);
+  const double t1 = tau_of_a(1.0, om, ol);
+  for (int k = 0; k <= K; ++k) {
+    ctx->a[k] = cfg->a_init + (cfg->a_final - cfg->a_init) * k / K;
+    t[k] = tau_of_a(ctx->a[k], om, ol);
+    ctx->chi[k] = C_OVER_H0 * (t1 - t[k]);
+    ctx->R[k] = ctx->chi[k] / cell + cfg->buffer_cells;
+  }
+  for (int k = 0; k < K; ++k) {
+    ctx->dtau[k] = t[k + 1] - t[k];
+    ctx->a_half[k] = a_of_tau(t[k] + 0.5 * ctx->dtau[k], om, ol);
+  }
+
+  const int n = ctx->n, P = ctx->P;
+  const long long N = ctx->N0;
+  const size_t padded = (size_t)P * P * P;
+  pm_status st = PM_OK;
+#define AL(ptr, bytes)                                           \
+  do {                                                           \
+    st = alloc(ctx, (void**)&(ptr), (bytes));                    \
+    if (st != PM_OK) { g_err = ctx->err; pm_destroy(ctx); return st; } \
+  } while (0)
+  AL(ctx->pos, sizeof(float4) * N);
+  AL(ctx->mom, sizeof(float4) * N);
+  AL(ctx->pos2, sizeof(float4) * N);
+  AL(ctx->mom2, sizeof(float4) * N);
+  AL(ctx->lc_pos, sizeof(float4) * N);
+  AL(ctx->lc_mom, sizeof(float4) * N);
+  if (cfg->store_forces) AL(ctx->forces, sizeof(float4) * N);
+  AL(ctx->flags, N);
+  const int nblk = gkd_blocks(N);
+  AL(ctx->block_keep, sizeof(unsigned int) * nblk);
+  AL(ctx->keep_off, sizeof(unsigned long long) * nblk);
+  AL(ctx->rho, sizeof(unsigned long long) * (size_t)n * n * n);
+  AL(ctx->phi_hi, sizeof(float) * padded);
+  AL(ctx->phi_lo, sizeof(float) * padded);
+  AL(ctx->f_hi, sizeof(float) * padded);
+  AL(ctx->f_lo, sizeof(float) * padded);
+  for (int sl = n;; sl /= 2) {
+    float *u = nullptr, *b = nullptr;
+    size_t bytes = sizeof(float) * (size_t)(sl + 2) * (sl + 2) * (sl + 2);
+    AL(u, bytes);
+    ctx->lu.push_back(u);
+    AL(b, bytes);
+    ctx->lb.push_back(b);
+    if (sl <= 4 || sl % 2) break;
+  }
+  const int maxblk = std::max(std::max(SRC_GRID, defect_blocks(n)), 4096);
+  AL(ctx->partial, sizeof(double) * 16 * maxblk);
+  AL(ctx->partial_m, 16 * 10 * (size_t)SRC_GRID);
+  AL(ctx->counter, sizeof(unsigned int) * 4);
+  AL(ctx->d_scal, sizeof(double) * 16);
+  AL(ctx->bgm, sizeof(double) * 10);
+  AL(ctx->d_cnt, sizeof(unsigned long long) * 4);
+  AL(ctx->d_overflow, sizeof(int));
+#undef AL
+  if (cudaMallocHost((void**)&ctx->h_scal, sizeof(double) * 16) != cudaSuccess ||
+      cudaMallocHost((void**)&ctx->h_cnt, sizeof(unsigned long long) * 4) != cudaSuccess) {
+    g_err = "pm_init: cudaMallocHost failed";
+    pm_destroy(ctx);
+    return PM_ENOMEM;
+  }
+  cudaStream_t s0 = ctx->st;
+#define Z(ptr, bytes)                                                        \
+  if (cudaMemsetAsync((ptr), 0, (bytes), s0) != cudaSuccess) {               \
+    g_err = "pm_init: cudaMemsetAsync failed"; pm_destroy(ctx); return PM_ECUDA; }
+  Z(ctx->rho, sizeof(unsigned long long) * (size_t)n * n * n);
+  Z(ctx->phi_hi, sizeof(float) * padded);
+  Z(ctx->phi_lo, sizeof(float) * padded);
+  Z(ctx->f_hi, sizeof(float) * padded);
+  Z(ctx->f_lo, sizeof(float) * padded);
+  Z(ctx->counter, sizeof(unsigned int) * 4);
+  Z(ctx->d_scal, sizeof(double) * 16);
+  Z(ctx->d_cnt, sizeof(unsigned long long) * 4);
+  Z(ctx->d_overflow, sizeof(int));
+#undef Z
+  cudaMemcpyKind kind = host_mem ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (cudaMemcpyAsync(ctx->pos, pos4, sizeof(float4) * N, kind, s0) != cudaSuccess ||
+      cudaMemcpyAsync(ctx->mom, mom4, sizeof(float4) * N, kind, s0) != cudaSuccess ||
+      cudaStreamSynchronize(s0) != cudaSuccess) {
+    g_err = "pm_init: copying particles failed";
+    pm_destroy(ctx);
+    return PM_ECUDA;
+  }
+  ctx->n_active = N;
+  *out = ctx;
+  return PM_OK;
+}
+
+pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
+  if (!ctx) return fail(nullptr, PM_EINVAL, "pm_step: NULL context");
+  if (n_steps < 0 || ctx->step + n_steps > ctx->cfg.n_steps)
+    return fail(ctx, PM_EINVAL, "pm_step: past the last step of the schedule");
+  const int n = ctx->n;
+  const bool mixed = ctx->cfg.precision == PM_MIXED;
+  for (int q = 0; q < n_steps; ++q) {
+    const int k = ctx->step;
+    const double R0 = ctx->R[k], R1 = ctx->R[k + 1];
+    int lo, s, per;
+    geometry(ctx, R0, &lo, &s, &per);
+    pm_status st = set_cube(ctx, lo, s, per, R0);
+    if (st != PM_OK) return st;
+    const long long N = ctx->n_active;
+    const double cells = (double)s * s * s;
+    // 1-2. half drift + CIC deposit: read x, p, write x (48 B/particle); the
+    // count grid is read and written once (16 B/cell)
+    int e = prof_begin(ctx);
+    launch_drift_deposit(ctx->st, std::max(1, std::min(gkd_blocks(N) * 4, 152 * 16)), ctx->pos,
+                         ctx->mom, N, (float)(ctx->dtau[k] / (2.0 * ctx->a[k])), true, n, lo, s,
+                         per, ctx->rho, ctx->d_cnt + 1);
+    prof_end(ctx, PM_PROF_DEPOSIT, e, 48.0 * N + 16.0 * cells);
+    // 3. source, boundary values, solve
+    const double S = 1.5 * ctx->cfg.omega_m / ctx->a_half[k];
+    const double nbar = (double)ctx->N0 / ((double)n * n * n);
+    const double invM = 1.0 / (281474976710656.0 * nbar);
+    int b0 = 0, b1 = n - 1;
+    if (!per) {
+      double c = 0.5 * n;
+      b0 = std::max(lo, (int)std::ceil(c - R0 - 0.5));
+      b1 = std::min(lo + s - 1, (int)std::floor(c + R0 - 0.5));
+    }
+    e = prof_begin(ctx);
+    launch_source(ctx->st, SRC_GRID, ctx->rho, n, lo, s, full_view(ctx, ctx->f_hi, lo, s),
+                  full_view(ctx, ctx->f_lo, lo, s), invM, S, b0, b1, !per, ctx->partial,
+                  ctx->partial_m, ctx->counter, ctx->d_scal, ctx->bgm, ctx->d_overflow);
+    // read the counts, clear them, write f hi + lo: 24 B/cell
+    prof_end(ctx, PM_PROF_SOURCE, e, 24.0 * cells);
+    if (!per) {
+      e = prof_begin(ctx);
+      launch_boundary(ctx->st, full_view(ctx, ctx->phi_hi, lo, s),
+                      full_view(ctx, ctx->phi_lo, lo, s), n, lo, ctx->d_scal + 1, S, mixed);
+      prof_end(ctx, PM_PROF_BOUNDARY, e, 8.0 * 6.0 * (s + 2.0) * (s + 2.0));
+    }
+    CKL();
+    st = solve(ctx);
+    if (st != PM_OK) return st;
+    // 4-6. gradient + gather + kick + half drift (+ keep flags)
+    const bool do_flag = ctx->cfg.shrink && ctx->cfg.bc != PM_BC_PERIODIC && is_open(ctx, R1);
+    float klo = 0.f, khi = 0.f;
+    if (do_flag) keep_bounds(0.5 * n, R1, &klo, &khi);
+    e = prof_begin(ctx);
+    launch_gather_kick_drift(ctx->st, ctx->pos, ctx->mom, N, ctx->phi_hi, ctx->phi_lo, n, lo, s,
+                             per, (float)(ctx->a_half[k] * ctx->dtau[k]),
+                             (float)(ctx->dtau[k] / (2.0 * ctx->a[k + 1])), do_flag, klo, khi,
+                             ctx->flags, ctx->block_keep, ctx->forces, ctx->d_cnt + 1);
+    // read x, p, write x, p (64 B/particle, + 1 B flag), read Phi hi + lo once
+    // (8 B/cell)
+    prof_end(ctx, PM_PROF_GATHER, e, (do_flag ? 65.0 : 64.0) * N + 8.0 * cells);
+    CKL();
+    ctx->forces_valid = ctx->forces != nullptr;
+    ctx->forces_n = N;
+    // 7. lightcone shrink
+    if (do_flag) {
+      st = shrink_to(ctx, R1, ctx->a[k + 1], true);
+      if (st != PM_OK) return st;
+    }
+    int ovf = 0;
+    CK(cudaMemcpyAsync(&ovf, ctx->d_overflow, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (ctx->prof_on) prof_flush(ctx);
+    if (ovf) return fail(ctx, PM_EOVERFLOW, "deposit: a cell count exceeded 2^62");
+    ctx->particle_steps += N;
+    ctx->step++;
+  }
+  return PM_OK;
+}
+
+pm_status pm_shrink(pm_ctx* ctx, double a, int64_t* n_active_out) {
+  if (!ctx) return fail(nullptr, PM_EINVAL, "pm_shrink: NULL context");
+  if (!(a > 0)) return fail(ctx, PM_EINVAL, "pm_shrink: a must be > 0");
+  const double om = ctx->cfg.omega_m, ol = ctx->cfg.omega_l;
+  double chi = C_OVER_H0 * (tau_of_a(1.0, om, ol) - tau_of_a(a, om, ol));
+  double R = chi / (ctx->cfg.box_mpch / ctx->n) + ctx->cfg.buffer_cells;
+  if (is_open(ctx, R) && ctx->cfg.bc != PM_BC_PERIODIC) {
+    pm_status st = shrink_to(ctx, R, a, false);
+    if (st != PM_OK) return st;
+  }
+  if (n_active_out) *n_active_out = ctx->n_active;
+  return PM_OK;
+}
+
+pm_status pm_potential(pm_ctx* ctx, const double* delta_dev, double a, int32_t bc,
+                       float* phi_out_dev, double* phi64_out_dev, int32_t* vcycles_out,
+                       double* resid_out) {
+  if (!ctx) return fail(nullptr, PM_EINVAL, "pm_potential: NULL context");
+  if (!delta_dev || !phi_out_dev || !(a > 0) || (bc != PM_BC_OPEN && bc != PM_BC_PERIODIC))
+    return fail(ctx, PM_EINVAL, "pm_potential: bad argument");
+  const int n = ctx->n;
+  const int per = bc == PM_BC_PERIODIC;
+  pm_status st = set_cube(ctx, 0, n, per, 1e300);
+  if (st != PM_OK) return st;
+  ctx->cube_valid = false;  // the next step re-derives its cube
+  const double S = 1.5 * ctx->cfg.omega_m / a;
+  Grid fh = full_view(ctx, ctx->f_hi, 0, n), fl = full_view(ctx, ctx->f_lo, 0, n);
+  Grid ph = full_view(ctx, ctx->phi_hi, 0, n), pl = full_view(ctx, ctx->phi_lo, 0, n);
+  launch_source_f64(ctx->st, SRC_GRID, delta_dev, n, fh, fl, S, !per, ctx->partial,
+                    ctx->counter, ctx->d_scal);
+  // launch_source_f64 writes (||f||^2, q0, d, S_ab) to d_scal[0..10]
+  if (!per) launch_boundary(ctx->st, ph, pl, n, 0, ctx->d_scal + 1, S,
+                            ctx->cfg.precision == PM_MIXED);
+  launch_fill(ctx->st, ph, 0.0f, false);
+  launch_fill(ctx->st, pl, 0.0f, false);
+  CKL();
+  int guess = ctx->cfg.guess;
+  ctx->cfg.guess = PM_GUESS_WARM;  // already zeroed
+  st = solve(ctx);
+  ctx->cfg.guess = guess;
+  if (vcycles_out) *vcycles_out = ctx->vcycles_last;
+  if (resid_out) *resid_out = ctx->resid_last;
+  if (st != PM_OK) return st;
+  double shift = 0.0;
+  if (per) {
+    launch_sum_phi(ctx->st, ph, pl, ctx->partial, ctx->counter, ctx->d_scal + 12);
+    CKL();
+    st = sync_read(ctx);
+    if (st != PM_OK) return st;
+    shift = ctx->h_scal[12] / ((double)n * n * n);
+  }
+  launch_phi_out(ctx->st, ph, pl, phi_out_dev, phi64_out_dev, shift);
+  CKL();
+  CK(cudaStreamSynchronize(ctx->st));
+  return PM_OK;
+}
+
+pm_status pm_deposit(float* pos4_dev, const float* mom4_dev, int64_t n, float drift_coef,
+                     int32_t n_mesh, int32_t lo, int32_t side, int32_t periodic,
+                     int64_t* rho_dev, int64_t* escaped_out, void* stream) {
+  pm_ctx* ctx = nullptr;
+  if (!pos4_dev || !rho_dev || n < 0 || n_mesh < 1 || side < 1 || lo < 0 || lo + side > n_mesh)
+    return fail(nullptr, PM_EINVAL, "pm_deposit: bad argument");
+  if (periodic && (lo != 0 || side != n_mesh))
+    return fail(nullptr, PM_EINVAL, "pm_deposit: periodic needs the whole mesh");
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long* esc = nullptr;
+  CK(cudaMallocAsync((void**)&esc, sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(esc, 0, sizeof(unsigned long long), st));
+  launch_drift_deposit(st, std::max(1, std::min(gkd_blocks(n) * 4, 152 * 16)), (float4*)pos4_dev,
+                       (const float4*)mom4_dev, n, drift_coef, mom4_dev != nullptr, n_mesh, lo,
+                       side, periodic, (unsigned long long*)rho_dev, esc);
+  CKL();
+  if (escaped_out) {
+    unsigned long long h = 0;
+    CK(cudaMemcpyAsync(&h, esc, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *escaped_out = (int64_t)h;
+  }
+  CK(cudaFreeAsync(esc, st));
+  return PM_OK;
+}
+
+pm_status pm_power_spectrum(const float* pos4_dev, int64_t n, double box, int32_t n_mesh,
+                            int32_t n_bins, int32_t subtract_shot, double* k_out,
+                            double* pk_out, double* modes_out, void* stream) {
+  if (!pos4_dev || n <= 0 || !(box > 0) || n_mesh < 2 || n_bins < 1 || n_bins > 2048 ||
+      !k_out || !pk_out || !modes_out)
+    return fail(nullptr, PM_EINVAL, "pm_power_spectrum: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t cells = (size_t)n_mesh * n_mesh * n_mesh;
+  const size_t modes = (size_t)n_mesh * n_mesh * (n_mesh / 2 + 1);
+  unsigned long long* rho = nullptr;
+  float* delta = nullptr;
+  cufftComplex* dk = nullptr;
+  double* acc = nullptr;
+  pm_status ret = PM_OK;
+  cufftHandle plan = 0;
+  bool have_plan = false;
+  do {
+    if (cudaMalloc((void**)&rho, sizeof(unsigned long long) * cells) != cudaSuccess ||
+        cudaMalloc((void**)&delta, sizeof(float) * cells) != cudaSuccess ||
+        cudaMalloc((void**)&dk, sizeof(cufftComplex) * modes) != cudaSuccess ||
+        cudaMalloc((void**)&acc, sizeof(double) * (3 * n_bins + 1)) != cudaSuccess) {
+      ret = fail(nullptr, PM_ENOMEM, "pm_power_spectrum: cudaMalloc failed");
+      break;
+    }
+    cudaMemsetAsync(rho, 0, sizeof(unsigned long long) * cells, st);
+    cudaMemsetAsync(acc, 0, sizeof(double) * (3 * n_bins + 1), st);
+    // positions are read-only here: no drift
+    launch_drift_deposit(st, std::max(1, std::min(gkd_blocks(n) * 4, 152 * 16)),
+                         (float4*)pos4_dev, nullptr, n, 0.f, false, n_mesh, 0, n_mesh, 1, rho,
+                         (unsigned long long*)(acc + 3 * n_bins));
+    const double mean = (double)n * 281474976710656.0 / (double)cells;
+    launch_pk_delta(st, rho, delta, n_mesh, 1.0 / mean);
+    if (cufftPlan3d(&plan, n_mesh, n_mesh, n_mesh, CUFFT_R2C) != CUFFT_SUCCESS) {
+      ret = fail(nullptr, PM_ECUDA, "pm_power_spectrum: cufftPlan3d failed");
+      break;
+    }
+    have_plan = true;
+    cufftSetStream(plan, st);
+    if (cufftExecR2C(plan, delta, dk) != CUFFT_SUCCESS) {
+      ret = fail(nullptr, PM_ECUDA, "pm_power_spectrum: cufftExecR2C failed");
+      break;
+    }
+    const double shot = subtract_shot ? box * box * box / (double)n : 0.0;
+    launch_pk_bin(st, (const float2*)dk, n_mesh, box, shot, n_bins, acc);
+    std::vector<double> h(3 * n_bins);
+    if (cudaMemcpyAsync(h.data(), acc, sizeof(double) * 3 * n_bins, cudaMemcpyDeviceToHost,
+                        st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      ret = fail(nullptr, PM_ECUDA, std::string("pm_power_spectrum: ") +
+                                        cudaGetErrorString(cudaGetLastError()));
+      break;
+    }
+    for (int b = 0; b < n_bins; ++b) {
+      double c = h[3 * b];
+      modes_out[b] = c;
+      k_out[b] = c > 0 ? h[3 * b + 1] / c : NAN;
+      pk_out[b] = c > 0 ? h[3 * b + 2] / c : NAN;
+    }
+  } while (0);
+  if (have_plan) cufftDestroy(plan);
+  cudaFree(rho);
+  cudaFree(delta);
+  cudaFree(dk);
+  cudaFree(acc);
+  return ret;
+}
+
+pm_status pm_stats(pm_ctx* ctx, pm_stats_t* o) {
+  if (!ctx || !o) return fail(ctx, PM_EINVAL, "pm_stats: NULL argument");
+  pm_status st = sync_read(ctx);
+  if (st != PM_OK) return st;
+  o->step = ctx->step;
+  o->a = ctx->a[ctx->step];
+  o->n_active = ctx->n_active;
+  o->n_lightcone = ctx->n_lc;
+  o->cube_lo = ctx->lo;
+  o->cube_side = ctx->s;
+  o->periodic = ctx->periodic;
+  o->vcycles_last = ctx->vcycles_last;
+  o->vcycles_total = ctx->vcycles_total;
+  o->resid_last = ctx->resid_last;
+  o->escaped = (int64_t)ctx->h_cnt[1];
+  o->particle_steps = ctx->particle_steps;
+  return PM_OK;
+}
+
+pm_status pm_schedule(pm_ctx* ctx, double* a, double* dtau, double* a_half, double* chi) {
+  if (!ctx) return fail(nullptr, PM_EINVAL, "pm_schedule: NULL context");
+  size_t m = ctx->a.size();
+  if (a) std::copy(ctx->a.begin(), ctx->a.end(), a);
+  if (dtau) std::copy(ctx->dtau.begin(), ctx->dtau.begin() + m, dtau);
+  if (a_half) std::copy(ctx->a_half.begin(), ctx->a_half.begin() + m, a_half);
+  if (chi) std::copy(ctx->chi.begin(), ctx->chi.end(), chi);
+  return PM_OK;
+}
+
+pm_status pm_get_particles(pm_ctx* ctx, float* pos4, float* mom4, int32_t host_mem,
+                           int64_t* n_active_out) {
+  if (!ctx) return fail(nullptr, PM_EINVAL, "pm_get_particles: NULL context");
+  cudaMemcpyKind kind = host_mem ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  size_t bytes = sizeof(float4) * ctx->n_active;
+  if (pos4 && bytes) CK(cudaMemcpyAsync(pos4, ctx->pos, bytes, kind, ctx->st));
+  if (mom4 && bytes) CK(cudaMemcpyAsync(mom4, ctx->mom, bytes, kind, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (n_active_out) *n_active_out = ctx->n_active;
+  return PM_OK;
+}
+
+pm_status pm_set_particles(pm_ctx* ctx, const float* pos4, const float* mom4, int64_t n,
+                           int32_t host_mem) {
+  if (!ctx) return fail(nullptr, PM_EINVAL, "pm_set_particles: NULL context");
+  if (!pos4 || !mom4 || n < 0 || n > ctx->N0)
+    return fail(ctx, PM_EINVAL, "pm_set_particles: bad argument");
+  cudaMemcpyKind kind = host_mem ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  size_t bytes = sizeof(float4) * n;
+  if (bytes) {
+    CK(cudaMemcpyAsync(ctx->pos, pos4, bytes, kind, ctx->st));
+    CK(cudaMemcpyAsync(ctx->mom, mom4, bytes, kind, ctx->st));
+  }
+  ctx->n_active = n;
+  return PM_OK;
+}
+
+pm_status pm_get_lightcone(pm_ctx* ctx, float* pos4, float* mom4, int32_t host_mem,
+                           int64_t* n_out) {
+  if (!ctx) return fail(nullptr, PM_EINVAL, "pm_get_lightcone: NULL context");
+  cudaMemcpyKind kind = host_mem ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  size_t bytes = sizeof(float4) * ctx->n_lc;
+  if (pos4 && bytes) CK(cudaMemcpyAsync(pos4, ctx->lc_pos, bytes, kind, ctx->st));
+  if (mom4 && bytes) CK(cudaMemcpyAsync(mom4, ctx->lc_mom, bytes, kind, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (n_out) *n_out = ctx->n_lc;
+  return PM_OK;
+}
+
+pm_status pm_get_forces(pm_ctx* ctx, float* f4, int32_t host_mem, int64_t* n_out) {
+  if (!ctx) return fail(nullptr, PM_EINVAL, "pm_get_forces: NULL context");
+  if (!ctx->forces || !ctx->forces_valid)
+    return fail(ctx, PM_EINVAL, "pm_get_forces: store_forces is off or no step ran");
+  cudaMemcpyKind kind = host_mem ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (f4 && ctx->forces_n)
+    CK(cudaMemcpyAsync(f4, ctx->forces, sizeof(float4) * ctx->forces_n, kind, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (n_out) *n_out = ctx->forces_n;
+  return PM_OK;
+}
+
+pm_status pm_get_potential(pm_ctx* ctx, double* phi_host, int32_t* lo_out, int32_t* side_out) {
+  if (!ctx) return fail(nullptr, PM_EINVAL, "pm_get_potential: NULL context");
+  const int P = ctx->P, lo = ctx->lo, s = ctx->s;
+  const size_t padded = (size_t)P * P * P;
+  std::vector<float> hi(padded), lo_(padded);
+  CK(cudaMemcpyAsync(hi.data(), ctx->phi_hi, sizeof(float) * padded, cudaMemcpyDeviceToHost,
+                     ctx->st));
+  CK(cudaMemcpyAsync(lo_.data(), ctx->phi_lo, sizeof(float) * padded, cudaMemcpyDeviceToHost,
+                     ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (phi_host) {
+    const int Q = s + 2;
+    for (int k = 0; k < Q; ++k)
+      for (int j = 0; j < Q; ++j)
+        for (int i = 0; i < Q; ++i) {
+          size_t src = ((size_t)(lo + k) * P + (lo + j)) * P + (lo + i);
+          phi_host[((size_t)k * Q + j) * Q + i] = (double)hi[src] + (double)lo_[src];
+        }
+  }
+  if (lo_out) *lo_out = lo;
+  if (side_out) *side_out = s;
+  return PM_OK;
+}
+
+pm_status pm_profile(pm_ctx* ctx, int32_t enable) {
+  if (!ctx) return fail(nullptr, PM_EINVAL, "pm_profile: NULL context");
+  CK(cudaStreamSynchronize(ctx->st));
+  prof_flush(ctx);
+  if (enable && ctx->ev.empty()) {
+    ctx->ev.resize(2048);
+    for (auto& e : ctx->ev) CK(cudaEventCreate(&e));
+  }
+  for (int c = 0; c < PM_PROF_N; ++c) {
+    ctx->prof_ms[c] = 0.0;
+    ctx->prof_groups[c] = 0;
+    ctx->prof_bytes[c] = 0.0;
+  }
+  ctx->prof_on = enable != 0;
+  return PM_OK;
+}
+
+pm_status pm_profile_read(pm_ctx* ctx, int32_t cls, double* ms, int64_t* groups,
+                          double* bytes) {
+  if (!ctx || cls < 0 || cls >= PM_PROF_N) return fail(ctx, PM_EINVAL, "pm_profile_read");
+  CK(cudaStreamSynchronize(ctx->st));
+  prof_flush(ctx);
+  if (ms) *ms = ctx->prof_ms[cls];
+  if (groups) *groups = ctx->prof_groups[cls];
+  if (bytes) *bytes = ctx->prof_bytes[cls];
+  return PM_OK;
+}
+
+int64_t pm_launch_count(void) { return g_launches.load(); }
+
+const char* pm_last_error(const pm_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_err.c_str();
+}
+
+void pm_destroy(pm_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->st) cudaStreamSynchronize(ctx->st);
+  void* ptrs[] = {ctx->pos, ctx->mom, ctx->pos2, ctx->mom2, ctx->lc_pos, ctx->lc_mom,
+                  ctx->forces, ctx->flags, ctx->block_keep, ctx->keep_off, ctx->rho,
+                  ctx->phi_hi, ctx->phi_lo, ctx->f_hi, ctx->f_lo, ctx->partial, ctx->partial_m,
+                  ctx->counter, ctx->d_scal, ctx->bgm, ctx->d_cnt, ctx->d_overflow};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (float* p : ctx->lu) if (p) cudaFree(p);
+  for (float* p : ctx->lb) if (p) cudaFree(p);
+  for (auto& e : ctx->ev) cudaEventDestroy(e);
+  if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
+  if (ctx->h_cnt) cudaFreeHost(ctx->h_cnt);
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,374 @@
+// Mesh-side kernels of the PM step: fused half drift + fixed-point CIC
+// deposit (Sec. 2.2 first DKD line; Sec. 2.4 footnote, CIC), the Poisson
+// source on the active cube (Sec. 2.1, Eq. 3) with its boundary multipoles,
+// and the open-boundary ghost layer (Table 1: open boundaries).
+#include "pm_kernels.cuh"
+
+namespace pm {
+
+// ---------------------------------------------------------------------------
+// K1: x += p * c0 (float32, two roundings), then 8 int64 atomics per particle.
+// Periodic: nodes wrap mod n.  Open: a particle with a node outside the cube
+// [lo, lo+s) deposits nothing and is counted as escaped.
+// ---------------------------------------------------------------------------
+template <bool DRIFT>
+__global__ void __launch_bounds__(256) k_drift_deposit(
+    float4* __restrict__ pos, const float4* __restrict__ mom, long long N,
+    float c0, int n, int lo, int s, int periodic,
+    unsigned long long* __restrict__ rho, unsigned long long* __restrict__ escaped) {
+  const float fn = (float)n;
+  unsigned int esc_local = 0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+       p += (long long)gridDim.x * blockDim.x) {
+    float4 x = pos[p];
+    if (DRIFT) {
+      float4 v = mom[p];
+      x.x = __fadd_rn(x.x, __fmul_rn(v.x, c0));
+      x.y = __fadd_rn(x.y, __fmul_rn(v.y, c0));
+      x.z = __fadd_rn(x.z, __fmul_rn(v.z, c0));
+      if (periodic) {
+        if (x.x < 0.f) x.x = __fadd_rn(x.x, fn);
+        if (x.x >= fn) x.x = __fsub_rn(x.x, fn);
+        if (x.y < 0.f) x.y = __fadd_rn(x.y, fn);
+        if (x.y >= fn) x.y = __fsub_rn(x.y, fn);
+        if (x.z < 0.f) x.z = __fadd_rn(x.z, fn);
+        if (x.z >= fn) x.z = __fsub_rn(x.z, fn);
+      }
+      pos[p] = x;
+    }
+    int ix, iy, iz, dx, dy, dz;
+    cic_axis(x.x, ix, dx);
+    cic_axis(x.y, iy, dy);
+    cic_axis(x.z, iz, dz);
+    int x0, x1, y0, y1, z0, z1;
+    if (periodic) {
+      // a wrapped position gives i in [-1, n-1]; anything else (a drift of
+      // more than a box length) is counted as escaped, never indexed
+      if (ix < -1 || ix > n - 1 || iy < -1 || iy > n - 1 || iz < -1 || iz > n - 1) {
+        ++esc_local;
+        continue;
+      }
+      x0 = ix < 0 ? ix + n : ix;  x1 = x0 + 1 == n ? 0 : x0 + 1;
+      y0 = iy < 0 ? iy + n : iy;  y1 = y0 + 1 == n ? 0 : y0 + 1;
+      z0 = iz < 0 ? iz + n : iz;  z1 = z0 + 1 == n ? 0 : z0 + 1;
+    } else {
+      const int hi = lo + s - 1;
+      if (ix < lo || ix + 1 > hi || iy < lo || iy + 1 > hi || iz < lo || iz + 1 > hi) {
+        ++esc_local;
+        continue;
+      }
+      x0 = ix; x1 = ix + 1; y0 = iy; y1 = iy + 1; z0 = iz; z1 = iz + 1;
+    }
+    const unsigned long long wx0 = 65536u - dx, wx1 = dx;
+    const unsigned long long wy0 = 65536u - dy, wy1 = dy;
+    const unsigned long long wz0 = 65536u - dz, wz1 = dz;
+    const unsigned long long a00 = wy0 * wz0, a10 = wy1 * wz0, a01 = wy0 * wz1,
+                             a11 = wy1 * wz1;
+    const long long r00 = ((long long)z0 * n + y0) * n, r10 = ((long long)z0 * n + y1) * n;
+    const long long r01 = ((long long)z1 * n + y0) * n, r11 = ((long long)z1 * n + y1) * n;
+    atomicAdd(rho + r00 + x0, wx0 * a00);
+    atomicAdd(rho + r00 + x1, wx1 * a00);
+    atomicAdd(rho + r10 + x0, wx0 * a10);
+    atomicAdd(rho + r10 + x1, wx1 * a10);
+    atomicAdd(rho + r01 + x0, wx0 * a01);
+    atomicAdd(rho + r01 + x1, wx1 * a01);
+    atomicAdd(rho + r11 + x0, wx0 * a11);
+    atomicAdd(rho + r11 + x1, wx1 * a11);
+  }
+  {
+    unsigned int w = esc_local;
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if ((threadIdx.x & 31) == 0 && w) atomicAdd(escaped, (unsigned long long)w);
+  }
+}
+
+void launch_drift_deposit(cudaStream_t st, int grid, float4* pos, const float4* mom,
+                          long long N, float c0, bool drift, int n, int lo, int s,
+                          int periodic, unsigned long long* rho,
+                          unsigned long long* escaped) {
+  if (N <= 0) return;
+  if (drift)
+    k_drift_deposit<true><<<grid, 256, 0, st>>>(pos, mom, N, c0, n, lo, s, periodic, rho,
+                                                escaped);
+  else
+    k_drift_deposit<false><<<grid, 256, 0, st>>>(pos, mom, N, c0, n, lo, s, periodic, rho,
+                                                 escaped);
+  note_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic "last block finishes" reduction helpers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool arrive_last(unsigned int* counter) {
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned int t = atomicAdd(counter, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  return last;
+}
+
+__device__ __forceinline__ double i128_to_double(__int128 v) {
+  bool neg = v < 0;
+  unsigned __int128 u = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+  double d = (double)(unsigned long long)(u >> 64) * 18446744073709551616.0 +
+             (double)(unsigned long long)u;
+  return neg ? -d : d;
+}
+
+__device__ __forceinline__ __int128 shfl_xor_i128(__int128 v, int o) {
+  unsigned long long lo = (unsigned long long)v;
+  long long hi = (long long)(v >> 64);
+  lo = __shfl_xor_sync(0xffffffffu, lo, o);
+  hi = __shfl_xor_sync(0xffffffffu, hi, o);
+  return ((__int128)hi << 64) | (__int128)lo;
+}
+
+// ---------------------------------------------------------------------------
+// K2: source on the active cube from the int64 counts.
+//   delta = rho / (2^48 nbar) - [cell centre inside the keep cube]
+//   f     = S delta                          (double-float, hi/lo planes)
+// clears rho for the next deposit, flags counts > 2^62, accumulates ||f||^2
+// and, in the open phase, the exact integer moments
+//   sum rho, sum rho X_a, sum rho X_a X_b   with X = 2 (cell centre - c),
+// finished by the last block into moments of delta (q0, d_a, S_ab) in cell
+// units.  out[0] = ||f||^2, out[1..10] = moments.
+// ---------------------------------------------------------------------------
+constexpr int SRC_NV = 10;
+
+template <bool MOMENTS>
+__global__ void __launch_bounds__(256) k_source(
+    unsigned long long* __restrict__ rho, int n, int lo, int s, Grid fh, Grid fl,
+    df invM, df S, int b0, int b1, double* __restrict__ partial_f2,
+    __int128* __restrict__ partial_m, unsigned int* counter, double* __restrict__ out,
+    const double* __restrict__ bgm, double invM2_hi, int* __restrict__ overflow) {
+  __int128 acc[SRC_NV];
+#pragma unroll
+  for (int q = 0; q < SRC_NV; ++q) acc[q] = 0;
+  float f2 = 0.f;
+  const long long total = (long long)s * s * s;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(t % s);
+    long long r = t / s;
+    int j = (int)(r % s);
+    int k = (int)(r / s);
+    int gi = lo + i, gj = lo + j, gk = lo + k;
+    long long ri = ((long long)gk * n + gj) * n + gi;
+    unsigned long long cnt = rho[ri];
+    rho[ri] = 0ull;
+    if (cnt > (1ull << 62)) atomicOr(overflow, 1);
+    long long c = (long long)cnt;
+    df d = df_mul(df_from_i64(c), invM);
+    bool inside = gi >= b0 && gi <= b1 && gj >= b0 && gj <= b1 && gk >= b0 && gk <= b1;
+    if (inside) d = df_add(d, df{-1.0f, 0.0f});
+    df f = df_mul(d, S);
+    int fi = gidx(fh, i, j, k);
+    fh.base[fi] = f.hi;
+    fl.base[fi] = f.lo;
+    f2 = __fmaf_rn(f.hi, f.hi, f2);
+    if (MOMENTS) {
+      int X = 2 * gi + 1 - n, Y = 2 * gj + 1 - n, Z = 2 * gk + 1 - n;
+      __int128 cc = (__int128)c;
+      acc[0] += cc;
+      acc[1] += cc * X;
+      acc[2] += cc * Y;
+      acc[3] += cc * Z;
+      acc[4] += cc * (long long)(X * X);
+      acc[5] += cc * (long long)(Y * Y);
+      acc[6] += cc * (long long)(Z * Z);
+      acc[7] += cc * (long long)(X * Y);
+      acc[8] += cc * (long long)(X * Z);
+      acc[9] += cc * (long long)(Y * Z);
+    }
+  }
+  // block reduction: ||f||^2 in double, moments in int128
+  __shared__ double sf[32];
+  __shared__ __int128 sm[32 * SRC_NV];
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double w = warp_sum((double)f2);
+  if (lane == 0) sf[warp] = w;
+  if (MOMENTS) {
+#pragma unroll
+    for (int q = 0; q < SRC_NV; ++q) {
+      __int128 v = acc[q];
+      for (int o = 16; o > 0; o >>= 1) v += shfl_xor_i128(v, o);
+      if (lane == 0) sm[warp * SRC_NV + q] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tf = 0.0;
+    for (int q = 0; q < nw; ++q) tf += sf[q];
+    partial_f2[blockIdx.x] = tf;
+    if (MOMENTS) {
+      for (int q = 0; q < SRC_NV; ++q) {
+        __int128 v = 0;
+        for (int u = 0; u < nw; ++u) v += sm[u * SRC_NV + q];
+        partial_m[blockIdx.x * SRC_NV + q] = v;
+      }
+    }
+  }
+  if (!arrive_last(counter)) return;
+  if (threadIdx.x == 0) {
+    double tf = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) tf += __ldcg(partial_f2 + b);
+    out[0] = tf;
+    if (MOMENTS) {
+      __int128 tot[SRC_NV];
+      for (int q = 0; q < SRC_NV; ++q) tot[q] = 0;
+      for (unsigned b = 0; b < gridDim.x; ++b)
+        for (int q = 0; q < SRC_NV; ++q) {
+          const unsigned long long* pp =
+              reinterpret_cast<const unsigned long long*>(partial_m + b * SRC_NV + q);
+          unsigned long long plo = __ldcg(pp), phi = __ldcg(pp + 1);
+          tot[q] += (__int128)(((unsigned __int128)phi << 64) | plo);
+        }
+      // moments of rho / M in cell units (X = 2y) minus the background's
+      double m[SRC_NV];
+      m[0] = i128_to_double(tot[0]) * invM2_hi;
+      for (int q = 1; q < 4; ++q) m[q] = i128_to_double(tot[q]) * invM2_hi * 0.5;
+      for (int q = 4; q < 10; ++q) m[q] = i128_to_double(tot[q]) * invM2_hi * 0.25;
+      for (int q = 0; q < SRC_NV; ++q) out[1 + q] = m[q] - bgm[q];
+    }
+    *counter = 0u;
+  }
+}
+
+void launch_source(cudaStream_t st, int grid, unsigned long long* rho, int n, int lo,
+                   int s, Grid fh, Grid fl, double invM, double S, int b0, int b1,
+                   bool moments, double* partial_f2, void* partial_m,
+                   unsigned int* counter, double* out, const double* bgm, int* overflow) {
+  df invMd, Sd;
+  invMd.hi = (float)invM;
+  invMd.lo = (float)(invM - (double)invMd.hi);
+  Sd.hi = (float)S;
+  Sd.lo = (float)(S - (double)Sd.hi);
+  if (moments)
+    k_source<true><<<grid, 256, 0, st>>>(rho, n, lo, s, fh, fl, invMd, Sd, b0, b1,
+                                         partial_f2, (__int128*)partial_m, counter, out,
+                                         bgm, invM, overflow);
+  else
+    k_source<false><<<grid, 256, 0, st>>>(rho, n, lo, s, fh, fl, invMd, Sd, b0, b1,
+                                          partial_f2, (__int128*)partial_m, counter, out,
+                                          bgm, invM, overflow);
+  note_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Source from a caller's FP64 delta on the whole n^3 mesh (pm_potential):
+// f = S delta split into hi/lo, ||f||^2, and FP64 moments of delta.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_source_f64(
+    const double* __restrict__ delta, int n, Grid fh, Grid fl, double S, int moments,
+    double* __restrict__ partial, unsigned int* counter, double* __restrict__ out) {
+  double acc[11];
+#pragma unroll
+  for (int q = 0; q < 11; ++q) acc[q] = 0.0;
+  const long long total = (long long)n * n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(t % n);
+    long long r = t / n;
+    int j = (int)(r % n);
+    int k = (int)(r / n);
+    double d = delta[t];
+    double f = S * d;
+    float hi = (float)f;
+    float lo = (float)(f - (double)hi);
+    int fi = gidx(fh, i, j, k);
+    fh.base[fi] = hi;
+    fl.base[fi] = lo;
+    acc[0] += f * f;
+    if (moments) {
+      double x = i + 0.5 - 0.5 * n, y = j + 0.5 - 0.5 * n, z = k + 0.5 - 0.5 * n;
+      acc[1] += d;
+      acc[2] += d * x;
+      acc[3] += d * y;
+      acc[4] += d * z;
+      acc[5] += d * x * x;
+      acc[6] += d * y * y;
+      acc[7] += d * z * z;
+      acc[8] += d * x * y;
+      acc[9] += d * x * z;
+      acc[10] += d * y * z;
+    }
+  }
+  __shared__ double sm[32 * 11];
+  block_sum<11>(acc, sm);
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 11; ++q) partial[blockIdx.x * 11 + q] = acc[q];
+  if (!arrive_last(counter)) return;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 11; ++q) {
+      double v = 0.0;
+      for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(partial + b * 11 + q);
+      out[q] = v;
+    }
+    *counter = 0u;
+  }
+}
+
+void launch_source_f64(cudaStream_t st, int grid, const double* delta, int n, Grid fh,
+                       Grid fl, double S, bool moments, double* partial,
+                       unsigned int* counter, double* out) {
+  k_source_f64<<<grid, 256, 0, st>>>(delta, n, fh, fl, S, moments ? 1 : 0, partial,
+                                     counter, out);
+  note_launch();
+}
+
+// ---------------------------------------------------------------------------
+// K3: open-boundary ghost layer.  At each ghost-cell centre r (relative to
+// the box centre): Phi = -(S/4pi) [q0/r + d.r/r^3 + r.Q.r/(2 r^5)],
+// Q_ab = 3 S_ab - delta_ab tr(S).  mom = (q0, dx, dy, dz, Sxx, Syy, Szz, Sxy,
+// Sxz, Syz).  Written to the hi/lo planes (lo = 0 when want_lo == 0).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_boundary(Grid ph, Grid pl, int n, int lo,
+                                                  const double* __restrict__ mom,
+                                                  double S, int want_lo) {
+  const int s = ph.s;
+  const int P = s + 2;
+  const long long per_face = (long long)P * P;
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= 6 * per_face) return;
+  int face = (int)(t / per_face);
+  int rem = (int)(t % per_face);
+  int u = rem % P - 1, v = rem / P - 1;
+  int i, j, k;
+  int side = (face & 1) ? s : -1;
+  switch (face >> 1) {
+    case 0: i = side; j = u; k = v; break;
+    case 1: j = side; i = u; k = v; break;
+    default: k = side; i = u; j = v; break;
+  }
+  const double q0 = mom[0], dx = mom[1], dy = mom[2], dz = mom[3];
+  const double sxx = mom[4], syy = mom[5], szz = mom[6];
+  const double sxy = mom[7], sxz = mom[8], syz = mom[9];
+  const double tr = sxx + syy + szz;
+  const double qxx = 3 * sxx - tr, qyy = 3 * syy - tr, qzz = 3 * szz - tr;
+  const double qxy = 3 * sxy, qxz = 3 * sxz, qyz = 3 * syz;
+  double x = lo + i + 0.5 - 0.5 * n, y = lo + j + 0.5 - 0.5 * n, z = lo + k + 0.5 - 0.5 * n;
+  double r2 = x * x + y * y + z * z;
+  double r = sqrt(r2);
+  double qr = qxx * x * x + qyy * y * y + qzz * z * z +
+              2.0 * (qxy * x * y + qxz * x * z + qyz * y * z);
+  double phi = -(S / (4.0 * 3.14159265358979323846)) *
+               (q0 / r + (dx * x + dy * y + dz * z) / (r * r2) + 0.5 * qr / (r2 * r2 * r));
+  float hi = (float)phi;
+  int gi = gidx(ph, i, j, k);
+  ph.base[gi] = hi;
+  pl.base[gi] = want_lo ? (float)(phi - (double)hi) : 0.0f;
+}
+
+void launch_boundary(cudaStream_t st, Grid ph, Grid pl, int n, int lo, const double* mom,
+                     double S, bool want_lo) {
+  long long tot = 6LL * (ph.s + 2) * (ph.s + 2);
+  int grid = (int)((tot + 255) / 256);
+  k_boundary<<<grid, 256, 0, st>>>(ph, pl, n, lo, mom, S, want_lo ? 1 : 0);
+  note_launch();
+}
+
+}  // namespace pm

@@ -1,0 +1,320 @@
+// Particle-side kernels: gradient + CIC gather + kick + half drift + keep
+// flag (Sec. 2.2, second and third DKD lines; Sec. 2.4 footnote: the gather
+// uses the deposit's CIC weights), and the order-preserving compaction that
+// drops particles leaving the lightcone (Sec. 2.4: active particles are
+// recomputed at the end of every step; Table 2, last row).
+#include "pm_kernels.cuh"
+
+namespace pm {
+
+constexpr int KT = 256;          // threads per block
+constexpr int KITEMS = 4;        // particles per thread
+constexpr int KCHUNK = KT * KITEMS;
+
+// ---------------------------------------------------------------------------
+// K9.  For each particle: the 4 mesh indices per axis around its CIC nodes
+// (i-1, i, i+1, i+2; wrapped when periodic, ghost cells reached when open),
+// centred differences of Phi = hi + lo at the 8 nodes, weighted with
+// (2^16 - dq, dq) / 2^16, then p -= kick * grad(Phi), x = fl(x + fl(p * c2)),
+// and keep = x inside [klo, khi]^3 (exact float bounds of |x - c| <= R).
+// Block b covers particles [b*KCHUNK, (b+1)*KCHUNK) and writes its keep count.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(KT) k_gather_kick_drift(
+    float4* __restrict__ pos, float4* __restrict__ mom, long long N,
+    const float* __restrict__ ph, const float* __restrict__ pl, int n, int lo, int s,
+    int periodic, float kick, float c2, int do_flag, float klo, float khi,
+    unsigned char* __restrict__ flags, unsigned int* __restrict__ block_keep,
+    float4* __restrict__ forces, unsigned long long* __restrict__ escaped) {
+  const int P = n + 2;
+  const float fn = (float)n;
+  const long long base = (long long)blockIdx.x * KCHUNK;
+  unsigned int keep_count = 0, esc = 0;
+#pragma unroll 1
+  for (int it = 0; it < KITEMS; ++it) {
+    long long p = base + it * KT + threadIdx.x;
+    if (p >= N) break;
+    float4 x = pos[p];
+    float4 v = mom[p];
+    int ix, iy, iz, dx, dy, dz;
+    cic_axis(x.x, ix, dx);
+    cic_axis(x.y, iy, dy);
+    cic_axis(x.z, iz, dz);
+    float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+    bool ok = true;
+    int X[4], Y[4], Z[4];
+    if (periodic) {
+      ok = !(ix < -1 || ix > n - 1 || iy < -1 || iy > n - 1 || iz < -1 || iz > n - 1);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int a = ix - 1 + q, b = iy - 1 + q, c = iz - 1 + q;
+        X[q] = ok ? (a < 0 ? a + n : (a >= n ? a - n : a)) : 0;
+        Y[q] = ok ? (b < 0 ? b + n : (b >= n ? b - n : b)) : 0;
+        Z[q] = ok ? (c < 0 ? c + n : (c >= n ? c - n : c)) : 0;
+      }
+    } else {
+      const int hi = lo + s - 1;
+      ok = !(ix < lo || ix + 1 > hi || iy < lo || iy + 1 > hi || iz < lo || iz + 1 > hi);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        X[q] = ok ? ix - 1 + q : lo;
+        Y[q] = ok ? iy - 1 + q : lo;
+        Z[q] = ok ? iz - 1 + q : lo;
+      }
+    }
+    if (ok) {
+      const float sc = 1.0f / 65536.0f;
+      const float wx[2] = {(float)(65536 - dx) * sc, (float)dx * sc};
+      const float wy[2] = {(float)(65536 - dy) * sc, (float)dy * sc};
+      const float wz[2] = {(float)(65536 - dz) * sc, (float)dz * sc};
+      int RY[4], RZ[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        RY[q] = (Y[q] + 1) * P;
+        RZ[q] = (Z[q] + 1) * P * P;
+      }
+      int CX[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) CX[q] = X[q] + 1;
+      // x-gradients: rows at (y node b, z node c), 4 samples along x
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          int r = RZ[c + 1] + RY[b + 1];
+          float h0 = ph[r + CX[0]], h1 = ph[r + CX[1]], h2 = ph[r + CX[2]], h3 = ph[r + CX[3]];
+          float l0 = pl[r + CX[0]], l1 = pl[r + CX[1]], l2 = pl[r + CX[2]], l3 = pl[r + CX[3]];
+          float g0 = (h2 - h0) + (l2 - l0);
+          float g1 = (h3 - h1) + (l3 - l1);
+          Fx += wy[b] * wz[c] * (wx[0] * g0 + wx[1] * g1);
+        }
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          int r = RZ[c + 1] + CX[a + 1];
+          float h0 = ph[r + RY[0]], h1 = ph[r + RY[1]], h2 = ph[r + RY[2]], h3 = ph[r + RY[3]];
+          float l0 = pl[r + RY[0]], l1 = pl[r + RY[1]], l2 = pl[r + RY[2]], l3 = pl[r + RY[3]];
+          float g0 = (h2 - h0) + (l2 - l0);
+          float g1 = (h3 - h1) + (l3 - l1);
+          Fy += wx[a] * wz[c] * (wy[0] * g0 + wy[1] * g1);
+        }
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          int r = RY[b + 1] + CX[a + 1];
+          float h0 = ph[r + RZ[0]], h1 = ph[r + RZ[1]], h2 = ph[r + RZ[2]], h3 = ph[r + RZ[3]];
+          float l0 = pl[r + RZ[0]], l1 = pl[r + RZ[1]], l2 = pl[r + RZ[2]], l3 = pl[r + RZ[3]];
+          float g0 = (h2 - h0) + (l2 - l0);
+          float g1 = (h3 - h1) + (l3 - l1);
+          Fz += wx[a] * wy[b] * (wz[0] * g0 + wz[1] * g1);
+        }
+      Fx *= 0.5f;
+      Fy *= 0.5f;
+      Fz *= 0.5f;
+    } else {
+      ++esc;
+    }
+    v.x -= kick * Fx;
+    v.y -= kick * Fy;
+    v.z -= kick * Fz;
+    x.x = __fadd_rn(x.x, __fmul_rn(v.x, c2));
+    x.y = __fadd_rn(x.y, __fmul_rn(v.y, c2));
+    x.z = __fadd_rn(x.z, __fmul_rn(v.z, c2));
+    if (periodic) {
+      if (x.x < 0.f) x.x = __fadd_rn(x.x, fn);
+      if (x.x >= fn) x.x = __fsub_rn(x.x, fn);
+      if (x.y < 0.f) x.y = __fadd_rn(x.y, fn);
+      if (x.y >= fn) x.y = __fsub_rn(x.y, fn);
+      if (x.z < 0.f) x.z = __fadd_rn(x.z, fn);
+      if (x.z >= fn) x.z = __fsub_rn(x.z, fn);
+    }
+    pos[p] = x;
+    mom[p] = v;
+    if (forces) forces[p] = make_float4(Fx, Fy, Fz, 0.f);
+    if (do_flag) {
+      bool keep = x.x >= klo && x.x <= khi && x.y >= klo && x.y <= khi && x.z >= klo &&
+                  x.z <= khi;
+      flags[p] = keep ? 1 : 0;
+      keep_count += keep ? 1u : 0u;
+    }
+  }
+  if (do_flag) {
+    __shared__ unsigned int sk[KT / 32];
+    unsigned int w = keep_count;
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if ((threadIdx.x & 31) == 0) sk[threadIdx.x >> 5] = w;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned int t = 0;
+      for (int q = 0; q < KT / 32; ++q) t += sk[q];
+      block_keep[blockIdx.x] = t;
+    }
+  }
+  {
+    unsigned int w = esc;
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if ((threadIdx.x & 31) == 0 && w) atomicAdd(escaped, (unsigned long long)w);
+  }
+}
+
+int gkd_blocks(long long N) { return (int)((N + KCHUNK - 1) / KCHUNK); }
+
+void launch_gather_kick_drift(cudaStream_t st, float4* pos, float4* mom, long long N,
+                              const float* ph, const float* pl, int n, int lo, int s,
+                              int periodic, float kick, float c2, bool do_flag, float klo,
+                              float khi, unsigned char* flags, unsigned int* block_keep,
+                              float4* forces, unsigned long long* escaped) {
+  if (N <= 0) return;
+  k_gather_kick_drift<<<gkd_blocks(N), KT, 0, st>>>(pos, mom, N, ph, pl, n, lo, s, periodic,
+                                                    kick, c2, do_flag ? 1 : 0, klo, khi, flags,
+                                                    block_keep, forces, escaped);
+  note_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Keep flags from an explicit keep cube (pm_shrink), same chunking.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(KT) k_flag(const float4* __restrict__ pos, long long N,
+                                             float klo, float khi,
+                                             unsigned char* __restrict__ flags,
+                                             unsigned int* __restrict__ block_keep) {
+  const long long base = (long long)blockIdx.x * KCHUNK;
+  unsigned int keep_count = 0;
+  for (int it = 0; it < KITEMS; ++it) {
+    long long p = base + it * KT + threadIdx.x;
+    if (p >= N) break;
+    float4 x = pos[p];
+    bool keep = x.x >= klo && x.x <= khi && x.y >= klo && x.y <= khi && x.z >= klo &&
+                x.z <= khi;
+    flags[p] = keep ? 1 : 0;
+    keep_count += keep;
+  }
+  __shared__ unsigned int sk[KT / 32];
+  unsigned int w = keep_count;
+  for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+  if ((threadIdx.x & 31) == 0) sk[threadIdx.x >> 5] = w;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int t = 0;
+    for (int q = 0; q < KT / 32; ++q) t += sk[q];
+    block_keep[blockIdx.x] = t;
+  }
+}
+
+void launch_flag(cudaStream_t st, const float4* pos, long long N, float klo, float khi,
+                 unsigned char* flags, unsigned int* block_keep) {
+  if (N <= 0) return;
+  k_flag<<<gkd_blocks(N), KT, 0, st>>>(pos, N, klo, khi, flags, block_keep);
+  note_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of the per-block keep counts (one CTA; nblk <= 2^24 at
+// 1024 threads x 16k items), total written to *n_keep.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_scan_blocks(const unsigned int* __restrict__ cnt,
+                                                      unsigned long long* __restrict__ off,
+                                                      int nblk,
+                                                      unsigned long long* __restrict__ n_keep) {
+  __shared__ unsigned long long part[1024];
+  const int tid = threadIdx.x;
+  const int per = (nblk + 1023) / 1024;
+  const int b0 = tid * per;
+  unsigned long long s = 0;
+  for (int q = 0; q < per; ++q) {
+    int b = b0 + q;
+    if (b < nblk) s += cnt[b];
+  }
+  part[tid] = s;
+  __syncthreads();
+  // Hillis-Steele inclusive scan over 1024 partials
+  for (int o = 1; o < 1024; o <<= 1) {
+    unsigned long long v = tid >= o ? part[tid - o] : 0ull;
+    __syncthreads();
+    part[tid] += v;
+    __syncthreads();
+  }
+  unsigned long long run = tid ? part[tid - 1] : 0ull;
+  for (int q = 0; q < per; ++q) {
+    int b = b0 + q;
+    if (b < nblk) {
+      off[b] = run;
+      run += cnt[b];
+    }
+  }
+  if (tid == 1023) *n_keep = part[1023];
+}
+
+void launch_scan_blocks(cudaStream_t st, const unsigned int* cnt, unsigned long long* off,
+                        int nblk, unsigned long long* n_keep) {
+  k_scan_blocks<<<1, 1024, 0, st>>>(cnt, off, nblk, n_keep);
+  note_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Stable scatter: survivors to out[keep_off[b] + rank], leavers to the
+// lightcone at lc_base + (b*KCHUNK - keep_off[b]) + rank, both in index order.
+// Leavers get mom.w = a_cross.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(KT) k_scatter(
+    const float4* __restrict__ pos, const float4* __restrict__ mom, long long N,
+    const unsigned char* __restrict__ flags, const unsigned long long* __restrict__ keep_off,
+    float4* __restrict__ pos_out, float4* __restrict__ mom_out, float4* __restrict__ lc_pos,
+    float4* __restrict__ lc_mom, long long lc_base, float a_cross) {
+  __shared__ unsigned int wk[KT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long base = (long long)blockIdx.x * KCHUNK;
+  unsigned long long keep_run = keep_off[blockIdx.x];
+  unsigned long long leave_run = (unsigned long long)base - keep_run;
+  for (int it = 0; it < KITEMS; ++it) {
+    long long p = base + it * KT + threadIdx.x;
+    bool valid = p < N;
+    bool keep = valid && flags[p];
+    unsigned int bal = __ballot_sync(0xffffffffu, keep);
+    unsigned int balv = __ballot_sync(0xffffffffu, valid);
+    if (lane == 0) wk[warp] = __popc(bal);
+    __syncthreads();
+    unsigned int before = 0, row_keep = 0;
+    for (int q = 0; q < KT / 32; ++q) {
+      unsigned int c = wk[q];
+      if (q < warp) before += c;
+      row_keep += c;
+    }
+    unsigned int lanemask = (1u << lane) - 1u;
+    unsigned int krank = before + __popc(bal & lanemask);
+    // leavers before this lane in the row: valid lanes before minus keepers
+    unsigned int vbefore = warp * 32 + __popc(balv & lanemask);
+    unsigned int lrank = vbefore - krank;
+    if (valid) {
+      float4 x = pos[p], v = mom[p];
+      if (keep) {
+        unsigned long long d = keep_run + krank;
+        pos_out[d] = x;
+        mom_out[d] = v;
+      } else {
+        long long d = lc_base + (long long)(leave_run + lrank);
+        v.w = a_cross;
+        lc_pos[d] = x;
+        lc_mom[d] = v;
+      }
+    }
+    long long row_valid = N - (base + it * KT);
+    row_valid = row_valid > KT ? KT : (row_valid < 0 ? 0 : row_valid);
+    keep_run += row_keep;
+    leave_run += (unsigned long long)row_valid - row_keep;
+    __syncthreads();
+  }
+}
+
+void launch_scatter(cudaStream_t st, const float4* pos, const float4* mom, long long N,
+                    const unsigned char* flags, const unsigned long long* keep_off,
+                    float4* pos_out, float4* mom_out, float4* lc_pos, float4* lc_mom,
+                    long long lc_base, float a_cross) {
+  if (N <= 0) return;
+  k_scatter<<<gkd_blocks(N), KT, 0, st>>>(pos, mom, N, flags, keep_off, pos_out, mom_out,
+                                          lc_pos, lc_mom, lc_base, a_cross);
+  note_launch();
+}
+
+}  // namespace pm

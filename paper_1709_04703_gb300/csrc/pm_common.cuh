@@ -1,0 +1,123 @@
+// Shared device types and helpers of libpmshrink (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pmshrink.h"
+
+namespace pm {
+
+// A cubic grid level: `base` points at interior cell (0,0,0); neighbours are
+// at +-1 (x), +-sy (y), +-sz (z).  Cells -1 and s along each axis are the
+// ghost layer (open boundaries) and always exist in memory.
+struct Grid {
+  float* base;
+  int s;
+  int sy;
+  int sz;
+};
+
+__host__ __device__ inline int gidx(const Grid& g, int i, int j, int k) {
+  return i + j * g.sy + k * g.sz;
+}
+
+// Neighbour index along one axis: wraps when periodic, else may reach the
+// ghost at -1 / s.
+__device__ __forceinline__ int wrap_m(int i, int s, int periodic) {
+  return (i == 0 && periodic) ? s - 1 : i - 1;
+}
+__device__ __forceinline__ int wrap_p(int i, int s, int periodic) {
+  return (i == s - 1 && periodic) ? 0 : i + 1;
+}
+
+// ---------------------------------------------------------------------------
+// double-float arithmetic: value = hi + lo, |lo| <= ulp(hi)/2.  Error-free
+// transforms of Knuth (TwoSum) and Dekker (FastTwoSum, TwoProd via FMA),
+// written with round-to-nearest intrinsics so that no contraction changes
+// them.
+// ---------------------------------------------------------------------------
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float e = __fsub_rn(b, __fsub_rn(s, a));
+  return {s, e};
+}
+__device__ __forceinline__ df two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  float e = __fmaf_rn(a, b, -p);
+  return {p, e};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  df t = two_sum(a.lo, b.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = fast_two_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df df_mul(df a, df b) {
+  df p = two_prod(a.hi, b.hi);
+  p.lo = __fadd_rn(p.lo, __fadd_rn(__fmul_rn(a.hi, b.lo), __fmul_rn(a.lo, b.hi)));
+  return fast_two_sum(p.hi, p.lo);
+}
+
+// int64 -> (hi, lo) float pair with relative error <= 2^-48 (exact hi part).
+__device__ __forceinline__ df df_from_i64(long long v) {
+  float hi = __ll2float_rn(v);
+  long long r = v - __float2ll_rn(hi);
+  return {hi, __ll2float_rn(r)};
+}
+
+// ---------------------------------------------------------------------------
+// Fixed-point CIC node and weight along one axis (exact for any float u):
+//   iq = floor(u * 2^16) - 2^15 = floor((u - 1/2) * 2^16),
+//   i  = iq >> 16 (floor division),  dq = iq & 0xffff.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cic_axis(float u, int& i, int& dq) {
+  int iq = __float2int_rd(__fmul_rn(u, 65536.0f)) - 32768;
+  i = iq >> 16;
+  dq = iq & 0xffff;
+}
+
+// Warp-level sum of a double (all lanes get it).
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide reduction of NV doubles into out[NV] (thread 0 holds result).
+template <int NV>
+__device__ inline void block_sum(double (&v)[NV], double* smem /* 32*NV */) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double w = warp_sum(v[q]);
+    if (lane == 0) smem[warp * NV + q] = w;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double w = lane < nw ? smem[lane * NV + q] : 0.0;
+      v[q] = warp_sum(w);
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace pm

@@ -1,0 +1,65 @@
+// Host-side launchers of the libpmshrink kernels (one stream each).
+#pragma once
+
+#include "pm_common.cuh"
+
+namespace pm {
+
+// Counts kernel launches made by the library (pm_launch_count).
+void note_launch();
+
+// k_mesh.cu
+void launch_drift_deposit(cudaStream_t st, int grid, float4* pos, const float4* mom,
+                          long long N, float c0, bool drift, int n, int lo, int s,
+                          int periodic, unsigned long long* rho,
+                          unsigned long long* escaped);
+void launch_source(cudaStream_t st, int grid, unsigned long long* rho, int n, int lo,
+                   int s, Grid fh, Grid fl, double invM, double S, int b0, int b1,
+                   bool moments, double* partial_f2, void* partial_m,
+                   unsigned int* counter, double* out, const double* bgm, int* overflow);
+void launch_source_f64(cudaStream_t st, int grid, const double* delta, int n, Grid fh,
+                       Grid fl, double S, bool moments, double* partial,
+                       unsigned int* counter, double* out);
+void launch_boundary(cudaStream_t st, Grid ph, Grid pl, int n, int lo, const double* mom,
+                     double S, bool want_lo);
+
+// k_mg.cu
+void launch_rbgs(cudaStream_t st, Grid u, Grid b, float h2, int color, int periodic);
+void launch_resid_restrict(cudaStream_t st, Grid u, Grid b, float inv_h2, Grid uc, Grid bc,
+                           int periodic);
+void launch_prolong(cudaStream_t st, Grid uc, Grid u, int periodic);
+void launch_coarse(cudaStream_t st, Grid u, Grid b, float h2, int periodic, int sweeps);
+void launch_defect(cudaStream_t st, Grid ph, Grid pl, Grid fh, Grid fl, Grid rb, Grid e,
+                   int periodic, bool write_r, double* partial, unsigned int* counter,
+                   double* out);
+int defect_blocks(int s);
+void launch_correct(cudaStream_t st, Grid ph, Grid pl, Grid e);
+void launch_fill(cudaStream_t st, Grid g, float v, bool with_ghost);
+void launch_phi_out(cudaStream_t st, Grid ph, Grid pl, float* out32, double* out64,
+                    double shift);
+void launch_sum_phi(cudaStream_t st, Grid ph, Grid pl, double* partial, unsigned int* counter,
+                    double* out);
+
+// k_part.cu
+int gkd_blocks(long long N);
+void launch_gather_kick_drift(cudaStream_t st, float4* pos, float4* mom, long long N,
+                              const float* ph, const float* pl, int n, int lo, int s,
+                              int periodic, float kick, float c2, bool do_flag, float klo,
+                              float khi, unsigned char* flags, unsigned int* block_keep,
+                              float4* forces, unsigned long long* escaped);
+void launch_flag(cudaStream_t st, const float4* pos, long long N, float klo, float khi,
+                 unsigned char* flags, unsigned int* block_keep);
+void launch_scan_blocks(cudaStream_t st, const unsigned int* cnt, unsigned long long* off,
+                        int nblk, unsigned long long* n_keep);
+void launch_scatter(cudaStream_t st, const float4* pos, const float4* mom, long long N,
+                    const unsigned char* flags, const unsigned long long* keep_off,
+                    float4* pos_out, float4* mom_out, float4* lc_pos, float4* lc_mom,
+                    long long lc_base, float a_cross);
+
+// k_pk.cu
+void launch_pk_delta(cudaStream_t st, const unsigned long long* rho, float* delta, int n,
+                     double inv_mean);
+void launch_pk_bin(cudaStream_t st, const float2* dk, int n, double box, double shot,
+                   int n_bins, double* acc);
+
+}  // namespace pm

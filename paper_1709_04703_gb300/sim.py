@@ -1,0 +1,221 @@
+"""Python front end of libpmshrink: torch supplies device memory and the
+stream, the C library does the work (see include/pmshrink.h)."""
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+_PREC = {"mixed": L.PM_MIXED, "fp32": L.PM_FP32_PLAIN}
+_GUESS = {"warm": L.PM_GUESS_WARM, "zero": L.PM_GUESS_ZERO}
+_BC = {"paper": L.PM_BC_PAPER, "open": L.PM_BC_OPEN, "periodic": L.PM_BC_PERIODIC}
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def pack(pos, mom, ids=None, extra=None):
+    """(N,3) float32 positions/momenta (+ int32 ids) -> two (N,4) float32
+    arrays: pos4 = (x, y, z, id bits), mom4 = (px, py, pz, extra)."""
+    pos = np.asarray(pos, dtype=np.float32)
+    mom = np.asarray(mom, dtype=np.float32)
+    n = len(pos)
+    p4 = np.zeros((n, 4), np.float32)
+    m4 = np.zeros((n, 4), np.float32)
+    p4[:, :3] = pos
+    m4[:, :3] = mom
+    ids = np.arange(n, dtype=np.int32) if ids is None else np.asarray(ids, np.int32)
+    p4[:, 3] = ids.view(np.float32)
+    if extra is not None:
+        m4[:, 3] = extra
+    return p4, m4
+
+
+def unpack(p4, m4):
+    p4 = np.asarray(p4, np.float32)
+    m4 = np.asarray(m4, np.float32)
+    ids = np.ascontiguousarray(p4[:, 3]).view(np.int32).copy()
+    return p4[:, :3].copy(), m4[:, :3].copy(), ids, m4[:, 3].copy()
+
+
+class Sim:
+    """One shrinking-domain PM run (one context of the C library)."""
+
+    def __init__(self, pos, mom, ids, n_mesh, box, a_init, a_final, n_steps,
+                 rtol=1e-7, precision="mixed", guess="warm", bc="paper",
+                 shrink=True, buffer_cells=1.0, max_vcycles=50, store_forces=False,
+                 omega_m=0.3, omega_l=0.7, host_init=False):
+        lib = L.load()
+        cfg = L.PmConfig()
+        lib.pm_config_default(C.byref(cfg))
+        cfg.n_mesh = int(n_mesh)
+        cfg.n_particles = int(len(pos))
+        cfg.box_mpch = float(box)
+        cfg.omega_m, cfg.omega_l = float(omega_m), float(omega_l)
+        cfg.a_init, cfg.a_final, cfg.n_steps = float(a_init), float(a_final), int(n_steps)
+        cfg.rtol, cfg.max_vcycles = float(rtol), int(max_vcycles)
+        cfg.precision = _PREC[precision]
+        cfg.guess = _GUESS[guess]
+        cfg.bc = _BC[bc]
+        cfg.shrink = 1 if shrink else 0
+        cfg.buffer_cells = float(buffer_cells)
+        cfg.store_forces = 1 if store_forces else 0
+        self.cfg = cfg
+        self.n_particles = int(len(pos))
+        p4, m4 = pack(pos, mom, ids)
+        self._ctx = C.c_void_p()
+        if host_init:
+            code = lib.pm_init(C.byref(cfg), p4.ctypes.data, m4.ctypes.data, 1,
+                               _stream(), C.byref(self._ctx))
+        else:
+            dp = torch.from_numpy(p4).cuda()
+            dm = torch.from_numpy(m4).cuda()
+            code = lib.pm_init(C.byref(cfg), _ptr(dp), _ptr(dm), 0, _stream(),
+                               C.byref(self._ctx))
+        L.check(code, None)
+        self._lib = lib
+
+    # -- lifecycle ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.pm_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, code):
+        L.check(code, self._ctx)
+
+    # -- stepping ----------------------------------------------------------
+    def step(self, k=1):
+        self._check(self._lib.pm_step(self._ctx, int(k)))
+
+    def shrink(self, a):
+        n = C.c_int64()
+        self._check(self._lib.pm_shrink(self._ctx, float(a), C.byref(n)))
+        return n.value
+
+    def stats(self):
+        s = L.PmStats()
+        self._check(self._lib.pm_stats(self._ctx, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in L.PmStats._fields_}
+
+    def schedule(self):
+        m = self.cfg.n_steps + 1
+        out = {k: np.zeros(m) for k in ("a", "dtau", "a_half", "chi")}
+        self._check(self._lib.pm_schedule(self._ctx, *[out[k].ctypes.data for k in
+                                                       ("a", "dtau", "a_half", "chi")]))
+        return out
+
+    # -- state -------------------------------------------------------------
+    def particles(self):
+        """(pos, mom, ids) of the active particles as numpy arrays."""
+        n = C.c_int64()
+        cap = self.n_particles
+        p4 = np.zeros((cap, 4), np.float32)
+        m4 = np.zeros((cap, 4), np.float32)
+        self._check(self._lib.pm_get_particles(self._ctx, p4.ctypes.data, m4.ctypes.data, 1,
+                                               C.byref(n)))
+        pos, mom, ids, _ = unpack(p4[:n.value], m4[:n.value])
+        return pos, mom, ids
+
+    def particles_device(self, pos4, mom4):
+        """Copy active particles into device float4 tensors (N_cap, 4)."""
+        n = C.c_int64()
+        self._check(self._lib.pm_get_particles(self._ctx, _ptr(pos4), _ptr(mom4), 0,
+                                               C.byref(n)))
+        return n.value
+
+    def set_particles(self, pos4, mom4, n, host=False):
+        if host:
+            self._check(self._lib.pm_set_particles(self._ctx, C.c_void_p(pos4.ctypes.data),
+                                                   C.c_void_p(mom4.ctypes.data), int(n), 1))
+        else:
+            self._check(self._lib.pm_set_particles(self._ctx, _ptr(pos4), _ptr(mom4),
+                                                   int(n), 0))
+
+    def get_particles_host(self, pos4, mom4):
+        """Copy active particles into caller-owned host float4 buffers."""
+        n = C.c_int64()
+        self._check(self._lib.pm_get_particles(
+            self._ctx, C.c_void_p(pos4.data_ptr() if torch.is_tensor(pos4) else pos4.ctypes.data),
+            C.c_void_p(mom4.data_ptr() if torch.is_tensor(mom4) else mom4.ctypes.data), 1,
+            C.byref(n)))
+        return n.value
+
+    def lightcone(self):
+        """(pos, mom, ids, a_cross) of the lightcone records."""
+        n = C.c_int64()
+        cap = self.n_particles
+        p4 = np.zeros((cap, 4), np.float32)
+        m4 = np.zeros((cap, 4), np.float32)
+        self._check(self._lib.pm_get_lightcone(self._ctx, p4.ctypes.data, m4.ctypes.data, 1,
+                                               C.byref(n)))
+        return unpack(p4[:n.value], m4[:n.value])
+
+    def forces(self):
+        n = C.c_int64()
+        f4 = np.zeros((self.n_particles, 4), np.float32)
+        self._check(self._lib.pm_get_forces(self._ctx, f4.ctypes.data, 1, C.byref(n)))
+        return f4[:n.value, :3].copy()
+
+    def potential(self):
+        """(phi (side+2)^3 float64 incl. ghost layer, lo, side) of the last solve."""
+        n = self.cfg.n_mesh
+        buf = np.zeros((n + 2) ** 3)
+        lo, side = C.c_int32(), C.c_int32()
+        self._check(self._lib.pm_get_potential(self._ctx, buf.ctypes.data, C.byref(lo),
+                                               C.byref(side)))
+        s = side.value
+        return buf[:(s + 2) ** 3].reshape(s + 2, s + 2, s + 2), lo.value, s
+
+    def solve_potential(self, delta, a, bc="open", want64=True):
+        """Solve sum_nb(Phi) - 6 Phi = S(a) delta on the whole mesh.
+        delta: (n,n,n) float64 (numpy or cuda tensor).  Returns
+        (phi32 cuda tensor, phi64 cuda tensor or None, vcycles, resid)."""
+        n = self.cfg.n_mesh
+        d = delta if torch.is_tensor(delta) else torch.from_numpy(np.ascontiguousarray(delta))
+        d = d.to(device="cuda", dtype=torch.float64).contiguous()
+        phi = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+        phi64 = torch.empty((n, n, n), dtype=torch.float64, device="cuda") if want64 else None
+        vc, res = C.c_int32(), C.c_double()
+        self._check(self._lib.pm_potential(self._ctx, _ptr(d), float(a), _BC[bc], _ptr(phi),
+                                           _ptr(phi64), C.byref(vc), C.byref(res)))
+        return phi, phi64, vc.value, res.value
+
+
+def power_spectrum(pos4_dev, box, n_mesh, n_bins, subtract_shot=True):
+    """P(k) of device float4 particles (positions in cells of n_mesh)."""
+    lib = L.load()
+    k = np.zeros(n_bins)
+    p = np.zeros(n_bins)
+    m = np.zeros(n_bins)
+    L.check(lib.pm_power_spectrum(_ptr(pos4_dev), int(pos4_dev.shape[0]), float(box),
+                                  int(n_mesh), int(n_bins), 1 if subtract_shot else 0,
+                                  k.ctypes.data, p.ctypes.data, m.ctypes.data, _stream()))
+    return k, p, m
+
+
+def deposit(pos4_dev, n_mesh, lo=0, side=None, periodic=True, mom4_dev=None,
+            drift_coef=0.0, rho=None):
+    """Fixed-point CIC deposit; returns (rho int64 cuda tensor [z,y,x], escaped).
+    With mom4_dev the positions are drifted in place first."""
+    lib = L.load()
+    side = n_mesh if side is None else side
+    if rho is None:
+        rho = torch.zeros((n_mesh, n_mesh, n_mesh), dtype=torch.int64, device="cuda")
+    esc = C.c_int64()
+    L.check(lib.pm_deposit(_ptr(pos4_dev), _ptr(mom4_dev), int(pos4_dev.shape[0]),
+                           float(drift_coef), int(n_mesh), int(lo), int(side),
+                           1 if periodic else 0, _ptr(rho), C.byref(esc), _stream()))
+    return rho, esc.value

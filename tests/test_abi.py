@@ -1,0 +1,77 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/pmshrink.h declares; host-side argument checks work without a GPU."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1709_04703_gb300 import _lib as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pmshrink.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pm_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1709_04703_gb300 import build
+    build.build()
+    return L.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("pm_init", "pm_step", "pm_shrink", "pm_potential", "pm_power_spectrum"):
+        assert must in names
+    assert set(names) == set(L.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", L.LIB_PATH],
+                         capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (pm_[a-z0-9_]+)", out))
+    missing = set(_declared()) - exported
+    assert not missing, missing
+    for name in _declared():
+        assert getattr(lib, name) is not None
+
+
+def test_config_defaults(lib):
+    cfg = L.PmConfig()
+    lib.pm_config_default(C.byref(cfg))
+    assert cfg.n_mesh == 32 and cfg.n_particles == 32**3
+    assert cfg.omega_m == 0.3 and cfg.omega_l == 0.7
+    assert cfg.precision == L.PM_MIXED and cfg.bc == L.PM_BC_PAPER
+    assert cfg.buffer_cells == 1.0 and cfg.shrink == 1
+
+
+@pytest.mark.parametrize("field,value", [("n_mesh", 40), ("n_mesh", 2), ("n_particles", 0),
+                                         ("n_steps", 0), ("rtol", 0.0), ("precision", 7),
+                                         ("bc", 9), ("a_final", 0.01)])
+def test_init_rejects_bad_config_before_touching_the_gpu(lib, field, value):
+    cfg = L.PmConfig()
+    lib.pm_config_default(C.byref(cfg))
+    setattr(cfg, field, value)
+    buf = (C.c_float * 8)()
+    ctx = C.c_void_p(123)
+    code = lib.pm_init(C.byref(cfg), C.cast(buf, C.c_void_p), C.cast(buf, C.c_void_p), 1,
+                       None, C.byref(ctx))
+    assert code == L.PM_EINVAL
+    assert ctx.value is None
+    assert lib.pm_last_error(None).decode().startswith("pm_init")
+
+
+def test_null_context_calls_fail_cleanly(lib):
+    assert lib.pm_step(None, 1) == L.PM_EINVAL
+    assert lib.pm_shrink(None, 0.5, None) == L.PM_EINVAL
+    assert lib.pm_stats(None, None) == L.PM_EINVAL
+    assert lib.pm_power_spectrum(None, 0, 1.0, 8, 4, 1, None, None, None, None) == L.PM_EINVAL
+    assert lib.pm_deposit(None, None, 0, 0.0, 8, 0, 8, 1, None, None, None) == L.PM_EINVAL
+    lib.pm_destroy(None)
