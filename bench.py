@@ -196,8 +196,8 @@ def run_ours(args):
 
     # timed: K steps from the ICs, device-resident inputs
     sim = _new_sim(pos, mom, ids, cfg, args.rtol, args.precision)
-    lib.pm_profile(sim._ctx, 1)
-    stream = torch.cuda.current_stream()
+    sim.profile(True)
+    stream = sim.stream   # the stream every kernel of the context is launched on
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0 = lib.pm_launch_count()
     ps0 = sim.stats()["particle_steps"]
@@ -215,12 +215,8 @@ def run_ours(args):
     st = sim.stats()
     psteps = st["particle_steps"] - ps0
     launches = lib.pm_launch_count() - l0
-    prof = {}
+    prof = sim.profile_read()
     import ctypes as C
-    for c, name in enumerate(L.PROF_CLASSES):
-        t, g, b = C.c_double(), C.c_int64(), C.c_double()
-        lib.pm_profile_read(sim._ctx, c, C.byref(t), C.byref(g), C.byref(b))
-        prof[name] = {"ms": t.value, "groups": g.value, "bytes": b.value}
     vstats = {"vcycles_total": st["vcycles_total"], "n_active_end": st["n_active"],
               "n_lightcone": st["n_lightcone"], "escaped": st["escaped"]}
     sim.close()

@@ -349,13 +349,22 @@ def shrink(arrays, keep):
 # the whole step and the whole run
 # --------------------------------------------------------------------------
 
-def step(pos, mom, k, sched, n, om, nbar, want=False):
-    """Advance FP64 state (pos, mom) by step k.  Returns (pos, mom, info)."""
+def step(pos, mom, k, sched, n, om, nbar, want=False, drift32=False):
+    """Advance FP64 state (pos, mom) by step k.  Returns (pos, mom, info).
+
+    drift32=True takes the first half drift in the CUDA kernel's documented
+    float32 arithmetic (drift_fp32) so that both sides deposit the same float
+    positions; everything after it stays FP64."""
     a0, a1 = sched["a"][k], sched["a"][k + 1]
     dtau, ah = sched["dtau"][k], sched["a_half"][k]
     R0 = sched["R"][k]
     lo, s, periodic = active_cube(R0, n)
-    pos = drift(pos, mom, dtau / (2 * a0), n, periodic)
+    if drift32:
+        pos = drift_fp32(np.asarray(pos, np.float32), np.asarray(mom, np.float32),
+                         dtau / (2 * a0), n, periodic).astype(np.float64)
+    else:
+        pos = drift(pos, mom, dtau / (2 * a0), n, periodic)
+    pos_half = pos
     rho, esc = deposit(pos, n, lo, s, periodic)
     f, phi = solve_step_potential(rho, n, lo, s, periodic, nbar, R0, ah, om)
     F, _ = gather_force(phi, pos, n, lo, s, periodic)
@@ -363,7 +372,7 @@ def step(pos, mom, k, sched, n, om, nbar, want=False):
     pos = drift(pos, mom, dtau / (2 * a1), n, periodic)
     info = dict(lo=lo, s=s, periodic=periodic, escaped=esc)
     if want:
-        info.update(rho=rho, f=f, phi=phi, F=F)
+        info.update(rho=rho, f=f, phi=phi, F=F, x_half=pos_half)
     return pos, mom, info
 
 

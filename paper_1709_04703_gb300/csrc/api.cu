@@ -7,6 +7,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -144,15 +145,30 @@ struct pm_ctx {
   int lo = 0, s = 0, periodic = 1;
   bool cube_valid = false;
 
+  // CUDA graph of one V-cycle for the current cube and level-0 grids (needs a
+  // non-default stream to capture on)
+  bool use_graphs = false;
+  bool capturing = false;
+  int ev_graph_next = 0;
+  struct VGraph {
+    bool valid = false;
+    int lo = 0, s = 0, per = 0, prof = 0;
+    float *u0 = nullptr, *b0 = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;
+  } vg;
+
   // per-class event timing (pm_profile)
   bool prof_on = false;
   std::vector<cudaEvent_t> ev;
   int ev_next = 0;
   struct Pend { int cls, e0, e1; double bytes; };
   std::vector<Pend> pend;
+  std::vector<Pend> pend_graph;  // event pairs recorded inside the V-cycle graph
   double prof_ms[PM_PROF_N] = {0};
   long long prof_groups[PM_PROF_N] = {0};
   double prof_bytes[PM_PROF_N] = {0};
+  long long prof_lost = 0;
 
   int vcycles_last = 0;
   long long vcycles_total = 0;
@@ -282,15 +298,27 @@ void prof_flush(pm_ctx* ctx) {
       ctx->prof_ms[p.cls] += ms;
       ctx->prof_groups[p.cls] += 1;
       ctx->prof_bytes[p.cls] += p.bytes;
+    } else {
+      cudaGetLastError();  // a timing failure must not surface as a launch error
+      ctx->prof_lost += 1;
     }
   }
   ctx->pend.clear();
   ctx->ev_next = 0;
 }
 
+constexpr int EV_POOL = 1024;  // events [0, EV_POOL) eager, [EV_POOL, 2 EV_POOL) graph
+
 int prof_begin(pm_ctx* ctx) {
   if (!ctx->prof_on) return -1;
-  if (ctx->ev_next + 2 > (int)ctx->ev.size()) {
+  if (ctx->capturing) {
+    if (ctx->ev_graph_next + 2 > 2 * EV_POOL) return -1;
+    int e = ctx->ev_graph_next++;
+    // inside a capture only an external record becomes a real event node
+    cudaEventRecordWithFlags(ctx->ev[e], ctx->st, cudaEventRecordExternal);
+    return e;
+  }
+  if (ctx->ev_next + 2 > EV_POOL) {
     cudaStreamSynchronize(ctx->st);
     prof_flush(ctx);
   }
@@ -301,6 +329,12 @@ int prof_begin(pm_ctx* ctx) {
 
 void prof_end(pm_ctx* ctx, int cls, int e0, double bytes) {
   if (e0 < 0) return;
+  if (ctx->capturing) {
+    int e1 = ctx->ev_graph_next++;
+    cudaEventRecordWithFlags(ctx->ev[e1], ctx->st, cudaEventRecordExternal);
+    ctx->pend_graph.push_back({cls, e0, e1, bytes});
+    return;
+  }
   int e1 = ctx->ev_next++;
   cudaEventRecord(ctx->ev[e1], ctx->st);
   ctx->pend.push_back({cls, e0, e1, bytes});
@@ -334,17 +368,19 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0) {
   // prolongation reads the coarse u (0.5) and updates the fine u (8).
   float h2 = 1.0f;
   int ec = -1;
+  // open-boundary ghost factor of level l (spacing H = 2^l), see k_mg.cu
+  auto gam = [](int l) { float H = (float)(1 << l); return (H - 1.0f) / (H + 1.0f); };
   for (int l = 0; l < L; ++l) {
     int e = l == 0 ? prof_begin(ctx) : -1;
     for (int sw = 0; sw < 2; ++sw) {
-      launch_rbgs(ctx->st, U[l], B[l], h2, 0, per);
-      launch_rbgs(ctx->st, U[l], B[l], h2, 1, per);
+      launch_rbgs(ctx->st, U[l], B[l], h2, 0, per, gam(l));
+      launch_rbgs(ctx->st, U[l], B[l], h2, 1, per, gam(l));
     }
     if (l == 0) {
       prof_end(ctx, PM_PROF_SMOOTH0, e, 4 * 8.0 * c0);
       e = prof_begin(ctx);
     }
-    launch_resid_restrict(ctx->st, U[l], B[l], 1.0f / h2, U[l + 1], B[l + 1], per);
+    launch_resid_restrict(ctx->st, U[l], B[l], 1.0f / h2, U[l + 1], B[l + 1], per, gam(l));
     if (l == 0) {
       prof_end(ctx, PM_PROF_TRANSFER0, e, 9.0 * c0);
       ec = prof_begin(ctx);
@@ -352,7 +388,7 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0) {
     h2 *= 4.0f;
   }
   if (L == 0) ec = prof_begin(ctx);
-  launch_coarse(ctx->st, U[L], B[L], h2, per, COARSE_SWEEPS);
+  launch_coarse(ctx->st, U[L], B[L], h2, per, COARSE_SWEEPS, gam(L));
   for (int l = L - 1; l >= 0; --l) {
     h2 *= 0.25f;
     int e = -1;
@@ -360,19 +396,69 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0) {
       prof_end(ctx, PM_PROF_COARSE, ec, (L > 0 ? 8.0 / 7.0 * 81.0 * c0 / 8.0 : 0.0));
       e = prof_begin(ctx);
     }
-    launch_prolong(ctx->st, U[l + 1], U[l], per);
+    launch_prolong(ctx->st, U[l + 1], U[l], per, gam(l + 1));
     if (l == 0) {
       prof_end(ctx, PM_PROF_TRANSFER0, e, 8.5 * c0);
       e = prof_begin(ctx);
     }
     for (int sw = 0; sw < 2; ++sw) {
-      launch_rbgs(ctx->st, U[l], B[l], h2, 0, per);
-      launch_rbgs(ctx->st, U[l], B[l], h2, 1, per);
+      launch_rbgs(ctx->st, U[l], B[l], h2, 0, per, gam(l));
+      launch_rbgs(ctx->st, U[l], B[l], h2, 1, per, gam(l));
     }
     if (l == 0) prof_end(ctx, PM_PROF_SMOOTH0, e, 4 * 8.0 * c0);
   }
   if (L == 0) prof_end(ctx, PM_PROF_COARSE, ec, 0.0);
   CKL();
+  return PM_OK;
+}
+
+void drop_graph(pm_ctx* ctx) {
+  if (ctx->vg.exec) cudaGraphExecDestroy(ctx->vg.exec);
+  ctx->vg = pm_ctx::VGraph();
+}
+
+// One V-cycle: replay of a graph captured for the current cube / grids, or
+// eager launches when the context's stream cannot be captured.
+pm_status vcycle_run(pm_ctx* ctx, Grid u0, Grid b0) {
+  if (!ctx->use_graphs) return vcycle(ctx, u0, b0);
+  auto& g = ctx->vg;
+  if (!(g.valid && g.lo == ctx->lo && g.s == ctx->s && g.per == ctx->periodic &&
+        g.u0 == u0.base && g.b0 == b0.base && g.prof == (int)ctx->prof_on)) {
+    drop_graph(ctx);
+    CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
+    ctx->capturing = true;
+    ctx->ev_graph_next = EV_POOL;
+    ctx->pend_graph.clear();
+    long long l0 = g_launches.load();
+    pm_status st = vcycle(ctx, u0, b0);
+    ctx->capturing = false;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->st, &graph);
+    long long nk = g_launches.load() - l0;
+    g_launches.fetch_sub(nk);
+    if (st != PM_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess)
+      return fail(ctx, PM_ECUDA, std::string("V-cycle capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess)
+      return fail(ctx, PM_ECUDA, std::string("V-cycle instantiate: ") + cudaGetErrorString(e));
+    g.valid = true;
+    g.lo = ctx->lo;
+    g.s = ctx->s;
+    g.per = ctx->periodic;
+    g.u0 = u0.base;
+    g.b0 = b0.base;
+    g.prof = ctx->prof_on;
+    g.kernels = nk;
+  }
+  CK(cudaGraphLaunch(g.exec, ctx->st));
+  g_launches.fetch_add(g.kernels);
+  if (ctx->prof_on)
+    ctx->pend.insert(ctx->pend.end(), ctx->pend_graph.begin(), ctx->pend_graph.end());
   return PM_OK;
 }
 
@@ -411,13 +497,13 @@ pm_status solve(pm_ctx* ctx) {
       return fail(ctx, PM_ENOCONV, buf);
     }
     if (mixed) {
-      pm_status v = vcycle(ctx, e0, r0);
+      pm_status v = vcycle_run(ctx, e0, r0);
       if (v != PM_OK) return v;
       int ee = prof_begin(ctx);
       launch_correct(ctx->st, ph, pl, e0);
       prof_end(ctx, PM_PROF_CORRECT, ee, 20.0 * cells);
     } else {
-      pm_status v = vcycle(ctx, ph, fh);
+      pm_status v = vcycle_run(ctx, ph, fh);
       if (v != PM_OK) return v;
     }
   }
@@ -507,6 +593,7 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
   ctx = new pm_ctx();
   ctx->cfg = *cfg;
   ctx->st = (cudaStream_t)stream;
+  ctx->use_graphs = stream != nullptr && getenv("PM_NO_GRAPHS") == nullptr;
   ctx->n = cfg->n_mesh;
   ctx->P = cfg->n_mesh + 2;
   ctx->N0 = cfg->n_particles;
@@ -569,7 +656,7 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
   }
   const int maxblk = std::max(std::max(SRC_GRID, defect_blocks(n)), 4096);
   AL(ctx->partial, sizeof(double) * 16 * maxblk);
-  AL(ctx->partial_m, 16 * 10 * (size_t)SRC_GRID);
+  AL(ctx->partial_m, 16 * 10 * (size_t)maxblk);
   AL(ctx->counter, sizeof(unsigned int) * 4);
   AL(ctx->d_scal, sizeof(double) * 16);
   AL(ctx->bgm, sizeof(double) * 10);
@@ -748,7 +835,7 @@ pm_status pm_deposit(float* pos4_dev, const float* mom4_dev, int64_t n, float dr
                      int32_t n_mesh, int32_t lo, int32_t side, int32_t periodic,
                      int64_t* rho_dev, int64_t* escaped_out, void* stream) {
   pm_ctx* ctx = nullptr;
-  if (!pos4_dev || !rho_dev || n < 0 || n_mesh < 1 || side < 1 || lo < 0 || lo + side > n_mesh)
+  if ((!pos4_dev && n > 0) || !rho_dev || n < 0 || n_mesh < 1 || side < 1 || lo < 0 || lo + side > n_mesh)
     return fail(nullptr, PM_EINVAL, "pm_deposit: bad argument");
   if (periodic && (lo != 0 || side != n_mesh))
     return fail(nullptr, PM_EINVAL, "pm_deposit: periodic needs the whole mesh");
@@ -946,7 +1033,7 @@ pm_status pm_profile(pm_ctx* ctx, int32_t enable) {
   CK(cudaStreamSynchronize(ctx->st));
   prof_flush(ctx);
   if (enable && ctx->ev.empty()) {
-    ctx->ev.resize(2048);
+    ctx->ev.resize(2 * EV_POOL);
     for (auto& e : ctx->ev) CK(cudaEventCreate(&e));
   }
   for (int c = 0; c < PM_PROF_N; ++c) {
@@ -986,6 +1073,7 @@ void pm_destroy(pm_ctx* ctx) {
     if (p) cudaFree(p);
   for (float* p : ctx->lu) if (p) cudaFree(p);
   for (float* p : ctx->lb) if (p) cudaFree(p);
+  drop_graph(ctx);
   for (auto& e : ctx->ev) cudaEventDestroy(e);
   if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
   if (ctx->h_cnt) cudaFreeHost(ctx->h_cnt);

@@ -149,13 +149,10 @@ __global__ void __launch_bounds__(256) k_source(
 #pragma unroll
   for (int q = 0; q < SRC_NV; ++q) acc[q] = 0;
   float f2 = 0.f;
-  const long long total = (long long)s * s * s;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    int i = (int)(t % s);
-    long long r = t / s;
-    int j = (int)(r % s);
-    int k = (int)(r / s);
+  // block (32, 8) covers an x-y tile; the grid's z dimension strides over planes
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  for (int k = blockIdx.z; k < s && i < s && j < s; k += gridDim.z) {
     int gi = lo + i, gj = lo + j, gk = lo + k;
     long long ri = ((long long)gk * n + gj) * n + gi;
     unsigned long long cnt = rho[ri];
@@ -188,7 +185,10 @@ __global__ void __launch_bounds__(256) k_source(
   // block reduction: ||f||^2 in double, moments in int128
   __shared__ double sf[32];
   __shared__ __int128 sm[32 * SRC_NV];
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+  int lane = tid & 31, warp = tid >> 5, nw = (blockDim.x * blockDim.y) >> 5;
   double w = warp_sum((double)f2);
   if (lane == 0) sf[warp] = w;
   if (MOMENTS) {
@@ -200,42 +200,77 @@ __global__ void __launch_bounds__(256) k_source(
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  __shared__ bool last;
+  if (tid == 0) {
     double tf = 0.0;
     for (int q = 0; q < nw; ++q) tf += sf[q];
-    partial_f2[blockIdx.x] = tf;
+    partial_f2[bid] = tf;
     if (MOMENTS) {
       for (int q = 0; q < SRC_NV; ++q) {
         __int128 v = 0;
         for (int u = 0; u < nw; ++u) v += sm[u * SRC_NV + q];
-        partial_m[blockIdx.x * SRC_NV + q] = v;
+        partial_m[bid * SRC_NV + q] = v;
+      }
+    }
+    __threadfence();
+    last = (atomicAdd(counter, 1u) == nblk - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  // the last block folds all partials: strided per thread, then block-wide
+  double tf = 0.0;
+  __int128 tot[SRC_NV];
+#pragma unroll
+  for (int q = 0; q < SRC_NV; ++q) tot[q] = 0;
+  const int nth = blockDim.x * blockDim.y;
+  for (unsigned b = tid; b < nblk; b += nth) {
+    tf += __ldcg(partial_f2 + b);
+    if (MOMENTS) {
+#pragma unroll
+      for (int q = 0; q < SRC_NV; ++q) {
+        const unsigned long long* pp =
+            reinterpret_cast<const unsigned long long*>(partial_m + b * SRC_NV + q);
+        unsigned long long plo = __ldcg(pp), phi = __ldcg(pp + 1);
+        tot[q] += (__int128)(((unsigned __int128)phi << 64) | plo);
       }
     }
   }
-  if (!arrive_last(counter)) return;
-  if (threadIdx.x == 0) {
-    double tf = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) tf += __ldcg(partial_f2 + b);
-    out[0] = tf;
+  tf = warp_sum(tf);
+  if (MOMENTS) {
+#pragma unroll
+    for (int q = 0; q < SRC_NV; ++q)
+      for (int o = 16; o > 0; o >>= 1) tot[q] += shfl_xor_i128(tot[q], o);
+  }
+  __syncthreads();
+  if (lane == 0) {
+    sf[warp] = tf;
+    if (MOMENTS)
+      for (int q = 0; q < SRC_NV; ++q) sm[warp * SRC_NV + q] = tot[q];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += sf[w];
+    out[0] = t;
     if (MOMENTS) {
-      __int128 tot[SRC_NV];
-      for (int q = 0; q < SRC_NV; ++q) tot[q] = 0;
-      for (unsigned b = 0; b < gridDim.x; ++b)
-        for (int q = 0; q < SRC_NV; ++q) {
-          const unsigned long long* pp =
-              reinterpret_cast<const unsigned long long*>(partial_m + b * SRC_NV + q);
-          unsigned long long plo = __ldcg(pp), phi = __ldcg(pp + 1);
-          tot[q] += (__int128)(((unsigned __int128)phi << 64) | plo);
-        }
+      __int128 T[SRC_NV];
+      for (int q = 0; q < SRC_NV; ++q) {
+        T[q] = 0;
+        for (int w = 0; w < nw; ++w) T[q] += sm[w * SRC_NV + q];
+      }
       // moments of rho / M in cell units (X = 2y) minus the background's
       double m[SRC_NV];
-      m[0] = i128_to_double(tot[0]) * invM2_hi;
-      for (int q = 1; q < 4; ++q) m[q] = i128_to_double(tot[q]) * invM2_hi * 0.5;
-      for (int q = 4; q < 10; ++q) m[q] = i128_to_double(tot[q]) * invM2_hi * 0.25;
+      m[0] = i128_to_double(T[0]) * invM2_hi;
+      for (int q = 1; q < 4; ++q) m[q] = i128_to_double(T[q]) * invM2_hi * 0.5;
+      for (int q = 4; q < 10; ++q) m[q] = i128_to_double(T[q]) * invM2_hi * 0.25;
       for (int q = 0; q < SRC_NV; ++q) out[1 + q] = m[q] - bgm[q];
     }
     *counter = 0u;
   }
+}
+
+dim3 source_grid(int s) {
+  return dim3((unsigned)((s + 31) / 32), (unsigned)((s + 7) / 8), (unsigned)(s < 16 ? s : 16));
 }
 
 void launch_source(cudaStream_t st, int grid, unsigned long long* rho, int n, int lo,
@@ -248,11 +283,11 @@ void launch_source(cudaStream_t st, int grid, unsigned long long* rho, int n, in
   Sd.hi = (float)S;
   Sd.lo = (float)(S - (double)Sd.hi);
   if (moments)
-    k_source<true><<<grid, 256, 0, st>>>(rho, n, lo, s, fh, fl, invMd, Sd, b0, b1,
+    k_source<true><<<source_grid(s), dim3(32, 8), 0, st>>>(rho, n, lo, s, fh, fl, invMd, Sd, b0, b1,
                                          partial_f2, (__int128*)partial_m, counter, out,
                                          bgm, invM, overflow);
   else
-    k_source<false><<<grid, 256, 0, st>>>(rho, n, lo, s, fh, fl, invMd, Sd, b0, b1,
+    k_source<false><<<source_grid(s), dim3(32, 8), 0, st>>>(rho, n, lo, s, fh, fl, invMd, Sd, b0, b1,
                                           partial_f2, (__int128*)partial_m, counter, out,
                                           bgm, invM, overflow);
   note_launch();

@@ -12,8 +12,20 @@ namespace pm {
 //   u = (sum_nb u - h^2 b) / 6.
 // Thread layout: x over half a row (s even), y, z over rows.
 // ---------------------------------------------------------------------------
+// Open boundaries on coarse levels: the fine problem's error vanishes at the
+// finest ghost-cell centre, half a fine cell outside the cube face.  On level
+// l (spacing H = 2^l) the ghost centre lies H/2 outside the face, so a linear
+// profile through that point gives ghost = -gam * (adjacent interior value)
+// with gam = (H - 1) / (H + 1) (0 on the finest level, where the ghost layer
+// holds the Dirichlet data itself).  Coarse ghosts are stored as zero and the
+// -gam term is folded into the diagonal: 6 + gam * (number of ghost faces).
+__device__ __forceinline__ float bnd_diag(int i, int j, int k, int s, float gam) {
+  int nb = (i == 0) + (i == s - 1) + (j == 0) + (j == s - 1) + (k == 0) + (k == s - 1);
+  return 6.0f + gam * (float)nb;
+}
+
 __global__ void __launch_bounds__(256) k_rbgs(Grid u, Grid b, float h2, int color,
-                                              int periodic) {
+                                              int periodic, float gam) {
   const int s = u.s;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -27,7 +39,10 @@ __global__ void __launch_bounds__(256) k_rbgs(Grid u, Grid b, float h2, int colo
   const float* p = u.base + c;
   float sum = (p[xm] + p[xp]) + (p[ym] + p[yp]) + (p[zm] + p[zp]);
   float bv = b.base[gidx(b, i, j, k)];
-  u.base[c] = (sum - h2 * bv) * (1.0f / 6.0f);
+  if (periodic || gam == 0.0f)
+    u.base[c] = (sum - h2 * bv) * (1.0f / 6.0f);
+  else
+    u.base[c] = (sum - h2 * bv) / bnd_diag(i, j, k, s, gam);
 }
 
 // ---------------------------------------------------------------------------
@@ -35,7 +50,8 @@ __global__ void __launch_bounds__(256) k_rbgs(Grid u, Grid b, float h2, int colo
 // averaged into the coarse right-hand side; the coarse unknown is zeroed.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_resid_restrict(Grid u, Grid b, float inv_h2,
-                                                        Grid uc, Grid bc, int periodic) {
+                                                        Grid uc, Grid bc, int periodic,
+                                                        float gam) {
   const int s = u.s;
   const int sc = uc.s;
   int I = blockIdx.x * blockDim.x + threadIdx.x;
@@ -55,7 +71,8 @@ __global__ void __launch_bounds__(256) k_resid_restrict(Grid u, Grid b, float in
         int xm = wrap_m(i, s, periodic) - i, xp = wrap_p(i, s, periodic) - i;
         int ym = (wrap_m(j, s, periodic) - j) * u.sy, yp = (wrap_p(j, s, periodic) - j) * u.sy;
         int zm = (wrap_m(k, s, periodic) - k) * u.sz, zp = (wrap_p(k, s, periodic) - k) * u.sz;
-        float lap = (p[xm] + p[xp]) + (p[ym] + p[yp]) + (p[zm] + p[zp]) - 6.0f * p[0];
+        float diag = (periodic || gam == 0.0f) ? 6.0f : bnd_diag(i, j, k, s, gam);
+        float lap = (p[xm] + p[xp]) + (p[ym] + p[yp]) + (p[zm] + p[zp]) - diag * p[0];
         acc += b.base[gidx(b, i, j, k)] - lap * inv_h2;
       }
   int cc = gidx(uc, I, J, K);
@@ -68,7 +85,8 @@ __global__ void __launch_bounds__(256) k_resid_restrict(Grid u, Grid b, float in
 // (weights 3/4 on the parent, 1/4 on the next coarse cell per axis).  Coarse
 // ghosts are zero (open) or wrap (periodic).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_prolong(Grid uc, Grid u, int periodic) {
+__global__ void __launch_bounds__(256) k_prolong(Grid uc, Grid u, int periodic,
+                                                 float gam_c) {
   const int s = u.s;
   const int sc = uc.s;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -79,16 +97,23 @@ __global__ void __launch_bounds__(256) k_prolong(Grid uc, Grid u, int periodic) 
   int I2 = (i & 1) ? I + 1 : I - 1;
   int J2 = (j & 1) ? J + 1 : J - 1;
   int K2 = (k & 1) ? K + 1 : K - 1;
+  // open: a coarse ghost is -gam_c times the interior value beside it (per
+  // axis), see bnd_diag
+  float fx = 1.0f, fy = 1.0f, fz = 1.0f;
   if (periodic) {
     I2 = (I2 + sc) % sc;
     J2 = (J2 + sc) % sc;
     K2 = (K2 + sc) % sc;
+  } else {
+    if (I2 < 0 || I2 >= sc) { I2 = I; fx = -gam_c; }
+    if (J2 < 0 || J2 >= sc) { J2 = J; fy = -gam_c; }
+    if (K2 < 0 || K2 >= sc) { K2 = K; fz = -gam_c; }
   }
   const float* q = uc.base;
-  float c000 = q[gidx(uc, I, J, K)], c100 = q[gidx(uc, I2, J, K)];
-  float c010 = q[gidx(uc, I, J2, K)], c110 = q[gidx(uc, I2, J2, K)];
-  float c001 = q[gidx(uc, I, J, K2)], c101 = q[gidx(uc, I2, J, K2)];
-  float c011 = q[gidx(uc, I, J2, K2)], c111 = q[gidx(uc, I2, J2, K2)];
+  float c000 = q[gidx(uc, I, J, K)], c100 = fx * q[gidx(uc, I2, J, K)];
+  float c010 = fy * q[gidx(uc, I, J2, K)], c110 = fx * fy * q[gidx(uc, I2, J2, K)];
+  float c001 = fz * q[gidx(uc, I, J, K2)], c101 = fx * fz * q[gidx(uc, I2, J, K2)];
+  float c011 = fy * fz * q[gidx(uc, I, J2, K2)], c111 = fx * fy * fz * q[gidx(uc, I2, J2, K2)];
   float a0 = 0.75f * c000 + 0.25f * c100, a1 = 0.75f * c010 + 0.25f * c110;
   float a2 = 0.75f * c001 + 0.25f * c101, a3 = 0.75f * c011 + 0.25f * c111;
   float b0 = 0.75f * a0 + 0.25f * a1, b1 = 0.75f * a2 + 0.25f * a3;
@@ -100,7 +125,7 @@ __global__ void __launch_bounds__(256) k_prolong(Grid uc, Grid u, int periodic) 
 // the right-hand side and the result are projected to zero mean.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(512) k_coarse(Grid u, Grid b, float h2, int periodic,
-                                                int sweeps) {
+                                                int sweeps, float gam) {
   const int s = u.s;
   const int P = s + 2;
   __shared__ float su[10 * 10 * 10];
@@ -143,7 +168,7 @@ __global__ void __launch_bounds__(512) k_coarse(Grid u, Grid b, float h2, int pe
 #define SU(a, b2, c2) su[((c2) + 1) * P * P + ((b2) + 1) * P + (a) + 1]
           float sum = SU(im, j, k) + SU(ip, j, k) + SU(i, jm, k) + SU(i, jp, k) +
                       SU(i, j, km) + SU(i, j, kp);
-          SU(i, j, k) = (sum - h2 * sb[t]) * (1.0f / 6.0f);
+          SU(i, j, k) = (sum - h2 * sb[t]) / (periodic ? 6.0f : bnd_diag(i, j, k, s, gam));
 #undef SU
         }
       }
@@ -160,7 +185,7 @@ __global__ void __launch_bounds__(512) k_coarse(Grid u, Grid b, float h2, int pe
 #define SU(a, b2, c2) su[((c2) + 1) * P * P + ((b2) + 1) * P + (a) + 1]
         float sum = SU(im, j, k) + SU(ip, j, k) + SU(i, jm, k) + SU(i, jp, k) +
                     SU(i, j, km) + SU(i, j, kp);
-        SU(i, j, k) = (sum - h2 * sb[t]) * (1.0f / 6.0f);
+        SU(i, j, k) = (sum - h2 * sb[t]) / (periodic ? 6.0f : bnd_diag(i, j, k, s, gam));
 #undef SU
       }
       __syncthreads();
@@ -194,21 +219,24 @@ __global__ void __launch_bounds__(512) k_coarse(Grid u, Grid b, float h2, int pe
 static inline dim3 grid_half(int s) { return dim3((unsigned)((s / 2 + 31) / 32), (unsigned)((s + 7) / 8), (unsigned)s); }
 static inline dim3 grid_full(int s) { return dim3((unsigned)((s + 31) / 32), (unsigned)((s + 7) / 8), (unsigned)s); }
 
-void launch_rbgs(cudaStream_t st, Grid u, Grid b, float h2, int color, int periodic) {
-  k_rbgs<<<grid_half(u.s), dim3(32, 8), 0, st>>>(u, b, h2, color, periodic);
+void launch_rbgs(cudaStream_t st, Grid u, Grid b, float h2, int color, int periodic,
+                 float gam) {
+  k_rbgs<<<grid_half(u.s), dim3(32, 8), 0, st>>>(u, b, h2, color, periodic, gam);
   note_launch();
 }
 void launch_resid_restrict(cudaStream_t st, Grid u, Grid b, float inv_h2, Grid uc, Grid bc,
-                           int periodic) {
-  k_resid_restrict<<<grid_full(uc.s), dim3(32, 8), 0, st>>>(u, b, inv_h2, uc, bc, periodic);
+                           int periodic, float gam) {
+  k_resid_restrict<<<grid_full(uc.s), dim3(32, 8), 0, st>>>(u, b, inv_h2, uc, bc, periodic,
+                                                            gam);
   note_launch();
 }
-void launch_prolong(cudaStream_t st, Grid uc, Grid u, int periodic) {
-  k_prolong<<<grid_full(u.s), dim3(32, 8), 0, st>>>(uc, u, periodic);
+void launch_prolong(cudaStream_t st, Grid uc, Grid u, int periodic, float gam_c) {
+  k_prolong<<<grid_full(u.s), dim3(32, 8), 0, st>>>(uc, u, periodic, gam_c);
   note_launch();
 }
-void launch_coarse(cudaStream_t st, Grid u, Grid b, float h2, int periodic, int sweeps) {
-  k_coarse<<<1, 512, 0, st>>>(u, b, h2, periodic, sweeps);
+void launch_coarse(cudaStream_t st, Grid u, Grid b, float h2, int periodic, int sweeps,
+                   float gam) {
+  k_coarse<<<1, 512, 0, st>>>(u, b, h2, periodic, sweeps, gam);
   note_launch();
 }
 

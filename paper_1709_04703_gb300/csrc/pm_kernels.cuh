@@ -24,11 +24,13 @@ void launch_boundary(cudaStream_t st, Grid ph, Grid pl, int n, int lo, const dou
                      double S, bool want_lo);
 
 // k_mg.cu
-void launch_rbgs(cudaStream_t st, Grid u, Grid b, float h2, int color, int periodic);
+void launch_rbgs(cudaStream_t st, Grid u, Grid b, float h2, int color, int periodic,
+                 float gam);
 void launch_resid_restrict(cudaStream_t st, Grid u, Grid b, float inv_h2, Grid uc, Grid bc,
-                           int periodic);
-void launch_prolong(cudaStream_t st, Grid uc, Grid u, int periodic);
-void launch_coarse(cudaStream_t st, Grid u, Grid b, float h2, int periodic, int sweeps);
+                           int periodic, float gam);
+void launch_prolong(cudaStream_t st, Grid uc, Grid u, int periodic, float gam_c);
+void launch_coarse(cudaStream_t st, Grid u, Grid b, float h2, int periodic, int sweeps,
+                   float gam);
 void launch_defect(cudaStream_t st, Grid ph, Grid pl, Grid fh, Grid fl, Grid rb, Grid e,
                    int periodic, bool write_r, double* partial, unsigned int* counter,
                    double* out);

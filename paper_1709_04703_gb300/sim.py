@@ -16,6 +16,20 @@ def _stream():
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
+class _On:
+    """Order work on `stream` after the caller's current stream, and the
+    caller's stream after it (device tensors cross between the two)."""
+
+    def __init__(self, stream):
+        self.stream = stream
+
+    def __enter__(self):
+        self.stream.wait_stream(torch.cuda.current_stream())
+
+    def __exit__(self, *a):
+        torch.cuda.current_stream().wait_stream(self.stream)
+
+
 def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
 
@@ -68,16 +82,21 @@ class Sim:
         cfg.store_forces = 1 if store_forces else 0
         self.cfg = cfg
         self.n_particles = int(len(pos))
+        # the context runs on its own stream so that its V-cycle can be
+        # captured as a CUDA graph
+        self.stream = torch.cuda.Stream()
+        self._sp = C.c_void_p(self.stream.cuda_stream)
         p4, m4 = pack(pos, mom, ids)
         self._ctx = C.c_void_p()
-        if host_init:
-            code = lib.pm_init(C.byref(cfg), p4.ctypes.data, m4.ctypes.data, 1,
-                               _stream(), C.byref(self._ctx))
-        else:
-            dp = torch.from_numpy(p4).cuda()
-            dm = torch.from_numpy(m4).cuda()
-            code = lib.pm_init(C.byref(cfg), _ptr(dp), _ptr(dm), 0, _stream(),
-                               C.byref(self._ctx))
+        with _On(self.stream):
+            if host_init:
+                code = lib.pm_init(C.byref(cfg), p4.ctypes.data, m4.ctypes.data, 1,
+                                   self._sp, C.byref(self._ctx))
+            else:
+                dp = torch.from_numpy(p4).cuda()
+                dm = torch.from_numpy(m4).cuda()
+                code = lib.pm_init(C.byref(cfg), _ptr(dp), _ptr(dm), 0, self._sp,
+                                   C.byref(self._ctx))
         L.check(code, None)
         self._lib = lib
 
@@ -132,8 +151,9 @@ class Sim:
     def particles_device(self, pos4, mom4):
         """Copy active particles into device float4 tensors (N_cap, 4)."""
         n = C.c_int64()
-        self._check(self._lib.pm_get_particles(self._ctx, _ptr(pos4), _ptr(mom4), 0,
-                                               C.byref(n)))
+        with _On(self.stream):
+            self._check(self._lib.pm_get_particles(self._ctx, _ptr(pos4), _ptr(mom4), 0,
+                                                   C.byref(n)))
         return n.value
 
     def set_particles(self, pos4, mom4, n, host=False):
@@ -141,8 +161,9 @@ class Sim:
             self._check(self._lib.pm_set_particles(self._ctx, C.c_void_p(pos4.ctypes.data),
                                                    C.c_void_p(mom4.ctypes.data), int(n), 1))
         else:
-            self._check(self._lib.pm_set_particles(self._ctx, _ptr(pos4), _ptr(mom4),
-                                                   int(n), 0))
+            with _On(self.stream):
+                self._check(self._lib.pm_set_particles(self._ctx, _ptr(pos4), _ptr(mom4),
+                                                       int(n), 0))
 
     def get_particles_host(self, pos4, mom4):
         """Copy active particles into caller-owned host float4 buffers."""
@@ -189,9 +210,24 @@ class Sim:
         phi = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
         phi64 = torch.empty((n, n, n), dtype=torch.float64, device="cuda") if want64 else None
         vc, res = C.c_int32(), C.c_double()
-        self._check(self._lib.pm_potential(self._ctx, _ptr(d), float(a), _BC[bc], _ptr(phi),
-                                           _ptr(phi64), C.byref(vc), C.byref(res)))
+        with _On(self.stream):
+            self._check(self._lib.pm_potential(self._ctx, _ptr(d), float(a), _BC[bc],
+                                               _ptr(phi), _ptr(phi64), C.byref(vc),
+                                               C.byref(res)))
         return phi, phi64, vc.value, res.value
+
+    def profile(self, enable=True):
+        self._check(self._lib.pm_profile(self._ctx, 1 if enable else 0))
+
+    def profile_read(self):
+        """{class: {"ms", "groups", "bytes"}} of the per-kernel-class timers."""
+        out = {}
+        for c, name in enumerate(L.PROF_CLASSES):
+            t, g, b = C.c_double(), C.c_int64(), C.c_double()
+            self._check(self._lib.pm_profile_read(self._ctx, c, C.byref(t), C.byref(g),
+                                                  C.byref(b)))
+            out[name] = {"ms": t.value, "groups": g.value, "bytes": b.value}
+        return out
 
 
 def power_spectrum(pos4_dev, box, n_mesh, n_bins, subtract_shot=True):

@@ -47,7 +47,7 @@ def test_deposit_bitexact_periodic(n, N, seed):
     ref, _ = opm.deposit(pos, n, 0, n, True)
     assert esc == 0
     np.testing.assert_array_equal(rho.cpu().numpy(), ref)
-    assert int(rho.sum().item()) == N * 2**48
+    assert int(ref.astype(object).sum()) == N * 2**48   # exact, no int64 overflow
 
 
 def test_deposit_bitexact_zeldovich_lattice():
@@ -127,7 +127,7 @@ def test_open_solve_matches_oracle(n):
     ref = opm.solve_open(f, opm.open_ghost_potential(f, S, 0, n))[1:-1, 1:-1, 1:-1]
     got = phi64.cpu().numpy()
     err = np.sqrt(np.mean((got - ref) ** 2) / np.mean(ref**2))
-    assert res <= 1e-10 and vc < 40
+    assert res <= 1e-10 and vc <= 16
     assert err < 1e-8, err
     np.testing.assert_allclose(phi32.cpu().numpy(), got.astype(np.float32), rtol=0, atol=0)
     sim.close()
@@ -143,7 +143,7 @@ def test_periodic_solve_matches_oracle(n):
     ref = opm.solve_periodic(opm.source_S(0.7, OM) * delta)
     got = phi64.cpu().numpy()
     err = np.sqrt(np.mean((got - ref) ** 2) / np.mean(ref**2))
-    assert res <= 1e-10
+    assert res <= 1e-10 and vc <= 16
     assert err < 1e-8, err
     sim.close()
 
@@ -195,8 +195,8 @@ def _one_step(n, box, a0, a1, steps, seed, alpha=-2.0, cutoff=None, take=0):
     p_gpu, m_gpu, id_gpu = sim.particles()
     sim.close()
     p_o, m_o, info = opm.step(pos.astype(np.float64), mom.astype(np.float64), 0, sched, n,
-                              OM, 1.0, want=True)
-    return F, info, st, (p_gpu, m_gpu, id_gpu), (p_o, m_o), sched
+                              OM, 1.0, want=True, drift32=True)
+    return F, info, st, (p_gpu, m_gpu, id_gpu), (p_o, m_o), sched, mom
 
 
 def _rel_rms(a, b):
@@ -204,19 +204,21 @@ def _rel_rms(a, b):
 
 
 def test_step_forces_periodic_phase():
-    F, info, st, (p, m, ids), (po, mo), _ = _one_step(32, 250.0, 0.02, 1.0, 20, 0)
+    F, info, st, (p, m, ids), (po, mo), _, m0 = _one_step(32, 250.0, 0.02, 1.0, 20, 0)
     assert st["periodic"] == 1 and st["cube_side"] == 32
     assert _rel_rms(F, info["F"]) <= 1e-5
-    # kick/drift in float32 against FP64 on the same inputs
+    # kick: the momentum change carries the force error (<= 1e-5) plus float32
+    # rounding of p; the drift adds float32 rounding of x (|x| < 32)
+    dp, dpo = m - m0, mo - m0
+    assert _rel_rms(dp, dpo) <= 2e-5
     d = np.abs(((p - po) + 16) % 32 - 16).max()
-    assert d < 1e-4
-    np.testing.assert_allclose(m, mo, rtol=0, atol=1e-6 * np.abs(mo).max())
+    assert d < 2e-5
     np.testing.assert_array_equal(ids, np.arange(32**3))
 
 
 def test_step_forces_open_phase():
     # box so large that the lightcone is inside the mesh from the start
-    F, info, st, (p, m, ids), (po, mo), sched = _one_step(32, 8000.0, 0.5, 1.0, 10, 1)
+    F, info, st, (p, m, ids), (po, mo), sched, _ = _one_step(32, 8000.0, 0.5, 1.0, 10, 1)
     assert st["periodic"] == 0 and info["periodic"] is False
     assert (st["cube_lo"], st["cube_side"]) == (info["lo"], info["s"])
     ok = info["F"].any(axis=1)
@@ -236,8 +238,10 @@ def test_step_forces_full_size_sampled():
     sim.close()
     k = 0
     lo, s, per = opm.active_cube(sched["R"][k], n)
-    x = opm.drift(pos.astype(np.float64), mom.astype(np.float64),
-                  sched["dtau"][k] / (2 * sched["a"][k]), n, per)
+    # the same float32 half drift as the kernel, so both deposit identical
+    # particles; from there on the oracle is FP64
+    x = opm.drift_fp32(pos, mom, sched["dtau"][k] / (2 * sched["a"][k]), n,
+                       per).astype(np.float64)
     rho, _ = opm.deposit(x, n, lo, s, per)
     f, phi = opm.solve_step_potential(rho, n, lo, s, per, 1.0, sched["R"][k],
                                       sched["a_half"][k], OM)
@@ -280,9 +284,17 @@ def test_all_particles_leave_and_empty_steps_run():
     sim = Sim(pos, mom, ids, n, 60000.0, 0.9, 1.0, 4)
     sim.step(4)
     st = sim.stats()
-    assert st["n_active"] + st["n_lightcone"] == n**3
-    assert st["n_active"] == 0
+    gp, _, gi = sim.particles()
     sim.close()
+    assert st["n_active"] + st["n_lightcone"] == n**3
+    # at a = 1 only the particles within the 1-cell buffer of the observer stay
+    sched = cz.schedule(n, 60000.0, OM, OL, 0.9, 1.0, 4)
+    assert sched["R"][-1] == 1.0
+    assert st["n_active"] <= 27
+    assert np.all(np.abs(gp.astype(np.float64) - n / 2).max(axis=1) <= 1.0)
+    out = opm.run(pos, mom, ids, sched, n, OM, 1.0)
+    assert set(gi) <= set(out["ids"]) | set(out["lc_ids"])
+    assert abs(len(out["ids"]) - st["n_active"]) <= 2
 
 
 # --------------------------------------------------------------- power spectrum

@@ -351,3 +351,23 @@ def test_shrinking_run_bookkeeping():
     assert sorted(np.concatenate([out["ids"], out["lc_ids"]])) == list(range(n**3))
     R = sched["R"][-1]
     assert np.all(np.abs(out["pos"] - n / 2).max(axis=1) <= R)
+
+
+def test_drift_fp32_exact_cases_and_wrap():
+    """drift_fp32 follows float32 arithmetic: exact where float32 is exact,
+    and the periodic wrap lands in [0, n)."""
+    n = 16
+    pos = np.array([[1.0, 15.75, 0.25], [8.0, 8.0, 8.0]], np.float32)
+    mom = np.array([[0.5, 0.5, -1.0], [2.0 ** -10, -3.0, 0.0]], np.float32)
+    x = pm.drift_fp32(pos, mom, 0.5, n, True)
+    np.testing.assert_array_equal(x, np.array([[1.25, 0.0, 15.75],
+                                               [8.0 + 2.0 ** -11, 6.5, 8.0]], np.float32))
+    assert x.dtype == np.float32
+    # a tiny negative step rounds to n in float32 and must wrap to 0
+    y = pm.drift_fp32(np.array([[0.0, 1.0, 1.0]], np.float32),
+                       np.array([[-1e-9, 0, 0]], np.float32), 1.0, n, True)
+    assert 0.0 <= y[0, 0] < n
+    # one rounding per operation: 1 + 2^-24 rounds to 1 in float32
+    z = pm.drift_fp32(np.array([[1.0, 1.0, 1.0]], np.float32),
+                       np.array([[2.0 ** -24, 0, 0]], np.float32), 1.0, n, False)
+    assert z[0, 0] == np.float32(1.0)
