@@ -223,6 +223,39 @@ pm_status pm_profile(pm_ctx* ctx, int32_t enable);
 pm_status pm_profile_read(pm_ctx* ctx, int32_t cls, double* ms, int64_t* groups,
                           double* bytes);
 
+/* Allocation-free lightcone compaction.  The paper has no counterpart: this
+ * is a variant of pm_shrink's compaction for callers that cannot allocate
+ * device memory — host programs that hand the library a fixed memory budget
+ * and forbid further allocation, and loops that cannot afford the implicit
+ * device synchronisation of cudaMalloc/cudaFree.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *
+ * Takes n float4 particle records on the device (pos4_in, mom4_in, layout as
+ * above) and writes, in their input order, the survivors of the keep cube of
+ * expansion factor a (the rule of pm_shrink with PM_BC_PAPER: keep iff
+ * max_d |x_d - n_mesh/2| <= chi(a)/(box_mpch/n_mesh) + buffer_cells, and
+ * everything is kept while that half-width exceeds n_mesh/2 - 1) to
+ * pos4_keep/mom4_keep and the leavers to pos4_leave/mom4_leave with
+ * mom.w = a.  Output buffers are caller-owned, n records each, and must not
+ * overlap the inputs.  *n_keep_out receives the survivor count; the stream
+ * (cudaStream_t, NULL = legacy default stream) is synchronised.
+ *
+ * Scratch: a static device array for at most PM_SHRINK_STATIC_MAX_PARTICLES
+ * particles (~4.1 MB, held on every GPU that loads the library until exit);
+ * larger n is rejected with PM_EINVAL.  The first call on a device looks up
+ * that array's device address (set-up), so make the first call before any
+ * stream capture.  All calls on a device share the one array: calls that
+ * overlap on the GPU (different streams or threads) race and must be
+ * serialised by the caller.  pm_shrink_static_error() describes the last
+ * failure. */
+#define PM_SHRINK_STATIC_MAX_PARTICLES (1 << 22)
+pm_status pm_shrink_static(const float* pos4_in, const float* mom4_in, int64_t n,
+                           int32_t n_mesh, double box_mpch, double omega_m, double omega_l,
+                           double buffer_cells, double a, float* pos4_keep, float* mom4_keep,
+                           float* pos4_leave, float* mom4_leave, int64_t* n_keep_out,
+                           void* stream);
+const char* pm_shrink_static_error(void);
+
 /* Kernel launches made by this library in this process so far. */
 int64_t pm_launch_count(void);
 

@@ -14,6 +14,7 @@ PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_ENOCONV, PM_EOVERFLOW, PM_ETIMEOUT = r
 PM_MIXED, PM_FP32_PLAIN = 0, 1
 PM_GUESS_WARM, PM_GUESS_ZERO = 0, 1
 PM_BC_PAPER, PM_BC_OPEN, PM_BC_PERIODIC = 0, 1, 2
+PM_SHRINK_STATIC_MAX_PARTICLES = 1 << 22
 
 STATUS_NAMES = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ECUDA",
                 4: "PM_ENOCONV", 5: "PM_EOVERFLOW", 6: "PM_ETIMEOUT"}
@@ -24,7 +25,7 @@ EXPORTED = [
     "pm_power_spectrum", "pm_deposit", "pm_stats", "pm_schedule",
     "pm_get_particles", "pm_set_particles", "pm_get_lightcone", "pm_get_forces",
     "pm_get_potential", "pm_profile", "pm_profile_read", "pm_launch_count", "pm_last_error",
-    "pm_destroy",
+    "pm_destroy", "pm_shrink_static", "pm_shrink_static_error",
 ]
 PROF_CLASSES = ["deposit", "source", "boundary", "smooth0", "transfer0", "coarse",
                 "defect", "correct", "gather", "compact"]
@@ -89,6 +90,9 @@ def load():
         "pm_profile": (I32, [P, I32]),
         "pm_profile_read": (I32, [P, I32, C.POINTER(D), C.POINTER(I64), C.POINTER(D)]),
         "pm_launch_count": (I64, []),
+        "pm_shrink_static": (I32, [P, P, I64, I32, D, D, D, D, D, P, P, P, P,
+                                   C.POINTER(I64), P]),
+        "pm_shrink_static_error": (C.c_char_p, []),
         "pm_last_error": (C.c_char_p, [P]),
         "pm_destroy": (None, [P]),
     }

@@ -549,6 +549,22 @@ pm_status alloc(pm_ctx* ctx, void** p, size_t bytes) {
 
 }  // namespace
 
+// Keep rule of pm_shrink for callers outside a context (see noalloc.cu).
+double pm::shrink_radius_cells(int n, double box, double om, double ol, double buffer,
+                               double a) {
+  double chi = C_OVER_H0 * (tau_of_a(1.0, om, ol) - tau_of_a(a, om, ol));
+  return chi / (box / n) + buffer;
+}
+
+void pm::shrink_keep_bounds(int n, double R, float* klo, float* khi) {
+  if (R <= 0.5 * n - 1.0) {
+    keep_bounds(0.5 * n, R, klo, khi);
+  } else {  // periodic phase under PM_BC_PAPER: nothing leaves
+    *klo = -3.402823466e38f;
+    *khi = 3.402823466e38f;
+  }
+}
+
 extern "C" {
 
 void pm_config_default(pm_config* c) {

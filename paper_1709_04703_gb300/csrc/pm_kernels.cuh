@@ -8,6 +8,11 @@ namespace pm {
 // Counts kernel launches made by the library (pm_launch_count).
 void note_launch();
 
+// pm_shrink's keep rule: R = chi(a)/cell + buffer (cells), and the exact
+// float bounds of |x - n/2| <= R (everything kept while R > n/2 - 1).
+double shrink_radius_cells(int n, double box, double om, double ol, double buffer, double a);
+void shrink_keep_bounds(int n, double R, float* klo, float* khi);
+
 // k_mesh.cu
 void launch_drift_deposit(cudaStream_t st, int grid, float4* pos, const float4* mom,
                           long long N, float c0, bool drift, int n, int lo, int s,
