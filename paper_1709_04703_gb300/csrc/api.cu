@@ -26,7 +26,7 @@ namespace {
 
 constexpr double C_OVER_H0 = 2997.92458;  // Mpc/h
 constexpr int SRC_GRID = 1216;            // 152 SMs x 8 blocks
-constexpr int COARSE_SWEEPS = 40;
+constexpr int COARSE_SWEEPS = 24;
 
 // ---------------------------------------------------------------------------
 // FP64 cosmology on the host.  tau(a) = int_0^a da'/(a'^2 E), H0 = 1, with
@@ -128,7 +128,15 @@ struct pm_ctx {
   unsigned long long* keep_off = nullptr;
 
   unsigned long long* rho = nullptr;
-  float *phi_hi = nullptr, *phi_lo = nullptr, *f_hi = nullptr, *f_lo = nullptr;
+  // potential as a double-float pair, two buffers: the defect evaluation
+  // that applies a V-cycle's correction writes Phi + e out of place
+  float* phi_h[2] = {nullptr, nullptr};
+  float* phi_l[2] = {nullptr, nullptr};
+  int cur = 0;
+  float *f_hi = nullptr, *f_lo = nullptr;
+  float *prev_hi = nullptr, *prev_lo = nullptr;  // previous step's solution
+  int n_sol = 0;            // consecutive warm-startable solutions
+  double ah_hist[2] = {0, 0};  // a_half of the last two solves
   std::vector<float*> lu, lb;   // level arrays (compact padded); level 0 for e / r
   std::vector<int> ls;          // level sides of the current cube
 
@@ -152,7 +160,7 @@ struct pm_ctx {
   int ev_graph_next = 0;
   struct VGraph {
     bool valid = false;
-    int lo = 0, s = 0, per = 0, prof = 0;
+    int lo = 0, s = 0, per = 0, prof = 0, zero0 = 0;
     float *u0 = nullptr, *b0 = nullptr;
     cudaGraphExec_t exec = nullptr;
     long long kernels = 0;
@@ -351,10 +359,21 @@ pm_status sync_read(pm_ctx* ctx) {
 }
 
 // V(2,2) cycle on level 0 grids (u0, b0) of the current cube.
-pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0) {
+// Two RB-GS sweeps (red, black, red, black) on a level; zero_start when the
+// iterate is known to be zero on entry.
+void smooth2(pm_ctx* ctx, Grid u, Grid b, float h2, int per, float g, bool zero_start) {
+  for (int sw = 0; sw < 2; ++sw) {
+    launch_rbgs(ctx->st, u, b, h2, 0, per, g, zero_start && sw == 0);
+    launch_rbgs(ctx->st, u, b, h2, 1, per, g);
+  }
+}
+
+// V(2,2) cycle on level-0 grids (u0, b0).
+pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
   const int per = ctx->periodic;
   const int L = (int)ctx->ls.size() - 1;
-  std::vector<Grid> U(L + 1), B(L + 1);
+  Grid U[16], B[16];
+  if (L >= 16) return fail(ctx, PM_EINVAL, "too many multigrid levels");
   U[0] = u0;
   B[0] = b0;
   for (int l = 1; l <= L; ++l) {
@@ -362,22 +381,24 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0) {
     B[l] = compact_view(ctx->lb[l], ctx->ls[l]);
   }
   const double c0 = (double)ctx->s * ctx->s * ctx->s;
-  // algorithmic bytes: a colour sweep reads u (4 B/cell) and half of b, writes
-  // half of u (8 B/cell per colour); residual+restriction reads u and b
+  // algorithmic bytes: a colour launch reads u (4 B/cell) and half of b and
+  // writes half of u (8 B/cell); residual+restriction reads u and b
   // (8 B/fine cell) and writes the coarse b and u (1 B/fine cell);
   // prolongation reads the coarse u (0.5) and updates the fine u (8).
+  const double smooth_bytes = 4 * 8.0 * c0;
   float h2 = 1.0f;
   int ec = -1;
   // open-boundary ghost factor of level l (spacing H = 2^l), see k_mg.cu
   auto gam = [](int l) { float H = (float)(1 << l); return (H - 1.0f) / (H + 1.0f); };
-  for (int l = 0; l < L; ++l) {
+  // levels below the first of side <= CMG_MAX_SIDE run inside one CTA
+  int Lc = 0;
+  while (Lc < L && ctx->ls[Lc] > CMG_MAX_SIDE) ++Lc;
+  for (int l = 0; l < Lc; ++l) {
     int e = l == 0 ? prof_begin(ctx) : -1;
-    for (int sw = 0; sw < 2; ++sw) {
-      launch_rbgs(ctx->st, U[l], B[l], h2, 0, per, gam(l));
-      launch_rbgs(ctx->st, U[l], B[l], h2, 1, per, gam(l));
-    }
+    // below level 0 the restriction zeroes the coarse iterate
+    smooth2(ctx, U[l], B[l], h2, per, gam(l), l == 0 ? zero0 : true);
     if (l == 0) {
-      prof_end(ctx, PM_PROF_SMOOTH0, e, 4 * 8.0 * c0);
+      prof_end(ctx, PM_PROF_SMOOTH0, e, smooth_bytes);
       e = prof_begin(ctx);
     }
     launch_resid_restrict(ctx->st, U[l], B[l], 1.0f / h2, U[l + 1], B[l + 1], per, gam(l));
@@ -387,13 +408,13 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0) {
     }
     h2 *= 4.0f;
   }
-  if (L == 0) ec = prof_begin(ctx);
-  launch_coarse(ctx->st, U[L], B[L], h2, per, COARSE_SWEEPS, gam(L));
-  for (int l = L - 1; l >= 0; --l) {
+  if (Lc == 0) ec = prof_begin(ctx);
+  launch_coarse_mg(ctx->st, U[Lc], B[Lc], Lc, per, COARSE_SWEEPS, Lc == 0 ? zero0 : true);
+  for (int l = Lc - 1; l >= 0; --l) {
     h2 *= 0.25f;
     int e = -1;
     if (l == 0) {
-      prof_end(ctx, PM_PROF_COARSE, ec, (L > 0 ? 8.0 / 7.0 * 81.0 * c0 / 8.0 : 0.0));
+      prof_end(ctx, PM_PROF_COARSE, ec, (Lc > 0 ? 8.0 / 7.0 * 81.0 * c0 / 8.0 : 0.0));
       e = prof_begin(ctx);
     }
     launch_prolong(ctx->st, U[l + 1], U[l], per, gam(l + 1));
@@ -401,13 +422,10 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0) {
       prof_end(ctx, PM_PROF_TRANSFER0, e, 8.5 * c0);
       e = prof_begin(ctx);
     }
-    for (int sw = 0; sw < 2; ++sw) {
-      launch_rbgs(ctx->st, U[l], B[l], h2, 0, per, gam(l));
-      launch_rbgs(ctx->st, U[l], B[l], h2, 1, per, gam(l));
-    }
-    if (l == 0) prof_end(ctx, PM_PROF_SMOOTH0, e, 4 * 8.0 * c0);
+    smooth2(ctx, U[l], B[l], h2, per, gam(l), false);
+    if (l == 0) prof_end(ctx, PM_PROF_SMOOTH0, e, smooth_bytes);
   }
-  if (L == 0) prof_end(ctx, PM_PROF_COARSE, ec, 0.0);
+  if (Lc == 0) prof_end(ctx, PM_PROF_COARSE, ec, 0.0);
   CKL();
   return PM_OK;
 }
@@ -419,18 +437,19 @@ void drop_graph(pm_ctx* ctx) {
 
 // One V-cycle: replay of a graph captured for the current cube / grids, or
 // eager launches when the context's stream cannot be captured.
-pm_status vcycle_run(pm_ctx* ctx, Grid u0, Grid b0) {
-  if (!ctx->use_graphs) return vcycle(ctx, u0, b0);
+pm_status vcycle_run(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
+  if (!ctx->use_graphs) return vcycle(ctx, u0, b0, zero0);
   auto& g = ctx->vg;
   if (!(g.valid && g.lo == ctx->lo && g.s == ctx->s && g.per == ctx->periodic &&
-        g.u0 == u0.base && g.b0 == b0.base && g.prof == (int)ctx->prof_on)) {
+        g.u0 == u0.base && g.b0 == b0.base && g.prof == (int)ctx->prof_on &&
+        g.zero0 == (int)zero0)) {
     drop_graph(ctx);
     CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
     ctx->capturing = true;
     ctx->ev_graph_next = EV_POOL;
     ctx->pend_graph.clear();
     long long l0 = g_launches.load();
-    pm_status st = vcycle(ctx, u0, b0);
+    pm_status st = vcycle(ctx, u0, b0, zero0);
     ctx->capturing = false;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(ctx->st, &graph);
@@ -453,6 +472,7 @@ pm_status vcycle_run(pm_ctx* ctx, Grid u0, Grid b0) {
     g.u0 = u0.base;
     g.b0 = b0.base;
     g.prof = ctx->prof_on;
+    g.zero0 = zero0;
     g.kernels = nk;
   }
   CK(cudaGraphLaunch(g.exec, ctx->st));
@@ -465,22 +485,33 @@ pm_status vcycle_run(pm_ctx* ctx, Grid u0, Grid b0) {
 // Iterate to rtol.  f2 = ||f||^2 already in d_scal[0] (read at first sync).
 pm_status solve(pm_ctx* ctx) {
   const int lo = ctx->lo, s = ctx->s, per = ctx->periodic;
-  Grid ph = full_view(ctx, ctx->phi_hi, lo, s), pl = full_view(ctx, ctx->phi_lo, lo, s);
   Grid fh = full_view(ctx, ctx->f_hi, lo, s), fl = full_view(ctx, ctx->f_lo, lo, s);
   Grid e0 = compact_view(ctx->lu[0], s), r0 = compact_view(ctx->lb[0], s);
   const bool mixed = ctx->cfg.precision == PM_MIXED;
+  auto ph_of = [&](int q) { return full_view(ctx, ctx->phi_h[q], lo, s); };
+  auto pl_of = [&](int q) { return full_view(ctx, ctx->phi_l[q], lo, s); };
   if (ctx->cfg.guess == PM_GUESS_ZERO) {
-    launch_fill(ctx->st, ph, 0.0f, false);
-    launch_fill(ctx->st, pl, 0.0f, false);
+    launch_fill(ctx->st, ph_of(ctx->cur), 0.0f, false);
+    launch_fill(ctx->st, pl_of(ctx->cur), 0.0f, false);
   }
   int it = 0;
   double rel = 0.0;
   const double cells = (double)s * s * s;
   for (;; ++it) {
     int e = prof_begin(ctx);
-    launch_defect(ctx->st, ph, pl, fh, fl, r0, e0, per, mixed, ctx->partial, ctx->counter,
-                  ctx->d_scal + 11);
-    prof_end(ctx, PM_PROF_DEFECT, e, (mixed ? 24.0 : 16.0) * cells);
+    const int c0 = ctx->cur;
+    if (mixed && it > 0) {
+      // Phi <- Phi + e of the last V-cycle, written to the other buffer;
+      // reads Phi (8 B), e (4), f (8), writes Phi (8) and r (4) per cell
+      launch_defect(ctx->st, ph_of(c0), pl_of(c0), &e0, ph_of(c0 ^ 1), pl_of(c0 ^ 1), fh, fl,
+                    r0, per, true, ctx->partial, ctx->counter, ctx->d_scal + 11);
+      ctx->cur ^= 1;
+      prof_end(ctx, PM_PROF_DEFECT, e, 32.0 * cells);
+    } else {
+      launch_defect(ctx->st, ph_of(c0), pl_of(c0), nullptr, ph_of(c0), pl_of(c0), fh, fl, r0,
+                    per, mixed, ctx->partial, ctx->counter, ctx->d_scal + 11);
+      prof_end(ctx, PM_PROF_DEFECT, e, (mixed ? 20.0 : 16.0) * cells);
+    }
     CKL();
     pm_status st = sync_read(ctx);
     if (st != PM_OK) return st;
@@ -496,16 +527,10 @@ pm_status solve(pm_ctx* ctx) {
                rel, it, ctx->cfg.rtol);
       return fail(ctx, PM_ENOCONV, buf);
     }
-    if (mixed) {
-      pm_status v = vcycle_run(ctx, e0, r0);
-      if (v != PM_OK) return v;
-      int ee = prof_begin(ctx);
-      launch_correct(ctx->st, ph, pl, e0);
-      prof_end(ctx, PM_PROF_CORRECT, ee, 20.0 * cells);
-    } else {
-      pm_status v = vcycle_run(ctx, ph, fh);
-      if (v != PM_OK) return v;
-    }
+    // the correction e starts at zero in every V-cycle (zero-start sweep)
+    pm_status v = mixed ? vcycle_run(ctx, e0, r0, true)
+                        : vcycle_run(ctx, ph_of(ctx->cur), fh, false);
+    if (v != PM_OK) return v;
   }
   ctx->vcycles_last = it;
   ctx->vcycles_total += it;
@@ -657,10 +682,14 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
   AL(ctx->block_keep, sizeof(unsigned int) * nblk);
   AL(ctx->keep_off, sizeof(unsigned long long) * nblk);
   AL(ctx->rho, sizeof(unsigned long long) * (size_t)n * n * n);
-  AL(ctx->phi_hi, sizeof(float) * padded);
-  AL(ctx->phi_lo, sizeof(float) * padded);
+  for (int q = 0; q < 2; ++q) {
+    AL(ctx->phi_h[q], sizeof(float) * padded);
+    AL(ctx->phi_l[q], sizeof(float) * padded);
+  }
   AL(ctx->f_hi, sizeof(float) * padded);
   AL(ctx->f_lo, sizeof(float) * padded);
+  AL(ctx->prev_hi, sizeof(float) * padded);
+  AL(ctx->prev_lo, sizeof(float) * padded);
   for (int sl = n;; sl /= 2) {
     float *u = nullptr, *b = nullptr;
     size_t bytes = sizeof(float) * (size_t)(sl + 2) * (sl + 2) * (sl + 2);
@@ -690,8 +719,10 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
   if (cudaMemsetAsync((ptr), 0, (bytes), s0) != cudaSuccess) {               \
     g_err = "pm_init: cudaMemsetAsync failed"; pm_destroy(ctx); return PM_ECUDA; }
   Z(ctx->rho, sizeof(unsigned long long) * (size_t)n * n * n);
-  Z(ctx->phi_hi, sizeof(float) * padded);
-  Z(ctx->phi_lo, sizeof(float) * padded);
+  Z(ctx->phi_h[0], sizeof(float) * padded);
+  Z(ctx->phi_l[0], sizeof(float) * padded);
+  Z(ctx->phi_h[1], sizeof(float) * padded);
+  Z(ctx->phi_l[1], sizeof(float) * padded);
   Z(ctx->f_hi, sizeof(float) * padded);
   Z(ctx->f_lo, sizeof(float) * padded);
   Z(ctx->counter, sizeof(unsigned int) * 4);
@@ -723,6 +754,7 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
     const double R0 = ctx->R[k], R1 = ctx->R[k + 1];
     int lo, s, per;
     geometry(ctx, R0, &lo, &s, &per);
+    const bool set_phase_changed = !ctx->cube_valid || per != ctx->periodic;
     pm_status st = set_cube(ctx, lo, s, per, R0);
     if (st != PM_OK) return st;
     const long long N = ctx->n_active;
@@ -752,19 +784,43 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
     prof_end(ctx, PM_PROF_SOURCE, e, 24.0 * cells);
     if (!per) {
       e = prof_begin(ctx);
-      launch_boundary(ctx->st, full_view(ctx, ctx->phi_hi, lo, s),
-                      full_view(ctx, ctx->phi_lo, lo, s), n, lo, ctx->d_scal + 1, S, mixed);
+      for (int q = 0; q < (mixed ? 2 : 1); ++q)  // both buffers carry the ghosts
+        launch_boundary(ctx->st, full_view(ctx, ctx->phi_h[q ^ ctx->cur], lo, s),
+                        full_view(ctx, ctx->phi_l[q ^ ctx->cur], lo, s), n, lo,
+                        ctx->d_scal + 1, S, mixed);
       prof_end(ctx, PM_PROF_BOUNDARY, e, 8.0 * 6.0 * (s + 2.0) * (s + 2.0));
     }
     CKL();
+    // warm start extrapolated linearly in a_half from the last two solutions
+    // of the same boundary phase
+    if (ctx->cfg.guess == PM_GUESS_WARM) {
+      if (set_phase_changed) ctx->n_sol = 0;
+      if (ctx->n_sol >= 1) {
+        float w = 0.0f;
+        if (ctx->n_sol >= 2) {
+          double d0 = ctx->ah_hist[1] - ctx->ah_hist[0];
+          w = d0 > 0 ? (float)((ctx->a_half[k] - ctx->ah_hist[1]) / d0) : 0.0f;
+        }
+        e = prof_begin(ctx);
+        launch_predict(ctx->st, full_view(ctx, ctx->phi_h[ctx->cur], lo, s),
+                       full_view(ctx, ctx->phi_l[ctx->cur], lo, s),
+                       full_view(ctx, ctx->prev_hi, lo, s),
+                       full_view(ctx, ctx->prev_lo, lo, s), w, mixed);
+        prof_end(ctx, PM_PROF_CORRECT, e, 32.0 * cells);
+      }
+    }
     st = solve(ctx);
     if (st != PM_OK) return st;
+    ctx->ah_hist[0] = ctx->ah_hist[1];
+    ctx->ah_hist[1] = ctx->a_half[k];
+    ctx->n_sol++;
     // 4-6. gradient + gather + kick + half drift (+ keep flags)
     const bool do_flag = ctx->cfg.shrink && ctx->cfg.bc != PM_BC_PERIODIC && is_open(ctx, R1);
     float klo = 0.f, khi = 0.f;
     if (do_flag) keep_bounds(0.5 * n, R1, &klo, &khi);
     e = prof_begin(ctx);
-    launch_gather_kick_drift(ctx->st, ctx->pos, ctx->mom, N, ctx->phi_hi, ctx->phi_lo, n, lo, s,
+    launch_gather_kick_drift(ctx->st, ctx->pos, ctx->mom, N, ctx->phi_h[ctx->cur],
+                             ctx->phi_l[ctx->cur], n, lo, s,
                              per, (float)(ctx->a_half[k] * ctx->dtau[k]),
                              (float)(ctx->dtau[k] / (2.0 * ctx->a[k + 1])), do_flag, klo, khi,
                              ctx->flags, ctx->block_keep, ctx->forces, ctx->d_cnt + 1);
@@ -815,16 +871,19 @@ pm_status pm_potential(pm_ctx* ctx, const double* delta_dev, double a, int32_t b
   pm_status st = set_cube(ctx, 0, n, per, 1e300);
   if (st != PM_OK) return st;
   ctx->cube_valid = false;  // the next step re-derives its cube
+  ctx->n_sol = 0;           // and does not extrapolate across this solve
   const double S = 1.5 * ctx->cfg.omega_m / a;
   Grid fh = full_view(ctx, ctx->f_hi, 0, n), fl = full_view(ctx, ctx->f_lo, 0, n);
-  Grid ph = full_view(ctx, ctx->phi_hi, 0, n), pl = full_view(ctx, ctx->phi_lo, 0, n);
+  const bool mixed = ctx->cfg.precision == PM_MIXED;
   launch_source_f64(ctx->st, SRC_GRID, delta_dev, n, fh, fl, S, !per, ctx->partial,
                     ctx->counter, ctx->d_scal);
   // launch_source_f64 writes (||f||^2, q0, d, S_ab) to d_scal[0..10]
-  if (!per) launch_boundary(ctx->st, ph, pl, n, 0, ctx->d_scal + 1, S,
-                            ctx->cfg.precision == PM_MIXED);
-  launch_fill(ctx->st, ph, 0.0f, false);
-  launch_fill(ctx->st, pl, 0.0f, false);
+  for (int q = 0; q < 2; ++q) {
+    Grid gh = full_view(ctx, ctx->phi_h[q], 0, n), gl = full_view(ctx, ctx->phi_l[q], 0, n);
+    if (!per) launch_boundary(ctx->st, gh, gl, n, 0, ctx->d_scal + 1, S, mixed);
+    launch_fill(ctx->st, gh, 0.0f, false);
+    launch_fill(ctx->st, gl, 0.0f, false);
+  }
   CKL();
   int guess = ctx->cfg.guess;
   ctx->cfg.guess = PM_GUESS_WARM;  // already zeroed
@@ -834,6 +893,7 @@ pm_status pm_potential(pm_ctx* ctx, const double* delta_dev, double a, int32_t b
   if (resid_out) *resid_out = ctx->resid_last;
   if (st != PM_OK) return st;
   double shift = 0.0;
+  Grid ph = full_view(ctx, ctx->phi_h[ctx->cur], 0, n), pl = full_view(ctx, ctx->phi_l[ctx->cur], 0, n);
   if (per) {
     launch_sum_phi(ctx->st, ph, pl, ctx->partial, ctx->counter, ctx->d_scal + 12);
     CKL();
@@ -1025,9 +1085,11 @@ pm_status pm_get_potential(pm_ctx* ctx, double* phi_host, int32_t* lo_out, int32
   const int P = ctx->P, lo = ctx->lo, s = ctx->s;
   const size_t padded = (size_t)P * P * P;
   std::vector<float> hi(padded), lo_(padded);
-  CK(cudaMemcpyAsync(hi.data(), ctx->phi_hi, sizeof(float) * padded, cudaMemcpyDeviceToHost,
+  CK(cudaMemcpyAsync(hi.data(), ctx->phi_h[ctx->cur], sizeof(float) * padded,
+                     cudaMemcpyDeviceToHost,
                      ctx->st));
-  CK(cudaMemcpyAsync(lo_.data(), ctx->phi_lo, sizeof(float) * padded, cudaMemcpyDeviceToHost,
+  CK(cudaMemcpyAsync(lo_.data(), ctx->phi_l[ctx->cur], sizeof(float) * padded,
+                     cudaMemcpyDeviceToHost,
                      ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   if (phi_host) {
@@ -1083,7 +1145,9 @@ void pm_destroy(pm_ctx* ctx) {
   if (ctx->st) cudaStreamSynchronize(ctx->st);
   void* ptrs[] = {ctx->pos, ctx->mom, ctx->pos2, ctx->mom2, ctx->lc_pos, ctx->lc_mom,
                   ctx->forces, ctx->flags, ctx->block_keep, ctx->keep_off, ctx->rho,
-                  ctx->phi_hi, ctx->phi_lo, ctx->f_hi, ctx->f_lo, ctx->partial, ctx->partial_m,
+                  ctx->phi_h[0], ctx->phi_l[0], ctx->phi_h[1], ctx->phi_l[1], ctx->f_hi,
+                  ctx->f_lo, ctx->prev_hi, ctx->prev_lo,
+                  ctx->partial, ctx->partial_m,
                   ctx->counter, ctx->d_scal, ctx->bgm, ctx->d_cnt, ctx->d_overflow};
   for (void* p : ptrs)
     if (p) cudaFree(p);

@@ -149,19 +149,32 @@ __global__ void __launch_bounds__(256) k_source(
 #pragma unroll
   for (int q = 0; q < SRC_NV; ++q) acc[q] = 0;
   float f2 = 0.f;
-  // block (32, 8) covers an x-y tile; the grid's z dimension strides over planes
+  // block (32, 8) covers an x-y tile; the grid's z dimension strides over
+  // planes, ZU planes per round with all loads issued before any use
+  constexpr int ZU = 4;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  for (int k = blockIdx.z; k < s && i < s && j < s; k += gridDim.z) {
-    int gi = lo + i, gj = lo + j, gk = lo + k;
-    long long ri = ((long long)gk * n + gj) * n + gi;
-    unsigned long long cnt = rho[ri];
-    rho[ri] = 0ull;
+  const bool in_xy = i < s && j < s;
+  const int gi = lo + i, gj = lo + j;
+  const bool in_xy_bg = gi >= b0 && gi <= b1 && gj >= b0 && gj <= b1;
+  for (int k0 = blockIdx.z; k0 < s && in_xy; k0 += ZU * gridDim.z) {
+    unsigned long long cnts[ZU];
+#pragma unroll
+    for (int u = 0; u < ZU; ++u) {
+      int k = k0 + u * gridDim.z;
+      cnts[u] = k < s ? rho[((long long)(lo + k) * n + gj) * n + gi] : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < ZU; ++u) {
+    int k = k0 + u * gridDim.z;
+    if (k >= s) break;
+    int gk = lo + k;
+    unsigned long long cnt = cnts[u];
+    rho[((long long)gk * n + gj) * n + gi] = 0ull;
     if (cnt > (1ull << 62)) atomicOr(overflow, 1);
     long long c = (long long)cnt;
-    df d = df_mul(df_from_i64(c), invM);
-    bool inside = gi >= b0 && gi <= b1 && gj >= b0 && gj <= b1 && gk >= b0 && gk <= b1;
-    if (inside) d = df_add(d, df{-1.0f, 0.0f});
+    df d = df_mul(df_from_u64(cnt), invM);
+    if (in_xy_bg && gk >= b0 && gk <= b1) d = df_add(d, df{-1.0f, 0.0f});
     df f = df_mul(d, S);
     int fi = gidx(fh, i, j, k);
     fh.base[fi] = f.hi;
@@ -181,6 +194,7 @@ __global__ void __launch_bounds__(256) k_source(
       acc[8] += cc * (long long)(X * Z);
       acc[9] += cc * (long long)(Y * Z);
     }
+    }
   }
   // block reduction: ||f||^2 in double, moments in int128
   __shared__ double sf[32];
@@ -189,8 +203,8 @@ __global__ void __launch_bounds__(256) k_source(
   const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
   const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
   int lane = tid & 31, warp = tid >> 5, nw = (blockDim.x * blockDim.y) >> 5;
-  double w = warp_sum((double)f2);
-  if (lane == 0) sf[warp] = w;
+  float wf = warp_sumf_all(f2);
+  if (lane == 0) sf[warp] = (double)wf;
   if (MOMENTS) {
 #pragma unroll
     for (int q = 0; q < SRC_NV; ++q) {

@@ -24,8 +24,11 @@ __device__ __forceinline__ float bnd_diag(int i, int j, int k, int s, float gam)
   return 6.0f + gam * (float)nb;
 }
 
+// zero_start (red only): the iterate is known to be zero, so the red cells
+// take (-h^2 b)/diag without reading u; the black sweep after it reads only
+// red neighbours, so u needs no clearing before a V-cycle.
 __global__ void __launch_bounds__(256) k_rbgs(Grid u, Grid b, float h2, int color,
-                                              int periodic, float gam) {
+                                              int periodic, float gam, int zero_start) {
   const int s = u.s;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -37,7 +40,7 @@ __global__ void __launch_bounds__(256) k_rbgs(Grid u, Grid b, float h2, int colo
   int ym = (wrap_m(j, s, periodic) - j) * u.sy, yp = (wrap_p(j, s, periodic) - j) * u.sy;
   int zm = (wrap_m(k, s, periodic) - k) * u.sz, zp = (wrap_p(k, s, periodic) - k) * u.sz;
   const float* p = u.base + c;
-  float sum = (p[xm] + p[xp]) + (p[ym] + p[yp]) + (p[zm] + p[zp]);
+  float sum = zero_start ? 0.0f : (p[xm] + p[xp]) + (p[ym] + p[yp]) + (p[zm] + p[zp]);
   float bv = b.base[gidx(b, i, j, k)];
   if (periodic || gam == 0.0f)
     u.base[c] = (sum - h2 * bv) * (1.0f / 6.0f);
@@ -101,9 +104,9 @@ __global__ void __launch_bounds__(256) k_prolong(Grid uc, Grid u, int periodic,
   // axis), see bnd_diag
   float fx = 1.0f, fy = 1.0f, fz = 1.0f;
   if (periodic) {
-    I2 = (I2 + sc) % sc;
-    J2 = (J2 + sc) % sc;
-    K2 = (K2 + sc) % sc;
+    I2 = I2 < 0 ? sc - 1 : (I2 >= sc ? 0 : I2);
+    J2 = J2 < 0 ? sc - 1 : (J2 >= sc ? 0 : J2);
+    K2 = K2 < 0 ? sc - 1 : (K2 >= sc ? 0 : K2);
   } else {
     if (I2 < 0 || I2 >= sc) { I2 = I; fx = -gam_c; }
     if (J2 < 0 || J2 >= sc) { J2 = J; fy = -gam_c; }
@@ -121,107 +124,231 @@ __global__ void __launch_bounds__(256) k_prolong(Grid uc, Grid u, int periodic,
 }
 
 // ---------------------------------------------------------------------------
-// Coarsest level (s <= 8): one CTA, RB-GS sweeps in shared memory.  Periodic:
-// the right-hand side and the result are projected to zero mean.
+// The bottom of the V-cycle in one CTA: from a level with side S <= 16 down to
+// side <= 4 (or odd) and back — V(2,2) with the same smoother, transfers and
+// boundary treatment as the multi-kernel levels — in shared memory.  The side
+// is a template parameter so that all index arithmetic uses constants.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) k_coarse(Grid u, Grid b, float h2, int periodic,
-                                                int sweeps, float gam) {
-  const int s = u.s;
-  const int P = s + 2;
-  __shared__ float su[10 * 10 * 10];
-  __shared__ float sb[8 * 8 * 8];
-  __shared__ float red[32];
-  const int tid = threadIdx.x;
-  const int ncell = s * s * s;
-  for (int t = tid; t < P * P * P; t += blockDim.x) {
-    int i = t % P - 1, j = (t / P) % P - 1, k = t / (P * P) - 1;
-    su[t] = u.base[gidx(u, i, j, k)];
+namespace {
+
+template <int S>
+__device__ __forceinline__ int sui(int i, int j, int k) {
+  return ((k + 1) * (S + 2) + (j + 1)) * (S + 2) + (i + 1);
+}
+
+struct CmgArgs {
+  int periodic;
+  int level;   // multigrid level of the top grid
+  int sweeps;  // bottom sweeps
+};
+
+__device__ __forceinline__ float cmg_gam(const CmgArgs& a, int l) {
+  float H = (float)(1 << l);
+  return a.periodic ? 0.0f : (H - 1.0f) / (H + 1.0f);
+}
+
+// one colour (or, for odd S, a lexicographic pass by one thread)
+template <int S>
+__device__ void c_sweep(float* u, const float* b, float h2, float gam, int periodic, int color) {
+  constexpr int N3 = S * S * S;
+  const bool simple = periodic || gam == 0.0f;
+  auto upd = [&](int t) {
+    int i = t % S, j = (t / S) % S, k = t / (S * S);
+    int im = i == 0 ? (periodic ? S - 1 : -1) : i - 1, ip = i == S - 1 ? (periodic ? 0 : S) : i + 1;
+    int jm = j == 0 ? (periodic ? S - 1 : -1) : j - 1, jp = j == S - 1 ? (periodic ? 0 : S) : j + 1;
+    int km = k == 0 ? (periodic ? S - 1 : -1) : k - 1, kp = k == S - 1 ? (periodic ? 0 : S) : k + 1;
+    float sum = u[sui<S>(im, j, k)] + u[sui<S>(ip, j, k)] + u[sui<S>(i, jm, k)] +
+                u[sui<S>(i, jp, k)] + u[sui<S>(i, j, km)] + u[sui<S>(i, j, kp)];
+    int nb = (i == 0) + (i == S - 1) + (j == 0) + (j == S - 1) + (k == 0) + (k == S - 1);
+    u[sui<S>(i, j, k)] = (sum - h2 * b[t]) / (simple ? 6.0f : 6.0f + gam * (float)nb);
+  };
+  if (S & 1) {
+    if (threadIdx.x == 0)
+      for (int t = 0; t < N3; ++t) upd(t);
+  } else {
+    for (int t = threadIdx.x; t < N3; t += blockDim.x) {
+      int i = t % S, j = (t / S) % S, k = t / (S * S);
+      if (((i + j + k) & 1) == color) upd(t);
+    }
   }
-  for (int t = tid; t < ncell; t += blockDim.x) {
-    int i = t % s, j = (t / s) % s, k = t / (s * s);
+  __syncthreads();
+}
+
+template <int S>
+__device__ void c_smooth(float* u, const float* b, float h2, float gam, int periodic, int n) {
+  for (int w = 0; w < n; ++w) {
+    c_sweep<S>(u, b, h2, gam, periodic, 0);
+    if (!(S & 1)) c_sweep<S>(u, b, h2, gam, periodic, 1);
+  }
+}
+
+template <int S>
+__device__ void c_restrict(const float* u, const float* b, float* uc, float* bc, float inv_h2,
+                           float gam, int periodic) {
+  constexpr int SC = S / 2;
+  const bool simple = periodic || gam == 0.0f;
+  for (int T = threadIdx.x; T < SC * SC * SC; T += blockDim.x) {
+    int I = T % SC, J = (T / SC) % SC, K = T / (SC * SC);
+    float acc = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      int i = 2 * I + (d & 1), j = 2 * J + ((d >> 1) & 1), k = 2 * K + (d >> 2);
+      int im = i == 0 ? (periodic ? S - 1 : -1) : i - 1, ip = i == S - 1 ? (periodic ? 0 : S) : i + 1;
+      int jm = j == 0 ? (periodic ? S - 1 : -1) : j - 1, jp = j == S - 1 ? (periodic ? 0 : S) : j + 1;
+      int km = k == 0 ? (periodic ? S - 1 : -1) : k - 1, kp = k == S - 1 ? (periodic ? 0 : S) : k + 1;
+      int nb = (i == 0) + (i == S - 1) + (j == 0) + (j == S - 1) + (k == 0) + (k == S - 1);
+      float lap = u[sui<S>(im, j, k)] + u[sui<S>(ip, j, k)] + u[sui<S>(i, jm, k)] +
+                  u[sui<S>(i, jp, k)] + u[sui<S>(i, j, km)] + u[sui<S>(i, j, kp)] -
+                  (simple ? 6.0f : 6.0f + gam * (float)nb) * u[sui<S>(i, j, k)];
+      acc += b[(k * S + j) * S + i] - lap * inv_h2;
+    }
+    bc[T] = 0.125f * acc;
+    uc[sui<SC>(I, J, K)] = 0.0f;
+  }
+  __syncthreads();
+}
+
+template <int S>
+__device__ void c_prolong(const float* uc, float* u, float gam_c, int periodic) {
+  constexpr int SC = S / 2;
+  for (int t = threadIdx.x; t < S * S * S; t += blockDim.x) {
+    int i = t % S, j = (t / S) % S, k = t / (S * S);
+    int I = i >> 1, J = j >> 1, K = k >> 1;
+    int I2 = (i & 1) ? I + 1 : I - 1, J2 = (j & 1) ? J + 1 : J - 1, K2 = (k & 1) ? K + 1 : K - 1;
+    float fx = 1.0f, fy = 1.0f, fz = 1.0f;
+    if (periodic) {
+      I2 = I2 < 0 ? SC - 1 : (I2 >= SC ? 0 : I2);
+      J2 = J2 < 0 ? SC - 1 : (J2 >= SC ? 0 : J2);
+      K2 = K2 < 0 ? SC - 1 : (K2 >= SC ? 0 : K2);
+    } else {
+      if (I2 < 0 || I2 >= SC) { I2 = I; fx = -gam_c; }
+      if (J2 < 0 || J2 >= SC) { J2 = J; fy = -gam_c; }
+      if (K2 < 0 || K2 >= SC) { K2 = K; fz = -gam_c; }
+    }
+    float c000 = uc[sui<SC>(I, J, K)], c100 = fx * uc[sui<SC>(I2, J, K)];
+    float c010 = fy * uc[sui<SC>(I, J2, K)], c110 = fx * fy * uc[sui<SC>(I2, J2, K)];
+    float c001 = fz * uc[sui<SC>(I, J, K2)], c101 = fx * fz * uc[sui<SC>(I2, J, K2)];
+    float c011 = fy * fz * uc[sui<SC>(I, J2, K2)];
+    float c111 = fx * fy * fz * uc[sui<SC>(I2, J2, K2)];
+    float a0 = 0.75f * c000 + 0.25f * c100, a1 = 0.75f * c010 + 0.25f * c110;
+    float a2 = 0.75f * c001 + 0.25f * c101, a3 = 0.75f * c011 + 0.25f * c111;
+    float b0 = 0.75f * a0 + 0.25f * a1, b1 = 0.75f * a2 + 0.25f * a3;
+    u[sui<S>(i, j, k)] += 0.75f * b0 + 0.25f * b1;
+  }
+  __syncthreads();
+}
+
+template <int S>
+__device__ float c_mean(const float* v, bool padded, float* red) {
+  float acc = 0.0f;
+  for (int t = threadIdx.x; t < S * S * S; t += blockDim.x) {
+    int i = t % S, j = (t / S) % S, k = t / (S * S);
+    acc += padded ? v[sui<S>(i, j, k)] : v[t];
+  }
+  acc = warp_sumf_all(acc);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  float m = 0.0f;
+  for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) m += red[w];
+  __syncthreads();
+  return m / (float)(S * S * S);
+}
+
+// V-cycle from side S (level l) in shared memory starting at `mem`:
+// u (padded) then b, then the next level.
+template <int S>
+__device__ void c_vcycle(float* mem, const CmgArgs& a, int l, float* red) {
+  float* u = mem;
+  float* b = mem + (S + 2) * (S + 2) * (S + 2);
+  const float H = (float)(1 << l), h2 = H * H;
+  if constexpr (S <= 4 || (S & 1)) {
+    if (a.periodic) {
+      float m = c_mean<S>(b, false, red);
+      for (int t = threadIdx.x; t < S * S * S; t += blockDim.x) b[t] -= m;
+      __syncthreads();
+    }
+    c_smooth<S>(u, b, h2, cmg_gam(a, l), a.periodic, a.sweeps);
+    if (a.periodic) {
+      float m = c_mean<S>(u, true, red);
+      for (int t = threadIdx.x; t < S * S * S; t += blockDim.x) {
+        int i = t % S, j = (t / S) % S, k = t / (S * S);
+        u[sui<S>(i, j, k)] -= m;
+      }
+      __syncthreads();
+    }
+  } else {
+    constexpr int SC = S / 2;
+    float* uc = b + S * S * S;
+    float* bc = uc + (SC + 2) * (SC + 2) * (SC + 2);
+    c_smooth<S>(u, b, h2, cmg_gam(a, l), a.periodic, 2);
+    c_restrict<S>(u, b, uc, bc, 1.0f / h2, cmg_gam(a, l), a.periodic);
+    c_vcycle<SC>(uc, a, l + 1, red);
+    c_prolong<S>(uc, u, cmg_gam(a, l + 1), a.periodic);
+    c_smooth<S>(u, b, h2, cmg_gam(a, l), a.periodic, 2);
+  }
+}
+
+template <int S>
+__device__ void c_run(Grid u, Grid b, float* sm, const CmgArgs& a, float* red, int zero_top) {
+  constexpr int P = S + 2;
+  float* su = sm;
+  float* sb = sm + P * P * P;
+  // zero everything below the top (ghosts of coarse levels stay zero)
+  for (int t = threadIdx.x; t < 11776; t += blockDim.x) sm[t] = 0.0f;
+  __syncthreads();
+  for (int t = threadIdx.x; t < P * P * P; t += blockDim.x) {
+    int i = t % P - 1, j = (t / P) % P - 1, k = t / (P * P) - 1;
+    bool ghost = i < 0 || j < 0 || k < 0 || i >= S || j >= S || k >= S;
+    su[t] = (zero_top && !ghost) ? 0.0f : u.base[gidx(u, i, j, k)];
+  }
+  for (int t = threadIdx.x; t < S * S * S; t += blockDim.x) {
+    int i = t % S, j = (t / S) % S, k = t / (S * S);
     sb[t] = b.base[gidx(b, i, j, k)];
   }
   __syncthreads();
-  if (periodic) {
-    float v = 0.f;
-    for (int t = tid; t < ncell; t += blockDim.x) v += sb[t];
-    v = warp_sumf(v);
-    if ((tid & 31) == 0) red[tid >> 5] = v;
-    __syncthreads();
-    float mean = 0.f;
-    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) mean += red[w];
-    mean /= ncell;
-    for (int t = tid; t < ncell; t += blockDim.x) sb[t] -= mean;
-    __syncthreads();
+  c_vcycle<S>(sm, a, a.level, red);
+  for (int t = threadIdx.x; t < S * S * S; t += blockDim.x) {
+    int i = t % S, j = (t / S) % S, k = t / (S * S);
+    u.base[gidx(u, i, j, k)] = su[sui<S>(i, j, k)];
   }
-  // Odd sides (3): same-colour cells meet across the periodic wrap, so one
-  // thread sweeps lexicographically to stay deterministic.
-  const bool serial = (s & 1) != 0;
-  for (int sw = 0; sw < sweeps; ++sw) {
-    if (serial) {
-      if (tid == 0) {
-        for (int t = 0; t < ncell; ++t) {
-          int i = t % s, j = (t / s) % s, k = t / (s * s);
-          int im = periodic ? (i + s - 1) % s : i - 1, ip = periodic ? (i + 1) % s : i + 1;
-          int jm = periodic ? (j + s - 1) % s : j - 1, jp = periodic ? (j + 1) % s : j + 1;
-          int km = periodic ? (k + s - 1) % s : k - 1, kp = periodic ? (k + 1) % s : k + 1;
-#define SU(a, b2, c2) su[((c2) + 1) * P * P + ((b2) + 1) * P + (a) + 1]
-          float sum = SU(im, j, k) + SU(ip, j, k) + SU(i, jm, k) + SU(i, jp, k) +
-                      SU(i, j, km) + SU(i, j, kp);
-          SU(i, j, k) = (sum - h2 * sb[t]) / (periodic ? 6.0f : bnd_diag(i, j, k, s, gam));
-#undef SU
-        }
-      }
-      __syncthreads();
-      continue;
-    }
-    for (int color = 0; color < 2; ++color) {
-      for (int t = tid; t < ncell; t += blockDim.x) {
-        int i = t % s, j = (t / s) % s, k = t / (s * s);
-        if (((i + j + k) & 1) != color) continue;
-        int im = periodic ? (i + s - 1) % s : i - 1, ip = periodic ? (i + 1) % s : i + 1;
-        int jm = periodic ? (j + s - 1) % s : j - 1, jp = periodic ? (j + 1) % s : j + 1;
-        int km = periodic ? (k + s - 1) % s : k - 1, kp = periodic ? (k + 1) % s : k + 1;
-#define SU(a, b2, c2) su[((c2) + 1) * P * P + ((b2) + 1) * P + (a) + 1]
-        float sum = SU(im, j, k) + SU(ip, j, k) + SU(i, jm, k) + SU(i, jp, k) +
-                    SU(i, j, km) + SU(i, j, kp);
-        SU(i, j, k) = (sum - h2 * sb[t]) / (periodic ? 6.0f : bnd_diag(i, j, k, s, gam));
-#undef SU
-      }
-      __syncthreads();
-    }
+}
+
+}  // namespace
+
+constexpr int CMG_SMEM_FLOATS = 11776;  // 16^3 -> 8^3 -> 4^3 needs 11720
+
+// level: multigrid level index of (u, b); sides 16, 12, 8, 6, 4, 3 supported.
+// zero_top: the top level's iterate starts at zero (its interior is not read).
+__global__ void __launch_bounds__(1024) k_coarse_mg(Grid u, Grid b, int level, int periodic,
+                                                    int coarse_sweeps, int zero_top) {
+  __shared__ float sm[CMG_SMEM_FLOATS];
+  __shared__ float red[32];
+  CmgArgs a{periodic, level, coarse_sweeps};
+  switch (u.s) {
+    case 16: c_run<16>(u, b, sm, a, red, zero_top); break;
+    case 12: c_run<12>(u, b, sm, a, red, zero_top); break;
+    case 8: c_run<8>(u, b, sm, a, red, zero_top); break;
+    case 6: c_run<6>(u, b, sm, a, red, zero_top); break;
+    case 4: c_run<4>(u, b, sm, a, red, zero_top); break;
+    case 3: c_run<3>(u, b, sm, a, red, zero_top); break;
+    default: break;
   }
-  if (periodic) {
-    float v = 0.f;
-    for (int t = tid; t < ncell; t += blockDim.x) {
-      int i = t % s, j = (t / s) % s, k = t / (s * s);
-      v += su[(k + 1) * P * P + (j + 1) * P + i + 1];
-    }
-    v = warp_sumf(v);
-    __syncthreads();
-    if ((tid & 31) == 0) red[tid >> 5] = v;
-    __syncthreads();
-    float mean = 0.f;
-    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) mean += red[w];
-    mean /= ncell;
-    for (int t = tid; t < ncell; t += blockDim.x) {
-      int i = t % s, j = (t / s) % s, k = t / (s * s);
-      su[(k + 1) * P * P + (j + 1) * P + i + 1] -= mean;
-    }
-    __syncthreads();
-  }
-  for (int t = tid; t < ncell; t += blockDim.x) {
-    int i = t % s, j = (t / s) % s, k = t / (s * s);
-    u.base[gidx(u, i, j, k)] = su[(k + 1) * P * P + (j + 1) * P + i + 1];
-  }
+}
+
+void launch_coarse_mg(cudaStream_t st, Grid u, Grid b, int level, int periodic,
+                      int coarse_sweeps, bool zero_top) {
+  k_coarse_mg<<<1, 1024, 0, st>>>(u, b, level, periodic, coarse_sweeps, zero_top ? 1 : 0);
+  note_launch();
 }
 
 static inline dim3 grid_half(int s) { return dim3((unsigned)((s / 2 + 31) / 32), (unsigned)((s + 7) / 8), (unsigned)s); }
 static inline dim3 grid_full(int s) { return dim3((unsigned)((s + 31) / 32), (unsigned)((s + 7) / 8), (unsigned)s); }
 
 void launch_rbgs(cudaStream_t st, Grid u, Grid b, float h2, int color, int periodic,
-                 float gam) {
-  k_rbgs<<<grid_half(u.s), dim3(32, 8), 0, st>>>(u, b, h2, color, periodic, gam);
+                 float gam, bool zero_start) {
+  k_rbgs<<<grid_half(u.s), dim3(32, 8), 0, st>>>(u, b, h2, color, periodic, gam,
+                                                 zero_start ? 1 : 0);
   note_launch();
 }
 void launch_resid_restrict(cudaStream_t st, Grid u, Grid b, float inv_h2, Grid uc, Grid bc,
@@ -234,11 +361,6 @@ void launch_prolong(cudaStream_t st, Grid uc, Grid u, int periodic, float gam_c)
   k_prolong<<<grid_full(u.s), dim3(32, 8), 0, st>>>(uc, u, periodic, gam_c);
   note_launch();
 }
-void launch_coarse(cudaStream_t st, Grid u, Grid b, float h2, int periodic, int sweeps,
-                   float gam) {
-  k_coarse<<<1, 512, 0, st>>>(u, b, h2, periodic, sweeps, gam);
-  note_launch();
-}
 
 // ---------------------------------------------------------------------------
 // Double-float defect: r = f - (sum_nb Phi - 6 Phi) with Phi = hi + lo and
@@ -249,9 +371,14 @@ void launch_coarse(cudaStream_t st, Grid u, Grid b, float h2, int periodic, int 
 // (plain precision) the lo planes are all zero and the same kernel gives the
 // residual of the FP32 potential.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_defect(Grid ph, Grid pl, Grid fh, Grid fl, Grid rb,
-                                                Grid e, int periodic, int write_r,
-                                                double* __restrict__ partial,
+// With CORRECT the potential is first advanced by the V-cycle's correction,
+// Phi' = Phi + e (the e grid has zero ghosts / the same wrap), evaluated on
+// the fly at all 7 stencil points; Phi' is written out of place to (qh, ql)
+// and the residual is that of Phi'.
+template <bool CORRECT>
+__global__ void __launch_bounds__(256) k_defect(Grid ph, Grid pl, Grid e, Grid qh, Grid ql,
+                                                Grid fh, Grid fl, Grid rb, int periodic,
+                                                int write_r, double* __restrict__ partial,
                                                 unsigned int* counter, double* __restrict__ out) {
   const int s = ph.s;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -260,38 +387,56 @@ __global__ void __launch_bounds__(256) k_defect(Grid ph, Grid pl, Grid fh, Grid 
   for (int k = blockIdx.z; k < s && i < s && j < s; k += gridDim.z) {
     int c = gidx(ph, i, j, k);
     int xm = wrap_m(i, s, periodic) - i, xp = wrap_p(i, s, periodic) - i;
-    int ym = (wrap_m(j, s, periodic) - j) * ph.sy, yp = (wrap_p(j, s, periodic) - j) * ph.sy;
-    int zm = (wrap_m(k, s, periodic) - k) * ph.sz, zp = (wrap_p(k, s, periodic) - k) * ph.sz;
+    int ym = wrap_m(j, s, periodic) - j, yp = wrap_p(j, s, periodic) - j;
+    int zm = wrap_m(k, s, periodic) - k, zp = wrap_p(k, s, periodic) - k;
+    const int off[7] = {0, xm, xp, ym * ph.sy, yp * ph.sy, zm * ph.sz, zp * ph.sz};
+    float H[7], Lo[7];
     const float* h = ph.base + c;
     const float* l = pl.base + c;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      H[q] = h[off[q]];
+      Lo[q] = l[off[q]];
+    }
+    if (CORRECT) {
+      const float* ec = e.base + gidx(e, i, j, k);
+      const int eoff[7] = {0, xm, xp, ym * e.sy, yp * e.sy, zm * e.sz, zp * e.sz};
+#pragma unroll
+      for (int q = 0; q < 7; ++q) {
+        df t = two_sum(H[q], ec[eoff[q]]);
+        H[q] = t.hi;
+        Lo[q] = __fadd_rn(Lo[q], t.lo);
+      }
+      df n = fast_two_sum(H[0], Lo[0]);
+      int qc = gidx(qh, i, j, k);
+      qh.base[qc] = n.hi;
+      ql.base[qc] = n.lo;
+    }
     int fc = gidx(fh, i, j, k);
-    // r = f - sum_nb + 6 phi
+    // r = f - sum_nb + 6 phi: TwoSum cascade on the hi parts, rounding errors
+    // and lo parts in a float compensation term
     float sacc = fh.base[fc];
     float comp = fl.base[fc];
     df t;
-    t = two_sum(sacc, -h[xm]); sacc = t.hi; comp += t.lo;
-    t = two_sum(sacc, -h[xp]); sacc = t.hi; comp += t.lo;
-    t = two_sum(sacc, -h[ym]); sacc = t.hi; comp += t.lo;
-    t = two_sum(sacc, -h[yp]); sacc = t.hi; comp += t.lo;
-    t = two_sum(sacc, -h[zm]); sacc = t.hi; comp += t.lo;
-    t = two_sum(sacc, -h[zp]); sacc = t.hi; comp += t.lo;
-    df p6 = two_prod(6.0f, h[0]);
-    t = two_sum(sacc, p6.hi); sacc = t.hi; comp += t.lo + p6.lo;
-    comp -= (l[xm] + l[xp]) + (l[ym] + l[yp]) + (l[zm] + l[zp]);
-    comp += 6.0f * l[0];
-    float r = sacc + comp;
-    if (write_r) {
-      int rc = gidx(rb, i, j, k);
-      rb.base[rc] = r;
-      e.base[gidx(e, i, j, k)] = 0.0f;
+#pragma unroll
+    for (int q = 1; q < 7; ++q) {
+      t = two_sum(sacc, -H[q]);
+      sacc = t.hi;
+      comp += t.lo;
     }
+    df p6 = two_prod(6.0f, H[0]);
+    t = two_sum(sacc, p6.hi); sacc = t.hi; comp += t.lo + p6.lo;
+    comp -= (Lo[1] + Lo[2]) + (Lo[3] + Lo[4]) + (Lo[5] + Lo[6]);
+    comp += 6.0f * Lo[0];
+    float r = sacc + comp;
+    if (write_r) rb.base[gidx(rb, i, j, k)] = r;
     r2 = __fmaf_rn(r, r, r2);
   }
   __shared__ double sm[32];
-  double v = warp_sum((double)r2);
+  float vf = warp_sumf_all(r2);
   int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
   int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
-  if (lane == 0) sm[warp] = v;
+  if (lane == 0) sm[warp] = (double)vf;
   __syncthreads();
   unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
   unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
@@ -331,11 +476,15 @@ int defect_blocks(int s) {
   return (int)(g.x * g.y * g.z);
 }
 
-void launch_defect(cudaStream_t st, Grid ph, Grid pl, Grid fh, Grid fl, Grid rb, Grid e,
-                   int periodic, bool write_r, double* partial, unsigned int* counter,
-                   double* out) {
-  k_defect<<<grid_defect(ph.s), dim3(32, 8), 0, st>>>(ph, pl, fh, fl, rb, e, periodic,
-                                                    write_r ? 1 : 0, partial, counter, out);
+void launch_defect(cudaStream_t st, Grid ph, Grid pl, const Grid* e, Grid qh, Grid ql,
+                   Grid fh, Grid fl, Grid rb, int periodic, bool write_r, double* partial,
+                   unsigned int* counter, double* out) {
+  if (e)
+    k_defect<true><<<grid_defect(ph.s), dim3(32, 8), 0, st>>>(
+        ph, pl, *e, qh, ql, fh, fl, rb, periodic, write_r ? 1 : 0, partial, counter, out);
+  else
+    k_defect<false><<<grid_defect(ph.s), dim3(32, 8), 0, st>>>(
+        ph, pl, ph, qh, ql, fh, fl, rb, periodic, write_r ? 1 : 0, partial, counter, out);
   note_launch();
 }
 
@@ -354,6 +503,37 @@ __global__ void __launch_bounds__(256) k_correct(Grid ph, Grid pl, Grid e) {
 
 void launch_correct(cudaStream_t st, Grid ph, Grid pl, Grid e) {
   k_correct<<<grid_full(ph.s), dim3(32, 8), 0, st>>>(ph, pl, e);
+  note_launch();
+}
+
+// Warm start extrapolated in time: Phi <- Phi + w (Phi - Phi_prev),
+// Phi_prev <- old Phi (interior only; the ghost layer keeps its boundary
+// values).  Double-float when `pair`, FP32 hi only otherwise.
+__global__ void __launch_bounds__(256) k_predict(Grid ph, Grid pl, Grid qh, Grid ql, float w,
+                                                 int pair) {
+  const int s = ph.s;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z;
+  if (i >= s || j >= s) return;
+  int c = gidx(ph, i, j, k);
+  if (pair) {
+    df cur{ph.base[c], pl.base[c]}, prev{qh.base[c], ql.base[c]};
+    df d = df_add(cur, df{-prev.hi, -prev.lo});
+    df v = df_add(cur, df_mul(d, df{w, 0.0f}));
+    qh.base[c] = cur.hi;
+    ql.base[c] = cur.lo;
+    ph.base[c] = v.hi;
+    pl.base[c] = v.lo;
+  } else {
+    float cur = ph.base[c], prev = qh.base[c];
+    qh.base[c] = cur;
+    ph.base[c] = cur + w * (cur - prev);
+  }
+}
+
+void launch_predict(cudaStream_t st, Grid ph, Grid pl, Grid qh, Grid ql, float w, bool pair) {
+  k_predict<<<grid_full(ph.s), dim3(32, 8), 0, st>>>(ph, pl, qh, ql, w, pair ? 1 : 0);
   note_launch();
 }
 

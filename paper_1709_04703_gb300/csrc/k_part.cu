@@ -75,38 +75,68 @@ __global__ void __launch_bounds__(KT) k_gather_kick_drift(
       int CX[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) CX[q] = X[q] + 1;
-      // x-gradients: rows at (y node b, z node c), 4 samples along x
+      // The 8 nodes' centred differences touch 32 distinct mesh points: the
+      // 16 of the x-rows (y, z in the node range), plus 8 more in y and 8 in
+      // z; each is loaded once (hi and lo).
+      float Hx[2][2][4], Lx[2][2][4];  // [c][b][q]: (X[q], Y[b+1], Z[c+1])
+      float Hy[2][2][2], Ly[2][2][2];  // [c][a][e]: (X[a+1], Y[3e], Z[c+1])
+      float Hz[2][2][2], Lz[2][2][2];  // [b][a][e]: (X[a+1], Y[b+1], Z[3e])
 #pragma unroll
       for (int c = 0; c < 2; ++c)
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
           int r = RZ[c + 1] + RY[b + 1];
-          float h0 = ph[r + CX[0]], h1 = ph[r + CX[1]], h2 = ph[r + CX[2]], h3 = ph[r + CX[3]];
-          float l0 = pl[r + CX[0]], l1 = pl[r + CX[1]], l2 = pl[r + CX[2]], l3 = pl[r + CX[3]];
-          float g0 = (h2 - h0) + (l2 - l0);
-          float g1 = (h3 - h1) + (l3 - l1);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            Hx[c][b][q] = ph[r + CX[q]];
+            Lx[c][b][q] = pl[r + CX[q]];
+          }
+        }
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            int r = RZ[c + 1] + RY[3 * e] + CX[a + 1];
+            Hy[c][a][e] = ph[r];
+            Ly[c][a][e] = pl[r];
+          }
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            int r = RZ[3 * e] + RY[b + 1] + CX[a + 1];
+            Hz[b][a][e] = ph[r];
+            Lz[b][a][e] = pl[r];
+          }
+      // differences first (hi and lo separately), then the CIC weights
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          float g0 = (Hx[c][b][2] - Hx[c][b][0]) + (Lx[c][b][2] - Lx[c][b][0]);
+          float g1 = (Hx[c][b][3] - Hx[c][b][1]) + (Lx[c][b][3] - Lx[c][b][1]);
           Fx += wy[b] * wz[c] * (wx[0] * g0 + wx[1] * g1);
         }
 #pragma unroll
       for (int c = 0; c < 2; ++c)
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
-          int r = RZ[c + 1] + CX[a + 1];
-          float h0 = ph[r + RY[0]], h1 = ph[r + RY[1]], h2 = ph[r + RY[2]], h3 = ph[r + RY[3]];
-          float l0 = pl[r + RY[0]], l1 = pl[r + RY[1]], l2 = pl[r + RY[2]], l3 = pl[r + RY[3]];
-          float g0 = (h2 - h0) + (l2 - l0);
-          float g1 = (h3 - h1) + (l3 - l1);
+          // y node 0: Y[2] - Y[0];  y node 1: Y[3] - Y[1]
+          float g0 = (Hx[c][1][a + 1] - Hy[c][a][0]) + (Lx[c][1][a + 1] - Ly[c][a][0]);
+          float g1 = (Hy[c][a][1] - Hx[c][0][a + 1]) + (Ly[c][a][1] - Lx[c][0][a + 1]);
           Fy += wx[a] * wz[c] * (wy[0] * g0 + wy[1] * g1);
         }
 #pragma unroll
       for (int b = 0; b < 2; ++b)
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
-          int r = RY[b + 1] + CX[a + 1];
-          float h0 = ph[r + RZ[0]], h1 = ph[r + RZ[1]], h2 = ph[r + RZ[2]], h3 = ph[r + RZ[3]];
-          float l0 = pl[r + RZ[0]], l1 = pl[r + RZ[1]], l2 = pl[r + RZ[2]], l3 = pl[r + RZ[3]];
-          float g0 = (h2 - h0) + (l2 - l0);
-          float g1 = (h3 - h1) + (l3 - l1);
+          // z node 0: Z[2] - Z[0];  z node 1: Z[3] - Z[1]
+          float g0 = (Hx[1][b][a + 1] - Hz[b][a][0]) + (Lx[1][b][a + 1] - Lz[b][a][0]);
+          float g1 = (Hz[b][a][1] - Hx[0][b][a + 1]) + (Lz[b][a][1] - Lx[0][b][a + 1]);
           Fz += wx[a] * wy[b] * (wz[0] * g0 + wz[1] * g1);
         }
       Fx *= 0.5f;

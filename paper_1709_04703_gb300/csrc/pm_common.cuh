@@ -71,11 +71,22 @@ __device__ __forceinline__ df df_mul(df a, df b) {
   return fast_two_sum(p.hi, p.lo);
 }
 
-// int64 -> (hi, lo) float pair with relative error <= 2^-48 (exact hi part).
-__device__ __forceinline__ df df_from_i64(long long v) {
-  float hi = __ll2float_rn(v);
-  long long r = v - __float2ll_rn(hi);
-  return {hi, __ll2float_rn(r)};
+// Non-negative 64-bit count -> (hi, lo) float pair, without 64-bit
+// conversions (those run on the FP64 pipe, 1/64 rate on GB300): v is split
+// into three 24-bit digits, each exact in float, and summed error-free.
+// Exact for v < 2^72 up to the final rounding of lo (relative 2^-48).
+__device__ __forceinline__ df df_from_u64(unsigned long long v) {
+  float a = (float)(unsigned)(v >> 48) * 281474976710656.0f;            // 2^48
+  float b = (float)(unsigned)((v >> 24) & 0xffffffu) * 16777216.0f;      // 2^24
+  float c = (float)(unsigned)(v & 0xffffffu);
+  df s = two_sum(a, b);
+  df t = two_sum(s.hi, c);
+  return fast_two_sum(t.hi, __fadd_rn(s.lo, t.lo));
+}
+
+__device__ __forceinline__ float warp_sumf_all(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
 // ---------------------------------------------------------------------------

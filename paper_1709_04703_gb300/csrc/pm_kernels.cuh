@@ -30,17 +30,21 @@ void launch_boundary(cudaStream_t st, Grid ph, Grid pl, int n, int lo, const dou
 
 // k_mg.cu
 void launch_rbgs(cudaStream_t st, Grid u, Grid b, float h2, int color, int periodic,
-                 float gam);
+                 float gam, bool zero_start = false);
+// the rest of a V-cycle from a level of side <= CMG_MAX_SIDE in one CTA
+constexpr int CMG_MAX_SIDE = 16;
+void launch_coarse_mg(cudaStream_t st, Grid u, Grid b, int level, int periodic,
+                      int coarse_sweeps, bool zero_top);
 void launch_resid_restrict(cudaStream_t st, Grid u, Grid b, float inv_h2, Grid uc, Grid bc,
                            int periodic, float gam);
 void launch_prolong(cudaStream_t st, Grid uc, Grid u, int periodic, float gam_c);
-void launch_coarse(cudaStream_t st, Grid u, Grid b, float h2, int periodic, int sweeps,
-                   float gam);
-void launch_defect(cudaStream_t st, Grid ph, Grid pl, Grid fh, Grid fl, Grid rb, Grid e,
-                   int periodic, bool write_r, double* partial, unsigned int* counter,
-                   double* out);
+// residual of Phi (e == NULL) or of Phi + e written to (qh, ql) (e != NULL)
+void launch_defect(cudaStream_t st, Grid ph, Grid pl, const Grid* e, Grid qh, Grid ql,
+                   Grid fh, Grid fl, Grid rb, int periodic, bool write_r, double* partial,
+                   unsigned int* counter, double* out);
 int defect_blocks(int s);
 void launch_correct(cudaStream_t st, Grid ph, Grid pl, Grid e);
+void launch_predict(cudaStream_t st, Grid ph, Grid pl, Grid qh, Grid ql, float w, bool pair);
 void launch_fill(cudaStream_t st, Grid g, float v, bool with_ghost);
 void launch_phi_out(cudaStream_t st, Grid ph, Grid pl, float* out32, double* out64,
                     double shift);
