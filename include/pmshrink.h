@@ -223,6 +223,33 @@ pm_status pm_profile(pm_ctx* ctx, int32_t enable);
 pm_status pm_profile_read(pm_ctx* ctx, int32_t cls, double* ms, int64_t* groups,
                           double* bytes);
 
+/* ---------------------------------------------------------------------------
+ * Batched step: many independent realisations (each its own configuration,
+ * mesh size, particles and lightcone schedule; Sec. 2.4 applied to each)
+ * advance together.  Every phase of pm_step runs as one kernel launch over
+ * all realisations (a device table maps each block to a realisation), and
+ * one CUDA graph per batch holds the V-cycle of every realisation; a
+ * realisation whose solve has converged is masked out of further V-cycles.
+ * Results equal those of separate contexts bit for bit.
+ * Requirements: 1 <= n_real <= 64, precision PM_MIXED, all realisations on
+ * the same number of steps and a_init/a_final (one schedule of a, each with
+ * its own chi(a)/cell), stream not NULL.
+ * pos4[r] / mom4[r]: cfgs[r].n_particles records each (host_mem as in
+ * pm_init).  Errors as pm_init / pm_step; pm_batch_last_error() explains.
+ * ------------------------------------------------------------------------- */
+typedef struct pm_batch pm_batch;
+pm_status pm_batch_init(int32_t n_real, const pm_config* cfgs, const float* const* pos4,
+                        const float* const* mom4, int32_t host_mem, void* stream,
+                        pm_batch** out);
+pm_status pm_batch_step(pm_batch* b, int32_t n_steps);
+pm_status pm_batch_stats(pm_batch* b, int32_t r, pm_stats_t* out);
+pm_status pm_batch_get_particles(pm_batch* b, int32_t r, float* pos4, float* mom4,
+                                 int32_t host_mem, int64_t* n_active_out);
+pm_status pm_batch_get_lightcone(pm_batch* b, int32_t r, float* pos4, float* mom4,
+                                 int32_t host_mem, int64_t* n_out);
+const char* pm_batch_last_error(const pm_batch* b);
+void pm_batch_destroy(pm_batch* b);
+
 /* Allocation-free lightcone compaction.  The paper has no counterpart: this
  * is a variant of pm_shrink's compaction for callers that cannot allocate
  * device memory — host programs that hand the library a fixed memory budget

@@ -26,6 +26,8 @@ EXPORTED = [
     "pm_get_particles", "pm_set_particles", "pm_get_lightcone", "pm_get_forces",
     "pm_get_potential", "pm_profile", "pm_profile_read", "pm_launch_count", "pm_last_error",
     "pm_destroy", "pm_shrink_static", "pm_shrink_static_error",
+    "pm_batch_init", "pm_batch_step", "pm_batch_stats", "pm_batch_get_particles",
+    "pm_batch_get_lightcone", "pm_batch_last_error", "pm_batch_destroy",
 ]
 PROF_CLASSES = ["deposit", "source", "boundary", "smooth0", "transfer0", "coarse",
                 "defect", "correct", "gather", "compact"]
@@ -93,6 +95,14 @@ def load():
         "pm_shrink_static": (I32, [P, P, I64, I32, D, D, D, D, D, P, P, P, P,
                                    C.POINTER(I64), P]),
         "pm_shrink_static_error": (C.c_char_p, []),
+        "pm_batch_init": (I32, [I32, C.POINTER(PmConfig), C.POINTER(P), C.POINTER(P), I32, P,
+                                C.POINTER(P)]),
+        "pm_batch_step": (I32, [P, I32]),
+        "pm_batch_stats": (I32, [P, I32, C.POINTER(PmStats)]),
+        "pm_batch_get_particles": (I32, [P, I32, P, P, I32, C.POINTER(I64)]),
+        "pm_batch_get_lightcone": (I32, [P, I32, P, P, I32, C.POINTER(I64)]),
+        "pm_batch_last_error": (C.c_char_p, [P]),
+        "pm_batch_destroy": (None, [P]),
         "pm_last_error": (C.c_char_p, [P]),
         "pm_destroy": (None, [P]),
     }

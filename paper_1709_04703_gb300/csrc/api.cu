@@ -26,7 +26,7 @@ namespace {
 
 constexpr double C_OVER_H0 = 2997.92458;  // Mpc/h
 constexpr int SRC_GRID = 1216;            // 152 SMs x 8 blocks
-constexpr int COARSE_SWEEPS = 24;
+constexpr int COARSE_SWEEPS = 12;
 
 // ---------------------------------------------------------------------------
 // FP64 cosmology on the host.  tau(a) = int_0^a da'/(a'^2 E), H0 = 1, with
@@ -1158,6 +1158,709 @@ void pm_destroy(pm_ctx* ctx) {
   if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
   if (ctx->h_cnt) cudaFreeHost(ctx->h_cnt);
   delete ctx;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Batched step: R realisations, one launch per phase, one V-cycle graph.
+// ===========================================================================
+namespace {
+
+// Device-resident descriptor table of one batched launch, with a pinned
+// staging copy on the host.
+struct BTab {
+  void* d_desc = nullptr;
+  BTable* d_tab = nullptr;
+  void* h_desc = nullptr;
+  BTable* h_tab = nullptr;
+  size_t desc_size = 0;
+  int grid_max = 0;  // largest block total seen (graph launches use it)
+};
+
+}  // namespace
+
+struct pm_batch {
+  int R = 0;
+  cudaStream_t st = nullptr;
+  std::vector<pm_ctx*> ctx;
+  int* d_active = nullptr;
+  int* h_active = nullptr;
+  double* d_scal = nullptr;  // 16 per realisation: [0] ||f||^2, [1..10] moments, [11] ||r||^2
+  double* h_scal = nullptr;
+  unsigned long long* d_cnt = nullptr;  // 4 per realisation: [0] survivors
+  unsigned long long* h_cnt = nullptr;
+  int* d_ovf = nullptr;
+  BTab t_dep, t_src, t_bnd, t_pred, t_def, t_gat, t_scan, t_scat;
+  std::vector<BTab> t_vc;  // V-cycle launch slots
+  int maxLc = 0;
+  bool tables_stale = true;
+  cudaGraphExec_t vgraph = nullptr;
+  long long vgraph_kernels = 0;
+  std::string err;
+};
+
+namespace {
+
+pm_status bfail(pm_batch* b, pm_status code, const std::string& msg) {
+  if (b) b->err = msg; else g_err = msg;
+  return code;
+}
+
+pm_status tab_alloc(pm_batch* B, BTab& t, size_t desc_size) {
+  t.desc_size = desc_size;
+  if (cudaMalloc(&t.d_desc, desc_size * MAX_MEMBERS) != cudaSuccess ||
+      cudaMalloc((void**)&t.d_tab, sizeof(BTable)) != cudaSuccess ||
+      cudaMallocHost(&t.h_desc, desc_size * MAX_MEMBERS) != cudaSuccess ||
+      cudaMallocHost((void**)&t.h_tab, sizeof(BTable)) != cudaSuccess)
+    return bfail(B, PM_ENOMEM, "pm_batch: table allocation failed");
+  t.h_tab->m = 0;
+  t.h_tab->off[0] = 0;
+  return PM_OK;
+}
+
+void tab_free(BTab& t) {
+  if (t.d_desc) cudaFree(t.d_desc);
+  if (t.d_tab) cudaFree(t.d_tab);
+  if (t.h_desc) cudaFreeHost(t.h_desc);
+  if (t.h_tab) cudaFreeHost(t.h_tab);
+  t = BTab();
+}
+
+// Stage descriptors (with their block counts) and upload; returns the block
+// total.  The staging buffers are reused only after the stream has passed
+// the previous upload (every batched phase is followed by a sync before the
+// same table is rebuilt).
+template <class D>
+int tab_upload(pm_batch* B, BTab& t, const std::vector<D>& d, const std::vector<int>& blocks) {
+  const int m = std::min((int)d.size(), MAX_MEMBERS);  // callers add <= 2 per realisation
+  std::memcpy(t.h_desc, d.data(), sizeof(D) * m);
+  t.h_tab->m = m;
+  t.h_tab->off[0] = 0;
+  for (int q = 0; q < m; ++q) t.h_tab->off[q + 1] = t.h_tab->off[q] + blocks[q];
+  if (m) cudaMemcpyAsync(t.d_desc, t.h_desc, sizeof(D) * m, cudaMemcpyHostToDevice, B->st);
+  cudaMemcpyAsync(t.d_tab, t.h_tab, sizeof(BTable), cudaMemcpyHostToDevice, B->st);
+  int tot = t.h_tab->off[m];
+  if (tot > t.grid_max) t.grid_max = tot;
+  return tot;
+}
+
+int nblocks(dim3 g) { return (int)(g.x * g.y * g.z); }
+
+template <class D>
+void set_dims(D& d, int r, dim3 g) {
+  d.r = r;
+  d.gx = (int)g.x;
+  d.gy = (int)g.y;
+  d.gz = (int)g.z;
+}
+
+int first_small_level(const pm_ctx* c) {
+  int L = (int)c->ls.size() - 1, Lc = 0;
+  while (Lc < L && c->ls[Lc] > CMG_MAX_SIDE) ++Lc;
+  return Lc;
+}
+
+float level_gam(int l) {
+  float H = (float)(1 << l);
+  return (H - 1.0f) / (H + 1.0f);
+}
+
+// V-cycle slot layout: down (4 sweeps + restriction per level), bottom, up
+// (prolongation + 4 sweeps per level).
+int slot_down(int l, int k) { return 5 * l + k; }            // k: 0..3 sweeps, 4 restrict
+int slot_bottom(int maxLc) { return 5 * maxLc; }
+int slot_up(int maxLc, int l, int k) { return 5 * maxLc + 1 + 5 * l + k; }  // k: 0 prolong, 1..4 sweeps
+int n_slots(int maxLc) { return 10 * maxLc + 1; }
+
+// Upload the descriptor tables of every V-cycle slot for the current cubes.
+void upload_vcycle_tables(pm_batch* B) {
+  const int R = B->R, M = B->maxLc;
+  for (int l = 0; l < M; ++l) {
+    for (int k = 0; k < 5; ++k) {  // down
+      std::vector<int> bl;
+      if (k < 4) {
+        std::vector<RbgsDesc> d;
+        for (int r = 0; r < R; ++r) {
+          pm_ctx* c = B->ctx[r];
+          if (l >= first_small_level(c)) continue;
+          RbgsDesc e{};
+          e.u = compact_view(c->lu[l], c->ls[l]);
+          e.b = compact_view(c->lb[l], c->ls[l]);
+          e.h2 = (float)(1 << (2 * l));
+          e.gam = level_gam(l);
+          e.color = k & 1;
+          e.periodic = c->periodic;
+          e.zero_start = k == 0;  // level 0: e is not cleared; coarser: restriction zeroed it
+          set_dims(e, r, rbgs_grid(c->ls[l]));
+          d.push_back(e);
+          bl.push_back(nblocks(rbgs_grid(c->ls[l])));
+        }
+        tab_upload(B, B->t_vc[slot_down(l, k)], d, bl);
+      } else {
+        std::vector<RestrictDesc> d;
+        for (int r = 0; r < R; ++r) {
+          pm_ctx* c = B->ctx[r];
+          if (l >= first_small_level(c)) continue;
+          RestrictDesc e{};
+          e.u = compact_view(c->lu[l], c->ls[l]);
+          e.b = compact_view(c->lb[l], c->ls[l]);
+          e.uc = compact_view(c->lu[l + 1], c->ls[l + 1]);
+          e.bc = compact_view(c->lb[l + 1], c->ls[l + 1]);
+          e.inv_h2 = 1.0f / (float)(1 << (2 * l));
+          e.gam = level_gam(l);
+          e.periodic = c->periodic;
+          set_dims(e, r, full_grid(c->ls[l + 1]));
+          d.push_back(e);
+          bl.push_back(nblocks(full_grid(c->ls[l + 1])));
+        }
+        tab_upload(B, B->t_vc[slot_down(l, k)], d, bl);
+      }
+    }
+  }
+  {  // bottom
+    std::vector<CmgDesc> d;
+    std::vector<int> bl;
+    for (int r = 0; r < R; ++r) {
+      pm_ctx* c = B->ctx[r];
+      int Lc = first_small_level(c);
+      CmgDesc e{};
+      e.u = compact_view(c->lu[Lc], c->ls[Lc]);
+      e.b = compact_view(c->lb[Lc], c->ls[Lc]);
+      e.level = Lc;
+      e.periodic = c->periodic;
+      e.sweeps = COARSE_SWEEPS;
+      e.zero_top = 1;
+      set_dims(e, r, dim3(1, 1, 1));
+      d.push_back(e);
+      bl.push_back(1);
+    }
+    tab_upload(B, B->t_vc[slot_bottom(M)], d, bl);
+  }
+  for (int l = 0; l < M; ++l) {
+    for (int k = 0; k < 5; ++k) {  // up
+      std::vector<int> bl;
+      if (k == 0) {
+        std::vector<ProlongDesc> d;
+        for (int r = 0; r < R; ++r) {
+          pm_ctx* c = B->ctx[r];
+          if (l >= first_small_level(c)) continue;
+          ProlongDesc e{};
+          e.uc = compact_view(c->lu[l + 1], c->ls[l + 1]);
+          e.u = compact_view(c->lu[l], c->ls[l]);
+          e.gam_c = level_gam(l + 1);
+          e.periodic = c->periodic;
+          set_dims(e, r, full_grid(c->ls[l]));
+          d.push_back(e);
+          bl.push_back(nblocks(full_grid(c->ls[l])));
+        }
+        tab_upload(B, B->t_vc[slot_up(M, l, k)], d, bl);
+      } else {
+        std::vector<RbgsDesc> d;
+        for (int r = 0; r < R; ++r) {
+          pm_ctx* c = B->ctx[r];
+          if (l >= first_small_level(c)) continue;
+          RbgsDesc e{};
+          e.u = compact_view(c->lu[l], c->ls[l]);
+          e.b = compact_view(c->lb[l], c->ls[l]);
+          e.h2 = (float)(1 << (2 * l));
+          e.gam = level_gam(l);
+          e.color = (k - 1) & 1;
+          e.periodic = c->periodic;
+          e.zero_start = 0;
+          set_dims(e, r, rbgs_grid(c->ls[l]));
+          d.push_back(e);
+          bl.push_back(nblocks(rbgs_grid(c->ls[l])));
+        }
+        tab_upload(B, B->t_vc[slot_up(M, l, k)], d, bl);
+      }
+    }
+  }
+}
+
+// Launch the V-cycle slots (captured once into a graph, grids at their
+// largest; members and their grids come from the tables).
+void launch_vcycle_slots(pm_batch* B) {
+  const int M = B->maxLc;
+  const int* act = B->d_active;
+  for (int l = 0; l < M; ++l) {
+    for (int k = 0; k < 4; ++k) {
+      BTab& t = B->t_vc[slot_down(l, k)];
+      launch_rbgs_b(B->st, t.grid_max, (const RbgsDesc*)t.d_desc, t.d_tab, act);
+    }
+    BTab& t = B->t_vc[slot_down(l, 4)];
+    launch_restrict_b(B->st, t.grid_max, (const RestrictDesc*)t.d_desc, t.d_tab, act);
+  }
+  BTab& tb = B->t_vc[slot_bottom(M)];
+  launch_coarse_mg_b(B->st, tb.grid_max, (const CmgDesc*)tb.d_desc, tb.d_tab, act);
+  for (int l = M - 1; l >= 0; --l) {
+    BTab& tp = B->t_vc[slot_up(M, l, 0)];
+    launch_prolong_b(B->st, tp.grid_max, (const ProlongDesc*)tp.d_desc, tp.d_tab, act);
+    for (int k = 1; k < 5; ++k) {
+      BTab& t = B->t_vc[slot_up(M, l, k)];
+      launch_rbgs_b(B->st, t.grid_max, (const RbgsDesc*)t.d_desc, t.d_tab, act);
+    }
+  }
+}
+
+pm_status batch_vcycle(pm_batch* B) {
+  if (B->tables_stale) {
+    upload_vcycle_tables(B);
+    B->tables_stale = false;
+  }
+  cudaMemcpyAsync(B->d_active, B->h_active, sizeof(int) * B->R, cudaMemcpyHostToDevice, B->st);
+  if (!B->vgraph) {
+    // grids of the graph: the largest totals (taken from the first cubes,
+    // which are the largest of the run)
+    cudaError_t e = cudaStreamBeginCapture(B->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bfail(B, PM_ECUDA, cudaGetErrorString(e));
+    long long l0 = g_launches.load();
+    launch_vcycle_slots(B);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(B->st, &g);
+    B->vgraph_kernels = g_launches.load() - l0;
+    g_launches.fetch_sub(B->vgraph_kernels);
+    if (e != cudaSuccess) return bfail(B, PM_ECUDA, cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&B->vgraph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bfail(B, PM_ECUDA, cudaGetErrorString(e));
+  }
+  cudaError_t e = cudaGraphLaunch(B->vgraph, B->st);
+  if (e != cudaSuccess) return bfail(B, PM_ECUDA, cudaGetErrorString(e));
+  g_launches.fetch_add(B->vgraph_kernels);
+  return PM_OK;
+}
+
+pm_status batch_sync(pm_batch* B) {
+  cudaMemcpyAsync(B->h_scal, B->d_scal, sizeof(double) * 16 * B->R, cudaMemcpyDeviceToHost,
+                  B->st);
+  cudaMemcpyAsync(B->h_cnt, B->d_cnt, sizeof(unsigned long long) * 4 * B->R,
+                  cudaMemcpyDeviceToHost, B->st);
+  cudaError_t e = cudaStreamSynchronize(B->st);
+  if (e != cudaSuccess) return bfail(B, PM_ECUDA, cudaGetErrorString(e));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return bfail(B, PM_ECUDA, cudaGetErrorString(e));
+  return PM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pm_status pm_batch_init(int32_t n_real, const pm_config* cfgs, const float* const* pos4,
+                        const float* const* mom4, int32_t host_mem, void* stream,
+                        pm_batch** out) {
+  if (!out) return bfail(nullptr, PM_EINVAL, "pm_batch_init: out is NULL");
+  *out = nullptr;
+  if (n_real < 1 || n_real > MAX_REAL || !cfgs || !pos4 || !mom4 || !stream)
+    return bfail(nullptr, PM_EINVAL, "pm_batch_init: bad argument");
+  for (int r = 0; r < n_real; ++r) {
+    if (cfgs[r].precision != PM_MIXED)
+      return bfail(nullptr, PM_EINVAL, "pm_batch_init: batches run in PM_MIXED precision");
+    if (cfgs[r].n_steps != cfgs[0].n_steps || cfgs[r].a_init != cfgs[0].a_init ||
+        cfgs[r].a_final != cfgs[0].a_final)
+      return bfail(nullptr, PM_EINVAL, "pm_batch_init: realisations must share the a schedule");
+  }
+  pm_batch* B = new pm_batch();
+  B->R = n_real;
+  B->st = (cudaStream_t)stream;
+  for (int r = 0; r < n_real; ++r) {
+    pm_ctx* c = nullptr;
+    pm_status s = pm_init(&cfgs[r], pos4[r], mom4[r], host_mem, stream, &c);
+    if (s != PM_OK) {
+      B->err = std::string("pm_batch_init: realisation ") + std::to_string(r) + ": " + g_err;
+      g_err = B->err;
+      pm_batch_destroy(B);
+      return s;
+    }
+    c->use_graphs = false;
+    B->ctx.push_back(c);
+  }
+  pm_status st = PM_OK;
+  if (cudaMalloc((void**)&B->d_active, sizeof(int) * MAX_REAL) != cudaSuccess ||
+      cudaMallocHost((void**)&B->h_active, sizeof(int) * MAX_REAL) != cudaSuccess ||
+      cudaMalloc((void**)&B->d_scal, sizeof(double) * 16 * MAX_REAL) != cudaSuccess ||
+      cudaMallocHost((void**)&B->h_scal, sizeof(double) * 16 * MAX_REAL) != cudaSuccess ||
+      cudaMalloc((void**)&B->d_cnt, sizeof(unsigned long long) * 4 * MAX_REAL) != cudaSuccess ||
+      cudaMallocHost((void**)&B->h_cnt, sizeof(unsigned long long) * 4 * MAX_REAL) !=
+          cudaSuccess ||
+      cudaMalloc((void**)&B->d_ovf, sizeof(int) * MAX_REAL) != cudaSuccess)
+    st = bfail(B, PM_ENOMEM, "pm_batch_init: allocation failed");
+  if (st == PM_OK) st = tab_alloc(B, B->t_dep, sizeof(DepositDesc));
+  if (st == PM_OK) st = tab_alloc(B, B->t_src, sizeof(SourceDesc));
+  if (st == PM_OK) st = tab_alloc(B, B->t_bnd, sizeof(BoundaryDesc));
+  if (st == PM_OK) st = tab_alloc(B, B->t_pred, sizeof(PredictDesc));
+  if (st == PM_OK) st = tab_alloc(B, B->t_def, sizeof(DefectDesc));
+  if (st == PM_OK) st = tab_alloc(B, B->t_gat, sizeof(GatherDesc));
+  if (st == PM_OK) st = tab_alloc(B, B->t_scan, sizeof(ScanDesc));
+  if (st == PM_OK) st = tab_alloc(B, B->t_scat, sizeof(ScatterDesc));
+  if (st != PM_OK) {
+    pm_batch_destroy(B);
+    return st;
+  }
+  cudaMemsetAsync(B->d_scal, 0, sizeof(double) * 16 * MAX_REAL, B->st);
+  cudaMemsetAsync(B->d_cnt, 0, sizeof(unsigned long long) * 4 * MAX_REAL, B->st);
+  cudaMemsetAsync(B->d_ovf, 0, sizeof(int) * MAX_REAL, B->st);
+  *out = B;
+  return PM_OK;
+}
+
+pm_status pm_batch_step(pm_batch* B, int32_t n_steps) {
+  if (!B) return bfail(nullptr, PM_EINVAL, "pm_batch_step: NULL batch");
+  const int R = B->R;
+  for (int q = 0; q < n_steps; ++q) {
+    const int k = B->ctx[0]->step;
+    if (k >= B->ctx[0]->cfg.n_steps) return bfail(B, PM_EINVAL, "pm_batch_step: past the end");
+    // per realisation: active cube, phase, schedule scalars
+    std::vector<int> phase_changed(R, 0);
+    for (int r = 0; r < R; ++r) {
+      pm_ctx* c = B->ctx[r];
+      int lo, s, per;
+      geometry(c, c->R[k], &lo, &s, &per);
+      phase_changed[r] = !c->cube_valid || per != c->periodic;
+      bool changed = !c->cube_valid || lo != c->lo || s != c->s || per != c->periodic;
+      pm_status st = set_cube(c, lo, s, per, c->R[k]);
+      if (st != PM_OK) return bfail(B, st, c->err);
+      if (changed) B->tables_stale = true;
+    }
+    if (B->tables_stale && !B->vgraph) {
+      // the first configuration fixes the V-cycle depth (cubes only shrink)
+      int M = 0;
+      for (int r = 0; r < R; ++r) M = std::max(M, first_small_level(B->ctx[r]));
+      B->maxLc = M;
+      B->t_vc.resize(n_slots(M));
+      for (auto& t : B->t_vc) {
+        size_t sz = std::max(std::max(sizeof(RbgsDesc), sizeof(RestrictDesc)),
+                             std::max(sizeof(ProlongDesc), sizeof(CmgDesc)));
+        pm_status st = tab_alloc(B, t, sz);
+        if (st != PM_OK) return st;
+      }
+    }
+    // 1-2. half drift + deposit
+    {
+      std::vector<DepositDesc> d;
+      std::vector<int> bl;
+      for (int r = 0; r < R; ++r) {
+        pm_ctx* c = B->ctx[r];
+        if (c->n_active <= 0) continue;
+        DepositDesc e{};
+        e.pos = c->pos;
+        e.mom = c->mom;
+        e.N = c->n_active;
+        e.c0 = (float)(c->dtau[k] / (2.0 * c->a[k]));
+        e.n = c->n;
+        e.lo = c->lo;
+        e.s = c->s;
+        e.periodic = c->periodic;
+        e.rho = c->rho;
+        e.escaped = c->d_cnt + 1;
+        int nb = deposit_blocks(c->n_active);
+        set_dims(e, r, dim3(nb, 1, 1));
+        d.push_back(e);
+        bl.push_back(nb);
+      }
+      int g = tab_upload(B, B->t_dep, d, bl);
+      launch_deposit_b(B->st, g, (const DepositDesc*)B->t_dep.d_desc, B->t_dep.d_tab);
+    }
+    // 3. source (+ moments), boundary ghosts in both potential buffers, predict
+    {
+      std::vector<SourceDesc> d;
+      std::vector<int> bl;
+      for (int r = 0; r < R; ++r) {
+        pm_ctx* c = B->ctx[r];
+        const int n = c->n, lo = c->lo, s = c->s;
+        const double S = 1.5 * c->cfg.omega_m / c->a_half[k];
+        const double nbar = (double)c->N0 / ((double)n * n * n);
+        const double invM = 1.0 / (281474976710656.0 * nbar);
+        int b0 = 0, b1 = n - 1;
+        if (!c->periodic) {
+          double cc = 0.5 * n;
+          b0 = std::max(lo, (int)std::ceil(cc - c->R[k] - 0.5));
+          b1 = std::min(lo + s - 1, (int)std::floor(cc + c->R[k] - 0.5));
+        }
+        SourceDesc e{};
+        e.rho = c->rho;
+        e.n = n;
+        e.lo = lo;
+        e.s = s;
+        e.fh = full_view(c, c->f_hi, lo, s);
+        e.fl = full_view(c, c->f_lo, lo, s);
+        e.invM.hi = (float)invM;
+        e.invM.lo = (float)(invM - (double)e.invM.hi);
+        e.S.hi = (float)S;
+        e.S.lo = (float)(S - (double)e.S.hi);
+        e.b0 = b0;
+        e.b1 = b1;
+        e.moments = !c->periodic;
+        e.partial_f2 = c->partial;
+        e.partial_m = c->partial_m;
+        e.counter = c->counter;
+        e.out = B->d_scal + 16 * r;
+        e.bgm = c->bgm;
+        e.invM_d = invM;
+        e.overflow = B->d_ovf + r;
+        set_dims(e, r, source_grid(s));
+        d.push_back(e);
+        bl.push_back(nblocks(source_grid(s)));
+      }
+      int g = tab_upload(B, B->t_src, d, bl);
+      launch_source_b(B->st, g, (const SourceDesc*)B->t_src.d_desc, B->t_src.d_tab);
+    }
+    {
+      std::vector<BoundaryDesc> d;
+      std::vector<int> bl;
+      for (int r = 0; r < R; ++r) {
+        pm_ctx* c = B->ctx[r];
+        if (c->periodic) continue;
+        for (int qb = 0; qb < 2; ++qb) {
+          BoundaryDesc e{};
+          e.ph = full_view(c, c->phi_h[qb], c->lo, c->s);
+          e.pl = full_view(c, c->phi_l[qb], c->lo, c->s);
+          e.n = c->n;
+          e.lo = c->lo;
+          e.mom = B->d_scal + 16 * r + 1;
+          e.S = 1.5 * c->cfg.omega_m / c->a_half[k];
+          e.want_lo = 1;
+          int nb = boundary_blocks(c->s);
+          set_dims(e, r, dim3(nb, 1, 1));
+          d.push_back(e);
+          bl.push_back(nb);
+        }
+      }
+      int g = tab_upload(B, B->t_bnd, d, bl);
+      launch_boundary_b(B->st, g, (const BoundaryDesc*)B->t_bnd.d_desc, B->t_bnd.d_tab);
+    }
+    {
+      std::vector<PredictDesc> d;
+      std::vector<int> bl;
+      for (int r = 0; r < R; ++r) {
+        pm_ctx* c = B->ctx[r];
+        if (c->cfg.guess != PM_GUESS_WARM) continue;
+        if (phase_changed[r]) c->n_sol = 0;
+        if (c->n_sol < 1) continue;
+        float w = 0.0f;
+        if (c->n_sol >= 2) {
+          double d0 = c->ah_hist[1] - c->ah_hist[0];
+          w = d0 > 0 ? (float)((c->a_half[k] - c->ah_hist[1]) / d0) : 0.0f;
+        }
+        PredictDesc e{};
+        e.ph = full_view(c, c->phi_h[c->cur], c->lo, c->s);
+        e.pl = full_view(c, c->phi_l[c->cur], c->lo, c->s);
+        e.qh = full_view(c, c->prev_hi, c->lo, c->s);
+        e.ql = full_view(c, c->prev_lo, c->lo, c->s);
+        e.w = w;
+        e.pair = 1;
+        set_dims(e, r, full_grid(c->s));
+        d.push_back(e);
+        bl.push_back(nblocks(full_grid(c->s)));
+      }
+      int g = tab_upload(B, B->t_pred, d, bl);
+      launch_predict_b(B->st, g, (const PredictDesc*)B->t_pred.d_desc, B->t_pred.d_tab);
+    }
+    // 4. solve every realisation to its rtol
+    std::vector<int> it(R, 0);
+    for (int r = 0; r < R; ++r) B->h_active[r] = 1;
+    for (;;) {
+      std::vector<DefectDesc> d;
+      std::vector<int> bl, swapped;
+      for (int r = 0; r < R; ++r) {
+        if (!B->h_active[r]) continue;
+        pm_ctx* c = B->ctx[r];
+        const int lo = c->lo, s = c->s, c0 = c->cur;
+        DefectDesc e{};
+        e.ph = full_view(c, c->phi_h[c0], lo, s);
+        e.pl = full_view(c, c->phi_l[c0], lo, s);
+        e.e = compact_view(c->lu[0], s);
+        e.correct = it[r] > 0;
+        e.qh = full_view(c, c->phi_h[e.correct ? c0 ^ 1 : c0], lo, s);
+        e.ql = full_view(c, c->phi_l[e.correct ? c0 ^ 1 : c0], lo, s);
+        e.fh = full_view(c, c->f_hi, lo, s);
+        e.fl = full_view(c, c->f_lo, lo, s);
+        e.rb = compact_view(c->lb[0], s);
+        e.periodic = c->periodic;
+        e.write_r = 1;
+        e.partial = c->partial;
+        e.counter = c->counter;
+        e.out = B->d_scal + 16 * r + 11;
+        set_dims(e, r, defect_grid(s));
+        d.push_back(e);
+        bl.push_back(nblocks(defect_grid(s)));
+        if (e.correct) c->cur ^= 1;
+      }
+      int g = tab_upload(B, B->t_def, d, bl);
+      launch_defect_b(B->st, g, (const DefectDesc*)B->t_def.d_desc, B->t_def.d_tab, nullptr);
+      pm_status st = batch_sync(B);
+      if (st != PM_OK) return st;
+      int n_act = 0;
+      for (int r = 0; r < R; ++r) {
+        if (!B->h_active[r]) continue;
+        pm_ctx* c = B->ctx[r];
+        double f2 = B->h_scal[16 * r], r2 = B->h_scal[16 * r + 11];
+        double rel = f2 > 0 ? std::sqrt(r2 / f2) : 0.0;
+        if (rel <= c->cfg.rtol || f2 == 0.0) {
+          B->h_active[r] = 0;
+          c->vcycles_last = it[r];
+          c->vcycles_total += it[r];
+          c->resid_last = rel;
+          continue;
+        }
+        if (it[r] >= c->cfg.max_vcycles) {
+          char buf[200];
+          snprintf(buf, sizeof buf,
+                   "realisation %d: relative residual %.3e after %d V-cycles (rtol %.1e)", r,
+                   rel, it[r], c->cfg.rtol);
+          return bfail(B, PM_ENOCONV, buf);
+        }
+        ++n_act;
+      }
+      if (n_act == 0) break;
+      st = batch_vcycle(B);
+      if (st != PM_OK) return st;
+      for (int r = 0; r < R; ++r)
+        if (B->h_active[r]) ++it[r];
+    }
+    for (int r = 0; r < R; ++r) {
+      pm_ctx* c = B->ctx[r];
+      c->ah_hist[0] = c->ah_hist[1];
+      c->ah_hist[1] = c->a_half[k];
+      c->n_sol++;
+    }
+    // 5-6. gather + kick + drift (+ keep flags)
+    bool any_flag = false;
+    std::vector<int> flagged(R, 0);
+    {
+      std::vector<GatherDesc> d;
+      std::vector<int> bl;
+      for (int r = 0; r < R; ++r) {
+        pm_ctx* c = B->ctx[r];
+        if (c->n_active <= 0) continue;
+        const double R1 = c->R[k + 1];
+        const bool do_flag = c->cfg.shrink && c->cfg.bc != PM_BC_PERIODIC && is_open(c, R1);
+        GatherDesc e{};
+        e.pos = c->pos;
+        e.mom = c->mom;
+        e.N = c->n_active;
+        e.ph = c->phi_h[c->cur];
+        e.pl = c->phi_l[c->cur];
+        e.n = c->n;
+        e.lo = c->lo;
+        e.s = c->s;
+        e.periodic = c->periodic;
+        e.kick = (float)(c->a_half[k] * c->dtau[k]);
+        e.c2 = (float)(c->dtau[k] / (2.0 * c->a[k + 1]));
+        e.do_flag = do_flag;
+        if (do_flag) keep_bounds(0.5 * c->n, R1, &e.klo, &e.khi);
+        e.flags = c->flags;
+        e.block_keep = c->block_keep;
+        e.forces = nullptr;
+        e.escaped = c->d_cnt + 1;
+        int nb = gkd_blocks(c->n_active);
+        set_dims(e, r, dim3(nb, 1, 1));
+        d.push_back(e);
+        bl.push_back(nb);
+        flagged[r] = do_flag;
+        any_flag |= do_flag;
+      }
+      int g = tab_upload(B, B->t_gat, d, bl);
+      launch_gather_b(B->st, g, (const GatherDesc*)B->t_gat.d_desc, B->t_gat.d_tab);
+    }
+    // 7. lightcone shrink of the flagged realisations
+    if (any_flag) {
+      std::vector<ScanDesc> ds;
+      std::vector<ScatterDesc> dc;
+      std::vector<int> bs, bc;
+      for (int r = 0; r < R; ++r) {
+        if (!flagged[r]) continue;
+        pm_ctx* c = B->ctx[r];
+        const int nb = gkd_blocks(c->n_active);
+        ScanDesc e{};
+        e.cnt = c->block_keep;
+        e.off = c->keep_off;
+        e.nblk = nb;
+        e.n_keep = B->d_cnt + 4 * r;
+        set_dims(e, r, dim3(1, 1, 1));
+        ds.push_back(e);
+        bs.push_back(1);
+        ScatterDesc f{};
+        f.pos = c->pos;
+        f.mom = c->mom;
+        f.N = c->n_active;
+        f.flags = c->flags;
+        f.keep_off = c->keep_off;
+        f.pos_out = c->pos2;
+        f.mom_out = c->mom2;
+        f.lc_pos = c->lc_pos;
+        f.lc_mom = c->lc_mom;
+        f.lc_base = c->n_lc;
+        f.a_cross = (float)c->a[k + 1];
+        set_dims(f, r, dim3(nb, 1, 1));
+        dc.push_back(f);
+        bc.push_back(nb);
+      }
+      int g = tab_upload(B, B->t_scan, ds, bs);
+      launch_scan_b(B->st, g, (const ScanDesc*)B->t_scan.d_desc, B->t_scan.d_tab);
+      g = tab_upload(B, B->t_scat, dc, bc);
+      launch_scatter_b(B->st, g, (const ScatterDesc*)B->t_scat.d_desc, B->t_scat.d_tab);
+    }
+    pm_status st = batch_sync(B);
+    if (st != PM_OK) return st;
+    for (int r = 0; r < R; ++r) {
+      pm_ctx* c = B->ctx[r];
+      c->particle_steps += c->n_active;
+      if (flagged[r]) {
+        long long keep = (long long)B->h_cnt[4 * r];
+        std::swap(c->pos, c->pos2);
+        std::swap(c->mom, c->mom2);
+        c->n_lc += c->n_active - keep;
+        c->n_active = keep;
+      }
+      c->step++;
+    }
+    int ovf[MAX_REAL];
+    if (cudaMemcpy(ovf, B->d_ovf, sizeof(int) * R, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return bfail(B, PM_ECUDA, "pm_batch_step: reading the overflow flags");
+    for (int r = 0; r < R; ++r)
+      if (ovf[r]) return bfail(B, PM_EOVERFLOW, "deposit: a cell count exceeded 2^62");
+  }
+  return PM_OK;
+}
+
+pm_status pm_batch_stats(pm_batch* B, int32_t r, pm_stats_t* out) {
+  if (!B || r < 0 || r >= B->R) return bfail(B, PM_EINVAL, "pm_batch_stats: bad argument");
+  return pm_stats(B->ctx[r], out);
+}
+
+pm_status pm_batch_get_particles(pm_batch* B, int32_t r, float* pos4, float* mom4,
+                                 int32_t host_mem, int64_t* n_active_out) {
+  if (!B || r < 0 || r >= B->R) return bfail(B, PM_EINVAL, "pm_batch_get_particles");
+  return pm_get_particles(B->ctx[r], pos4, mom4, host_mem, n_active_out);
+}
+
+pm_status pm_batch_get_lightcone(pm_batch* B, int32_t r, float* pos4, float* mom4,
+                                 int32_t host_mem, int64_t* n_out) {
+  if (!B || r < 0 || r >= B->R) return bfail(B, PM_EINVAL, "pm_batch_get_lightcone");
+  return pm_get_lightcone(B->ctx[r], pos4, mom4, host_mem, n_out);
+}
+
+const char* pm_batch_last_error(const pm_batch* B) { return B ? B->err.c_str() : g_err.c_str(); }
+
+void pm_batch_destroy(pm_batch* B) {
+  if (!B) return;
+  if (B->st) cudaStreamSynchronize(B->st);
+  if (B->vgraph) cudaGraphExecDestroy(B->vgraph);
+  for (pm_ctx* c : B->ctx) pm_destroy(c);
+  for (BTab* t : {&B->t_dep, &B->t_src, &B->t_bnd, &B->t_pred, &B->t_def, &B->t_gat,
+                  &B->t_scan, &B->t_scat})
+    tab_free(*t);
+  for (auto& t : B->t_vc) tab_free(t);
+  if (B->d_active) cudaFree(B->d_active);
+  if (B->h_active) cudaFreeHost(B->h_active);
+  if (B->d_scal) cudaFree(B->d_scal);
+  if (B->h_scal) cudaFreeHost(B->h_scal);
+  if (B->d_cnt) cudaFree(B->d_cnt);
+  if (B->h_cnt) cudaFreeHost(B->h_cnt);
+  if (B->d_ovf) cudaFree(B->d_ovf);
+  delete B;
 }
 
 }  // extern "C"

@@ -12,14 +12,14 @@ namespace pm {
 // [lo, lo+s) deposits nothing and is counted as escaped.
 // ---------------------------------------------------------------------------
 template <bool DRIFT>
-__global__ void __launch_bounds__(256) k_drift_deposit(
+__device__ __forceinline__ void d_drift_deposit(const BI& bi, 
     float4* __restrict__ pos, const float4* __restrict__ mom, long long N,
     float c0, int n, int lo, int s, int periodic,
-    unsigned long long* __restrict__ rho, unsigned long long* __restrict__ escaped) {
+    unsigned long long* __restrict__ rho, unsigned long long* __restrict__ escaped){
   const float fn = (float)n;
   unsigned int esc_local = 0;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
-       p += (long long)gridDim.x * blockDim.x) {
+  for (long long p = bi.x * (long long)blockDim.x + threadIdx.x; p < N;
+       p += (long long)bi.gx * blockDim.x) {
     float4 x = pos[p];
     if (DRIFT) {
       float4 v = mom[p];
@@ -82,6 +82,14 @@ __global__ void __launch_bounds__(256) k_drift_deposit(
   }
 }
 
+template <bool DRIFT>
+__global__ void __launch_bounds__(256) k_drift_deposit(
+    float4* __restrict__ pos, const float4* __restrict__ mom, long long N,
+    float c0, int n, int lo, int s, int periodic,
+    unsigned long long* __restrict__ rho, unsigned long long* __restrict__ escaped) {
+  d_drift_deposit<DRIFT>(bi_native(), pos, mom, N, c0, n, lo, s, periodic, rho, escaped);
+}
+
 void launch_drift_deposit(cudaStream_t st, int grid, float4* pos, const float4* mom,
                           long long N, float c0, bool drift, int n, int lo, int s,
                           int periodic, unsigned long long* rho,
@@ -140,11 +148,11 @@ __device__ __forceinline__ __int128 shfl_xor_i128(__int128 v, int o) {
 constexpr int SRC_NV = 10;
 
 template <bool MOMENTS>
-__global__ void __launch_bounds__(256) k_source(
+__device__ __forceinline__ void d_source(const BI& bi, 
     unsigned long long* __restrict__ rho, int n, int lo, int s, Grid fh, Grid fl,
     df invM, df S, int b0, int b1, double* __restrict__ partial_f2,
     __int128* __restrict__ partial_m, unsigned int* counter, double* __restrict__ out,
-    const double* __restrict__ bgm, double invM2_hi, int* __restrict__ overflow) {
+    const double* __restrict__ bgm, double invM2_hi, int* __restrict__ overflow){
   __int128 acc[SRC_NV];
 #pragma unroll
   for (int q = 0; q < SRC_NV; ++q) acc[q] = 0;
@@ -152,21 +160,21 @@ __global__ void __launch_bounds__(256) k_source(
   // block (32, 8) covers an x-y tile; the grid's z dimension strides over
   // planes, ZU planes per round with all loads issued before any use
   constexpr int ZU = 4;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int i = bi.x * blockDim.x + threadIdx.x;
+  const int j = bi.y * blockDim.y + threadIdx.y;
   const bool in_xy = i < s && j < s;
   const int gi = lo + i, gj = lo + j;
   const bool in_xy_bg = gi >= b0 && gi <= b1 && gj >= b0 && gj <= b1;
-  for (int k0 = blockIdx.z; k0 < s && in_xy; k0 += ZU * gridDim.z) {
+  for (int k0 = bi.z; k0 < s && in_xy; k0 += ZU * bi.gz) {
     unsigned long long cnts[ZU];
 #pragma unroll
     for (int u = 0; u < ZU; ++u) {
-      int k = k0 + u * gridDim.z;
+      int k = k0 + u * bi.gz;
       cnts[u] = k < s ? rho[((long long)(lo + k) * n + gj) * n + gi] : 0ull;
     }
 #pragma unroll
     for (int u = 0; u < ZU; ++u) {
-    int k = k0 + u * gridDim.z;
+    int k = k0 + u * bi.gz;
     if (k >= s) break;
     int gk = lo + k;
     unsigned long long cnt = cnts[u];
@@ -200,8 +208,8 @@ __global__ void __launch_bounds__(256) k_source(
   __shared__ double sf[32];
   __shared__ __int128 sm[32 * SRC_NV];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-  const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+  const unsigned bid = bi.x + bi.gx * (bi.y + bi.gy * bi.z);
+  const unsigned nblk = bi.gx * bi.gy * bi.gz;
   int lane = tid & 31, warp = tid >> 5, nw = (blockDim.x * blockDim.y) >> 5;
   float wf = warp_sumf_all(f2);
   if (lane == 0) sf[warp] = (double)wf;
@@ -281,6 +289,15 @@ __global__ void __launch_bounds__(256) k_source(
     }
     *counter = 0u;
   }
+}
+
+template <bool MOMENTS>
+__global__ void __launch_bounds__(256) k_source(
+    unsigned long long* __restrict__ rho, int n, int lo, int s, Grid fh, Grid fl,
+    df invM, df S, int b0, int b1, double* __restrict__ partial_f2,
+    __int128* __restrict__ partial_m, unsigned int* counter, double* __restrict__ out,
+    const double* __restrict__ bgm, double invM2_hi, int* __restrict__ overflow) {
+  d_source<MOMENTS>(bi_native(), rho, n, lo, s, fh, fl, invM, S, b0, b1, partial_f2, partial_m, counter, out, bgm, invM2_hi, overflow);
 }
 
 dim3 source_grid(int s) {
@@ -375,13 +392,13 @@ void launch_source_f64(cudaStream_t st, int grid, const double* delta, int n, Gr
 // Q_ab = 3 S_ab - delta_ab tr(S).  mom = (q0, dx, dy, dz, Sxx, Syy, Szz, Sxy,
 // Sxz, Syz).  Written to the hi/lo planes (lo = 0 when want_lo == 0).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_boundary(Grid ph, Grid pl, int n, int lo,
+__device__ __forceinline__ void d_boundary(const BI& bi, Grid ph, Grid pl, int n, int lo,
                                                   const double* __restrict__ mom,
-                                                  double S, int want_lo) {
+                                                  double S, int want_lo){
   const int s = ph.s;
   const int P = s + 2;
   const long long per_face = (long long)P * P;
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long t = bi.x * (long long)blockDim.x + threadIdx.x;
   if (t >= 6 * per_face) return;
   int face = (int)(t / per_face);
   int rem = (int)(t % per_face);
@@ -412,12 +429,71 @@ __global__ void __launch_bounds__(256) k_boundary(Grid ph, Grid pl, int n, int l
   pl.base[gi] = want_lo ? (float)(phi - (double)hi) : 0.0f;
 }
 
+__global__ void __launch_bounds__(256) k_boundary(Grid ph, Grid pl, int n, int lo,
+                                                  const double* __restrict__ mom,
+                                                  double S, int want_lo) {
+  d_boundary(bi_native(), ph, pl, n, lo, mom, S, want_lo);
+}
+
 void launch_boundary(cudaStream_t st, Grid ph, Grid pl, int n, int lo, const double* mom,
                      double S, bool want_lo) {
   long long tot = 6LL * (ph.s + 2) * (ph.s + 2);
   int grid = (int)((tot + 255) / 256);
   k_boundary<<<grid, 256, 0, st>>>(ph, pl, n, lo, mom, S, want_lo ? 1 : 0);
   note_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Batched forms.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) kb_deposit(const DepositDesc* d, const BTable* t) {
+  int q;
+  BI bi;
+  if (!batch_map(d, t, (const int*)nullptr, q, bi)) return;
+  const DepositDesc& e = d[q];
+  d_drift_deposit<true>(bi, e.pos, e.mom, e.N, e.c0, e.n, e.lo, e.s, e.periodic, e.rho,
+                        e.escaped);
+}
+__global__ void __launch_bounds__(256) kb_source(const SourceDesc* d, const BTable* t) {
+  int q;
+  BI bi;
+  if (!batch_map(d, t, (const int*)nullptr, q, bi)) return;
+  const SourceDesc& e = d[q];
+  if (e.moments)
+    d_source<true>(bi, e.rho, e.n, e.lo, e.s, e.fh, e.fl, e.invM, e.S, e.b0, e.b1, e.partial_f2,
+                   (__int128*)e.partial_m, e.counter, e.out, e.bgm, e.invM_d, e.overflow);
+  else
+    d_source<false>(bi, e.rho, e.n, e.lo, e.s, e.fh, e.fl, e.invM, e.S, e.b0, e.b1,
+                    e.partial_f2, (__int128*)e.partial_m, e.counter, e.out, e.bgm, e.invM_d,
+                    e.overflow);
+}
+__global__ void __launch_bounds__(256) kb_boundary(const BoundaryDesc* d, const BTable* t) {
+  int q;
+  BI bi;
+  if (!batch_map(d, t, (const int*)nullptr, q, bi)) return;
+  const BoundaryDesc& e = d[q];
+  d_boundary(bi, e.ph, e.pl, e.n, e.lo, e.mom, e.S, e.want_lo);
+}
+
+void launch_deposit_b(cudaStream_t st, int grid, const DepositDesc* d, const BTable* t) {
+  if (grid <= 0) return;
+  kb_deposit<<<grid, 256, 0, st>>>(d, t);
+  note_launch();
+}
+void launch_source_b(cudaStream_t st, int grid, const SourceDesc* d, const BTable* t) {
+  if (grid <= 0) return;
+  kb_source<<<grid, dim3(32, 8), 0, st>>>(d, t);
+  note_launch();
+}
+void launch_boundary_b(cudaStream_t st, int grid, const BoundaryDesc* d, const BTable* t) {
+  if (grid <= 0) return;
+  kb_boundary<<<grid, 256, 0, st>>>(d, t);
+  note_launch();
+}
+int boundary_blocks(int s) { return (int)((6LL * (s + 2) * (s + 2) + 255) / 256); }
+int deposit_blocks(long long N) {
+  long long b = (N + 1023) / 1024 * 4;
+  return (int)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
 }
 
 }  // namespace pm

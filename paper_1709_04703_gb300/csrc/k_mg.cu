@@ -27,39 +27,65 @@ __device__ __forceinline__ float bnd_diag(int i, int j, int k, int s, float gam)
 // zero_start (red only): the iterate is known to be zero, so the red cells
 // take (-h^2 b)/diag without reading u; the black sweep after it reads only
 // red neighbours, so u needs no clearing before a V-cycle.
+__device__ __forceinline__ void d_rbgs(const BI& bi, Grid u, Grid b, float h2, int color,
+                                              int periodic, float gam, int zero_start){
+  // each thread updates the two cells of its colour at i0 and i0 + 2
+  // (independent loads in flight, the shared x-neighbour loaded once)
+  const int s = u.s;
+  int t = bi.x * blockDim.x + threadIdx.x;
+  int j = bi.y * blockDim.y + threadIdx.y;
+  int k = bi.z;
+  const int half = s >> 1;
+  if (2 * t >= half || j >= s) return;
+  const int i0 = 4 * t + ((j + k + color) & 1);
+  const bool two = 2 * t + 1 < half;
+  const int ym = (wrap_m(j, s, periodic) - j) * u.sy, yp = (wrap_p(j, s, periodic) - j) * u.sy;
+  const int zm = (wrap_m(k, s, periodic) - k) * u.sz, zp = (wrap_p(k, s, periodic) - k) * u.sz;
+  const bool simple = periodic || gam == 0.0f;
+  const int c0 = gidx(u, i0, j, k);
+  const int bc0 = gidx(b, i0, j, k);
+  float* p0 = u.base + c0;
+  const float* bb = b.base + bc0;
+  float b0v = bb[0], b1v = two ? bb[2] : 0.0f;
+  float s0 = 0.0f, s1 = 0.0f;
+  if (!zero_start) {
+    const int xm = wrap_m(i0, s, periodic) - i0;
+    const int xp = wrap_p(i0, s, periodic) - i0;  // 1 unless i0 = s - 1 (then no i0 + 2)
+    float xmid = p0[xp];  // right neighbour of i0, left of i0 + 2
+    s0 = (p0[xm] + xmid) + (p0[ym] + p0[yp]) + (p0[zm] + p0[zp]);
+    if (two) {
+      const int i1 = i0 + 2;
+      const int xp1 = wrap_p(i1, s, periodic) - i1;
+      float* p1 = p0 + 2;
+      s1 = (xmid + p1[xp1]) + (p1[ym] + p1[yp]) + (p1[zm] + p1[zp]);
+    }
+  }
+  if (simple) {
+    p0[0] = (s0 - h2 * b0v) * (1.0f / 6.0f);
+    if (two) p0[2] = (s1 - h2 * b1v) * (1.0f / 6.0f);
+  } else {
+    p0[0] = (s0 - h2 * b0v) / bnd_diag(i0, j, k, s, gam);
+    if (two) p0[2] = (s1 - h2 * b1v) / bnd_diag(i0 + 2, j, k, s, gam);
+  }
+}
+
 __global__ void __launch_bounds__(256) k_rbgs(Grid u, Grid b, float h2, int color,
                                               int periodic, float gam, int zero_start) {
-  const int s = u.s;
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y * blockDim.y + threadIdx.y;
-  int k = blockIdx.z;
-  if (t >= (s >> 1) || j >= s) return;
-  int i = 2 * t + ((j + k + color) & 1);
-  int c = gidx(u, i, j, k);
-  int xm = wrap_m(i, s, periodic) - i, xp = wrap_p(i, s, periodic) - i;
-  int ym = (wrap_m(j, s, periodic) - j) * u.sy, yp = (wrap_p(j, s, periodic) - j) * u.sy;
-  int zm = (wrap_m(k, s, periodic) - k) * u.sz, zp = (wrap_p(k, s, periodic) - k) * u.sz;
-  const float* p = u.base + c;
-  float sum = zero_start ? 0.0f : (p[xm] + p[xp]) + (p[ym] + p[yp]) + (p[zm] + p[zp]);
-  float bv = b.base[gidx(b, i, j, k)];
-  if (periodic || gam == 0.0f)
-    u.base[c] = (sum - h2 * bv) * (1.0f / 6.0f);
-  else
-    u.base[c] = (sum - h2 * bv) / bnd_diag(i, j, k, s, gam);
+  d_rbgs(bi_native(), u, b, h2, color, periodic, gam, zero_start);
 }
 
 // ---------------------------------------------------------------------------
 // Residual r = b - (sum_nb u - 6u)/h^2 on the 8 children of each coarse cell,
 // averaged into the coarse right-hand side; the coarse unknown is zeroed.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_resid_restrict(Grid u, Grid b, float inv_h2,
+__device__ __forceinline__ void d_resid_restrict(const BI& bi, Grid u, Grid b, float inv_h2,
                                                         Grid uc, Grid bc, int periodic,
-                                                        float gam) {
+                                                        float gam){
   const int s = u.s;
   const int sc = uc.s;
-  int I = blockIdx.x * blockDim.x + threadIdx.x;
-  int J = blockIdx.y * blockDim.y + threadIdx.y;
-  int K = blockIdx.z;
+  int I = bi.x * blockDim.x + threadIdx.x;
+  int J = bi.y * blockDim.y + threadIdx.y;
+  int K = bi.z;
   if (I >= sc || J >= sc) return;
   float acc = 0.f;
 #pragma unroll
@@ -83,18 +109,24 @@ __global__ void __launch_bounds__(256) k_resid_restrict(Grid u, Grid b, float in
   uc.base[cc] = 0.0f;
 }
 
+__global__ void __launch_bounds__(256) k_resid_restrict(Grid u, Grid b, float inv_h2,
+                                                        Grid uc, Grid bc, int periodic,
+                                                        float gam) {
+  d_resid_restrict(bi_native(), u, b, inv_h2, uc, bc, periodic, gam);
+}
+
 // ---------------------------------------------------------------------------
 // u += P uc: trilinear interpolation of the cell-centred coarse correction
 // (weights 3/4 on the parent, 1/4 on the next coarse cell per axis).  Coarse
 // ghosts are zero (open) or wrap (periodic).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_prolong(Grid uc, Grid u, int periodic,
-                                                 float gam_c) {
+__device__ __forceinline__ void d_prolong(const BI& bi, Grid uc, Grid u, int periodic,
+                                                 float gam_c){
   const int s = u.s;
   const int sc = uc.s;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y * blockDim.y + threadIdx.y;
-  int k = blockIdx.z;
+  int i = bi.x * blockDim.x + threadIdx.x;
+  int j = bi.y * blockDim.y + threadIdx.y;
+  int k = bi.z;
   if (i >= s || j >= s) return;
   int I = i >> 1, J = j >> 1, K = k >> 1;
   int I2 = (i & 1) ? I + 1 : I - 1;
@@ -121,6 +153,11 @@ __global__ void __launch_bounds__(256) k_prolong(Grid uc, Grid u, int periodic,
   float a2 = 0.75f * c001 + 0.25f * c101, a3 = 0.75f * c011 + 0.25f * c111;
   float b0 = 0.75f * a0 + 0.25f * a1, b1 = 0.75f * a2 + 0.25f * a3;
   u.base[gidx(u, i, j, k)] += 0.75f * b0 + 0.25f * b1;
+}
+
+__global__ void __launch_bounds__(256) k_prolong(Grid uc, Grid u, int periodic,
+                                                 float gam_c) {
+  d_prolong(bi_native(), uc, u, periodic, gam_c);
 }
 
 // ---------------------------------------------------------------------------
@@ -342,7 +379,9 @@ void launch_coarse_mg(cudaStream_t st, Grid u, Grid b, int level, int periodic,
   note_launch();
 }
 
-static inline dim3 grid_half(int s) { return dim3((unsigned)((s / 2 + 31) / 32), (unsigned)((s + 7) / 8), (unsigned)s); }
+static inline dim3 grid_half(int s) {
+  return dim3((unsigned)(((s / 2 + 1) / 2 + 31) / 32), (unsigned)((s + 7) / 8), (unsigned)s);
+}
 static inline dim3 grid_full(int s) { return dim3((unsigned)((s + 31) / 32), (unsigned)((s + 7) / 8), (unsigned)s); }
 
 void launch_rbgs(cudaStream_t st, Grid u, Grid b, float h2, int color, int periodic,
@@ -376,15 +415,15 @@ void launch_prolong(cudaStream_t st, Grid uc, Grid u, int periodic, float gam_c)
 // the fly at all 7 stencil points; Phi' is written out of place to (qh, ql)
 // and the residual is that of Phi'.
 template <bool CORRECT>
-__global__ void __launch_bounds__(256) k_defect(Grid ph, Grid pl, Grid e, Grid qh, Grid ql,
+__device__ __forceinline__ void d_defect(const BI& bi, Grid ph, Grid pl, Grid e, Grid qh, Grid ql,
                                                 Grid fh, Grid fl, Grid rb, int periodic,
                                                 int write_r, double* __restrict__ partial,
-                                                unsigned int* counter, double* __restrict__ out) {
+                                                unsigned int* counter, double* __restrict__ out){
   const int s = ph.s;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int i = bi.x * blockDim.x + threadIdx.x;
+  int j = bi.y * blockDim.y + threadIdx.y;
   float r2 = 0.f;
-  for (int k = blockIdx.z; k < s && i < s && j < s; k += gridDim.z) {
+  for (int k = bi.z; k < s && i < s && j < s; k += bi.gz) {
     int c = gidx(ph, i, j, k);
     int xm = wrap_m(i, s, periodic) - i, xp = wrap_p(i, s, periodic) - i;
     int ym = wrap_m(j, s, periodic) - j, yp = wrap_p(j, s, periodic) - j;
@@ -393,17 +432,19 @@ __global__ void __launch_bounds__(256) k_defect(Grid ph, Grid pl, Grid e, Grid q
     float H[7], Lo[7];
     const float* h = ph.base + c;
     const float* l = pl.base + c;
+    // read-only loads (__ldg): lets the next plane's loads overlap this
+    // plane's stores, which go to other buffers
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
-      H[q] = h[off[q]];
-      Lo[q] = l[off[q]];
+      H[q] = __ldg(h + off[q]);
+      Lo[q] = __ldg(l + off[q]);
     }
     if (CORRECT) {
       const float* ec = e.base + gidx(e, i, j, k);
       const int eoff[7] = {0, xm, xp, ym * e.sy, yp * e.sy, zm * e.sz, zp * e.sz};
 #pragma unroll
       for (int q = 0; q < 7; ++q) {
-        df t = two_sum(H[q], ec[eoff[q]]);
+        df t = two_sum(H[q], __ldg(ec + eoff[q]));
         H[q] = t.hi;
         Lo[q] = __fadd_rn(Lo[q], t.lo);
       }
@@ -415,8 +456,8 @@ __global__ void __launch_bounds__(256) k_defect(Grid ph, Grid pl, Grid e, Grid q
     int fc = gidx(fh, i, j, k);
     // r = f - sum_nb + 6 phi: TwoSum cascade on the hi parts, rounding errors
     // and lo parts in a float compensation term
-    float sacc = fh.base[fc];
-    float comp = fl.base[fc];
+    float sacc = __ldg(fh.base + fc);
+    float comp = __ldg(fl.base + fc);
     df t;
 #pragma unroll
     for (int q = 1; q < 7; ++q) {
@@ -438,8 +479,8 @@ __global__ void __launch_bounds__(256) k_defect(Grid ph, Grid pl, Grid e, Grid q
   int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
   if (lane == 0) sm[warp] = (double)vf;
   __syncthreads();
-  unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
-  unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  unsigned nblk = bi.gx * bi.gy * bi.gz;
+  unsigned bid = bi.x + bi.gx * (bi.y + bi.gy * bi.z);
   __shared__ bool last;
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     double tb = 0.0;
@@ -466,6 +507,14 @@ __global__ void __launch_bounds__(256) k_defect(Grid ph, Grid pl, Grid e, Grid q
     *out = tt;
     *counter = 0u;
   }
+}
+
+template <bool CORRECT>
+__global__ void __launch_bounds__(256) k_defect(Grid ph, Grid pl, Grid e, Grid qh, Grid ql,
+                                                Grid fh, Grid fl, Grid rb, int periodic,
+                                                int write_r, double* __restrict__ partial,
+                                                unsigned int* counter, double* __restrict__ out) {
+  d_defect<CORRECT>(bi_native(), ph, pl, e, qh, ql, fh, fl, rb, periodic, write_r, partial, counter, out);
 }
 
 static inline dim3 grid_defect(int s) {
@@ -509,12 +558,12 @@ void launch_correct(cudaStream_t st, Grid ph, Grid pl, Grid e) {
 // Warm start extrapolated in time: Phi <- Phi + w (Phi - Phi_prev),
 // Phi_prev <- old Phi (interior only; the ghost layer keeps its boundary
 // values).  Double-float when `pair`, FP32 hi only otherwise.
-__global__ void __launch_bounds__(256) k_predict(Grid ph, Grid pl, Grid qh, Grid ql, float w,
-                                                 int pair) {
+__device__ __forceinline__ void d_predict(const BI& bi, Grid ph, Grid pl, Grid qh, Grid ql, float w,
+                                                 int pair){
   const int s = ph.s;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y * blockDim.y + threadIdx.y;
-  int k = blockIdx.z;
+  int i = bi.x * blockDim.x + threadIdx.x;
+  int j = bi.y * blockDim.y + threadIdx.y;
+  int k = bi.z;
   if (i >= s || j >= s) return;
   int c = gidx(ph, i, j, k);
   if (pair) {
@@ -530,6 +579,11 @@ __global__ void __launch_bounds__(256) k_predict(Grid ph, Grid pl, Grid qh, Grid
     qh.base[c] = cur;
     ph.base[c] = cur + w * (cur - prev);
   }
+}
+
+__global__ void __launch_bounds__(256) k_predict(Grid ph, Grid pl, Grid qh, Grid ql, float w,
+                                                 int pair) {
+  d_predict(bi_native(), ph, pl, qh, ql, w, pair);
 }
 
 void launch_predict(cudaStream_t st, Grid ph, Grid pl, Grid qh, Grid ql, float w, bool pair) {
@@ -615,5 +669,112 @@ void launch_sum_phi(cudaStream_t st, Grid ph, Grid pl, double* partial, unsigned
   k_sum_phi<<<grid_defect(ph.s), dim3(32, 8), 0, st>>>(ph, pl, partial, counter, out);
   note_launch();
 }
+
+// ---------------------------------------------------------------------------
+// Batched forms (one launch over the member realisations of a table).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) kb_rbgs(const RbgsDesc* d, const BTable* t,
+                                               const int* active) {
+  int q;
+  BI bi;
+  if (!batch_map(d, t, active, q, bi)) return;
+  const RbgsDesc& e = d[q];
+  d_rbgs(bi, e.u, e.b, e.h2, e.color, e.periodic, e.gam, e.zero_start);
+}
+__global__ void __launch_bounds__(256) kb_restrict(const RestrictDesc* d, const BTable* t,
+                                                   const int* active) {
+  int q;
+  BI bi;
+  if (!batch_map(d, t, active, q, bi)) return;
+  const RestrictDesc& e = d[q];
+  d_resid_restrict(bi, e.u, e.b, e.inv_h2, e.uc, e.bc, e.periodic, e.gam);
+}
+__global__ void __launch_bounds__(256) kb_prolong(const ProlongDesc* d, const BTable* t,
+                                                  const int* active) {
+  int q;
+  BI bi;
+  if (!batch_map(d, t, active, q, bi)) return;
+  const ProlongDesc& e = d[q];
+  d_prolong(bi, e.uc, e.u, e.periodic, e.gam_c);
+}
+__global__ void __launch_bounds__(1024) kb_coarse_mg(const CmgDesc* d, const BTable* t,
+                                                     const int* active) {
+  int q;
+  BI bi;
+  if (!batch_map(d, t, active, q, bi)) return;
+  const CmgDesc& e = d[q];
+  __shared__ float sm[CMG_SMEM_FLOATS];
+  __shared__ float red[32];
+  CmgArgs a{e.periodic, e.level, e.sweeps};
+  switch (e.u.s) {
+    case 16: c_run<16>(e.u, e.b, sm, a, red, e.zero_top); break;
+    case 12: c_run<12>(e.u, e.b, sm, a, red, e.zero_top); break;
+    case 8: c_run<8>(e.u, e.b, sm, a, red, e.zero_top); break;
+    case 6: c_run<6>(e.u, e.b, sm, a, red, e.zero_top); break;
+    case 4: c_run<4>(e.u, e.b, sm, a, red, e.zero_top); break;
+    case 3: c_run<3>(e.u, e.b, sm, a, red, e.zero_top); break;
+    default: break;
+  }
+}
+__global__ void __launch_bounds__(256) kb_defect(const DefectDesc* d, const BTable* t,
+                                                 const int* active) {
+  int q;
+  BI bi;
+  if (!batch_map(d, t, active, q, bi)) return;
+  const DefectDesc& e = d[q];
+  if (e.correct)
+    d_defect<true>(bi, e.ph, e.pl, e.e, e.qh, e.ql, e.fh, e.fl, e.rb, e.periodic, e.write_r,
+                   e.partial, e.counter, e.out);
+  else
+    d_defect<false>(bi, e.ph, e.pl, e.e, e.qh, e.ql, e.fh, e.fl, e.rb, e.periodic, e.write_r,
+                    e.partial, e.counter, e.out);
+}
+__global__ void __launch_bounds__(256) kb_predict(const PredictDesc* d, const BTable* t) {
+  int q;
+  BI bi;
+  if (!batch_map(d, t, (const int*)nullptr, q, bi)) return;
+  const PredictDesc& e = d[q];
+  d_predict(bi, e.ph, e.pl, e.qh, e.ql, e.w, e.pair);
+}
+
+void launch_rbgs_b(cudaStream_t st, int grid, const RbgsDesc* d, const BTable* t,
+                   const int* active) {
+  if (grid <= 0) return;
+  kb_rbgs<<<grid, dim3(32, 8), 0, st>>>(d, t, active);
+  note_launch();
+}
+void launch_restrict_b(cudaStream_t st, int grid, const RestrictDesc* d, const BTable* t,
+                       const int* active) {
+  if (grid <= 0) return;
+  kb_restrict<<<grid, dim3(32, 8), 0, st>>>(d, t, active);
+  note_launch();
+}
+void launch_prolong_b(cudaStream_t st, int grid, const ProlongDesc* d, const BTable* t,
+                      const int* active) {
+  if (grid <= 0) return;
+  kb_prolong<<<grid, dim3(32, 8), 0, st>>>(d, t, active);
+  note_launch();
+}
+void launch_coarse_mg_b(cudaStream_t st, int grid, const CmgDesc* d, const BTable* t,
+                        const int* active) {
+  if (grid <= 0) return;
+  kb_coarse_mg<<<grid, 1024, 0, st>>>(d, t, active);
+  note_launch();
+}
+void launch_defect_b(cudaStream_t st, int grid, const DefectDesc* d, const BTable* t,
+                     const int* active) {
+  if (grid <= 0) return;
+  kb_defect<<<grid, dim3(32, 8), 0, st>>>(d, t, active);
+  note_launch();
+}
+void launch_predict_b(cudaStream_t st, int grid, const PredictDesc* d, const BTable* t) {
+  if (grid <= 0) return;
+  kb_predict<<<grid, dim3(32, 8), 0, st>>>(d, t);
+  note_launch();
+}
+
+dim3 rbgs_grid(int s) { return grid_half(s); }
+dim3 full_grid(int s) { return grid_full(s); }
+dim3 defect_grid(int s) { return grid_defect(s); }
 
 }  // namespace pm

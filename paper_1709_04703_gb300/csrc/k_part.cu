@@ -19,15 +19,15 @@ constexpr int KCHUNK = KT * KITEMS;
 // and keep = x inside [klo, khi]^3 (exact float bounds of |x - c| <= R).
 // Block b covers particles [b*KCHUNK, (b+1)*KCHUNK) and writes its keep count.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(KT) k_gather_kick_drift(
+__device__ __forceinline__ void d_gather_kick_drift(const BI& bi, 
     float4* __restrict__ pos, float4* __restrict__ mom, long long N,
     const float* __restrict__ ph, const float* __restrict__ pl, int n, int lo, int s,
     int periodic, float kick, float c2, int do_flag, float klo, float khi,
     unsigned char* __restrict__ flags, unsigned int* __restrict__ block_keep,
-    float4* __restrict__ forces, unsigned long long* __restrict__ escaped) {
+    float4* __restrict__ forces, unsigned long long* __restrict__ escaped){
   const int P = n + 2;
   const float fn = (float)n;
-  const long long base = (long long)blockIdx.x * KCHUNK;
+  const long long base = (long long)bi.x * KCHUNK;
   unsigned int keep_count = 0, esc = 0;
 #pragma unroll 1
   for (int it = 0; it < KITEMS; ++it) {
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(KT) k_gather_kick_drift(
     if (threadIdx.x == 0) {
       unsigned int t = 0;
       for (int q = 0; q < KT / 32; ++q) t += sk[q];
-      block_keep[blockIdx.x] = t;
+      block_keep[bi.x] = t;
     }
   }
   {
@@ -186,6 +186,15 @@ __global__ void __launch_bounds__(KT) k_gather_kick_drift(
     for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
     if ((threadIdx.x & 31) == 0 && w) atomicAdd(escaped, (unsigned long long)w);
   }
+}
+
+__global__ void __launch_bounds__(KT) k_gather_kick_drift(
+    float4* __restrict__ pos, float4* __restrict__ mom, long long N,
+    const float* __restrict__ ph, const float* __restrict__ pl, int n, int lo, int s,
+    int periodic, float kick, float c2, int do_flag, float klo, float khi,
+    unsigned char* __restrict__ flags, unsigned int* __restrict__ block_keep,
+    float4* __restrict__ forces, unsigned long long* __restrict__ escaped) {
+  d_gather_kick_drift(bi_native(), pos, mom, N, ph, pl, n, lo, s, periodic, kick, c2, do_flag, klo, khi, flags, block_keep, forces, escaped);
 }
 
 int gkd_blocks(long long N) { return (int)((N + KCHUNK - 1) / KCHUNK); }
@@ -243,10 +252,10 @@ void launch_flag(cudaStream_t st, const float4* pos, long long N, float klo, flo
 // Exclusive scan of the per-block keep counts (one CTA; nblk <= 2^24 at
 // 1024 threads x 16k items), total written to *n_keep.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_scan_blocks(const unsigned int* __restrict__ cnt,
+__device__ __forceinline__ void d_scan_blocks(const BI& bi, const unsigned int* __restrict__ cnt,
                                                       unsigned long long* __restrict__ off,
                                                       int nblk,
-                                                      unsigned long long* __restrict__ n_keep) {
+                                                      unsigned long long* __restrict__ n_keep){
   __shared__ unsigned long long part[1024];
   const int tid = threadIdx.x;
   const int per = (nblk + 1023) / 1024;
@@ -276,6 +285,13 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(const unsigned int* __rest
   if (tid == 1023) *n_keep = part[1023];
 }
 
+__global__ void __launch_bounds__(1024) k_scan_blocks(const unsigned int* __restrict__ cnt,
+                                                      unsigned long long* __restrict__ off,
+                                                      int nblk,
+                                                      unsigned long long* __restrict__ n_keep) {
+  d_scan_blocks(bi_native(), cnt, off, nblk, n_keep);
+}
+
 void launch_scan_blocks(cudaStream_t st, const unsigned int* cnt, unsigned long long* off,
                         int nblk, unsigned long long* n_keep) {
   k_scan_blocks<<<1, 1024, 0, st>>>(cnt, off, nblk, n_keep);
@@ -287,15 +303,15 @@ void launch_scan_blocks(cudaStream_t st, const unsigned int* cnt, unsigned long 
 // lightcone at lc_base + (b*KCHUNK - keep_off[b]) + rank, both in index order.
 // Leavers get mom.w = a_cross.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(KT) k_scatter(
+__device__ __forceinline__ void d_scatter(const BI& bi, 
     const float4* __restrict__ pos, const float4* __restrict__ mom, long long N,
     const unsigned char* __restrict__ flags, const unsigned long long* __restrict__ keep_off,
     float4* __restrict__ pos_out, float4* __restrict__ mom_out, float4* __restrict__ lc_pos,
-    float4* __restrict__ lc_mom, long long lc_base, float a_cross) {
+    float4* __restrict__ lc_mom, long long lc_base, float a_cross){
   __shared__ unsigned int wk[KT / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long base = (long long)blockIdx.x * KCHUNK;
-  unsigned long long keep_run = keep_off[blockIdx.x];
+  const long long base = (long long)bi.x * KCHUNK;
+  unsigned long long keep_run = keep_off[bi.x];
   unsigned long long leave_run = (unsigned long long)base - keep_run;
   for (int it = 0; it < KITEMS; ++it) {
     long long p = base + it * KT + threadIdx.x;
@@ -337,6 +353,14 @@ __global__ void __launch_bounds__(KT) k_scatter(
   }
 }
 
+__global__ void __launch_bounds__(KT) k_scatter(
+    const float4* __restrict__ pos, const float4* __restrict__ mom, long long N,
+    const unsigned char* __restrict__ flags, const unsigned long long* __restrict__ keep_off,
+    float4* __restrict__ pos_out, float4* __restrict__ mom_out, float4* __restrict__ lc_pos,
+    float4* __restrict__ lc_mom, long long lc_base, float a_cross) {
+  d_scatter(bi_native(), pos, mom, N, flags, keep_off, pos_out, mom_out, lc_pos, lc_mom, lc_base, a_cross);
+}
+
 void launch_scatter(cudaStream_t st, const float4* pos, const float4* mom, long long N,
                     const unsigned char* flags, const unsigned long long* keep_off,
                     float4* pos_out, float4* mom_out, float4* lc_pos, float4* lc_mom,
@@ -344,6 +368,49 @@ void launch_scatter(cudaStream_t st, const float4* pos, const float4* mom, long 
   if (N <= 0) return;
   k_scatter<<<gkd_blocks(N), KT, 0, st>>>(pos, mom, N, flags, keep_off, pos_out, mom_out,
                                           lc_pos, lc_mom, lc_base, a_cross);
+  note_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Batched forms.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(KT) kb_gather(const GatherDesc* d, const BTable* t) {
+  int q;
+  BI bi;
+  if (!batch_map(d, t, (const int*)nullptr, q, bi)) return;
+  const GatherDesc& e = d[q];
+  d_gather_kick_drift(bi, e.pos, e.mom, e.N, e.ph, e.pl, e.n, e.lo, e.s, e.periodic, e.kick,
+                      e.c2, e.do_flag, e.klo, e.khi, e.flags, e.block_keep, e.forces, e.escaped);
+}
+__global__ void __launch_bounds__(1024) kb_scan(const ScanDesc* d, const BTable* t) {
+  int q;
+  BI bi;
+  if (!batch_map(d, t, (const int*)nullptr, q, bi)) return;
+  const ScanDesc& e = d[q];
+  d_scan_blocks(bi, e.cnt, e.off, e.nblk, e.n_keep);
+}
+__global__ void __launch_bounds__(KT) kb_scatter(const ScatterDesc* d, const BTable* t) {
+  int q;
+  BI bi;
+  if (!batch_map(d, t, (const int*)nullptr, q, bi)) return;
+  const ScatterDesc& e = d[q];
+  d_scatter(bi, e.pos, e.mom, e.N, e.flags, e.keep_off, e.pos_out, e.mom_out, e.lc_pos,
+            e.lc_mom, e.lc_base, e.a_cross);
+}
+
+void launch_gather_b(cudaStream_t st, int grid, const GatherDesc* d, const BTable* t) {
+  if (grid <= 0) return;
+  kb_gather<<<grid, KT, 0, st>>>(d, t);
+  note_launch();
+}
+void launch_scan_b(cudaStream_t st, int grid, const ScanDesc* d, const BTable* t) {
+  if (grid <= 0) return;
+  kb_scan<<<grid, 1024, 0, st>>>(d, t);
+  note_launch();
+}
+void launch_scatter_b(cudaStream_t st, int grid, const ScatterDesc* d, const BTable* t) {
+  if (grid <= 0) return;
+  kb_scatter<<<grid, KT, 0, st>>>(d, t);
   note_launch();
 }
 

@@ -22,6 +22,16 @@ __host__ __device__ inline int gidx(const Grid& g, int i, int j, int k) {
   return i + j * g.sy + k * g.sz;
 }
 
+// Block coordinates of one launch: the native blockIdx / gridDim, or those of
+// a realisation's share of a batched launch.
+struct BI {
+  int x, y, z, gx, gy, gz;
+};
+__device__ __forceinline__ BI bi_native() {
+  return BI{(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z,
+            (int)gridDim.x, (int)gridDim.y, (int)gridDim.z};
+}
+
 // Neighbour index along one axis: wraps when periodic, else may reach the
 // ghost at -1 / s.
 __device__ __forceinline__ int wrap_m(int i, int s, int periodic) {
@@ -129,6 +139,46 @@ __device__ inline void block_sum(double (&v)[NV], double* smem /* 32*NV */) {
     }
   }
   __syncthreads();
+}
+
+}  // namespace pm
+
+namespace pm {
+
+// ---------------------------------------------------------------------------
+// Batched launches: one launch covers the blocks of several realisations.
+// A table in device memory lists the member realisations' cumulative block
+// counts; block b of the launch belongs to member q with off[q] <= b <
+// off[q+1], and becomes block b - off[q] of that member's own grid (gx, gy,
+// gz in its descriptor).  Blocks past off[m] and blocks of realisations
+// whose `active` flag is 0 return at once, so a graph captured with the
+// largest grid stays valid while the members' grids shrink.
+// ---------------------------------------------------------------------------
+constexpr int MAX_REAL = 64;
+constexpr int MAX_MEMBERS = 2 * MAX_REAL;  // a realisation may appear twice in a table
+
+struct BTable {
+  int m;                       // members
+  int off[MAX_MEMBERS + 1];    // cumulative block counts
+};
+
+template <class D>
+__device__ __forceinline__ bool batch_map(const D* d, const BTable* t, const int* active, int& q,
+                                          BI& bi) {
+  const int b = (int)blockIdx.x;
+  const int m = t->m;
+  if (m <= 0 || b >= t->off[m]) return false;
+  int lo = 0, hi = m - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (t->off[mid] <= b) lo = mid; else hi = mid - 1;
+  }
+  q = lo;
+  const D& e = d[lo];
+  if (active && !active[e.r]) return false;
+  const int lb = b - t->off[lo];
+  bi = BI{lb % e.gx, (lb / e.gx) % e.gy, lb / (e.gx * e.gy), e.gx, e.gy, e.gz};
+  return true;
 }
 
 }  // namespace pm

@@ -74,3 +74,141 @@ void launch_pk_bin(cudaStream_t st, const float2* dk, int n, double box, double 
                    int n_bins, double* acc);
 
 }  // namespace pm
+
+namespace pm {
+
+// ---------------------------------------------------------------------------
+// Descriptors of batched launches (one entry per member realisation r; the
+// fields are the arguments of the single-realisation kernel of that name,
+// plus the member's grid dimensions).
+// ---------------------------------------------------------------------------
+struct RbgsDesc {
+  Grid u, b;
+  float h2, gam;
+  int color, periodic, zero_start;
+  int r, gx, gy, gz;
+};
+struct RestrictDesc {
+  Grid u, b, uc, bc;
+  float inv_h2, gam;
+  int periodic;
+  int r, gx, gy, gz;
+};
+struct ProlongDesc {
+  Grid uc, u;
+  float gam_c;
+  int periodic;
+  int r, gx, gy, gz;
+};
+struct CmgDesc {
+  Grid u, b;
+  int level, periodic, sweeps, zero_top;
+  int r, gx, gy, gz;
+};
+struct DefectDesc {
+  Grid ph, pl, e, qh, ql, fh, fl, rb;
+  int periodic, write_r, correct;
+  double* partial;
+  unsigned int* counter;
+  double* out;
+  int r, gx, gy, gz;
+};
+struct PredictDesc {
+  Grid ph, pl, qh, ql;
+  float w;
+  int pair;
+  int r, gx, gy, gz;
+};
+struct DepositDesc {
+  float4* pos;
+  const float4* mom;
+  long long N;
+  float c0;
+  int n, lo, s, periodic;
+  unsigned long long* rho;
+  unsigned long long* escaped;
+  int r, gx, gy, gz;
+};
+struct SourceDesc {
+  unsigned long long* rho;
+  int n, lo, s;
+  Grid fh, fl;
+  df invM, S;
+  int b0, b1, moments;
+  double* partial_f2;
+  void* partial_m;
+  unsigned int* counter;
+  double* out;
+  const double* bgm;
+  double invM_d;
+  int* overflow;
+  int r, gx, gy, gz;
+};
+struct BoundaryDesc {
+  Grid ph, pl;
+  int n, lo;
+  const double* mom;
+  double S;
+  int want_lo;
+  int r, gx, gy, gz;
+};
+struct GatherDesc {
+  float4 *pos, *mom;
+  long long N;
+  const float *ph, *pl;
+  int n, lo, s, periodic;
+  float kick, c2;
+  int do_flag;
+  float klo, khi;
+  unsigned char* flags;
+  unsigned int* block_keep;
+  float4* forces;
+  unsigned long long* escaped;
+  int r, gx, gy, gz;
+};
+struct ScanDesc {
+  const unsigned int* cnt;
+  unsigned long long* off;
+  int nblk;
+  unsigned long long* n_keep;
+  int r, gx, gy, gz;
+};
+struct ScatterDesc {
+  const float4 *pos, *mom;
+  long long N;
+  const unsigned char* flags;
+  const unsigned long long* keep_off;
+  float4 *pos_out, *mom_out, *lc_pos, *lc_mom;
+  long long lc_base;
+  float a_cross;
+  int r, gx, gy, gz;
+};
+
+// batched launchers: `grid` blocks (the members' total, or more), tables in
+// device memory, `active` (may be NULL) masks realisations by index
+void launch_rbgs_b(cudaStream_t st, int grid, const RbgsDesc* d, const BTable* t, const int* active);
+void launch_restrict_b(cudaStream_t st, int grid, const RestrictDesc* d, const BTable* t,
+                       const int* active);
+void launch_prolong_b(cudaStream_t st, int grid, const ProlongDesc* d, const BTable* t,
+                      const int* active);
+void launch_coarse_mg_b(cudaStream_t st, int grid, const CmgDesc* d, const BTable* t,
+                        const int* active);
+void launch_defect_b(cudaStream_t st, int grid, const DefectDesc* d, const BTable* t,
+                     const int* active);
+void launch_predict_b(cudaStream_t st, int grid, const PredictDesc* d, const BTable* t);
+void launch_deposit_b(cudaStream_t st, int grid, const DepositDesc* d, const BTable* t);
+void launch_source_b(cudaStream_t st, int grid, const SourceDesc* d, const BTable* t);
+void launch_boundary_b(cudaStream_t st, int grid, const BoundaryDesc* d, const BTable* t);
+void launch_gather_b(cudaStream_t st, int grid, const GatherDesc* d, const BTable* t);
+void launch_scan_b(cudaStream_t st, int grid, const ScanDesc* d, const BTable* t);
+void launch_scatter_b(cudaStream_t st, int grid, const ScatterDesc* d, const BTable* t);
+
+// grid shapes of the single-realisation launches (blocks per dimension)
+dim3 rbgs_grid(int s);
+dim3 full_grid(int s);
+dim3 defect_grid(int s);
+dim3 source_grid(int s);
+int boundary_blocks(int s);
+int deposit_blocks(long long N);
+
+}  // namespace pm

@@ -58,6 +58,104 @@ def unpack(p4, m4):
     return p4[:, :3].copy(), m4[:, :3].copy(), ids, m4[:, 3].copy()
 
 
+def _config(n_mesh, n_particles, box, a_init, a_final, n_steps, rtol=1e-7, precision="mixed",
+            guess="warm", bc="paper", shrink=True, buffer_cells=1.0, max_vcycles=50,
+            store_forces=False, omega_m=0.3, omega_l=0.7):
+    lib = L.load()
+    cfg = L.PmConfig()
+    lib.pm_config_default(C.byref(cfg))
+    cfg.n_mesh = int(n_mesh)
+    cfg.n_particles = int(n_particles)
+    cfg.box_mpch = float(box)
+    cfg.omega_m, cfg.omega_l = float(omega_m), float(omega_l)
+    cfg.a_init, cfg.a_final, cfg.n_steps = float(a_init), float(a_final), int(n_steps)
+    cfg.rtol, cfg.max_vcycles = float(rtol), int(max_vcycles)
+    cfg.precision = _PREC[precision]
+    cfg.guess = _GUESS[guess]
+    cfg.bc = _BC[bc]
+    cfg.shrink = 1 if shrink else 0
+    cfg.buffer_cells = float(buffer_cells)
+    cfg.store_forces = 1 if store_forces else 0
+    return cfg
+
+
+class Batch:
+    """Many independent realisations advancing together (pm_batch_*):
+    one kernel launch per phase over all of them."""
+
+    def __init__(self, realisations, a_init, a_final, n_steps, rtol=1e-7, max_vcycles=50,
+                 buffer_cells=1.0):
+        """realisations: list of dicts with pos, mom, ids, n_mesh, box."""
+        lib = L.load()
+        R = len(realisations)
+        cfgs = (L.PmConfig * R)()
+        self.stream = torch.cuda.Stream()
+        self._sp = C.c_void_p(self.stream.cuda_stream)
+        self.caps = []
+        keep = []
+        pp = (C.c_void_p * R)()
+        mp = (C.c_void_p * R)()
+        for r, re in enumerate(realisations):
+            cfgs[r] = _config(re["n_mesh"], len(re["pos"]), re["box"], a_init, a_final,
+                              n_steps, rtol=rtol, max_vcycles=max_vcycles,
+                              buffer_cells=buffer_cells)
+            p4, m4 = pack(re["pos"], re["mom"], re["ids"])
+            dp, dm = torch.from_numpy(p4).cuda(), torch.from_numpy(m4).cuda()
+            keep += [dp, dm]
+            pp[r] = dp.data_ptr()
+            mp[r] = dm.data_ptr()
+            self.caps.append(len(re["pos"]))
+        self._b = C.c_void_p()
+        with _On(self.stream):
+            code = lib.pm_batch_init(R, cfgs, pp, mp, 0, self._sp, C.byref(self._b))
+        if code != L.PM_OK:
+            raise L.PmError(code, lib.pm_batch_last_error(None).decode())
+        self._lib = lib
+        self.R = R
+
+    def _check(self, code):
+        if code != L.PM_OK:
+            raise L.PmError(code, self._lib.pm_batch_last_error(self._b).decode())
+
+    def step(self, k=1):
+        self._check(self._lib.pm_batch_step(self._b, int(k)))
+
+    def stats(self, r):
+        s = L.PmStats()
+        self._check(self._lib.pm_batch_stats(self._b, int(r), C.byref(s)))
+        return {f: getattr(s, f) for f, _ in L.PmStats._fields_}
+
+    def particles(self, r):
+        n = C.c_int64()
+        cap = self.caps[r]
+        p4 = np.zeros((cap, 4), np.float32)
+        m4 = np.zeros((cap, 4), np.float32)
+        self._check(self._lib.pm_batch_get_particles(self._b, int(r), p4.ctypes.data,
+                                                     m4.ctypes.data, 1, C.byref(n)))
+        pos, mom, ids, _ = unpack(p4[:n.value], m4[:n.value])
+        return pos, mom, ids
+
+    def lightcone(self, r):
+        n = C.c_int64()
+        cap = self.caps[r]
+        p4 = np.zeros((cap, 4), np.float32)
+        m4 = np.zeros((cap, 4), np.float32)
+        self._check(self._lib.pm_batch_get_lightcone(self._b, int(r), p4.ctypes.data,
+                                                     m4.ctypes.data, 1, C.byref(n)))
+        return unpack(p4[:n.value], m4[:n.value])
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._lib.pm_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Sim:
     """One shrinking-domain PM run (one context of the C library)."""
 
