@@ -283,6 +283,19 @@ pm_status pm_shrink_static(const float* pos4_in, const float* mom4_in, int64_t n
                            void* stream);
 const char* pm_shrink_static_error(void);
 
+/* ---------------------------------------------------------------------------
+ * Learned initial guess (not in the paper; a build requirement): a BF16
+ * convolutional network on the tensor cores (tcgen05, FP32 accumulation in
+ * tensor memory) that maps a source to a potential guess for the solver.
+ * ------------------------------------------------------------------------- */
+
+/* C[M x N] (FP32, row-major) = A[M x K] B[N x K]^T with A, B row-major BF16
+ * device matrices; M % 128 == 0, K % 64 == 0, N in {16, 32, 64, 128}.  The
+ * tile engine under every convolution of the learned guess.  PM_ETIMEOUT if
+ * an MMA completion wait gave up.  Synchronises stream. */
+pm_status pm_nn_gemm_bf16(const void* A, const void* B, float* C, int32_t M, int32_t N,
+                          int32_t K, void* stream);
+
 /* Kernel launches made by this library in this process so far. */
 int64_t pm_launch_count(void);
 

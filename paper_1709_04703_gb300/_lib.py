@@ -28,6 +28,7 @@ EXPORTED = [
     "pm_destroy", "pm_shrink_static", "pm_shrink_static_error",
     "pm_batch_init", "pm_batch_step", "pm_batch_stats", "pm_batch_get_particles",
     "pm_batch_get_lightcone", "pm_batch_last_error", "pm_batch_destroy",
+    "pm_nn_gemm_bf16",
 ]
 PROF_CLASSES = ["deposit", "source", "boundary", "smooth0", "transfer0", "coarse",
                 "defect", "correct", "gather", "compact"]
@@ -103,6 +104,7 @@ def load():
         "pm_batch_get_lightcone": (I32, [P, I32, P, P, I32, C.POINTER(I64)]),
         "pm_batch_last_error": (C.c_char_p, [P]),
         "pm_batch_destroy": (None, [P]),
+        "pm_nn_gemm_bf16": (I32, [P, P, P, I32, I32, I32, P]),
         "pm_last_error": (C.c_char_p, [P]),
         "pm_destroy": (None, [P]),
     }

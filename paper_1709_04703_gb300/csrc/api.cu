@@ -1864,3 +1864,27 @@ void pm_batch_destroy(pm_batch* B) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Tensor-core building blocks of the learned guess
+// ===========================================================================
+extern "C" pm_status pm_nn_gemm_bf16(const void* A, const void* B, float* C, int32_t M,
+                                     int32_t N, int32_t K, void* stream) {
+  if (!A || !B || !C || M <= 0 || M % 128 || K <= 0 || K % 64 ||
+      (N != 16 && N != 32 && N != 64 && N != 128))
+    return fail(nullptr, PM_EINVAL, "pm_nn_gemm_bf16: M % 128, K % 64, N in {16,32,64,128}");
+  cudaStream_t st = (cudaStream_t)stream;
+  int* err = nullptr;
+  if (cudaMallocAsync((void**)&err, sizeof(int), st) != cudaSuccess)
+    return fail(nullptr, PM_ENOMEM, "pm_nn_gemm_bf16: cudaMallocAsync");
+  cudaMemsetAsync(err, 0, sizeof(int), st);
+  launch_gemm_tc(st, A, B, C, M, N, K, err);
+  cudaError_t e = cudaGetLastError();
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(err, st);
+  if (e != cudaSuccess) return fail(nullptr, PM_ECUDA, cudaGetErrorString(e));
+  if (h) return fail(nullptr, PM_ETIMEOUT, "pm_nn_gemm_bf16: MMA completion wait timed out");
+  return PM_OK;
+}

@@ -212,3 +212,9 @@ int boundary_blocks(int s);
 int deposit_blocks(long long N);
 
 }  // namespace pm
+
+namespace pm {
+// k_nn.cu
+void launch_gemm_tc(cudaStream_t st, const void* A, const void* B, float* C, int M, int N,
+                    int K, int* err);
+}  // namespace pm
