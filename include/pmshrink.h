@@ -49,7 +49,7 @@ typedef enum {
 } pm_status;
 
 enum { PM_MIXED = 0, PM_FP32_PLAIN = 1 };               /* pm_config.precision */
-enum { PM_GUESS_WARM = 0, PM_GUESS_ZERO = 1 };          /* pm_config.guess */
+enum { PM_GUESS_WARM = 0, PM_GUESS_ZERO = 1, PM_GUESS_LEARNED = 2 };  /* pm_config.guess */
 enum { PM_BC_PAPER = 0, PM_BC_OPEN = 1, PM_BC_PERIODIC = 2 };  /* pm_config.bc */
 
 typedef struct {
@@ -65,7 +65,9 @@ typedef struct {
   int32_t max_vcycles;   /* V-cycles allowed per solve before PM_ENOCONV */
   int32_t precision;     /* PM_MIXED: FP32 V-cycles inside a double-float
                             defect-correction loop; PM_FP32_PLAIN: FP32 only */
-  int32_t guess;         /* PM_GUESS_WARM: previous step's Phi; PM_GUESS_ZERO */
+  int32_t guess;         /* PM_GUESS_WARM: previous step's Phi; PM_GUESS_ZERO;
+                            PM_GUESS_LEARNED: the warm start corrected by the
+                            network attached with pm_set_guess */
   int32_t bc;            /* PM_BC_PAPER: periodic until the lightcone reaches
                             the box edge, open afterwards; PM_BC_OPEN /
                             PM_BC_PERIODIC force one kind for the whole run */
@@ -167,6 +169,8 @@ typedef struct {
   double resid_last;     /* final relative residual of the last solve */
   int64_t escaped;       /* particle-steps skipped because a CIC node left the cube */
   int64_t particle_steps;/* sum over completed steps of the active count */
+  int32_t guess_used_last;  /* 1 if the network corrected the last solve's start */
+  int64_t guess_used_total; /* solves started from the network's correction */
 } pm_stats_t;
 
 pm_status pm_stats(pm_ctx* ctx, pm_stats_t* out);
@@ -214,6 +218,7 @@ enum {
   PM_PROF_CORRECT,      /* Phi += e                                         */
   PM_PROF_GATHER,       /* gradient + gather + kick + drift + keep flags    */
   PM_PROF_COMPACT,      /* scan + stable scatter                            */
+  PM_PROF_GUESS,        /* learned initial guess (network forward)          */
   PM_PROF_N
 };
 /* enable = 1 starts (and zeroes) the counters, 0 stops them. */
@@ -295,6 +300,57 @@ const char* pm_shrink_static_error(void);
  * an MMA completion wait gave up.  Synchronises stream. */
 pm_status pm_nn_gemm_bf16(const void* A, const void* B, float* C, int32_t M, int32_t N,
                           int32_t K, void* stream);
+
+/* The network.  levels L in 1..4, channels 8 * 2^l per level: encoder of
+ * 3x3x3 convolutions + ReLU with 2x average pooling between levels, decoder
+ * of nearest 2x upsampling, concatenation with the encoder output of the
+ * same level, convolution + ReLU, and a final linear 3x3x3 convolution to
+ * 8 channels whose first is the guess.  The input is the source scaled to
+ * unit RMS per sample; the guess is rescaled by RMS(source) * out_scale.
+ * Activations BF16 channels-last, accumulation FP32 in tensor memory,
+ * parameters FP32 masters (per convolution, encoder then decoder then
+ * output: weights [cout][27 cin] with tap index (dz+1)*9+(dy+1)*3+(dx+1),
+ * then biases [cout]).  Zero padding outside each sample. */
+typedef struct pm_guess pm_guess;
+pm_status pm_guess_create(int32_t levels, void* stream, pm_guess** out);
+int64_t pm_guess_num_params(const pm_guess* g);
+/* Host parameters in, Adam state reset. */
+pm_status pm_guess_set_params(pm_guess* g, const float* params_host, float out_scale);
+/* Parameters and the gradient of the last pm_guess_loss_grad (host; either
+ * may be NULL). */
+pm_status pm_guess_get_params(pm_guess* g, float* params_host, float* grad_host);
+/* guess[b] for B sources of side S (device FP32 arrays B*S^3, [b][z][y][x]);
+ * S a multiple of 2^(L-1). */
+pm_status pm_guess_forward(pm_guess* g, const float* src_dev, int32_t B, int32_t S,
+                           int32_t periodic, float* guess_dev);
+/* Loss between the network output y and t = target / (RMS(source) *
+ * out_scale), and its gradient with respect to the parameters (kept for
+ * pm_guess_adam / pm_guess_get_params).  loss_kind 0: mean over voxels of
+ * (y - t)^2; 1: mean of (A (y - t))^2 with A the 7-point Laplacian (zero
+ * outside each sample unless periodic), i.e. the residual the guess leaves.
+ * periodic = 1 makes every convolution and A wrap around each sample. */
+pm_status pm_guess_loss_grad(pm_guess* g, const float* src_dev, const float* target_dev,
+                             int32_t B, int32_t S, int32_t periodic, int32_t loss_kind,
+                             double* loss_out);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) with learning rate lr. */
+pm_status pm_guess_adam(pm_guess* g, float lr);
+const char* pm_guess_last_error(const pm_guess* g);
+void pm_guess_destroy(pm_guess* g);
+
+/* Attach a network (or NULL) to a context for PM_GUESS_LEARNED.  In every
+ * solve whose cube side is >= 16 and a multiple of 2^(levels-1), the
+ * residual r of the warm start is fed to the network and its output, a
+ * correction e ~ A^-1 r, is added to the start before the V-cycles, which
+ * still iterate to rtol.  The context does not own the network; the
+ * network's parameters must not change while a step runs.  Allocates two
+ * n_mesh^3 FP32 scratch fields.  Not in the paper. */
+pm_status pm_set_guess(pm_ctx* ctx, pm_guess* net);
+/* Training pairs from the solver: while armed (r_dev, e_dev non-NULL, device
+ * arrays of n_mesh^3 floats), every solve writes the residual of its warm
+ * start (r) and the correction that the solve added to it (e = Phi - start)
+ * as dense side^3 arrays [z][y][x], side = pm_stats cube_side.  PM_MIXED
+ * only.  NULLs disarm.  Not in the paper. */
+pm_status pm_capture(pm_ctx* ctx, float* r_dev, float* e_dev);
 
 /* Kernel launches made by this library in this process so far. */
 int64_t pm_launch_count(void);

@@ -12,7 +12,7 @@ LIB_PATH = os.path.join(HERE, "libpmshrink.so")
 
 PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_ENOCONV, PM_EOVERFLOW, PM_ETIMEOUT = range(7)
 PM_MIXED, PM_FP32_PLAIN = 0, 1
-PM_GUESS_WARM, PM_GUESS_ZERO = 0, 1
+PM_GUESS_WARM, PM_GUESS_ZERO, PM_GUESS_LEARNED = 0, 1, 2
 PM_BC_PAPER, PM_BC_OPEN, PM_BC_PERIODIC = 0, 1, 2
 PM_SHRINK_STATIC_MAX_PARTICLES = 1 << 22
 
@@ -28,10 +28,12 @@ EXPORTED = [
     "pm_destroy", "pm_shrink_static", "pm_shrink_static_error",
     "pm_batch_init", "pm_batch_step", "pm_batch_stats", "pm_batch_get_particles",
     "pm_batch_get_lightcone", "pm_batch_last_error", "pm_batch_destroy",
-    "pm_nn_gemm_bf16",
+    "pm_nn_gemm_bf16", "pm_guess_create", "pm_guess_num_params", "pm_guess_set_params",
+    "pm_guess_get_params", "pm_guess_forward", "pm_guess_loss_grad", "pm_guess_adam",
+    "pm_guess_last_error", "pm_guess_destroy", "pm_set_guess", "pm_capture",
 ]
 PROF_CLASSES = ["deposit", "source", "boundary", "smooth0", "transfer0", "coarse",
-                "defect", "correct", "gather", "compact"]
+                "defect", "correct", "gather", "compact", "guess"]
 
 
 class PmConfig(C.Structure):
@@ -52,6 +54,7 @@ class PmStats(C.Structure):
         ("periodic", C.c_int32), ("vcycles_last", C.c_int32),
         ("vcycles_total", C.c_int64), ("resid_last", C.c_double),
         ("escaped", C.c_int64), ("particle_steps", C.c_int64),
+        ("guess_used_last", C.c_int32), ("guess_used_total", C.c_int64),
     ]
 
 
@@ -105,6 +108,17 @@ def load():
         "pm_batch_last_error": (C.c_char_p, [P]),
         "pm_batch_destroy": (None, [P]),
         "pm_nn_gemm_bf16": (I32, [P, P, P, I32, I32, I32, P]),
+        "pm_guess_create": (I32, [I32, P, C.POINTER(P)]),
+        "pm_guess_num_params": (I64, [P]),
+        "pm_guess_set_params": (I32, [P, P, C.c_float]),
+        "pm_guess_get_params": (I32, [P, P, P]),
+        "pm_guess_forward": (I32, [P, P, I32, I32, I32, P]),
+        "pm_guess_loss_grad": (I32, [P, P, P, I32, I32, I32, I32, C.POINTER(D)]),
+        "pm_set_guess": (I32, [P, P]),
+        "pm_capture": (I32, [P, P, P]),
+        "pm_guess_adam": (I32, [P, C.c_float]),
+        "pm_guess_last_error": (C.c_char_p, [P]),
+        "pm_guess_destroy": (None, [P]),
         "pm_last_error": (C.c_char_p, [P]),
         "pm_destroy": (None, [P]),
     }

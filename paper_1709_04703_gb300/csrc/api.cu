@@ -178,6 +178,14 @@ struct pm_ctx {
   double prof_bytes[PM_PROF_N] = {0};
   long long prof_lost = 0;
 
+  // learned initial guess (not owned) and its dense scratch fields
+  pm_guess* net = nullptr;
+  float *nn_in = nullptr, *nn_out = nullptr;
+  int guess_used_last = 0;
+  long long guess_used_total = 0;
+  // training-pair capture targets (caller's device memory)
+  float *cap_r = nullptr, *cap_e = nullptr;
+
   int vcycles_last = 0;
   long long vcycles_total = 0;
   double resid_last = 0.0;
@@ -483,6 +491,8 @@ pm_status vcycle_run(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
 }
 
 // Iterate to rtol.  f2 = ||f||^2 already in d_scal[0] (read at first sync).
+// With a learned guess, the first correction comes from the network applied
+// to the residual of the start instead of from a V-cycle.
 pm_status solve(pm_ctx* ctx) {
   const int lo = ctx->lo, s = ctx->s, per = ctx->periodic;
   Grid fh = full_view(ctx, ctx->f_hi, lo, s), fl = full_view(ctx, ctx->f_lo, lo, s);
@@ -494,24 +504,36 @@ pm_status solve(pm_ctx* ctx) {
     launch_fill(ctx->st, ph_of(ctx->cur), 0.0f, false);
     launch_fill(ctx->st, pl_of(ctx->cur), 0.0f, false);
   }
-  int it = 0;
+  bool net_todo = ctx->cfg.guess == PM_GUESS_LEARNED && guess_fits(ctx->net, s);
+  const bool capture = mixed && ctx->cap_r != nullptr;
+  ctx->guess_used_last = 0;
+  int it = 0;            // V-cycles run
+  bool pending = false;  // e0 holds a correction not yet added to Phi
+  bool first = true;
   double rel = 0.0;
   const double cells = (double)s * s * s;
-  for (;; ++it) {
+  for (;;) {
     int e = prof_begin(ctx);
     const int c0 = ctx->cur;
-    if (mixed && it > 0) {
-      // Phi <- Phi + e of the last V-cycle, written to the other buffer;
-      // reads Phi (8 B), e (4), f (8), writes Phi (8) and r (4) per cell
+    if (mixed && pending) {
+      // Phi <- Phi + e, written to the other buffer; reads Phi (8 B), e (4),
+      // f (8), writes Phi (8) and r (4) per cell
+      if (capture) launch_to_dense(ctx->st, e0, ctx->cap_e, true);
       launch_defect(ctx->st, ph_of(c0), pl_of(c0), &e0, ph_of(c0 ^ 1), pl_of(c0 ^ 1), fh, fl,
                     r0, per, true, ctx->partial, ctx->counter, ctx->d_scal + 11);
       ctx->cur ^= 1;
       prof_end(ctx, PM_PROF_DEFECT, e, 32.0 * cells);
     } else {
       launch_defect(ctx->st, ph_of(c0), pl_of(c0), nullptr, ph_of(c0), pl_of(c0), fh, fl, r0,
-                    per, mixed, ctx->partial, ctx->counter, ctx->d_scal + 11);
+                    per, mixed || net_todo, ctx->partial, ctx->counter, ctx->d_scal + 11);
       prof_end(ctx, PM_PROF_DEFECT, e, (mixed ? 20.0 : 16.0) * cells);
     }
+    pending = false;
+    if (first && capture) {
+      launch_to_dense(ctx->st, r0, ctx->cap_r, false);
+      CK(cudaMemsetAsync(ctx->cap_e, 0, sizeof(float) * (size_t)cells, ctx->st));
+    }
+    first = false;
     CKL();
     pm_status st = sync_read(ctx);
     if (st != PM_OK) return st;
@@ -527,10 +549,35 @@ pm_status solve(pm_ctx* ctx) {
                rel, it, ctx->cfg.rtol);
       return fail(ctx, PM_ENOCONV, buf);
     }
+    if (net_todo) {
+      // e ~ A^-1 r from the network; r = f - A Phi of the start
+      net_todo = false;
+      e = prof_begin(ctx);
+      launch_to_dense(ctx->st, r0, ctx->nn_in, false);
+      st = guess_apply(ctx->net, ctx->st, ctx->nn_in, s, per, ctx->nn_out);
+      if (st != PM_OK) return fail(ctx, st, pm_guess_last_error(ctx->net));
+      if (mixed) {
+        launch_from_dense(ctx->st, ctx->nn_out, e0, false);
+        pending = true;
+      } else {
+        launch_from_dense(ctx->st, ctx->nn_out, ph_of(ctx->cur), true);
+      }
+      prof_end(ctx, PM_PROF_GUESS, e, 16.0 * cells);
+      CKL();
+      ctx->guess_used_last = 1;
+      ctx->guess_used_total++;
+      continue;
+    }
     // the correction e starts at zero in every V-cycle (zero-start sweep)
     pm_status v = mixed ? vcycle_run(ctx, e0, r0, true)
                         : vcycle_run(ctx, ph_of(ctx->cur), fh, false);
     if (v != PM_OK) return v;
+    ++it;
+    pending = mixed;
+  }
+  if (ctx->guess_used_last) {
+    pm_status st = guess_check(ctx->net, ctx->st);
+    if (st != PM_OK) return fail(ctx, st, "learned guess: an MMA completion wait timed out");
   }
   ctx->vcycles_last = it;
   ctx->vcycles_total += it;
@@ -630,6 +677,8 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
     return fail(nullptr, PM_EINVAL, "pm_init: unknown precision");
   if (cfg->bc < PM_BC_PAPER || cfg->bc > PM_BC_PERIODIC)
     return fail(nullptr, PM_EINVAL, "pm_init: unknown bc");
+  if (cfg->guess < PM_GUESS_WARM || cfg->guess > PM_GUESS_LEARNED)
+    return fail(nullptr, PM_EINVAL, "pm_init: unknown guess");
 
   ctx = new pm_ctx();
   ctx->cfg = *cfg;
@@ -747,6 +796,8 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
   if (!ctx) return fail(nullptr, PM_EINVAL, "pm_step: NULL context");
   if (n_steps < 0 || ctx->step + n_steps > ctx->cfg.n_steps)
     return fail(ctx, PM_EINVAL, "pm_step: past the last step of the schedule");
+  if (ctx->cfg.guess == PM_GUESS_LEARNED && !ctx->net)
+    return fail(ctx, PM_EINVAL, "pm_step: PM_GUESS_LEARNED without a network (pm_set_guess)");
   const int n = ctx->n;
   const bool mixed = ctx->cfg.precision == PM_MIXED;
   for (int q = 0; q < n_steps; ++q) {
@@ -793,7 +844,7 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
     CKL();
     // warm start extrapolated linearly in a_half from the last two solutions
     // of the same boundary phase
-    if (ctx->cfg.guess == PM_GUESS_WARM) {
+    if (ctx->cfg.guess == PM_GUESS_WARM || ctx->cfg.guess == PM_GUESS_LEARNED) {
       if (set_phase_changed) ctx->n_sol = 0;
       if (ctx->n_sol >= 1) {
         float w = 0.0f;
@@ -1016,6 +1067,32 @@ pm_status pm_stats(pm_ctx* ctx, pm_stats_t* o) {
   o->resid_last = ctx->resid_last;
   o->escaped = (int64_t)ctx->h_cnt[1];
   o->particle_steps = ctx->particle_steps;
+  o->guess_used_last = ctx->guess_used_last;
+  o->guess_used_total = ctx->guess_used_total;
+  return PM_OK;
+}
+
+pm_status pm_set_guess(pm_ctx* ctx, pm_guess* net) {
+  if (!ctx) return fail(nullptr, PM_EINVAL, "pm_set_guess: NULL context");
+  if (net && !ctx->nn_in) {
+    const size_t bytes = sizeof(float) * (size_t)ctx->n * ctx->n * ctx->n;
+    pm_status st = alloc(ctx, (void**)&ctx->nn_in, bytes);
+    if (st == PM_OK) st = alloc(ctx, (void**)&ctx->nn_out, bytes);
+    if (st != PM_OK) return st;
+  }
+  CK(cudaDeviceSynchronize());  // parameters written on the network's stream
+  ctx->net = net;
+  return PM_OK;
+}
+
+pm_status pm_capture(pm_ctx* ctx, float* r_dev, float* e_dev) {
+  if (!ctx) return fail(nullptr, PM_EINVAL, "pm_capture: NULL context");
+  if ((r_dev == nullptr) != (e_dev == nullptr))
+    return fail(ctx, PM_EINVAL, "pm_capture: give both arrays or neither");
+  if (r_dev && ctx->cfg.precision != PM_MIXED)
+    return fail(ctx, PM_EINVAL, "pm_capture: needs PM_MIXED");
+  ctx->cap_r = r_dev;
+  ctx->cap_e = e_dev;
   return PM_OK;
 }
 
@@ -1148,7 +1225,8 @@ void pm_destroy(pm_ctx* ctx) {
                   ctx->phi_h[0], ctx->phi_l[0], ctx->phi_h[1], ctx->phi_l[1], ctx->f_hi,
                   ctx->f_lo, ctx->prev_hi, ctx->prev_lo,
                   ctx->partial, ctx->partial_m,
-                  ctx->counter, ctx->d_scal, ctx->bgm, ctx->d_cnt, ctx->d_overflow};
+                  ctx->counter, ctx->d_scal, ctx->bgm, ctx->d_cnt, ctx->d_overflow,
+                  ctx->nn_in, ctx->nn_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (float* p : ctx->lu) if (p) cudaFree(p);
@@ -1457,6 +1535,8 @@ pm_status pm_batch_init(int32_t n_real, const pm_config* cfgs, const float* cons
   for (int r = 0; r < n_real; ++r) {
     if (cfgs[r].precision != PM_MIXED)
       return bfail(nullptr, PM_EINVAL, "pm_batch_init: batches run in PM_MIXED precision");
+    if (cfgs[r].guess == PM_GUESS_LEARNED)
+      return bfail(nullptr, PM_EINVAL, "pm_batch_init: the learned guess runs per context");
     if (cfgs[r].n_steps != cfgs[0].n_steps || cfgs[r].a_init != cfgs[0].a_init ||
         cfgs[r].a_final != cfgs[0].a_final)
       return bfail(nullptr, PM_EINVAL, "pm_batch_init: realisations must share the a schedule");

@@ -555,6 +555,40 @@ void launch_correct(cudaStream_t st, Grid ph, Grid pl, Grid e) {
   note_launch();
 }
 
+// Dense [z][y][x] FP32 arrays of side s <-> grid interiors (the learned
+// guess and training-pair capture).  to_dense: d (=|+=) g; from_dense:
+// g (=|+=) d.
+__global__ void __launch_bounds__(256) k_to_dense(Grid g, float* __restrict__ d, int add) {
+  const int s = g.s;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z;
+  if (i >= s || j >= s) return;
+  long long o = ((long long)k * s + j) * s + i;
+  float v = g.base[gidx(g, i, j, k)];
+  d[o] = add ? d[o] + v : v;
+}
+
+__global__ void __launch_bounds__(256) k_from_dense(const float* __restrict__ d, Grid g, int add) {
+  const int s = g.s;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z;
+  if (i >= s || j >= s) return;
+  long long o = ((long long)k * s + j) * s + i;
+  int c = gidx(g, i, j, k);
+  g.base[c] = add ? g.base[c] + d[o] : d[o];
+}
+
+void launch_to_dense(cudaStream_t st, Grid g, float* d, bool add) {
+  k_to_dense<<<grid_full(g.s), dim3(32, 8), 0, st>>>(g, d, add ? 1 : 0);
+  note_launch();
+}
+void launch_from_dense(cudaStream_t st, const float* d, Grid g, bool add) {
+  k_from_dense<<<grid_full(g.s), dim3(32, 8), 0, st>>>(d, g, add ? 1 : 0);
+  note_launch();
+}
+
 // Warm start extrapolated in time: Phi <- Phi + w (Phi - Phi_prev),
 // Phi_prev <- old Phi (interior only; the ghost layer keeps its boundary
 // values).  Double-float when `pair`, FP32 hi only otherwise.

@@ -12,7 +12,7 @@
 //   * elementwise    ReLU backward, 2x average pooling / nearest upsampling
 //                    (and their backward), channel concatenation, MSE, Adam
 // The input-gradient of a convolution is the forward convolution of the
-// output-gradient with mirrored, transposed weights (k_conv_wt_flip).
+// output-gradient with mirrored, transposed weights (k_pack_w).
 #include <cuda_bf16.h>
 
 #include "pm_kernels.cuh"
@@ -155,6 +155,594 @@ void launch_gemm_tc(cudaStream_t st, const void* A, const void* B, float* C, int
     case 128: k_gemm_tc<128><<<grid, 128, 0, st>>>((const bf16*)A, (const bf16*)B, C, M, K, err); break;
     default: return;
   }
+  note_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Activations: channels-last BF16 tensors [B][D][H][W][C], C % 8 == 0.
+// ---------------------------------------------------------------------------
+struct Vol {
+  int B, D, H, W;  // samples and spatial extent
+  int per = 0;     // convolutions wrap around each sample (else zero padding)
+  __host__ __device__ long long voxels() const { return (long long)B * D * H * W; }
+};
+
+// 3x3x3 "same" convolution, out[v][co] = bias[co] + sum_tap,ci in[v+tap][ci] w[co][tap*cin+ci]
+// (zero outside each sample, or periodic when g.per), as a GEMM: rows = 128 voxels, N = output
+// columns (>= cout, multiple of 16), K = 27 cin padded to 64.
+// wp: [N][kp] BF16, rows >= cout and columns >= 27 cin zero.
+template <int N>
+__global__ void __launch_bounds__(128) k_conv_fwd(const bf16* __restrict__ in, Vol g, int cin,
+                                                  const bf16* __restrict__ wp, int kp,
+                                                  const float* __restrict__ bias, int cout,
+                                                  int relu, bf16* __restrict__ out_bf,
+                                                  float* __restrict__ out_f, int* err) {
+  constexpr int KC = 64;
+  __shared__ __align__(1024) uint8_t sA[tc::TM * KC * 2];
+  __shared__ __align__(1024) uint8_t sB[N * KC * 2];
+  __shared__ uint32_t tslot;
+  __shared__ __align__(8) uint64_t mbar;
+  constexpr int NC = tc::tmem_cols(N);
+  TcCtx c = tc_begin<NC>(&tslot, &mbar);
+  const long long nvox = g.voxels();
+  const long long m0 = (long long)blockIdx.x * tc::TM;
+  // this thread's row (voxel) and its coordinates
+  const long long v = m0 + threadIdx.x;
+  const bool vin = v < nvox;
+  int x = 0, y = 0, z = 0;
+  long long smp = 0;
+  if (vin) {
+    long long t = v;
+    x = (int)(t % g.W); t /= g.W;
+    y = (int)(t % g.H); t /= g.H;
+    z = (int)(t % g.D); smp = t / g.D;
+  }
+  uint32_t phase = 0;
+  auto fa = [&](int kt, uint8_t* s) {
+    uint8_t* row = s;
+#pragma unroll
+    for (int vv = 0; vv < KC / 8; ++vv) {
+      int k = kt * KC + 8 * vv;
+      int tap = k / cin, ci = k - tap * cin;
+      uint4 val = make_uint4(0, 0, 0, 0);
+      if (vin && tap < 27) {
+        int zz = z + tap / 9 - 1, yy = y + (tap / 3) % 3 - 1, xx = x + tap % 3 - 1;
+        if (g.per) {
+          zz = zz < 0 ? zz + g.D : (zz >= g.D ? zz - g.D : zz);
+          yy = yy < 0 ? yy + g.H : (yy >= g.H ? yy - g.H : yy);
+          xx = xx < 0 ? xx + g.W : (xx >= g.W ? xx - g.W : xx);
+        }
+        if (zz >= 0 && zz < g.D && yy >= 0 && yy < g.H && xx >= 0 && xx < g.W) {
+          long long nv = ((smp * g.D + zz) * g.H + yy) * (long long)g.W + xx;
+          val = *reinterpret_cast<const uint4*>(in + nv * cin + ci);
+        }
+      }
+      *reinterpret_cast<uint4*>(row + tc::tile_offset(threadIdx.x, 8 * vv, KC)) = val;
+    }
+  };
+  auto fb = [&](int kt, uint8_t* s) {
+    fill_tile<KC>(s, N, [&](int r, int vv) {
+      return *reinterpret_cast<const uint4*>(wp + (long long)r * kp + kt * KC + 8 * vv);
+    });
+  };
+  bool ok = tc_mainloop<N, KC>(fa, fb, kp / KC, c.taddr, sA, sB, c.mbar, phase, err);
+  if (ok) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long row = m0 + 32 * w + lane;
+    const int coutp = (cout + 7) & ~7;
+#pragma unroll
+    for (int col = 0; col < N; col += 8) {
+      float val[8];
+      tc::tmem_ld8(c.taddr, w, col, val);
+      if (row < nvox && col < coutp) {
+        __align__(16) bf16 ob[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          float o = col + q < cout ? val[q] + (bias ? bias[col + q] : 0.0f) : 0.0f;
+          if (relu) o = fmaxf(o, 0.0f);
+          ob[q] = __float2bfloat16_rn(o);
+          if (out_f) out_f[row * coutp + col + q] = o;
+        }
+        if (out_bf) *reinterpret_cast<uint4*>(out_bf + row * coutp + col) =
+                        *reinterpret_cast<const uint4*>(ob);
+      }
+    }
+  }
+  tc_end<NC>(c);
+}
+
+// Weight gradient, dw[co][tap*cin+ci] += sum_v in[v+tap][ci] dy[v][co]:
+// rows m = tap*cin + ci (128 per block), N >= cout, K = voxels, each block
+// folding `chunks` chunks of 64 voxels starting at its split.
+template <int N>
+__global__ void __launch_bounds__(128) k_conv_wgrad(const bf16* __restrict__ in, Vol g, int cin,
+                                                    const bf16* __restrict__ dy, int cout,
+                                                    float* __restrict__ dw, int chunks,
+                                                    int* err) {
+  constexpr int KC = 64;
+  __shared__ __align__(1024) uint8_t sA[tc::TM * KC * 2];
+  __shared__ __align__(1024) uint8_t sB[N * KC * 2];
+  __shared__ uint32_t tslot;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ int vz[KC], vy[KC], vx[KC];
+  __shared__ long long vs[KC];
+  constexpr int NC = tc::tmem_cols(N);
+  TcCtx c = tc_begin<NC>(&tslot, &mbar);
+  const long long nvox = g.voxels();
+  const int m = blockIdx.x * tc::TM + threadIdx.x;  // this thread's row
+  const int rows = 27 * cin;
+  const int tap = m / cin, ci = m - (m / cin) * cin;
+  const int dz = tap / 9 - 1, dyy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+  const int coutp = (cout + 7) & ~7;
+  const long long k0 = (long long)blockIdx.y * chunks * KC;
+  uint32_t phase = 0;
+  auto fa = [&](int kt, uint8_t* s) {
+    // voxel coordinates of this chunk
+    if (threadIdx.x < KC) {
+      long long v = k0 + (long long)kt * KC + threadIdx.x;
+      long long t = v < nvox ? v : 0;
+      vx[threadIdx.x] = (int)(t % g.W); t /= g.W;
+      vy[threadIdx.x] = (int)(t % g.H); t /= g.H;
+      vz[threadIdx.x] = (int)(t % g.D);
+      vs[threadIdx.x] = v < nvox ? t / g.D : -1;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int vv = 0; vv < KC / 8; ++vv) {
+      __align__(16) bf16 e[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        int kk = 8 * vv + q;
+        bf16 val = __float2bfloat16_rn(0.0f);
+        if (m < rows && vs[kk] >= 0) {
+          int zz = vz[kk] + dz, yy = vy[kk] + dyy, xx = vx[kk] + dx;
+          if (g.per) {
+            zz = zz < 0 ? zz + g.D : (zz >= g.D ? zz - g.D : zz);
+            yy = yy < 0 ? yy + g.H : (yy >= g.H ? yy - g.H : yy);
+            xx = xx < 0 ? xx + g.W : (xx >= g.W ? xx - g.W : xx);
+          }
+          if (zz >= 0 && zz < g.D && yy >= 0 && yy < g.H && xx >= 0 && xx < g.W)
+            val = in[(((vs[kk] * g.D + zz) * g.H + yy) * (long long)g.W + xx) * cin + ci];
+        }
+        e[q] = val;
+      }
+      *reinterpret_cast<uint4*>(s + tc::tile_offset(threadIdx.x, 8 * vv, KC)) =
+          *reinterpret_cast<const uint4*>(e);
+    }
+  };
+  auto fb = [&](int kt, uint8_t* s) {
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+#pragma unroll 1
+      for (int vv = 0; vv < KC / 8; ++vv) {
+        __align__(16) bf16 e[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          long long v = k0 + (long long)kt * KC + 8 * vv + q;
+          e[q] = (r < cout && v < nvox) ? dy[v * coutp + r] : __float2bfloat16_rn(0.0f);
+        }
+        *reinterpret_cast<uint4*>(s + tc::tile_offset(r, 8 * vv, KC)) =
+            *reinterpret_cast<const uint4*>(e);
+      }
+    }
+  };
+  long long left = nvox - k0;
+  int kt_n = (int)((left + KC - 1) / KC);
+  if (kt_n > chunks) kt_n = chunks;
+  bool ok = kt_n > 0 ? tc_mainloop<N, KC>(fa, fb, kt_n, c.taddr, sA, sB, c.mbar, phase, err)
+                     : false;
+  if (ok) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x * tc::TM + 32 * w + lane;
+#pragma unroll
+    for (int col = 0; col < N; col += 8) {
+      float val[8];
+      tc::tmem_ld8(c.taddr, w, col, val);
+      if (row < rows)
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (col + q < cout) atomicAdd(&dw[(long long)(col + q) * rows + row], val[q]);
+    }
+  }
+  tc_end<NC>(c);
+}
+
+#define PM_CONV_DISPATCH(KERNEL, N, ...)                                 \
+  switch (N) {                                                           \
+    case 16: KERNEL<16><<<__VA_ARGS__>>>; break;                         \
+    case 32: KERNEL<32><<<__VA_ARGS__>>>; break;                         \
+    case 48: KERNEL<48><<<__VA_ARGS__>>>; break;                         \
+    case 64: KERNEL<64><<<__VA_ARGS__>>>; break;                         \
+    case 96: KERNEL<96><<<__VA_ARGS__>>>; break;                         \
+    default: break;                                                      \
+  }
+
+void launch_conv_fwd(cudaStream_t st, const void* in, int B, int D, int H, int W, int per,
+                     int cin, const void* wp, int n, int kp, const float* bias, int cout,
+                     int relu, void* out_bf, float* out_f, int* err) {
+  Vol g{B, D, H, W, per};
+  dim3 grid((unsigned)((g.voxels() + tc::TM - 1) / tc::TM));
+  switch (n) {
+    case 16: k_conv_fwd<16><<<grid, 128, 0, st>>>((const bf16*)in, g, cin, (const bf16*)wp, kp, bias, cout, relu, (bf16*)out_bf, out_f, err); break;
+    case 32: k_conv_fwd<32><<<grid, 128, 0, st>>>((const bf16*)in, g, cin, (const bf16*)wp, kp, bias, cout, relu, (bf16*)out_bf, out_f, err); break;
+    case 48: k_conv_fwd<48><<<grid, 128, 0, st>>>((const bf16*)in, g, cin, (const bf16*)wp, kp, bias, cout, relu, (bf16*)out_bf, out_f, err); break;
+    case 64: k_conv_fwd<64><<<grid, 128, 0, st>>>((const bf16*)in, g, cin, (const bf16*)wp, kp, bias, cout, relu, (bf16*)out_bf, out_f, err); break;
+    case 96: k_conv_fwd<96><<<grid, 128, 0, st>>>((const bf16*)in, g, cin, (const bf16*)wp, kp, bias, cout, relu, (bf16*)out_bf, out_f, err); break;
+    default: return;
+  }
+  note_launch();
+}
+
+void launch_conv_wgrad(cudaStream_t st, const void* in, int B, int D, int H, int W, int per,
+                       int cin, const void* dy, int cout, int n, float* dw, int* err) {
+  Vol g{B, D, H, W, per};
+  const long long nvox = g.voxels();
+  const int rows = 27 * cin;
+  const int mt = (rows + tc::TM - 1) / tc::TM;
+  const long long kchunks = (nvox + 63) / 64;
+  // about 4 blocks per SM in total
+  long long splits = (608 + mt - 1) / mt;
+  if (splits > kchunks) splits = kchunks;
+  if (splits < 1) splits = 1;
+  const int chunks = (int)((kchunks + splits - 1) / splits);
+  splits = (kchunks + chunks - 1) / chunks;
+  dim3 grid((unsigned)mt, (unsigned)splits);
+  switch (n) {
+    case 16: k_conv_wgrad<16><<<grid, 128, 0, st>>>((const bf16*)in, g, cin, (const bf16*)dy, cout, dw, chunks, err); break;
+    case 32: k_conv_wgrad<32><<<grid, 128, 0, st>>>((const bf16*)in, g, cin, (const bf16*)dy, cout, dw, chunks, err); break;
+    case 48: k_conv_wgrad<48><<<grid, 128, 0, st>>>((const bf16*)in, g, cin, (const bf16*)dy, cout, dw, chunks, err); break;
+    case 64: k_conv_wgrad<64><<<grid, 128, 0, st>>>((const bf16*)in, g, cin, (const bf16*)dy, cout, dw, chunks, err); break;
+    case 96: k_conv_wgrad<96><<<grid, 128, 0, st>>>((const bf16*)in, g, cin, (const bf16*)dy, cout, dw, chunks, err); break;
+    default: return;
+  }
+  note_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Weight packing.  w: FP32 master [cout][27 cin].  Forward operand
+// wp[n][kp] (rows cout.., columns 27 cin.. zero); input-gradient operand
+// wt[nt][kpt]: wt[ci][t' cout + co] = w[co][(26 - t') cin + ci].
+// ---------------------------------------------------------------------------
+__global__ void k_pack_w(const float* __restrict__ w, int cin, int cout, bf16* __restrict__ wp,
+                         int n, int kp, bf16* __restrict__ wt, int nt, int kpt) {
+  const int K = 27 * cin;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * kp; t += gridDim.x * blockDim.x) {
+    int r = t / kp, k = t - r * kp;
+    float v = (r < cout && k < K) ? w[(long long)r * K + k] : 0.0f;
+    wp[t] = __float2bfloat16_rn(v);
+  }
+  const int Kt = 27 * cout;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt * kpt; t += gridDim.x * blockDim.x) {
+    int ci = t / kpt, k = t - ci * kpt;
+    float v = 0.0f;
+    if (ci < cin && k < Kt) {
+      int tp = k / cout, co = k - tp * cout;
+      v = w[(long long)co * K + (26 - tp) * cin + ci];
+    }
+    wt[t] = __float2bfloat16_rn(v);
+  }
+}
+
+void launch_pack_w(cudaStream_t st, const float* w, int cin, int cout, void* wp, int n, int kp,
+                   void* wt, int nt, int kpt) {
+  k_pack_w<<<304, 256, 0, st>>>(w, cin, cout, (bf16*)wp, n, kp, (bf16*)wt, nt, kpt);
+  note_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Elementwise kernels (channels-last BF16 unless stated).
+// ---------------------------------------------------------------------------
+// dy <- dy * (y > 0)
+__global__ void k_relu_bwd(bf16* __restrict__ dy, const bf16* __restrict__ y, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    if (!(__bfloat162float(y[t]) > 0.0f)) dy[t] = __float2bfloat16_rn(0.0f);
+}
+
+// 2x2x2 average pooling: out [B][D/2][H/2][W/2][C]
+__global__ void k_pool2(const bf16* __restrict__ in, Vol g, int C, bf16* __restrict__ out) {
+  const int D2 = g.D / 2, H2 = g.H / 2, W2 = g.W / 2;
+  const long long n = (long long)g.B * D2 * H2 * W2 * C;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    int c = (int)(t % C);
+    long long r = t / C;
+    int x = (int)(r % W2); r /= W2;
+    int y = (int)(r % H2); r /= H2;
+    int z = (int)(r % D2);
+    long long b = r / D2;
+    float acc = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      long long v = ((b * g.D + 2 * z + (d >> 2)) * g.H + 2 * y + ((d >> 1) & 1)) * (long long)g.W +
+                    2 * x + (d & 1);
+      acc += __bfloat162float(in[v * C + c]);
+    }
+    out[t] = __float2bfloat16_rn(0.125f * acc);
+  }
+}
+
+// backward of pooling: din[v] = dout[parent] / 8 (din has the fine shape g)
+__global__ void k_pool2_bwd(const bf16* __restrict__ dout, Vol g, int C, bf16* __restrict__ din) {
+  const long long n = g.voxels() * C;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    int c = (int)(t % C);
+    long long r = t / C;
+    int x = (int)(r % g.W); r /= g.W;
+    int y = (int)(r % g.H); r /= g.H;
+    int z = (int)(r % g.D);
+    long long b = r / g.D;
+    long long p = ((b * (g.D / 2) + z / 2) * (g.H / 2) + y / 2) * (long long)(g.W / 2) + x / 2;
+    din[t] = __float2bfloat16_rn(0.125f * __bfloat162float(dout[p * C + c]));
+  }
+}
+
+// nearest upsampling by 2 into channels [c0, c0 + C) of an output with Cout
+// channels (fine shape g); optional accumulate-free backward below
+__global__ void k_up2(const bf16* __restrict__ in, Vol g, int C, bf16* __restrict__ out, int Cout,
+                      int c0) {
+  const long long n = g.voxels() * C;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    int c = (int)(t % C);
+    long long v = t / C, r = v;
+    int x = (int)(r % g.W); r /= g.W;
+    int y = (int)(r % g.H); r /= g.H;
+    int z = (int)(r % g.D);
+    long long b = r / g.D;
+    long long p = ((b * (g.D / 2) + z / 2) * (g.H / 2) + y / 2) * (long long)(g.W / 2) + x / 2;
+    out[v * Cout + c0 + c] = in[p * C + c];
+  }
+}
+
+// backward of upsampling: din[p] = sum of the 8 children of channels
+// [c0, c0 + C) of dout (fine shape g, Cout channels)
+__global__ void k_up2_bwd(const bf16* __restrict__ dout, Vol g, int Cout, int c0, int C,
+                          bf16* __restrict__ din) {
+  const int D2 = g.D / 2, H2 = g.H / 2, W2 = g.W / 2;
+  const long long n = (long long)g.B * D2 * H2 * W2 * C;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    int c = (int)(t % C);
+    long long r = t / C;
+    int x = (int)(r % W2); r /= W2;
+    int y = (int)(r % H2); r /= H2;
+    int z = (int)(r % D2);
+    long long b = r / D2;
+    float acc = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      long long v = ((b * g.D + 2 * z + (d >> 2)) * g.H + 2 * y + ((d >> 1) & 1)) * (long long)g.W +
+                    2 * x + (d & 1);
+      acc += __bfloat162float(dout[v * Cout + c0 + c]);
+    }
+    din[t] = __float2bfloat16_rn(acc);
+  }
+}
+
+// copy channels [0, C) of a tensor into channels [c0, c0 + C) of another
+// (Cout channels); with `add` the destination is accumulated into
+__global__ void k_chan_copy(const bf16* __restrict__ src, long long nvox, int C, int Csrc,
+                            int s0, bf16* __restrict__ dst, int Cdst, int c0, int add) {
+  const long long n = nvox * C;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    int c = (int)(t % C);
+    long long v = t / C;
+    bf16 val = src[v * Csrc + s0 + c];
+    if (add)
+      dst[v * Cdst + c0 + c] =
+          __float2bfloat16_rn(__bfloat162float(dst[v * Cdst + c0 + c]) + __bfloat162float(val));
+    else
+      dst[v * Cdst + c0 + c] = val;
+  }
+}
+
+// network input: channel 0 = f * scale[b], channel 1 = 1 (the domain mask:
+// zero padding turns it into a boundary indicator), channels 2..7 zero
+__global__ void k_nn_input(const float* __restrict__ f, long long vps, const float* __restrict__ scale,
+                           int B, bf16* __restrict__ x) {
+  const long long n = (long long)B * vps * 8;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    int c = (int)(t & 7);
+    long long v = t >> 3;
+    x[t] = __float2bfloat16_rn(c == 0 ? f[v] * scale[v / vps] : (c == 1 ? 1.0f : 0.0f));
+  }
+}
+
+// loss = mean over voxels of (y0 - target * scale_t[b])^2; dy (8 channels)
+// = d loss / d y in channel 0; partial sums of the loss per block
+__global__ void k_mse(const float* __restrict__ y, const float* __restrict__ target,
+                      long long vps, const float* __restrict__ tscale, int B,
+                      bf16* __restrict__ dy, double* __restrict__ loss) {
+  const long long n = (long long)B * vps;
+  const float inv = 1.0f / (float)n;
+  double acc = 0.0;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x) {
+    float d = y[v * 8] - target[v] * tscale[v / vps];
+    acc += (double)d * d;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) dy[v * 8 + c] = __float2bfloat16_rn(c == 0 ? 2.0f * d * inv : 0.0f);
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc / (double)n);
+}
+
+// Residual-norm loss, in three passes over FP32 fields of B samples:
+//   d = y0 - target * tscale[b]           (k_loss_diff)
+//   q = A d,  loss = mean q^2             (k_lap_loss; A the 7-point Laplacian
+//                                          sum_nb d - 6 d, zero outside a
+//                                          sample or periodic)
+//   dy0 = 2 A q / n                       (k_lap_grad; A is symmetric)
+__global__ void k_loss_diff(const float* __restrict__ y, const float* __restrict__ target,
+                            long long vps, const float* __restrict__ tscale, int B,
+                            float* __restrict__ d) {
+  const long long n = (long long)B * vps;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x)
+    d[v] = y[v * 8] - target[v] * tscale[v / vps];
+}
+
+__device__ __forceinline__ float lap7(const float* __restrict__ d, const Vol& g, long long v) {
+  long long t = v;
+  int x = (int)(t % g.W); t /= g.W;
+  int y = (int)(t % g.H); t /= g.H;
+  int z = (int)(t % g.D);
+  const long long sy = g.W, sz = (long long)g.W * g.H;
+  float c = d[v], acc = -6.0f * c;
+  auto nb = [&](int coord, int ext, long long stride, int dir) {
+    int q = coord + dir;
+    if (q < 0 || q >= ext) {
+      if (!g.per) return 0.0f;
+      q = q < 0 ? q + ext : q - ext;
+    }
+    return d[v + (long long)(q - coord) * stride];
+  };
+  acc += nb(x, g.W, 1, -1) + nb(x, g.W, 1, 1);
+  acc += nb(y, g.H, sy, -1) + nb(y, g.H, sy, 1);
+  acc += nb(z, g.D, sz, -1) + nb(z, g.D, sz, 1);
+  return acc;
+}
+
+__global__ void k_lap_loss(const float* __restrict__ d, Vol g, float* __restrict__ q,
+                           double* __restrict__ loss) {
+  const long long n = g.voxels();
+  double acc = 0.0;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x) {
+    float a = lap7(d, g, v);
+    q[v] = a;
+    acc += (double)a * a;
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc / (double)n);
+}
+
+__global__ void k_lap_grad(const float* __restrict__ q, Vol g, bf16* __restrict__ dy) {
+  const long long n = g.voxels();
+  const float inv = 2.0f / (float)n;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x) {
+    float a = lap7(q, g, v) * inv;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) dy[v * 8 + c] = __float2bfloat16_rn(c == 0 ? a : 0.0f);
+  }
+}
+
+// bias gradient: db[c] += sum_v dy[v][c] for c < cout (dy has coutp channels)
+__global__ void k_bias_grad(const bf16* __restrict__ dy, long long nvox, int cout, int coutp,
+                            float* __restrict__ db) {
+  __shared__ float sacc[64];
+  for (int c = threadIdx.x; c < 64; c += blockDim.x) sacc[c] = 0.0f;
+  __syncthreads();
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nvox * coutp;
+       t += (long long)gridDim.x * blockDim.x) {
+    int c = (int)(t % coutp);
+    if (c < cout) atomicAdd(&sacc[c], __bfloat162float(dy[t]));
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < cout; c += blockDim.x) atomicAdd(&db[c], sacc[c]);
+}
+
+// Adam on FP32 master parameters
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, long long n, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    float gt = g[t];
+    float mt = b1 * m[t] + (1.0f - b1) * gt;
+    float vt = b2 * v[t] + (1.0f - b2) * gt * gt;
+    m[t] = mt;
+    v[t] = vt;
+    w[t] -= lr * (mt / c1) / (sqrtf(vt / c2) + eps);
+  }
+}
+
+// network output (FP32, 8 channels) to a potential field: phi = y0 * scale
+__global__ void k_nn_output(const float* __restrict__ y, long long vps, const float* __restrict__ scale,
+                            int B, float* __restrict__ phi) {
+  const long long n = (long long)B * vps;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x)
+    phi[v] = y[v * 8] * scale[v / vps];
+}
+
+static inline int ew_grid(long long n) {
+  long long b = (n + 255) / 256;
+  return (int)(b > 1216 ? 1216 : (b < 1 ? 1 : b));
+}
+
+void launch_relu_bwd(cudaStream_t st, void* dy, const void* y, long long n) {
+  k_relu_bwd<<<ew_grid(n), 256, 0, st>>>((bf16*)dy, (const bf16*)y, n);
+  note_launch();
+}
+void launch_pool2(cudaStream_t st, const void* in, int B, int D, int H, int W, int C, void* out) {
+  Vol g{B, D, H, W};
+  k_pool2<<<ew_grid(g.voxels() * C / 8), 256, 0, st>>>((const bf16*)in, g, C, (bf16*)out);
+  note_launch();
+}
+void launch_pool2_bwd(cudaStream_t st, const void* dout, int B, int D, int H, int W, int C,
+                      void* din) {
+  Vol g{B, D, H, W};
+  k_pool2_bwd<<<ew_grid(g.voxels() * C), 256, 0, st>>>((const bf16*)dout, g, C, (bf16*)din);
+  note_launch();
+}
+void launch_up2(cudaStream_t st, const void* in, int B, int D, int H, int W, int C, void* out,
+                int Cout, int c0) {
+  Vol g{B, D, H, W};
+  k_up2<<<ew_grid(g.voxels() * C), 256, 0, st>>>((const bf16*)in, g, C, (bf16*)out, Cout, c0);
+  note_launch();
+}
+void launch_up2_bwd(cudaStream_t st, const void* dout, int B, int D, int H, int W, int Cout,
+                    int c0, int C, void* din) {
+  Vol g{B, D, H, W};
+  k_up2_bwd<<<ew_grid(g.voxels() * C / 8), 256, 0, st>>>((const bf16*)dout, g, Cout, c0, C,
+                                                          (bf16*)din);
+  note_launch();
+}
+void launch_chan_copy(cudaStream_t st, const void* src, long long nvox, int C, int Csrc, int s0,
+                      void* dst, int Cdst, int c0, bool add) {
+  k_chan_copy<<<ew_grid(nvox * C), 256, 0, st>>>((const bf16*)src, nvox, C, Csrc, s0, (bf16*)dst,
+                                                 Cdst, c0, add ? 1 : 0);
+  note_launch();
+}
+void launch_nn_input(cudaStream_t st, const float* f, long long vps, const float* scale, int B,
+                     void* x) {
+  k_nn_input<<<ew_grid((long long)B * vps * 8), 256, 0, st>>>(f, vps, scale, B, (bf16*)x);
+  note_launch();
+}
+void launch_mse(cudaStream_t st, const float* y, const float* target, long long vps,
+                const float* tscale, int B, void* dy, double* loss) {
+  k_mse<<<ew_grid((long long)B * vps), 256, 0, st>>>(y, target, vps, tscale, B, (bf16*)dy, loss);
+  note_launch();
+}
+void launch_resid_loss(cudaStream_t st, const float* y, const float* target, int B, int S,
+                       int per, const float* tscale, float* d, float* q, void* dy, double* loss) {
+  Vol g{B, S, S, S, per};
+  const long long vps = (long long)S * S * S, n = g.voxels();
+  k_loss_diff<<<ew_grid(n), 256, 0, st>>>(y, target, vps, tscale, B, d);
+  k_lap_loss<<<ew_grid(n), 256, 0, st>>>(d, g, q, loss);
+  k_lap_grad<<<ew_grid(n), 256, 0, st>>>(q, g, (bf16*)dy);
+  note_launch();
+  note_launch();
+  note_launch();
+}
+void launch_bias_grad(cudaStream_t st, const void* dy, long long nvox, int cout, int coutp,
+                      float* db) {
+  k_bias_grad<<<ew_grid(nvox * coutp), 256, 0, st>>>((const bf16*)dy, nvox, cout, coutp, db);
+  note_launch();
+}
+void launch_adam(cudaStream_t st, float* w, const float* g, float* m, float* v, long long n,
+                 float lr, float b1, float b2, float eps, float c1, float c2) {
+  k_adam<<<ew_grid(n), 256, 0, st>>>(w, g, m, v, n, lr, b1, b2, eps, c1, c2);
+  note_launch();
+}
+void launch_nn_output(cudaStream_t st, const float* y, long long vps, const float* scale, int B,
+                      float* phi) {
+  k_nn_output<<<ew_grid((long long)B * vps), 256, 0, st>>>(y, vps, scale, B, phi);
   note_launch();
 }
 

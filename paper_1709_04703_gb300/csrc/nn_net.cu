@@ -1,0 +1,440 @@
+// The learned initial guess: a small U-shaped 3-D convolutional network
+// (levels of 8/16/32/64 channels, 3x3x3 convolutions, 2x average pooling
+// down, nearest upsampling + skip concatenation up) evaluated and trained
+// with the BF16 tensor-core kernels of k_nn.cu.
+//
+// Architecture for L levels, channels c_l = 8 * 2^l:
+//   x   = [f * s_in, 1, 0 x 6]                   (8 channels; the constant
+//                                                 channel marks the domain)
+//   e_0 = relu(conv(x; 8 -> c_0)),  e_l = relu(conv(pool(e_{l-1}); c_{l-1} -> c_l))
+//   d_{L-1} = e_{L-1},  d_l = relu(conv([up(d_{l+1}), e_l]; c_{l+1} + c_l -> c_l))
+//   y   = conv(d_0; c_0 -> 8),  guess = y[channel 0] / s_in * out_scale
+// with s_in = 1 / rms(f) per sample (the map from source to potential is
+// linear, so the network sees unit-variance sources).  Convolutions pad with
+// zeros (open boundaries: the correction vanishes on the ghost layer) or wrap
+// (periodic domains).  Parameters are FP32
+// masters (per convolution in the order enc_0..enc_{L-1}, dec_{L-2}..dec_0,
+// out: weights [cout][27 cin] then biases [cout]), packed to BF16 operands
+// for the tensor cores; Adam updates the masters.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pm_kernels.cuh"
+
+using namespace pm;
+
+namespace {
+
+struct ConvL {
+  int cin, cout, relu;
+  int n, kp;    // forward GEMM: N (>= cout, multiple of 16), K padded to 64
+  int nt, kpt;  // input-gradient GEMM
+  long long w_off, b_off;  // offsets in the master parameter vector
+  void *wp = nullptr, *wt = nullptr;  // packed BF16 operands
+};
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+int mma_n(int c) { return round_up(c < 16 ? 16 : c, 16); }
+
+struct Buf {  // BF16 activation of one layer output
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct pm_guess {
+  int L = 4;
+  cudaStream_t st0 = nullptr;  // the stream given at creation
+  cudaStream_t st = nullptr;   // the stream of the current call
+  std::vector<ConvL> conv;
+  long long n_params = 0;
+  float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // FP32 masters, grads, Adam
+  long long adam_t = 0;
+  float out_scale = 1.0f;
+  // activations, sized for cap_vox full-resolution voxels
+  long long cap_vox = 0;
+  std::vector<Buf> act;  // named slots, see SLOT_* below
+  float* y = nullptr;     // FP32 network output [vox][8]
+  float *ld = nullptr, *lq = nullptr;  // FP32 scratch of the residual loss
+  float* scale_in = nullptr;   // per sample s_in
+  float* scale_out = nullptr;  // per sample out_scale / s_in
+  float* tscale = nullptr;     // per sample s_in / out_scale (training targets)
+  double* loss = nullptr;
+  int* err = nullptr;
+  bool packed = false;
+  std::string msg;
+};
+
+namespace {
+
+pm_status gfail(pm_guess* g, pm_status c, const std::string& m) {
+  if (g) g->msg = m;
+  return c;
+}
+
+// activation slots: for level l: x (l = 0 only), e_l, p_l (pooled input of
+// enc l), d_l, cat_l (concat input of dec l); plus scratch gradient buffers
+enum { SLOT_X = 0, SLOT_E = 1, SLOT_P = 5, SLOT_D = 9, SLOT_C = 13, SLOT_G0 = 17, SLOT_G1 = 18,
+       SLOT_G2 = 19, SLOT_N = 20 };
+
+long long vox(int B, int S, int l) {
+  long long s = S >> l;
+  return (long long)B * s * s * s;
+}
+
+pm_status ensure_shape(pm_guess* g, int B, int S) {
+  if (S % (1 << (g->L - 1)) != 0 || S < (1 << (g->L - 1)))
+    return gfail(g, PM_EINVAL, "guess: grid side must be a multiple of 2^(levels-1)");
+  // every slot holds a fixed number of values per full-resolution voxel
+  // (vox(B, S, l) = vox(B, S, 0) / 8^l), so a smaller shape reuses the
+  // buffers of a larger one
+  const long long need = vox(B, S, 0);
+  if (need <= g->cap_vox) return PM_OK;
+  for (auto& b : g->act)
+    if (b.p) cudaFree(b.p);
+  for (float* p : {g->y, g->ld, g->lq})
+    if (p) cudaFree(p);
+  g->y = g->ld = g->lq = nullptr;
+  g->cap_vox = 0;
+  g->act.assign(SLOT_N, Buf());
+  auto alloc = [&](int slot, long long elems) -> bool {
+    g->act[slot].bytes = (size_t)elems * 2;
+    return cudaMalloc(&g->act[slot].p, g->act[slot].bytes) == cudaSuccess;
+  };
+  bool ok = alloc(SLOT_X, vox(B, S, 0) * 8);
+  long long gmax = vox(B, S, 0) * 8;
+  for (int l = 0; l < g->L; ++l) {
+    int c = 8 << l;
+    ok = ok && alloc(SLOT_E + l, vox(B, S, l) * c);
+    if (l > 0) ok = ok && alloc(SLOT_P + l, vox(B, S, l) * (c / 2));
+    if (l < g->L - 1) {
+      ok = ok && alloc(SLOT_D + l, vox(B, S, l) * c);
+      ok = ok && alloc(SLOT_C + l, vox(B, S, l) * (c + 2 * c));
+      gmax = std::max(gmax, vox(B, S, l) * 3 * c);
+    }
+    gmax = std::max(gmax, vox(B, S, l) * c);
+  }
+  ok = ok && alloc(SLOT_G0, gmax) && alloc(SLOT_G1, gmax) && alloc(SLOT_G2, gmax);
+  ok = ok && cudaMalloc((void**)&g->y, sizeof(float) * need * 8) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&g->ld, sizeof(float) * need) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&g->lq, sizeof(float) * need) == cudaSuccess;
+  if (!ok) return gfail(g, PM_ENOMEM, "guess: activation allocation failed");
+  g->cap_vox = need;
+  return PM_OK;
+}
+
+void pack_all(pm_guess* g) {
+  for (auto& c : g->conv)
+    launch_pack_w(g->st, g->w + c.w_off, c.cin, c.cout, c.wp, c.n, c.kp, c.wt, c.nt, c.kpt);
+  g->packed = true;
+}
+
+// per-sample s_in = 1/rms(f)
+__global__ void k_rms(const float* __restrict__ f, long long vps, int B, float out_scale,
+                      float* __restrict__ sin_, float* __restrict__ sout,
+                      float* __restrict__ tsc) {
+  int b = blockIdx.x;
+  double acc = 0.0;
+  for (long long t = threadIdx.x; t < vps; t += blockDim.x) {
+    double x = f[b * vps + t];
+    acc += x * x;
+  }
+  __shared__ double sm[32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)blockDim.x / 32; ++w) t += sm[w];
+    double rms = sqrt(t / (double)vps);
+    float si = rms > 0 ? (float)(1.0 / rms) : 0.0f;
+    sin_[b] = si;
+    sout[b] = rms > 0 ? (float)(rms * out_scale) : 0.0f;
+    tsc[b] = rms > 0 ? (float)(1.0 / (rms * out_scale)) : 0.0f;
+  }
+}
+
+#define GCK()                                                                          \
+  do {                                                                                 \
+    cudaError_t e_ = cudaGetLastError();                                               \
+    if (e_ != cudaSuccess) return gfail(g, PM_ECUDA, cudaGetErrorString(e_));          \
+  } while (0)
+
+// forward pass for B samples of side S starting from f (FP32, B*S^3)
+pm_status forward(pm_guess* g, const float* f, int B, int S, int per) {
+  pm_status st = ensure_shape(g, B, S);
+  if (st != PM_OK) return st;
+  if (!g->packed) pack_all(g);
+  const long long vps = (long long)S * S * S;
+  k_rms<<<B, 256, 0, g->st>>>(f, vps, B, g->out_scale, g->scale_in, g->scale_out, g->tscale);
+  note_launch();
+  launch_nn_input(g->st, f, vps, g->scale_in, B, g->act[SLOT_X].p);
+  const int L = g->L;
+  int ci = 0;
+  // encoder
+  for (int l = 0; l < L; ++l) {
+    int s = S >> l;
+    const void* in = g->act[SLOT_X].p;
+    if (l > 0) {
+      launch_pool2(g->st, g->act[SLOT_E + l - 1].p, B, 2 * s, 2 * s, 2 * s, 8 << (l - 1),
+                   g->act[SLOT_P + l].p);
+      in = g->act[SLOT_P + l].p;
+    }
+    ConvL& c = g->conv[ci++];
+    launch_conv_fwd(g->st, in, B, s, s, s, per, c.cin, c.wp, c.n, c.kp, g->w + c.b_off, c.cout, 1,
+                    g->act[SLOT_E + l].p, nullptr, g->err);
+  }
+  // decoder
+  for (int l = L - 2; l >= 0; --l) {
+    int s = S >> l, cl = 8 << l, cu = 8 << (l + 1);
+    const void* up = (l + 1 == L - 1) ? g->act[SLOT_E + l + 1].p : g->act[SLOT_D + l + 1].p;
+    launch_up2(g->st, up, B, s, s, s, cu, g->act[SLOT_C + l].p, cu + cl, 0);
+    launch_chan_copy(g->st, g->act[SLOT_E + l].p, vox(B, S, l), cl, cl, 0, g->act[SLOT_C + l].p,
+                     cu + cl, cu, false);
+    ConvL& c = g->conv[ci++];
+    launch_conv_fwd(g->st, g->act[SLOT_C + l].p, B, s, s, s, per, c.cin, c.wp, c.n, c.kp,
+                    g->w + c.b_off, c.cout, 1, g->act[SLOT_D + l].p, nullptr, g->err);
+  }
+  ConvL& c = g->conv[ci];
+  const void* d0 = L == 1 ? g->act[SLOT_E].p : g->act[SLOT_D].p;
+  launch_conv_fwd(g->st, d0, B, S, S, S, per, c.cin, c.wp, c.n, c.kp, g->w + c.b_off, c.cout, 0,
+                  nullptr, g->y, g->err);
+  GCK();
+  return PM_OK;
+}
+
+// backward of a convolution: given dy (relu already applied), accumulate
+// dW, db and write dx (input gradient, BF16) unless dx == NULL
+void conv_bwd(pm_guess* g, ConvL& c, const void* x, int B, int s, int per, const void* dy,
+              void* dx) {
+  launch_conv_wgrad(g->st, x, B, s, s, s, per, c.cin, dy, c.cout, c.n, g->g + c.w_off, g->err);
+  launch_bias_grad(g->st, dy, (long long)B * s * s * s, c.cout, round_up(c.cout, 8),
+                   g->g + c.b_off);
+  if (dx)
+    launch_conv_fwd(g->st, dy, B, s, s, s, per, round_up(c.cout, 8), c.wt, c.nt, c.kpt,
+                    nullptr /*no bias*/, c.cin, 0, dx, nullptr, g->err);
+}
+
+// loss_kind 0: mean squared error of the output; 1: mean squared Laplacian
+// of the output error (the residual norm the solver measures)
+pm_status backward(pm_guess* g, const float* phi, int B, int S, int per, int loss_kind) {
+  const long long vps = (long long)S * S * S;
+  const int L = g->L;
+  cudaMemsetAsync(g->loss, 0, sizeof(double), g->st);
+  cudaMemsetAsync(g->g, 0, sizeof(float) * g->n_params, g->st);
+  void* G0 = g->act[SLOT_G0].p;
+  void* G1 = g->act[SLOT_G1].p;
+  void* G2 = g->act[SLOT_G2].p;
+  if (loss_kind == 1)
+    launch_resid_loss(g->st, g->y, phi, B, S, per, g->tscale, g->ld, g->lq, G0, g->loss);
+  else
+    launch_mse(g->st, g->y, phi, vps, g->tscale, B, G0, g->loss);
+  int ci = (int)g->conv.size() - 1;
+  // output convolution: dy in G0 (8 channels), input d_0
+  {
+    ConvL& c = g->conv[ci--];
+    const void* d0 = L == 1 ? g->act[SLOT_E].p : g->act[SLOT_D].p;
+    conv_bwd(g, c, d0, B, S, per, G0, G1);  // G1 = grad wrt d_0 (c_0 channels)
+  }
+  // decoder in reverse creation order: l = 0 .. L-2
+  for (int l = 0; l <= L - 2; ++l) {
+    int s = S >> l, cl = 8 << l, cu = 8 << (l + 1);
+    // G1 holds grad wrt d_l (cl channels): through the relu
+    launch_relu_bwd(g->st, G1, g->act[SLOT_D + l].p, vox(B, S, l) * cl);
+    ConvL& c = g->conv[ci--];
+    conv_bwd(g, c, g->act[SLOT_C + l].p, B, s, per, G1, G2);  // G2 = grad wrt cat_l
+    // skip branch: grad wrt e_l accumulates later; stash it in G0 (cl ch)
+    // up branch: grad wrt d_{l+1} (or e_{L-1}) = up2_bwd of channels [0, cu)
+    launch_up2_bwd(g->st, G2, B, s, s, s, cu + cl, 0, cu, G1);  // G1: grad at level l+1
+    // keep the skip gradient of level l in its own slot (reuse P slot memory? no:
+    // use the cat slot, which is no longer needed, as storage)
+    launch_chan_copy(g->st, G2, vox(B, S, l), cl, cu + cl, cu, g->act[SLOT_C + l].p, cl, 0,
+                     false);
+  }
+  // G1 now holds grad wrt d_{L-1} = e_{L-1} (top of the encoder)
+  for (int l = L - 1; l >= 0; --l) {
+    int s = S >> l, cl = 8 << l;
+    if (l < L - 1)  // add the skip gradient stored in cat slot l (cl channels)
+      launch_chan_copy(g->st, g->act[SLOT_C + l].p, vox(B, S, l), cl, cl, 0, G1, cl, 0, true);
+    launch_relu_bwd(g->st, G1, g->act[SLOT_E + l].p, vox(B, S, l) * cl);
+    ConvL& c = g->conv[ci--];
+    const void* in = l == 0 ? g->act[SLOT_X].p : g->act[SLOT_P + l].p;
+    conv_bwd(g, c, in, B, s, per, G1, l == 0 ? nullptr : G2);  // G2 = grad wrt pooled input
+    if (l > 0)  // through the pooling into grad wrt e_{l-1}
+      launch_pool2_bwd(g->st, G2, B, 2 * s, 2 * s, 2 * s, 8 << (l - 1), G1);
+  }
+  GCK();
+  return PM_OK;
+}
+
+}  // namespace
+
+// Entry points for the solver (api.cu): the guess of one source field of
+// side S on stream st, without synchronising; the MMA wait flag is read by
+// guess_check.
+bool pm::guess_fits(const pm_guess* g, int S) {
+  return g && S >= 16 && S % (1 << (g->L - 1)) == 0;
+}
+
+pm_status pm::guess_apply(pm_guess* g, cudaStream_t st, const float* src, int S, int per,
+                          float* out) {
+  g->st = st;
+  pm_status r = forward(g, src, 1, S, per);
+  if (r == PM_OK) launch_nn_output(st, g->y, (long long)S * S * S, g->scale_out, 1, out);
+  g->st = g->st0;
+  return r;
+}
+
+pm_status pm::guess_check(pm_guess* g, cudaStream_t st) {
+  int h = 0;
+  if (cudaMemcpyAsync(&h, g->err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return PM_ECUDA;
+  return h ? PM_ETIMEOUT : PM_OK;
+}
+
+extern "C" {
+
+pm_status pm_guess_create(int32_t levels, void* stream, pm_guess** out) {
+  if (!out || levels < 1 || levels > 4) return PM_EINVAL;
+  *out = nullptr;
+  pm_guess* g = new pm_guess();
+  g->L = levels;
+  g->st0 = g->st = (cudaStream_t)stream;
+  auto add = [&](int cin, int cout, int relu) {
+    ConvL c{};
+    c.cin = cin;
+    c.cout = cout;
+    c.relu = relu;
+    c.n = mma_n(cout);
+    c.kp = round_up(27 * cin, 64);
+    c.nt = mma_n(cin);
+    c.kpt = round_up(27 * round_up(cout, 8), 64);
+    c.w_off = g->n_params;
+    g->n_params += 27LL * cin * cout;
+    c.b_off = g->n_params;
+    g->n_params += cout;
+    g->conv.push_back(c);
+  };
+  for (int l = 0; l < levels; ++l) add(l == 0 ? 8 : 8 << (l - 1), 8 << l, 1);
+  for (int l = levels - 2; l >= 0; --l) add((8 << (l + 1)) + (8 << l), 8 << l, 1);
+  add(8, 8, 0);
+  bool ok = true;
+  for (auto& c : g->conv) {
+    ok = ok && cudaMalloc(&c.wp, (size_t)c.n * c.kp * 2) == cudaSuccess;
+    ok = ok && cudaMalloc(&c.wt, (size_t)c.nt * c.kpt * 2) == cudaSuccess;
+  }
+  size_t pb = sizeof(float) * g->n_params;
+  ok = ok && cudaMalloc((void**)&g->w, pb) == cudaSuccess &&
+       cudaMalloc((void**)&g->g, pb) == cudaSuccess &&
+       cudaMalloc((void**)&g->m, pb) == cudaSuccess &&
+       cudaMalloc((void**)&g->v, pb) == cudaSuccess &&
+       cudaMalloc((void**)&g->scale_in, sizeof(float) * 4096) == cudaSuccess &&
+       cudaMalloc((void**)&g->scale_out, sizeof(float) * 4096) == cudaSuccess &&
+       cudaMalloc((void**)&g->tscale, sizeof(float) * 4096) == cudaSuccess &&
+       cudaMalloc((void**)&g->loss, sizeof(double)) == cudaSuccess &&
+       cudaMalloc((void**)&g->err, sizeof(int)) == cudaSuccess;
+  if (!ok) {
+    pm_guess_destroy(g);
+    return PM_ENOMEM;
+  }
+  cudaMemsetAsync(g->w, 0, pb, g->st);
+  cudaMemsetAsync(g->m, 0, pb, g->st);
+  cudaMemsetAsync(g->v, 0, pb, g->st);
+  cudaMemsetAsync(g->err, 0, sizeof(int), g->st);
+  *out = g;
+  return PM_OK;
+}
+
+int64_t pm_guess_num_params(const pm_guess* g) { return g ? g->n_params : 0; }
+
+pm_status pm_guess_set_params(pm_guess* g, const float* host, float out_scale) {
+  if (!g || !host) return PM_EINVAL;
+  g->st = g->st0;
+  if (cudaMemcpyAsync(g->w, host, sizeof(float) * g->n_params, cudaMemcpyHostToDevice, g->st) !=
+      cudaSuccess)
+    return gfail(g, PM_ECUDA, "pm_guess_set_params: copy failed");
+  g->out_scale = out_scale;
+  g->packed = false;
+  g->adam_t = 0;
+  cudaMemsetAsync(g->m, 0, sizeof(float) * g->n_params, g->st);
+  cudaMemsetAsync(g->v, 0, sizeof(float) * g->n_params, g->st);
+  return cudaStreamSynchronize(g->st) == cudaSuccess ? PM_OK : PM_ECUDA;
+}
+
+pm_status pm_guess_get_params(pm_guess* g, float* host, float* grad_host) {
+  if (!g) return PM_EINVAL;
+  g->st = g->st0;
+  if (host) cudaMemcpyAsync(host, g->w, sizeof(float) * g->n_params, cudaMemcpyDeviceToHost, g->st);
+  if (grad_host)
+    cudaMemcpyAsync(grad_host, g->g, sizeof(float) * g->n_params, cudaMemcpyDeviceToHost, g->st);
+  return cudaStreamSynchronize(g->st) == cudaSuccess ? PM_OK : PM_ECUDA;
+}
+
+pm_status pm_guess_forward(pm_guess* g, const float* f_dev, int32_t B, int32_t S,
+                           int32_t periodic, float* phi_dev) {
+  if (!g || !f_dev || !phi_dev || B < 1 || B > 4096 || S < 1) return PM_EINVAL;
+  g->st = g->st0;
+  pm_status st = forward(g, f_dev, B, S, periodic ? 1 : 0);
+  if (st != PM_OK) return st;
+  launch_nn_output(g->st, g->y, (long long)S * S * S, g->scale_out, B, phi_dev);
+  int h = 0;
+  cudaMemcpyAsync(&h, g->err, sizeof(int), cudaMemcpyDeviceToHost, g->st);
+  if (cudaStreamSynchronize(g->st) != cudaSuccess) return gfail(g, PM_ECUDA, "forward");
+  if (h) return gfail(g, PM_ETIMEOUT, "guess: an MMA completion wait timed out");
+  return PM_OK;
+}
+
+pm_status pm_guess_loss_grad(pm_guess* g, const float* f_dev, const float* phi_dev, int32_t B,
+                             int32_t S, int32_t periodic, int32_t loss_kind, double* loss_out) {
+  if (!g || !f_dev || !phi_dev || B < 1 || B > 4096 || S < 1 || loss_kind < 0 || loss_kind > 1)
+    return PM_EINVAL;
+  g->st = g->st0;
+  pm_status st = forward(g, f_dev, B, S, periodic ? 1 : 0);
+  if (st != PM_OK) return st;
+  st = backward(g, phi_dev, B, S, periodic ? 1 : 0, loss_kind);
+  if (st != PM_OK) return st;
+  double h = 0.0;
+  int e = 0;
+  cudaMemcpyAsync(&h, g->loss, sizeof(double), cudaMemcpyDeviceToHost, g->st);
+  cudaMemcpyAsync(&e, g->err, sizeof(int), cudaMemcpyDeviceToHost, g->st);
+  if (cudaStreamSynchronize(g->st) != cudaSuccess) return gfail(g, PM_ECUDA, "loss_grad");
+  if (e) return gfail(g, PM_ETIMEOUT, "guess: an MMA completion wait timed out");
+  if (loss_out) *loss_out = h;
+  return PM_OK;
+}
+
+pm_status pm_guess_adam(pm_guess* g, float lr) {
+  if (!g) return PM_EINVAL;
+  g->st = g->st0;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  g->adam_t++;
+  float c1 = 1.0f - std::pow(b1, (float)g->adam_t), c2 = 1.0f - std::pow(b2, (float)g->adam_t);
+  launch_adam(g->st, g->w, g->g, g->m, g->v, g->n_params, lr, b1, b2, eps, c1, c2);
+  pack_all(g);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? PM_OK : gfail(g, PM_ECUDA, cudaGetErrorString(e));
+}
+
+const char* pm_guess_last_error(const pm_guess* g) { return g ? g->msg.c_str() : ""; }
+
+void pm_guess_destroy(pm_guess* g) {
+  if (!g) return;
+  if (g->st) cudaStreamSynchronize(g->st);
+  for (auto& c : g->conv) {
+    if (c.wp) cudaFree(c.wp);
+    if (c.wt) cudaFree(c.wt);
+  }
+  for (auto& b : g->act)
+    if (b.p) cudaFree(b.p);
+  void* ps[] = {g->y, g->ld, g->lq, g->w, g->g, g->m, g->v, g->scale_in, g->scale_out, g->tscale, g->loss, g->err};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  delete g;
+}
+
+}  // extern "C"

@@ -44,6 +44,8 @@ void launch_defect(cudaStream_t st, Grid ph, Grid pl, const Grid* e, Grid qh, Gr
                    unsigned int* counter, double* out);
 int defect_blocks(int s);
 void launch_correct(cudaStream_t st, Grid ph, Grid pl, Grid e);
+void launch_to_dense(cudaStream_t st, Grid g, float* d, bool add);
+void launch_from_dense(cudaStream_t st, const float* d, Grid g, bool add);
 void launch_predict(cudaStream_t st, Grid ph, Grid pl, Grid qh, Grid ql, float w, bool pair);
 void launch_fill(cudaStream_t st, Grid g, float v, bool with_ghost);
 void launch_phi_out(cudaStream_t st, Grid ph, Grid pl, float* out32, double* out64,
@@ -217,4 +219,37 @@ namespace pm {
 // k_nn.cu
 void launch_gemm_tc(cudaStream_t st, const void* A, const void* B, float* C, int M, int N,
                     int K, int* err);
+void launch_conv_fwd(cudaStream_t st, const void* in, int B, int D, int H, int W, int per,
+                     int cin, const void* wp, int n, int kp, const float* bias, int cout,
+                     int relu, void* out_bf, float* out_f, int* err);
+void launch_conv_wgrad(cudaStream_t st, const void* in, int B, int D, int H, int W, int per,
+                       int cin, const void* dy, int cout, int n, float* dw, int* err);
+void launch_resid_loss(cudaStream_t st, const float* y, const float* target, int B, int S,
+                       int per, const float* tscale, float* d, float* q, void* dy, double* loss);
+void launch_pack_w(cudaStream_t st, const float* w, int cin, int cout, void* wp, int n, int kp,
+                   void* wt, int nt, int kpt);
+void launch_relu_bwd(cudaStream_t st, void* dy, const void* y, long long n);
+void launch_pool2(cudaStream_t st, const void* in, int B, int D, int H, int W, int C, void* out);
+void launch_pool2_bwd(cudaStream_t st, const void* dout, int B, int D, int H, int W, int C,
+                      void* din);
+void launch_up2(cudaStream_t st, const void* in, int B, int D, int H, int W, int C, void* out,
+                int Cout, int c0);
+void launch_up2_bwd(cudaStream_t st, const void* dout, int B, int D, int H, int W, int Cout,
+                    int c0, int C, void* din);
+void launch_chan_copy(cudaStream_t st, const void* src, long long nvox, int C, int Csrc, int s0,
+                      void* dst, int Cdst, int c0, bool add);
+void launch_nn_input(cudaStream_t st, const float* f, long long vps, const float* scale, int B,
+                     void* x);
+void launch_mse(cudaStream_t st, const float* y, const float* target, long long vps,
+                const float* tscale, int B, void* dy, double* loss);
+void launch_bias_grad(cudaStream_t st, const void* dy, long long nvox, int cout, int coutp,
+                      float* db);
+void launch_adam(cudaStream_t st, float* w, const float* g, float* m, float* v, long long n,
+                 float lr, float b1, float b2, float eps, float c1, float c2);
+void launch_nn_output(cudaStream_t st, const float* y, long long vps, const float* scale, int B,
+                      float* phi);
+// the learned guess as seen by the solver (nn_net.cu)
+bool guess_fits(const pm_guess* g, int S);
+pm_status guess_apply(pm_guess* g, cudaStream_t st, const float* src, int S, int per, float* out);
+pm_status guess_check(pm_guess* g, cudaStream_t st);
 }  // namespace pm

@@ -8,7 +8,7 @@ import torch
 from . import _lib as L
 
 _PREC = {"mixed": L.PM_MIXED, "fp32": L.PM_FP32_PLAIN}
-_GUESS = {"warm": L.PM_GUESS_WARM, "zero": L.PM_GUESS_ZERO}
+_GUESS = {"warm": L.PM_GUESS_WARM, "zero": L.PM_GUESS_ZERO, "learned": L.PM_GUESS_LEARNED}
 _BC = {"paper": L.PM_BC_PAPER, "open": L.PM_BC_OPEN, "periodic": L.PM_BC_PERIODIC}
 
 
@@ -313,6 +313,24 @@ class Sim:
                                                _ptr(phi), _ptr(phi64), C.byref(vc),
                                                C.byref(res)))
         return phi, phi64, vc.value, res.value
+
+    # -- learned initial guess ---------------------------------------------
+    def set_guess(self, net):
+        """Attach a GuessNet (or None) for guess="learned"."""
+        self._net = net
+        self._check(self._lib.pm_set_guess(self._ctx, net._g if net is not None else None))
+
+    def capture(self, r, e):
+        """Arm (device float32 tensors of n_mesh^3 elements) or disarm (None,
+        None) the capture of (residual of the start, correction) pairs."""
+        if r is not None:
+            n3 = self.cfg.n_mesh ** 3
+            for t in (r, e):
+                if t.dtype != torch.float32 or not t.is_cuda or t.numel() < n3:
+                    raise ValueError("capture buffers: CUDA float32 of n_mesh^3 elements")
+        self._cap = (r, e)
+        torch.cuda.synchronize()
+        self._check(self._lib.pm_capture(self._ctx, _ptr(r), _ptr(e)))
 
     def profile(self, enable=True):
         self._check(self._lib.pm_profile(self._ctx, 1 if enable else 0))
