@@ -108,6 +108,16 @@ def conv_backward(x, w, g, periodic, need_dx=True):
     return dw, db, dx
 
 
+def conv_backward_abs(x, g, periodic):
+    """Sums of |terms| of dW and db (sum_v |x(v + tap)| |g(v)| and
+    sum_v |g(v)|): the scale of the rounding error of those sums."""
+    ax, ag = np.abs(x), np.abs(g)
+    dw = np.zeros((g.shape[-1], 27, x.shape[-1]))
+    for t, (dz, dy, dx) in enumerate(TAPS):
+        dw[:, t, :] = np.einsum('bzyxo,bzyxc->oc', ag, shift(ax, dz, dy, dx, periodic))
+    return dw, ag.sum(axis=(0, 1, 2, 3))
+
+
 def pool2(x):
     B, D, H, W, C = x.shape
     return x.reshape(B, D // 2, 2, H // 2, 2, W // 2, 2, C).mean(axis=(2, 4, 6))
@@ -189,10 +199,14 @@ def guess(params, r, L, periodic, out_scale=1.0, quant=False):
     return y[..., 0] * c['s_out'].reshape(-1, 1, 1, 1)
 
 
-def loss_grad(params, r, target, L, periodic, loss_kind, out_scale=1.0, quant=False):
+def loss_grad(params, r, target, L, periodic, loss_kind, out_scale=1.0, quant=False,
+              want_scale=False):
     """Loss and its gradient with respect to the flat parameter vector.
     t = target * t_scale (per sample); loss_kind 0: mean (y0 - t)^2;
-    1: mean (A (y0 - t))^2 with A the 7-point operator."""
+    1: mean (A (y0 - t))^2 with A the 7-point operator.  want_scale adds a
+    third result: per parameter, the sum of the absolute values of the terms
+    its gradient sums (where the terms cancel, the rounding error of the
+    gradient is measured against this)."""
     q = bf16 if quant else (lambda a: a)
     y, c = forward(params, r, L, periodic, out_scale, quant)
     B = r.shape[0]
@@ -208,10 +222,13 @@ def loss_grad(params, r, target, L, periodic, loss_kind, out_scale=1.0, quant=Fa
         gy[..., 0] = q(2.0 * laplacian(a, periodic) / n)
     P = c['P']
     grads = [None] * len(P)
+    scales = [None] * len(P)
     k = len(P) - 1
     w, _ = P[k]
     dw, db, g = conv_backward(c['d'][0], w, gy, periodic)
     grads[k] = (dw, db)
+    if want_scale:
+        scales[k] = conv_backward_abs(c['d'][0], gy, periodic)
     g = q(g)
     k -= 1
     skip = [None] * L
@@ -220,6 +237,8 @@ def loss_grad(params, r, target, L, periodic, loss_kind, out_scale=1.0, quant=Fa
         w, _ = P[k]
         dw, db, gcat = conv_backward(c['cat'][l], w, g, periodic)
         grads[k] = (dw, db)
+        if want_scale:
+            scales[k] = conv_backward_abs(c['cat'][l], g, periodic)
         k -= 1
         gcat = q(gcat)
         cu = 8 << (l + 1)
@@ -233,8 +252,13 @@ def loss_grad(params, r, target, L, periodic, loss_kind, out_scale=1.0, quant=Fa
         inp = c['x'] if l == 0 else c['p'][l]
         dw, db, gin = conv_backward(inp, w, g, periodic, need_dx=l > 0)
         grads[k] = (dw, db)
+        if want_scale:
+            scales[k] = conv_backward_abs(inp, g, periodic)
         k -= 1
         if l > 0:
             g = q(pool2_backward(q(gin)))
     flat = np.concatenate([np.concatenate([dw.reshape(-1), db]) for dw, db in grads])
+    if want_scale:
+        sc = np.concatenate([np.concatenate([dw.reshape(-1), db]) for dw, db in scales])
+        return loss, flat, sc
     return loss, flat

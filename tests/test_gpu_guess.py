@@ -25,15 +25,21 @@ def _net(L, params, out_scale):
     return GuessNet(L, params=params, out_scale=out_scale)
 
 
-def _inputs(L, S, B, seed):
+def _inputs(L, S, B, seed, periodic=False):
     rng = np.random.default_rng(seed)
     p = cn.init_params(L, rng).astype(np.float32)
     p += (0.02 * rng.standard_normal(p.size)).astype(np.float32)
     # a smooth-plus-noise source, like a residual field
     r = rng.standard_normal((B, S, S, S))
     r += 0.5 * np.roll(r, 1, axis=1) + 0.5 * np.roll(r, 1, axis=3)
-    t = rng.standard_normal((B, S, S, S)) * 0.7
-    return p, r.astype(np.float32), t.astype(np.float32)
+    r = r.astype(np.float32)
+    # targets correlated with the input, as potentials are with sources: the
+    # output of another network.  (With targets independent of the input
+    # the loss gradient is a small residue of cancelling terms and moves by
+    # tens of percent under BF16 storage alone.)
+    teacher = cn.init_params(L, np.random.default_rng(seed + 1000))
+    t = cn.guess(teacher, r.astype(np.float64), L, periodic, 0.5)
+    return p, r, t.astype(np.float32)
 
 
 def _rel(a, b):
@@ -48,7 +54,7 @@ CASES = [(2, 8, 2, False), (3, 20, 1, False), (3, 20, 1, True), (4, 16, 1, True)
 
 @pytest.mark.parametrize("L,S,B,periodic", CASES)
 def test_forward_matches_oracle(L, S, B, periodic):
-    p, r, _ = _inputs(L, S, B, 100 + S)
+    p, r, _ = _inputs(L, S, B, 100 + S, periodic)
     net = _net(L, p, 0.5)
     got = net.forward(torch.from_numpy(r).cuda(), periodic).cpu().numpy().astype(np.float64)
     ref = cn.guess(p.astype(np.float64), r.astype(np.float64), L, periodic, 0.5, quant=True)
@@ -62,19 +68,30 @@ def test_forward_matches_oracle(L, S, B, periodic):
 @pytest.mark.parametrize("L,S,B,periodic", CASES)
 @pytest.mark.parametrize("kind", [0, 1])
 def test_loss_and_gradient_match_oracle(L, S, B, periodic, kind):
-    p, r, t = _inputs(L, S, B, 200 + S + kind)
+    p, r, t = _inputs(L, S, B, 200 + S + kind, periodic)
     net = _net(L, p, 0.5)
     loss = net.loss_grad(torch.from_numpy(r).cuda(), torch.from_numpy(t).cuda(), periodic,
                          kind)
     g = net.grad().astype(np.float64)
-    rl, rg = cn.loss_grad(p.astype(np.float64), r.astype(np.float64), t.astype(np.float64),
-                          L, periodic, kind, 0.5, quant=True)
+    args = (p.astype(np.float64), r.astype(np.float64), t.astype(np.float64), L, periodic,
+            kind, 0.5)
+    rl, rg, sc = cn.loss_grad(*args, quant=True, want_scale=True)
+    _, rg64 = cn.loss_grad(*args)
     assert abs(loss - rl) <= 1e-2 * abs(rl)
     o = 0
     for ci, co, _ in cn.layers(L):
         nw = 27 * ci * co
         for a, b in ((slice(o, o + nw), "w"), (slice(o + nw, o + nw + co), "b")):
-            assert _rel(g[a], rg[a]) < 3e-2, (ci, co, b, _rel(g[a], rg[a]))
+            # against the oracle with the same BF16 storage: relative to the
+            # gradient or, where its terms cancel (the output bias under the
+            # periodic residual loss sums a Laplacian: zero), to the sum of
+            # the terms' magnitudes
+            err = np.linalg.norm(g[a] - rg[a])
+            assert err < 1.5e-2 * np.linalg.norm(rg[a]) or err < 1e-2 * np.linalg.norm(sc[a]), \
+                (ci, co, b, _rel(g[a], rg[a]), err / np.linalg.norm(sc[a]))
+            # and against the FP64 network: the whole effect of BF16 storage
+            err64 = np.linalg.norm(g[a] - rg64[a])
+            assert err64 < 8e-2 * np.linalg.norm(rg64[a]) or err64 < 1e-2 * np.linalg.norm(sc[a])
         o += nw + co
     net.close()
 
