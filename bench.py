@@ -106,10 +106,38 @@ def _ics():
     return ics.workload_ics(WORKLOAD), ics.WORKLOADS[WORKLOAD]
 
 
-def _new_sim(pos, mom, ids, cfg, rtol, precision):
+def _new_sim(pos, mom, ids, cfg, rtol, precision, guess="warm"):
     from paper_1709_04703_gb300.sim import Sim
     return Sim(pos, mom, ids, cfg["n"], cfg["box"], cfg["a_init"], cfg["a_final"],
-               cfg["steps"], rtol=rtol, precision=precision, max_vcycles=100)
+               cfg["steps"], rtol=rtol, precision=precision, max_vcycles=100, guess=guess)
+
+
+def _variant(pos, mom, ids, cfg, K, rtol, precision, guess="warm", net=None):
+    """The same K steps in another solver configuration, device-timed."""
+    import torch
+    from paper_1709_04703_gb300 import _lib as L
+    sim = _new_sim(pos, mom, ids, cfg, rtol, precision, guess)
+    if net is not None:
+        sim.set_guess(net)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(sim.stream)
+    out = {"precision": precision, "guess": guess, "rtol": rtol}
+    try:
+        sim.step(K)
+    except L.PmError as e:
+        st = sim.stats()
+        out.update(error=str(e), steps_done=st["step"], resid_last=st["resid_last"])
+        sim.close()
+        return out
+    ev1.record(sim.stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    st = sim.stats()
+    sim.close()
+    out.update(value=st["particle_steps"] / (ms * 1e-3), ms_per_step=ms / K,
+               vcycles_total=st["vcycles_total"], guess_used=st["guess_used_total"])
+    return out
 
 
 def cpu_baseline(budget_s=20.0, n_sample=128):
@@ -288,6 +316,18 @@ def run_ours(args):
               "n_lightcone": st["n_lightcone"], "escaped": st["escaped"]}
     sim.close()
 
+    # the same steps with plain FP32 V-cycles and with the learned guess
+    compare = None
+    if not args.no_compare:
+        from paper_1709_04703_gb300 import train_guess
+        compare = {"plain_fp32": _variant(pos, mom, ids, cfg, K, args.rtol, "fp32")}
+        net = train_guess.load(train_guess.DEFAULT_WEIGHTS)
+        compare["learned_guess"] = _variant(pos, mom, ids, cfg, K, args.rtol, args.precision,
+                                            "learned", net)
+        compare["learned_guess"]["weights"] = os.path.relpath(train_guess.DEFAULT_WEIGHTS,
+                                                              ROOT)
+        net.close()
+
     # end to end through the C ABI with host buffers (pinned)
     e2e = None
     if not args.no_e2e:
@@ -355,6 +395,8 @@ def run_ours(args):
     }
     if e2e is not None:
         line["e2e"] = e2e
+    if compare is not None:
+        line["compare"] = compare
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_budget)
     print(json.dumps(line), flush=True)
@@ -372,6 +414,8 @@ def main():
     ap.add_argument("--rtol", type=float, default=1e-7)
     ap.add_argument("--precision", choices=["mixed", "fp32"], default="mixed")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the plain-FP32 and learned-guess runs of the same steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--workload", choices=["pm256", "batch48"], default="pm256")

@@ -171,6 +171,9 @@ typedef struct {
   int64_t particle_steps;/* sum over completed steps of the active count */
   int32_t guess_used_last;  /* 1 if the network corrected the last solve's start */
   int64_t guess_used_total; /* solves started from the network's correction */
+  double resid_start;       /* relative residual of the last solve's start */
+  double resid_guess;       /* ... after the network's correction (= resid_start
+                               when the network did not run) */
 } pm_stats_t;
 
 pm_status pm_stats(pm_ctx* ctx, pm_stats_t* out);

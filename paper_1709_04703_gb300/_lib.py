@@ -55,6 +55,7 @@ class PmStats(C.Structure):
         ("vcycles_total", C.c_int64), ("resid_last", C.c_double),
         ("escaped", C.c_int64), ("particle_steps", C.c_int64),
         ("guess_used_last", C.c_int32), ("guess_used_total", C.c_int64),
+        ("resid_start", C.c_double), ("resid_guess", C.c_double),
     ]
 
 

@@ -189,6 +189,7 @@ struct pm_ctx {
   int vcycles_last = 0;
   long long vcycles_total = 0;
   double resid_last = 0.0;
+  double resid_start = 0.0, resid_guess = 0.0;  // of the last solve
   long long particle_steps = 0;
   std::string err;
 };
@@ -539,6 +540,10 @@ pm_status solve(pm_ctx* ctx) {
     if (st != PM_OK) return st;
     double f2 = ctx->h_scal[0], r2 = ctx->h_scal[11];
     rel = f2 > 0 ? std::sqrt(r2 / f2) : 0.0;
+    if (it == 0) {
+      if (!ctx->guess_used_last) ctx->resid_start = rel;
+      ctx->resid_guess = rel;
+    }
     if (rel <= ctx->cfg.rtol || f2 == 0.0) break;
     if (it >= ctx->cfg.max_vcycles) {
       ctx->vcycles_last = it;
@@ -1069,6 +1074,8 @@ pm_status pm_stats(pm_ctx* ctx, pm_stats_t* o) {
   o->particle_steps = ctx->particle_steps;
   o->guess_used_last = ctx->guess_used_last;
   o->guess_used_total = ctx->guess_used_total;
+  o->resid_start = ctx->resid_start;
+  o->resid_guess = ctx->resid_guess;
   return PM_OK;
 }
 
