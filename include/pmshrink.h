@@ -297,6 +297,21 @@ const char* pm_shrink_static_error(void);
  * tensor memory) that maps a source to a potential guess for the solver.
  * ------------------------------------------------------------------------- */
 
+/* The multigrid smoother of the Poisson solve (Sec. 2.1, Eq. 3 as the
+ * 7-point system h^-2 (sum_nb u - diag u) = b): two red-black Gauss-Seidel
+ * sweeps (red = (i+j+k) even first, then black, twice), u_out = S(u_in).
+ * Arrays are padded (s+2)^3 FP32 device arrays, [z][y][x], one ghost layer
+ * (read, never written).  periodic = 1 wraps instead; gam > 0 adds gam per
+ * ghost face to the diagonal 6 (the coarse-level open boundary).
+ * zero_start: u_in is taken as zero (ghosts included) and not read.
+ * fused = 1: one pass over the grid (u_in and u_out distinct unless
+ * zero_start); fused = 0: four one-colour passes in place on u_out after
+ * copying u_in.  Both give the same bits.  zchunk: planes per CTA of the
+ * fused pass (0 = default).  s even, >= 4.  Synchronises stream. */
+pm_status pm_mg_smooth(const float* u_in, float* u_out, const float* b, int32_t s,
+                       int32_t periodic, float h2, float gam, int32_t zero_start, int32_t fused,
+                       int32_t zchunk, void* stream);
+
 /* C[M x N] (FP32, row-major) = A[M x K] B[N x K]^T with A, B row-major BF16
  * device matrices; M % 128 == 0, K % 64 == 0, N in {16, 32, 64, 128}.  The
  * tile engine under every convolution of the learned guess.  PM_ETIMEOUT if

@@ -27,6 +27,7 @@ namespace {
 constexpr double C_OVER_H0 = 2997.92458;  // Mpc/h
 constexpr int SRC_GRID = 1216;            // 152 SMs x 8 blocks
 constexpr int COARSE_SWEEPS = 12;
+constexpr int FUSED_MIN = 192;  // smallest level side smoothed by the fused pass
 
 // ---------------------------------------------------------------------------
 // FP64 cosmology on the host.  tau(a) = int_0^a da'/(a'^2 E), H0 = 1, with
@@ -138,6 +139,7 @@ struct pm_ctx {
   int n_sol = 0;            // consecutive warm-startable solutions
   double ah_hist[2] = {0, 0};  // a_half of the last two solves
   std::vector<float*> lu, lb;   // level arrays (compact padded); level 0 for e / r
+  std::vector<float*> lu2;      // second iterate per level (u + P uc before post-smoothing)
   std::vector<int> ls;          // level sides of the current cube
 
   double* partial = nullptr;    // per-block FP64 partial sums
@@ -302,6 +304,7 @@ pm_status set_cube(pm_ctx* ctx, int lo, int s, int periodic, double R) {
     size_t bytes = sizeof(float) * (size_t)(ctx->ls[l] + 2) * (ctx->ls[l] + 2) * (ctx->ls[l] + 2);
     CK(cudaMemsetAsync(ctx->lu[l], 0, bytes, ctx->st));
     CK(cudaMemsetAsync(ctx->lb[l], 0, bytes, ctx->st));
+    CK(cudaMemsetAsync(ctx->lu2[l], 0, bytes, ctx->st));
   }
   return PM_OK;
 }
@@ -377,11 +380,16 @@ void smooth2(pm_ctx* ctx, Grid u, Grid b, float h2, int per, float g, bool zero_
   }
 }
 
-// V(2,2) cycle on level-0 grids (u0, b0).
+// V(2,2) cycle on level-0 grids (u0, b0).  On levels of side >= FUSED_MIN
+// the two pre- and two post-smoothing sweeps are each one fused pass
+// (k_rbgs2): the pre-smoothing starts from zero on every level but, in the
+// plain path, the finest one, where it writes a scratch grid instead of u0;
+// the prolongation writes u + P uc to a second grid that the post-smoothing
+// reads back into u.  Smaller levels take four one-colour passes in place.
 pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
   const int per = ctx->periodic;
   const int L = (int)ctx->ls.size() - 1;
-  Grid U[16], B[16];
+  Grid U[16], B[16], Upre[16];
   if (L >= 16) return fail(ctx, PM_EINVAL, "too many multigrid levels");
   U[0] = u0;
   B[0] = b0;
@@ -390,11 +398,10 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
     B[l] = compact_view(ctx->lb[l], ctx->ls[l]);
   }
   const double c0 = (double)ctx->s * ctx->s * ctx->s;
-  // algorithmic bytes: a colour launch reads u (4 B/cell) and half of b and
-  // writes half of u (8 B/cell); residual+restriction reads u and b
-  // (8 B/fine cell) and writes the coarse b and u (1 B/fine cell);
-  // prolongation reads the coarse u (0.5) and updates the fine u (8).
-  const double smooth_bytes = 4 * 8.0 * c0;
+  // algorithmic bytes per fine cell: pre-smoothing from zero reads b and
+  // writes u (8), otherwise reads u, b and writes u (12); residual +
+  // restriction reads u and b and writes the coarse b and u (9);
+  // prolongation reads u and the coarse u and writes u + P uc (8.5)
   float h2 = 1.0f;
   int ec = -1;
   // open-boundary ghost factor of level l (spacing H = 2^l), see k_mg.cu
@@ -405,12 +412,20 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
   for (int l = 0; l < Lc; ++l) {
     int e = l == 0 ? prof_begin(ctx) : -1;
     // below level 0 the restriction zeroes the coarse iterate
-    smooth2(ctx, U[l], B[l], h2, per, gam(l), l == 0 ? zero0 : true);
+    const bool zs = l == 0 ? zero0 : true;
+    const bool fused = ctx->ls[l] >= FUSED_MIN;
+    Upre[l] = (zs || !fused) ? U[l] : compact_view(ctx->lu[0], ctx->ls[0]);
+    if (fused && !zs && !per)  // the scratch grids take u0's Dirichlet ghost values
+      launch_copy_ghosts(ctx->st, U[0], Upre[0], compact_view(ctx->lu2[0], ctx->ls[0]));
+    if (fused)
+      launch_rbgs2(ctx->st, U[l], Upre[l], B[l], h2, per, gam(l), zs);
+    else
+      smooth2(ctx, U[l], B[l], h2, per, gam(l), zs);
     if (l == 0) {
-      prof_end(ctx, PM_PROF_SMOOTH0, e, smooth_bytes);
+      prof_end(ctx, PM_PROF_SMOOTH0, e, (fused ? (zs ? 8.0 : 12.0) : 32.0) * c0);
       e = prof_begin(ctx);
     }
-    launch_resid_restrict(ctx->st, U[l], B[l], 1.0f / h2, U[l + 1], B[l + 1], per, gam(l));
+    launch_resid_restrict(ctx->st, Upre[l], B[l], 1.0f / h2, U[l + 1], B[l + 1], per, gam(l));
     if (l == 0) {
       prof_end(ctx, PM_PROF_TRANSFER0, e, 9.0 * c0);
       ec = prof_begin(ctx);
@@ -426,13 +441,21 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
       prof_end(ctx, PM_PROF_COARSE, ec, (Lc > 0 ? 8.0 / 7.0 * 81.0 * c0 / 8.0 : 0.0));
       e = prof_begin(ctx);
     }
-    launch_prolong(ctx->st, U[l + 1], U[l], per, gam(l + 1));
+    const bool fused = ctx->ls[l] >= FUSED_MIN;
+    Grid W = compact_view(ctx->lu2[l], ctx->ls[l]);
+    if (fused)
+      launch_prolong_to(ctx->st, U[l + 1], Upre[l], W, per, gam(l + 1));
+    else
+      launch_prolong(ctx->st, U[l + 1], U[l], per, gam(l + 1));
     if (l == 0) {
       prof_end(ctx, PM_PROF_TRANSFER0, e, 8.5 * c0);
       e = prof_begin(ctx);
     }
-    smooth2(ctx, U[l], B[l], h2, per, gam(l), false);
-    if (l == 0) prof_end(ctx, PM_PROF_SMOOTH0, e, smooth_bytes);
+    if (fused)
+      launch_rbgs2(ctx->st, W, U[l], B[l], h2, per, gam(l), false);
+    else
+      smooth2(ctx, U[l], B[l], h2, per, gam(l), false);
+    if (l == 0) prof_end(ctx, PM_PROF_SMOOTH0, e, (fused ? 12.0 : 32.0) * c0);
   }
   if (Lc == 0) prof_end(ctx, PM_PROF_COARSE, ec, 0.0);
   CKL();
@@ -685,6 +708,8 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
   if (cfg->guess < PM_GUESS_WARM || cfg->guess > PM_GUESS_LEARNED)
     return fail(nullptr, PM_EINVAL, "pm_init: unknown guess");
 
+  if (mg_prepare() != cudaSuccess)
+    return fail(nullptr, PM_ECUDA, "pm_init: setting kernel attributes failed");
   ctx = new pm_ctx();
   ctx->cfg = *cfg;
   ctx->st = (cudaStream_t)stream;
@@ -751,6 +776,9 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
     ctx->lu.push_back(u);
     AL(b, bytes);
     ctx->lb.push_back(b);
+    float* u2 = nullptr;
+    AL(u2, bytes);
+    ctx->lu2.push_back(u2);
     if (sl <= 4 || sl % 2) break;
   }
   const int maxblk = std::max(std::max(SRC_GRID, defect_blocks(n)), 4096);
@@ -1238,6 +1266,7 @@ void pm_destroy(pm_ctx* ctx) {
     if (p) cudaFree(p);
   for (float* p : ctx->lu) if (p) cudaFree(p);
   for (float* p : ctx->lb) if (p) cudaFree(p);
+  for (float* p : ctx->lu2) if (p) cudaFree(p);
   drop_graph(ctx);
   for (auto& e : ctx->ev) cudaEventDestroy(e);
   if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
@@ -1955,6 +1984,43 @@ void pm_batch_destroy(pm_batch* B) {
 // ===========================================================================
 // Tensor-core building blocks of the learned guess
 // ===========================================================================
+extern "C" pm_status pm_mg_smooth(const float* u_in, float* u_out, const float* b, int32_t s,
+                                  int32_t periodic, float h2, float gam, int32_t zero_start,
+                                  int32_t fused, int32_t zchunk, void* stream) {
+  if (!u_out || !b || (!u_in && !zero_start) || s < 4 || (s & 1) || s > 2048 || zchunk < 0 ||
+      (fused && !zero_start && u_in == u_out))
+    return fail(nullptr, PM_EINVAL, "pm_mg_smooth: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (mg_prepare() != cudaSuccess) return fail(nullptr, PM_ECUDA, "pm_mg_smooth: attributes");
+  auto view = [&](const float* base) {
+    Grid g;
+    g.s = s;
+    g.sy = s + 2;
+    g.sz = (s + 2) * (s + 2);
+    g.base = const_cast<float*>(base) + 1 + g.sy + g.sz;
+    return g;
+  };
+  Grid wi = view(u_in ? u_in : u_out), wo = view(u_out), gb = view(b);
+  if (fused) {
+    launch_rbgs2(st, wi, wo, gb, h2, periodic, gam, zero_start != 0, zchunk);
+  } else {
+    const size_t bytes = sizeof(float) * (size_t)(s + 2) * (s + 2) * (s + 2);
+    if (zero_start && cudaMemsetAsync(u_out, 0, bytes, st) != cudaSuccess)
+      return fail(nullptr, PM_ECUDA, "pm_mg_smooth: clear");
+    if (!zero_start && u_in != u_out &&
+        cudaMemcpyAsync(u_out, u_in, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return fail(nullptr, PM_ECUDA, "pm_mg_smooth: copy");
+    for (int sw = 0; sw < 2; ++sw) {
+      launch_rbgs(st, wo, gb, h2, 0, periodic, gam, zero_start && sw == 0);
+      launch_rbgs(st, wo, gb, h2, 1, periodic, gam, false);
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(nullptr, PM_ECUDA, cudaGetErrorString(e));
+  return PM_OK;
+}
+
 extern "C" pm_status pm_nn_gemm_bf16(const void* A, const void* B, float* C, int32_t M,
                                      int32_t N, int32_t K, void* stream) {
   if (!A || !B || !C || M <= 0 || M % 128 || K <= 0 || K % 64 ||

@@ -24,6 +24,29 @@ __device__ __forceinline__ float bnd_diag(int i, int j, int k, int s, float gam)
   return 6.0f + gam * (float)nb;
 }
 
+// The update arithmetic of the smoother and the transfers, written with
+// explicit round-to-nearest operations so that every kernel that applies
+// them (one colour per launch, the fused two-sweep pass, the batched forms)
+// produces the same bits.
+__device__ __forceinline__ float nb6(float xm, float xp, float ym, float yp, float zm, float zp) {
+  return __fadd_rn(__fadd_rn(__fadd_rn(xm, xp), __fadd_rn(ym, yp)), __fadd_rn(zm, zp));
+}
+// Gauss-Seidel value (sum_nb u - h^2 b) / diag
+__device__ __forceinline__ float gs_value(float s0, float bv, float h2, bool simple, float diag) {
+  float t = __fsub_rn(s0, __fmul_rn(h2, bv));
+  return simple ? __fmul_rn(t, 1.0f / 6.0f) : __fdiv_rn(t, diag);
+}
+// residual b - (sum_nb u - diag u) / h^2
+__device__ __forceinline__ float resid_value(float s0, float uc, float bv, float diag,
+                                             float inv_h2) {
+  float lap = __fsub_rn(s0, __fmul_rn(diag, uc));
+  return __fsub_rn(bv, __fmul_rn(lap, inv_h2));
+}
+// trilinear weights 3/4, 1/4 per axis (x, then y, then z)
+__device__ __forceinline__ float lerp34(float a, float b) {
+  return __fadd_rn(__fmul_rn(0.75f, a), __fmul_rn(0.25f, b));
+}
+
 // zero_start (red only): the iterate is known to be zero, so the red cells
 // take (-h^2 b)/diag without reading u; the black sweep after it reads only
 // red neighbours, so u needs no clearing before a V-cycle.
@@ -52,21 +75,16 @@ __device__ __forceinline__ void d_rbgs(const BI& bi, Grid u, Grid b, float h2, i
     const int xm = wrap_m(i0, s, periodic) - i0;
     const int xp = wrap_p(i0, s, periodic) - i0;  // 1 unless i0 = s - 1 (then no i0 + 2)
     float xmid = p0[xp];  // right neighbour of i0, left of i0 + 2
-    s0 = (p0[xm] + xmid) + (p0[ym] + p0[yp]) + (p0[zm] + p0[zp]);
+    s0 = nb6(p0[xm], xmid, p0[ym], p0[yp], p0[zm], p0[zp]);
     if (two) {
       const int i1 = i0 + 2;
       const int xp1 = wrap_p(i1, s, periodic) - i1;
       float* p1 = p0 + 2;
-      s1 = (xmid + p1[xp1]) + (p1[ym] + p1[yp]) + (p1[zm] + p1[zp]);
+      s1 = nb6(xmid, p1[xp1], p1[ym], p1[yp], p1[zm], p1[zp]);
     }
   }
-  if (simple) {
-    p0[0] = (s0 - h2 * b0v) * (1.0f / 6.0f);
-    if (two) p0[2] = (s1 - h2 * b1v) * (1.0f / 6.0f);
-  } else {
-    p0[0] = (s0 - h2 * b0v) / bnd_diag(i0, j, k, s, gam);
-    if (two) p0[2] = (s1 - h2 * b1v) / bnd_diag(i0 + 2, j, k, s, gam);
-  }
+  p0[0] = gs_value(s0, b0v, h2, simple, simple ? 6.0f : bnd_diag(i0, j, k, s, gam));
+  if (two) p0[2] = gs_value(s1, b1v, h2, simple, simple ? 6.0f : bnd_diag(i0 + 2, j, k, s, gam));
 }
 
 __global__ void __launch_bounds__(256) k_rbgs(Grid u, Grid b, float h2, int color,
@@ -101,11 +119,11 @@ __device__ __forceinline__ void d_resid_restrict(const BI& bi, Grid u, Grid b, f
         int ym = (wrap_m(j, s, periodic) - j) * u.sy, yp = (wrap_p(j, s, periodic) - j) * u.sy;
         int zm = (wrap_m(k, s, periodic) - k) * u.sz, zp = (wrap_p(k, s, periodic) - k) * u.sz;
         float diag = (periodic || gam == 0.0f) ? 6.0f : bnd_diag(i, j, k, s, gam);
-        float lap = (p[xm] + p[xp]) + (p[ym] + p[yp]) + (p[zm] + p[zp]) - diag * p[0];
-        acc += b.base[gidx(b, i, j, k)] - lap * inv_h2;
+        float s0 = nb6(p[xm], p[xp], p[ym], p[yp], p[zm], p[zp]);
+        acc = __fadd_rn(acc, resid_value(s0, p[0], b.base[gidx(b, i, j, k)], diag, inv_h2));
       }
   int cc = gidx(uc, I, J, K);
-  bc.base[cc] = 0.125f * acc;
+  bc.base[cc] = __fmul_rn(0.125f, acc);
   uc.base[cc] = 0.0f;
 }
 
@@ -120,14 +138,9 @@ __global__ void __launch_bounds__(256) k_resid_restrict(Grid u, Grid b, float in
 // (weights 3/4 on the parent, 1/4 on the next coarse cell per axis).  Coarse
 // ghosts are zero (open) or wrap (periodic).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void d_prolong(const BI& bi, Grid uc, Grid u, int periodic,
-                                                 float gam_c){
-  const int s = u.s;
+__device__ __forceinline__ float prolong_value(Grid uc, int i, int j, int k, int periodic,
+                                               float gam_c) {
   const int sc = uc.s;
-  int i = bi.x * blockDim.x + threadIdx.x;
-  int j = bi.y * blockDim.y + threadIdx.y;
-  int k = bi.z;
-  if (i >= s || j >= s) return;
   int I = i >> 1, J = j >> 1, K = k >> 1;
   int I2 = (i & 1) ? I + 1 : I - 1;
   int J2 = (j & 1) ? J + 1 : J - 1;
@@ -145,19 +158,324 @@ __device__ __forceinline__ void d_prolong(const BI& bi, Grid uc, Grid u, int per
     if (K2 < 0 || K2 >= sc) { K2 = K; fz = -gam_c; }
   }
   const float* q = uc.base;
-  float c000 = q[gidx(uc, I, J, K)], c100 = fx * q[gidx(uc, I2, J, K)];
-  float c010 = fy * q[gidx(uc, I, J2, K)], c110 = fx * fy * q[gidx(uc, I2, J2, K)];
-  float c001 = fz * q[gidx(uc, I, J, K2)], c101 = fx * fz * q[gidx(uc, I2, J, K2)];
-  float c011 = fy * fz * q[gidx(uc, I, J2, K2)], c111 = fx * fy * fz * q[gidx(uc, I2, J2, K2)];
-  float a0 = 0.75f * c000 + 0.25f * c100, a1 = 0.75f * c010 + 0.25f * c110;
-  float a2 = 0.75f * c001 + 0.25f * c101, a3 = 0.75f * c011 + 0.25f * c111;
-  float b0 = 0.75f * a0 + 0.25f * a1, b1 = 0.75f * a2 + 0.25f * a3;
-  u.base[gidx(u, i, j, k)] += 0.75f * b0 + 0.25f * b1;
+  const float fxy = __fmul_rn(fx, fy), fxz = __fmul_rn(fx, fz), fyz = __fmul_rn(fy, fz);
+  const float fxyz = __fmul_rn(fxy, fz);
+  float c000 = q[gidx(uc, I, J, K)], c100 = __fmul_rn(fx, q[gidx(uc, I2, J, K)]);
+  float c010 = __fmul_rn(fy, q[gidx(uc, I, J2, K)]), c110 = __fmul_rn(fxy, q[gidx(uc, I2, J2, K)]);
+  float c001 = __fmul_rn(fz, q[gidx(uc, I, J, K2)]), c101 = __fmul_rn(fxz, q[gidx(uc, I2, J, K2)]);
+  float c011 = __fmul_rn(fyz, q[gidx(uc, I, J2, K2)]);
+  float c111 = __fmul_rn(fxyz, q[gidx(uc, I2, J2, K2)]);
+  float a0 = lerp34(c000, c100), a1 = lerp34(c010, c110);
+  float a2 = lerp34(c001, c101), a3 = lerp34(c011, c111);
+  return lerp34(lerp34(a0, a1), lerp34(a2, a3));
+}
+
+__device__ __forceinline__ void d_prolong(const BI& bi, Grid uc, Grid u, int periodic,
+                                                 float gam_c){
+  const int s = u.s;
+  int i = bi.x * blockDim.x + threadIdx.x;
+  int j = bi.y * blockDim.y + threadIdx.y;
+  int k = bi.z;
+  if (i >= s || j >= s) return;
+  float* p = u.base + gidx(u, i, j, k);
+  *p = __fadd_rn(*p, prolong_value(uc, i, j, k, periodic, gam_c));
+}
+
+// out-of-place form: w = u + P uc (w and u may be different layouts)
+__global__ void __launch_bounds__(256) k_prolong_to(Grid uc, Grid u, Grid w, int periodic,
+                                                    float gam_c) {
+  const int s = u.s;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z;
+  if (i >= s || j >= s) return;
+  w.base[gidx(w, i, j, k)] =
+      __fadd_rn(u.base[gidx(u, i, j, k)], prolong_value(uc, i, j, k, periodic, gam_c));
 }
 
 __global__ void __launch_bounds__(256) k_prolong(Grid uc, Grid u, int periodic,
                                                  float gam_c) {
   d_prolong(bi_native(), uc, u, periodic, gam_c);
+}
+
+// ---------------------------------------------------------------------------
+// Two RB-GS sweeps (red, black, red, black) in one pass: win -> wout.
+//
+// A CTA owns a 32 x 16 tile of (x, y) and a chunk of zc planes and marches
+// z.  Each of its 480 threads owns a pair of x-adjacent columns of the tile
+// + 4-cell halo (40 x 24 cells) and keeps their values on planes t-4 .. t+1
+// (and b on t-3 .. t) in registers; a ring of 5 planes in shared memory
+// exposes them to the neighbouring columns.  Step t updates
+//   red   on plane t   over the tile + 3   (old black values),
+//   black on plane t-1 over the tile + 2,
+//   red   on plane t-2 over the tile + 1,
+//   black on plane t-3 over the tile       (final: stored),
+// one cell of each pair per stage (the pair holds one cell of each colour).
+// Within a step no stage reads a shared-memory value written in the same
+// step (x/y neighbours live on the stage's own plane, written one step
+// earlier; z neighbours are the thread's own registers), so one barrier per
+// step suffices.  Every update applies gs_value to the values the four
+// one-colour launches would give it: the same bits.  win and wout must be
+// different arrays unless zero_start (win is then not read: the iterate
+// starts at zero, ghosts included).  Open boundaries: ghost cells are read,
+// never updated; periodic: coordinates wrap.  Needs s even.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int F2_TX = 32, F2_TY = 16, F2_H = 4;
+constexpr int F2_W = F2_TX + 2 * F2_H, F2_HH = F2_TY + 2 * F2_H;  // region 40 x 24
+constexpr int F2_PW = F2_W / 2;                                   // pairs per row
+constexpr int F2_NT = F2_PW * F2_HH;                              // 480 threads
+constexpr int F2_PL = F2_W * F2_HH;                               // floats per plane
+constexpr int F2_R = 8;        // shared ring depth (planes t-3 .. t+1 used; power of 2)
+constexpr int F2_D = 6;        // prefetch distance
+constexpr int F2_PR = 8;       // prefetch ring depth (>= F2_D + 2; power of 2)
+constexpr size_t F2_SMEM = sizeof(float) * (size_t)F2_PL * (F2_R + 2 * F2_PR);
+
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sa), "l"(gmem),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+}  // namespace
+
+// Registers hold each plane of the pair in colour order: R the red cell
+// ((x + y + p) even), K the black one; the red cell sits at x offset
+// r(p) = (y + p) & 1 of the pair.  A cell's z neighbours have the other
+// colour and the same x, i.e. the other register of the planes above and
+// below.  The in-pair x neighbour is the partner register; the other x
+// neighbour is in shared memory at offset -1 (cell at offset 0) or +2.  The
+// four stages of step t all update the cell at offset r(t) (the colours
+// alternate along z), and the register ring of six planes is renamed
+// statically by unrolling the step loop six times.
+template <bool PERIODIC, bool SIMPLE, bool ZERO>
+struct Rbgs2 {
+  static constexpr int RING = 6;
+  const Grid win, wout, b;
+  const float h2, gam;
+  const int s, x0, y0, z0, z1, ly, lx0, y, xa, me;
+  float* sp;
+  float* pu;
+  float* pb;
+  int uoff[2], boff[2];
+  unsigned rmask[2];  // bit h: the cell is updated by the stage covering tile + h
+  bool out_tile;
+  float R[RING], K[RING], BR[RING], BK[RING];  // plane t-4+m in slot (j + m) % 6
+
+  __device__ int zmem(int P) const {
+    if (PERIODIC) {
+      while (P < 0) P += s;
+      while (P >= s) P -= s;
+      return P;
+    }
+    return (P < -1 || P > s) ? -2 : P;
+  }
+
+  // asynchronous copy of u(P) and b(P) for this pair into prefetch slot P
+  __device__ void issue(int P) {
+    const int sl = P & (F2_PR - 1);
+    const int z = zmem(P);
+    const bool zok = z >= -1;
+    const float* gu = win.base - 1 - win.sy + (long long)(zok ? z : 0) * win.sz;
+    const float* gb = b.base - 1 - b.sy + (long long)(zok ? z : 0) * b.sz;
+    float* du = pu + sl * F2_PL + me;
+    float* db = pb + sl * F2_PL + me;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      if (ZERO) {
+        du[k] = 0.0f;
+      } else {
+        const bool ok = zok && uoff[k] >= 0;
+        cp_async4(du + k, gu + (ok ? uoff[k] : 0), ok);
+      }
+      const bool okb = zok && boff[k] >= 0;
+      cp_async4(db + k, gb + (okb ? boff[k] : 0), okb);
+    }
+    cp_async_commit();
+  }
+
+  // the prefetched plane P (cells in x order) into colour-ordered slot Q
+  template <int Q>
+  __device__ void take(int P) {
+    constexpr int q = Q;
+    const int sl = P & (F2_PR - 1);
+    const float* du = pu + sl * F2_PL + me;
+    const float* db = pb + sl * F2_PL + me;
+    const bool r1 = ((y + P) & 1) != 0;
+    const float a = du[0], c = du[1], e = db[0], f = db[1];
+    R[q] = r1 ? c : a;
+    K[q] = r1 ? a : c;
+    BR[q] = r1 ? f : e;
+    BK[q] = r1 ? e : f;
+  }
+
+  template <int Q>
+  __device__ void put(int p) {  // plane p (slot Q) into the shared ring
+    constexpr int q = Q;
+    float* d = sp + (p & (F2_R - 1)) * F2_PL + me;
+    const int r = (y + p) & 1;
+    d[r] = R[q];
+    d[1 - r] = K[q];
+  }
+
+  template <int J>
+  __device__ void step(int t) {
+    issue(t + F2_D + 1);
+    __syncthreads();
+    const int kc = (y + t) & 1;  // x offset of the cell updated by all four stages
+    const unsigned mask = kc ? rmask[1] : rmask[0];
+    const int xo = kc ? 1 : -1;
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+      const int p = t - st;
+      const int m = 4 - st;
+      const int q = (J + m) % RING, qm = (J + m - 1) % RING, qp = (J + m + 1) % RING;
+      const bool zact = (st == 0 || (st == 1 ? p >= z0 - 2 : st == 2 ? (p >= z0 - 1 && p <= z1)
+                                                                      : (p >= z0 && p < z1))) &&
+                        (PERIODIC || (p >= 0 && p < s));
+      if (zact && ((mask >> (3 - st)) & 1u)) {
+        float* c = sp + (p & (F2_R - 1)) * F2_PL + me + kc;
+        const float xv = c[xo], ym = c[-F2_W], yp = c[F2_W];
+        float nv;
+        if ((st & 1) == 0) {  // red: partner and z neighbours are black
+          const float s0 = nb6(xv, K[q], ym, yp, K[qm], K[qp]);
+          nv = SIMPLE ? gs_value(s0, BR[q], h2, true, 6.0f)
+                      : gs_value(s0, BR[q], h2, false, bnd_diag(xa + kc, y, p, s, gam));
+          R[q] = nv;
+        } else {              // black: partner and z neighbours are red
+          const float s0 = nb6(xv, R[q], ym, yp, R[qm], R[qp]);
+          nv = SIMPLE ? gs_value(s0, BK[q], h2, true, 6.0f)
+                      : gs_value(s0, BK[q], h2, false, bnd_diag(xa + kc, y, p, s, gam));
+          K[q] = nv;
+        }
+        *c = nv;
+      }
+    }
+    if (t - 3 >= z0 && t - 3 < z1 && out_tile) {
+      constexpr int q1 = (J + 1) % RING;  // plane t-3
+      const int r = (y + t - 3) & 1;
+      float* g = wout.base + (long long)(t - 3) * wout.sz + (xa + y * wout.sy);
+      if (xa < s && y < s) g[0] = r ? K[q1] : R[q1];
+      if (xa + 1 < s && y < s) g[1] = r ? R[q1] : K[q1];
+    }
+    put<(J + 5) % RING>(t + 1);
+    cp_async_wait<F2_D - 1>();
+    take<J % RING>(t + 2);  // the slot of plane t-4 takes plane t+2
+  }
+};
+
+template <bool PERIODIC, bool SIMPLE, bool ZERO>
+__global__ void __launch_bounds__(F2_NT, 2) k_rbgs2(Grid win, Grid wout, Grid b, float h2,
+                                                    float gam, int zc) {
+  extern __shared__ float f2_smem[];
+  const int s = wout.s;
+  const int ly = threadIdx.x / F2_PW, lx0 = 2 * (threadIdx.x - ly * F2_PW);
+  const int x0 = blockIdx.x * F2_TX, y0 = blockIdx.y * F2_TY, z0 = blockIdx.z * zc;
+  Rbgs2<PERIODIC, SIMPLE, ZERO> g{win, wout, b, h2, gam, s, x0, y0, z0, min(z0 + zc, s), ly,
+                                  lx0, y0 - F2_H + ly, x0 - F2_H + lx0, ly * F2_W + lx0};
+  g.sp = f2_smem;
+  g.pu = g.sp + F2_R * F2_PL;
+  g.pb = g.pu + F2_PR * F2_PL;
+  auto mc = [&](int v) -> int {
+    if (PERIODIC) {
+      v %= s;
+      return v < 0 ? v + s : v;
+    }
+    return (v < -1 || v > s) ? -(1 << 30) : v;
+  };
+  {
+    const int yy = mc(g.y);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int xx = mc(g.xa + k);
+      const bool ok = xx >= -1 && yy >= -1;
+      g.uoff[k] = ok ? (xx + 1) + (yy + 1) * win.sy : -1;
+      g.boff[k] = ok ? (xx + 1) + (yy + 1) * b.sy : -1;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    unsigned mk = 0;
+    const int lx = lx0 + k, x = g.xa + k;
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const bool in = lx >= F2_H - h && lx < F2_H + F2_TX + h && ly >= F2_H - h &&
+                      ly < F2_H + F2_TY + h &&
+                      (PERIODIC || (x >= 0 && x < s && g.y >= 0 && g.y < s));
+      mk |= (in ? 1u : 0u) << h;
+    }
+    g.rmask[k] = mk;
+  }
+  g.out_tile = ly >= F2_H && ly < F2_H + F2_TY && lx0 >= F2_H && lx0 < F2_H + F2_TX;
+#pragma unroll
+  for (int m = 0; m < 6; ++m) g.R[m] = g.K[m] = g.BR[m] = g.BK[m] = 0.0f;
+  const int tz = z0 - 3;  // first step; it needs planes tz-1 .. tz+1
+  for (int P = tz - 1; P <= tz + F2_D; ++P) g.issue(P);
+  cp_async_wait<F2_D - 1>();  // groups tz-1 .. tz+1 have landed
+  g.template take<3>(tz - 1);
+  g.template take<4>(tz);
+  g.template take<5>(tz + 1);
+  g.template put<4>(tz);
+  const int tend = g.z1 + 2;
+  for (int t = tz; t <= tend; t += 6) {
+    g.template step<0>(t);
+    if (t + 1 <= tend) g.template step<1>(t + 1); else break;
+    if (t + 2 <= tend) g.template step<2>(t + 2); else break;
+    if (t + 3 <= tend) g.template step<3>(t + 3); else break;
+    if (t + 4 <= tend) g.template step<4>(t + 4); else break;
+    if (t + 5 <= tend) g.template step<5>(t + 5); else break;
+  }
+  cp_async_wait<0>();
+}
+
+// kernel attributes that must be set outside any stream capture
+cudaError_t mg_prepare() {
+  cudaError_t e = cudaSuccess;
+  auto set = [&](auto k) {
+    cudaError_t r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)F2_SMEM);
+    if (r != cudaSuccess) e = r;
+  };
+  set(k_rbgs2<false, false, false>);
+  set(k_rbgs2<false, false, true>);
+  set(k_rbgs2<false, true, false>);
+  set(k_rbgs2<false, true, true>);
+  set(k_rbgs2<true, true, false>);
+  set(k_rbgs2<true, true, true>);
+  return e;
+}
+
+int rbgs2_zchunk(int s) {
+  // long chunks (each costs 6 extra steps), but at least ~2 CTAs per SM
+  const long long tiles = (long long)((s + F2_TX - 1) / F2_TX) * ((s + F2_TY - 1) / F2_TY);
+  int zc = 64;
+  while (zc > 8 && tiles * ((s + zc - 1) / zc) < 304) zc /= 2;
+  return zc;
+}
+
+void launch_rbgs2(cudaStream_t st, Grid win, Grid wout, Grid b, float h2, int periodic,
+                  float gam, bool zero_start, int zc) {
+  if (zc <= 0) zc = rbgs2_zchunk(wout.s);
+  dim3 grid((unsigned)((wout.s + F2_TX - 1) / F2_TX), (unsigned)((wout.s + F2_TY - 1) / F2_TY),
+            (unsigned)((wout.s + zc - 1) / zc));
+  const bool simple = periodic || gam == 0.0f;
+#define PM_RBGS2(P, S, Z) k_rbgs2<P, S, Z><<<grid, F2_NT, F2_SMEM, st>>>(win, wout, b, h2, gam, zc)
+  if (periodic) {
+    if (zero_start) PM_RBGS2(true, true, true); else PM_RBGS2(true, true, false);
+  } else if (simple) {
+    if (zero_start) PM_RBGS2(false, true, true); else PM_RBGS2(false, true, false);
+  } else {
+    if (zero_start) PM_RBGS2(false, false, true); else PM_RBGS2(false, false, false);
+  }
+#undef PM_RBGS2
+  note_launch();
 }
 
 // ---------------------------------------------------------------------------
@@ -394,6 +712,34 @@ void launch_resid_restrict(cudaStream_t st, Grid u, Grid b, float inv_h2, Grid u
                            int periodic, float gam) {
   k_resid_restrict<<<grid_full(uc.s), dim3(32, 8), 0, st>>>(u, b, inv_h2, uc, bc, periodic,
                                                             gam);
+  note_launch();
+}
+// ghost layer of src copied into d1 and d2 (same side, any layouts)
+__global__ void k_copy_ghosts(Grid src, Grid d1, Grid d2) {
+  const int s = src.s, n = s + 2;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 6 * n * n;
+       t += gridDim.x * blockDim.x) {
+    const int f = t / (n * n), r = t - f * n * n;
+    const int a = r % n - 1, c = r / n - 1, side = (f & 1) ? s : -1;
+    int i, j, k;
+    if (f < 2) { i = side; j = a; k = c; }
+    else if (f < 4) { i = a; j = side; k = c; }
+    else { i = a; j = c; k = side; }
+    const float v = src.base[gidx(src, i, j, k)];
+    d1.base[gidx(d1, i, j, k)] = v;
+    d2.base[gidx(d2, i, j, k)] = v;
+  }
+}
+
+void launch_copy_ghosts(cudaStream_t st, Grid src, Grid d1, Grid d2) {
+  const int n = src.s + 2;
+  int blocks = (6 * n * n + 255) / 256;
+  k_copy_ghosts<<<blocks < 1024 ? blocks : 1024, 256, 0, st>>>(src, d1, d2);
+  note_launch();
+}
+
+void launch_prolong_to(cudaStream_t st, Grid uc, Grid u, Grid w, int periodic, float gam_c) {
+  k_prolong_to<<<grid_full(u.s), dim3(32, 8), 0, st>>>(uc, u, w, periodic, gam_c);
   note_launch();
 }
 void launch_prolong(cudaStream_t st, Grid uc, Grid u, int periodic, float gam_c) {

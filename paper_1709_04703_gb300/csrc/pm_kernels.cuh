@@ -37,6 +37,12 @@ void launch_coarse_mg(cudaStream_t st, Grid u, Grid b, int level, int periodic,
                       int coarse_sweeps, bool zero_top);
 void launch_resid_restrict(cudaStream_t st, Grid u, Grid b, float inv_h2, Grid uc, Grid bc,
                            int periodic, float gam);
+void launch_prolong_to(cudaStream_t st, Grid uc, Grid u, Grid w, int periodic, float gam_c);
+void launch_copy_ghosts(cudaStream_t st, Grid src, Grid d1, Grid d2);
+void launch_rbgs2(cudaStream_t st, Grid win, Grid wout, Grid b, float h2, int periodic, float gam,
+                  bool zero_start, int zc = 0);
+int rbgs2_zchunk(int s);
+cudaError_t mg_prepare();
 void launch_prolong(cudaStream_t st, Grid uc, Grid u, int periodic, float gam_c);
 // residual of Phi (e == NULL) or of Phi + e written to (qh, ql) (e != NULL)
 void launch_defect(cudaStream_t st, Grid ph, Grid pl, const Grid* e, Grid qh, Grid ql,

@@ -122,6 +122,33 @@ def load(path):
     return GuessNet(int(z["levels"]), params=z["params"], out_scale=float(z["out_scale"]))
 
 
+def compare(workload, weights=DEFAULT_WEIGHTS, modes=("warm", "learned"), steps=None):
+    """The same realisation solved from each start: V-cycles, time and the
+    factor by which the network shrank the start residual."""
+    cfg = dict(ics.WORKLOADS[workload])
+    out = {"workload": workload, "weights": os.path.basename(weights)}
+    for mode in modes:
+        net = load(weights) if mode == "learned" else None
+        r = evaluate(cfg, net, guess=mode, steps=steps, profile=True)
+        if net is not None:
+            net.close()
+        prof = r.pop("profile")
+        row = {k: r[k] for k in ("steps", "vcycles_total", "guess_used", "particle_steps")}
+        row["ms"] = round(r["ms"], 2)
+        row["particle_steps_per_s"] = r["particle_steps"] / (r["ms"] * 1e-3)
+        row["guess_ms"] = round(prof["guess"]["ms"], 2)
+        row["vcycle_ms"] = round(sum(prof[k]["ms"] for k in
+                                     ("smooth0", "transfer0", "coarse", "defect")), 2)
+        if mode == "learned":
+            ratio = [g / s for g, s, u in zip(r["resid_guess"], r["resid_start"], r["vcycles"])
+                     if s > 0]
+            row["resid_ratio_median"] = float(np.median(ratio))
+        out[mode] = row
+    if "warm" in out and "learned" in out:
+        out["vcycles_saved"] = out["warm"]["vcycles_total"] - out["learned"]["vcycles_total"]
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--workload", default="pm256")
@@ -131,10 +158,19 @@ def main(argv=None):
     ap.add_argument("--levels", type=int, default=4)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--init", default=None, help="start from saved weights")
-    ap.add_argument("--out", required=True)
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--eval", action="store_true",
+                    help="compare warm and learned starts on --workload instead of training")
+    ap.add_argument("--weights", default=DEFAULT_WEIGHTS)
+    ap.add_argument("--modes", nargs="+", default=["warm", "learned"])
     a = ap.parse_args(argv)
     from . import build
     build.build()
+    if a.eval:
+        print(json.dumps(compare(a.workload, a.weights, a.modes, a.steps)))
+        return 0
+    if not a.out:
+        ap.error("--out is required for training")
     net = load(a.init) if a.init else GuessNet(a.levels, out_scale=1.0)
     cfgs = []
     for s in a.seeds:

@@ -24,11 +24,11 @@ def _realisation(n, box, seed, a0):
     return dict(pos=pos, mom=mom, ids=ids, n_mesh=n, box=box)
 
 
-def _single(re, a0, a1, steps, rtol):
+def _single(re, a0, a1, steps, rtol, k=None):
     from paper_1709_04703_gb300.sim import Sim
     sim = Sim(re["pos"], re["mom"], re["ids"], re["n_mesh"], re["box"], a0, a1, steps,
               rtol=rtol)
-    sim.step(steps)
+    sim.step(steps if k is None else k)
     out = sim.particles(), sim.lightcone(), sim.stats()
     sim.close()
     return out
@@ -97,4 +97,19 @@ def test_many_open_realisations():
     for r in (0, 17, 39):
         assert batch.stats(r)["periodic"] == 0
         _compare(batch, r, _single(reals[r], a0, a1, steps, 1e-7))
+    batch.close()
+
+
+def test_fused_finest_level_matches_batched_passes():
+    """At n = 192 a single context smooths its finest level with the fused
+    two-sweep pass; the batched step uses one-colour passes: the same bits,
+    in the periodic and in the open phase."""
+    from paper_1709_04703_gb300.sim import Batch
+    a0, a1, steps, rtol = 0.4, 1.0, 8, 1e-7
+    reals = [_realisation(192, 6000.0, 300, a0)]
+    batch = Batch(reals, a0, a1, steps, rtol=rtol)
+    batch.step(4)   # periodic 192, open 192, open 192, open 128
+    ref = _single(reals[0], a0, a1, steps, rtol, 4)
+    _compare(batch, 0, ref)
+    assert ref[2]["periodic"] == 0
     batch.close()

@@ -1,0 +1,94 @@
+"""The multigrid smoother (two red-black Gauss-Seidel sweeps of the 7-point
+system of Eq. 3): the fused one-pass kernel against the four one-colour
+passes (same bits) and against an FP64 statement of the sweeps."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from paper_1709_04703_gb300 import _lib as L  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1709_04703_gb300 import build
+    build.build()
+    return L.load()
+
+
+def _p(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def _smooth(lib, u, b, s, periodic, h2, gam, zero, fused, zchunk=0):
+    out = torch.full_like(u, float("nan")) if (fused and not zero) else u.clone()
+    uin = u if not zero else None
+    code = lib.pm_mg_smooth(_p(uin) if uin is not None else None, _p(out), _p(b), s,
+                            int(periodic), C.c_float(h2), C.c_float(gam), int(zero), int(fused),
+                            int(zchunk), None)
+    assert code == L.PM_OK, lib.pm_last_error(None)
+    return out
+
+
+def _inputs(s, seed):
+    rng = np.random.default_rng(seed)
+    u = rng.standard_normal((s + 2,) * 3).astype(np.float32)
+    b = rng.standard_normal((s + 2,) * 3).astype(np.float32)
+    return torch.from_numpy(u).cuda(), torch.from_numpy(b).cuda()
+
+
+CASES = [(s, per, gam) for s in (8, 24, 32, 48, 64, 100) for per, gam in
+         ((0, 0.0), (1, 0.0), (0, 3.0 / 5.0))]
+
+
+@pytest.mark.parametrize("s,periodic,gam", CASES)
+@pytest.mark.parametrize("zero", [0, 1])
+def test_fused_pass_gives_the_same_bits(lib, s, periodic, gam, zero):
+    u, b = _inputs(s, 10 * s + periodic + zero)
+    h2 = 4.0 if gam else 1.0
+    ref = _smooth(lib, u, b, s, periodic, h2, gam, zero, fused=0)
+    for zc in (0, 5, 16):
+        got = _smooth(lib, u, b, s, periodic, h2, gam, zero, fused=1, zchunk=zc)
+        a = got[1:-1, 1:-1, 1:-1].cpu().numpy()
+        r = ref[1:-1, 1:-1, 1:-1].cpu().numpy()
+        assert np.array_equal(a.view(np.uint32), r.view(np.uint32)), (zc, np.abs(a - r).max())
+
+
+def _sweeps_fp64(u, b, s, periodic, h2, gam, zero):
+    """Red then black, twice, in FP64 (ghosts read as stored; periodic wraps)."""
+    u = np.zeros_like(u, dtype=np.float64) if zero else u.astype(np.float64)
+    b = b.astype(np.float64)
+    idx = np.arange(s)
+    Z, Y, X = np.meshgrid(idx, idx, idx, indexing="ij")
+    nghost = sum((c == e).astype(np.int64) for c in (X, Y, Z) for e in (0, s - 1))
+    diag = 6.0 + (0.0 if periodic else gam) * nghost
+    for _ in range(2):
+        for colour in (0, 1):
+            v = u[1:-1, 1:-1, 1:-1]
+            if periodic:
+                nb = sum(np.roll(v, sh, axis=ax) for ax in range(3) for sh in (1, -1))
+            else:
+                nb = (u[2:, 1:-1, 1:-1] + u[:-2, 1:-1, 1:-1] + u[1:-1, 2:, 1:-1]
+                      + u[1:-1, :-2, 1:-1] + u[1:-1, 1:-1, 2:] + u[1:-1, 1:-1, :-2])
+            new = (nb - h2 * b[1:-1, 1:-1, 1:-1]) / diag
+            m = (X + Y + Z) % 2 == colour
+            v[m] = new[m]
+    return u
+
+
+@pytest.mark.parametrize("s,periodic,gam", [(8, 0, 0.0), (12, 1, 0.0), (16, 0, 1.0 / 3.0)])
+@pytest.mark.parametrize("zero", [0, 1])
+def test_fused_pass_matches_fp64_sweeps(lib, s, periodic, gam, zero):
+    u, b = _inputs(s, 7 + s)
+    if zero:
+        u = torch.zeros_like(u)
+    got = _smooth(lib, u, b, s, periodic, 2.0, gam, zero, fused=1)
+    ref = _sweeps_fp64(u.cpu().numpy(), b.cpu().numpy(), s, periodic, 2.0, gam, zero)
+    np.testing.assert_allclose(got[1:-1, 1:-1, 1:-1].cpu().numpy(), ref[1:-1, 1:-1, 1:-1],
+                               rtol=1e-5, atol=1e-5 * np.abs(ref).max())

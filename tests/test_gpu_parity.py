@@ -115,7 +115,8 @@ def _sim_for_solve(n, precision="mixed", rtol=1e-10):
                max_vcycles=60)
 
 
-@pytest.mark.parametrize("n", [16, 32, 48, 64])
+# 192 and up: the finest level is smoothed by the fused two-sweep pass
+@pytest.mark.parametrize("n", [16, 32, 48, 64, 192])
 def test_open_solve_matches_oracle(n):
     rng = np.random.default_rng(n)
     delta = rng.standard_normal((n, n, n))
@@ -133,7 +134,7 @@ def test_open_solve_matches_oracle(n):
     sim.close()
 
 
-@pytest.mark.parametrize("n", [32, 48])
+@pytest.mark.parametrize("n", [32, 48, 192])
 def test_periodic_solve_matches_oracle(n):
     rng = np.random.default_rng(100 + n)
     delta = rng.standard_normal((n, n, n))
@@ -166,8 +167,8 @@ def test_gaussian_closed_form_through_gpu():
     sim.close()
 
 
-def test_plain_fp32_solve_reaches_its_tolerance():
-    n = 32
+@pytest.mark.parametrize("n", [32, 192])
+def test_plain_fp32_solve_reaches_its_tolerance(n):
     rng = np.random.default_rng(3)
     delta = rng.standard_normal((n, n, n))
     sim = _sim_for_solve(n, precision="fp32", rtol=1e-4)
