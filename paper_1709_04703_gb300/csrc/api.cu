@@ -121,6 +121,7 @@ struct pm_ctx {
 
   float4 *pos = nullptr, *mom = nullptr, *pos2 = nullptr, *mom2 = nullptr;
   float4 *lc_pos = nullptr, *lc_mom = nullptr, *forces = nullptr;
+  float4* grad = nullptr;  // gradient field of the potential, (n+2)^3
   long long n_active = 0, n_lc = 0;
   bool forces_valid = false;
   long long forces_n = 0;
@@ -765,6 +766,7 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
     AL(ctx->phi_h[q], sizeof(float) * padded);
     AL(ctx->phi_l[q], sizeof(float) * padded);
   }
+  AL(ctx->grad, sizeof(float4) * padded);
   AL(ctx->f_hi, sizeof(float) * padded);
   AL(ctx->f_lo, sizeof(float) * padded);
   AL(ctx->prev_hi, sizeof(float) * padded);
@@ -903,14 +905,16 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
     float klo = 0.f, khi = 0.f;
     if (do_flag) keep_bounds(0.5 * n, R1, &klo, &khi);
     e = prof_begin(ctx);
+    // gradient field: read Phi hi + lo, write G (24 B/cell)
+    launch_grad(ctx->st, ctx->phi_h[ctx->cur], ctx->phi_l[ctx->cur], n, lo, s, per, ctx->grad);
     launch_gather_kick_drift(ctx->st, ctx->pos, ctx->mom, N, ctx->phi_h[ctx->cur],
-                             ctx->phi_l[ctx->cur], n, lo, s,
+                             ctx->phi_l[ctx->cur], ctx->grad, n, lo, s,
                              per, (float)(ctx->a_half[k] * ctx->dtau[k]),
                              (float)(ctx->dtau[k] / (2.0 * ctx->a[k + 1])), do_flag, klo, khi,
                              ctx->flags, ctx->block_keep, ctx->forces, ctx->d_cnt + 1);
-    // read x, p, write x, p (64 B/particle, + 1 B flag), read Phi hi + lo once
-    // (8 B/cell)
-    prof_end(ctx, PM_PROF_GATHER, e, (do_flag ? 65.0 : 64.0) * N + 8.0 * cells);
+    // gather: read x, p, write x, p (64 B/particle, + 1 B flag), read G once
+    // (16 B/cell)
+    prof_end(ctx, PM_PROF_GATHER, e, (do_flag ? 65.0 : 64.0) * N + (24.0 + 16.0) * cells);
     CKL();
     ctx->forces_valid = ctx->forces != nullptr;
     ctx->forces_n = N;
@@ -1261,7 +1265,7 @@ void pm_destroy(pm_ctx* ctx) {
                   ctx->f_lo, ctx->prev_hi, ctx->prev_lo,
                   ctx->partial, ctx->partial_m,
                   ctx->counter, ctx->d_scal, ctx->bgm, ctx->d_cnt, ctx->d_overflow,
-                  ctx->nn_in, ctx->nn_out};
+                  ctx->nn_in, ctx->nn_out, ctx->grad};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (float* p : ctx->lu) if (p) cudaFree(p);

@@ -769,55 +769,80 @@ __device__ __forceinline__ void d_defect(const BI& bi, Grid ph, Grid pl, Grid e,
   int i = bi.x * blockDim.x + threadIdx.x;
   int j = bi.y * blockDim.y + threadIdx.y;
   float r2 = 0.f;
-  for (int k = bi.z; k < s && i < s && j < s; k += bi.gz) {
-    int c = gidx(ph, i, j, k);
-    int xm = wrap_m(i, s, periodic) - i, xp = wrap_p(i, s, periodic) - i;
-    int ym = wrap_m(j, s, periodic) - j, yp = wrap_p(j, s, periodic) - j;
-    int zm = wrap_m(k, s, periodic) - k, zp = wrap_p(k, s, periodic) - k;
-    const int off[7] = {0, xm, xp, ym * ph.sy, yp * ph.sy, zm * ph.sz, zp * ph.sz};
-    float H[7], Lo[7];
-    const float* h = ph.base + c;
-    const float* l = pl.base + c;
-    // read-only loads (__ldg): lets the next plane's loads overlap this
-    // plane's stores, which go to other buffers
-#pragma unroll
-    for (int q = 0; q < 7; ++q) {
-      H[q] = __ldg(h + off[q]);
-      Lo[q] = __ldg(l + off[q]);
-    }
-    if (CORRECT) {
-      const float* ec = e.base + gidx(e, i, j, k);
-      const int eoff[7] = {0, xm, xp, ym * e.sy, yp * e.sy, zm * e.sz, zp * e.sz};
-#pragma unroll
-      for (int q = 0; q < 7; ++q) {
-        df t = two_sum(H[q], __ldg(ec + eoff[q]));
-        H[q] = t.hi;
-        Lo[q] = __fadd_rn(Lo[q], t.lo);
+  // a contiguous run of planes per thread; the (i, j) column's values at
+  // k-1, k, k+1 (with the correction added) roll through registers
+  const int chunk = (s + bi.gz - 1) / bi.gz;
+  const int k0 = bi.z * chunk, k1 = min(s, k0 + chunk);
+  if (i < s && j < s && k0 < k1) {
+    const int xm = wrap_m(i, s, periodic) - i, xp = wrap_p(i, s, periodic) - i;
+    const int ym = wrap_m(j, s, periodic) - j, yp = wrap_p(j, s, periodic) - j;
+    // the corrected double-float value of Phi at (i, j, kk)
+    auto column = [&](int kk, float& H, float& L) {
+      const int c = gidx(ph, i, j, kk);
+      H = __ldg(ph.base + c);
+      L = __ldg(pl.base + c);
+      if (CORRECT) {
+        df t = two_sum(H, __ldg(e.base + gidx(e, i, j, kk)));
+        H = t.hi;
+        L = __fadd_rn(L, t.lo);
       }
-      df n = fast_two_sum(H[0], Lo[0]);
-      int qc = gidx(qh, i, j, k);
-      qh.base[qc] = n.hi;
-      ql.base[qc] = n.lo;
-    }
-    int fc = gidx(fh, i, j, k);
-    // r = f - sum_nb + 6 phi: TwoSum cascade on the hi parts, rounding errors
-    // and lo parts in a float compensation term
-    float sacc = __ldg(fh.base + fc);
-    float comp = __ldg(fl.base + fc);
-    df t;
+    };
+    float Hm, Lm, Hc, Lc, Hp, Lp;
+    column(wrap_m(k0, s, periodic), Hm, Lm);
+    column(k0, Hc, Lc);
+    for (int k = k0; k < k1; ++k) {
+      column(wrap_p(k, s, periodic), Hp, Lp);
+      const int c = gidx(ph, i, j, k);
+      const int off[4] = {xm, xp, ym * ph.sy, yp * ph.sy};
+      float H[7], Lo[7];
+      H[0] = Hc;
+      Lo[0] = Lc;
+      const float* h = ph.base + c;
+      const float* l = pl.base + c;
 #pragma unroll
-    for (int q = 1; q < 7; ++q) {
-      t = two_sum(sacc, -H[q]);
-      sacc = t.hi;
-      comp += t.lo;
+      for (int q = 0; q < 4; ++q) {
+        H[q + 1] = __ldg(h + off[q]);
+        Lo[q + 1] = __ldg(l + off[q]);
+      }
+      H[5] = Hm;
+      Lo[5] = Lm;
+      H[6] = Hp;
+      Lo[6] = Lp;
+      if (CORRECT) {
+        const float* ec = e.base + gidx(e, i, j, k);
+        const int eoff[4] = {xm, xp, ym * e.sy, yp * e.sy};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          df t = two_sum(H[q + 1], __ldg(ec + eoff[q]));
+          H[q + 1] = t.hi;
+          Lo[q + 1] = __fadd_rn(Lo[q + 1], t.lo);
+        }
+        df n = fast_two_sum(H[0], Lo[0]);
+        int qc = gidx(qh, i, j, k);
+        qh.base[qc] = n.hi;
+        ql.base[qc] = n.lo;
+      }
+      int fc = gidx(fh, i, j, k);
+      // r = f - sum_nb + 6 phi: TwoSum cascade on the hi parts, rounding errors
+      // and lo parts in a float compensation term
+      float sacc = __ldg(fh.base + fc);
+      float comp = __ldg(fl.base + fc);
+      df t;
+#pragma unroll
+      for (int q = 1; q < 7; ++q) {
+        t = two_sum(sacc, -H[q]);
+        sacc = t.hi;
+        comp += t.lo;
+      }
+      df p6 = two_prod(6.0f, H[0]);
+      t = two_sum(sacc, p6.hi); sacc = t.hi; comp += t.lo + p6.lo;
+      comp -= (Lo[1] + Lo[2]) + (Lo[3] + Lo[4]) + (Lo[5] + Lo[6]);
+      comp += 6.0f * Lo[0];
+      float r = sacc + comp;
+      if (write_r) rb.base[gidx(rb, i, j, k)] = r;
+      r2 = __fmaf_rn(r, r, r2);
+      Hm = Hc; Lm = Lc; Hc = Hp; Lc = Lp;
     }
-    df p6 = two_prod(6.0f, H[0]);
-    t = two_sum(sacc, p6.hi); sacc = t.hi; comp += t.lo + p6.lo;
-    comp -= (Lo[1] + Lo[2]) + (Lo[3] + Lo[4]) + (Lo[5] + Lo[6]);
-    comp += 6.0f * Lo[0];
-    float r = sacc + comp;
-    if (write_r) rb.base[gidx(rb, i, j, k)] = r;
-    r2 = __fmaf_rn(r, r, r2);
   }
   __shared__ double sm[32];
   float vf = warp_sumf_all(r2);

@@ -12,16 +12,34 @@ constexpr int KITEMS = 4;        // particles per thread
 constexpr int KCHUNK = KT * KITEMS;
 
 // ---------------------------------------------------------------------------
-// K9.  For each particle: the 4 mesh indices per axis around its CIC nodes
-// (i-1, i, i+1, i+2; wrapped when periodic, ghost cells reached when open),
-// centred differences of Phi = hi + lo at the 8 nodes, weighted with
-// (2^16 - dq, dq) / 2^16, then p -= kick * grad(Phi), x = fl(x + fl(p * c2)),
-// and keep = x inside [klo, khi]^3 (exact float bounds of |x - c| <= R).
-// Block b covers particles [b*KCHUNK, (b+1)*KCHUNK) and writes its keep count.
+// Gradient + CIC gather + kick + drift + keep flag.  For each particle: the
+// CIC nodes (i, i+1 per axis; wrapped when periodic), the centred difference
+// of Phi = hi + lo at each node, g = (hi(i+1) - hi(i-1)) + (lo(i+1) -
+// lo(i-1)), weighted with (2^16 - dq, dq) / 2^16, then p -= kick grad(Phi),
+// x = fl(x + fl(p c2)), and keep = x inside [klo, khi]^3 (exact float bounds
+// of |x - c| <= R).  Block b covers particles [b KCHUNK, (b+1) KCHUNK) and
+// writes its keep count.
+//
+// GF: the node differences come from the gradient field G (k_grad, one
+// float4 per mesh cell: 8 loads per particle) instead of from Phi (32 mesh
+// points, hi and lo: 64 loads).  Both forms apply the same operations in the
+// same order, so they give the same bits.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void d_gather_kick_drift(const BI& bi, 
+__device__ __forceinline__ float gdiff(float hp, float hm, float lp, float lm) {
+  return __fadd_rn(__fsub_rn(hp, hm), __fsub_rn(lp, lm));
+}
+// F += wa wb (w0 g0 + w1 g1)
+__device__ __forceinline__ float cic_acc(float F, float wa, float wb, float w0, float g0,
+                                         float w1, float g1) {
+  const float inner = __fmaf_rn(w1, g1, __fmul_rn(w0, g0));
+  return __fmaf_rn(__fmul_rn(wa, wb), inner, F);
+}
+
+template <bool GF>
+__device__ __forceinline__ void d_gather_kick_drift(const BI& bi,
     float4* __restrict__ pos, float4* __restrict__ mom, long long N,
-    const float* __restrict__ ph, const float* __restrict__ pl, int n, int lo, int s,
+    const float* __restrict__ ph, const float* __restrict__ pl,
+    const float4* __restrict__ G, int n, int lo, int s,
     int periodic, float kick, float c2, int do_flag, float klo, float khi,
     unsigned char* __restrict__ flags, unsigned int* __restrict__ block_keep,
     float4* __restrict__ forces, unsigned long long* __restrict__ escaped){
@@ -66,88 +84,109 @@ __device__ __forceinline__ void d_gather_kick_drift(const BI& bi,
       const float wx[2] = {(float)(65536 - dx) * sc, (float)dx * sc};
       const float wy[2] = {(float)(65536 - dy) * sc, (float)dy * sc};
       const float wz[2] = {(float)(65536 - dz) * sc, (float)dz * sc};
-      int RY[4], RZ[4];
+      int RY[4], RZ[4], CX[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         RY[q] = (Y[q] + 1) * P;
         RZ[q] = (Z[q] + 1) * P * P;
+        CX[q] = X[q] + 1;
       }
-      int CX[4];
+      // gx/gy/gz[c][b][a]: the centred differences at node (X[a+1], Y[b+1], Z[c+1])
+      float gx[2][2][2], gy[2][2][2], gz[2][2][2];
+      if (GF) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) CX[q] = X[q] + 1;
-      // The 8 nodes' centred differences touch 32 distinct mesh points: the
-      // 16 of the x-rows (y, z in the node range), plus 8 more in y and 8 in
-      // z; each is loaded once (hi and lo).
-      float Hx[2][2][4], Lx[2][2][4];  // [c][b][q]: (X[q], Y[b+1], Z[c+1])
-      float Hy[2][2][2], Ly[2][2][2];  // [c][a][e]: (X[a+1], Y[3e], Z[c+1])
-      float Hz[2][2][2], Lz[2][2][2];  // [b][a][e]: (X[a+1], Y[b+1], Z[3e])
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+          for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+              const float4 g = __ldg(G + RZ[c + 1] + RY[b + 1] + CX[a + 1]);
+              gx[c][b][a] = g.x;
+              gy[c][b][a] = g.y;
+              gz[c][b][a] = g.z;
+            }
+      } else {
+        // the 8 nodes' centred differences touch 32 distinct mesh points:
+        // the 16 of the x-rows (y, z in the node range), plus 8 more in y
+        // and 8 in z; each is loaded once (hi and lo)
+        float Hx[2][2][4], Lx[2][2][4];  // [c][b][q]: (X[q], Y[b+1], Z[c+1])
+        float Hy[2][2][2], Ly[2][2][2];  // [c][a][e]: (X[a+1], Y[3e], Z[c+1])
+        float Hz[2][2][2], Lz[2][2][2];  // [b][a][e]: (X[a+1], Y[b+1], Z[3e])
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+          for (int b = 0; b < 2; ++b) {
+            int r = RZ[c + 1] + RY[b + 1];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              Hx[c][b][q] = ph[r + CX[q]];
+              Lx[c][b][q] = pl[r + CX[q]];
+            }
+          }
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+          for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              int r = RZ[c + 1] + RY[3 * e] + CX[a + 1];
+              Hy[c][a][e] = ph[r];
+              Ly[c][a][e] = pl[r];
+            }
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              int r = RZ[3 * e] + RY[b + 1] + CX[a + 1];
+              Hz[b][a][e] = ph[r];
+              Lz[b][a][e] = pl[r];
+            }
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+          for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+              gx[c][b][a] = gdiff(Hx[c][b][a + 2], Hx[c][b][a], Lx[c][b][a + 2], Lx[c][b][a]);
+              // y: node Y[b+1] takes Y[b+2] - Y[b]
+              const float yp = b == 0 ? Hx[c][1][a + 1] : Hy[c][a][1];
+              const float ym = b == 0 ? Hy[c][a][0] : Hx[c][0][a + 1];
+              const float lyp = b == 0 ? Lx[c][1][a + 1] : Ly[c][a][1];
+              const float lym = b == 0 ? Ly[c][a][0] : Lx[c][0][a + 1];
+              gy[c][b][a] = gdiff(yp, ym, lyp, lym);
+              const float zp = c == 0 ? Hx[1][b][a + 1] : Hz[b][a][1];
+              const float zm = c == 0 ? Hz[b][a][0] : Hx[0][b][a + 1];
+              const float lzp = c == 0 ? Lx[1][b][a + 1] : Lz[b][a][1];
+              const float lzm = c == 0 ? Lz[b][a][0] : Lx[0][b][a + 1];
+              gz[c][b][a] = gdiff(zp, zm, lzp, lzm);
+            }
+      }
 #pragma unroll
       for (int c = 0; c < 2; ++c)
 #pragma unroll
-        for (int b = 0; b < 2; ++b) {
-          int r = RZ[c + 1] + RY[b + 1];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            Hx[c][b][q] = ph[r + CX[q]];
-            Lx[c][b][q] = pl[r + CX[q]];
-          }
-        }
+        for (int b = 0; b < 2; ++b)
+          Fx = cic_acc(Fx, wy[b], wz[c], wx[0], gx[c][b][0], wx[1], gx[c][b][1]);
 #pragma unroll
       for (int c = 0; c < 2; ++c)
 #pragma unroll
         for (int a = 0; a < 2; ++a)
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            int r = RZ[c + 1] + RY[3 * e] + CX[a + 1];
-            Hy[c][a][e] = ph[r];
-            Ly[c][a][e] = pl[r];
-          }
+          Fy = cic_acc(Fy, wx[a], wz[c], wy[0], gy[c][0][a], wy[1], gy[c][1][a]);
 #pragma unroll
       for (int b = 0; b < 2; ++b)
 #pragma unroll
         for (int a = 0; a < 2; ++a)
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            int r = RZ[3 * e] + RY[b + 1] + CX[a + 1];
-            Hz[b][a][e] = ph[r];
-            Lz[b][a][e] = pl[r];
-          }
-      // differences first (hi and lo separately), then the CIC weights
-#pragma unroll
-      for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-          float g0 = (Hx[c][b][2] - Hx[c][b][0]) + (Lx[c][b][2] - Lx[c][b][0]);
-          float g1 = (Hx[c][b][3] - Hx[c][b][1]) + (Lx[c][b][3] - Lx[c][b][1]);
-          Fx += wy[b] * wz[c] * (wx[0] * g0 + wx[1] * g1);
-        }
-#pragma unroll
-      for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int a = 0; a < 2; ++a) {
-          // y node 0: Y[2] - Y[0];  y node 1: Y[3] - Y[1]
-          float g0 = (Hx[c][1][a + 1] - Hy[c][a][0]) + (Lx[c][1][a + 1] - Ly[c][a][0]);
-          float g1 = (Hy[c][a][1] - Hx[c][0][a + 1]) + (Ly[c][a][1] - Lx[c][0][a + 1]);
-          Fy += wx[a] * wz[c] * (wy[0] * g0 + wy[1] * g1);
-        }
-#pragma unroll
-      for (int b = 0; b < 2; ++b)
-#pragma unroll
-        for (int a = 0; a < 2; ++a) {
-          // z node 0: Z[2] - Z[0];  z node 1: Z[3] - Z[1]
-          float g0 = (Hx[1][b][a + 1] - Hz[b][a][0]) + (Lx[1][b][a + 1] - Lz[b][a][0]);
-          float g1 = (Hz[b][a][1] - Hx[0][b][a + 1]) + (Lz[b][a][1] - Lx[0][b][a + 1]);
-          Fz += wx[a] * wy[b] * (wz[0] * g0 + wz[1] * g1);
-        }
-      Fx *= 0.5f;
-      Fy *= 0.5f;
-      Fz *= 0.5f;
+          Fz = cic_acc(Fz, wx[a], wy[b], wz[0], gz[0][b][a], wz[1], gz[1][b][a]);
+      Fx = __fmul_rn(Fx, 0.5f);
+      Fy = __fmul_rn(Fy, 0.5f);
+      Fz = __fmul_rn(Fz, 0.5f);
     } else {
       ++esc;
     }
-    v.x -= kick * Fx;
-    v.y -= kick * Fy;
-    v.z -= kick * Fz;
+    v.x = __fmaf_rn(-kick, Fx, v.x);
+    v.y = __fmaf_rn(-kick, Fy, v.y);
+    v.z = __fmaf_rn(-kick, Fz, v.z);
     x.x = __fadd_rn(x.x, __fmul_rn(v.x, c2));
     x.y = __fadd_rn(x.y, __fmul_rn(v.y, c2));
     x.z = __fadd_rn(x.z, __fmul_rn(v.z, c2));
@@ -188,26 +227,63 @@ __device__ __forceinline__ void d_gather_kick_drift(const BI& bi,
   }
 }
 
+template <bool GF>
 __global__ void __launch_bounds__(KT) k_gather_kick_drift(
     float4* __restrict__ pos, float4* __restrict__ mom, long long N,
-    const float* __restrict__ ph, const float* __restrict__ pl, int n, int lo, int s,
-    int periodic, float kick, float c2, int do_flag, float klo, float khi,
+    const float* __restrict__ ph, const float* __restrict__ pl, const float4* __restrict__ G,
+    int n, int lo, int s, int periodic, float kick, float c2, int do_flag, float klo, float khi,
     unsigned char* __restrict__ flags, unsigned int* __restrict__ block_keep,
     float4* __restrict__ forces, unsigned long long* __restrict__ escaped) {
-  d_gather_kick_drift(bi_native(), pos, mom, N, ph, pl, n, lo, s, periodic, kick, c2, do_flag, klo, khi, flags, block_keep, forces, escaped);
+  d_gather_kick_drift<GF>(bi_native(), pos, mom, N, ph, pl, G, n, lo, s, periodic, kick, c2,
+                          do_flag, klo, khi, flags, block_keep, forces, escaped);
+}
+
+// G(c) = (gx, gy, gz, 0): centred differences of Phi = hi + lo at every cell
+// of the active cube (wrapped when periodic, ghost values when open), in the
+// full (n+2)^3 layout of Phi.
+__global__ void __launch_bounds__(256) k_grad(const float* __restrict__ ph,
+                                              const float* __restrict__ pl, int n, int lo,
+                                              int s, int periodic, float4* __restrict__ G) {
+  const int P = n + 2;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= s || j >= s) return;
+  const int X = lo + i, Y = lo + j, Z = lo + k;
+  auto w = [&](int a) { return periodic ? (a < 0 ? a + n : (a >= n ? a - n : a)) : a; };
+  const long long c = ((long long)(Z + 1) * P + (Y + 1)) * P + (X + 1);
+  const long long xm = ((long long)(Z + 1) * P + (Y + 1)) * P + (w(X - 1) + 1);
+  const long long xp = ((long long)(Z + 1) * P + (Y + 1)) * P + (w(X + 1) + 1);
+  const long long ym = ((long long)(Z + 1) * P + (w(Y - 1) + 1)) * P + (X + 1);
+  const long long yp = ((long long)(Z + 1) * P + (w(Y + 1) + 1)) * P + (X + 1);
+  const long long zm = ((long long)(w(Z - 1) + 1) * P + (Y + 1)) * P + (X + 1);
+  const long long zp = ((long long)(w(Z + 1) + 1) * P + (Y + 1)) * P + (X + 1);
+  G[c] = make_float4(gdiff(ph[xp], ph[xm], pl[xp], pl[xm]), gdiff(ph[yp], ph[ym], pl[yp], pl[ym]),
+                     gdiff(ph[zp], ph[zm], pl[zp], pl[zm]), 0.0f);
 }
 
 int gkd_blocks(long long N) { return (int)((N + KCHUNK - 1) / KCHUNK); }
 
 void launch_gather_kick_drift(cudaStream_t st, float4* pos, float4* mom, long long N,
-                              const float* ph, const float* pl, int n, int lo, int s,
-                              int periodic, float kick, float c2, bool do_flag, float klo,
+                              const float* ph, const float* pl, const float4* G, int n, int lo,
+                              int s, int periodic, float kick, float c2, bool do_flag, float klo,
                               float khi, unsigned char* flags, unsigned int* block_keep,
                               float4* forces, unsigned long long* escaped) {
   if (N <= 0) return;
-  k_gather_kick_drift<<<gkd_blocks(N), KT, 0, st>>>(pos, mom, N, ph, pl, n, lo, s, periodic,
-                                                    kick, c2, do_flag ? 1 : 0, klo, khi, flags,
-                                                    block_keep, forces, escaped);
+  if (G)
+    k_gather_kick_drift<true><<<gkd_blocks(N), KT, 0, st>>>(
+        pos, mom, N, ph, pl, G, n, lo, s, periodic, kick, c2, do_flag ? 1 : 0, klo, khi, flags,
+        block_keep, forces, escaped);
+  else
+    k_gather_kick_drift<false><<<gkd_blocks(N), KT, 0, st>>>(
+        pos, mom, N, ph, pl, G, n, lo, s, periodic, kick, c2, do_flag ? 1 : 0, klo, khi, flags,
+        block_keep, forces, escaped);
+  note_launch();
+}
+
+void launch_grad(cudaStream_t st, const float* ph, const float* pl, int n, int lo, int s,
+                 int periodic, float4* G) {
+  dim3 grid((unsigned)((s + 31) / 32), (unsigned)((s + 7) / 8), (unsigned)s);
+  k_grad<<<grid, dim3(32, 8), 0, st>>>(ph, pl, n, lo, s, periodic, G);
   note_launch();
 }
 
@@ -379,8 +455,9 @@ __global__ void __launch_bounds__(KT) kb_gather(const GatherDesc* d, const BTabl
   BI bi;
   if (!batch_map(d, t, (const int*)nullptr, q, bi)) return;
   const GatherDesc& e = d[q];
-  d_gather_kick_drift(bi, e.pos, e.mom, e.N, e.ph, e.pl, e.n, e.lo, e.s, e.periodic, e.kick,
-                      e.c2, e.do_flag, e.klo, e.khi, e.flags, e.block_keep, e.forces, e.escaped);
+  d_gather_kick_drift<false>(bi, e.pos, e.mom, e.N, e.ph, e.pl, nullptr, e.n, e.lo, e.s,
+                             e.periodic, e.kick, e.c2, e.do_flag, e.klo, e.khi, e.flags,
+                             e.block_keep, e.forces, e.escaped);
 }
 __global__ void __launch_bounds__(1024) kb_scan(const ScanDesc* d, const BTable* t) {
   int q;

@@ -61,11 +61,14 @@ void launch_sum_phi(cudaStream_t st, Grid ph, Grid pl, double* partial, unsigned
 
 // k_part.cu
 int gkd_blocks(long long N);
+// G: gradient field of k_grad (NULL: differences taken from Phi directly)
 void launch_gather_kick_drift(cudaStream_t st, float4* pos, float4* mom, long long N,
-                              const float* ph, const float* pl, int n, int lo, int s,
-                              int periodic, float kick, float c2, bool do_flag, float klo,
+                              const float* ph, const float* pl, const float4* G, int n, int lo,
+                              int s, int periodic, float kick, float c2, bool do_flag, float klo,
                               float khi, unsigned char* flags, unsigned int* block_keep,
                               float4* forces, unsigned long long* escaped);
+void launch_grad(cudaStream_t st, const float* ph, const float* pl, int n, int lo, int s,
+                 int periodic, float4* G);
 void launch_flag(cudaStream_t st, const float4* pos, long long N, float klo, float khi,
                  unsigned char* flags, unsigned int* block_keep);
 void launch_scan_blocks(cudaStream_t st, const unsigned int* cnt, unsigned long long* off,
