@@ -105,6 +105,30 @@ __device__ __forceinline__ void d_resid_restrict(const BI& bi, Grid u, Grid b, f
   int J = bi.y * blockDim.y + threadIdx.y;
   int K = bi.z;
   if (I >= sc || J >= sc) return;
+  // fine coordinates 2c-1 .. 2c+2 along each axis (wrapped, or the ghost
+  // layer), as offsets
+  const int i0 = 2 * I, j0 = 2 * J, k0 = 2 * K;
+  const int xo[4] = {wrap_m(i0, s, periodic), i0, i0 + 1, wrap_p(i0 + 1, s, periodic)};
+  const int yo[4] = {wrap_m(j0, s, periodic) * u.sy, j0 * u.sy, (j0 + 1) * u.sy,
+                     wrap_p(j0 + 1, s, periodic) * u.sy};
+  const int zo[4] = {wrap_m(k0, s, periodic) * u.sz, k0 * u.sz, (k0 + 1) * u.sz,
+                     wrap_p(k0 + 1, s, periodic) * u.sz};
+  const float* p = u.base;
+  // the 8 children and their 24 face neighbours, each loaded once
+  float V[2][2][2], XM[2][2], XP[2][2], YM[2][2], YP[2][2], ZM[2][2], ZP[2][2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      XM[c][d] = p[xo[0] + yo[1 + d] + zo[1 + c]];
+      XP[c][d] = p[xo[3] + yo[1 + d] + zo[1 + c]];
+      YM[c][d] = p[xo[1 + d] + yo[0] + zo[1 + c]];
+      YP[c][d] = p[xo[1 + d] + yo[3] + zo[1 + c]];
+      ZM[c][d] = p[xo[1 + d] + yo[1 + c] + zo[0]];
+      ZP[c][d] = p[xo[1 + d] + yo[1 + c] + zo[3]];
+#pragma unroll
+      for (int a = 0; a < 2; ++a) V[c][d][a] = p[xo[1 + a] + yo[1 + d] + zo[1 + c]];
+    }
   float acc = 0.f;
 #pragma unroll
   for (int dz = 0; dz < 2; ++dz)
@@ -112,15 +136,14 @@ __device__ __forceinline__ void d_resid_restrict(const BI& bi, Grid u, Grid b, f
     for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
       for (int dx = 0; dx < 2; ++dx) {
-        int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
-        int c = gidx(u, i, j, k);
-        const float* p = u.base + c;
-        int xm = wrap_m(i, s, periodic) - i, xp = wrap_p(i, s, periodic) - i;
-        int ym = (wrap_m(j, s, periodic) - j) * u.sy, yp = (wrap_p(j, s, periodic) - j) * u.sy;
-        int zm = (wrap_m(k, s, periodic) - k) * u.sz, zp = (wrap_p(k, s, periodic) - k) * u.sz;
+        const int i = i0 + dx, j = j0 + dy, k = k0 + dz;
+        const float xm = dx ? V[dz][dy][0] : XM[dz][dy], xp = dx ? XP[dz][dy] : V[dz][dy][1];
+        const float ym = dy ? V[dz][0][dx] : YM[dz][dx], yp = dy ? YP[dz][dx] : V[dz][1][dx];
+        const float zm = dz ? V[0][dy][dx] : ZM[dy][dx], zp = dz ? ZP[dy][dx] : V[1][dy][dx];
         float diag = (periodic || gam == 0.0f) ? 6.0f : bnd_diag(i, j, k, s, gam);
-        float s0 = nb6(p[xm], p[xp], p[ym], p[yp], p[zm], p[zp]);
-        acc = __fadd_rn(acc, resid_value(s0, p[0], b.base[gidx(b, i, j, k)], diag, inv_h2));
+        float s0 = nb6(xm, xp, ym, yp, zm, zp);
+        acc = __fadd_rn(acc, resid_value(s0, V[dz][dy][dx], b.base[gidx(b, i, j, k)], diag,
+                                         inv_h2));
       }
   int cc = gidx(uc, I, J, K);
   bc.base[cc] = __fmul_rn(0.125f, acc);
@@ -181,21 +204,73 @@ __device__ __forceinline__ void d_prolong(const BI& bi, Grid uc, Grid u, int per
   *p = __fadd_rn(*p, prolong_value(uc, i, j, k, periodic, gam_c));
 }
 
-// out-of-place form: w = u + P uc (w and u may be different layouts)
-__global__ void __launch_bounds__(256) k_prolong_to(Grid uc, Grid u, Grid w, int periodic,
-                                                    float gam_c) {
-  const int s = u.s;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y * blockDim.y + threadIdx.y;
-  int k = blockIdx.z;
-  if (i >= s || j >= s) return;
-  w.base[gidx(w, i, j, k)] =
-      __fadd_rn(u.base[gidx(u, i, j, k)], prolong_value(uc, i, j, k, periodic, gam_c));
-}
-
 __global__ void __launch_bounds__(256) k_prolong(Grid uc, Grid u, int periodic,
                                                  float gam_c) {
   d_prolong(bi_native(), uc, u, periodic, gam_c);
+}
+
+// out-of-place form: w = u + P uc (w and u may be different layouts).  One
+// thread per coarse cell: its 3x3x3 coarse neighbourhood is loaded once and
+// its 8 fine children take prolong_value's arithmetic on those values.
+__global__ void __launch_bounds__(256) k_prolong_to(Grid uc, Grid u, Grid w, int periodic,
+                                                    float gam_c) {
+  const int sc = uc.s;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int K = blockIdx.z;
+  if (I >= sc || J >= sc) return;
+  // coarse index of offset o in {-1, 0, +1} along an axis: wrapped, or (open)
+  // the cell itself when outside, with factor -gam_c applied below
+  auto idx = [&](int c, int o) {
+    int v = c + o;
+    if (v < 0 || v >= sc) v = periodic ? (v < 0 ? sc - 1 : 0) : c;
+    return v;
+  };
+  auto fac = [&](int c, int o) {
+    int v = c + o;
+    return (!periodic && (v < 0 || v >= sc)) ? -gam_c : 1.0f;
+  };
+  int xi[3], yi[3], zi[3];
+  float fxv[3], fyv[3], fzv[3];
+#pragma unroll
+  for (int o = 0; o < 3; ++o) {
+    xi[o] = idx(I, o - 1);
+    yi[o] = idx(J, o - 1);
+    zi[o] = idx(K, o - 1);
+    fxv[o] = fac(I, o - 1);
+    fyv[o] = fac(J, o - 1);
+    fzv[o] = fac(K, o - 1);
+  }
+  float Q[3][3][3];  // [z][y][x]
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) Q[c][b][a] = uc.base[gidx(uc, xi[a], yi[b], zi[c])];
+#pragma unroll
+  for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) {
+        // the child's second coarse cell per axis: below for an even child,
+        // above for an odd one (neighbourhood index 0 or 2)
+        const int ax = dx ? 2 : 0, ay = dy ? 2 : 0, az = dz ? 2 : 0;
+        const float fx = fxv[ax], fy = fyv[ay], fz = fzv[az];
+        const float fxy = __fmul_rn(fx, fy), fxz = __fmul_rn(fx, fz), fyz = __fmul_rn(fy, fz);
+        const float fxyz = __fmul_rn(fxy, fz);
+        const float c000 = Q[1][1][1], c100 = __fmul_rn(fx, Q[1][1][ax]);
+        const float c010 = __fmul_rn(fy, Q[1][ay][1]), c110 = __fmul_rn(fxy, Q[1][ay][ax]);
+        const float c001 = __fmul_rn(fz, Q[az][1][1]), c101 = __fmul_rn(fxz, Q[az][1][ax]);
+        const float c011 = __fmul_rn(fyz, Q[az][ay][1]);
+        const float c111 = __fmul_rn(fxyz, Q[az][ay][ax]);
+        const float a0 = lerp34(c000, c100), a1 = lerp34(c010, c110);
+        const float a2 = lerp34(c001, c101), a3 = lerp34(c011, c111);
+        const float pv = lerp34(lerp34(a0, a1), lerp34(a2, a3));
+        const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
+        w.base[gidx(w, i, j, k)] = __fadd_rn(u.base[gidx(u, i, j, k)], pv);
+      }
 }
 
 // ---------------------------------------------------------------------------
@@ -739,7 +814,7 @@ void launch_copy_ghosts(cudaStream_t st, Grid src, Grid d1, Grid d2) {
 }
 
 void launch_prolong_to(cudaStream_t st, Grid uc, Grid u, Grid w, int periodic, float gam_c) {
-  k_prolong_to<<<grid_full(u.s), dim3(32, 8), 0, st>>>(uc, u, w, periodic, gam_c);
+  k_prolong_to<<<grid_full(uc.s), dim3(32, 8), 0, st>>>(uc, u, w, periodic, gam_c);
   note_launch();
 }
 void launch_prolong(cudaStream_t st, Grid uc, Grid u, int periodic, float gam_c) {
