@@ -17,63 +17,86 @@ __device__ __forceinline__ void d_drift_deposit(const BI& bi,
     float c0, int n, int lo, int s, int periodic,
     unsigned long long* __restrict__ rho, unsigned long long* __restrict__ escaped){
   const float fn = (float)n;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
   unsigned int esc_local = 0;
-  for (long long p = bi.x * (long long)blockDim.x + threadIdx.x; p < N;
-       p += (long long)bi.gx * blockDim.x) {
-    float4 x = pos[p];
-    if (DRIFT) {
-      float4 v = mom[p];
-      x.x = __fadd_rn(x.x, __fmul_rn(v.x, c0));
-      x.y = __fadd_rn(x.y, __fmul_rn(v.y, c0));
-      x.z = __fadd_rn(x.z, __fmul_rn(v.z, c0));
+  // whole warps iterate together (the loop bound is the warp's first
+  // particle) so that neighbouring lanes can merge their contributions
+  for (long long pw = bi.x * (long long)blockDim.x + (threadIdx.x & ~31); pw < N;
+       pw += (long long)bi.gx * blockDim.x) {
+    const long long p = pw + lane;
+    bool act = p < N;
+    int x0 = 0, x1 = 0, y0 = 0, y1 = 0, z0 = 0, z1 = 0, dx = 0, dy = 0, dz = 0;
+    if (act) {
+      float4 x = pos[p];
+      if (DRIFT) {
+        float4 v = mom[p];
+        x.x = __fadd_rn(x.x, __fmul_rn(v.x, c0));
+        x.y = __fadd_rn(x.y, __fmul_rn(v.y, c0));
+        x.z = __fadd_rn(x.z, __fmul_rn(v.z, c0));
+        if (periodic) {
+          if (x.x < 0.f) x.x = __fadd_rn(x.x, fn);
+          if (x.x >= fn) x.x = __fsub_rn(x.x, fn);
+          if (x.y < 0.f) x.y = __fadd_rn(x.y, fn);
+          if (x.y >= fn) x.y = __fsub_rn(x.y, fn);
+          if (x.z < 0.f) x.z = __fadd_rn(x.z, fn);
+          if (x.z >= fn) x.z = __fsub_rn(x.z, fn);
+        }
+        pos[p] = x;
+      }
+      int ix, iy, iz;
+      cic_axis(x.x, ix, dx);
+      cic_axis(x.y, iy, dy);
+      cic_axis(x.z, iz, dz);
       if (periodic) {
-        if (x.x < 0.f) x.x = __fadd_rn(x.x, fn);
-        if (x.x >= fn) x.x = __fsub_rn(x.x, fn);
-        if (x.y < 0.f) x.y = __fadd_rn(x.y, fn);
-        if (x.y >= fn) x.y = __fsub_rn(x.y, fn);
-        if (x.z < 0.f) x.z = __fadd_rn(x.z, fn);
-        if (x.z >= fn) x.z = __fsub_rn(x.z, fn);
+        // a wrapped position gives i in [-1, n-1]; anything else (a drift of
+        // more than a box length) is counted as escaped, never indexed
+        if (ix < -1 || ix > n - 1 || iy < -1 || iy > n - 1 || iz < -1 || iz > n - 1) {
+          act = false;
+        } else {
+          x0 = ix < 0 ? ix + n : ix;  x1 = x0 + 1 == n ? 0 : x0 + 1;
+          y0 = iy < 0 ? iy + n : iy;  y1 = y0 + 1 == n ? 0 : y0 + 1;
+          z0 = iz < 0 ? iz + n : iz;  z1 = z0 + 1 == n ? 0 : z0 + 1;
+        }
+      } else {
+        const int hi = lo + s - 1;
+        if (ix < lo || ix + 1 > hi || iy < lo || iy + 1 > hi || iz < lo || iz + 1 > hi) {
+          act = false;
+        } else {
+          x0 = ix; x1 = ix + 1; y0 = iy; y1 = iy + 1; z0 = iz; z1 = iz + 1;
+        }
       }
-      pos[p] = x;
-    }
-    int ix, iy, iz, dx, dy, dz;
-    cic_axis(x.x, ix, dx);
-    cic_axis(x.y, iy, dy);
-    cic_axis(x.z, iz, dz);
-    int x0, x1, y0, y1, z0, z1;
-    if (periodic) {
-      // a wrapped position gives i in [-1, n-1]; anything else (a drift of
-      // more than a box length) is counted as escaped, never indexed
-      if (ix < -1 || ix > n - 1 || iy < -1 || iy > n - 1 || iz < -1 || iz > n - 1) {
-        ++esc_local;
-        continue;
-      }
-      x0 = ix < 0 ? ix + n : ix;  x1 = x0 + 1 == n ? 0 : x0 + 1;
-      y0 = iy < 0 ? iy + n : iy;  y1 = y0 + 1 == n ? 0 : y0 + 1;
-      z0 = iz < 0 ? iz + n : iz;  z1 = z0 + 1 == n ? 0 : z0 + 1;
-    } else {
-      const int hi = lo + s - 1;
-      if (ix < lo || ix + 1 > hi || iy < lo || iy + 1 > hi || iz < lo || iz + 1 > hi) {
-        ++esc_local;
-        continue;
-      }
-      x0 = ix; x1 = ix + 1; y0 = iy; y1 = iy + 1; z0 = iz; z1 = iz + 1;
+      if (!act) ++esc_local;
     }
     const unsigned long long wx0 = 65536u - dx, wx1 = dx;
     const unsigned long long wy0 = 65536u - dy, wy1 = dy;
     const unsigned long long wz0 = 65536u - dz, wz1 = dz;
     const unsigned long long a00 = wy0 * wz0, a10 = wy1 * wz0, a01 = wy0 * wz1,
                              a11 = wy1 * wz1;
-    const long long r00 = ((long long)z0 * n + y0) * n, r10 = ((long long)z0 * n + y1) * n;
-    const long long r01 = ((long long)z1 * n + y0) * n, r11 = ((long long)z1 * n + y1) * n;
-    atomicAdd(rho + r00 + x0, wx0 * a00);
-    atomicAdd(rho + r00 + x1, wx1 * a00);
-    atomicAdd(rho + r10 + x0, wx0 * a10);
-    atomicAdd(rho + r10 + x1, wx1 * a10);
-    atomicAdd(rho + r01 + x0, wx0 * a01);
-    atomicAdd(rho + r01 + x1, wx1 * a01);
-    atomicAdd(rho + r11 + x0, wx0 * a11);
-    atomicAdd(rho + r11 + x1, wx1 * a11);
+    // the x1 column of lane l is the x0 column of lane l+1 when their cells
+    // are x-neighbours: lane l+1 adds lane l's x1 weights to its own atomics
+    unsigned long long c00 = wx1 * a00, c10 = wx1 * a10, c01 = wx1 * a01, c11 = wx1 * a11;
+    const int px1 = __shfl_up_sync(FULL, x1, 1), py0 = __shfl_up_sync(FULL, y0, 1);
+    const int pz0 = __shfl_up_sync(FULL, z0, 1);
+    const bool pact = __shfl_up_sync(FULL, act ? 1 : 0, 1) != 0;
+    const unsigned long long q00 = __shfl_up_sync(FULL, c00, 1), q10 = __shfl_up_sync(FULL, c10, 1);
+    const unsigned long long q01 = __shfl_up_sync(FULL, c01, 1), q11 = __shfl_up_sync(FULL, c11, 1);
+    const bool take = lane > 0 && act && pact && px1 == x0 && py0 == y0 && pz0 == z0;
+    const bool given = __shfl_down_sync(FULL, take ? 1 : 0, 1) != 0 && lane < 31;
+    if (act) {
+      const long long r00 = ((long long)z0 * n + y0) * n, r10 = ((long long)z0 * n + y1) * n;
+      const long long r01 = ((long long)z1 * n + y0) * n, r11 = ((long long)z1 * n + y1) * n;
+      atomicAdd(rho + r00 + x0, wx0 * a00 + (take ? q00 : 0ull));
+      atomicAdd(rho + r10 + x0, wx0 * a10 + (take ? q10 : 0ull));
+      atomicAdd(rho + r01 + x0, wx0 * a01 + (take ? q01 : 0ull));
+      atomicAdd(rho + r11 + x0, wx0 * a11 + (take ? q11 : 0ull));
+      if (!given) {
+        atomicAdd(rho + r00 + x1, c00);
+        atomicAdd(rho + r10 + x1, c10);
+        atomicAdd(rho + r01 + x1, c01);
+        atomicAdd(rho + r11 + x1, c11);
+      }
+    }
   }
   {
     unsigned int w = esc_local;
