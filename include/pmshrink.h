@@ -50,6 +50,7 @@ typedef enum {
 
 enum { PM_MIXED = 0, PM_FP32_PLAIN = 1 };               /* pm_config.precision */
 enum { PM_GUESS_WARM = 0, PM_GUESS_ZERO = 1, PM_GUESS_LEARNED = 2 };  /* pm_config.guess */
+enum { PM_GRAVITY_POISSON = 0, PM_GRAVITY_DIFFUSION = 1 };           /* pm_config.gravity */
 enum { PM_BC_PAPER = 0, PM_BC_OPEN = 1, PM_BC_PERIODIC = 2 };  /* pm_config.bc */
 
 typedef struct {
@@ -75,6 +76,12 @@ typedef struct {
                             the lightcone buffer); 0: keep everything */
   double buffer_cells;   /* keep half-width R = chi(a)/cell + buffer_cells */
   int32_t store_forces;  /* 1: keep grad(Phi) at each particle of the last step */
+  int32_t gravity;       /* PM_GRAVITY_POISSON: static Eq. 3 every step;
+                            PM_GRAVITY_DIFFUSION: the diffusion equation (Eq. 4,
+                            Sec. 2.3) advanced by two implicit half-substeps
+                            per step in the Table 2 order (see pm_step) */
+  double c_eff_factor;   /* diffusion only: c_eff = factor * cell (Mpc/h) * c,
+                            0.019 in Sec. 3.1.1 */
 } pm_config;
 
 /* Fill *cfg with defaults: 32^3 mesh and particles, 250 Mpc/h, Om=0.3,
@@ -96,10 +103,18 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
 
 /* Advance n_steps steps in the order of Table 2 (Sec. 2.4): half drift,
  * CIC deposit, Poisson solve (Sec. 2.1, Eq. 3), gradient + CIC gather, kick,
- * half drift, lightcone shrink (Sec. 2.4).  Stops early with PM_EINVAL past
- * the last step of the schedule, PM_ENOCONV if a solve fails to converge,
- * PM_EOVERFLOW on fixed-point overflow.  Synchronises the stream once per
- * V-cycle (convergence test) and once per shrink (new active count). */
+ * half drift, lightcone shrink (Sec. 2.4).  With PM_GRAVITY_DIFFUSION the
+ * solve is replaced by Table 2's right column: the field is advanced from t
+ * to t+dt/2 before the gradient and from t+dt/2 to t+dt after the second
+ * half drift, each half-substep one backward-Euler step of Eq. 4,
+ * (A - sig) Phi = S delta - sig Phi_old with sig = 3 H / (c_eff^2 dtau/2),
+ * H = a E(a) and S at the substep's end, the density of t+dt/2 for both,
+ * solved by the same multigrid with a diagonal shift to rtol of
+ * ||g - (A - sig) Phi|| / ||g||; the field starts from the static solution
+ * of the initial density.  Stops early with PM_EINVAL past the last step of
+ * the schedule, PM_ENOCONV if a solve fails to converge, PM_EOVERFLOW on
+ * fixed-point overflow.  Synchronises the stream once per V-cycle
+ * (convergence test) and once per shrink (new active count). */
 pm_status pm_step(pm_ctx* ctx, int32_t n_steps);
 
 /* Drop particles outside the keep cube of expansion factor a (Sec. 2.4:

@@ -96,9 +96,11 @@ def initial_field(pos, sched, n, om, nbar):
     return phi, (lo, s, per)
 
 
-def step(pos, mom, state, k, sched, n, om, ol, nbar, c_cells=None, want=False):
+def step(pos, mom, state, k, sched, n, om, ol, nbar, c_cells=None, want=False, drift32=False):
     """Advance (pos, mom) and the field state (phi, (lo, s, periodic)) by
-    step k in the Table 2 order.  Returns (pos, mom, state, info)."""
+    step k in the Table 2 order.  Returns (pos, mom, state, info).
+    drift32: the first half drift in the float32 arithmetic the CUDA kernel
+    documents (pm.drift_fp32), so that both deposit the same positions."""
     c_cells = c_eff_cells() if c_cells is None else c_cells
     a0, a1 = sched["a"][k], sched["a"][k + 1]
     dtau, ah = sched["dtau"][k], sched["a_half"][k]
@@ -106,7 +108,11 @@ def step(pos, mom, state, k, sched, n, om, ol, nbar, c_cells=None, want=False):
     phi_prev, (lo_p, s_p, per_p) = state
     phi_old = restrict_field(phi_prev, lo_p, s_p, per_p, lo, s)
     # 1-2. half drift, density at t + dt/2
-    pos = pm.drift(pos, mom, dtau / (2 * a0), n, per)
+    if drift32:
+        pos = pm.drift_fp32(np.asarray(pos, np.float32), np.asarray(mom, np.float32),
+                            dtau / (2 * a0), n, per).astype(np.float64)
+    else:
+        pos = pm.drift(pos, mom, dtau / (2 * a0), n, per)
     x_half = pos
     rho, esc = pm.deposit(pos, n, lo, s, per)
     delta = pm.delta_cube(rho, n, lo, s, nbar, sched["R"][k], per)
@@ -131,3 +137,24 @@ def step(pos, mom, state, k, sched, n, om, ol, nbar, c_cells=None, want=False):
     if want:
         info.update(F=F, phi_half=phi_h, phi_end=phi_1, x_half=x_half, f=f1)
     return pos, mom, (phi_1, (lo, s, per)), info
+
+
+def run(pos, mom, ids, sched, n, om, ol, nbar, steps=None, c_cells=None):
+    """Whole run with shrinking (as pm.run, with the diffusion field)."""
+    pos = np.asarray(pos, dtype=np.float64).copy()
+    mom = np.asarray(mom, dtype=np.float64).copy()
+    ids = np.asarray(ids).copy()
+    lc = [np.zeros((0, 3)), np.zeros((0, 3)), np.zeros(0, dtype=ids.dtype), np.zeros(0)]
+    state = initial_field(pos, sched, n, om, nbar)
+    nsteps = len(sched["dtau"]) if steps is None else steps
+    for k in range(nsteps):
+        pos, mom, state, _ = step(pos, mom, state, k, sched, n, om, ol, nbar, c_cells)
+        R1 = sched["R"][k + 1]
+        if pm.is_open(R1, n):
+            keep = pm.keep_mask(pos, R1, n)
+            (pos, mom, ids), (lp, lm, li) = pm.shrink([pos, mom, ids], keep)
+            lc = [np.concatenate([lc[0], lp]), np.concatenate([lc[1], lm]),
+                  np.concatenate([lc[2], li]),
+                  np.concatenate([lc[3], np.full(len(li), sched["a"][k + 1])])]
+    return dict(pos=pos, mom=mom, ids=ids, lc_pos=lc[0], lc_mom=lc[1], lc_ids=lc[2],
+                lc_a=lc[3])

@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(HERE, "libpmshrink.so")
 PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_ENOCONV, PM_EOVERFLOW, PM_ETIMEOUT = range(7)
 PM_MIXED, PM_FP32_PLAIN = 0, 1
 PM_GUESS_WARM, PM_GUESS_ZERO, PM_GUESS_LEARNED = 0, 1, 2
+PM_GRAVITY_POISSON, PM_GRAVITY_DIFFUSION = 0, 1
 PM_BC_PAPER, PM_BC_OPEN, PM_BC_PERIODIC = 0, 1, 2
 PM_SHRINK_STATIC_MAX_PARTICLES = 1 << 22
 
@@ -43,7 +44,7 @@ class PmConfig(C.Structure):
         ("a_final", C.c_double), ("n_steps", C.c_int32), ("rtol", C.c_double),
         ("max_vcycles", C.c_int32), ("precision", C.c_int32), ("guess", C.c_int32),
         ("bc", C.c_int32), ("shrink", C.c_int32), ("buffer_cells", C.c_double),
-        ("store_forces", C.c_int32),
+        ("store_forces", C.c_int32), ("gravity", C.c_int32), ("c_eff_factor", C.c_double),
     ]
 
 

@@ -189,6 +189,12 @@ struct pm_ctx {
   // training-pair capture targets (caller's device memory)
   float *cap_r = nullptr, *cap_e = nullptr;
 
+  // diffusion gravity: diagonal shift of the current solve (0: Poisson) and
+  // whether the field holds the state of the last step
+  float sig = 0.0f;       // in the FP32 V-cycle (preconditioner)
+  double sig_d = 0.0;     // in the double-float defect and right-hand side
+  bool field_ready = false;
+
   int vcycles_last = 0;
   long long vcycles_total = 0;
   double resid_last = 0.0;
@@ -374,10 +380,11 @@ pm_status sync_read(pm_ctx* ctx) {
 // V(2,2) cycle on level 0 grids (u0, b0) of the current cube.
 // Two RB-GS sweeps (red, black, red, black) on a level; zero_start when the
 // iterate is known to be zero on entry.
-void smooth2(pm_ctx* ctx, Grid u, Grid b, float h2, int per, float g, bool zero_start) {
+void smooth2(pm_ctx* ctx, Grid u, Grid b, float h2, int per, float g, bool zero_start,
+             float d0) {
   for (int sw = 0; sw < 2; ++sw) {
-    launch_rbgs(ctx->st, u, b, h2, 0, per, g, zero_start && sw == 0);
-    launch_rbgs(ctx->st, u, b, h2, 1, per, g);
+    launch_rbgs(ctx->st, u, b, h2, 0, per, g, zero_start && sw == 0, d0);
+    launch_rbgs(ctx->st, u, b, h2, 1, per, g, false, d0);
   }
 }
 
@@ -415,18 +422,20 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
     // below level 0 the restriction zeroes the coarse iterate
     const bool zs = l == 0 ? zero0 : true;
     const bool fused = ctx->ls[l] >= FUSED_MIN;
+    const float d0 = 6.0f + ctx->sig * h2;  // h2 = 4^l
     Upre[l] = (zs || !fused) ? U[l] : compact_view(ctx->lu[0], ctx->ls[0]);
     if (fused && !zs && !per)  // the scratch grids take u0's Dirichlet ghost values
       launch_copy_ghosts(ctx->st, U[0], Upre[0], compact_view(ctx->lu2[0], ctx->ls[0]));
     if (fused)
-      launch_rbgs2(ctx->st, U[l], Upre[l], B[l], h2, per, gam(l), zs);
+      launch_rbgs2(ctx->st, U[l], Upre[l], B[l], h2, per, gam(l), zs, 0, d0);
     else
-      smooth2(ctx, U[l], B[l], h2, per, gam(l), zs);
+      smooth2(ctx, U[l], B[l], h2, per, gam(l), zs, d0);
     if (l == 0) {
       prof_end(ctx, PM_PROF_SMOOTH0, e, (fused ? (zs ? 8.0 : 12.0) : 32.0) * c0);
       e = prof_begin(ctx);
     }
-    launch_resid_restrict(ctx->st, Upre[l], B[l], 1.0f / h2, U[l + 1], B[l + 1], per, gam(l));
+    launch_resid_restrict(ctx->st, Upre[l], B[l], 1.0f / h2, U[l + 1], B[l + 1], per, gam(l),
+                          d0);
     if (l == 0) {
       prof_end(ctx, PM_PROF_TRANSFER0, e, 9.0 * c0);
       ec = prof_begin(ctx);
@@ -434,7 +443,8 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
     h2 *= 4.0f;
   }
   if (Lc == 0) ec = prof_begin(ctx);
-  launch_coarse_mg(ctx->st, U[Lc], B[Lc], Lc, per, COARSE_SWEEPS, Lc == 0 ? zero0 : true);
+  launch_coarse_mg(ctx->st, U[Lc], B[Lc], Lc, per, COARSE_SWEEPS, Lc == 0 ? zero0 : true,
+                   ctx->sig);
   for (int l = Lc - 1; l >= 0; --l) {
     h2 *= 0.25f;
     int e = -1;
@@ -443,6 +453,7 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
       e = prof_begin(ctx);
     }
     const bool fused = ctx->ls[l] >= FUSED_MIN;
+    const float d0 = 6.0f + ctx->sig * h2;
     Grid W = compact_view(ctx->lu2[l], ctx->ls[l]);
     if (fused)
       launch_prolong_to(ctx->st, U[l + 1], Upre[l], W, per, gam(l + 1));
@@ -453,9 +464,9 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
       e = prof_begin(ctx);
     }
     if (fused)
-      launch_rbgs2(ctx->st, W, U[l], B[l], h2, per, gam(l), false);
+      launch_rbgs2(ctx->st, W, U[l], B[l], h2, per, gam(l), false, 0, d0);
     else
-      smooth2(ctx, U[l], B[l], h2, per, gam(l), false);
+      smooth2(ctx, U[l], B[l], h2, per, gam(l), false, d0);
     if (l == 0) prof_end(ctx, PM_PROF_SMOOTH0, e, (fused ? 12.0 : 32.0) * c0);
   }
   if (Lc == 0) prof_end(ctx, PM_PROF_COARSE, ec, 0.0);
@@ -471,7 +482,8 @@ void drop_graph(pm_ctx* ctx) {
 // One V-cycle: replay of a graph captured for the current cube / grids, or
 // eager launches when the context's stream cannot be captured.
 pm_status vcycle_run(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
-  if (!ctx->use_graphs) return vcycle(ctx, u0, b0, zero0);
+  // the diffusion substeps change the shift every solve: no graph for them
+  if (!ctx->use_graphs || ctx->sig != 0.0f) return vcycle(ctx, u0, b0, zero0);
   auto& g = ctx->vg;
   if (!(g.valid && g.lo == ctx->lo && g.s == ctx->s && g.per == ctx->periodic &&
         g.u0 == u0.base && g.b0 == b0.base && g.prof == (int)ctx->prof_on &&
@@ -545,12 +557,14 @@ pm_status solve(pm_ctx* ctx) {
       // f (8), writes Phi (8) and r (4) per cell
       if (capture) launch_to_dense(ctx->st, e0, ctx->cap_e, true);
       launch_defect(ctx->st, ph_of(c0), pl_of(c0), &e0, ph_of(c0 ^ 1), pl_of(c0 ^ 1), fh, fl,
-                    r0, per, true, ctx->partial, ctx->counter, ctx->d_scal + 11);
+                    r0, per, true, ctx->partial, ctx->counter, ctx->d_scal + 11,
+                    6.0 + ctx->sig_d);
       ctx->cur ^= 1;
       prof_end(ctx, PM_PROF_DEFECT, e, 32.0 * cells);
     } else {
       launch_defect(ctx->st, ph_of(c0), pl_of(c0), nullptr, ph_of(c0), pl_of(c0), fh, fl, r0,
-                    per, mixed || net_todo, ctx->partial, ctx->counter, ctx->d_scal + 11);
+                    per, mixed || net_todo, ctx->partial, ctx->counter, ctx->d_scal + 11,
+                    6.0 + ctx->sig_d);
       prof_end(ctx, PM_PROF_DEFECT, e, (mixed ? 20.0 : 16.0) * cells);
     }
     pending = false;
@@ -686,6 +700,8 @@ void pm_config_default(pm_config* c) {
   c->shrink = 1;
   c->buffer_cells = 1.0;
   c->store_forces = 0;
+  c->gravity = PM_GRAVITY_POISSON;
+  c->c_eff_factor = 0.019;
 }
 
 pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
@@ -708,6 +724,11 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
     return fail(nullptr, PM_EINVAL, "pm_init: unknown bc");
   if (cfg->guess < PM_GUESS_WARM || cfg->guess > PM_GUESS_LEARNED)
     return fail(nullptr, PM_EINVAL, "pm_init: unknown guess");
+  if (cfg->gravity != PM_GRAVITY_POISSON &&
+      (cfg->gravity != PM_GRAVITY_DIFFUSION || !(cfg->c_eff_factor > 0) ||
+       cfg->precision != PM_MIXED || cfg->guess == PM_GUESS_LEARNED))
+    return fail(nullptr, PM_EINVAL,
+                "pm_init: diffusion gravity needs c_eff_factor > 0, PM_MIXED, no learned guess");
 
   if (mg_prepare() != cudaSuccess)
     return fail(nullptr, PM_ECUDA, "pm_init: setting kernel attributes failed");
@@ -845,6 +866,47 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
     if (st != PM_OK) return st;
     const long long N = ctx->n_active;
     const double cells = (double)s * s * s;
+    const bool diffusion = ctx->cfg.gravity == PM_GRAVITY_DIFFUSION;
+    const double nbar = (double)ctx->N0 / ((double)n * n * n);
+    const double invM = 1.0 / (281474976710656.0 * nbar);
+    int b0 = 0, b1 = n - 1;
+    if (!per) {
+      double c = 0.5 * n;
+      b0 = std::max(lo, (int)std::ceil(c - R0 - 0.5));
+      b1 = std::min(lo + s - 1, (int)std::floor(c + R0 - 0.5));
+    }
+    Grid fh = full_view(ctx, ctx->f_hi, lo, s), fl = full_view(ctx, ctx->f_lo, lo, s);
+    // boundary values of the current source (moments in d_scal) with factor S
+    auto ghosts = [&](double Sb) {
+      if (per) return;
+      int eb = prof_begin(ctx);
+      for (int q = 0; q < 2; ++q)  // both buffers carry the ghosts
+        launch_boundary(ctx->st, full_view(ctx, ctx->phi_h[q ^ ctx->cur], lo, s),
+                        full_view(ctx, ctx->phi_l[q ^ ctx->cur], lo, s), n, lo,
+                        ctx->d_scal + 1, Sb, true);
+      prof_end(ctx, PM_PROF_BOUNDARY, eb, 8.0 * 6.0 * (s + 2.0) * (s + 2.0));
+    };
+    if (diffusion && !ctx->field_ready) {
+      // the field starts from the static solution for the initial density
+      const double S0 = 1.5 * ctx->cfg.omega_m / ctx->a[k];
+      launch_drift_deposit(ctx->st, std::max(1, std::min(gkd_blocks(N) * 4, 152 * 16)),
+                           ctx->pos, ctx->mom, N, 0.0f, false, n, lo, s, per, ctx->rho,
+                           ctx->d_cnt + 1);
+      launch_source(ctx->st, SRC_GRID, ctx->rho, n, lo, s, fh, fl, invM, S0, b0, b1, !per,
+                    ctx->partial, ctx->partial_m, ctx->counter, ctx->d_scal, ctx->bgm,
+                    ctx->d_overflow);
+      ghosts(S0);
+      for (int q = 0; q < 2; ++q) {
+        launch_fill(ctx->st, full_view(ctx, ctx->phi_h[q], lo, s), 0.0f, false);
+        launch_fill(ctx->st, full_view(ctx, ctx->phi_l[q], lo, s), 0.0f, false);
+      }
+      ctx->sig = 0.0f;
+      ctx->sig_d = 0.0;
+      CKL();
+      st = solve(ctx);
+      if (st != PM_OK) return st;
+      ctx->field_ready = true;
+    }
     // 1-2. half drift + CIC deposit: read x, p, write x (48 B/particle); the
     // count grid is read and written once (16 B/cell)
     int e = prof_begin(ctx);
@@ -854,21 +916,35 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
     prof_end(ctx, PM_PROF_DEPOSIT, e, 48.0 * N + 16.0 * cells);
     // 3. source, boundary values, solve
     const double S = 1.5 * ctx->cfg.omega_m / ctx->a_half[k];
-    const double nbar = (double)ctx->N0 / ((double)n * n * n);
-    const double invM = 1.0 / (281474976710656.0 * nbar);
-    int b0 = 0, b1 = n - 1;
-    if (!per) {
-      double c = 0.5 * n;
-      b0 = std::max(lo, (int)std::ceil(c - R0 - 0.5));
-      b1 = std::min(lo + s - 1, (int)std::floor(c + R0 - 0.5));
-    }
     e = prof_begin(ctx);
-    launch_source(ctx->st, SRC_GRID, ctx->rho, n, lo, s, full_view(ctx, ctx->f_hi, lo, s),
-                  full_view(ctx, ctx->f_lo, lo, s), invM, S, b0, b1, !per, ctx->partial,
-                  ctx->partial_m, ctx->counter, ctx->d_scal, ctx->bgm, ctx->d_overflow);
+    launch_source(ctx->st, SRC_GRID, ctx->rho, n, lo, s, fh, fl, invM, S, b0, b1, !per,
+                  ctx->partial, ctx->partial_m, ctx->counter, ctx->d_scal, ctx->bgm,
+                  ctx->d_overflow);
     // read the counts, clear them, write f hi + lo: 24 B/cell
     prof_end(ctx, PM_PROF_SOURCE, e, 24.0 * cells);
-    if (!per) {
+    // diffusion: the shift of a half-substep ending at a_e
+    const double c_cells = ctx->cfg.c_eff_factor * C_OVER_H0;
+    auto shift = [&](double a_e) {
+      const double E = std::sqrt(ctx->cfg.omega_m / (a_e * a_e * a_e) + ctx->cfg.omega_l);
+      return 3.0 * a_e * E / (c_cells * c_cells * 0.5 * ctx->dtau[k]);
+    };
+    auto set_shift = [&](double sg) {
+      ctx->sig_d = sg;
+      ctx->sig = (float)sg;
+    };
+    if (diffusion) {
+      // substep 1 (t -> t + dt/2): g = f - sig Phi_old, f kept for substep 2
+      ghosts(S);
+      const double sg = shift(ctx->a_half[k]);
+      e = prof_begin(ctx);
+      launch_diff_rhs(ctx->st, SRC_GRID, fh, fl, 1.0, full_view(ctx, ctx->phi_h[ctx->cur], lo, s),
+                      full_view(ctx, ctx->phi_l[ctx->cur], lo, s), sg, fh, fl,
+                      full_view(ctx, ctx->prev_hi, lo, s), full_view(ctx, ctx->prev_lo, lo, s),
+                      true, ctx->partial, ctx->counter, ctx->d_scal);
+      prof_end(ctx, PM_PROF_CORRECT, e, 32.0 * cells);
+      set_shift(sg);
+      CKL();
+    } else if (!per) {
       e = prof_begin(ctx);
       for (int q = 0; q < (mixed ? 2 : 1); ++q)  // both buffers carry the ghosts
         launch_boundary(ctx->st, full_view(ctx, ctx->phi_h[q ^ ctx->cur], lo, s),
@@ -878,8 +954,9 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
     }
     CKL();
     // warm start extrapolated linearly in a_half from the last two solutions
-    // of the same boundary phase
-    if (ctx->cfg.guess == PM_GUESS_WARM || ctx->cfg.guess == PM_GUESS_LEARNED) {
+    // of the same boundary phase (the diffusion substeps start from Phi_old)
+    if (!diffusion &&
+        (ctx->cfg.guess == PM_GUESS_WARM || ctx->cfg.guess == PM_GUESS_LEARNED)) {
       if (set_phase_changed) ctx->n_sol = 0;
       if (ctx->n_sol >= 1) {
         float w = 0.0f;
@@ -896,6 +973,8 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
       }
     }
     st = solve(ctx);
+    ctx->sig = 0.0f;
+    ctx->sig_d = 0.0;
     if (st != PM_OK) return st;
     ctx->ah_hist[0] = ctx->ah_hist[1];
     ctx->ah_hist[1] = ctx->a_half[k];
@@ -918,6 +997,25 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
     CKL();
     ctx->forces_valid = ctx->forces != nullptr;
     ctx->forces_n = N;
+    if (diffusion) {
+      // substep 2 (t + dt/2 -> t + dt): the same density, S and H at a_{n+1}
+      const double S2 = 1.5 * ctx->cfg.omega_m / ctx->a[k + 1];
+      ghosts(S2);
+      const double sg = shift(ctx->a[k + 1]);
+      e = prof_begin(ctx);
+      launch_diff_rhs(ctx->st, SRC_GRID, full_view(ctx, ctx->prev_hi, lo, s),
+                      full_view(ctx, ctx->prev_lo, lo, s), S2 / S,
+                      full_view(ctx, ctx->phi_h[ctx->cur], lo, s),
+                      full_view(ctx, ctx->phi_l[ctx->cur], lo, s), sg, fh, fl, fh, fl, false,
+                      ctx->partial, ctx->counter, ctx->d_scal);
+      prof_end(ctx, PM_PROF_CORRECT, e, 28.0 * cells);
+      set_shift(sg);
+      CKL();
+      st = solve(ctx);
+      ctx->sig = 0.0f;
+      ctx->sig_d = 0.0;
+      if (st != PM_OK) return st;
+    }
     // 7. lightcone shrink
     if (do_flag) {
       st = shrink_to(ctx, R1, ctx->a[k + 1], true);
@@ -960,6 +1058,7 @@ pm_status pm_potential(pm_ctx* ctx, const double* delta_dev, double a, int32_t b
   if (st != PM_OK) return st;
   ctx->cube_valid = false;  // the next step re-derives its cube
   ctx->n_sol = 0;           // and does not extrapolate across this solve
+  ctx->field_ready = false; // a diffusion run restarts its field
   const double S = 1.5 * ctx->cfg.omega_m / a;
   Grid fh = full_view(ctx, ctx->f_hi, 0, n), fl = full_view(ctx, ctx->f_lo, 0, n);
   const bool mixed = ctx->cfg.precision == PM_MIXED;
@@ -1577,6 +1676,8 @@ pm_status pm_batch_init(int32_t n_real, const pm_config* cfgs, const float* cons
       return bfail(nullptr, PM_EINVAL, "pm_batch_init: batches run in PM_MIXED precision");
     if (cfgs[r].guess == PM_GUESS_LEARNED)
       return bfail(nullptr, PM_EINVAL, "pm_batch_init: the learned guess runs per context");
+    if (cfgs[r].gravity != PM_GRAVITY_POISSON)
+      return bfail(nullptr, PM_EINVAL, "pm_batch_init: batches solve Poisson's equation");
     if (cfgs[r].n_steps != cfgs[0].n_steps || cfgs[r].a_init != cfgs[0].a_init ||
         cfgs[r].a_final != cfgs[0].a_final)
       return bfail(nullptr, PM_EINVAL, "pm_batch_init: realisations must share the a schedule");

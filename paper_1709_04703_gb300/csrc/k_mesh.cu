@@ -410,6 +410,63 @@ void launch_source_f64(cudaStream_t st, int grid, const double* delta, int n, Gr
 }
 
 // ---------------------------------------------------------------------------
+// Right-hand side of an implicit diffusion substep (backward Euler on Eq. 4):
+// g = scale * src - sig * Phi_old in double-float on the cube interior,
+// written to (gh, gl); with `stash` the source is first copied to (qh, ql).
+// ||g||^2 into out[0] (deterministic block partials).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_diff_rhs(Grid sh, Grid sl, float scale_hi,
+                                                  float scale_lo, Grid ph, Grid pl, float sig_hi,
+                                                  float sig_lo,
+                                                  Grid gh, Grid gl, Grid qh, Grid ql, int stash,
+                                                  double* __restrict__ partial,
+                                                  unsigned int* counter,
+                                                  double* __restrict__ out) {
+  const int s = ph.s;
+  const long long total = (long long)s * s * s;
+  double acc[1] = {0.0};
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % s);
+    const long long r = t / s;
+    const int j = (int)(r % s), k = (int)(r / s);
+    const int cs = gidx(sh, i, j, k), cp = gidx(ph, i, j, k), cg = gidx(gh, i, j, k);
+    const df src{sh.base[cs], sl.base[cs]};
+    if (stash) {
+      const int cq = gidx(qh, i, j, k);
+      qh.base[cq] = src.hi;
+      ql.base[cq] = src.lo;
+    }
+    const df a = df_mul(src, df{scale_hi, scale_lo});
+    const df b = df_mul(df{ph.base[cp], pl.base[cp]}, df{-sig_hi, -sig_lo});
+    const df g = df_add(a, b);
+    gh.base[cg] = g.hi;
+    gl.base[cg] = g.lo;
+    acc[0] += (double)g.hi * (double)g.hi;
+  }
+  __shared__ double sm[32];
+  block_sum<1>(acc, sm);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc[0];
+  if (!arrive_last(counter)) return;
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(partial + b);
+    out[0] = v;
+    *counter = 0u;
+  }
+}
+
+void launch_diff_rhs(cudaStream_t st, int grid, Grid sh, Grid sl, double scale, Grid ph,
+                     Grid pl, double sig, Grid gh, Grid gl, Grid qh, Grid ql, bool stash,
+                     double* partial, unsigned int* counter, double* out) {
+  const float shi = (float)scale, slo = (float)(scale - (double)shi);
+  const float ghi = (float)sig, glo = (float)(sig - (double)ghi);
+  k_diff_rhs<<<grid, 256, 0, st>>>(sh, sl, shi, slo, ph, pl, ghi, glo, gh, gl, qh, ql,
+                                   stash ? 1 : 0, partial, counter, out);
+  note_launch();
+}
+
+// ---------------------------------------------------------------------------
 // K3: open-boundary ghost layer.  At each ghost-cell centre r (relative to
 // the box centre): Phi = -(S/4pi) [q0/r + d.r/r^3 + r.Q.r/(2 r^5)],
 // Q_ab = 3 S_ab - delta_ab tr(S).  mom = (q0, dx, dy, dz, Sxx, Syy, Szz, Sxy,

@@ -23,6 +23,18 @@ __device__ __forceinline__ float bnd_diag(int i, int j, int k, int s, float gam)
   int nb = (i == 0) + (i == s - 1) + (j == 0) + (j == s - 1) + (k == 0) + (k == s - 1);
   return 6.0f + gam * (float)nb;
 }
+// Diagonal with a shift: the operator sum_nb u - d0 u (d0 = 6 + sig h^2 for
+// the implicit diffusion substeps, 6 for Poisson) plus the coarse open
+// ghost term.  "simple" (d0 = 6, no ghost term) keeps the exact x(1/6) form.
+__device__ __forceinline__ float mg_diag(int i, int j, int k, int s, int periodic, float gam,
+                                         float d0) {
+  if (periodic) return d0;
+  int nb = (i == 0) + (i == s - 1) + (j == 0) + (j == s - 1) + (k == 0) + (k == s - 1);
+  return d0 + gam * (float)nb;
+}
+__device__ __forceinline__ bool mg_simple(int periodic, float gam, float d0) {
+  return (periodic || gam == 0.0f) && d0 == 6.0f;
+}
 
 // The update arithmetic of the smoother and the transfers, written with
 // explicit round-to-nearest operations so that every kernel that applies
@@ -51,7 +63,8 @@ __device__ __forceinline__ float lerp34(float a, float b) {
 // take (-h^2 b)/diag without reading u; the black sweep after it reads only
 // red neighbours, so u needs no clearing before a V-cycle.
 __device__ __forceinline__ void d_rbgs(const BI& bi, Grid u, Grid b, float h2, int color,
-                                              int periodic, float gam, int zero_start){
+                                              int periodic, float gam, int zero_start,
+                                              float d0){
   // each thread updates the two cells of its colour at i0 and i0 + 2
   // (independent loads in flight, the shared x-neighbour loaded once)
   const int s = u.s;
@@ -64,7 +77,7 @@ __device__ __forceinline__ void d_rbgs(const BI& bi, Grid u, Grid b, float h2, i
   const bool two = 2 * t + 1 < half;
   const int ym = (wrap_m(j, s, periodic) - j) * u.sy, yp = (wrap_p(j, s, periodic) - j) * u.sy;
   const int zm = (wrap_m(k, s, periodic) - k) * u.sz, zp = (wrap_p(k, s, periodic) - k) * u.sz;
-  const bool simple = periodic || gam == 0.0f;
+  const bool simple = mg_simple(periodic, gam, d0);
   const int c0 = gidx(u, i0, j, k);
   const int bc0 = gidx(b, i0, j, k);
   float* p0 = u.base + c0;
@@ -83,13 +96,15 @@ __device__ __forceinline__ void d_rbgs(const BI& bi, Grid u, Grid b, float h2, i
       s1 = nb6(xmid, p1[xp1], p1[ym], p1[yp], p1[zm], p1[zp]);
     }
   }
-  p0[0] = gs_value(s0, b0v, h2, simple, simple ? 6.0f : bnd_diag(i0, j, k, s, gam));
-  if (two) p0[2] = gs_value(s1, b1v, h2, simple, simple ? 6.0f : bnd_diag(i0 + 2, j, k, s, gam));
+  p0[0] = gs_value(s0, b0v, h2, simple, simple ? 6.0f : mg_diag(i0, j, k, s, periodic, gam, d0));
+  if (two)
+    p0[2] = gs_value(s1, b1v, h2, simple,
+                     simple ? 6.0f : mg_diag(i0 + 2, j, k, s, periodic, gam, d0));
 }
 
 __global__ void __launch_bounds__(256) k_rbgs(Grid u, Grid b, float h2, int color,
-                                              int periodic, float gam, int zero_start) {
-  d_rbgs(bi_native(), u, b, h2, color, periodic, gam, zero_start);
+                                              int periodic, float gam, int zero_start, float d0) {
+  d_rbgs(bi_native(), u, b, h2, color, periodic, gam, zero_start, d0);
 }
 
 // ---------------------------------------------------------------------------
@@ -98,7 +113,7 @@ __global__ void __launch_bounds__(256) k_rbgs(Grid u, Grid b, float h2, int colo
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void d_resid_restrict(const BI& bi, Grid u, Grid b, float inv_h2,
                                                         Grid uc, Grid bc, int periodic,
-                                                        float gam){
+                                                        float gam, float d0){
   const int s = u.s;
   const int sc = uc.s;
   int I = bi.x * blockDim.x + threadIdx.x;
@@ -140,7 +155,7 @@ __device__ __forceinline__ void d_resid_restrict(const BI& bi, Grid u, Grid b, f
         const float xm = dx ? V[dz][dy][0] : XM[dz][dy], xp = dx ? XP[dz][dy] : V[dz][dy][1];
         const float ym = dy ? V[dz][0][dx] : YM[dz][dx], yp = dy ? YP[dz][dx] : V[dz][1][dx];
         const float zm = dz ? V[0][dy][dx] : ZM[dy][dx], zp = dz ? ZP[dy][dx] : V[1][dy][dx];
-        float diag = (periodic || gam == 0.0f) ? 6.0f : bnd_diag(i, j, k, s, gam);
+        float diag = mg_simple(periodic, gam, d0) ? 6.0f : mg_diag(i, j, k, s, periodic, gam, d0);
         float s0 = nb6(xm, xp, ym, yp, zm, zp);
         acc = __fadd_rn(acc, resid_value(s0, V[dz][dy][dx], b.base[gidx(b, i, j, k)], diag,
                                          inv_h2));
@@ -152,8 +167,8 @@ __device__ __forceinline__ void d_resid_restrict(const BI& bi, Grid u, Grid b, f
 
 __global__ void __launch_bounds__(256) k_resid_restrict(Grid u, Grid b, float inv_h2,
                                                         Grid uc, Grid bc, int periodic,
-                                                        float gam) {
-  d_resid_restrict(bi_native(), u, b, inv_h2, uc, bc, periodic, gam);
+                                                        float gam, float d0) {
+  d_resid_restrict(bi_native(), u, b, inv_h2, uc, bc, periodic, gam, d0);
 }
 
 // ---------------------------------------------------------------------------
@@ -334,7 +349,7 @@ template <bool PERIODIC, bool SIMPLE, bool ZERO>
 struct Rbgs2 {
   static constexpr int RING = 6;
   const Grid win, wout, b;
-  const float h2, gam;
+  const float h2, gam, d0;
   const int s, x0, y0, z0, z1, ly, lx0, y, xa, me;
   float* sp;
   float* pu;
@@ -422,12 +437,14 @@ struct Rbgs2 {
         if ((st & 1) == 0) {  // red: partner and z neighbours are black
           const float s0 = nb6(xv, K[q], ym, yp, K[qm], K[qp]);
           nv = SIMPLE ? gs_value(s0, BR[q], h2, true, 6.0f)
-                      : gs_value(s0, BR[q], h2, false, bnd_diag(xa + kc, y, p, s, gam));
+                      : gs_value(s0, BR[q], h2, false,
+                                 mg_diag(xa + kc, y, p, s, PERIODIC, gam, d0));
           R[q] = nv;
         } else {              // black: partner and z neighbours are red
           const float s0 = nb6(xv, R[q], ym, yp, R[qm], R[qp]);
           nv = SIMPLE ? gs_value(s0, BK[q], h2, true, 6.0f)
-                      : gs_value(s0, BK[q], h2, false, bnd_diag(xa + kc, y, p, s, gam));
+                      : gs_value(s0, BK[q], h2, false,
+                                 mg_diag(xa + kc, y, p, s, PERIODIC, gam, d0));
           K[q] = nv;
         }
         *c = nv;
@@ -448,12 +465,12 @@ struct Rbgs2 {
 
 template <bool PERIODIC, bool SIMPLE, bool ZERO>
 __global__ void __launch_bounds__(F2_NT, 2) k_rbgs2(Grid win, Grid wout, Grid b, float h2,
-                                                    float gam, int zc) {
+                                                    float gam, float d0, int zc) {
   extern __shared__ float f2_smem[];
   const int s = wout.s;
   const int ly = threadIdx.x / F2_PW, lx0 = 2 * (threadIdx.x - ly * F2_PW);
   const int x0 = blockIdx.x * F2_TX, y0 = blockIdx.y * F2_TY, z0 = blockIdx.z * zc;
-  Rbgs2<PERIODIC, SIMPLE, ZERO> g{win, wout, b, h2, gam, s, x0, y0, z0, min(z0 + zc, s), ly,
+  Rbgs2<PERIODIC, SIMPLE, ZERO> g{win, wout, b, h2, gam, d0, s, x0, y0, z0, min(z0 + zc, s), ly,
                                   lx0, y0 - F2_H + ly, x0 - F2_H + lx0, ly * F2_W + lx0};
   g.sp = f2_smem;
   g.pu = g.sp + F2_R * F2_PL;
@@ -524,6 +541,8 @@ cudaError_t mg_prepare() {
   set(k_rbgs2<false, true, true>);
   set(k_rbgs2<true, true, false>);
   set(k_rbgs2<true, true, true>);
+  set(k_rbgs2<true, false, false>);
+  set(k_rbgs2<true, false, true>);
   return e;
 }
 
@@ -536,14 +555,17 @@ int rbgs2_zchunk(int s) {
 }
 
 void launch_rbgs2(cudaStream_t st, Grid win, Grid wout, Grid b, float h2, int periodic,
-                  float gam, bool zero_start, int zc) {
+                  float gam, bool zero_start, int zc, float d0) {
   if (zc <= 0) zc = rbgs2_zchunk(wout.s);
   dim3 grid((unsigned)((wout.s + F2_TX - 1) / F2_TX), (unsigned)((wout.s + F2_TY - 1) / F2_TY),
             (unsigned)((wout.s + zc - 1) / zc));
-  const bool simple = periodic || gam == 0.0f;
-#define PM_RBGS2(P, S, Z) k_rbgs2<P, S, Z><<<grid, F2_NT, F2_SMEM, st>>>(win, wout, b, h2, gam, zc)
-  if (periodic) {
+  const bool simple = (periodic || gam == 0.0f) && d0 == 6.0f;
+#define PM_RBGS2(P, S, Z) \
+  k_rbgs2<P, S, Z><<<grid, F2_NT, F2_SMEM, st>>>(win, wout, b, h2, gam, d0, zc)
+  if (periodic && simple) {
     if (zero_start) PM_RBGS2(true, true, true); else PM_RBGS2(true, true, false);
+  } else if (periodic) {
+    if (zero_start) PM_RBGS2(true, false, true); else PM_RBGS2(true, false, false);
   } else if (simple) {
     if (zero_start) PM_RBGS2(false, true, true); else PM_RBGS2(false, true, false);
   } else {
@@ -570,7 +592,13 @@ struct CmgArgs {
   int periodic;
   int level;   // multigrid level of the top grid
   int sweeps;  // bottom sweeps
+  float sig0;  // diagonal shift per unit h^2 of level 0 (0: Poisson)
 };
+
+// base diagonal of level l: 6 + sig0 4^l
+__device__ __forceinline__ float cmg_d0(const CmgArgs& a, int l) {
+  return 6.0f + a.sig0 * (float)(1 << (2 * l));
+}
 
 __device__ __forceinline__ float cmg_gam(const CmgArgs& a, int l) {
   float H = (float)(1 << l);
@@ -579,7 +607,8 @@ __device__ __forceinline__ float cmg_gam(const CmgArgs& a, int l) {
 
 // one colour (or, for odd S, a lexicographic pass by one thread)
 template <int S>
-__device__ void c_sweep(float* u, const float* b, float h2, float gam, int periodic, int color) {
+__device__ void c_sweep(float* u, const float* b, float h2, float gam, int periodic, int color,
+                        float d0) {
   constexpr int N3 = S * S * S;
   const bool simple = periodic || gam == 0.0f;
   auto upd = [&](int t) {
@@ -590,7 +619,7 @@ __device__ void c_sweep(float* u, const float* b, float h2, float gam, int perio
     float sum = u[sui<S>(im, j, k)] + u[sui<S>(ip, j, k)] + u[sui<S>(i, jm, k)] +
                 u[sui<S>(i, jp, k)] + u[sui<S>(i, j, km)] + u[sui<S>(i, j, kp)];
     int nb = (i == 0) + (i == S - 1) + (j == 0) + (j == S - 1) + (k == 0) + (k == S - 1);
-    u[sui<S>(i, j, k)] = (sum - h2 * b[t]) / (simple ? 6.0f : 6.0f + gam * (float)nb);
+    u[sui<S>(i, j, k)] = (sum - h2 * b[t]) / (simple ? d0 : d0 + gam * (float)nb);
   };
   if (S & 1) {
     if (threadIdx.x == 0)
@@ -605,16 +634,17 @@ __device__ void c_sweep(float* u, const float* b, float h2, float gam, int perio
 }
 
 template <int S>
-__device__ void c_smooth(float* u, const float* b, float h2, float gam, int periodic, int n) {
+__device__ void c_smooth(float* u, const float* b, float h2, float gam, int periodic, int n,
+                         float d0) {
   for (int w = 0; w < n; ++w) {
-    c_sweep<S>(u, b, h2, gam, periodic, 0);
-    if (!(S & 1)) c_sweep<S>(u, b, h2, gam, periodic, 1);
+    c_sweep<S>(u, b, h2, gam, periodic, 0, d0);
+    if (!(S & 1)) c_sweep<S>(u, b, h2, gam, periodic, 1, d0);
   }
 }
 
 template <int S>
 __device__ void c_restrict(const float* u, const float* b, float* uc, float* bc, float inv_h2,
-                           float gam, int periodic) {
+                           float gam, int periodic, float d0) {
   constexpr int SC = S / 2;
   const bool simple = periodic || gam == 0.0f;
   for (int T = threadIdx.x; T < SC * SC * SC; T += blockDim.x) {
@@ -629,7 +659,7 @@ __device__ void c_restrict(const float* u, const float* b, float* uc, float* bc,
       int nb = (i == 0) + (i == S - 1) + (j == 0) + (j == S - 1) + (k == 0) + (k == S - 1);
       float lap = u[sui<S>(im, j, k)] + u[sui<S>(ip, j, k)] + u[sui<S>(i, jm, k)] +
                   u[sui<S>(i, jp, k)] + u[sui<S>(i, j, km)] + u[sui<S>(i, j, kp)] -
-                  (simple ? 6.0f : 6.0f + gam * (float)nb) * u[sui<S>(i, j, k)];
+                  (simple ? d0 : d0 + gam * (float)nb) * u[sui<S>(i, j, k)];
       acc += b[(k * S + j) * S + i] - lap * inv_h2;
     }
     bc[T] = 0.125f * acc;
@@ -692,14 +722,17 @@ __device__ void c_vcycle(float* mem, const CmgArgs& a, int l, float* red) {
   float* u = mem;
   float* b = mem + (S + 2) * (S + 2) * (S + 2);
   const float H = (float)(1 << l), h2 = H * H;
+  // the periodic Poisson problem is singular: project out the mean (not
+  // needed, and wrong, with a diagonal shift)
+  const bool proj = a.periodic && a.sig0 == 0.0f;
   if constexpr (S <= 4 || (S & 1)) {
-    if (a.periodic) {
+    if (proj) {
       float m = c_mean<S>(b, false, red);
       for (int t = threadIdx.x; t < S * S * S; t += blockDim.x) b[t] -= m;
       __syncthreads();
     }
-    c_smooth<S>(u, b, h2, cmg_gam(a, l), a.periodic, a.sweeps);
-    if (a.periodic) {
+    c_smooth<S>(u, b, h2, cmg_gam(a, l), a.periodic, a.sweeps, cmg_d0(a, l));
+    if (proj) {
       float m = c_mean<S>(u, true, red);
       for (int t = threadIdx.x; t < S * S * S; t += blockDim.x) {
         int i = t % S, j = (t / S) % S, k = t / (S * S);
@@ -711,11 +744,11 @@ __device__ void c_vcycle(float* mem, const CmgArgs& a, int l, float* red) {
     constexpr int SC = S / 2;
     float* uc = b + S * S * S;
     float* bc = uc + (SC + 2) * (SC + 2) * (SC + 2);
-    c_smooth<S>(u, b, h2, cmg_gam(a, l), a.periodic, 2);
-    c_restrict<S>(u, b, uc, bc, 1.0f / h2, cmg_gam(a, l), a.periodic);
+    c_smooth<S>(u, b, h2, cmg_gam(a, l), a.periodic, 2, cmg_d0(a, l));
+    c_restrict<S>(u, b, uc, bc, 1.0f / h2, cmg_gam(a, l), a.periodic, cmg_d0(a, l));
     c_vcycle<SC>(uc, a, l + 1, red);
     c_prolong<S>(uc, u, cmg_gam(a, l + 1), a.periodic);
-    c_smooth<S>(u, b, h2, cmg_gam(a, l), a.periodic, 2);
+    c_smooth<S>(u, b, h2, cmg_gam(a, l), a.periodic, 2, cmg_d0(a, l));
   }
 }
 
@@ -751,10 +784,11 @@ constexpr int CMG_SMEM_FLOATS = 11776;  // 16^3 -> 8^3 -> 4^3 needs 11720
 // level: multigrid level index of (u, b); sides 16, 12, 8, 6, 4, 3 supported.
 // zero_top: the top level's iterate starts at zero (its interior is not read).
 __global__ void __launch_bounds__(1024) k_coarse_mg(Grid u, Grid b, int level, int periodic,
-                                                    int coarse_sweeps, int zero_top) {
+                                                    int coarse_sweeps, int zero_top,
+                                                    float sig0) {
   __shared__ float sm[CMG_SMEM_FLOATS];
   __shared__ float red[32];
-  CmgArgs a{periodic, level, coarse_sweeps};
+  CmgArgs a{periodic, level, coarse_sweeps, sig0};
   switch (u.s) {
     case 16: c_run<16>(u, b, sm, a, red, zero_top); break;
     case 12: c_run<12>(u, b, sm, a, red, zero_top); break;
@@ -767,8 +801,8 @@ __global__ void __launch_bounds__(1024) k_coarse_mg(Grid u, Grid b, int level, i
 }
 
 void launch_coarse_mg(cudaStream_t st, Grid u, Grid b, int level, int periodic,
-                      int coarse_sweeps, bool zero_top) {
-  k_coarse_mg<<<1, 1024, 0, st>>>(u, b, level, periodic, coarse_sweeps, zero_top ? 1 : 0);
+                      int coarse_sweeps, bool zero_top, float sig0) {
+  k_coarse_mg<<<1, 1024, 0, st>>>(u, b, level, periodic, coarse_sweeps, zero_top ? 1 : 0, sig0);
   note_launch();
 }
 
@@ -778,15 +812,15 @@ static inline dim3 grid_half(int s) {
 static inline dim3 grid_full(int s) { return dim3((unsigned)((s + 31) / 32), (unsigned)((s + 7) / 8), (unsigned)s); }
 
 void launch_rbgs(cudaStream_t st, Grid u, Grid b, float h2, int color, int periodic,
-                 float gam, bool zero_start) {
+                 float gam, bool zero_start, float d0) {
   k_rbgs<<<grid_half(u.s), dim3(32, 8), 0, st>>>(u, b, h2, color, periodic, gam,
-                                                 zero_start ? 1 : 0);
+                                                 zero_start ? 1 : 0, d0);
   note_launch();
 }
 void launch_resid_restrict(cudaStream_t st, Grid u, Grid b, float inv_h2, Grid uc, Grid bc,
-                           int periodic, float gam) {
+                           int periodic, float gam, float d0) {
   k_resid_restrict<<<grid_full(uc.s), dim3(32, 8), 0, st>>>(u, b, inv_h2, uc, bc, periodic,
-                                                            gam);
+                                                            gam, d0);
   note_launch();
 }
 // ghost layer of src copied into d1 and d2 (same side, any layouts)
@@ -839,7 +873,8 @@ template <bool CORRECT>
 __device__ __forceinline__ void d_defect(const BI& bi, Grid ph, Grid pl, Grid e, Grid qh, Grid ql,
                                                 Grid fh, Grid fl, Grid rb, int periodic,
                                                 int write_r, double* __restrict__ partial,
-                                                unsigned int* counter, double* __restrict__ out){
+                                                unsigned int* counter, double* __restrict__ out,
+                                                float d0, float d0l){
   const int s = ph.s;
   int i = bi.x * blockDim.x + threadIdx.x;
   int j = bi.y * blockDim.y + threadIdx.y;
@@ -909,10 +944,11 @@ __device__ __forceinline__ void d_defect(const BI& bi, Grid ph, Grid pl, Grid e,
         sacc = t.hi;
         comp += t.lo;
       }
-      df p6 = two_prod(6.0f, H[0]);
+      df p6 = two_prod(d0, H[0]);
+      p6.lo = __fmaf_rn(d0l, H[0], p6.lo);  // d0 = d0 + d0l exactly (diffusion shift)
       t = two_sum(sacc, p6.hi); sacc = t.hi; comp += t.lo + p6.lo;
       comp -= (Lo[1] + Lo[2]) + (Lo[3] + Lo[4]) + (Lo[5] + Lo[6]);
-      comp += 6.0f * Lo[0];
+      comp += d0 * Lo[0];
       float r = sacc + comp;
       if (write_r) rb.base[gidx(rb, i, j, k)] = r;
       r2 = __fmaf_rn(r, r, r2);
@@ -959,8 +995,10 @@ template <bool CORRECT>
 __global__ void __launch_bounds__(256) k_defect(Grid ph, Grid pl, Grid e, Grid qh, Grid ql,
                                                 Grid fh, Grid fl, Grid rb, int periodic,
                                                 int write_r, double* __restrict__ partial,
-                                                unsigned int* counter, double* __restrict__ out) {
-  d_defect<CORRECT>(bi_native(), ph, pl, e, qh, ql, fh, fl, rb, periodic, write_r, partial, counter, out);
+                                                unsigned int* counter, double* __restrict__ out,
+                                                float d0, float d0l) {
+  d_defect<CORRECT>(bi_native(), ph, pl, e, qh, ql, fh, fl, rb, periodic, write_r, partial,
+                    counter, out, d0, d0l);
 }
 
 static inline dim3 grid_defect(int s) {
@@ -973,13 +1011,16 @@ int defect_blocks(int s) {
 
 void launch_defect(cudaStream_t st, Grid ph, Grid pl, const Grid* e, Grid qh, Grid ql,
                    Grid fh, Grid fl, Grid rb, int periodic, bool write_r, double* partial,
-                   unsigned int* counter, double* out) {
+                   unsigned int* counter, double* out, double d0) {
+  const float d0h = (float)d0, d0l = (float)(d0 - (double)d0h);
   if (e)
     k_defect<true><<<grid_defect(ph.s), dim3(32, 8), 0, st>>>(
-        ph, pl, *e, qh, ql, fh, fl, rb, periodic, write_r ? 1 : 0, partial, counter, out);
+        ph, pl, *e, qh, ql, fh, fl, rb, periodic, write_r ? 1 : 0, partial, counter, out, d0h,
+        d0l);
   else
     k_defect<false><<<grid_defect(ph.s), dim3(32, 8), 0, st>>>(
-        ph, pl, ph, qh, ql, fh, fl, rb, periodic, write_r ? 1 : 0, partial, counter, out);
+        ph, pl, ph, qh, ql, fh, fl, rb, periodic, write_r ? 1 : 0, partial, counter, out, d0h,
+        d0l);
   note_launch();
 }
 
@@ -1159,7 +1200,7 @@ __global__ void __launch_bounds__(256) kb_rbgs(const RbgsDesc* d, const BTable* 
   BI bi;
   if (!batch_map(d, t, active, q, bi)) return;
   const RbgsDesc& e = d[q];
-  d_rbgs(bi, e.u, e.b, e.h2, e.color, e.periodic, e.gam, e.zero_start);
+  d_rbgs(bi, e.u, e.b, e.h2, e.color, e.periodic, e.gam, e.zero_start, 6.0f);
 }
 __global__ void __launch_bounds__(256) kb_restrict(const RestrictDesc* d, const BTable* t,
                                                    const int* active) {
@@ -1167,7 +1208,7 @@ __global__ void __launch_bounds__(256) kb_restrict(const RestrictDesc* d, const 
   BI bi;
   if (!batch_map(d, t, active, q, bi)) return;
   const RestrictDesc& e = d[q];
-  d_resid_restrict(bi, e.u, e.b, e.inv_h2, e.uc, e.bc, e.periodic, e.gam);
+  d_resid_restrict(bi, e.u, e.b, e.inv_h2, e.uc, e.bc, e.periodic, e.gam, 6.0f);
 }
 __global__ void __launch_bounds__(256) kb_prolong(const ProlongDesc* d, const BTable* t,
                                                   const int* active) {
@@ -1185,7 +1226,7 @@ __global__ void __launch_bounds__(1024) kb_coarse_mg(const CmgDesc* d, const BTa
   const CmgDesc& e = d[q];
   __shared__ float sm[CMG_SMEM_FLOATS];
   __shared__ float red[32];
-  CmgArgs a{e.periodic, e.level, e.sweeps};
+  CmgArgs a{e.periodic, e.level, e.sweeps, 0.0f};
   switch (e.u.s) {
     case 16: c_run<16>(e.u, e.b, sm, a, red, e.zero_top); break;
     case 12: c_run<12>(e.u, e.b, sm, a, red, e.zero_top); break;
@@ -1204,10 +1245,10 @@ __global__ void __launch_bounds__(256) kb_defect(const DefectDesc* d, const BTab
   const DefectDesc& e = d[q];
   if (e.correct)
     d_defect<true>(bi, e.ph, e.pl, e.e, e.qh, e.ql, e.fh, e.fl, e.rb, e.periodic, e.write_r,
-                   e.partial, e.counter, e.out);
+                   e.partial, e.counter, e.out, 6.0f, 0.0f);
   else
     d_defect<false>(bi, e.ph, e.pl, e.e, e.qh, e.ql, e.fh, e.fl, e.rb, e.periodic, e.write_r,
-                    e.partial, e.counter, e.out);
+                    e.partial, e.counter, e.out, 6.0f, 0.0f);
 }
 __global__ void __launch_bounds__(256) kb_predict(const PredictDesc* d, const BTable* t) {
   int q;

@@ -25,29 +25,34 @@ void launch_source(cudaStream_t st, int grid, unsigned long long* rho, int n, in
 void launch_source_f64(cudaStream_t st, int grid, const double* delta, int n, Grid fh,
                        Grid fl, double S, bool moments, double* partial,
                        unsigned int* counter, double* out);
+void launch_diff_rhs(cudaStream_t st, int grid, Grid sh, Grid sl, double scale, Grid ph,
+                     Grid pl, double sig, Grid gh, Grid gl, Grid qh, Grid ql, bool stash,
+                     double* partial, unsigned int* counter, double* out);
 void launch_boundary(cudaStream_t st, Grid ph, Grid pl, int n, int lo, const double* mom,
                      double S, bool want_lo);
 
 // k_mg.cu
+// d0: base diagonal of the operator sum_nb u - d0 u (6: Poisson; 6 + sig h^2:
+// an implicit diffusion substep)
 void launch_rbgs(cudaStream_t st, Grid u, Grid b, float h2, int color, int periodic,
-                 float gam, bool zero_start = false);
+                 float gam, bool zero_start = false, float d0 = 6.0f);
 // the rest of a V-cycle from a level of side <= CMG_MAX_SIDE in one CTA
 constexpr int CMG_MAX_SIDE = 16;
 void launch_coarse_mg(cudaStream_t st, Grid u, Grid b, int level, int periodic,
-                      int coarse_sweeps, bool zero_top);
+                      int coarse_sweeps, bool zero_top, float sig0 = 0.0f);
 void launch_resid_restrict(cudaStream_t st, Grid u, Grid b, float inv_h2, Grid uc, Grid bc,
-                           int periodic, float gam);
+                           int periodic, float gam, float d0 = 6.0f);
 void launch_prolong_to(cudaStream_t st, Grid uc, Grid u, Grid w, int periodic, float gam_c);
 void launch_copy_ghosts(cudaStream_t st, Grid src, Grid d1, Grid d2);
 void launch_rbgs2(cudaStream_t st, Grid win, Grid wout, Grid b, float h2, int periodic, float gam,
-                  bool zero_start, int zc = 0);
+                  bool zero_start, int zc = 0, float d0 = 6.0f);
 int rbgs2_zchunk(int s);
 cudaError_t mg_prepare();
 void launch_prolong(cudaStream_t st, Grid uc, Grid u, int periodic, float gam_c);
 // residual of Phi (e == NULL) or of Phi + e written to (qh, ql) (e != NULL)
 void launch_defect(cudaStream_t st, Grid ph, Grid pl, const Grid* e, Grid qh, Grid ql,
                    Grid fh, Grid fl, Grid rb, int periodic, bool write_r, double* partial,
-                   unsigned int* counter, double* out);
+                   unsigned int* counter, double* out, double d0 = 6.0);
 int defect_blocks(int s);
 void launch_correct(cudaStream_t st, Grid ph, Grid pl, Grid e);
 void launch_to_dense(cudaStream_t st, Grid g, float* d, bool add);

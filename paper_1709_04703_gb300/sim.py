@@ -10,6 +10,7 @@ from . import _lib as L
 _PREC = {"mixed": L.PM_MIXED, "fp32": L.PM_FP32_PLAIN}
 _GUESS = {"warm": L.PM_GUESS_WARM, "zero": L.PM_GUESS_ZERO, "learned": L.PM_GUESS_LEARNED}
 _BC = {"paper": L.PM_BC_PAPER, "open": L.PM_BC_OPEN, "periodic": L.PM_BC_PERIODIC}
+_GRAVITY = {"poisson": L.PM_GRAVITY_POISSON, "diffusion": L.PM_GRAVITY_DIFFUSION}
 
 
 def _stream():
@@ -162,7 +163,8 @@ class Sim:
     def __init__(self, pos, mom, ids, n_mesh, box, a_init, a_final, n_steps,
                  rtol=1e-7, precision="mixed", guess="warm", bc="paper",
                  shrink=True, buffer_cells=1.0, max_vcycles=50, store_forces=False,
-                 omega_m=0.3, omega_l=0.7, host_init=False):
+                 omega_m=0.3, omega_l=0.7, host_init=False, gravity="poisson",
+                 c_eff_factor=0.019):
         lib = L.load()
         cfg = L.PmConfig()
         lib.pm_config_default(C.byref(cfg))
@@ -178,6 +180,8 @@ class Sim:
         cfg.shrink = 1 if shrink else 0
         cfg.buffer_cells = float(buffer_cells)
         cfg.store_forces = 1 if store_forces else 0
+        cfg.gravity = _GRAVITY[gravity]
+        cfg.c_eff_factor = float(c_eff_factor)
         self.cfg = cfg
         self.n_particles = int(len(pos))
         # the context runs on its own stream so that its V-cycle can be
