@@ -137,17 +137,21 @@ def _plain_floor(pos, mom, ids, cfg):
     return floor
 
 
-def _variant(pos, mom, ids, cfg, K, rtol, precision, guess="warm", net=None):
+def _variant(pos, mom, ids, cfg, K, rtol, precision, guess="warm", net=None,
+             gravity="poisson"):
     """The same K steps in another solver configuration, device-timed."""
     import torch
     from paper_1709_04703_gb300 import _lib as L
-    sim = _new_sim(pos, mom, ids, cfg, rtol, precision, guess)
+    from paper_1709_04703_gb300.sim import Sim
+    sim = Sim(pos, mom, ids, cfg["n"], cfg["box"], cfg["a_init"], cfg["a_final"],
+              cfg["steps"], rtol=rtol, precision=precision, max_vcycles=100, guess=guess,
+              gravity=gravity)
     if net is not None:
         sim.set_guess(net)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     ev0.record(sim.stream)
-    out = {"precision": precision, "guess": guess, "rtol": rtol}
+    out = {"precision": precision, "guess": guess, "rtol": rtol, "gravity": gravity}
     try:
         sim.step(K)
     except L.PmError as e:
@@ -369,6 +373,9 @@ def run_ours(args):
                                                            "mixed"),
                    f"plain_fp32_rtol_{STRICT_RTOL:g}": _variant(pos, mom, ids, cfg, 1,
                                                                 STRICT_RTOL, "fp32")}
+        # the paper's diffusion-equation gravity (two implicit half-substeps)
+        compare["diffusion_gravity"] = _variant(pos, mom, ids, cfg, K, rtol, "mixed",
+                                                gravity="diffusion")
         net = train_guess.load(train_guess.DEFAULT_WEIGHTS)
         for tol in (rtol, STRICT_RTOL):
             key = "learned_guess" + ("" if tol == rtol else f"_rtol_{tol:g}")
