@@ -138,20 +138,22 @@ def _plain_floor(pos, mom, ids, cfg):
 
 
 def _variant(pos, mom, ids, cfg, K, rtol, precision, guess="warm", net=None,
-             gravity="poisson"):
+             gravity="poisson", bc="paper", shrink=True):
     """The same K steps in another solver configuration, device-timed."""
     import torch
     from paper_1709_04703_gb300 import _lib as L
     from paper_1709_04703_gb300.sim import Sim
     sim = Sim(pos, mom, ids, cfg["n"], cfg["box"], cfg["a_init"], cfg["a_final"],
               cfg["steps"], rtol=rtol, precision=precision, max_vcycles=100, guess=guess,
-              gravity=gravity)
+              gravity=gravity, bc=bc, shrink=shrink)
     if net is not None:
         sim.set_guess(net)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     ev0.record(sim.stream)
     out = {"precision": precision, "guess": guess, "rtol": rtol, "gravity": gravity}
+    if not shrink:
+        out["box"] = "fixed periodic (no shrinking)"
     try:
         sim.step(K)
     except L.PmError as e:
@@ -311,6 +313,75 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
     return 0
 
+TABLE4 = {512.0: 1.08, 2048.0: 1.44, 8192.0: 3.02}   # Table 4, 512^3 particles
+
+
+def _timed_run(pos, mom, ids, n, box, a0, steps, rtol, gravity, shrink):
+    """One whole run, each step device-timed on the context stream; per-step
+    active particles and milliseconds."""
+    import torch
+    from paper_1709_04703_gb300.sim import Sim
+    sim = Sim(pos, mom, ids, n, box, a0, 1.0, steps, rtol=rtol, precision="mixed",
+              max_vcycles=100, gravity=gravity, bc="paper" if shrink else "periodic",
+              shrink=shrink)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    n_act = []
+    torch.cuda.synchronize()
+    ev[0].record(sim.stream)
+    for k in range(steps):
+        n_act.append(sim.stats()["n_active"])
+        sim.step(1)
+        ev[k + 1].record(sim.stream)
+    torch.cuda.synchronize()
+    ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    st = sim.stats()
+    sim.close()
+    return {"ms": sum(ms), "ms_step": ms, "n_active": n_act,
+            "vcycles_total": int(st["vcycles_total"])}
+
+
+def run_shrink_table(args):
+    """--workload shrink_table: the whole-run time of the fixed periodic box
+    over that of the shrinking box (Table 4's speed-up, Sec. 3.3), with the
+    paper's run shape: n^3 particles on an n^3 mesh, a from 1/41 (z = 40) to
+    1 in 1000 steps uniform in a, boxes 512, 2048 and 8192 Mpc/h.  Both
+    gravities: the diffusion equation (the paper's pair of codes) and the
+    static Poisson solve.  The same seeded ICs (in cell units) serve every
+    box; the box sets the lightcone radius in cells and so the shrinking."""
+    import torch
+    from paper_1709_04703_gb300 import ics
+    torch.cuda.set_device(0)
+    n, steps, a0 = args.table_n, args.steps if args.steps_given else 1000, 1.0 / 41.0
+    tol = args.rtol if args.rtol is not None else 1e-5
+    pos, mom, ids = ics.zeldovich(n, -1.5, 0.5, 1, a0)
+    # warm-up: a few steps of each kind
+    for grav in args.gravities:
+        for shrink in (True, False):
+            _timed_run(pos, mom, ids, n, 8192.0, a0, max(3, args.warmup), tol, grav, shrink)
+    rows = []
+    for grav in args.gravities:
+        for box in (512.0, 2048.0, 8192.0):
+            sh = _timed_run(pos, mom, ids, n, box, a0, steps, tol, grav, True)
+            fx = _timed_run(pos, mom, ids, n, box, a0, steps, tol, grav, False)
+            q = [steps // 4, steps // 2, (3 * steps) // 4]
+            rows.append({
+                "gravity": grav, "box_mpch": box, "shrink_s": round(sh["ms"] * 1e-3, 3),
+                "fixed_s": round(fx["ms"] * 1e-3, 3), "speedup": round(fx["ms"] / sh["ms"], 3),
+                "paper_speedup": TABLE4[box],
+                # Figs. 5 and 6 at a quarter, half and three quarters of the run
+                "n_active_frac": [round(sh["n_active"][k] / n**3, 4) for k in q],
+                "ms_step_ratio": [round(sh["ms_step"][k] / fx["ms_step"][k], 4) for k in q],
+                "vcycles": [sh["vcycles_total"], fx["vcycles_total"]]})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    line = {"metric": "whole-run speed-up, shrinking vs fixed periodic box", "unit": "x",
+            "higher_is_better": True, "n_gpus": 1, "steps": steps,
+            "data": "synthetic (seeded Zel'dovich ICs)",
+            "config": {"workload": "shrink_table", "n_mesh": n, "n_particles": n**3,
+                       "a": [a0, 1.0], "rtol": tol, "precision": "mixed"},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
 
 def run_ours(args):
     import torch
@@ -376,6 +447,9 @@ def run_ours(args):
         # the paper's diffusion-equation gravity (two implicit half-substeps)
         compare["diffusion_gravity"] = _variant(pos, mom, ids, cfg, K, rtol, "mixed",
                                                 gravity="diffusion")
+        # the same steps in the fixed periodic box (every particle, every step)
+        compare["no_shrink"] = _variant(pos, mom, ids, cfg, K, rtol, "mixed", bc="periodic",
+                                        shrink=False)
         net = train_guess.load(train_guess.DEFAULT_WEIGHTS)
         for tol in (rtol, STRICT_RTOL):
             key = "learned_guess" + ("" if tol == rtol else f"_rtol_{tol:g}")
@@ -477,14 +551,21 @@ def main():
                     help="skip the plain-FP32 and learned-guess runs of the same steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
-    ap.add_argument("--workload", choices=["pm256", "batch48"], default="pm256")
+    ap.add_argument("--workload", choices=["pm256", "batch48", "shrink_table"], default="pm256")
+    ap.add_argument("--table-n", type=int, default=512,
+                    help="shrink_table: particles and mesh per side")
+    ap.add_argument("--gravities", nargs="+", default=["diffusion", "poisson"],
+                    choices=["diffusion", "poisson"], help="shrink_table: gravity solvers")
     args = ap.parse_args()
+    args.steps_given = "--steps" in sys.argv
     if args.impl == "reference":
         return run_reference(args)
     from paper_1709_04703_gb300 import build
     build.build()
     if args.workload == "batch48":
         return run_batch(args)
+    if args.workload == "shrink_table":
+        return run_shrink_table(args)
     return run_ours(args)
 
 
