@@ -35,10 +35,15 @@ library, which implements them independently):
   c at the centres of one ghost-cell layer.
 * Active mesh cube in the open phase: half-width m = ceil(R) + 1 cells, side
   the smallest 2^j or 3*2^j >= 2m (multigrid-friendly), at most n.
-* Density contrast: delta = rho/rho_mean - 1 with the cosmic mean N/n^3;
-  the "-1" background is subtracted only on cells whose centre lies inside
-  the keep cube (the whole box in the periodic phase), so that cells of the
-  mesh cube outside the lightcone carry no spurious negative source.
+* Density contrast: delta = rho/rho_mean - W with the cosmic mean N/n^3 and
+  W the mean density's own CIC image: the keep cube [c-R, c+R]^3 filled
+  uniformly and assigned with the deposit's tent, i.e. per axis
+  w_i = T(c + R - x_i) - T(c - R - x_i), T the integral of the tent
+  max(0, 1 - |t|), x_i = i + 0.5, and W = w_x w_y w_z (W = 1 everywhere in
+  the periodic phase).  A uniform density inside the keep cube then has
+  zero mean contrast on every cell, the edge cells included; cells of the
+  mesh cube beyond the lightcone carry no source; and sum W = (2R)^3, the
+  keep cube's volume, changes smoothly as R shrinks.
 * Fixed-point CIC (not in the paper): on the float position u,
   v = u - 0.5, i = floor(v), dq = floor(v*2^16) - i*2^16 in [0, 2^16);
   per-axis weights (2^16 - dq, dq); the product (<= 2^48) is added to an
@@ -81,12 +86,22 @@ def active_cube(R, n):
     return n // 2 - s // 2, s, False
 
 
-def background_range(R, n, periodic):
-    """Index range [b0, b1] of cells whose centre is inside the keep cube."""
+def tent_integral(u):
+    """T(u): integral of the CIC tent max(0, 1 - |t|) over t < u."""
+    u = np.asarray(u, dtype=np.float64)
+    return np.where(u <= -1.0, 0.0,
+                    np.where(u <= 0.0, 0.5 * (u + 1.0) * (u + 1.0),
+                             np.where(u <= 1.0, 1.0 - 0.5 * (1.0 - u) * (1.0 - u), 1.0)))
+
+
+def background_weights(R, n, lo, s, periodic):
+    """Per-axis weight w_i of the mean density on cells lo..lo+s-1: the CIC
+    image of the keep interval [c - R, c + R] (all ones when periodic)."""
     if periodic:
-        return 0, n - 1
+        return np.ones(s)
     c = n / 2
-    return math.ceil(c - R - 0.5), math.floor(c + R - 0.5)
+    x = np.arange(lo, lo + s) + 0.5
+    return tent_integral((c + R) - x) - tent_integral((c - R) - x)
 
 
 # --------------------------------------------------------------------------
@@ -140,11 +155,8 @@ def delta_cube(rho, n, lo, s, nbar, R, periodic):
     """Density contrast on the active cube [z,y,x] (s^3, float64)."""
     sub = rho[lo:lo + s, lo:lo + s, lo:lo + s].astype(np.float64)
     d = sub / (MASS_UNIT * nbar)
-    b0, b1 = background_range(R, n, periodic)
-    idx = np.arange(lo, lo + s)
-    inside = (idx >= b0) & (idx <= b1)
-    mask = inside[:, None, None] & inside[None, :, None] & inside[None, None, :]
-    return d - mask.astype(np.float64)
+    w = background_weights(R, n, lo, s, periodic)
+    return d - w[:, None, None] * w[None, :, None] * w[None, None, :]
 
 
 def multipoles(delta, lo, n):

@@ -291,6 +291,44 @@ def test_keep_boundary_is_inclusive():
     assert list(pm.keep_mask(pos, 9.5, 32)) == [True, True, False]
 
 
+def test_background_weights_partition_the_keep_interval():
+    """The tents of all cells sum to one at every point, so the weights of
+    the keep interval [c - R, c + R] sum to its length 2R, whatever R."""
+    n = 64
+    for R in (1.0, 3.5, 7.25, 12.0, 19.999):
+        lo, s, _ = pm.active_cube(R, n)
+        w = pm.background_weights(R, n, lo, s, False)
+        assert abs(w.sum() - 2 * R) < 1e-12, R
+        assert w.min() >= 0 and w.max() <= 1
+        np.testing.assert_allclose(w, w[::-1], rtol=0, atol=1e-14)   # centred on c = n/2
+        x = np.arange(lo, lo + s) + 0.5
+        assert np.all(w[np.abs(x - n / 2) <= R - 1] == 1.0)
+        assert np.all(w[np.abs(x - n / 2) >= R + 1] == 0.0)
+    assert np.all(pm.background_weights(5.0, 32, 0, 32, True) == 1.0)
+    # tent integral: 0, 1/2 at the node, 1, and the quadratic pieces
+    np.testing.assert_allclose(pm.tent_integral([-2.0, -1.0, -0.5, 0.0, 0.5, 1.0, 3.0]),
+                               [0.0, 0.0, 0.125, 0.5, 0.875, 1.0, 1.0], rtol=0, atol=0)
+
+
+def test_uniform_density_has_zero_contrast_on_every_cell():
+    """Particles filling the keep cube uniformly: delta sums to zero exactly
+    (the deposit conserves mass, the background sums to (2R)^3) and its
+    mean over each plane of cells, the edge planes included, is zero to the
+    sampling noise."""
+    n, R, N = 32, 9.3, 3_000_000
+    rng = np.random.default_rng(12)
+    pos = n / 2 + rng.uniform(-R, R, (N, 3))
+    lo, s, per = pm.active_cube(R, n)
+    rho, esc = pm.deposit(pos, n, lo, s, per)
+    assert esc == 0
+    nbar = N / (2 * R) ** 3                      # the density inside the cube
+    d = pm.delta_cube(rho, n, lo, s, nbar, R, per)
+    assert abs(d.sum()) < 1e-9 * (2 * R) ** 3
+    layer = d.mean(axis=(0, 1)) * s * s / np.count_nonzero(
+        pm.background_weights(R, n, lo, s, per)) ** 2
+    assert np.abs(layer).max() < 0.02, layer
+
+
 # ---------------------------------------------------------------- dynamics
 
 def test_free_particle_drift_integrates_schedule():
