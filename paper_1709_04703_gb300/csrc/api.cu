@@ -28,6 +28,7 @@ constexpr double C_OVER_H0 = 2997.92458;  // Mpc/h
 constexpr int SRC_GRID = 1216;            // 152 SMs x 8 blocks
 constexpr int COARSE_SWEEPS = 12;
 constexpr int FUSED_MIN = 192;  // smallest level side smoothed by the fused pass
+constexpr size_t BGW_OFF = 128;  // byte offset of the background weights in bgm
 
 // ---------------------------------------------------------------------------
 // FP64 cosmology on the host.  tau(a) = int_0^a da'/(a'^2 E), H0 = 1, with
@@ -147,7 +148,9 @@ struct pm_ctx {
   void* partial_m = nullptr;    // per-block int128 moments
   unsigned int* counter = nullptr;
   double* d_scal = nullptr;     // [0] ||f||^2, [1..10] moments, [11] ||r||^2, [12] sum phi
-  double* bgm = nullptr;        // background moments (10)
+  double* bgm = nullptr;        // background moments (10), then at BGW_OFF the weights
+  df* bgw = nullptr;            // per-axis mean-density weights w_g, g in [0, n)
+  std::vector<unsigned char> h_bg;  // host image of bgm + bgw
   unsigned long long* d_cnt = nullptr;  // [0] n_keep, [1] escaped
   int* d_overflow = nullptr;
   double* h_scal = nullptr;     // pinned mirrors
@@ -272,31 +275,46 @@ void keep_bounds(double c, double R, float* klo, float* khi) {
   *khi = h;
 }
 
+// Integral of the CIC tent max(0, 1 - |t|) over t < u.
+static double tent_integral(double u) {
+  if (u <= -1.0) return 0.0;
+  if (u <= 0.0) return 0.5 * (u + 1.0) * (u + 1.0);
+  if (u <= 1.0) return 1.0 - 0.5 * (1.0 - u) * (1.0 - u);
+  return 1.0;
+}
+
 pm_status set_cube(pm_ctx* ctx, int lo, int s, int periodic, double R) {
   bool same = ctx->cube_valid && lo == ctx->lo && s == ctx->s && periodic == ctx->periodic;
   ctx->lo = lo;
   ctx->s = s;
   ctx->periodic = periodic;
   ctx->cube_valid = true;
-  // background moments over the cells whose centre is in the keep cube
+  // mean-density term of delta: per axis the CIC image of the keep interval
+  // [c - R, c + R], w_g = T(c + R - x_g) - T(c - R - x_g) at x_g = g + 1/2
+  // (ones when periodic), and its moments about c (separable sums)
   const int n = ctx->n;
-  int b0 = 0, b1 = n - 1;
-  if (!periodic) {
-    double c = 0.5 * n;
-    b0 = std::max(lo, (int)std::ceil(c - R - 0.5));
-    b1 = std::min(lo + s - 1, (int)std::floor(c + R - 0.5));
+  double* h = (double*)ctx->h_bg.data();
+  df* hw = (df*)(ctx->h_bg.data() + BGW_OFF);
+  const double c = 0.5 * n;
+  double W0 = 0.0, W1 = 0.0, W2 = 0.0;
+  for (int g = 0; g < n; ++g) {
+    const double x = g + 0.5;
+    const double w = periodic ? 1.0 : tent_integral((c + R) - x) - tent_integral((c - R) - x);
+    hw[g].hi = (float)w;
+    hw[g].lo = (float)(w - (double)hw[g].hi);
+    if (g >= lo && g < lo + s) {
+      const double y = x - c;
+      W0 += w;
+      W1 += w * y;
+      W2 += w * y * y;
+    }
   }
-  double S1 = 0.0, S2 = 0.0;
-  long long L = b1 >= b0 ? b1 - b0 + 1 : 0;
-  for (int i = b0; i <= b1; ++i) {
-    double y = i + 0.5 - 0.5 * n;
-    S1 += y;
-    S2 += y * y;
-  }
-  double L2 = (double)L * L, L3 = L2 * L;
-  double h[10] = {L3, L2 * S1, L2 * S1, L2 * S1, L2 * S2, L2 * S2, L2 * S2,
-                  L * S1 * S1, L * S1 * S1, L * S1 * S1};
-  CK(cudaMemcpyAsync(ctx->bgm, h, sizeof(h), cudaMemcpyHostToDevice, ctx->st));
+  const double W00 = W0 * W0;
+  const double mom[10] = {W00 * W0, W00 * W1, W00 * W1, W00 * W1, W00 * W2, W00 * W2, W00 * W2,
+                          W0 * W1 * W1, W0 * W1 * W1, W0 * W1 * W1};
+  std::memcpy(h, mom, sizeof(mom));
+  CK(cudaMemcpyAsync(ctx->bgm, ctx->h_bg.data(), ctx->h_bg.size(), cudaMemcpyHostToDevice,
+                     ctx->st));
   if (same) return PM_OK;
   // multigrid level sides: halve while > 4
   ctx->ls.clear();
@@ -809,7 +827,9 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
   AL(ctx->partial_m, 16 * 10 * (size_t)maxblk);
   AL(ctx->counter, sizeof(unsigned int) * 4);
   AL(ctx->d_scal, sizeof(double) * 16);
-  AL(ctx->bgm, sizeof(double) * 10);
+  AL(ctx->bgm, BGW_OFF + sizeof(df) * (size_t)n);
+  ctx->bgw = (df*)((char*)ctx->bgm + BGW_OFF);
+  ctx->h_bg.assign(BGW_OFF + sizeof(df) * (size_t)n, 0);
   AL(ctx->d_cnt, sizeof(unsigned long long) * 4);
   AL(ctx->d_overflow, sizeof(int));
 #undef AL
@@ -869,12 +889,6 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
     const bool diffusion = ctx->cfg.gravity == PM_GRAVITY_DIFFUSION;
     const double nbar = (double)ctx->N0 / ((double)n * n * n);
     const double invM = 1.0 / (281474976710656.0 * nbar);
-    int b0 = 0, b1 = n - 1;
-    if (!per) {
-      double c = 0.5 * n;
-      b0 = std::max(lo, (int)std::ceil(c - R0 - 0.5));
-      b1 = std::min(lo + s - 1, (int)std::floor(c + R0 - 0.5));
-    }
     Grid fh = full_view(ctx, ctx->f_hi, lo, s), fl = full_view(ctx, ctx->f_lo, lo, s);
     // boundary values of the current source (moments in d_scal) with factor S
     auto ghosts = [&](double Sb) {
@@ -892,7 +906,7 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
       launch_drift_deposit(ctx->st, std::max(1, std::min(gkd_blocks(N) * 4, 152 * 16)),
                            ctx->pos, ctx->mom, N, 0.0f, false, n, lo, s, per, ctx->rho,
                            ctx->d_cnt + 1);
-      launch_source(ctx->st, SRC_GRID, ctx->rho, n, lo, s, fh, fl, invM, S0, b0, b1, !per,
+      launch_source(ctx->st, SRC_GRID, ctx->rho, n, lo, s, fh, fl, invM, S0, ctx->bgw, !per,
                     ctx->partial, ctx->partial_m, ctx->counter, ctx->d_scal, ctx->bgm,
                     ctx->d_overflow);
       ghosts(S0);
@@ -917,7 +931,7 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
     // 3. source, boundary values, solve
     const double S = 1.5 * ctx->cfg.omega_m / ctx->a_half[k];
     e = prof_begin(ctx);
-    launch_source(ctx->st, SRC_GRID, ctx->rho, n, lo, s, fh, fl, invM, S, b0, b1, !per,
+    launch_source(ctx->st, SRC_GRID, ctx->rho, n, lo, s, fh, fl, invM, S, ctx->bgw, !per,
                   ctx->partial, ctx->partial_m, ctx->counter, ctx->d_scal, ctx->bgm,
                   ctx->d_overflow);
     // read the counts, clear them, write f hi + lo: 24 B/cell
@@ -1793,12 +1807,6 @@ pm_status pm_batch_step(pm_batch* B, int32_t n_steps) {
         const double S = 1.5 * c->cfg.omega_m / c->a_half[k];
         const double nbar = (double)c->N0 / ((double)n * n * n);
         const double invM = 1.0 / (281474976710656.0 * nbar);
-        int b0 = 0, b1 = n - 1;
-        if (!c->periodic) {
-          double cc = 0.5 * n;
-          b0 = std::max(lo, (int)std::ceil(cc - c->R[k] - 0.5));
-          b1 = std::min(lo + s - 1, (int)std::floor(cc + c->R[k] - 0.5));
-        }
         SourceDesc e{};
         e.rho = c->rho;
         e.n = n;
@@ -1810,8 +1818,7 @@ pm_status pm_batch_step(pm_batch* B, int32_t n_steps) {
         e.invM.lo = (float)(invM - (double)e.invM.hi);
         e.S.hi = (float)S;
         e.S.lo = (float)(S - (double)e.S.hi);
-        e.b0 = b0;
-        e.b1 = b1;
+        e.bgw = c->bgw;
         e.moments = !c->periodic;
         e.partial_f2 = c->partial;
         e.partial_m = c->partial_m;

@@ -173,7 +173,7 @@ constexpr int SRC_NV = 10;
 template <bool MOMENTS>
 __device__ __forceinline__ void d_source(const BI& bi, 
     unsigned long long* __restrict__ rho, int n, int lo, int s, Grid fh, Grid fl,
-    df invM, df S, int b0, int b1, double* __restrict__ partial_f2,
+    df invM, df S, const df* __restrict__ bgw, double* __restrict__ partial_f2,
     __int128* __restrict__ partial_m, unsigned int* counter, double* __restrict__ out,
     const double* __restrict__ bgm, double invM2_hi, int* __restrict__ overflow){
   __int128 acc[SRC_NV];
@@ -187,7 +187,10 @@ __device__ __forceinline__ void d_source(const BI& bi,
   const int j = bi.y * blockDim.y + threadIdx.y;
   const bool in_xy = i < s && j < s;
   const int gi = lo + i, gj = lo + j;
-  const bool in_xy_bg = gi >= b0 && gi <= b1 && gj >= b0 && gj <= b1;
+  // mean-density weight W = w_x w_y w_z (per-axis CIC image of the keep
+  // interval, indexed by global cell; all ones in the periodic phase)
+  df wxy{0.0f, 0.0f};
+  if (in_xy) wxy = df_mul(bgw[gi], bgw[gj]);
   for (int k0 = bi.z; k0 < s && in_xy; k0 += ZU * bi.gz) {
     unsigned long long cnts[ZU];
 #pragma unroll
@@ -205,7 +208,8 @@ __device__ __forceinline__ void d_source(const BI& bi,
     if (cnt > (1ull << 62)) atomicOr(overflow, 1);
     long long c = (long long)cnt;
     df d = df_mul(df_from_u64(cnt), invM);
-    if (in_xy_bg && gk >= b0 && gk <= b1) d = df_add(d, df{-1.0f, 0.0f});
+    const df w = df_mul(wxy, bgw[gk]);
+    d = df_add(d, df{-w.hi, -w.lo});
     df f = df_mul(d, S);
     int fi = gidx(fh, i, j, k);
     fh.base[fi] = f.hi;
@@ -317,10 +321,11 @@ __device__ __forceinline__ void d_source(const BI& bi,
 template <bool MOMENTS>
 __global__ void __launch_bounds__(256) k_source(
     unsigned long long* __restrict__ rho, int n, int lo, int s, Grid fh, Grid fl,
-    df invM, df S, int b0, int b1, double* __restrict__ partial_f2,
+    df invM, df S, const df* __restrict__ bgw, double* __restrict__ partial_f2,
     __int128* __restrict__ partial_m, unsigned int* counter, double* __restrict__ out,
     const double* __restrict__ bgm, double invM2_hi, int* __restrict__ overflow) {
-  d_source<MOMENTS>(bi_native(), rho, n, lo, s, fh, fl, invM, S, b0, b1, partial_f2, partial_m, counter, out, bgm, invM2_hi, overflow);
+  d_source<MOMENTS>(bi_native(), rho, n, lo, s, fh, fl, invM, S, bgw, partial_f2, partial_m,
+                    counter, out, bgm, invM2_hi, overflow);
 }
 
 dim3 source_grid(int s) {
@@ -328,7 +333,7 @@ dim3 source_grid(int s) {
 }
 
 void launch_source(cudaStream_t st, int grid, unsigned long long* rho, int n, int lo,
-                   int s, Grid fh, Grid fl, double invM, double S, int b0, int b1,
+                   int s, Grid fh, Grid fl, double invM, double S, const df* bgw,
                    bool moments, double* partial_f2, void* partial_m,
                    unsigned int* counter, double* out, const double* bgm, int* overflow) {
   df invMd, Sd;
@@ -337,11 +342,11 @@ void launch_source(cudaStream_t st, int grid, unsigned long long* rho, int n, in
   Sd.hi = (float)S;
   Sd.lo = (float)(S - (double)Sd.hi);
   if (moments)
-    k_source<true><<<source_grid(s), dim3(32, 8), 0, st>>>(rho, n, lo, s, fh, fl, invMd, Sd, b0, b1,
+    k_source<true><<<source_grid(s), dim3(32, 8), 0, st>>>(rho, n, lo, s, fh, fl, invMd, Sd, bgw,
                                          partial_f2, (__int128*)partial_m, counter, out,
                                          bgm, invM, overflow);
   else
-    k_source<false><<<source_grid(s), dim3(32, 8), 0, st>>>(rho, n, lo, s, fh, fl, invMd, Sd, b0, b1,
+    k_source<false><<<source_grid(s), dim3(32, 8), 0, st>>>(rho, n, lo, s, fh, fl, invMd, Sd, bgw,
                                           partial_f2, (__int128*)partial_m, counter, out,
                                           bgm, invM, overflow);
   note_launch();
@@ -540,10 +545,10 @@ __global__ void __launch_bounds__(256) kb_source(const SourceDesc* d, const BTab
   if (!batch_map(d, t, (const int*)nullptr, q, bi)) return;
   const SourceDesc& e = d[q];
   if (e.moments)
-    d_source<true>(bi, e.rho, e.n, e.lo, e.s, e.fh, e.fl, e.invM, e.S, e.b0, e.b1, e.partial_f2,
+    d_source<true>(bi, e.rho, e.n, e.lo, e.s, e.fh, e.fl, e.invM, e.S, e.bgw, e.partial_f2,
                    (__int128*)e.partial_m, e.counter, e.out, e.bgm, e.invM_d, e.overflow);
   else
-    d_source<false>(bi, e.rho, e.n, e.lo, e.s, e.fh, e.fl, e.invM, e.S, e.b0, e.b1,
+    d_source<false>(bi, e.rho, e.n, e.lo, e.s, e.fh, e.fl, e.invM, e.S, e.bgw,
                     e.partial_f2, (__int128*)e.partial_m, e.counter, e.out, e.bgm, e.invM_d,
                     e.overflow);
 }

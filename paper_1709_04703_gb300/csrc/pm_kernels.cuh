@@ -19,7 +19,7 @@ void launch_drift_deposit(cudaStream_t st, int grid, float4* pos, const float4* 
                           int periodic, unsigned long long* rho,
                           unsigned long long* escaped);
 void launch_source(cudaStream_t st, int grid, unsigned long long* rho, int n, int lo,
-                   int s, Grid fh, Grid fl, double invM, double S, int b0, int b1,
+                   int s, Grid fh, Grid fl, double invM, double S, const df* bgw,
                    bool moments, double* partial_f2, void* partial_m,
                    unsigned int* counter, double* out, const double* bgm, int* overflow);
 void launch_source_f64(cudaStream_t st, int grid, const double* delta, int n, Grid fh,
@@ -150,7 +150,8 @@ struct SourceDesc {
   int n, lo, s;
   Grid fh, fl;
   df invM, S;
-  int b0, b1, moments;
+  const df* bgw;
+  int moments;
   double* partial_f2;
   void* partial_m;
   unsigned int* counter;
