@@ -361,16 +361,17 @@ def shrink(arrays, keep):
 # the whole step and the whole run
 # --------------------------------------------------------------------------
 
-def step(pos, mom, k, sched, n, om, nbar, want=False, drift32=False):
+def step(pos, mom, k, sched, n, om, nbar, want=False, drift32=False, fixed_box=False):
     """Advance FP64 state (pos, mom) by step k.  Returns (pos, mom, info).
 
     drift32=True takes the first half drift in the CUDA kernel's documented
     float32 arithmetic (drift_fp32) so that both sides deposit the same float
-    positions; everything after it stays FP64."""
+    positions; everything after it stays FP64.  fixed_box=True solves on the
+    whole periodic box at every step (the run without shrinking)."""
     a0, a1 = sched["a"][k], sched["a"][k + 1]
     dtau, ah = sched["dtau"][k], sched["a_half"][k]
     R0 = sched["R"][k]
-    lo, s, periodic = active_cube(R0, n)
+    lo, s, periodic = (0, n, True) if fixed_box else active_cube(R0, n)
     if drift32:
         pos = drift_fp32(np.asarray(pos, np.float32), np.asarray(mom, np.float32),
                          dtau / (2 * a0), n, periodic).astype(np.float64)
@@ -388,24 +389,37 @@ def step(pos, mom, k, sched, n, om, nbar, want=False, drift32=False):
     return pos, mom, info
 
 
-def run(pos, mom, ids, sched, n, om, nbar, steps=None):
-    """Whole run with shrinking.  Returns survivors, lightcone, per-step n_active."""
+def run(pos, mom, ids, sched, n, om, nbar, steps=None, record_only=False):
+    """Whole run with shrinking.  Returns survivors, lightcone, per-step n_active.
+
+    record_only=True is the run without shrinking that the paper compares
+    with (Sec. 3.3): every particle stays active on the whole periodic box,
+    and a particle enters the lightcone catalogue, with the step's a_{n+1},
+    at the end of the first step after which it lies outside the keep cube
+    (same rule and index order as the shrink).  `recorded` then marks the
+    catalogued particles."""
     pos = np.asarray(pos, dtype=np.float64).copy()
     mom = np.asarray(mom, dtype=np.float64).copy()
     ids = np.asarray(ids).copy()
     lc = [np.zeros((0, 3)), np.zeros((0, 3)), np.zeros(0, dtype=ids.dtype),
           np.zeros(0)]
+    recorded = np.zeros(len(pos), dtype=bool)
     n_active = []
     nsteps = len(sched["dtau"]) if steps is None else steps
     for k in range(nsteps):
         n_active.append(len(pos))
-        pos, mom, _ = step(pos, mom, k, sched, n, om, nbar)
+        pos, mom, _ = step(pos, mom, k, sched, n, om, nbar, fixed_box=record_only)
         R1 = sched["R"][k + 1]
         if is_open(R1, n):
             keep = keep_mask(pos, R1, n)
-            (pos, mom, ids), (lp, lm, li) = shrink([pos, mom, ids], keep)
+            if record_only:
+                new = ~keep & ~recorded
+                lp, lm, li = pos[new], mom[new], ids[new]
+                recorded |= new
+            else:
+                (pos, mom, ids), (lp, lm, li) = shrink([pos, mom, ids], keep)
             lc = [np.concatenate([lc[0], lp]), np.concatenate([lc[1], lm]),
                   np.concatenate([lc[2], li]),
                   np.concatenate([lc[3], np.full(len(li), sched["a"][k + 1])])]
     return dict(pos=pos, mom=mom, ids=ids, lc_pos=lc[0], lc_mom=lc[1],
-                lc_ids=lc[2], lc_a=lc[3], n_active=np.array(n_active))
+                lc_ids=lc[2], lc_a=lc[3], n_active=np.array(n_active), recorded=recorded)

@@ -391,6 +391,45 @@ def test_shrinking_run_bookkeeping():
     assert np.all(np.abs(out["pos"] - n / 2).max(axis=1) <= R)
 
 
+def test_fixed_box_record_bookkeeping():
+    """Without shrinking every particle stays active; each one is catalogued
+    at most once, at the end of a step after which it lies outside the keep
+    cube, and in index order within a step."""
+    n = 16
+    pos, mom, ids = ics.zeldovich(n, -2.0, None, 2, 0.5)
+    sched = cz.schedule(n, 4000.0, OM, OL, 0.5, 1.0, 6)
+    out = pm.run(pos, mom, ids, sched, n, OM, 1.0, record_only=True)
+    assert len(out["ids"]) == n**3 and np.all(out["n_active"] == n**3)
+    assert len(np.unique(out["lc_ids"])) == len(out["lc_ids"]) == out["recorded"].sum()
+    assert set(out["lc_ids"]) == set(out["ids"][out["recorded"]])
+    for a in np.unique(out["lc_a"]):
+        k1 = int(np.argmin(np.abs(sched["a"] - a)))
+        sel = out["lc_a"] == a
+        assert np.all(np.abs(out["lc_pos"][sel] - n / 2).max(axis=1) > sched["R"][k1])
+        assert np.all(np.diff(out["lc_ids"][sel]) > 0)     # ids are the index order here
+    # a particle never catalogued is inside the final keep cube, or was
+    # inside at every check (R shrinks, so it is inside now)
+    rest = ~out["recorded"]
+    assert np.all(np.abs(out["pos"][rest] - n / 2).max(axis=1) <= sched["R"][-1])
+
+
+def test_fixed_box_record_equals_shrink_without_forces():
+    """With gravity switched off (Omega_m -> 0: no source) trajectories do
+    not depend on the boundary, so the catalogue of the fixed-box record
+    is the shrinking run's lightcone: same particles, order, a, positions."""
+    n, om = 16, 1e-12
+    pos, mom, ids = ics.zeldovich(n, -2.0, None, 3, 0.5, om=om, ol=1 - om)
+    mom = mom + np.float32(0.02) * np.sign(pos - n / 2).astype(np.float32)   # outward streaming
+    sched = cz.schedule(n, 4000.0, om, 1 - om, 0.5, 1.0, 8)
+    shr = pm.run(pos, mom, ids, sched, n, om, 1.0)
+    rec = pm.run(pos, mom, ids, sched, n, om, 1.0, record_only=True)
+    assert len(shr["lc_ids"]) > n**3 // 4
+    np.testing.assert_array_equal(rec["lc_ids"], shr["lc_ids"])
+    np.testing.assert_array_equal(rec["lc_a"], shr["lc_a"])
+    np.testing.assert_allclose(rec["lc_pos"], shr["lc_pos"], rtol=0, atol=1e-9)
+    np.testing.assert_allclose(rec["lc_mom"], shr["lc_mom"], rtol=0, atol=1e-12)
+
+
 def test_drift_fp32_exact_cases_and_wrap():
     """drift_fp32 follows float32 arithmetic: exact where float32 is exact,
     and the periodic wrap lands in [0, n)."""
