@@ -318,12 +318,14 @@ TABLE4 = {512.0: 1.08, 2048.0: 1.44, 8192.0: 3.02}   # Table 4, 512^3 particles
 
 def _timed_run(pos, mom, ids, n, box, a0, steps, rtol, gravity, shrink):
     """One whole run, each step device-timed on the context stream; per-step
-    active particles and milliseconds."""
+    active particles and milliseconds, and the run's catalogue (lightcone
+    records plus the particles never recorded) for P(k).  shrink=False is
+    the fixed periodic box with the lightcone recorded (PM_SHRINK_RECORD)."""
     import torch
     from paper_1709_04703_gb300.sim import Sim
     sim = Sim(pos, mom, ids, n, box, a0, 1.0, steps, rtol=rtol, precision="mixed",
               max_vcycles=100, gravity=gravity, bc="paper" if shrink else "periodic",
-              shrink=shrink)
+              shrink=True if shrink else "record")
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     n_act = []
     torch.cuda.synchronize()
@@ -335,14 +337,28 @@ def _timed_run(pos, mom, ids, n, box, a0, steps, rtol, gravity, shrink):
     torch.cuda.synchronize()
     ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
     st = sim.stats()
+    ap, _, ai = sim.particles()
+    lp, _, li, _ = sim.lightcone()
     sim.close()
+    rest = ap if shrink else ap[~np.isin(ai, li)]
     return {"ms": sum(ms), "ms_step": ms, "n_active": n_act,
-            "vcycles_total": int(st["vcycles_total"])}
+            "vcycles_total": int(st["vcycles_total"]),
+            "catalogue": np.concatenate([lp, rest]).astype(np.float32)}
+
+
+def _catalogue_pk(cat, box, n):
+    import torch
+    from paper_1709_04703_gb300.sim import pack, power_spectrum
+    p4, _ = pack(np.mod(cat, n).astype(np.float32), np.zeros_like(cat))
+    k, p, _ = power_spectrum(torch.from_numpy(p4).cuda(), box, n, n // 2)
+    return k, p
 
 
 def run_shrink_table(args):
     """--workload shrink_table: the whole-run time of the fixed periodic box
-    over that of the shrinking box (Table 4's speed-up, Sec. 3.3), with the
+    (lightcone recorded, every particle integrated) over that of the
+    shrinking box (Table 4's speed-up, Sec. 3.3), and the relative difference
+    of the two lightcone catalogues' P(k) (Fig. 4), with the
     paper's run shape: n^3 particles on an n^3 mesh, a from 1/41 (z = 40) to
     1 in 1000 steps uniform in a, boxes 512, 2048 and 8192 Mpc/h.  Both
     gravities: the diffusion equation (the paper's pair of codes) and the
@@ -364,6 +380,10 @@ def run_shrink_table(args):
             sh = _timed_run(pos, mom, ids, n, box, a0, steps, tol, grav, True)
             fx = _timed_run(pos, mom, ids, n, box, a0, steps, tol, grav, False)
             q = [steps // 4, steps // 2, (3 * steps) // 4]
+            # Fig. 4: P(k) of the two catalogues in the original box, k <= k_Ny/2
+            _, p_sh = _catalogue_pk(sh["catalogue"], box, n)
+            _, p_fx = _catalogue_pk(fx["catalogue"], box, n)
+            rel = np.abs(p_sh[: n // 4] / p_fx[: n // 4] - 1.0)
             rows.append({
                 "gravity": grav, "box_mpch": box, "shrink_s": round(sh["ms"] * 1e-3, 3),
                 "fixed_s": round(fx["ms"] * 1e-3, 3), "speedup": round(fx["ms"] / sh["ms"], 3),
@@ -371,7 +391,10 @@ def run_shrink_table(args):
                 # Figs. 5 and 6 at a quarter, half and three quarters of the run
                 "n_active_frac": [round(sh["n_active"][k] / n**3, 4) for k in q],
                 "ms_step_ratio": [round(sh["ms_step"][k] / fx["ms_step"][k], 4) for k in q],
-                "vcycles": [sh["vcycles_total"], fx["vcycles_total"]]})
+                "vcycles": [sh["vcycles_total"], fx["vcycles_total"]],
+                "lightcone_pk_rel_diff": {"max": float(rel.max()),
+                                          "rms": float(np.sqrt(np.mean(rel**2))),
+                                          "k_range": "k_f .. k_Ny/2"}})
             print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
     line = {"metric": "whole-run speed-up, shrinking vs fixed periodic box", "unit": "x",
             "higher_is_better": True, "n_gpus": 1, "steps": steps,

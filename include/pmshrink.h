@@ -52,12 +52,14 @@ enum { PM_MIXED = 0, PM_FP32_PLAIN = 1 };               /* pm_config.precision *
 enum { PM_GUESS_WARM = 0, PM_GUESS_ZERO = 1, PM_GUESS_LEARNED = 2 };  /* pm_config.guess */
 enum { PM_GRAVITY_POISSON = 0, PM_GRAVITY_DIFFUSION = 1 };           /* pm_config.gravity */
 enum { PM_BC_PAPER = 0, PM_BC_OPEN = 1, PM_BC_PERIODIC = 2 };  /* pm_config.bc */
+enum { PM_SHRINK_OFF = 0, PM_SHRINK_ON = 1, PM_SHRINK_RECORD = 2 };  /* pm_config.shrink */
 
 typedef struct {
   int32_t n_mesh;        /* cells per side, of the form 2^j or 3*2^j, 4..1024 */
   int64_t n_particles;   /* particle count N at the start of the run */
   double box_mpch;       /* comoving side of the initial box, Mpc/h */
-  double omega_m;        /* flat background: omega_m + omega_l = 1 expected */
+  double omega_m;        /* flat background: omega_m + omega_l = 1 expected;
+                            omega_m >= 1e-6 (PM_EINVAL below) */
   double omega_l;
   double a_init;         /* first expansion factor */
   double a_final;        /* last expansion factor */
@@ -72,8 +74,19 @@ typedef struct {
   int32_t bc;            /* PM_BC_PAPER: periodic until the lightcone reaches
                             the box edge, open afterwards; PM_BC_OPEN /
                             PM_BC_PERIODIC force one kind for the whole run */
-  int32_t shrink;        /* 1: drop particles that leave the keep cube (into
-                            the lightcone buffer); 0: keep everything */
+  int32_t shrink;        /* PM_SHRINK_ON: drop particles that leave the keep
+                            cube (into the lightcone buffer; needs open
+                            boundaries, i.e. bc != PM_BC_PERIODIC);
+                            PM_SHRINK_OFF: keep everything, record nothing;
+                            PM_SHRINK_RECORD: keep and integrate every
+                            particle (the fixed-box run the paper compares
+                            against, Sec. 3.3) and copy each one, with
+                            a_cross, into the lightcone buffer at the end of
+                            the first step after which it lies outside the
+                            keep cube, with the rule and order of the shrink.
+                            In this mode an active particle's mom.w is its
+                            record mark (0: not yet recorded; pm_init
+                            clears it) */
   double buffer_cells;   /* keep half-width R = chi(a)/cell + buffer_cells */
   int32_t store_forces;  /* 1: keep grad(Phi) at each particle of the last step */
   int32_t gravity;       /* PM_GRAVITY_POISSON: static Eq. 3 every step;

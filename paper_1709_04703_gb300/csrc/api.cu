@@ -671,6 +671,33 @@ pm_status shrink_to(pm_ctx* ctx, double R, double a_cross, bool flags_ready) {
   return PM_OK;
 }
 
+// Fixed-box lightcone record: copy the active particles that lie outside the
+// keep cube of radius R and carry no record mark into the lightcone buffer
+// (index order), marking them; nobody leaves the active set.
+pm_status record_to(pm_ctx* ctx, double R, double a_cross) {
+  float klo, khi;
+  keep_bounds(0.5 * ctx->n, R, &klo, &khi);
+  const long long N = ctx->n_active;
+  if (N == 0) return PM_OK;
+  const int nblk = gkd_blocks(N);
+  int e = prof_begin(ctx);
+  launch_flag_record(ctx->st, ctx->pos, ctx->mom, N, klo, khi, ctx->flags, ctx->block_keep);
+  launch_scan_blocks(ctx->st, ctx->block_keep, ctx->keep_off, nblk, ctx->d_cnt);
+  launch_record(ctx->st, ctx->pos, ctx->mom, N, ctx->flags, ctx->keep_off, ctx->lc_pos,
+                ctx->lc_mom, ctx->n_lc, ctx->N0, (float)a_cross);
+  // read both records and the flag (33 B), write the recorded ones
+  prof_end(ctx, PM_PROF_COMPACT, e, 33.0 * N);
+  CKL();
+  pm_status st = sync_read(ctx);
+  if (st != PM_OK) return st;
+  const long long rec = (long long)ctx->h_cnt[0];
+  if (ctx->n_lc + rec > ctx->N0)
+    return fail(ctx, PM_EOVERFLOW, "lightcone record: more records than particles (a set "
+                                   "of particles without cleared record marks?)");
+  ctx->n_lc += rec;
+  return PM_OK;
+}
+
 pm_status alloc(pm_ctx* ctx, void** p, size_t bytes) {
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
@@ -732,8 +759,11 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
     return fail(nullptr, PM_EINVAL, "pm_init: n_mesh must be 2^j or 3*2^j in [4, 1024]");
   if (cfg->n_particles <= 0 || cfg->n_particles >= (1LL << 31))
     return fail(nullptr, PM_EINVAL, "pm_init: n_particles must be in [1, 2^31)");
+  // omega_m >= 1e-6: the conformal-time quadrature (64 Gauss panels in
+  // u = sqrt(a)) resolves the peak of width (omega_m / omega_l)^(1/6) at u = 0
   if (cfg->n_steps <= 0 || !(cfg->a_init > 0) || !(cfg->a_final > cfg->a_init) ||
-      !(cfg->box_mpch > 0) || !(cfg->omega_m > 0) || cfg->omega_l < 0 || !(cfg->rtol > 0) ||
+      !(cfg->box_mpch > 0) || !(cfg->omega_m >= 1e-6) || cfg->omega_l < 0 ||
+      !(cfg->rtol > 0) ||
       cfg->max_vcycles < 1)
     return fail(nullptr, PM_EINVAL, "pm_init: invalid schedule, cosmology or tolerance");
   if (cfg->precision != PM_MIXED && cfg->precision != PM_FP32_PLAIN)
@@ -742,6 +772,8 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
     return fail(nullptr, PM_EINVAL, "pm_init: unknown bc");
   if (cfg->guess < PM_GUESS_WARM || cfg->guess > PM_GUESS_LEARNED)
     return fail(nullptr, PM_EINVAL, "pm_init: unknown guess");
+  if (cfg->shrink < PM_SHRINK_OFF || cfg->shrink > PM_SHRINK_RECORD)
+    return fail(nullptr, PM_EINVAL, "pm_init: unknown shrink mode");
   if (cfg->gravity != PM_GRAVITY_POISSON &&
       (cfg->gravity != PM_GRAVITY_DIFFUSION || !(cfg->c_eff_factor > 0) ||
        cfg->precision != PM_MIXED || cfg->guess == PM_GUESS_LEARNED))
@@ -858,6 +890,9 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
   cudaMemcpyKind kind = host_mem ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   if (cudaMemcpyAsync(ctx->pos, pos4, sizeof(float4) * N, kind, s0) != cudaSuccess ||
       cudaMemcpyAsync(ctx->mom, mom4, sizeof(float4) * N, kind, s0) != cudaSuccess ||
+      (cfg->shrink == PM_SHRINK_RECORD &&
+       cudaMemset2DAsync((char*)ctx->mom + 3 * sizeof(float), sizeof(float4), 0, sizeof(float),
+                         (size_t)N, s0) != cudaSuccess) ||
       cudaStreamSynchronize(s0) != cudaSuccess) {
     g_err = "pm_init: copying particles failed";
     pm_destroy(ctx);
@@ -994,7 +1029,8 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
     ctx->ah_hist[1] = ctx->a_half[k];
     ctx->n_sol++;
     // 4-6. gradient + gather + kick + half drift (+ keep flags)
-    const bool do_flag = ctx->cfg.shrink && ctx->cfg.bc != PM_BC_PERIODIC && is_open(ctx, R1);
+    const bool do_flag =
+        ctx->cfg.shrink == PM_SHRINK_ON && ctx->cfg.bc != PM_BC_PERIODIC && is_open(ctx, R1);
     float klo = 0.f, khi = 0.f;
     if (do_flag) keep_bounds(0.5 * n, R1, &klo, &khi);
     e = prof_begin(ctx);
@@ -1030,9 +1066,13 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
       ctx->sig_d = 0.0;
       if (st != PM_OK) return st;
     }
-    // 7. lightcone shrink
+    // 7. lightcone shrink (or, in the fixed box, the lightcone record)
     if (do_flag) {
       st = shrink_to(ctx, R1, ctx->a[k + 1], true);
+      if (st != PM_OK) return st;
+    } else if (ctx->cfg.shrink == PM_SHRINK_RECORD && R1 <= 0.5 * n - 1.0) {
+      // the keep cube lies inside the box (whatever the solve's boundary)
+      st = record_to(ctx, R1, ctx->a[k + 1]);
       if (st != PM_OK) return st;
     }
     int ovf = 0;
@@ -1692,6 +1732,9 @@ pm_status pm_batch_init(int32_t n_real, const pm_config* cfgs, const float* cons
       return bfail(nullptr, PM_EINVAL, "pm_batch_init: the learned guess runs per context");
     if (cfgs[r].gravity != PM_GRAVITY_POISSON)
       return bfail(nullptr, PM_EINVAL, "pm_batch_init: batches solve Poisson's equation");
+    if (cfgs[r].shrink == PM_SHRINK_RECORD)
+      return bfail(nullptr, PM_EINVAL, "pm_batch_init: the fixed-box lightcone record runs "
+                                       "per context");
     if (cfgs[r].n_steps != cfgs[0].n_steps || cfgs[r].a_init != cfgs[0].a_init ||
         cfgs[r].a_final != cfgs[0].a_final)
       return bfail(nullptr, PM_EINVAL, "pm_batch_init: realisations must share the a schedule");
@@ -1963,7 +2006,8 @@ pm_status pm_batch_step(pm_batch* B, int32_t n_steps) {
         pm_ctx* c = B->ctx[r];
         if (c->n_active <= 0) continue;
         const double R1 = c->R[k + 1];
-        const bool do_flag = c->cfg.shrink && c->cfg.bc != PM_BC_PERIODIC && is_open(c, R1);
+        const bool do_flag =
+            c->cfg.shrink == PM_SHRINK_ON && c->cfg.bc != PM_BC_PERIODIC && is_open(c, R1);
         GatherDesc e{};
         e.pos = c->pos;
         e.mom = c->mom;

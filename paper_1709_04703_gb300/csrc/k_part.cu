@@ -448,6 +448,94 @@ void launch_scatter(cudaStream_t st, const float4* pos, const float4* mom, long 
 }
 
 // ---------------------------------------------------------------------------
+// Lightcone record without removal (fixed-box run): flag = outside the keep
+// cube and not yet recorded (mom.w == 0); the flagged records are copied in
+// index order to lc_base + off[b] + rank with mom.w = a_cross, and their
+// mom.w in place is set to a_cross.  Nothing is written at or beyond lc_cap
+// (the host compares the count with the capacity afterwards).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(KT) k_flag_record(const float4* __restrict__ pos,
+                                                    const float4* __restrict__ mom, long long N,
+                                                    float klo, float khi,
+                                                    unsigned char* __restrict__ flags,
+                                                    unsigned int* __restrict__ block_cnt) {
+  const long long base = (long long)blockIdx.x * KCHUNK;
+  unsigned int cnt = 0;
+  for (int it = 0; it < KITEMS; ++it) {
+    long long p = base + it * KT + threadIdx.x;
+    if (p >= N) break;
+    const float4 x = pos[p];
+    const bool inside = x.x >= klo && x.x <= khi && x.y >= klo && x.y <= khi &&
+                        x.z >= klo && x.z <= khi;
+    const bool rec = !inside && mom[p].w == 0.0f;
+    flags[p] = rec ? 1 : 0;
+    cnt += rec ? 1u : 0u;
+  }
+  __shared__ unsigned int sk[KT / 32];
+  unsigned int w = cnt;
+  for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+  if ((threadIdx.x & 31) == 0) sk[threadIdx.x >> 5] = w;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int t = 0;
+    for (int q = 0; q < KT / 32; ++q) t += sk[q];
+    block_cnt[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(KT) k_record(const float4* __restrict__ pos,
+                                               float4* __restrict__ mom, long long N,
+                                               const unsigned char* __restrict__ flags,
+                                               const unsigned long long* __restrict__ off,
+                                               float4* __restrict__ lc_pos,
+                                               float4* __restrict__ lc_mom, long long lc_base,
+                                               long long lc_cap, float a_cross) {
+  __shared__ unsigned int wk[KT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long base = (long long)blockIdx.x * KCHUNK;
+  unsigned long long run = off[blockIdx.x];
+  for (int it = 0; it < KITEMS; ++it) {
+    const long long p = base + it * KT + threadIdx.x;
+    const bool rec = p < N && flags[p];
+    const unsigned int bal = __ballot_sync(0xffffffffu, rec);
+    if (lane == 0) wk[warp] = __popc(bal);
+    __syncthreads();
+    unsigned int before = 0, row = 0;
+    for (int q = 0; q < KT / 32; ++q) {
+      const unsigned int c = wk[q];
+      if (q < warp) before += c;
+      row += c;
+    }
+    const long long d = lc_base + (long long)(run + before + __popc(bal & ((1u << lane) - 1u)));
+    if (rec && d < lc_cap) {
+      float4 v = mom[p];
+      v.w = a_cross;
+      lc_pos[d] = pos[p];
+      lc_mom[d] = v;
+      mom[p].w = a_cross;
+    }
+    run += row;
+    __syncthreads();
+  }
+}
+
+void launch_flag_record(cudaStream_t st, const float4* pos, const float4* mom, long long N,
+                        float klo, float khi, unsigned char* flags, unsigned int* block_cnt) {
+  if (N <= 0) return;
+  k_flag_record<<<gkd_blocks(N), KT, 0, st>>>(pos, mom, N, klo, khi, flags, block_cnt);
+  note_launch();
+}
+
+void launch_record(cudaStream_t st, const float4* pos, float4* mom, long long N,
+                   const unsigned char* flags, const unsigned long long* off, float4* lc_pos,
+                   float4* lc_mom, long long lc_base, long long lc_cap, float a_cross) {
+  if (N <= 0) return;
+  k_record<<<gkd_blocks(N), KT, 0, st>>>(pos, mom, N, flags, off, lc_pos, lc_mom, lc_base,
+                                         lc_cap, a_cross);
+  note_launch();
+}
+
+// ---------------------------------------------------------------------------
 // Batched forms.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(KT) kb_gather(const GatherDesc* d, const BTable* t) {

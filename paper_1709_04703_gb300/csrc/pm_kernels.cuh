@@ -82,6 +82,11 @@ void launch_scatter(cudaStream_t st, const float4* pos, const float4* mom, long 
                     const unsigned char* flags, const unsigned long long* keep_off,
                     float4* pos_out, float4* mom_out, float4* lc_pos, float4* lc_mom,
                     long long lc_base, float a_cross);
+void launch_flag_record(cudaStream_t st, const float4* pos, const float4* mom, long long N,
+                        float klo, float khi, unsigned char* flags, unsigned int* block_cnt);
+void launch_record(cudaStream_t st, const float4* pos, float4* mom, long long N,
+                   const unsigned char* flags, const unsigned long long* off, float4* lc_pos,
+                   float4* lc_mom, long long lc_base, long long lc_cap, float a_cross);
 
 // k_pk.cu
 void launch_pk_delta(cudaStream_t st, const unsigned long long* rho, float* delta, int n,

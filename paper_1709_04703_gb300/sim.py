@@ -11,6 +11,10 @@ _PREC = {"mixed": L.PM_MIXED, "fp32": L.PM_FP32_PLAIN}
 _GUESS = {"warm": L.PM_GUESS_WARM, "zero": L.PM_GUESS_ZERO, "learned": L.PM_GUESS_LEARNED}
 _BC = {"paper": L.PM_BC_PAPER, "open": L.PM_BC_OPEN, "periodic": L.PM_BC_PERIODIC}
 _GRAVITY = {"poisson": L.PM_GRAVITY_POISSON, "diffusion": L.PM_GRAVITY_DIFFUSION}
+# shrink: True / "on" drops leavers into the lightcone; False / "off" keeps
+# everything; "record" keeps everything and records lightcone crossings
+_SHRINK = {False: L.PM_SHRINK_OFF, True: L.PM_SHRINK_ON, "off": L.PM_SHRINK_OFF,
+           "on": L.PM_SHRINK_ON, "record": L.PM_SHRINK_RECORD}
 
 
 def _stream():
@@ -74,7 +78,7 @@ def _config(n_mesh, n_particles, box, a_init, a_final, n_steps, rtol=1e-7, preci
     cfg.precision = _PREC[precision]
     cfg.guess = _GUESS[guess]
     cfg.bc = _BC[bc]
-    cfg.shrink = 1 if shrink else 0
+    cfg.shrink = _SHRINK[shrink]
     cfg.buffer_cells = float(buffer_cells)
     cfg.store_forces = 1 if store_forces else 0
     return cfg
@@ -177,7 +181,7 @@ class Sim:
         cfg.precision = _PREC[precision]
         cfg.guess = _GUESS[guess]
         cfg.bc = _BC[bc]
-        cfg.shrink = 1 if shrink else 0
+        cfg.shrink = _SHRINK[shrink]
         cfg.buffer_cells = float(buffer_cells)
         cfg.store_forces = 1 if store_forces else 0
         cfg.gravity = _GRAVITY[gravity]
