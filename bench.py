@@ -347,10 +347,11 @@ def _timed_run(pos, mom, ids, n, box, a0, steps, rtol, gravity, shrink):
 
 
 def _catalogue_pk(cat, box, n):
+    """P(k) of a catalogue in the original box, alias-corrected (Jing 2005)."""
     import torch
-    from paper_1709_04703_gb300.sim import pack, power_spectrum
+    from paper_1709_04703_gb300.sim import pack, power_spectrum_jing
     p4, _ = pack(np.mod(cat, n).astype(np.float32), np.zeros_like(cat))
-    k, p, _ = power_spectrum(torch.from_numpy(p4).cuda(), box, n, n // 2)
+    k, p, _, _, _ = power_spectrum_jing(torch.from_numpy(p4).cuda(), box, n, n // 2)
     return k, p
 
 

@@ -168,6 +168,27 @@ pm_status pm_power_spectrum(const float* pos4_dev, int64_t n, double box,
                             double* k_out, double* pk_out, double* modes_out,
                             void* stream);
 
+/* The same spectrum with the full alias correction of Jing (2005), the
+ * discreteness correction Sec. 2.4 names.  The FFT at k (|k_d| <= k_N) holds
+ * every alias k + 2 k_N v (v an integer vector) weighted by the CIC window W:
+ *   P_obs(k) = sum_v W^2(k + 2k_N v) P(|k + 2k_N v|) + (L^3/n) C1(k),
+ *   C1 = prod_d [1 - (2/3) sin^2(k_d h/2)]  (closed form of sum_v W^2);
+ * with P a local power law of slope nu,
+ *   P(k) = (P_obs(k) - (L^3/n) C1(k)) / sum_v W^2(k + 2k_N v) (|k + 2k_N v|/|k|)^nu,
+ * the sum over v in [-alias_range, alias_range]^3 (1..3).  Each mode takes the
+ * slope of its bin; the slopes start from the first-order estimate and are
+ * re-measured from the corrected binned spectrum (centred difference of ln P
+ * in ln k over the neighbouring bins, clipped to [-6, 4]) until they move by
+ * less than tol, at most max_iter passes.  Bins as pm_power_spectrum;
+ * nu_out (host, n_bins, may be NULL) receives the slopes, *passes_out (may
+ * be NULL) the passes made.  Allocates its own scratch; synchronises stream
+ * once per pass.  subtract_shot = 0 drops the (L^3/n) C1 term. */
+pm_status pm_power_spectrum_jing(const float* pos4_dev, int64_t n, double box,
+                                 int32_t n_mesh, int32_t n_bins, int32_t subtract_shot,
+                                 int32_t alias_range, int32_t max_iter, double tol,
+                                 double* k_out, double* pk_out, double* modes_out,
+                                 double* nu_out, int32_t* passes_out, void* stream);
+
 /* Fixed-point CIC deposit of n particles into rho_dev (n_mesh^3 int64,
  * device, accumulated into: clear it first) over the cube [lo, lo+side)^3
  * (Sec. 2.4 footnote: CIC).  On the float position u per axis:

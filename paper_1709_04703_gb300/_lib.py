@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ECUDA",
 # every entry point declared in include/pmshrink.h
 EXPORTED = [
     "pm_config_default", "pm_init", "pm_step", "pm_shrink", "pm_potential",
-    "pm_power_spectrum", "pm_deposit", "pm_stats", "pm_schedule",
+    "pm_power_spectrum", "pm_power_spectrum_jing", "pm_deposit", "pm_stats", "pm_schedule",
     "pm_get_particles", "pm_set_particles", "pm_get_lightcone", "pm_get_forces",
     "pm_get_potential", "pm_profile", "pm_profile_read", "pm_launch_count", "pm_last_error",
     "pm_destroy", "pm_shrink_static", "pm_shrink_static_error",
@@ -88,6 +88,8 @@ def load():
         "pm_shrink": (I32, [P, D, C.POINTER(I64)]),
         "pm_potential": (I32, [P, P, D, I32, P, P, C.POINTER(I32), C.POINTER(D)]),
         "pm_power_spectrum": (I32, [P, I64, D, I32, I32, I32, P, P, P, P]),
+        "pm_power_spectrum_jing": (I32, [P, I64, D, I32, I32, I32, I32, I32, D, P, P, P, P, P,
+                                         P]),
         "pm_deposit": (I32, [P, P, I64, F, I32, I32, I32, I32, P, C.POINTER(I64), P]),
         "pm_stats": (I32, [P, C.POINTER(PmStats)]),
         "pm_schedule": (I32, [P, P, P, P, P]),

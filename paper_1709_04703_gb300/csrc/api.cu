@@ -1174,6 +1174,92 @@ pm_status pm_deposit(float* pos4_dev, const float* mom4_dev, int64_t n, float dr
   return PM_OK;
 }
 
+namespace {
+// Device work space of one P(k) call: CIC counts, contrast, its R2C
+// transform, bin accumulators (3 per bin + the escape counter) and slopes.
+struct PkWork {
+  unsigned long long* rho = nullptr;
+  float* delta = nullptr;
+  cufftComplex* dk = nullptr;
+  double* acc = nullptr;
+  double* nu = nullptr;
+  cufftHandle plan = 0;
+  bool have_plan = false;
+  ~PkWork() {
+    if (have_plan) cufftDestroy(plan);
+    cudaFree(rho);
+    cudaFree(delta);
+    cudaFree(dk);
+    cudaFree(acc);
+    cudaFree(nu);
+  }
+};
+
+// CIC deposit of the particles on the periodic n_mesh^3 mesh, contrast,
+// forward FFT into w.dk; w.acc cleared.
+pm_status pk_transform(PkWork& w, const char* who, const float* pos4_dev, int64_t n,
+                       int n_mesh, int n_bins, cudaStream_t st) {
+  const size_t cells = (size_t)n_mesh * n_mesh * n_mesh;
+  const size_t modes = (size_t)n_mesh * n_mesh * (n_mesh / 2 + 1);
+  if (cudaMalloc((void**)&w.rho, sizeof(unsigned long long) * cells) != cudaSuccess ||
+      cudaMalloc((void**)&w.delta, sizeof(float) * cells) != cudaSuccess ||
+      cudaMalloc((void**)&w.dk, sizeof(cufftComplex) * modes) != cudaSuccess ||
+      cudaMalloc((void**)&w.acc, sizeof(double) * (3 * n_bins + 1)) != cudaSuccess ||
+      cudaMalloc((void**)&w.nu, sizeof(double) * n_bins) != cudaSuccess)
+    return fail(nullptr, PM_ENOMEM, std::string(who) + ": cudaMalloc failed");
+  cudaMemsetAsync(w.rho, 0, sizeof(unsigned long long) * cells, st);
+  cudaMemsetAsync(w.acc, 0, sizeof(double) * (3 * n_bins + 1), st);
+  // positions are read-only here: no drift
+  launch_drift_deposit(st, std::max(1, std::min(gkd_blocks(n) * 4, 152 * 16)),
+                       (float4*)pos4_dev, nullptr, n, 0.f, false, n_mesh, 0, n_mesh, 1, w.rho,
+                       (unsigned long long*)(w.acc + 3 * n_bins));
+  const double mean = (double)n * 281474976710656.0 / (double)cells;
+  launch_pk_delta(st, w.rho, w.delta, n_mesh, 1.0 / mean);
+  if (cufftPlan3d(&w.plan, n_mesh, n_mesh, n_mesh, CUFFT_R2C) != CUFFT_SUCCESS)
+    return fail(nullptr, PM_ECUDA, std::string(who) + ": cufftPlan3d failed");
+  w.have_plan = true;
+  cufftSetStream(w.plan, st);
+  if (cufftExecR2C(w.plan, w.delta, w.dk) != CUFFT_SUCCESS)
+    return fail(nullptr, PM_ECUDA, std::string(who) + ": cufftExecR2C failed");
+  return PM_OK;
+}
+
+// Binned (k, P, modes) from the accumulators (synchronises st), then clears them.
+pm_status pk_read(PkWork& w, const char* who, int n_bins, cudaStream_t st, double* k_out,
+                  double* pk_out, double* modes_out) {
+  std::vector<double> h(3 * n_bins);
+  if (cudaMemcpyAsync(h.data(), w.acc, sizeof(double) * 3 * n_bins, cudaMemcpyDeviceToHost,
+                      st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(nullptr, PM_ECUDA,
+                std::string(who) + ": " + cudaGetErrorString(cudaGetLastError()));
+  for (int b = 0; b < n_bins; ++b) {
+    double c = h[3 * b];
+    modes_out[b] = c;
+    k_out[b] = c > 0 ? h[3 * b + 1] / c : NAN;
+    pk_out[b] = c > 0 ? h[3 * b + 2] / c : NAN;
+  }
+  cudaMemsetAsync(w.acc, 0, sizeof(double) * 3 * n_bins, st);
+  return PM_OK;
+}
+
+// Local slope d ln P / d ln k per bin: centred over bins b-1, b+1 (one-sided
+// at the ends), the previous value kept where a P involved is not positive,
+// clipped to [-6, 4].
+void pk_slopes(const std::vector<double>& k, const std::vector<double>& p,
+               std::vector<double>& nu) {
+  const int nb = (int)p.size();
+  std::vector<double> out = nu;
+  for (int b = 0; b < nb; ++b) {
+    const int lo = std::max(b - 1, 0), hi = std::min(b + 1, nb - 1);
+    if (hi == lo) continue;
+    if (p[lo] > 0 && p[hi] > 0 && k[lo] > 0 && k[hi] > 0)
+      out[b] = std::log(p[hi] / p[lo]) / std::log(k[hi] / k[lo]);
+  }
+  for (int b = 0; b < nb; ++b) nu[b] = std::min(4.0, std::max(-6.0, out[b]));
+}
+}  // namespace
+
 pm_status pm_power_spectrum(const float* pos4_dev, int64_t n, double box, int32_t n_mesh,
                             int32_t n_bins, int32_t subtract_shot, double* k_out,
                             double* pk_out, double* modes_out, void* stream) {
@@ -1181,64 +1267,59 @@ pm_status pm_power_spectrum(const float* pos4_dev, int64_t n, double box, int32_
       !k_out || !pk_out || !modes_out)
     return fail(nullptr, PM_EINVAL, "pm_power_spectrum: bad argument");
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t cells = (size_t)n_mesh * n_mesh * n_mesh;
-  const size_t modes = (size_t)n_mesh * n_mesh * (n_mesh / 2 + 1);
-  unsigned long long* rho = nullptr;
-  float* delta = nullptr;
-  cufftComplex* dk = nullptr;
-  double* acc = nullptr;
-  pm_status ret = PM_OK;
-  cufftHandle plan = 0;
-  bool have_plan = false;
-  do {
-    if (cudaMalloc((void**)&rho, sizeof(unsigned long long) * cells) != cudaSuccess ||
-        cudaMalloc((void**)&delta, sizeof(float) * cells) != cudaSuccess ||
-        cudaMalloc((void**)&dk, sizeof(cufftComplex) * modes) != cudaSuccess ||
-        cudaMalloc((void**)&acc, sizeof(double) * (3 * n_bins + 1)) != cudaSuccess) {
-      ret = fail(nullptr, PM_ENOMEM, "pm_power_spectrum: cudaMalloc failed");
-      break;
-    }
-    cudaMemsetAsync(rho, 0, sizeof(unsigned long long) * cells, st);
-    cudaMemsetAsync(acc, 0, sizeof(double) * (3 * n_bins + 1), st);
-    // positions are read-only here: no drift
-    launch_drift_deposit(st, std::max(1, std::min(gkd_blocks(n) * 4, 152 * 16)),
-                         (float4*)pos4_dev, nullptr, n, 0.f, false, n_mesh, 0, n_mesh, 1, rho,
-                         (unsigned long long*)(acc + 3 * n_bins));
-    const double mean = (double)n * 281474976710656.0 / (double)cells;
-    launch_pk_delta(st, rho, delta, n_mesh, 1.0 / mean);
-    if (cufftPlan3d(&plan, n_mesh, n_mesh, n_mesh, CUFFT_R2C) != CUFFT_SUCCESS) {
-      ret = fail(nullptr, PM_ECUDA, "pm_power_spectrum: cufftPlan3d failed");
-      break;
-    }
-    have_plan = true;
-    cufftSetStream(plan, st);
-    if (cufftExecR2C(plan, delta, dk) != CUFFT_SUCCESS) {
-      ret = fail(nullptr, PM_ECUDA, "pm_power_spectrum: cufftExecR2C failed");
-      break;
-    }
-    const double shot = subtract_shot ? box * box * box / (double)n : 0.0;
-    launch_pk_bin(st, (const float2*)dk, n_mesh, box, shot, n_bins, acc);
-    std::vector<double> h(3 * n_bins);
-    if (cudaMemcpyAsync(h.data(), acc, sizeof(double) * 3 * n_bins, cudaMemcpyDeviceToHost,
-                        st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess) {
-      ret = fail(nullptr, PM_ECUDA, std::string("pm_power_spectrum: ") +
-                                        cudaGetErrorString(cudaGetLastError()));
-      break;
-    }
-    for (int b = 0; b < n_bins; ++b) {
-      double c = h[3 * b];
-      modes_out[b] = c;
-      k_out[b] = c > 0 ? h[3 * b + 1] / c : NAN;
-      pk_out[b] = c > 0 ? h[3 * b + 2] / c : NAN;
-    }
-  } while (0);
-  if (have_plan) cufftDestroy(plan);
-  cudaFree(rho);
-  cudaFree(delta);
-  cudaFree(dk);
-  cudaFree(acc);
-  return ret;
+  PkWork w;
+  pm_status ret = pk_transform(w, "pm_power_spectrum", pos4_dev, n, n_mesh, n_bins, st);
+  if (ret != PM_OK) return ret;
+  const double shot = subtract_shot ? box * box * box / (double)n : 0.0;
+  launch_pk_bin(st, (const float2*)w.dk, n_mesh, box, shot, n_bins, w.acc);
+  return pk_read(w, "pm_power_spectrum", n_bins, st, k_out, pk_out, modes_out);
+}
+
+pm_status pm_power_spectrum_jing(const float* pos4_dev, int64_t n, double box, int32_t n_mesh,
+                                 int32_t n_bins, int32_t subtract_shot, int32_t alias_range,
+                                 int32_t max_iter, double tol, double* k_out, double* pk_out,
+                                 double* modes_out, double* nu_out, int32_t* passes_out,
+                                 void* stream) {
+  if (!pos4_dev || n <= 0 || !(box > 0) || n_mesh < 2 || n_bins < 1 || n_bins > 2048 ||
+      alias_range < 1 || alias_range > 3 || max_iter < 1 || !(tol > 0) || !k_out || !pk_out ||
+      !modes_out)
+    return fail(nullptr, PM_EINVAL, "pm_power_spectrum_jing: bad argument");
+  const char* who = "pm_power_spectrum_jing";
+  cudaStream_t st = (cudaStream_t)stream;
+  PkWork w;
+  pm_status ret = pk_transform(w, who, pos4_dev, n, n_mesh, n_bins, st);
+  if (ret != PM_OK) return ret;
+  const double shot = subtract_shot ? box * box * box / (double)n : 0.0;
+  std::vector<double> k(n_bins), p(n_bins), c(n_bins), nu(n_bins, -1.0);
+  // first-order estimate for the starting slopes
+  launch_pk_bin(st, (const float2*)w.dk, n_mesh, box, shot, n_bins, w.acc);
+  ret = pk_read(w, who, n_bins, st, k.data(), p.data(), c.data());
+  if (ret != PM_OK) return ret;
+  pk_slopes(k, p, nu);
+  int passes = 0;
+  for (passes = 1; passes <= max_iter; ++passes) {
+    if (cudaMemcpyAsync(w.nu, nu.data(), sizeof(double) * n_bins, cudaMemcpyHostToDevice,
+                        st) != cudaSuccess)
+      return fail(nullptr, PM_ECUDA, std::string(who) + ": uploading slopes failed");
+    launch_pk_jing(st, (const float2*)w.dk, n_mesh, box, shot, n_bins, alias_range, w.nu,
+                   w.acc);
+    ret = pk_read(w, who, n_bins, st, k.data(), p.data(), c.data());
+    if (ret != PM_OK) return ret;
+    std::vector<double> nn = nu;
+    pk_slopes(k, p, nn);
+    double dmax = 0.0;
+    for (int b = 0; b < n_bins; ++b) dmax = std::max(dmax, std::fabs(nn[b] - nu[b]));
+    nu = nn;
+    if (dmax < tol) break;
+  }
+  for (int b = 0; b < n_bins; ++b) {
+    k_out[b] = k[b];
+    pk_out[b] = p[b];
+    modes_out[b] = c[b];
+    if (nu_out) nu_out[b] = nu[b];
+  }
+  if (passes_out) *passes_out = std::min(passes, (int)max_iter);
+  return PM_OK;
 }
 
 pm_status pm_stats(pm_ctx* ctx, pm_stats_t* o) {

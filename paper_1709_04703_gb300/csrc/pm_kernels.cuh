@@ -93,6 +93,8 @@ void launch_pk_delta(cudaStream_t st, const unsigned long long* rho, float* delt
                      double inv_mean);
 void launch_pk_bin(cudaStream_t st, const float2* dk, int n, double box, double shot,
                    int n_bins, double* acc);
+void launch_pk_jing(cudaStream_t st, const float2* dk, int n, double box, double shot,
+                    int n_bins, int m, const double* nu, double* acc);
 
 }  // namespace pm
 

@@ -379,3 +379,21 @@ def deposit(pos4_dev, n_mesh, lo=0, side=None, periodic=True, mom4_dev=None,
                            float(drift_coef), int(n_mesh), int(lo), int(side),
                            1 if periodic else 0, _ptr(rho), C.byref(esc), _stream()))
     return rho, esc.value
+
+
+def power_spectrum_jing(pos4_dev, box, n_mesh, n_bins, subtract_shot=True, alias_range=3,
+                        max_iter=30, tol=1e-6):
+    """P(k) with the full alias correction (pm_power_spectrum_jing):
+    (k, P, modes, slopes, passes)."""
+    lib = L.load()
+    k = np.zeros(n_bins)
+    p = np.zeros(n_bins)
+    m = np.zeros(n_bins)
+    nu = np.zeros(n_bins)
+    passes = C.c_int32()
+    L.check(lib.pm_power_spectrum_jing(_ptr(pos4_dev), int(pos4_dev.shape[0]), float(box),
+                                       int(n_mesh), int(n_bins), 1 if subtract_shot else 0,
+                                       int(alias_range), int(max_iter), float(tol),
+                                       k.ctypes.data, p.ctypes.data, m.ctypes.data,
+                                       nu.ctypes.data, C.byref(passes), _stream()))
+    return k, p, m, nu, passes.value
