@@ -34,7 +34,8 @@ library, which implements them independently):
   values from a monopole + dipole + quadrupole expansion of the source about
   c at the centres of one ghost-cell layer.
 * Active mesh cube in the open phase: half-width m = ceil(R) + 1 cells, side
-  the smallest 2^j or 3*2^j >= 2m (multigrid-friendly), at most n.
+  the smallest q*2^j >= 2m with q in {1, 3, 5, 7} (halves down to a side of
+  at most 7 for the multigrid), at most n.
 * Density contrast: delta = rho/rho_mean - W with the cosmic mean N/n^3 and
   W the mean density's own CIC image: the keep cube [c-R, c+R]^3 filled
   uniformly and assigned with the deposit's tent, i.e. per axis
@@ -72,8 +73,8 @@ def is_open(R, n):
 
 
 def _mg_size(m):
-    """Smallest 2^j or 3*2^j that is >= m."""
-    sizes = sorted({2 ** j for j in range(40)} | {3 * 2 ** j for j in range(40)})
+    """Smallest q*2^j (q = 1, 3, 5 or 7) that is >= m."""
+    sizes = sorted({q * 2 ** j for q in (1, 3, 5, 7) for j in range(40)})
     return next(x for x in sizes if x >= m)
 
 

@@ -97,13 +97,14 @@ bool mg_size_ok(int n) {
   return n == 1 || n == 3;
 }
 
+// Smallest q * 2^j >= m with q in {1, 3, 5, 7}: sides that halve down to at
+// most 7 for the multigrid (open cubes; the periodic box is the mesh itself).
 int mg_round_up(int m) {
   int best = 1 << 30;
-  for (int p = 1; p < (1 << 29); p *= 2) {
-    if (p >= m) { best = std::min(best, p); break; }
-  }
-  for (int p = 3; p < (1 << 29); p *= 2) {
-    if (p >= m) { best = std::min(best, p); break; }
+  for (int q : {1, 3, 5, 7}) {
+    for (int p = q; p < (1 << 29); p *= 2) {
+      if (p >= m) { best = std::min(best, p); break; }
+    }
   }
   return best;
 }

@@ -790,7 +790,7 @@ __device__ void c_run(Grid u, Grid b, float* sm, const CmgArgs& a, float* red, i
 
 constexpr int CMG_SMEM_FLOATS = 11776;  // 16^3 -> 8^3 -> 4^3 needs 11720
 
-// level: multigrid level index of (u, b); sides 16, 12, 8, 6, 4, 3 supported.
+// level: multigrid level index of (u, b); sides 16, 14, 12, 10, 8, 7, 6, 5, 4, 3.
 // zero_top: the top level's iterate starts at zero (its interior is not read).
 __global__ void __launch_bounds__(1024) k_coarse_mg(Grid u, Grid b, int level, int periodic,
                                                     int coarse_sweeps, int zero_top,
@@ -800,9 +800,13 @@ __global__ void __launch_bounds__(1024) k_coarse_mg(Grid u, Grid b, int level, i
   CmgArgs a{periodic, level, coarse_sweeps, sig0};
   switch (u.s) {
     case 16: c_run<16>(u, b, sm, a, red, zero_top); break;
+    case 14: c_run<14>(u, b, sm, a, red, zero_top); break;
     case 12: c_run<12>(u, b, sm, a, red, zero_top); break;
+    case 10: c_run<10>(u, b, sm, a, red, zero_top); break;
     case 8: c_run<8>(u, b, sm, a, red, zero_top); break;
+    case 7: c_run<7>(u, b, sm, a, red, zero_top); break;
     case 6: c_run<6>(u, b, sm, a, red, zero_top); break;
+    case 5: c_run<5>(u, b, sm, a, red, zero_top); break;
     case 4: c_run<4>(u, b, sm, a, red, zero_top); break;
     case 3: c_run<3>(u, b, sm, a, red, zero_top); break;
     default: break;
@@ -1238,9 +1242,13 @@ __global__ void __launch_bounds__(1024) kb_coarse_mg(const CmgDesc* d, const BTa
   CmgArgs a{e.periodic, e.level, e.sweeps, 0.0f};
   switch (e.u.s) {
     case 16: c_run<16>(e.u, e.b, sm, a, red, e.zero_top); break;
+    case 14: c_run<14>(e.u, e.b, sm, a, red, e.zero_top); break;
     case 12: c_run<12>(e.u, e.b, sm, a, red, e.zero_top); break;
+    case 10: c_run<10>(e.u, e.b, sm, a, red, e.zero_top); break;
     case 8: c_run<8>(e.u, e.b, sm, a, red, e.zero_top); break;
+    case 7: c_run<7>(e.u, e.b, sm, a, red, e.zero_top); break;
     case 6: c_run<6>(e.u, e.b, sm, a, red, e.zero_top); break;
+    case 5: c_run<5>(e.u, e.b, sm, a, red, e.zero_top); break;
     case 4: c_run<4>(e.u, e.b, sm, a, red, e.zero_top); break;
     case 3: c_run<3>(e.u, e.b, sm, a, red, e.zero_top); break;
     default: break;

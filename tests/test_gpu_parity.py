@@ -226,6 +226,28 @@ def test_step_forces_open_phase():
     assert _rel_rms(F[ok], info["F"][ok]) <= 1e-5
 
 
+def _a_for_side(n, box, side):
+    """First a in [0.3, 0.995] whose keep radius gives an open cube of this side."""
+    for a in np.linspace(0.3, 0.995, 4000):
+        R = cz.chi(a, OM, OL) / (box / n) + 1.0
+        lo, s, per = opm.active_cube(R, n)
+        if not per and s == side:
+            return a
+    raise AssertionError(side)
+
+
+@pytest.mark.parametrize("side", [56, 40, 28, 20, 14, 10])
+def test_step_forces_open_cubes_of_factor_5_and_7(side):
+    """Open cubes of side 5 * 2^j and 7 * 2^j: the levels halve down to a
+    5^3 or 7^3 bottom solved by red-black SOR in one CTA."""
+    a0 = _a_for_side(64, 8000.0, side)
+    F, info, st, _, _, _, _ = _one_step(64, 8000.0, a0, 1.0, 10, 2)
+    assert st["periodic"] == 0 and st["cube_side"] == side == info["s"]
+    ok = info["F"].any(axis=1)
+    assert ok.sum() > 0
+    assert _rel_rms(F[ok], info["F"][ok]) <= 1e-5
+
+
 def test_step_forces_full_size_sampled():
     """256^3 mesh and particles (the benchmarked launch configuration): the
     oracle recomputes the step's forces at a sample of particles."""

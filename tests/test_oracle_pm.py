@@ -267,6 +267,21 @@ def test_active_cube_rules():
     assert (lo, s, per) == (80, 96, False)
     lo, s, per = pm.active_cube(1.0, 32)         # m = 2 -> 4
     assert (lo, s, per) == (14, 4, False)
+    lo, s, per = pm.active_cube(50.0, 256)       # m = 51 -> 102 -> 112 = 7 * 16
+    assert (lo, s, per) == (72, 112, False)
+    lo, s, per = pm.active_cube(35.0, 256)       # m = 36 -> 72 -> 80 = 5 * 16
+    assert (lo, s, per) == (88, 80, False)
+    lo, s, per = pm.active_cube(1.5, 32)         # m = 3 -> 6
+    assert (lo, s, per) == (13, 6, False)
+    # the cube holds the keep cube plus the CIC reach on both sides
+    for R in np.linspace(1.0, 126.9, 500):
+        lo, s, per = pm.active_cube(R, 256)
+        m = math.ceil(R) + 1
+        assert lo <= 128 - m and lo + s >= 128 + m
+        q = s
+        while q % 2 == 0:
+            q //= 2
+        assert q in (1, 3, 5, 7)
 
 
 def test_shrink_is_stable_partition():
