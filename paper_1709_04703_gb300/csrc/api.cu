@@ -200,6 +200,7 @@ struct pm_ctx {
   bool field_ready = false;
 
   int vcycles_last = 0;
+  int vc_prev = 0;          // V-cycles of the previous solve
   long long vcycles_total = 0;
   double resid_last = 0.0;
   double resid_start = 0.0, resid_guess = 0.0;  // of the last solve
@@ -566,23 +567,33 @@ pm_status solve(pm_ctx* ctx) {
   int it = 0;            // V-cycles run
   bool pending = false;  // e0 holds a correction not yet added to Phi
   bool first = true;
+  bool started = false;  // the start residual has been read
+  int slot = 11;         // d_scal slot of the latest defect's ||r||^2 (13: the first)
   double rel = 0.0;
   const double cells = (double)s * s * s;
+  // V-cycles run back to back before the residual is first read on the host:
+  // one fewer than the previous solve took (consecutive solves need similar
+  // counts), so the GPU does not wait for a host round trip after each; the
+  // network start and the pair capture read every residual.
+  const int blind = (net_todo || capture)
+                        ? 0
+                        : std::min(std::max(0, ctx->vc_prev - 1), ctx->cfg.max_vcycles - 1);
   for (;;) {
     int e = prof_begin(ctx);
     const int c0 = ctx->cur;
+    slot = first ? 13 : 11;
     if (mixed && pending) {
       // Phi <- Phi + e, written to the other buffer; reads Phi (8 B), e (4),
       // f (8), writes Phi (8) and r (4) per cell
       if (capture) launch_to_dense(ctx->st, e0, ctx->cap_e, true);
       launch_defect(ctx->st, ph_of(c0), pl_of(c0), &e0, ph_of(c0 ^ 1), pl_of(c0 ^ 1), fh, fl,
-                    r0, per, true, ctx->partial, ctx->counter, ctx->d_scal + 11,
+                    r0, per, true, ctx->partial, ctx->counter, ctx->d_scal + slot,
                     6.0 + ctx->sig_d);
       ctx->cur ^= 1;
       prof_end(ctx, PM_PROF_DEFECT, e, 32.0 * cells);
     } else {
       launch_defect(ctx->st, ph_of(c0), pl_of(c0), nullptr, ph_of(c0), pl_of(c0), fh, fl, r0,
-                    per, mixed || net_todo, ctx->partial, ctx->counter, ctx->d_scal + 11,
+                    per, mixed || net_todo, ctx->partial, ctx->counter, ctx->d_scal + slot,
                     6.0 + ctx->sig_d);
       prof_end(ctx, PM_PROF_DEFECT, e, (mixed ? 20.0 : 16.0) * cells);
     }
@@ -593,13 +604,24 @@ pm_status solve(pm_ctx* ctx) {
     }
     first = false;
     CKL();
+    if (it < blind) {
+      pm_status v = mixed ? vcycle_run(ctx, e0, r0, true)
+                          : vcycle_run(ctx, ph_of(ctx->cur), fh, false);
+      if (v != PM_OK) return v;
+      ++it;
+      pending = mixed;
+      continue;
+    }
     pm_status st = sync_read(ctx);
     if (st != PM_OK) return st;
-    double f2 = ctx->h_scal[0], r2 = ctx->h_scal[11];
+    double f2 = ctx->h_scal[0], r2 = ctx->h_scal[slot];
     rel = f2 > 0 ? std::sqrt(r2 / f2) : 0.0;
-    if (it == 0) {
-      if (!ctx->guess_used_last) ctx->resid_start = rel;
-      ctx->resid_guess = rel;
+    if (!started) {
+      started = true;
+      ctx->resid_start = f2 > 0 ? std::sqrt(ctx->h_scal[13] / f2) : 0.0;
+      ctx->resid_guess = ctx->resid_start;
+    } else if (it == 0) {
+      ctx->resid_guess = rel;  // after the network's correction
     }
     if (rel <= ctx->cfg.rtol || f2 == 0.0) break;
     if (it >= ctx->cfg.max_vcycles) {
@@ -644,6 +666,7 @@ pm_status solve(pm_ctx* ctx) {
   ctx->vcycles_last = it;
   ctx->vcycles_total += it;
   ctx->resid_last = rel;
+  ctx->vc_prev = it;
   return PM_OK;
 }
 
@@ -864,7 +887,7 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
   ctx->bgw = (df*)((char*)ctx->bgm + BGW_OFF);
   ctx->h_bg.assign(BGW_OFF + sizeof(df) * (size_t)n, 0);
   AL(ctx->d_cnt, sizeof(unsigned long long) * 4);
-  AL(ctx->d_overflow, sizeof(int));
+  ctx->d_overflow = (int*)(ctx->d_cnt + 3);  // read back with every sync_read
 #undef AL
   if (cudaMallocHost((void**)&ctx->h_scal, sizeof(double) * 16) != cudaSuccess ||
       cudaMallocHost((void**)&ctx->h_cnt, sizeof(unsigned long long) * 4) != cudaSuccess) {
@@ -886,7 +909,6 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
   Z(ctx->counter, sizeof(unsigned int) * 4);
   Z(ctx->d_scal, sizeof(double) * 16);
   Z(ctx->d_cnt, sizeof(unsigned long long) * 4);
-  Z(ctx->d_overflow, sizeof(int));
 #undef Z
   cudaMemcpyKind kind = host_mem ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   if (cudaMemcpyAsync(ctx->pos, pos4, sizeof(float4) * N, kind, s0) != cudaSuccess ||
@@ -1076,11 +1098,10 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
       st = record_to(ctx, R1, ctx->a[k + 1]);
       if (st != PM_OK) return st;
     }
-    int ovf = 0;
-    CK(cudaMemcpyAsync(&ovf, ctx->d_overflow, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
-    CK(cudaStreamSynchronize(ctx->st));
-    if (ctx->prof_on) prof_flush(ctx);
-    if (ovf) return fail(ctx, PM_EOVERFLOW, "deposit: a cell count exceeded 2^62");
+    // the source kernel flags a cell count above 2^62 in d_cnt[3], which the
+    // solve's residual reads bring back; the step itself ends without a
+    // host synchronisation (its profile events are flushed at the next read)
+    if (ctx->h_cnt[3]) return fail(ctx, PM_EOVERFLOW, "deposit: a cell count exceeded 2^62");
     ctx->particle_steps += N;
     ctx->step++;
   }
@@ -1499,7 +1520,7 @@ void pm_destroy(pm_ctx* ctx) {
                   ctx->phi_h[0], ctx->phi_l[0], ctx->phi_h[1], ctx->phi_l[1], ctx->f_hi,
                   ctx->f_lo, ctx->prev_hi, ctx->prev_lo,
                   ctx->partial, ctx->partial_m,
-                  ctx->counter, ctx->d_scal, ctx->bgm, ctx->d_cnt, ctx->d_overflow,
+                  ctx->counter, ctx->d_scal, ctx->bgm, ctx->d_cnt,
                   ctx->nn_in, ctx->nn_out, ctx->grad};
   for (void* p : ptrs)
     if (p) cudaFree(p);

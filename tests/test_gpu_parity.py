@@ -300,6 +300,22 @@ def test_shrink_bitexact(N):
     sim.close()
 
 
+def test_cell_count_overflow_is_reported():
+    """More than 2^14 particles in one cell push its Q16 count past 2^62: the
+    step reports PM_EOVERFLOW (the flag is read back with the solve's
+    residual, not by a read of its own)."""
+    from paper_1709_04703_gb300 import _lib as L
+    from paper_1709_04703_gb300.sim import Sim
+    n, N = 16, 20000
+    pos = np.full((N, 3), 8.5, np.float32)
+    mom = np.zeros((N, 3), np.float32)
+    sim = Sim(pos, mom, np.arange(N, dtype=np.int32), n, 1000.0, 0.5, 1.0, 4)
+    with pytest.raises(L.PmError) as err:
+        sim.step(1)
+    assert err.value.code == L.PM_EOVERFLOW, str(err.value)
+    sim.close()
+
+
 def test_all_particles_leave_and_empty_steps_run():
     from paper_1709_04703_gb300.sim import Sim
     n = 16
