@@ -115,3 +115,97 @@ def test_fast_light_step_is_the_poisson_step():
     p2, m2, info2 = pm.step(pos.copy(), mom.copy(), 0, sched, n, OM, nbar, want=True)
     np.testing.assert_allclose(info["F"], info2["F"], rtol=0, atol=1e-8 * np.abs(info2["F"]).max())
     np.testing.assert_allclose(m1, m2, rtol=0, atol=1e-10)
+
+
+# ---------------------------------------------------------------- ADE scheme
+
+def _ade_dense(phi_old, f, lam, upward, periodic, ghost=None):
+    """The ADE sweep as one linear solve: cell c (flat lexicographic index)
+    is coupled to its neighbours with a smaller index (upward; larger
+    downward) at the new level, to the others at the old level."""
+    n = f.shape[0]
+    N = n**3
+    A = np.zeros((N, N))
+    b = np.zeros(N)
+    flat = lambda z, y, x: (z * n + y) * n + x  # noqa: E731
+    for z in range(n):
+        for y in range(n):
+            for x in range(n):
+                c = flat(z, y, x)
+                rhs = -lam * f[z, y, x]
+                m_new = 0
+                for ax in range(3):
+                    for sg in (-1, 1):
+                        q = [z, y, x]
+                        q[ax] += sg
+                        inside = 0 <= q[ax] < n
+                        if periodic:
+                            q[ax] %= n
+                            inside = True
+                        if inside:
+                            qc = flat(*q)
+                            new = qc < c if upward else qc > c
+                            if new:
+                                A[c, qc] -= lam
+                            else:
+                                rhs += lam * phi_old[q[0], q[1], q[2]]
+                        else:
+                            g = ghost[q[0] + 1, q[1] + 1, q[2] + 1]
+                            new = (q[ax] < 0) if upward else (q[ax] >= n)
+                            rhs += lam * g
+                        m_new += 1 if new else 0
+                A[c, c] += 1 + lam * m_new
+                b[c] = rhs + (1 - lam * (6 - m_new)) * phi_old[z, y, x]
+    return np.linalg.solve(A, b).reshape(n, n, n)
+
+
+@pytest.mark.parametrize("periodic,upward", [(False, True), (False, False), (True, True),
+                                             (True, False)])
+def test_ade_sweep_is_its_triangular_system(periodic, upward):
+    n, lam = 4, 0.7
+    rng = np.random.default_rng(5)
+    phi = rng.standard_normal((n, n, n))
+    f = rng.standard_normal((n, n, n))
+    ghost = None if periodic else rng.standard_normal((n + 2,) * 3)
+    got = df.ade_substep(phi, f, lam, upward, periodic, ghost)
+    if not periodic:
+        np.testing.assert_array_equal(got[0], ghost[0])
+        got = got[1:-1, 1:-1, 1:-1]
+    ref = _ade_dense(phi, f, lam, upward, periodic, ghost)
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_ade_sweeps_converge_to_the_poisson_solution():
+    """The fixed point of an ADE sweep is lap Phi = f: alternating sweeps
+    with a fixed source reach the static solution (open and periodic)."""
+    s = 6
+    rng = np.random.default_rng(6)
+    f = rng.standard_normal((s, s, s))
+    ghost = np.zeros((s + 2,) * 3)
+    ghost[0] = 0.2
+    ghost[:, -1] = -0.1
+    ref = pm.solve_open(f, ghost)[1:-1, 1:-1, 1:-1]
+    phi = np.zeros((s, s, s))
+    for it in range(120):
+        phi = df.ade_substep(phi, f, 1.0, it % 2 == 0, False, ghost)[1:-1, 1:-1, 1:-1]
+    np.testing.assert_allclose(phi, ref, rtol=0, atol=1e-8 * np.abs(ref).max())
+    fp = f - f.mean()
+    refp = pm.solve_periodic(fp)
+    phi = np.zeros((s, s, s))
+    for it in range(160):
+        phi = df.ade_substep(phi, fp, 1.0, it % 2 == 0, True)
+    np.testing.assert_allclose(phi - phi.mean(), refp, rtol=0, atol=1e-8 * np.abs(refp).max())
+
+
+def test_ade_small_step_follows_the_diffusion_equation():
+    """For a smooth mode with no source, one up + down pair with lam -> 0
+    approaches the exact decay exp(2 lam lap_k); the error shrinks as lam does."""
+    n = 12
+    phi0 = _mode(n, 1)
+    lapk = -4.0 * np.sin(np.pi / n) ** 2
+    errs = []
+    for lam in (0.2, 0.1, 0.05):
+        u = df.ade_substep(phi0, np.zeros((n, n, n)), lam, True, True)
+        u = df.ade_substep(u, np.zeros((n, n, n)), lam, False, True)
+        errs.append(np.abs(u - phi0 * np.exp(2 * lam * lapk)).max())
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 0.01, errs
