@@ -471,6 +471,9 @@ def run_ours(args):
         # the paper's diffusion-equation gravity (two implicit half-substeps)
         compare["diffusion_gravity"] = _variant(pos, mom, ids, cfg, K, rtol, "mixed",
                                                 gravity="diffusion")
+        # ... and with the paper's own explicit (ADE) sweeps instead of solves
+        compare["diffusion_ade"] = _variant(pos, mom, ids, cfg, K, rtol, "mixed",
+                                            gravity="diffusion_ade")
         # the same steps in the fixed periodic box (every particle, every step)
         compare["no_shrink"] = _variant(pos, mom, ids, cfg, K, rtol, "mixed", bc="periodic",
                                         shrink=False)
@@ -579,7 +582,8 @@ def main():
     ap.add_argument("--table-n", type=int, default=512,
                     help="shrink_table: particles and mesh per side")
     ap.add_argument("--gravities", nargs="+", default=["diffusion", "poisson"],
-                    choices=["diffusion", "poisson"], help="shrink_table: gravity solvers")
+                    choices=["diffusion", "diffusion_ade", "poisson"],
+                    help="shrink_table: gravity solvers")
     args = ap.parse_args()
     args.steps_given = "--steps" in sys.argv
     if args.impl == "reference":

@@ -50,7 +50,8 @@ typedef enum {
 
 enum { PM_MIXED = 0, PM_FP32_PLAIN = 1 };               /* pm_config.precision */
 enum { PM_GUESS_WARM = 0, PM_GUESS_ZERO = 1, PM_GUESS_LEARNED = 2 };  /* pm_config.guess */
-enum { PM_GRAVITY_POISSON = 0, PM_GRAVITY_DIFFUSION = 1 };           /* pm_config.gravity */
+enum { PM_GRAVITY_POISSON = 0, PM_GRAVITY_DIFFUSION = 1,
+       PM_GRAVITY_DIFFUSION_ADE = 2 };                                 /* pm_config.gravity */
 enum { PM_BC_PAPER = 0, PM_BC_OPEN = 1, PM_BC_PERIODIC = 2 };  /* pm_config.bc */
 enum { PM_SHRINK_OFF = 0, PM_SHRINK_ON = 1, PM_SHRINK_RECORD = 2 };  /* pm_config.shrink */
 
@@ -92,7 +93,10 @@ typedef struct {
   int32_t gravity;       /* PM_GRAVITY_POISSON: static Eq. 3 every step;
                             PM_GRAVITY_DIFFUSION: the diffusion equation (Eq. 4,
                             Sec. 2.3) advanced by two implicit half-substeps
-                            per step in the Table 2 order (see pm_step) */
+                            per step in the Table 2 order (see pm_step);
+                            PM_GRAVITY_DIFFUSION_ADE: the same equation and
+                            order with the paper's alternating-direction
+                            explicit scheme (see pm_step) */
   double c_eff_factor;   /* diffusion only: c_eff = factor * cell (Mpc/h) * c,
                             0.019 in Sec. 3.1.1 */
 } pm_config;
@@ -124,10 +128,17 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
  * H = a E(a) and S at the substep's end, the density of t+dt/2 for both,
  * solved by the same multigrid with a diagonal shift to rtol of
  * ||g - (A - sig) Phi|| / ||g||; the field starts from the static solution
- * of the initial density.  Stops early with PM_EINVAL past the last step of
- * the schedule, PM_ENOCONV if a solve fails to converge, PM_EOVERFLOW on
- * fixed-point overflow.  Synchronises the stream once per V-cycle
- * (convergence test) and once per shrink (new active count). */
+ * of the initial density.  With PM_GRAVITY_DIFFUSION_ADE each half-substep
+ * is instead one sweep of the paper's alternating-direction explicit scheme
+ * (Sec. 2.3, Saul'yev form) with lam = 1/sig:
+ *   Phi_c (1 + lam m) = Phi_c,old (1 - lam (6 - m)) + lam (sum_q Phi_q - S delta)
+ * over the cells in lexicographic order, upward in the first half-substep
+ * and downward in the second, Phi_q as already updated by the sweep (m of
+ * the six) or not; no solve.  Stops early with PM_EINVAL past the last step
+ * of the schedule, PM_ENOCONV if a solve fails to converge, PM_EOVERFLOW on
+ * fixed-point overflow.  Synchronises the stream for the solver's residual
+ * reads (after a run of V-cycles as long as the previous solve's, less one,
+ * then after each) and once per shrink (new active count). */
 pm_status pm_step(pm_ctx* ctx, int32_t n_steps);
 
 /* Drop particles outside the keep cube of expansion factor a (Sec. 2.4:
@@ -271,6 +282,7 @@ enum {
   PM_PROF_GATHER,       /* gradient + gather + kick + drift + keep flags    */
   PM_PROF_COMPACT,      /* scan + stable scatter                            */
   PM_PROF_GUESS,        /* learned initial guess (network forward)          */
+  PM_PROF_ADE,          /* explicit diffusion sweeps (PM_GRAVITY_DIFFUSION_ADE) */
   PM_PROF_N
 };
 /* enable = 1 starts (and zeroes) the counters, 0 stops them. */

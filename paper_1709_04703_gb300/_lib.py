@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(HERE, "libpmshrink.so")
 PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_ENOCONV, PM_EOVERFLOW, PM_ETIMEOUT = range(7)
 PM_MIXED, PM_FP32_PLAIN = 0, 1
 PM_GUESS_WARM, PM_GUESS_ZERO, PM_GUESS_LEARNED = 0, 1, 2
-PM_GRAVITY_POISSON, PM_GRAVITY_DIFFUSION = 0, 1
+PM_GRAVITY_POISSON, PM_GRAVITY_DIFFUSION, PM_GRAVITY_DIFFUSION_ADE = 0, 1, 2
 PM_BC_PAPER, PM_BC_OPEN, PM_BC_PERIODIC = 0, 1, 2
 PM_SHRINK_OFF, PM_SHRINK_ON, PM_SHRINK_RECORD = 0, 1, 2
 PM_SHRINK_STATIC_MAX_PARTICLES = 1 << 22
@@ -35,7 +35,7 @@ EXPORTED = [
     "pm_guess_last_error", "pm_guess_destroy", "pm_set_guess", "pm_capture",
 ]
 PROF_CLASSES = ["deposit", "source", "boundary", "smooth0", "transfer0", "coarse",
-                "defect", "correct", "gather", "compact", "guess"]
+                "defect", "correct", "gather", "compact", "guess", "ade"]
 
 
 class PmConfig(C.Structure):

@@ -799,8 +799,9 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
   if (cfg->shrink < PM_SHRINK_OFF || cfg->shrink > PM_SHRINK_RECORD)
     return fail(nullptr, PM_EINVAL, "pm_init: unknown shrink mode");
   if (cfg->gravity != PM_GRAVITY_POISSON &&
-      (cfg->gravity != PM_GRAVITY_DIFFUSION || !(cfg->c_eff_factor > 0) ||
-       cfg->precision != PM_MIXED || cfg->guess == PM_GUESS_LEARNED))
+      ((cfg->gravity != PM_GRAVITY_DIFFUSION && cfg->gravity != PM_GRAVITY_DIFFUSION_ADE) ||
+       !(cfg->c_eff_factor > 0) || cfg->precision != PM_MIXED ||
+       cfg->guess == PM_GUESS_LEARNED))
     return fail(nullptr, PM_EINVAL,
                 "pm_init: diffusion gravity needs c_eff_factor > 0, PM_MIXED, no learned guess");
 
@@ -944,7 +945,8 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
     if (st != PM_OK) return st;
     const long long N = ctx->n_active;
     const double cells = (double)s * s * s;
-    const bool diffusion = ctx->cfg.gravity == PM_GRAVITY_DIFFUSION;
+    const bool diffusion = ctx->cfg.gravity != PM_GRAVITY_POISSON;
+    const bool ade = ctx->cfg.gravity == PM_GRAVITY_DIFFUSION_ADE;
     const double nbar = (double)ctx->N0 / ((double)n * n * n);
     const double invM = 1.0 / (281474976710656.0 * nbar);
     Grid fh = full_view(ctx, ctx->f_hi, lo, s), fl = full_view(ctx, ctx->f_lo, lo, s);
@@ -1004,7 +1006,17 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
       ctx->sig_d = sg;
       ctx->sig = (float)sg;
     };
-    if (diffusion) {
+    if (ade) {
+      // substep 1 (t -> t + dt/2): one upward explicit sweep, in place
+      ghosts(S);
+      e = prof_begin(ctx);
+      CK(launch_ade_sweep(ctx->st, full_view(ctx, ctx->phi_h[ctx->cur], lo, s),
+                          full_view(ctx, ctx->phi_l[ctx->cur], lo, s), fh, fl, 1.0, per,
+                          1.0 / shift(ctx->a_half[k]), true));
+      // read f and Phi (16 B), write Phi (8 B) per cell
+      prof_end(ctx, PM_PROF_ADE, e, 24.0 * cells);
+      CKL();
+    } else if (diffusion) {
       // substep 1 (t -> t + dt/2): g = f - sig Phi_old, f kept for substep 2
       ghosts(S);
       const double sg = shift(ctx->a_half[k]);
@@ -1044,13 +1056,15 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
         prof_end(ctx, PM_PROF_CORRECT, e, 32.0 * cells);
       }
     }
-    st = solve(ctx);
-    ctx->sig = 0.0f;
-    ctx->sig_d = 0.0;
-    if (st != PM_OK) return st;
-    ctx->ah_hist[0] = ctx->ah_hist[1];
-    ctx->ah_hist[1] = ctx->a_half[k];
-    ctx->n_sol++;
+    if (!ade) {
+      st = solve(ctx);
+      ctx->sig = 0.0f;
+      ctx->sig_d = 0.0;
+      if (st != PM_OK) return st;
+      ctx->ah_hist[0] = ctx->ah_hist[1];
+      ctx->ah_hist[1] = ctx->a_half[k];
+      ctx->n_sol++;
+    }
     // 4-6. gradient + gather + kick + half drift (+ keep flags)
     const bool do_flag =
         ctx->cfg.shrink == PM_SHRINK_ON && ctx->cfg.bc != PM_BC_PERIODIC && is_open(ctx, R1);
@@ -1070,7 +1084,18 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
     CKL();
     ctx->forces_valid = ctx->forces != nullptr;
     ctx->forces_n = N;
-    if (diffusion) {
+    if (ade) {
+      // substep 2 (t + dt/2 -> t + dt): the same density, S and H at a_{n+1},
+      // one downward sweep
+      const double S2 = 1.5 * ctx->cfg.omega_m / ctx->a[k + 1];
+      ghosts(S2);
+      e = prof_begin(ctx);
+      CK(launch_ade_sweep(ctx->st, full_view(ctx, ctx->phi_h[ctx->cur], lo, s),
+                          full_view(ctx, ctx->phi_l[ctx->cur], lo, s), fh, fl, S2 / S, per,
+                          1.0 / shift(ctx->a[k + 1]), false));
+      prof_end(ctx, PM_PROF_ADE, e, 24.0 * cells);
+      CKL();
+    } else if (diffusion) {
       // substep 2 (t + dt/2 -> t + dt): the same density, S and H at a_{n+1}
       const double S2 = 1.5 * ctx->cfg.omega_m / ctx->a[k + 1];
       ghosts(S2);

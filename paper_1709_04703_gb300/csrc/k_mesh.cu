@@ -2,7 +2,11 @@
 // deposit (Sec. 2.2 first DKD line; Sec. 2.4 footnote, CIC), the Poisson
 // source on the active cube (Sec. 2.1, Eq. 3) with its boundary multipoles,
 // and the open-boundary ghost layer (Table 1: open boundaries).
+#include <cooperative_groups.h>
+
 #include "pm_kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace pm {
 
@@ -526,6 +530,112 @@ void launch_boundary(cudaStream_t st, Grid ph, Grid pl, int n, int lo, const dou
   int grid = (int)((tot + 255) / 256);
   k_boundary<<<grid, 256, 0, st>>>(ph, pl, n, lo, mom, S, want_lo ? 1 : 0);
   note_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Alternating-direction explicit half-substep (Sec. 2.3; Saul'yev form) of
+// dPhi/dtau = D (lap Phi - f), lam = D dtau_sub:
+//   Phi_c (1 + lam m_new) = Phi_c,old (1 - lam (6 - m_new)) + lam (sum_q Phi_q - fscale f)
+// over a sweep of the cube in lexicographic order (upward or downward),
+// Phi_q as it stands in memory (m_new of the six already swept).  The sweep
+// runs as a wavefront: one launch per plane i + j + k = d, whose cells
+// depend only on the planes before it; a cell's lower neighbours (upper when
+// downward) lie on the plane before and its upper ones on the plane after,
+// and across the periodic wrap the neighbour of a first cell lies on a later
+// plane, that of a last cell on an earlier one -- exactly as in the
+// sequential sweep, whose result this is.  FP64 arithmetic on the
+// double-float potential; c_a[m] = 1 - lam (6 - m), c_b[m] = 1 / (1 + lam m).
+// Open cubes: the ghost layer holds the Dirichlet values (read only).
+// ---------------------------------------------------------------------------
+struct AdeCoef {
+  double a[7], b[7];
+};
+
+template <bool UP>
+__device__ __forceinline__ void ade_cell(Grid ph, Grid pl, Grid fh, Grid fl, double fscale,
+                                         double lam, const AdeCoef& cf, int periodic, int i,
+                                         int j, int k) {
+  const int s = ph.s;
+  const int im = periodic ? (i == 0 ? s - 1 : i - 1) : i - 1;
+  const int ip = periodic ? (i == s - 1 ? 0 : i + 1) : i + 1;
+  const int jm = periodic ? (j == 0 ? s - 1 : j - 1) : j - 1;
+  const int jp = periodic ? (j == s - 1 ? 0 : j + 1) : j + 1;
+  const int km = periodic ? (k == 0 ? s - 1 : k - 1) : k - 1;
+  const int kp = periodic ? (k == s - 1 ? 0 : k + 1) : k + 1;
+  const int nb[6] = {gidx(ph, im, j, k), gidx(ph, ip, j, k), gidx(ph, i, jm, k),
+                     gidx(ph, i, jp, k), gidx(ph, i, j, km), gidx(ph, i, j, kp)};
+  int m_new = 3;
+  if (periodic) {
+    // swept before: upward the lower neighbour unless it wraps, and the upper
+    // one when it wraps (mirror image downward)
+    const int idx[3] = {i, j, k};
+    m_new = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      m_new += UP ? (idx[a] > 0) + (idx[a] == s - 1) : (idx[a] < s - 1) + (idx[a] == 0);
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) sum += (double)ph.base[nb[q]] + (double)pl.base[nb[q]];
+  const int c = gidx(ph, i, j, k);
+  const double old = (double)ph.base[c] + (double)pl.base[c];
+  const int fc = gidx(fh, i, j, k);
+  const double f = ((double)fh.base[fc] + (double)fl.base[fc]) * fscale;
+  const double v = (cf.a[m_new] * old + lam * (sum - f)) * cf.b[m_new];
+  const float h = (float)v;
+  ph.base[c] = h;
+  pl.base[c] = (float)(v - (double)h);
+}
+
+// The whole sweep in one cooperative launch: every thread takes its share of
+// a plane's cells, then the grid waits (grid-wide barrier) before the next
+// plane.  All blocks are resident (the launch is sized by the occupancy).
+template <bool UP>
+__global__ void __launch_bounds__(256) k_ade_sweep(Grid ph, Grid pl, Grid fh, Grid fl,
+                                                   double fscale, double lam, AdeCoef cf,
+                                                   int periodic) {
+  cg::grid_group grid = cg::this_grid();
+  const int s = ph.s, np = 3 * s - 2;
+  const int stride = gridDim.x * blockDim.x;
+  for (int q = 0; q < np; ++q) {
+    const int d = UP ? q : np - 1 - q;
+    // cells of the plane: j + k in [d - s + 1, d], i = d - j - k
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < s * s; t += stride) {
+      const int j = t % s, k = t / s, i = d - j - k;
+      if (i >= 0 && i < s) ade_cell<UP>(ph, pl, fh, fl, fscale, lam, cf, periodic, i, j, k);
+    }
+    grid.sync();
+  }
+}
+
+cudaError_t launch_ade_sweep(cudaStream_t st, Grid ph, Grid pl, Grid fh, Grid fl,
+                             double fscale, int periodic, double lam, bool upward) {
+  AdeCoef cf;
+  for (int m = 0; m <= 6; ++m) {
+    cf.a[m] = 1.0 - lam * (6 - m);
+    cf.b[m] = 1.0 / (1.0 + lam * m);
+  }
+  // resident blocks: queried once per direction
+  static int per_sm[2] = {-1, -1};
+  static int n_sm = 0;
+  const int u = upward ? 1 : 0;
+  if (per_sm[u] < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm[u], upward ? (const void*)k_ade_sweep<true> : (const void*)k_ade_sweep<false>,
+        256, 0);
+    if (e != cudaSuccess) return e;
+  }
+  const int need = (ph.s * ph.s + 255) / 256;
+  const int blocks = std::max(1, std::min(need, per_sm[u] * n_sm));
+  void* args[] = {&ph, &pl, &fh, &fl, &fscale, &lam, &cf, &periodic};
+  cudaError_t e = cudaLaunchCooperativeKernel(
+      upward ? (const void*)k_ade_sweep<true> : (const void*)k_ade_sweep<false>,
+      dim3((unsigned)blocks), dim3(256), args, 0, st);
+  note_launch();
+  return e;
 }
 
 // ---------------------------------------------------------------------------

@@ -25,6 +25,8 @@ void launch_source(cudaStream_t st, int grid, unsigned long long* rho, int n, in
 void launch_source_f64(cudaStream_t st, int grid, const double* delta, int n, Grid fh,
                        Grid fl, double S, bool moments, double* partial,
                        unsigned int* counter, double* out);
+cudaError_t launch_ade_sweep(cudaStream_t st, Grid ph, Grid pl, Grid fh, Grid fl,
+                             double fscale, int periodic, double lam, bool upward);
 void launch_diff_rhs(cudaStream_t st, int grid, Grid sh, Grid sl, double scale, Grid ph,
                      Grid pl, double sig, Grid gh, Grid gl, Grid qh, Grid ql, bool stash,
                      double* partial, unsigned int* counter, double* out);

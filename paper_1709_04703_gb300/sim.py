@@ -10,7 +10,8 @@ from . import _lib as L
 _PREC = {"mixed": L.PM_MIXED, "fp32": L.PM_FP32_PLAIN}
 _GUESS = {"warm": L.PM_GUESS_WARM, "zero": L.PM_GUESS_ZERO, "learned": L.PM_GUESS_LEARNED}
 _BC = {"paper": L.PM_BC_PAPER, "open": L.PM_BC_OPEN, "periodic": L.PM_BC_PERIODIC}
-_GRAVITY = {"poisson": L.PM_GRAVITY_POISSON, "diffusion": L.PM_GRAVITY_DIFFUSION}
+_GRAVITY = {"poisson": L.PM_GRAVITY_POISSON, "diffusion": L.PM_GRAVITY_DIFFUSION,
+            "diffusion_ade": L.PM_GRAVITY_DIFFUSION_ADE}
 # shrink: True / "on" drops leavers into the lightcone; False / "off" keeps
 # everything; "record" keeps everything and records lightcone crossings
 _SHRINK = {False: L.PM_SHRINK_OFF, True: L.PM_SHRINK_ON, "off": L.PM_SHRINK_OFF,

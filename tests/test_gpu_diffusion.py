@@ -32,12 +32,12 @@ def _rel_rms(a, b):
     return np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum())
 
 
-def _one_step(n, box, a0, steps, seed):
+def _one_step(n, box, a0, steps, seed, scheme="implicit"):
     from paper_1709_04703_gb300.sim import Sim
     pos, mom, ids = ics.zeldovich(n, -2.0, None, seed, a0)
     sched = cz.schedule(n, box, OM, OL, a0, 1.0, steps)
     sim = Sim(pos, mom, ids, n, box, a0, 1.0, steps, rtol=1e-10, store_forces=True,
-              max_vcycles=60, gravity="diffusion")
+              max_vcycles=60, gravity="diffusion" if scheme == "implicit" else "diffusion_ade")
     sim.step(1)
     F = sim.forces()
     phi, lo, s = sim.potential()
@@ -45,7 +45,8 @@ def _one_step(n, box, a0, steps, seed):
     sim.close()
     state = odf.initial_field(pos.astype(np.float64), sched, n, OM, 1.0)
     _, _, (phi_o, geo), info = odf.step(pos.astype(np.float64), mom.astype(np.float64), state,
-                                        0, sched, n, OM, OL, 1.0, want=True, drift32=True)
+                                        0, sched, n, OM, OL, 1.0, want=True, drift32=True,
+                                        scheme=scheme)
     return F, phi, (lo, s), st, info, phi_o
 
 
@@ -68,6 +69,48 @@ def test_diffusion_step_open_phase():
     assert _rel_rms(phi[1:-1, 1:-1, 1:-1], phi_o[1:-1, 1:-1, 1:-1]) <= 1e-7
     # the ghost layer carries the static multipole values of the last source
     np.testing.assert_allclose(phi[0, 1:-1, 1:-1], phi_o[0, 1:-1, 1:-1], rtol=1e-6)
+
+
+# ------------------------------------------------------------------ ADE scheme
+
+def test_ade_step_periodic_phase():
+    """One step with the paper's explicit scheme (an upward sweep, kick, a
+    downward sweep), periodic phase: forces and field against the oracle's
+    plain sequential sweeps."""
+    F, phi, (lo, s), st, info, phi_o = _one_step(16, 125.0, 0.02, 20, 3, scheme="ade")
+    assert st["periodic"] == 1 and s == 16
+    assert _rel_rms(F, info["F"]) <= 1e-5
+    g = phi[1:-1, 1:-1, 1:-1]
+    assert _rel_rms(g - g.mean(), phi_o - phi_o.mean()) <= 1e-7
+
+
+def test_ade_step_open_phase():
+    F, phi, (lo, s), st, info, phi_o = _one_step(32, 8000.0, 0.5, 10, 4, scheme="ade")
+    assert st["periodic"] == 0 and (lo, s) == (info["lo"], info["s"])
+    ok = info["F"].any(axis=1)
+    assert _rel_rms(F[ok], info["F"][ok]) <= 1e-5
+    assert _rel_rms(phi[1:-1, 1:-1, 1:-1], phi_o[1:-1, 1:-1, 1:-1]) <= 1e-7
+
+
+def test_ade_run_power_spectrum_matches_oracle():
+    """16^3 particles and mesh, 125 Mpc/h, a 0.02 -> 1 in 20 steps with the
+    explicit scheme: final P(k) of lightcone + survivors within 0.5 %."""
+    from paper_1709_04703_gb300.sim import Sim
+    n, box, a0, steps = 16, 125.0, 0.02, 20
+    pos, mom, ids = ics.zeldovich(n, -2.0, None, 5, a0)
+    sim = Sim(pos, mom, ids, n, box, a0, 1.0, steps, rtol=1e-9, gravity="diffusion_ade")
+    sim.step(steps)
+    st = sim.stats()
+    k, pg, _ = _final_pk(sim, n, box)
+    sim.close()
+    sched = cz.schedule(n, box, OM, OL, a0, 1.0, steps)
+    out = odf.run(pos, mom, ids, sched, n, OM, OL, 1.0, scheme="ade")
+    assert st["n_active"] + st["n_lightcone"] == n ** 3
+    allo = np.concatenate([out["pos"], out["lc_pos"]]) % n
+    _, po, _ = opk(allo, n, box, n // 2)
+    sel = slice(0, n // 4)
+    rel = np.abs(pg[sel] / po[sel] - 1)
+    assert rel.max() <= 5e-3, rel
 
 
 def _dev4(p):
@@ -108,20 +151,22 @@ def test_diffusion_run_pm32_power_spectrum_matches_oracle():
     assert rel.max() <= 5e-3, rel
 
 
-def test_diffusion_against_static_power_spectrum():
+@pytest.mark.parametrize("gravity", ["diffusion", "diffusion_ade"])
+def test_diffusion_against_static_power_spectrum(gravity):
     """Sec. 3.1 finds the diffusion and static solvers' spectra a few per
-    cent apart: the same holds for the 64^3 analogue of the 128^3 workload."""
+    cent apart: the same holds for the 64^3 analogue of the 128^3 workload,
+    with the implicit half-substeps and with the paper's explicit sweeps."""
     from paper_1709_04703_gb300.sim import Sim
     n, box, a0, steps = 64, 500.0, 0.02, 50
     pos, mom, ids = ics.zeldovich(n, -1.5, 0.5, 1, a0)
     out = {}
-    for g in ("poisson", "diffusion"):
+    for g in ("poisson", gravity):
         sim = Sim(pos, mom, ids, n, box, a0, 1.0, steps, rtol=1e-7, gravity=g)
         sim.step(steps)
         out[g] = _final_pk(sim, n, box)
         sim.close()
     sel = slice(0, n // 4)
-    rel = np.abs(out["diffusion"][1][sel] / out["poisson"][1][sel] - 1)
+    rel = np.abs(out[gravity][1][sel] / out["poisson"][1][sel] - 1)
     assert rel.max() < 0.1, rel
 
 
