@@ -151,13 +151,16 @@ def test_diffusion_run_pm32_power_spectrum_matches_oracle():
     assert rel.max() <= 5e-3, rel
 
 
-@pytest.mark.parametrize("gravity", ["diffusion", "diffusion_ade"])
-def test_diffusion_against_static_power_spectrum(gravity):
-    """Sec. 3.1 finds the diffusion and static solvers' spectra a few per
-    cent apart: the same holds for the 64^3 analogue of the 128^3 workload,
-    with the implicit half-substeps and with the paper's explicit sweeps."""
+@pytest.mark.parametrize("gravity,steps,bound", [("diffusion", 50, 0.1),
+                                                  ("diffusion_ade", 1000, 0.075)])
+def test_diffusion_against_static_power_spectrum(gravity, steps, bound):
+    """Sec. 3.1 finds the diffusion and static solvers' spectra within 7.5 %
+    (1000 steps): the same holds for the 64^3 analogue of the 128^3
+    workload, with the implicit half-substeps (already at 50 steps) and with
+    the paper's explicit sweeps at its 1000 steps (whose splitting error
+    grows with the step: 27 % at 50 steps, 3.7 % at 200)."""
     from paper_1709_04703_gb300.sim import Sim
-    n, box, a0, steps = 64, 500.0, 0.02, 50
+    n, box, a0 = 64, 500.0, 0.02
     pos, mom, ids = ics.zeldovich(n, -1.5, 0.5, 1, a0)
     out = {}
     for g in ("poisson", gravity):
@@ -167,7 +170,7 @@ def test_diffusion_against_static_power_spectrum(gravity):
         sim.close()
     sel = slice(0, n // 4)
     rel = np.abs(out[gravity][1][sel] / out["poisson"][1][sel] - 1)
-    assert rel.max() < 0.1, rel
+    assert rel.max() < bound, rel
 
 
 def test_batches_refuse_diffusion():
