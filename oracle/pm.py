@@ -78,11 +78,13 @@ def _mg_size(m):
     return next(x for x in sizes if x >= m)
 
 
-def active_cube(R, n):
-    """(lo, s, periodic) of the mesh cube worked on while the keep radius is R."""
+def active_cube(R, n, reach=1):
+    """(lo, s, periodic) of the mesh cube worked on while the keep radius is R;
+    reach: cells the assignment extends beyond a particle's cell (CIC 1,
+    TSC 2)."""
     if not is_open(R, n):
         return 0, n, True
-    m = math.ceil(R) + 1
+    m = math.ceil(R) + reach
     s = min(_mg_size(2 * m), n)
     return n // 2 - s // 2, s, False
 
@@ -95,14 +97,27 @@ def tent_integral(u):
                              np.where(u <= 1.0, 1.0 - 0.5 * (1.0 - u) * (1.0 - u), 1.0)))
 
 
-def background_weights(R, n, lo, s, periodic):
-    """Per-axis weight w_i of the mean density on cells lo..lo+s-1: the CIC
-    image of the keep interval [c - R, c + R] (all ones when periodic)."""
+def tsc_integral(u):
+    """Integral over t < u of the TSC kernel, 3/4 - t^2 on |t| <= 1/2 and
+    (3/2 - |t|)^2 / 2 on 1/2 <= |t| <= 3/2."""
+    u = np.asarray(u, dtype=np.float64)
+    lo = (1.5 + u) ** 3 / 6.0
+    mid = 1.0 / 6.0 + 0.75 * (u + 0.5) - (u ** 3 + 0.125) / 3.0
+    hi = 1.0 - (1.5 - u) ** 3 / 6.0
+    return np.where(u <= -1.5, 0.0, np.where(u <= -0.5, lo, np.where(
+        u <= 0.5, mid, np.where(u <= 1.5, hi, 1.0))))
+
+
+def background_weights(R, n, lo, s, periodic, assign="cic"):
+    """Per-axis weight w_i of the mean density on cells lo..lo+s-1: the
+    image of the keep interval [c - R, c + R] under the assignment kernel
+    (CIC tent or TSC; all ones when periodic)."""
     if periodic:
         return np.ones(s)
     c = n / 2
     x = np.arange(lo, lo + s) + 0.5
-    return tent_integral((c + R) - x) - tent_integral((c - R) - x)
+    cdf = tsc_integral if assign == "tsc" else tent_integral
+    return cdf((c + R) - x) - cdf((c - R) - x)
 
 
 # --------------------------------------------------------------------------
@@ -152,11 +167,11 @@ def source_S(a, om):
     return 1.5 * om / a
 
 
-def delta_cube(rho, n, lo, s, nbar, R, periodic):
+def delta_cube(rho, n, lo, s, nbar, R, periodic, assign="cic"):
     """Density contrast on the active cube [z,y,x] (s^3, float64)."""
     sub = rho[lo:lo + s, lo:lo + s, lo:lo + s].astype(np.float64)
     d = sub / (MASS_UNIT * nbar)
-    w = background_weights(R, n, lo, s, periodic)
+    w = background_weights(R, n, lo, s, periodic, assign)
     return d - w[:, None, None] * w[None, :, None] * w[None, None, :]
 
 
@@ -270,11 +285,11 @@ def apply_laplacian_periodic(phi):
             - 6.0 * phi)
 
 
-def solve_step_potential(rho, n, lo, s, periodic, nbar, R, a_half, om):
+def solve_step_potential(rho, n, lo, s, periodic, nbar, R, a_half, om, assign="cic"):
     """Source and potential of one step.  Returns (f_cube, phi) where phi is
     n^3 (periodic) or padded (s+2)^3 (open, ghosts included)."""
     S = source_S(a_half, om)
-    f = S * delta_cube(rho, n, lo, s, nbar, R, periodic)
+    f = S * delta_cube(rho, n, lo, s, nbar, R, periodic, assign)
     if periodic:
         return f, solve_periodic(f)
     return f, solve_open(f, open_ghost_potential(f, S, lo, n))
@@ -313,6 +328,82 @@ def gather_force(phi, pos, n, lo, s, periodic):
                 F[:, 0] += wt * gx
                 F[:, 1] += wt * gy
                 F[:, 2] += wt * gz
+    F[~ok] = 0.0
+    return F, int((~ok).sum())
+
+
+# --------------------------------------------------------------------------
+# TSC with fixed-point weights (Sec. 2.4 footnote: CIC or TSC, the same
+# scheme for the density and the force)
+# --------------------------------------------------------------------------
+
+def tsc_index(pos):
+    """Cell i (the node nearest the particle) and Q16 weights of nodes
+    i-1, i, i+1 per axis.  The position within the cell is taken in Q16,
+    frac = floor(2^16 u) - 2^16 i (exact), and d = frac - 2^15 is the offset
+    from the cell centre; the outer weights are floor((2^15 -+ d)^2 / 2^17)
+    (the kernel's (1/2 -+ d)^2 / 2 in Q16) and the centre takes the rest, so
+    every axis sums to exactly 2^16."""
+    u = np.asarray(pos, dtype=np.float64)
+    i = np.floor(u)
+    frac = np.floor(u * Q16) - i * Q16
+    d = frac - Q16 // 2
+    a = Q16 // 2 - d
+    b = Q16 // 2 + d
+    wm = np.floor(a * a / 2.0 ** 17)
+    wp = np.floor(b * b / 2.0 ** 17)
+    w0 = Q16 - wm - wp
+    return i.astype(np.int64), np.stack([wm, w0, wp], axis=-1).astype(np.int64)
+
+
+def _valid_tsc(i, lo, s):
+    return np.all((i - 1 >= lo) & (i + 1 <= lo + s - 1), axis=1)
+
+
+def deposit_tsc(pos, n, lo, s, periodic):
+    """Integer TSC mass counts rho[z,y,x] (int64), and the escaped count."""
+    i, w = tsc_index(pos)
+    rho = np.zeros((n, n, n), dtype=np.int64)
+    ok = np.ones(len(i), dtype=bool) if periodic else _valid_tsc(i, lo, s)
+    i, w = i[ok], w[ok]
+    for cz in range(3):
+        for cy in range(3):
+            for cx in range(3):
+                x = i[:, 0] + cx - 1
+                y = i[:, 1] + cy - 1
+                z = i[:, 2] + cz - 1
+                if periodic:
+                    x, y, z = x % n, y % n, z % n
+                np.add.at(rho, (z, y, x), w[:, 0, cx] * w[:, 1, cy] * w[:, 2, cz])
+    return rho, int((~ok).sum())
+
+
+def gather_force_tsc(phi, pos, n, lo, s, periodic):
+    """grad(Phi) at the particles with the TSC weights; escaped get 0."""
+    i, w = tsc_index(pos)
+    N = len(i)
+    F = np.zeros((N, 3))
+    ok = np.ones(N, dtype=bool) if periodic else _valid_tsc(i, lo, s)
+    wf = w / Q16
+
+    if periodic:
+        def val(ix, iy, iz):
+            return phi[iz % n, iy % n, ix % n]
+        base = i
+    else:
+        def val(ix, iy, iz):
+            return phi[iz, iy, ix]
+        base = np.where(ok[:, None], i - lo + 1, 2)  # padded local index
+    for cz in range(3):
+        for cy in range(3):
+            for cx in range(3):
+                x = base[:, 0] + cx - 1
+                y = base[:, 1] + cy - 1
+                z = base[:, 2] + cz - 1
+                wt = wf[:, 0, cx] * wf[:, 1, cy] * wf[:, 2, cz]
+                F[:, 0] += wt * 0.5 * (val(x + 1, y, z) - val(x - 1, y, z))
+                F[:, 1] += wt * 0.5 * (val(x, y + 1, z) - val(x, y - 1, z))
+                F[:, 2] += wt * 0.5 * (val(x, y, z + 1) - val(x, y, z - 1))
     F[~ok] = 0.0
     return F, int((~ok).sum())
 
@@ -362,26 +453,29 @@ def shrink(arrays, keep):
 # the whole step and the whole run
 # --------------------------------------------------------------------------
 
-def step(pos, mom, k, sched, n, om, nbar, want=False, drift32=False, fixed_box=False):
+def step(pos, mom, k, sched, n, om, nbar, want=False, drift32=False, fixed_box=False,
+         assign="cic"):
     """Advance FP64 state (pos, mom) by step k.  Returns (pos, mom, info).
 
     drift32=True takes the first half drift in the CUDA kernel's documented
     float32 arithmetic (drift_fp32) so that both sides deposit the same float
     positions; everything after it stays FP64.  fixed_box=True solves on the
-    whole periodic box at every step (the run without shrinking)."""
+    whole periodic box at every step (the run without shrinking).  assign:
+    "cic" or "tsc" (density assignment and force interpolation alike)."""
     a0, a1 = sched["a"][k], sched["a"][k + 1]
     dtau, ah = sched["dtau"][k], sched["a_half"][k]
     R0 = sched["R"][k]
-    lo, s, periodic = (0, n, True) if fixed_box else active_cube(R0, n)
+    tsc = assign == "tsc"
+    lo, s, periodic = (0, n, True) if fixed_box else active_cube(R0, n, 2 if tsc else 1)
     if drift32:
         pos = drift_fp32(np.asarray(pos, np.float32), np.asarray(mom, np.float32),
                          dtau / (2 * a0), n, periodic).astype(np.float64)
     else:
         pos = drift(pos, mom, dtau / (2 * a0), n, periodic)
     pos_half = pos
-    rho, esc = deposit(pos, n, lo, s, periodic)
-    f, phi = solve_step_potential(rho, n, lo, s, periodic, nbar, R0, ah, om)
-    F, _ = gather_force(phi, pos, n, lo, s, periodic)
+    rho, esc = (deposit_tsc if tsc else deposit)(pos, n, lo, s, periodic)
+    f, phi = solve_step_potential(rho, n, lo, s, periodic, nbar, R0, ah, om, assign)
+    F, _ = (gather_force_tsc if tsc else gather_force)(phi, pos, n, lo, s, periodic)
     mom = mom - ah * dtau * F
     pos = drift(pos, mom, dtau / (2 * a1), n, periodic)
     info = dict(lo=lo, s=s, periodic=periodic, escaped=esc)
@@ -390,7 +484,7 @@ def step(pos, mom, k, sched, n, om, nbar, want=False, drift32=False, fixed_box=F
     return pos, mom, info
 
 
-def run(pos, mom, ids, sched, n, om, nbar, steps=None, record_only=False):
+def run(pos, mom, ids, sched, n, om, nbar, steps=None, record_only=False, assign="cic"):
     """Whole run with shrinking.  Returns survivors, lightcone, per-step n_active.
 
     record_only=True is the run without shrinking that the paper compares
@@ -409,7 +503,8 @@ def run(pos, mom, ids, sched, n, om, nbar, steps=None, record_only=False):
     nsteps = len(sched["dtau"]) if steps is None else steps
     for k in range(nsteps):
         n_active.append(len(pos))
-        pos, mom, _ = step(pos, mom, k, sched, n, om, nbar, fixed_box=record_only)
+        pos, mom, _ = step(pos, mom, k, sched, n, om, nbar, fixed_box=record_only,
+                           assign=assign)
         R1 = sched["R"][k + 1]
         if is_open(R1, n):
             keep = keep_mask(pos, R1, n)

@@ -463,3 +463,71 @@ def test_drift_fp32_exact_cases_and_wrap():
     z = pm.drift_fp32(np.array([[1.0, 1.0, 1.0]], np.float32),
                        np.array([[2.0 ** -24, 0, 0]], np.float32), 1.0, n, False)
     assert z[0, 0] == np.float32(1.0)
+
+
+# ---------------------------------------------------------------- TSC variant
+
+def test_tsc_weights_are_exact_and_sum_to_one():
+    """Q16 TSC weights from exact rational arithmetic on the float position:
+    q = floor(2^16 u) - 2^16 i, outer nodes floor((2^16 - q)^2 / 2^17) and
+    floor(q^2 / 2^17), the centre the remainder; within 3 * 2^-16 of the
+    kernel 3/4 - d^2 at the exact offset d = u - (i + 1/2)."""
+    rng = np.random.default_rng(3)
+    pos = rng.uniform(0, 16, (200, 3)).astype(np.float32)
+    i, w = pm.tsc_index(pos)
+    assert np.all(w.sum(axis=-1) == 2**16)
+    for p, ii, ww in zip(pos[:50], i[:50], w[:50]):
+        for ax in range(3):
+            u = Fraction(float(p[ax]))
+            c = math.floor(u)
+            q = math.floor(u * 2**16) - c * 2**16
+            d = u - c - Fraction(1, 2)
+            wm = math.floor(Fraction((2**16 - q) ** 2, 2**17))
+            wp = math.floor(Fraction(q * q, 2**17))
+            assert ii[ax] == c and ww[ax, 0] == wm and ww[ax, 2] == wp
+            assert abs(ww[ax, 1] / 2**16 - float(Fraction(3, 4) - d * d)) <= 3 * 2.0**-16
+
+
+def test_tsc_deposit_conserves_mass_and_a_lattice_is_uniform():
+    n = 8
+    pos, _, _ = ics.random_particles(500, n, seed=4)
+    rho, esc = pm.deposit_tsc(pos, n, 0, n, True)
+    assert esc == 0 and int(rho.astype(object).sum()) == 500 * 2**48
+    g = np.arange(n) + 0.5
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    lat = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1).astype(np.float32)
+    rho, _ = pm.deposit_tsc(lat, n, 0, n, True)
+    assert np.all(rho == 2**48)
+
+
+def test_tsc_background_partitions_the_keep_interval():
+    np.testing.assert_allclose(pm.tsc_integral([-2, -1.5, -0.5, 0, 0.5, 1.5, 2]),
+                               [0, 0, 1 / 6, 0.5, 5 / 6, 1, 1], rtol=0, atol=1e-15)
+    u = np.linspace(-1.6, 1.6, 3201)
+    c = pm.tsc_integral(u)
+    assert np.all(np.diff(c) >= 0) and np.max(np.abs(np.diff(c))) < 1e-3   # continuous
+    n = 64
+    for R in (2.0, 7.3, 15.5):
+        lo, s, _ = pm.active_cube(R, n, 2)
+        w = pm.background_weights(R, n, lo, s, False, "tsc")
+        assert abs(w.sum() - 2 * R) < 1e-12
+
+
+def test_tsc_forces_conserve_momentum_and_follow_the_inverse_square():
+    n = 16
+    pos, _, _ = ics.random_particles(300, n, seed=9)
+    rho, _ = pm.deposit_tsc(pos, n, 0, n, True)
+    f = pm.source_S(0.5, OM) * (rho / (300 * 2**48 / n**3) - 1.0)
+    F, _ = pm.gather_force_tsc(pm.solve_periodic(f), pos, n, 0, n, True)
+    assert np.abs(F.sum(axis=0)).max() < 1e-11 * np.abs(F).sum()
+    n = 64
+    S = pm.source_S(0.5, OM)
+    for d in (8.0, 12.0):
+        p2 = np.array([[32.0 - d / 2 + 0.5, 32.5, 32.5], [32.0 + d / 2 + 0.5, 32.5, 32.5]],
+                      np.float32)
+        rho, _ = pm.deposit_tsc(p2, n, 0, n, False)
+        f = S * rho.astype(np.float64) / 2**48
+        phi = pm.solve_open(f, pm.open_ghost_potential(f, S, 0, n))
+        F, _ = pm.gather_force_tsc(phi, p2, n, 0, n, False)
+        ratio = -F[0, 0] / (S / (4 * math.pi * d * d))
+        assert abs(ratio - 1) < 2.5 / d**2, (d, ratio)
