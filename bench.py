@@ -138,20 +138,21 @@ def _plain_floor(pos, mom, ids, cfg):
 
 
 def _variant(pos, mom, ids, cfg, K, rtol, precision, guess="warm", net=None,
-             gravity="poisson", bc="paper", shrink=True):
+             gravity="poisson", bc="paper", shrink=True, assignment="cic"):
     """The same K steps in another solver configuration, device-timed."""
     import torch
     from paper_1709_04703_gb300 import _lib as L
     from paper_1709_04703_gb300.sim import Sim
     sim = Sim(pos, mom, ids, cfg["n"], cfg["box"], cfg["a_init"], cfg["a_final"],
               cfg["steps"], rtol=rtol, precision=precision, max_vcycles=100, guess=guess,
-              gravity=gravity, bc=bc, shrink=shrink)
+              gravity=gravity, bc=bc, shrink=shrink, assignment=assignment)
     if net is not None:
         sim.set_guess(net)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     ev0.record(sim.stream)
-    out = {"precision": precision, "guess": guess, "rtol": rtol, "gravity": gravity}
+    out = {"precision": precision, "guess": guess, "rtol": rtol, "gravity": gravity,
+           "assignment": assignment}
     if not shrink:
         out["box"] = "fixed periodic (no shrinking)"
     try:
@@ -474,6 +475,8 @@ def run_ours(args):
         # ... and with the paper's own explicit (ADE) sweeps instead of solves
         compare["diffusion_ade"] = _variant(pos, mom, ids, cfg, K, rtol, "mixed",
                                             gravity="diffusion_ade")
+        # TSC density assignment and force interpolation instead of CIC
+        compare["tsc"] = _variant(pos, mom, ids, cfg, K, rtol, "mixed", assignment="tsc")
         # the same steps in the fixed periodic box (every particle, every step)
         compare["no_shrink"] = _variant(pos, mom, ids, cfg, K, rtol, "mixed", bc="periodic",
                                         shrink=False)

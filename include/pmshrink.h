@@ -54,6 +54,7 @@ enum { PM_GRAVITY_POISSON = 0, PM_GRAVITY_DIFFUSION = 1,
        PM_GRAVITY_DIFFUSION_ADE = 2 };                                 /* pm_config.gravity */
 enum { PM_BC_PAPER = 0, PM_BC_OPEN = 1, PM_BC_PERIODIC = 2 };  /* pm_config.bc */
 enum { PM_SHRINK_OFF = 0, PM_SHRINK_ON = 1, PM_SHRINK_RECORD = 2 };  /* pm_config.shrink */
+enum { PM_ASSIGN_CIC = 0, PM_ASSIGN_TSC = 1 };                  /* pm_config.assignment */
 
 typedef struct {
   int32_t n_mesh;        /* cells per side, of the form 2^j or 3*2^j, 4..1024 */
@@ -99,6 +100,10 @@ typedef struct {
                             explicit scheme (see pm_step) */
   double c_eff_factor;   /* diffusion only: c_eff = factor * cell (Mpc/h) * c,
                             0.019 in Sec. 3.1.1 */
+  int32_t assignment;    /* PM_ASSIGN_CIC or PM_ASSIGN_TSC (Sec. 2.4 footnote:
+                            the same scheme for the density and the force);
+                            TSC needs PM_GRAVITY_POISSON and widens the open
+                            cube by one cell (half-width ceil(R) + 2) */
 } pm_config;
 
 /* Fill *cfg with defaults: 32^3 mesh and particles, 250 Mpc/h, Om=0.3,
@@ -215,6 +220,17 @@ pm_status pm_deposit(float* pos4_dev, const float* mom4_dev, int64_t n,
                      float drift_coef, int32_t n_mesh, int32_t lo, int32_t side,
                      int32_t periodic, int64_t* rho_dev, int64_t* escaped_out,
                      void* stream);
+
+/* The same deposit with the TSC weights (Sec. 2.4 footnote): per axis the
+ * cell i = floor(u) and q = floor(u 2^16) - i 2^16 give nodes i-1, i, i+1
+ * the weights (2^16 - q)^2 >> 17, the remainder, q^2 >> 17 (exactly 2^16 in
+ * total); their products are added as int64.  Open: a particle with a node
+ * outside [lo, lo+side) deposits nothing and is counted as escaped.
+ * Arguments, drift and synchronisation as pm_deposit. */
+pm_status pm_deposit_tsc(float* pos4_dev, const float* mom4_dev, int64_t n,
+                         float drift_coef, int32_t n_mesh, int32_t lo, int32_t side,
+                         int32_t periodic, int64_t* rho_dev, int64_t* escaped_out,
+                         void* stream);
 
 typedef struct {
   int32_t step;          /* steps completed */

@@ -16,6 +16,7 @@ PM_GUESS_WARM, PM_GUESS_ZERO, PM_GUESS_LEARNED = 0, 1, 2
 PM_GRAVITY_POISSON, PM_GRAVITY_DIFFUSION, PM_GRAVITY_DIFFUSION_ADE = 0, 1, 2
 PM_BC_PAPER, PM_BC_OPEN, PM_BC_PERIODIC = 0, 1, 2
 PM_SHRINK_OFF, PM_SHRINK_ON, PM_SHRINK_RECORD = 0, 1, 2
+PM_ASSIGN_CIC, PM_ASSIGN_TSC = 0, 1
 PM_SHRINK_STATIC_MAX_PARTICLES = 1 << 22
 
 STATUS_NAMES = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ECUDA",
@@ -24,7 +25,7 @@ STATUS_NAMES = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ECUDA",
 # every entry point declared in include/pmshrink.h
 EXPORTED = [
     "pm_config_default", "pm_init", "pm_step", "pm_shrink", "pm_potential",
-    "pm_power_spectrum", "pm_power_spectrum_jing", "pm_deposit", "pm_stats", "pm_schedule",
+    "pm_power_spectrum", "pm_power_spectrum_jing", "pm_deposit", "pm_deposit_tsc", "pm_stats", "pm_schedule",
     "pm_get_particles", "pm_set_particles", "pm_get_lightcone", "pm_get_forces",
     "pm_get_potential", "pm_profile", "pm_profile_read", "pm_launch_count", "pm_last_error",
     "pm_destroy", "pm_shrink_static", "pm_shrink_static_error",
@@ -46,6 +47,7 @@ class PmConfig(C.Structure):
         ("max_vcycles", C.c_int32), ("precision", C.c_int32), ("guess", C.c_int32),
         ("bc", C.c_int32), ("shrink", C.c_int32), ("buffer_cells", C.c_double),
         ("store_forces", C.c_int32), ("gravity", C.c_int32), ("c_eff_factor", C.c_double),
+        ("assignment", C.c_int32),
     ]
 
 
@@ -91,6 +93,7 @@ def load():
         "pm_power_spectrum_jing": (I32, [P, I64, D, I32, I32, I32, I32, I32, D, P, P, P, P, P,
                                          P]),
         "pm_deposit": (I32, [P, P, I64, F, I32, I32, I32, I32, P, C.POINTER(I64), P]),
+        "pm_deposit_tsc": (I32, [P, P, I64, F, I32, I32, I32, I32, P, C.POINTER(I64), P]),
         "pm_stats": (I32, [P, C.POINTER(PmStats)]),
         "pm_schedule": (I32, [P, P, P, P, P]),
         "pm_get_particles": (I32, [P, P, P, I32, C.POINTER(I64)]),

@@ -259,7 +259,8 @@ void geometry(const pm_ctx* c, double R, int* lo, int* s, int* periodic) {
   if (!is_open(c, R)) { *lo = 0; *s = n; *periodic = 1; return; }
   *periodic = 0;
   if (R > 0.5 * n - 1.0) { *lo = 0; *s = n; return; }
-  int m = (int)std::ceil(R) + 1;
+  // the assignment reaches one cell (CIC) or two (TSC) beyond the keep cube
+  int m = (int)std::ceil(R) + (c->cfg.assignment == PM_ASSIGN_TSC ? 2 : 1);
   int side = std::min(mg_round_up(2 * m), n);
   *s = side;
   *lo = n / 2 - side / 2;
@@ -285,15 +286,27 @@ static double tent_integral(double u) {
   return 1.0;
 }
 
+// Integral of the TSC kernel (3/4 - t^2 on |t| <= 1/2, (3/2 - |t|)^2 / 2 on
+// 1/2 <= |t| <= 3/2) over t < u.
+static double tsc_integral(double u) {
+  if (u <= -1.5) return 0.0;
+  if (u <= -0.5) return (1.5 + u) * (1.5 + u) * (1.5 + u) / 6.0;
+  if (u <= 0.5) return 1.0 / 6.0 + 0.75 * (u + 0.5) - (u * u * u + 0.125) / 3.0;
+  if (u <= 1.5) return 1.0 - (1.5 - u) * (1.5 - u) * (1.5 - u) / 6.0;
+  return 1.0;
+}
+
 pm_status set_cube(pm_ctx* ctx, int lo, int s, int periodic, double R) {
   bool same = ctx->cube_valid && lo == ctx->lo && s == ctx->s && periodic == ctx->periodic;
   ctx->lo = lo;
   ctx->s = s;
   ctx->periodic = periodic;
   ctx->cube_valid = true;
-  // mean-density term of delta: per axis the CIC image of the keep interval
-  // [c - R, c + R], w_g = T(c + R - x_g) - T(c - R - x_g) at x_g = g + 1/2
-  // (ones when periodic), and its moments about c (separable sums)
+  // mean-density term of delta: per axis the image of the keep interval
+  // [c - R, c + R] under the assignment kernel (CIC tent or TSC),
+  // w_g = T(c + R - x_g) - T(c - R - x_g) at x_g = g + 1/2 with T the
+  // kernel's integral (ones when periodic), and its moments about c
+  // (separable sums)
   const int n = ctx->n;
   double* h = (double*)ctx->h_bg.data();
   df* hw = (df*)(ctx->h_bg.data() + BGW_OFF);
@@ -301,7 +314,10 @@ pm_status set_cube(pm_ctx* ctx, int lo, int s, int periodic, double R) {
   double W0 = 0.0, W1 = 0.0, W2 = 0.0;
   for (int g = 0; g < n; ++g) {
     const double x = g + 0.5;
-    const double w = periodic ? 1.0 : tent_integral((c + R) - x) - tent_integral((c - R) - x);
+    const bool tsc = ctx->cfg.assignment == PM_ASSIGN_TSC;
+    const double w = periodic ? 1.0
+                     : tsc    ? tsc_integral((c + R) - x) - tsc_integral((c - R) - x)
+                              : tent_integral((c + R) - x) - tent_integral((c - R) - x);
     hw[g].hi = (float)w;
     hw[g].lo = (float)(w - (double)hw[g].hi);
     if (g >= lo && g < lo + s) {
@@ -771,6 +787,7 @@ void pm_config_default(pm_config* c) {
   c->store_forces = 0;
   c->gravity = PM_GRAVITY_POISSON;
   c->c_eff_factor = 0.019;
+  c->assignment = PM_ASSIGN_CIC;
 }
 
 pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
@@ -798,6 +815,9 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
     return fail(nullptr, PM_EINVAL, "pm_init: unknown guess");
   if (cfg->shrink < PM_SHRINK_OFF || cfg->shrink > PM_SHRINK_RECORD)
     return fail(nullptr, PM_EINVAL, "pm_init: unknown shrink mode");
+  if (cfg->assignment != PM_ASSIGN_CIC &&
+      (cfg->assignment != PM_ASSIGN_TSC || cfg->gravity != PM_GRAVITY_POISSON))
+    return fail(nullptr, PM_EINVAL, "pm_init: assignment is CIC, or TSC with Poisson gravity");
   if (cfg->gravity != PM_GRAVITY_POISSON &&
       ((cfg->gravity != PM_GRAVITY_DIFFUSION && cfg->gravity != PM_GRAVITY_DIFFUSION_ADE) ||
        !(cfg->c_eff_factor > 0) || cfg->precision != PM_MIXED ||
@@ -984,9 +1004,14 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
     // 1-2. half drift + CIC deposit: read x, p, write x (48 B/particle); the
     // count grid is read and written once (16 B/cell)
     int e = prof_begin(ctx);
-    launch_drift_deposit(ctx->st, std::max(1, std::min(gkd_blocks(N) * 4, 152 * 16)), ctx->pos,
-                         ctx->mom, N, (float)(ctx->dtau[k] / (2.0 * ctx->a[k])), true, n, lo, s,
-                         per, ctx->rho, ctx->d_cnt + 1);
+    if (ctx->cfg.assignment == PM_ASSIGN_TSC)
+      launch_drift_deposit_tsc(ctx->st, N, ctx->pos, ctx->mom,
+                               (float)(ctx->dtau[k] / (2.0 * ctx->a[k])), true, n, lo, s, per,
+                               ctx->rho, ctx->d_cnt + 1);
+    else
+      launch_drift_deposit(ctx->st, std::max(1, std::min(gkd_blocks(N) * 4, 152 * 16)),
+                           ctx->pos, ctx->mom, N, (float)(ctx->dtau[k] / (2.0 * ctx->a[k])),
+                           true, n, lo, s, per, ctx->rho, ctx->d_cnt + 1);
     prof_end(ctx, PM_PROF_DEPOSIT, e, 48.0 * N + 16.0 * cells);
     // 3. source, boundary values, solve
     const double S = 1.5 * ctx->cfg.omega_m / ctx->a_half[k];
@@ -1073,11 +1098,17 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
     e = prof_begin(ctx);
     // gradient field: read Phi hi + lo, write G (24 B/cell)
     launch_grad(ctx->st, ctx->phi_h[ctx->cur], ctx->phi_l[ctx->cur], n, lo, s, per, ctx->grad);
-    launch_gather_kick_drift(ctx->st, ctx->pos, ctx->mom, N, ctx->phi_h[ctx->cur],
-                             ctx->phi_l[ctx->cur], ctx->grad, n, lo, s,
-                             per, (float)(ctx->a_half[k] * ctx->dtau[k]),
-                             (float)(ctx->dtau[k] / (2.0 * ctx->a[k + 1])), do_flag, klo, khi,
-                             ctx->flags, ctx->block_keep, ctx->forces, ctx->d_cnt + 1);
+    if (ctx->cfg.assignment == PM_ASSIGN_TSC)
+      launch_gather_tsc(ctx->st, ctx->pos, ctx->mom, N, ctx->grad, n, lo, s, per,
+                        (float)(ctx->a_half[k] * ctx->dtau[k]),
+                        (float)(ctx->dtau[k] / (2.0 * ctx->a[k + 1])), do_flag, klo, khi,
+                        ctx->flags, ctx->block_keep, ctx->forces, ctx->d_cnt + 1);
+    else
+      launch_gather_kick_drift(ctx->st, ctx->pos, ctx->mom, N, ctx->phi_h[ctx->cur],
+                               ctx->phi_l[ctx->cur], ctx->grad, n, lo, s,
+                               per, (float)(ctx->a_half[k] * ctx->dtau[k]),
+                               (float)(ctx->dtau[k] / (2.0 * ctx->a[k + 1])), do_flag, klo,
+                               khi, ctx->flags, ctx->block_keep, ctx->forces, ctx->d_cnt + 1);
     // gather: read x, p, write x, p (64 B/particle, + 1 B flag), read G once
     // (16 B/cell)
     prof_end(ctx, PM_PROF_GATHER, e, (do_flag ? 65.0 : 64.0) * N + (24.0 + 16.0) * cells);
@@ -1195,21 +1226,29 @@ pm_status pm_potential(pm_ctx* ctx, const double* delta_dev, double a, int32_t b
   return PM_OK;
 }
 
-pm_status pm_deposit(float* pos4_dev, const float* mom4_dev, int64_t n, float drift_coef,
-                     int32_t n_mesh, int32_t lo, int32_t side, int32_t periodic,
-                     int64_t* rho_dev, int64_t* escaped_out, void* stream) {
+namespace {
+pm_status deposit_any(bool tsc, const char* who, float* pos4_dev, const float* mom4_dev,
+                      int64_t n, float drift_coef, int32_t n_mesh, int32_t lo, int32_t side,
+                      int32_t periodic, int64_t* rho_dev, int64_t* escaped_out,
+                      void* stream) {
   pm_ctx* ctx = nullptr;
   if ((!pos4_dev && n > 0) || !rho_dev || n < 0 || n_mesh < 1 || side < 1 || lo < 0 || lo + side > n_mesh)
-    return fail(nullptr, PM_EINVAL, "pm_deposit: bad argument");
+    return fail(nullptr, PM_EINVAL, std::string(who) + ": bad argument");
   if (periodic && (lo != 0 || side != n_mesh))
-    return fail(nullptr, PM_EINVAL, "pm_deposit: periodic needs the whole mesh");
+    return fail(nullptr, PM_EINVAL, std::string(who) + ": periodic needs the whole mesh");
   cudaStream_t st = (cudaStream_t)stream;
   unsigned long long* esc = nullptr;
   CK(cudaMallocAsync((void**)&esc, sizeof(unsigned long long), st));
   CK(cudaMemsetAsync(esc, 0, sizeof(unsigned long long), st));
-  launch_drift_deposit(st, std::max(1, std::min(gkd_blocks(n) * 4, 152 * 16)), (float4*)pos4_dev,
-                       (const float4*)mom4_dev, n, drift_coef, mom4_dev != nullptr, n_mesh, lo,
-                       side, periodic, (unsigned long long*)rho_dev, esc);
+  if (tsc)
+    launch_drift_deposit_tsc(st, n, (float4*)pos4_dev, (const float4*)mom4_dev, drift_coef,
+                             mom4_dev != nullptr, n_mesh, lo, side, periodic,
+                             (unsigned long long*)rho_dev, esc);
+  else
+    launch_drift_deposit(st, std::max(1, std::min(gkd_blocks(n) * 4, 152 * 16)),
+                         (float4*)pos4_dev, (const float4*)mom4_dev, n, drift_coef,
+                         mom4_dev != nullptr, n_mesh, lo, side, periodic,
+                         (unsigned long long*)rho_dev, esc);
   CKL();
   if (escaped_out) {
     unsigned long long h = 0;
@@ -1219,6 +1258,21 @@ pm_status pm_deposit(float* pos4_dev, const float* mom4_dev, int64_t n, float dr
   }
   CK(cudaFreeAsync(esc, st));
   return PM_OK;
+}
+}  // namespace
+
+pm_status pm_deposit(float* pos4_dev, const float* mom4_dev, int64_t n, float drift_coef,
+                     int32_t n_mesh, int32_t lo, int32_t side, int32_t periodic,
+                     int64_t* rho_dev, int64_t* escaped_out, void* stream) {
+  return deposit_any(false, "pm_deposit", pos4_dev, mom4_dev, n, drift_coef, n_mesh, lo, side,
+                     periodic, rho_dev, escaped_out, stream);
+}
+
+pm_status pm_deposit_tsc(float* pos4_dev, const float* mom4_dev, int64_t n, float drift_coef,
+                         int32_t n_mesh, int32_t lo, int32_t side, int32_t periodic,
+                         int64_t* rho_dev, int64_t* escaped_out, void* stream) {
+  return deposit_any(true, "pm_deposit_tsc", pos4_dev, mom4_dev, n, drift_coef, n_mesh, lo,
+                     side, periodic, rho_dev, escaped_out, stream);
 }
 
 namespace {
@@ -1860,6 +1914,8 @@ pm_status pm_batch_init(int32_t n_real, const pm_config* cfgs, const float* cons
       return bfail(nullptr, PM_EINVAL, "pm_batch_init: the learned guess runs per context");
     if (cfgs[r].gravity != PM_GRAVITY_POISSON)
       return bfail(nullptr, PM_EINVAL, "pm_batch_init: batches solve Poisson's equation");
+    if (cfgs[r].assignment != PM_ASSIGN_CIC)
+      return bfail(nullptr, PM_EINVAL, "pm_batch_init: batches assign by CIC");
     if (cfgs[r].shrink == PM_SHRINK_RECORD)
       return bfail(nullptr, PM_EINVAL, "pm_batch_init: the fixed-box lightcone record runs "
                                        "per context");

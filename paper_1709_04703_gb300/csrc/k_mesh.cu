@@ -2,6 +2,7 @@
 // deposit (Sec. 2.2 first DKD line; Sec. 2.4 footnote, CIC), the Poisson
 // source on the active cube (Sec. 2.1, Eq. 3) with its boundary multipoles,
 // and the open-boundary ghost layer (Table 1: open boundaries).
+#include <algorithm>
 #include <cooperative_groups.h>
 
 #include "pm_kernels.cuh"
@@ -128,6 +129,105 @@ void launch_drift_deposit(cudaStream_t st, int grid, float4* pos, const float4* 
   else
     k_drift_deposit<false><<<grid, 256, 0, st>>>(pos, mom, N, c0, n, lo, s, periodic, rho,
                                                  escaped);
+  note_launch();
+}
+
+// ---------------------------------------------------------------------------
+// TSC variant of the drift + deposit (Sec. 2.4 footnote: CIC or TSC).  Per
+// axis the particle's cell i = floor(u) and its position in the cell in
+// Q16, q = floor(2^16 u) - 2^16 i, give the weights of nodes i-1, i, i+1:
+// (2^16 - q)^2 >> 17, the rest, q^2 >> 17 (the kernel (1/2 -+ d)^2 / 2 and
+// 3/4 - d^2 at d = u - i - 1/2), summing to exactly 2^16; the 27 products
+// (<= 2^48, 2^48 in total) go to int64 cell counts.  Periodic: nodes wrap;
+// open: a particle with a node outside the cube deposits nothing (escaped).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void tsc_axis(float u, int& i, unsigned int w[3]) {
+  const int iq = __float2int_rd(__fmul_rn(u, 65536.0f));
+  i = iq >> 16;
+  const unsigned long long q = (unsigned long long)(iq & 0xffff);
+  const unsigned long long a = 65536ull - q;
+  w[0] = (unsigned int)((a * a) >> 17);
+  w[2] = (unsigned int)((q * q) >> 17);
+  w[1] = 65536u - w[0] - w[2];
+}
+
+template <bool DRIFT>
+__global__ void __launch_bounds__(256) k_drift_deposit_tsc(
+    float4* __restrict__ pos, const float4* __restrict__ mom, long long N, float c0, int n,
+    int lo, int s, int periodic, unsigned long long* __restrict__ rho,
+    unsigned long long* __restrict__ escaped) {
+  const float fn = (float)n;
+  unsigned int esc_local = 0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+       p += (long long)gridDim.x * blockDim.x) {
+    float4 x = pos[p];
+    if (DRIFT) {
+      const float4 v = mom[p];
+      x.x = __fadd_rn(x.x, __fmul_rn(v.x, c0));
+      x.y = __fadd_rn(x.y, __fmul_rn(v.y, c0));
+      x.z = __fadd_rn(x.z, __fmul_rn(v.z, c0));
+      if (periodic) {
+        if (x.x < 0.f) x.x = __fadd_rn(x.x, fn);
+        if (x.x >= fn) x.x = __fsub_rn(x.x, fn);
+        if (x.y < 0.f) x.y = __fadd_rn(x.y, fn);
+        if (x.y >= fn) x.y = __fsub_rn(x.y, fn);
+        if (x.z < 0.f) x.z = __fadd_rn(x.z, fn);
+        if (x.z >= fn) x.z = __fsub_rn(x.z, fn);
+      }
+      pos[p] = x;
+    }
+    int i3[3];
+    unsigned int w[3][3];
+    tsc_axis(x.x, i3[0], w[0]);
+    tsc_axis(x.y, i3[1], w[1]);
+    tsc_axis(x.z, i3[2], w[2]);
+    bool ok = true;
+    int nd[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (periodic) {
+        ok = ok && i3[a] >= 0 && i3[a] <= n - 1;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const int v = i3[a] - 1 + c;
+          nd[a][c] = v < 0 ? v + n : (v >= n ? v - n : v);
+        }
+      } else {
+        ok = ok && i3[a] - 1 >= lo && i3[a] + 1 <= lo + s - 1;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) nd[a][c] = i3[a] - 1 + c;
+      }
+    }
+    if (!ok) {
+      ++esc_local;
+      continue;
+    }
+#pragma unroll
+    for (int cz = 0; cz < 3; ++cz)
+#pragma unroll
+      for (int cy = 0; cy < 3; ++cy) {
+        const unsigned long long wyz = (unsigned long long)w[1][cy] * w[2][cz];
+        const long long row = ((long long)nd[2][cz] * n + nd[1][cy]) * n;
+#pragma unroll
+        for (int cx = 0; cx < 3; ++cx) atomicAdd(rho + row + nd[0][cx], wyz * w[0][cx]);
+      }
+  }
+  unsigned int w = esc_local;
+  for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+  if ((threadIdx.x & 31) == 0 && w) atomicAdd(escaped, (unsigned long long)w);
+}
+
+void launch_drift_deposit_tsc(cudaStream_t st, long long N, float4* pos, const float4* mom,
+                              float c0, bool drift, int n, int lo, int s, int periodic,
+                              unsigned long long* rho, unsigned long long* escaped) {
+  if (N <= 0) return;
+  const int g = (int)std::min<long long>((N + 255) / 256, 152 * 16);
+  if (drift)
+    k_drift_deposit_tsc<true><<<g, 256, 0, st>>>(pos, mom, N, c0, n, lo, s, periodic, rho,
+                                                 escaped);
+  else
+    k_drift_deposit_tsc<false><<<g, 256, 0, st>>>(pos, mom, N, c0, n, lo, s, periodic, rho,
+                                                  escaped);
   note_launch();
 }
 

@@ -261,6 +261,138 @@ __global__ void __launch_bounds__(256) k_grad(const float* __restrict__ ph,
                      gdiff(ph[zp], ph[zm], pl[zp], pl[zm]), 0.0f);
 }
 
+// ---------------------------------------------------------------------------
+// TSC variant of the gather + kick + drift (+ keep flags): the node
+// differences of G at the 27 TSC nodes with the deposit's Q16 weights
+// (tsc_axis) scaled to float; same chunking as the CIC gather, so the keep
+// counts feed the same scan.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void tsc_axis_f(float u, int& i, float w[3]) {
+  const int iq = __float2int_rd(__fmul_rn(u, 65536.0f));
+  i = iq >> 16;
+  const unsigned long long q = (unsigned long long)(iq & 0xffff);
+  const unsigned long long a = 65536ull - q;
+  const unsigned int w0 = (unsigned int)((a * a) >> 17), w2 = (unsigned int)((q * q) >> 17);
+  const float sc = 1.0f / 65536.0f;
+  w[0] = (float)w0 * sc;
+  w[1] = (float)(65536u - w0 - w2) * sc;
+  w[2] = (float)w2 * sc;
+}
+
+__global__ void __launch_bounds__(KT) k_gather_tsc(
+    float4* __restrict__ pos, float4* __restrict__ mom, long long N,
+    const float4* __restrict__ G, int n, int lo, int s, int periodic, float kick, float c2,
+    int do_flag, float klo, float khi, unsigned char* __restrict__ flags,
+    unsigned int* __restrict__ block_keep, float4* __restrict__ forces,
+    unsigned long long* __restrict__ escaped) {
+  const int P = n + 2;
+  const float fn = (float)n;
+  const long long base = (long long)blockIdx.x * KCHUNK;
+  unsigned int keep_count = 0, esc = 0;
+#pragma unroll 1
+  for (int it = 0; it < KITEMS; ++it) {
+    const long long p = base + it * KT + threadIdx.x;
+    if (p >= N) break;
+    float4 x = pos[p];
+    float4 v = mom[p];
+    int i3[3];
+    float w[3][3];
+    tsc_axis_f(x.x, i3[0], w[0]);
+    tsc_axis_f(x.y, i3[1], w[1]);
+    tsc_axis_f(x.z, i3[2], w[2]);
+    bool ok = true;
+    int nd[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (periodic) {
+        ok = ok && i3[a] >= 0 && i3[a] <= n - 1;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const int q = i3[a] - 1 + c;
+          nd[a][c] = q < 0 ? q + n : (q >= n ? q - n : q);
+        }
+      } else {
+        ok = ok && i3[a] - 1 >= lo && i3[a] + 1 <= lo + s - 1;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) nd[a][c] = i3[a] - 1 + c;
+      }
+    }
+    float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+    if (ok) {
+#pragma unroll
+      for (int cz = 0; cz < 3; ++cz)
+#pragma unroll
+        for (int cy = 0; cy < 3; ++cy) {
+          const float wyz = __fmul_rn(w[1][cy], w[2][cz]);
+          const long long row = ((long long)(nd[2][cz] + 1) * P + (nd[1][cy] + 1)) * P + 1;
+#pragma unroll
+          for (int cx = 0; cx < 3; ++cx) {
+            const float4 g = __ldg(G + row + nd[0][cx]);
+            const float wt = __fmul_rn(wyz, w[0][cx]);
+            Fx = __fmaf_rn(wt, g.x, Fx);
+            Fy = __fmaf_rn(wt, g.y, Fy);
+            Fz = __fmaf_rn(wt, g.z, Fz);
+          }
+        }
+      Fx = __fmul_rn(Fx, 0.5f);
+      Fy = __fmul_rn(Fy, 0.5f);
+      Fz = __fmul_rn(Fz, 0.5f);
+    } else {
+      ++esc;
+    }
+    v.x = __fmaf_rn(-kick, Fx, v.x);
+    v.y = __fmaf_rn(-kick, Fy, v.y);
+    v.z = __fmaf_rn(-kick, Fz, v.z);
+    x.x = __fadd_rn(x.x, __fmul_rn(v.x, c2));
+    x.y = __fadd_rn(x.y, __fmul_rn(v.y, c2));
+    x.z = __fadd_rn(x.z, __fmul_rn(v.z, c2));
+    if (periodic) {
+      if (x.x < 0.f) x.x = __fadd_rn(x.x, fn);
+      if (x.x >= fn) x.x = __fsub_rn(x.x, fn);
+      if (x.y < 0.f) x.y = __fadd_rn(x.y, fn);
+      if (x.y >= fn) x.y = __fsub_rn(x.y, fn);
+      if (x.z < 0.f) x.z = __fadd_rn(x.z, fn);
+      if (x.z >= fn) x.z = __fsub_rn(x.z, fn);
+    }
+    pos[p] = x;
+    mom[p] = v;
+    if (forces) forces[p] = make_float4(Fx, Fy, Fz, 0.f);
+    if (do_flag) {
+      const bool keep = x.x >= klo && x.x <= khi && x.y >= klo && x.y <= khi &&
+                        x.z >= klo && x.z <= khi;
+      flags[p] = keep ? 1 : 0;
+      keep_count += keep ? 1u : 0u;
+    }
+  }
+  if (do_flag) {
+    __shared__ unsigned int sk[KT / 32];
+    unsigned int wsum = keep_count;
+    for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+    if ((threadIdx.x & 31) == 0) sk[threadIdx.x >> 5] = wsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned int t = 0;
+      for (int q = 0; q < KT / 32; ++q) t += sk[q];
+      block_keep[blockIdx.x] = t;
+    }
+  }
+  unsigned int we = esc;
+  for (int o = 16; o > 0; o >>= 1) we += __shfl_xor_sync(0xffffffffu, we, o);
+  if ((threadIdx.x & 31) == 0 && we) atomicAdd(escaped, (unsigned long long)we);
+}
+
+void launch_gather_tsc(cudaStream_t st, float4* pos, float4* mom, long long N,
+                       const float4* G, int n, int lo, int s, int periodic, float kick,
+                       float c2, int do_flag, float klo, float khi, unsigned char* flags,
+                       unsigned int* block_keep, float4* forces,
+                       unsigned long long* escaped) {
+  if (N <= 0) return;
+  k_gather_tsc<<<gkd_blocks(N), KT, 0, st>>>(pos, mom, N, G, n, lo, s, periodic, kick, c2,
+                                             do_flag, klo, khi, flags, block_keep, forces,
+                                             escaped);
+  note_launch();
+}
+
 int gkd_blocks(long long N) { return (int)((N + KCHUNK - 1) / KCHUNK); }
 
 void launch_gather_kick_drift(cudaStream_t st, float4* pos, float4* mom, long long N,

@@ -67,6 +67,14 @@ void launch_sum_phi(cudaStream_t st, Grid ph, Grid pl, double* partial, unsigned
                     double* out);
 
 // k_part.cu
+void launch_drift_deposit_tsc(cudaStream_t st, long long N, float4* pos, const float4* mom,
+                              float c0, bool drift, int n, int lo, int s, int periodic,
+                              unsigned long long* rho, unsigned long long* escaped);
+void launch_gather_tsc(cudaStream_t st, float4* pos, float4* mom, long long N,
+                       const float4* G, int n, int lo, int s, int periodic, float kick,
+                       float c2, int do_flag, float klo, float khi, unsigned char* flags,
+                       unsigned int* block_keep, float4* forces,
+                       unsigned long long* escaped);
 int gkd_blocks(long long N);
 // G: gradient field of k_grad (NULL: differences taken from Phi directly)
 void launch_gather_kick_drift(cudaStream_t st, float4* pos, float4* mom, long long N,

@@ -169,7 +169,7 @@ class Sim:
                  rtol=1e-7, precision="mixed", guess="warm", bc="paper",
                  shrink=True, buffer_cells=1.0, max_vcycles=50, store_forces=False,
                  omega_m=0.3, omega_l=0.7, host_init=False, gravity="poisson",
-                 c_eff_factor=0.019):
+                 c_eff_factor=0.019, assignment="cic"):
         lib = L.load()
         cfg = L.PmConfig()
         lib.pm_config_default(C.byref(cfg))
@@ -187,6 +187,7 @@ class Sim:
         cfg.store_forces = 1 if store_forces else 0
         cfg.gravity = _GRAVITY[gravity]
         cfg.c_eff_factor = float(c_eff_factor)
+        cfg.assignment = {"cic": L.PM_ASSIGN_CIC, "tsc": L.PM_ASSIGN_TSC}[assignment]
         self.cfg = cfg
         self.n_particles = int(len(pos))
         # the context runs on its own stream so that its V-cycle can be
@@ -368,15 +369,16 @@ def power_spectrum(pos4_dev, box, n_mesh, n_bins, subtract_shot=True):
 
 
 def deposit(pos4_dev, n_mesh, lo=0, side=None, periodic=True, mom4_dev=None,
-            drift_coef=0.0, rho=None):
-    """Fixed-point CIC deposit; returns (rho int64 cuda tensor [z,y,x], escaped).
-    With mom4_dev the positions are drifted in place first."""
+            drift_coef=0.0, rho=None, assignment="cic"):
+    """Fixed-point CIC (or TSC) deposit; returns (rho int64 cuda tensor
+    [z,y,x], escaped).  With mom4_dev the positions are drifted in place first."""
     lib = L.load()
     side = n_mesh if side is None else side
     if rho is None:
         rho = torch.zeros((n_mesh, n_mesh, n_mesh), dtype=torch.int64, device="cuda")
     esc = C.c_int64()
-    L.check(lib.pm_deposit(_ptr(pos4_dev), _ptr(mom4_dev), int(pos4_dev.shape[0]),
+    fn = lib.pm_deposit_tsc if assignment == "tsc" else lib.pm_deposit
+    L.check(fn(_ptr(pos4_dev), _ptr(mom4_dev), int(pos4_dev.shape[0]),
                            float(drift_coef), int(n_mesh), int(lo), int(side),
                            1 if periodic else 0, _ptr(rho), C.byref(esc), _stream()))
     return rho, esc.value
