@@ -122,6 +122,19 @@ def _new_sim(pos, mom, ids, cfg, rtol, precision, guess="warm"):
 
 STRICT_RTOL = 1e-7
 
+# ncu dram__bytes_read.sum + dram__bytes_write.sum over the algorithmic bytes
+# of the kernel class's launches at 256^3 on the current kernels
+TRAFFIC_RATIO = {
+    "smooth0": (290.7e6 / 335.5e6, "k_rbgs2 pre + post at 256^3, "
+                "profiles/rbgs2_pm256_level0.md"),
+    "defect": (328.2e6 / 335.5e6, "k_defect<0> at 256^3, "
+               "profiles/defect_gather_deposit_pm256.md"),
+    "deposit": (1162.3e6 / 1073.7e6, "k_drift_deposit at 256^3, "
+                "profiles/defect_gather_deposit_pm256.md"),
+    "gather": (1295.6e6 / 1342.2e6, "k_gather_kick_drift at 256^3, "
+               "profiles/defect_gather_deposit_pm256.md"),
+}
+
 
 def _plain_floor(pos, mom, ids, cfg):
     """Relative residual at which the plain FP32 path stalls on the first
@@ -530,6 +543,12 @@ def run_ours(args):
     dom = max(prof, key=lambda k: prof[k]["ms"])
     d = prof[dom]
     achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
+    # DRAM traffic per launch: the ncu ratio of DRAM to algorithmic bytes of
+    # the class's 256^3 launches (profiles/), times this run's algorithmic
+    # bytes per launch of the class
+    traffic = None
+    if dom in TRAFFIC_RATIO and d["groups"] > 0:
+        traffic = TRAFFIC_RATIO[dom][0] * d["bytes"] / d["groups"]
     kernels = {k: {"ms": round(v["ms"], 3), "share": round(v["ms"] / max(1e-9, sum(
         x["ms"] for x in prof.values())), 4), "GB/s": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1)
         if v["ms"] > 0 else None} for k, v in prof.items()}
@@ -549,7 +568,10 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (particles 537 MB, mesh 134 MB)"},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None},
+                     "frac": round(achieved / peak, 4),
+                     "traffic": round(traffic) if traffic is not None else None,
+                     "algorithmic_bytes_per_launch": round(d["bytes"] / max(1, d["groups"])),
+                     "traffic_source": TRAFFIC_RATIO[dom][1] if dom in TRAFFIC_RATIO else None},
         "kernels": kernels,
         "solver": vstats,
         "clocks": clk.summary(),
