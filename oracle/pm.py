@@ -28,7 +28,10 @@ Readings taken where the paper is silent (each also applies to the CUDA
 library, which implements them independently):
 * Domain shape: the implementation restricts loop bounds (Sec. 2.4), i.e. a
   cube, centred on the observer at the box centre c = n/2.  Keep half-width
-  R = chi(a)/cell + buffer (1 cell).  Keep iff max_d |x_d - c| <= R.
+  R = chi(a)/cell + buffer (1 cell).  Keep iff max_d |x_d - c| <= R.  The
+  sphere of Table 1 is the variant domain="sphere": keep iff |x - c| <= R,
+  solved on the same cube, its mean-density term the CIC image of the ball
+  (background_ball).
 * Boundary conditions: periodic until the lightcone reaches the box border
   (Sec. 3), read as R > n/2 - 1; afterwards open (Table 1) with Dirichlet
   values from a monopole + dipole + quadrupole expansion of the source about
@@ -167,10 +170,47 @@ def source_S(a, om):
     return 1.5 * om / a
 
 
-def delta_cube(rho, n, lo, s, nbar, R, periodic, assign="cic"):
+BALL_GL = 16  # Gauss-Legendre points per axis and quadrant of the ball image
+
+
+def background_ball(R, n, lo, s):
+    """Mean-density term for a spherical keep region: the CIC image of the
+    ball |x - c| <= R on the cells of [lo, lo+s)^3 (float64, [z,y,x]).
+    Per cell with centre p (a = p - c): the z integral of the tent over the
+    ball's chord is exact, T(h - a_z) - T(-h - a_z) with
+    h = sqrt(R^2 - X^2 - Y^2); the x-y integral of the tents runs over the
+    four quadrants of [-1, 1]^2 by BALL_GL-point Gauss-Legendre rules.
+    Cells with |a| + sqrt(3) <= R are 1, with |a| - sqrt(3) >= R are 0."""
+    c = n / 2
+    a1 = np.arange(lo, lo + s) + 0.5 - c
+    AZ, AY, AX = np.meshgrid(a1, a1, a1, indexing="ij")
+    r = np.sqrt(AX * AX + AY * AY + AZ * AZ)
+    W = np.where(r + math.sqrt(3.0) <= R, 1.0, 0.0)
+    shell = (r + math.sqrt(3.0) > R) & (r - math.sqrt(3.0) < R)
+    ax, ay, az = AX[shell], AY[shell], AZ[shell]
+    xg, wg = np.polynomial.legendre.leggauss(BALL_GL)
+    xi = 0.5 * (xg + 1.0)
+    om = 0.5 * wg * (1.0 - xi)          # rule on [0, 1] times the tent 1 - xi
+    tot = np.zeros(len(ax))
+    for qx in (-1.0, 1.0):
+        for qy in (-1.0, 1.0):
+            X = ax[:, None, None] + qx * xi[None, :, None]
+            Y = ay[:, None, None] + qy * xi[None, None, :]
+            h2 = R * R - X * X - Y * Y
+            h = np.sqrt(np.maximum(h2, 0.0))
+            Z = np.where(h2 > 0.0, tent_integral(h - az[:, None, None])
+                         - tent_integral(-h - az[:, None, None]), 0.0)
+            tot += np.einsum("cij,i,j->c", Z, om, om)
+    W[shell] = tot
+    return W
+
+
+def delta_cube(rho, n, lo, s, nbar, R, periodic, assign="cic", domain="cube"):
     """Density contrast on the active cube [z,y,x] (s^3, float64)."""
     sub = rho[lo:lo + s, lo:lo + s, lo:lo + s].astype(np.float64)
     d = sub / (MASS_UNIT * nbar)
+    if domain == "sphere" and not periodic:
+        return d - background_ball(R, n, lo, s)
     w = background_weights(R, n, lo, s, periodic, assign)
     return d - w[:, None, None] * w[None, :, None] * w[None, None, :]
 
@@ -285,11 +325,12 @@ def apply_laplacian_periodic(phi):
             - 6.0 * phi)
 
 
-def solve_step_potential(rho, n, lo, s, periodic, nbar, R, a_half, om, assign="cic"):
+def solve_step_potential(rho, n, lo, s, periodic, nbar, R, a_half, om, assign="cic",
+                         domain="cube"):
     """Source and potential of one step.  Returns (f_cube, phi) where phi is
     n^3 (periodic) or padded (s+2)^3 (open, ghosts included)."""
     S = source_S(a_half, om)
-    f = S * delta_cube(rho, n, lo, s, nbar, R, periodic, assign)
+    f = S * delta_cube(rho, n, lo, s, nbar, R, periodic, assign, domain)
     if periodic:
         return f, solve_periodic(f)
     return f, solve_open(f, open_ghost_potential(f, S, lo, n))
@@ -436,10 +477,14 @@ def drift_fp32(pos32, mom32, coef, n, periodic):
     return x.astype(np.float32)
 
 
-def keep_mask(pos, R, n):
-    """Keep iff max_d |x_d - c| <= R, compared in FP64 (Sec. 2.4)."""
-    d = np.abs(np.asarray(pos, dtype=np.float64) - n / 2)
-    return d.max(axis=1) <= R
+def keep_mask(pos, R, n, domain="cube"):
+    """Keep iff max_d |x_d - c| <= R (cube), or iff
+    ((x - c)^2 + (y - c)^2) + (z - c)^2 <= R^2 (sphere), in FP64 on the
+    position (Sec. 2.4 / Table 1)."""
+    d = np.asarray(pos, dtype=np.float64) - n / 2
+    if domain == "sphere":
+        return (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2] <= R * R
+    return np.abs(d).max(axis=1) <= R
 
 
 def shrink(arrays, keep):
@@ -454,14 +499,15 @@ def shrink(arrays, keep):
 # --------------------------------------------------------------------------
 
 def step(pos, mom, k, sched, n, om, nbar, want=False, drift32=False, fixed_box=False,
-         assign="cic"):
+         assign="cic", domain="cube"):
     """Advance FP64 state (pos, mom) by step k.  Returns (pos, mom, info).
 
     drift32=True takes the first half drift in the CUDA kernel's documented
     float32 arithmetic (drift_fp32) so that both sides deposit the same float
     positions; everything after it stays FP64.  fixed_box=True solves on the
     whole periodic box at every step (the run without shrinking).  assign:
-    "cic" or "tsc" (density assignment and force interpolation alike)."""
+    "cic" or "tsc" (density assignment and force interpolation alike).
+    domain: "cube" or "sphere" keep region (its mean-density term)."""
     a0, a1 = sched["a"][k], sched["a"][k + 1]
     dtau, ah = sched["dtau"][k], sched["a_half"][k]
     R0 = sched["R"][k]
@@ -474,7 +520,7 @@ def step(pos, mom, k, sched, n, om, nbar, want=False, drift32=False, fixed_box=F
         pos = drift(pos, mom, dtau / (2 * a0), n, periodic)
     pos_half = pos
     rho, esc = (deposit_tsc if tsc else deposit)(pos, n, lo, s, periodic)
-    f, phi = solve_step_potential(rho, n, lo, s, periodic, nbar, R0, ah, om, assign)
+    f, phi = solve_step_potential(rho, n, lo, s, periodic, nbar, R0, ah, om, assign, domain)
     F, _ = (gather_force_tsc if tsc else gather_force)(phi, pos, n, lo, s, periodic)
     mom = mom - ah * dtau * F
     pos = drift(pos, mom, dtau / (2 * a1), n, periodic)
@@ -484,7 +530,8 @@ def step(pos, mom, k, sched, n, om, nbar, want=False, drift32=False, fixed_box=F
     return pos, mom, info
 
 
-def run(pos, mom, ids, sched, n, om, nbar, steps=None, record_only=False, assign="cic"):
+def run(pos, mom, ids, sched, n, om, nbar, steps=None, record_only=False, assign="cic",
+        domain="cube"):
     """Whole run with shrinking.  Returns survivors, lightcone, per-step n_active.
 
     record_only=True is the run without shrinking that the paper compares
@@ -504,10 +551,10 @@ def run(pos, mom, ids, sched, n, om, nbar, steps=None, record_only=False, assign
     for k in range(nsteps):
         n_active.append(len(pos))
         pos, mom, _ = step(pos, mom, k, sched, n, om, nbar, fixed_box=record_only,
-                           assign=assign)
+                           assign=assign, domain=domain)
         R1 = sched["R"][k + 1]
         if is_open(R1, n):
-            keep = keep_mask(pos, R1, n)
+            keep = keep_mask(pos, R1, n, domain)
             if record_only:
                 new = ~keep & ~recorded
                 lp, lm, li = pos[new], mom[new], ids[new]

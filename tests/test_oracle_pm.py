@@ -531,3 +531,50 @@ def test_tsc_forces_conserve_momentum_and_follow_the_inverse_square():
         F, _ = pm.gather_force_tsc(phi, p2, n, 0, n, False)
         ratio = -F[0, 0] / (S / (4 * math.pi * d * d))
         assert abs(ratio - 1) < 2.5 / d**2, (d, ratio)
+
+
+# ---------------------------------------------------------------- spherical domain
+
+def test_sphere_keep_rule_is_exact():
+    rng = np.random.default_rng(13)
+    n, R = 32, 9.3
+    pos = (n / 2 + rng.uniform(-10, 10, (2000, 3))).astype(np.float32)
+    got = pm.keep_mask(pos, R, n, "sphere")
+    Rf = Fraction(R)
+    ref = [sum((Fraction(float(v)) - n // 2) ** 2 for v in p) <= Rf * Rf for p in pos]
+    assert list(got) == ref
+    assert 0 < got.sum() < len(pos)
+
+
+def test_ball_background_has_the_ball_volume_and_its_symmetry():
+    n = 32
+    for R, tol in ((3.2, 3e-4), (9.3, 5e-5), (14.0, 5e-5)):   # the rule's error ~ 1/R^2
+        lo, s, _ = pm.active_cube(R, n)
+        W = pm.background_ball(R, n, lo, s)
+        assert abs(W.sum() / (4 / 3 * math.pi * R**3) - 1) < tol, R
+        assert W.min() >= -1e-12 and W.max() <= 1 + 1e-12
+        np.testing.assert_allclose(W, W[::-1, ::-1, ::-1], rtol=0, atol=1e-12)
+        np.testing.assert_allclose(W, W.transpose(0, 2, 1), rtol=0, atol=1e-12)
+        # z is integrated in closed form, x and y by the rule, whose error per
+        # cell (the chord length has a square-root edge) is below 1e-2
+        np.testing.assert_allclose(W, W.transpose(2, 1, 0), rtol=0, atol=1e-2)
+
+
+def test_uniform_density_in_the_ball_has_zero_contrast():
+    n, R, N = 32, 9.3, 3_000_000
+    rng = np.random.default_rng(14)
+    v = rng.normal(size=(N, 3))
+    v *= (R * rng.uniform(0, 1, N) ** (1 / 3) / np.linalg.norm(v, axis=1))[:, None]
+    pos = n / 2 + v
+    lo, s, per = pm.active_cube(R, n)
+    rho, esc = pm.deposit(pos, n, lo, s, per)
+    assert esc == 0
+    nbar = N / (4 / 3 * math.pi * R**3)
+    d = pm.delta_cube(rho, n, lo, s, nbar, R, per, domain="sphere")
+    assert abs(d.sum()) < 1e-4 * 4 / 3 * math.pi * R**3
+    a1 = np.arange(lo, lo + s) + 0.5 - n / 2
+    AZ, AY, AX = np.meshgrid(a1, a1, a1, indexing="ij")
+    r = np.sqrt(AX**2 + AY**2 + AZ**2)
+    for r0 in np.arange(R - 2.0, R + 1.5, 0.5):    # shells across the surface
+        sel = (r >= r0) & (r < r0 + 0.5)
+        assert abs(d[sel].mean()) < 0.03, (r0, d[sel].mean())
