@@ -55,6 +55,7 @@ enum { PM_GRAVITY_POISSON = 0, PM_GRAVITY_DIFFUSION = 1,
 enum { PM_BC_PAPER = 0, PM_BC_OPEN = 1, PM_BC_PERIODIC = 2 };  /* pm_config.bc */
 enum { PM_SHRINK_OFF = 0, PM_SHRINK_ON = 1, PM_SHRINK_RECORD = 2 };  /* pm_config.shrink */
 enum { PM_ASSIGN_CIC = 0, PM_ASSIGN_TSC = 1 };                  /* pm_config.assignment */
+enum { PM_DOMAIN_CUBE = 0, PM_DOMAIN_SPHERE = 1 };                  /* pm_config.domain */
 
 typedef struct {
   int32_t n_mesh;        /* cells per side, of the form 2^j or 3*2^j, 4..1024 */
@@ -104,6 +105,14 @@ typedef struct {
                             the same scheme for the density and the force);
                             TSC needs PM_GRAVITY_POISSON and widens the open
                             cube by one cell (half-width ceil(R) + 2) */
+  int32_t domain;        /* keep region: PM_DOMAIN_CUBE (max_d |x_d - c| <= R,
+                            the loop-bounded domain of Sec. 2.4) or
+                            PM_DOMAIN_SPHERE (|x - c| <= R, Table 1, in FP64:
+                            ((x-c)^2 + (y-c)^2) + (z-c)^2 <= R^2); the solve
+                            stays on the cube; with the sphere the mean-density
+                            term is the CIC image of the ball (exact chord
+                            integral, 16-point Gauss-Legendre over the tents);
+                            the sphere needs PM_ASSIGN_CIC */
 } pm_config;
 
 /* Fill *cfg with defaults: 32^3 mesh and particles, 250 Mpc/h, Om=0.3,

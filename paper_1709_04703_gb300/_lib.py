@@ -17,6 +17,7 @@ PM_GRAVITY_POISSON, PM_GRAVITY_DIFFUSION, PM_GRAVITY_DIFFUSION_ADE = 0, 1, 2
 PM_BC_PAPER, PM_BC_OPEN, PM_BC_PERIODIC = 0, 1, 2
 PM_SHRINK_OFF, PM_SHRINK_ON, PM_SHRINK_RECORD = 0, 1, 2
 PM_ASSIGN_CIC, PM_ASSIGN_TSC = 0, 1
+PM_DOMAIN_CUBE, PM_DOMAIN_SPHERE = 0, 1
 PM_SHRINK_STATIC_MAX_PARTICLES = 1 << 22
 
 STATUS_NAMES = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ECUDA",
@@ -47,7 +48,7 @@ class PmConfig(C.Structure):
         ("max_vcycles", C.c_int32), ("precision", C.c_int32), ("guess", C.c_int32),
         ("bc", C.c_int32), ("shrink", C.c_int32), ("buffer_cells", C.c_double),
         ("store_forces", C.c_int32), ("gravity", C.c_int32), ("c_eff_factor", C.c_double),
-        ("assignment", C.c_int32),
+        ("assignment", C.c_int32), ("domain", C.c_int32),
     ]
 
 

@@ -151,6 +151,8 @@ struct pm_ctx {
   double* d_scal = nullptr;     // [0] ||f||^2, [1..10] moments, [11] ||r||^2, [12] sum phi
   double* bgm = nullptr;        // background moments (10), then at BGW_OFF the weights
   df* bgw = nullptr;            // per-axis mean-density weights w_g, g in [0, n)
+  float* ballw = nullptr;       // spherical keep region: mean-density image, n^3
+  BallRule ball_rule{};         // its Gauss-Legendre rule
   std::vector<unsigned char> h_bg;  // host image of bgm + bgw
   unsigned long long* d_cnt = nullptr;  // [0] n_keep, [1] escaped
   int* d_overflow = nullptr;
@@ -253,6 +255,45 @@ bool is_open(const pm_ctx* c, double R) {
   return R <= 0.5 * c->n - 1.0;
 }
 
+// Keep test of radius R (the cube's float bounds are passed separately).
+KeepBall keep_ball(const pm_ctx* c, double R) {
+  return KeepBall{c->cfg.domain == PM_DOMAIN_SPHERE ? 1 : 0, 0.5 * c->n, R * R};
+}
+
+// m-point Gauss-Legendre rule on [0, 1] (Newton on the Legendre recurrence)
+// with each weight times the tent 1 - xi.
+BallRule ball_rule() {
+  BallRule r{};
+  const int m = BALL_GL;
+  for (int i = 0; i < m; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (m + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= m; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = m * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= m; ++k) {
+      const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = m * (z * p1 - p0) / (z * z - 1.0);
+    const double w = 2.0 / ((1.0 - z * z) * dp * dp);
+    const double xi = 0.5 * (z + 1.0);
+    r.xi[i] = (float)xi;
+    r.om[i] = (float)(0.5 * w * (1.0 - xi));
+  }
+  return r;
+}
+
 // Active mesh cube for keep half-width R (see pm_config.bc).
 void geometry(const pm_ctx* c, double R, int* lo, int* s, int* periodic) {
   const int n = c->n;
@@ -333,6 +374,9 @@ pm_status set_cube(pm_ctx* ctx, int lo, int s, int periodic, double R) {
   std::memcpy(h, mom, sizeof(mom));
   CK(cudaMemcpyAsync(ctx->bgm, ctx->h_bg.data(), ctx->h_bg.size(), cudaMemcpyHostToDevice,
                      ctx->st));
+  if (ctx->ballw && !periodic)  // spherical keep region: image of the ball and its moments
+    launch_ball_w(ctx->st, ctx->ballw, n, lo, s, R, ctx->ball_rule, ctx->partial, ctx->counter,
+                  ctx->bgm);
   if (same) return PM_OK;
   // multigrid level sides: halve while > 4
   ctx->ls.clear();
@@ -694,7 +738,8 @@ pm_status shrink_to(pm_ctx* ctx, double R, double a_cross, bool flags_ready) {
   if (N == 0) return PM_OK;
   const int nblk = gkd_blocks(N);
   int e = prof_begin(ctx);
-  if (!flags_ready) launch_flag(ctx->st, ctx->pos, N, klo, khi, ctx->flags, ctx->block_keep);
+  if (!flags_ready)
+    launch_flag(ctx->st, ctx->pos, N, klo, khi, ctx->flags, ctx->block_keep, keep_ball(ctx, R));
   launch_scan_blocks(ctx->st, ctx->block_keep, ctx->keep_off, nblk, ctx->d_cnt);
   launch_scatter(ctx->st, ctx->pos, ctx->mom, N, ctx->flags, ctx->keep_off, ctx->pos2,
                  ctx->mom2, ctx->lc_pos, ctx->lc_mom, ctx->n_lc, (float)a_cross);
@@ -721,7 +766,8 @@ pm_status record_to(pm_ctx* ctx, double R, double a_cross) {
   if (N == 0) return PM_OK;
   const int nblk = gkd_blocks(N);
   int e = prof_begin(ctx);
-  launch_flag_record(ctx->st, ctx->pos, ctx->mom, N, klo, khi, ctx->flags, ctx->block_keep);
+  launch_flag_record(ctx->st, ctx->pos, ctx->mom, N, klo, khi, ctx->flags, ctx->block_keep,
+                     keep_ball(ctx, R));
   launch_scan_blocks(ctx->st, ctx->block_keep, ctx->keep_off, nblk, ctx->d_cnt);
   launch_record(ctx->st, ctx->pos, ctx->mom, N, ctx->flags, ctx->keep_off, ctx->lc_pos,
                 ctx->lc_mom, ctx->n_lc, ctx->N0, (float)a_cross);
@@ -788,6 +834,7 @@ void pm_config_default(pm_config* c) {
   c->gravity = PM_GRAVITY_POISSON;
   c->c_eff_factor = 0.019;
   c->assignment = PM_ASSIGN_CIC;
+  c->domain = PM_DOMAIN_CUBE;
 }
 
 pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
@@ -815,6 +862,9 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
     return fail(nullptr, PM_EINVAL, "pm_init: unknown guess");
   if (cfg->shrink < PM_SHRINK_OFF || cfg->shrink > PM_SHRINK_RECORD)
     return fail(nullptr, PM_EINVAL, "pm_init: unknown shrink mode");
+  if (cfg->domain != PM_DOMAIN_CUBE &&
+      (cfg->domain != PM_DOMAIN_SPHERE || cfg->assignment != PM_ASSIGN_CIC))
+    return fail(nullptr, PM_EINVAL, "pm_init: domain is the cube, or the sphere with CIC");
   if (cfg->assignment != PM_ASSIGN_CIC &&
       (cfg->assignment != PM_ASSIGN_TSC || cfg->gravity != PM_GRAVITY_POISSON))
     return fail(nullptr, PM_EINVAL, "pm_init: assignment is CIC, or TSC with Poisson gravity");
@@ -906,6 +956,10 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
   AL(ctx->d_scal, sizeof(double) * 16);
   AL(ctx->bgm, BGW_OFF + sizeof(df) * (size_t)n);
   ctx->bgw = (df*)((char*)ctx->bgm + BGW_OFF);
+  if (cfg->domain == PM_DOMAIN_SPHERE) {
+    AL(ctx->ballw, sizeof(float) * (size_t)n * n * n);
+    ctx->ball_rule = ball_rule();
+  }
   ctx->h_bg.assign(BGW_OFF + sizeof(df) * (size_t)n, 0);
   AL(ctx->d_cnt, sizeof(unsigned long long) * 4);
   ctx->d_overflow = (int*)(ctx->d_cnt + 3);  // read back with every sync_read
@@ -986,7 +1040,8 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
       launch_drift_deposit(ctx->st, std::max(1, std::min(gkd_blocks(N) * 4, 152 * 16)),
                            ctx->pos, ctx->mom, N, 0.0f, false, n, lo, s, per, ctx->rho,
                            ctx->d_cnt + 1);
-      launch_source(ctx->st, SRC_GRID, ctx->rho, n, lo, s, fh, fl, invM, S0, ctx->bgw, !per,
+      launch_source(ctx->st, SRC_GRID, ctx->rho, n, lo, s, fh, fl, invM, S0, ctx->bgw,
+                    per ? nullptr : ctx->ballw, !per,
                     ctx->partial, ctx->partial_m, ctx->counter, ctx->d_scal, ctx->bgm,
                     ctx->d_overflow);
       ghosts(S0);
@@ -1016,7 +1071,8 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
     // 3. source, boundary values, solve
     const double S = 1.5 * ctx->cfg.omega_m / ctx->a_half[k];
     e = prof_begin(ctx);
-    launch_source(ctx->st, SRC_GRID, ctx->rho, n, lo, s, fh, fl, invM, S, ctx->bgw, !per,
+    launch_source(ctx->st, SRC_GRID, ctx->rho, n, lo, s, fh, fl, invM, S, ctx->bgw,
+                  per ? nullptr : ctx->ballw, !per,
                   ctx->partial, ctx->partial_m, ctx->counter, ctx->d_scal, ctx->bgm,
                   ctx->d_overflow);
     // read the counts, clear them, write f hi + lo: 24 B/cell
@@ -1108,7 +1164,8 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
                                ctx->phi_l[ctx->cur], ctx->grad, n, lo, s,
                                per, (float)(ctx->a_half[k] * ctx->dtau[k]),
                                (float)(ctx->dtau[k] / (2.0 * ctx->a[k + 1])), do_flag, klo,
-                               khi, ctx->flags, ctx->block_keep, ctx->forces, ctx->d_cnt + 1);
+                               khi, keep_ball(ctx, R1), ctx->flags, ctx->block_keep,
+                               ctx->forces, ctx->d_cnt + 1);
     // gather: read x, p, write x, p (64 B/particle, + 1 B flag), read G once
     // (16 B/cell)
     prof_end(ctx, PM_PROF_GATHER, e, (do_flag ? 65.0 : 64.0) * N + (24.0 + 16.0) * cells);
@@ -1599,7 +1656,7 @@ void pm_destroy(pm_ctx* ctx) {
                   ctx->phi_h[0], ctx->phi_l[0], ctx->phi_h[1], ctx->phi_l[1], ctx->f_hi,
                   ctx->f_lo, ctx->prev_hi, ctx->prev_lo,
                   ctx->partial, ctx->partial_m,
-                  ctx->counter, ctx->d_scal, ctx->bgm, ctx->d_cnt,
+                  ctx->counter, ctx->d_scal, ctx->bgm, ctx->d_cnt, ctx->ballw,
                   ctx->nn_in, ctx->nn_out, ctx->grad};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -1914,6 +1971,8 @@ pm_status pm_batch_init(int32_t n_real, const pm_config* cfgs, const float* cons
       return bfail(nullptr, PM_EINVAL, "pm_batch_init: the learned guess runs per context");
     if (cfgs[r].gravity != PM_GRAVITY_POISSON)
       return bfail(nullptr, PM_EINVAL, "pm_batch_init: batches solve Poisson's equation");
+    if (cfgs[r].domain != PM_DOMAIN_CUBE)
+      return bfail(nullptr, PM_EINVAL, "pm_batch_init: batches keep a cube");
     if (cfgs[r].assignment != PM_ASSIGN_CIC)
       return bfail(nullptr, PM_EINVAL, "pm_batch_init: batches assign by CIC");
     if (cfgs[r].shrink == PM_SHRINK_RECORD)

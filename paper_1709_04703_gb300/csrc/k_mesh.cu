@@ -133,6 +133,115 @@ void launch_drift_deposit(cudaStream_t st, int grid, float4* pos, const float4* 
 }
 
 // ---------------------------------------------------------------------------
+// Mean-density term of a spherical keep region (Table 1's domain): the CIC
+// image of the ball |x - c| <= R on every cell of the cube, written to the
+// full-mesh array W [z][y][x], and its moments (sum W, sum W y_a,
+// sum W y_a y_b, y the cell centre - c) reduced in a fixed order into
+// out[0..9] (the layout of the source kernel's background moments).  Per
+// cell: 1 when |y| + sqrt(3) <= R, 0 when |y| - sqrt(3) >= R, otherwise the
+// z integral of the tent over the ball's chord in closed form,
+// T(h - y_z) - T(-h - y_z) with h = sqrt(R^2 - X^2 - Y^2), summed over the
+// four quadrants of the x-y tent support with the product Gauss-Legendre
+// rule `rule` (nodes xi on [0, 1], weights times the tent 1 - xi).  FP32.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float tent_cdf(float u) {
+  if (u <= -1.0f) return 0.0f;
+  if (u <= 0.0f) return 0.5f * (u + 1.0f) * (u + 1.0f);
+  if (u <= 1.0f) return 1.0f - 0.5f * (1.0f - u) * (1.0f - u);
+  return 1.0f;
+}
+
+__global__ void __launch_bounds__(256) k_ball_w(float* __restrict__ W, int n, int lo, int s,
+                                                double R, BallRule rule,
+                                                double* __restrict__ partial,
+                                                unsigned int* counter, double* __restrict__ out) {
+  double m[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const long long cells = (long long)s * s * s;
+  const float R2 = (float)(R * R);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < cells;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % s), j = (int)((t / s) % s), k = (int)(t / ((long long)s * s));
+    const int gi = lo + i, gj = lo + j, gk = lo + k;
+    const double yx = gi + 0.5 - 0.5 * n, yy = gj + 0.5 - 0.5 * n, yz = gk + 0.5 - 0.5 * n;
+    const double r = sqrt(yx * yx + yy * yy + yz * yz);
+    float w;
+    if (r + 1.7320508075688772 <= R) {
+      w = 1.0f;
+    } else if (r - 1.7320508075688772 >= R) {
+      w = 0.0f;
+    } else {
+      const float ax = (float)yx, ay = (float)yy, az = (float)yz;
+      float acc = 0.0f;
+      for (int q = 0; q < 4; ++q) {
+        const float sx = (q & 1) ? 1.0f : -1.0f, sy = (q & 2) ? 1.0f : -1.0f;
+        for (int g = 0; g < BALL_GL; ++g) {
+          const float X = ax + sx * rule.xi[g];
+          float row = 0.0f;
+          for (int hh = 0; hh < BALL_GL; ++hh) {
+            const float Y = ay + sy * rule.xi[hh];
+            const float h2 = R2 - X * X - Y * Y;
+            if (h2 > 0.0f) {
+              const float h = sqrtf(h2);
+              row += rule.om[hh] * (tent_cdf(h - az) - tent_cdf(-h - az));
+            }
+          }
+          acc += rule.om[g] * row;
+        }
+      }
+      w = acc;
+    }
+    W[((long long)gk * n + gj) * n + gi] = w;
+    const double wd = (double)w;
+    m[0] += wd;
+    m[1] += wd * yx;
+    m[2] += wd * yy;
+    m[3] += wd * yz;
+    m[4] += wd * yx * yx;
+    m[5] += wd * yy * yy;
+    m[6] += wd * yz * yz;
+    m[7] += wd * yx * yy;
+    m[8] += wd * yx * yz;
+    m[9] += wd * yy * yz;
+  }
+  // block sums (fixed order), then the last block folds the partials in order
+  __shared__ double sm[8][10];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 10; ++q) {
+    const double v = warp_sum(m[q]);
+    if (lane == 0) sm[warp][q] = v;
+  }
+  __syncthreads();
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 10; ++q) {
+      double v = 0.0;
+      for (int w8 = 0; w8 < (int)(blockDim.x >> 5); ++w8) v += sm[w8][q];
+      partial[blockIdx.x * 10 + q] = v;
+    }
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  if (threadIdx.x < 10) {
+    double v = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(partial + b * 10 + threadIdx.x);
+    out[threadIdx.x] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+void launch_ball_w(cudaStream_t st, float* W, int n, int lo, int s, double R,
+                   const BallRule& rule, double* partial, unsigned int* counter, double* out) {
+  const long long cells = (long long)s * s * s;
+  const int g = (int)std::min<long long>((cells + 255) / 256, 1216);
+  k_ball_w<<<g, 256, 0, st>>>(W, n, lo, s, R, rule, partial, counter, out);
+  note_launch();
+}
+
+// ---------------------------------------------------------------------------
 // TSC variant of the drift + deposit (Sec. 2.4 footnote: CIC or TSC).  Per
 // axis the particle's cell i = floor(u) and its position in the cell in
 // Q16, q = floor(2^16 u) - 2^16 i, give the weights of nodes i-1, i, i+1:
@@ -277,7 +386,8 @@ constexpr int SRC_NV = 10;
 template <bool MOMENTS>
 __device__ __forceinline__ void d_source(const BI& bi, 
     unsigned long long* __restrict__ rho, int n, int lo, int s, Grid fh, Grid fl,
-    df invM, df S, const df* __restrict__ bgw, double* __restrict__ partial_f2,
+    df invM, df S, const df* __restrict__ bgw, const float* __restrict__ ballw,
+    double* __restrict__ partial_f2,
     __int128* __restrict__ partial_m, unsigned int* counter, double* __restrict__ out,
     const double* __restrict__ bgm, double invM2_hi, int* __restrict__ overflow){
   __int128 acc[SRC_NV];
@@ -312,7 +422,9 @@ __device__ __forceinline__ void d_source(const BI& bi,
     if (cnt > (1ull << 62)) atomicOr(overflow, 1);
     long long c = (long long)cnt;
     df d = df_mul(df_from_u64(cnt), invM);
-    const df w = df_mul(wxy, bgw[gk]);
+    // ballw (spherical keep region): the mean density's image per cell
+    const df w = ballw ? df{ballw[((long long)gk * n + gj) * n + gi], 0.0f}
+                       : df_mul(wxy, bgw[gk]);
     d = df_add(d, df{-w.hi, -w.lo});
     df f = df_mul(d, S);
     int fi = gidx(fh, i, j, k);
@@ -425,11 +537,12 @@ __device__ __forceinline__ void d_source(const BI& bi,
 template <bool MOMENTS>
 __global__ void __launch_bounds__(256) k_source(
     unsigned long long* __restrict__ rho, int n, int lo, int s, Grid fh, Grid fl,
-    df invM, df S, const df* __restrict__ bgw, double* __restrict__ partial_f2,
+    df invM, df S, const df* __restrict__ bgw, const float* __restrict__ ballw,
+    double* __restrict__ partial_f2,
     __int128* __restrict__ partial_m, unsigned int* counter, double* __restrict__ out,
     const double* __restrict__ bgm, double invM2_hi, int* __restrict__ overflow) {
-  d_source<MOMENTS>(bi_native(), rho, n, lo, s, fh, fl, invM, S, bgw, partial_f2, partial_m,
-                    counter, out, bgm, invM2_hi, overflow);
+  d_source<MOMENTS>(bi_native(), rho, n, lo, s, fh, fl, invM, S, bgw, ballw, partial_f2,
+                    partial_m, counter, out, bgm, invM2_hi, overflow);
 }
 
 dim3 source_grid(int s) {
@@ -438,6 +551,7 @@ dim3 source_grid(int s) {
 
 void launch_source(cudaStream_t st, int grid, unsigned long long* rho, int n, int lo,
                    int s, Grid fh, Grid fl, double invM, double S, const df* bgw,
+                   const float* ballw,
                    bool moments, double* partial_f2, void* partial_m,
                    unsigned int* counter, double* out, const double* bgm, int* overflow) {
   df invMd, Sd;
@@ -446,11 +560,11 @@ void launch_source(cudaStream_t st, int grid, unsigned long long* rho, int n, in
   Sd.hi = (float)S;
   Sd.lo = (float)(S - (double)Sd.hi);
   if (moments)
-    k_source<true><<<source_grid(s), dim3(32, 8), 0, st>>>(rho, n, lo, s, fh, fl, invMd, Sd, bgw,
+    k_source<true><<<source_grid(s), dim3(32, 8), 0, st>>>(rho, n, lo, s, fh, fl, invMd, Sd, bgw, ballw,
                                          partial_f2, (__int128*)partial_m, counter, out,
                                          bgm, invM, overflow);
   else
-    k_source<false><<<source_grid(s), dim3(32, 8), 0, st>>>(rho, n, lo, s, fh, fl, invMd, Sd, bgw,
+    k_source<false><<<source_grid(s), dim3(32, 8), 0, st>>>(rho, n, lo, s, fh, fl, invMd, Sd, bgw, ballw,
                                           partial_f2, (__int128*)partial_m, counter, out,
                                           bgm, invM, overflow);
   note_launch();
@@ -755,10 +869,11 @@ __global__ void __launch_bounds__(256) kb_source(const SourceDesc* d, const BTab
   if (!batch_map(d, t, (const int*)nullptr, q, bi)) return;
   const SourceDesc& e = d[q];
   if (e.moments)
-    d_source<true>(bi, e.rho, e.n, e.lo, e.s, e.fh, e.fl, e.invM, e.S, e.bgw, e.partial_f2,
+    d_source<true>(bi, e.rho, e.n, e.lo, e.s, e.fh, e.fl, e.invM, e.S, e.bgw, nullptr,
+                   e.partial_f2,
                    (__int128*)e.partial_m, e.counter, e.out, e.bgm, e.invM_d, e.overflow);
   else
-    d_source<false>(bi, e.rho, e.n, e.lo, e.s, e.fh, e.fl, e.invM, e.S, e.bgw,
+    d_source<false>(bi, e.rho, e.n, e.lo, e.s, e.fh, e.fl, e.invM, e.S, e.bgw, nullptr,
                     e.partial_f2, (__int128*)e.partial_m, e.counter, e.out, e.bgm, e.invM_d,
                     e.overflow);
 }

@@ -40,7 +40,7 @@ __device__ __forceinline__ void d_gather_kick_drift(const BI& bi,
     float4* __restrict__ pos, float4* __restrict__ mom, long long N,
     const float* __restrict__ ph, const float* __restrict__ pl,
     const float4* __restrict__ G, int n, int lo, int s,
-    int periodic, float kick, float c2, int do_flag, float klo, float khi,
+    int periodic, float kick, float c2, int do_flag, float klo, float khi, KeepBall kb,
     unsigned char* __restrict__ flags, unsigned int* __restrict__ block_keep,
     float4* __restrict__ forces, unsigned long long* __restrict__ escaped){
   const int P = n + 2;
@@ -202,8 +202,7 @@ __device__ __forceinline__ void d_gather_kick_drift(const BI& bi,
     mom[p] = v;
     if (forces) forces[p] = make_float4(Fx, Fy, Fz, 0.f);
     if (do_flag) {
-      bool keep = x.x >= klo && x.x <= khi && x.y >= klo && x.y <= khi && x.z >= klo &&
-                  x.z <= khi;
+      const bool keep = in_keep(x, klo, khi, kb);
       flags[p] = keep ? 1 : 0;
       keep_count += keep ? 1u : 0u;
     }
@@ -232,10 +231,10 @@ __global__ void __launch_bounds__(KT) k_gather_kick_drift(
     float4* __restrict__ pos, float4* __restrict__ mom, long long N,
     const float* __restrict__ ph, const float* __restrict__ pl, const float4* __restrict__ G,
     int n, int lo, int s, int periodic, float kick, float c2, int do_flag, float klo, float khi,
-    unsigned char* __restrict__ flags, unsigned int* __restrict__ block_keep,
+    KeepBall kb, unsigned char* __restrict__ flags, unsigned int* __restrict__ block_keep,
     float4* __restrict__ forces, unsigned long long* __restrict__ escaped) {
   d_gather_kick_drift<GF>(bi_native(), pos, mom, N, ph, pl, G, n, lo, s, periodic, kick, c2,
-                          do_flag, klo, khi, flags, block_keep, forces, escaped);
+                          do_flag, klo, khi, kb, flags, block_keep, forces, escaped);
 }
 
 // G(c) = (gx, gy, gz, 0): centred differences of Phi = hi + lo at every cell
@@ -398,17 +397,18 @@ int gkd_blocks(long long N) { return (int)((N + KCHUNK - 1) / KCHUNK); }
 void launch_gather_kick_drift(cudaStream_t st, float4* pos, float4* mom, long long N,
                               const float* ph, const float* pl, const float4* G, int n, int lo,
                               int s, int periodic, float kick, float c2, bool do_flag, float klo,
-                              float khi, unsigned char* flags, unsigned int* block_keep,
-                              float4* forces, unsigned long long* escaped) {
+                              float khi, KeepBall kb, unsigned char* flags,
+                              unsigned int* block_keep, float4* forces,
+                              unsigned long long* escaped) {
   if (N <= 0) return;
   if (G)
     k_gather_kick_drift<true><<<gkd_blocks(N), KT, 0, st>>>(
-        pos, mom, N, ph, pl, G, n, lo, s, periodic, kick, c2, do_flag ? 1 : 0, klo, khi, flags,
-        block_keep, forces, escaped);
+        pos, mom, N, ph, pl, G, n, lo, s, periodic, kick, c2, do_flag ? 1 : 0, klo, khi, kb,
+        flags, block_keep, forces, escaped);
   else
     k_gather_kick_drift<false><<<gkd_blocks(N), KT, 0, st>>>(
-        pos, mom, N, ph, pl, G, n, lo, s, periodic, kick, c2, do_flag ? 1 : 0, klo, khi, flags,
-        block_keep, forces, escaped);
+        pos, mom, N, ph, pl, G, n, lo, s, periodic, kick, c2, do_flag ? 1 : 0, klo, khi, kb,
+        flags, block_keep, forces, escaped);
   note_launch();
 }
 
@@ -423,7 +423,7 @@ void launch_grad(cudaStream_t st, const float* ph, const float* pl, int n, int l
 // Keep flags from an explicit keep cube (pm_shrink), same chunking.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(KT) k_flag(const float4* __restrict__ pos, long long N,
-                                             float klo, float khi,
+                                             float klo, float khi, KeepBall kb,
                                              unsigned char* __restrict__ flags,
                                              unsigned int* __restrict__ block_keep) {
   const long long base = (long long)blockIdx.x * KCHUNK;
@@ -431,9 +431,8 @@ __global__ void __launch_bounds__(KT) k_flag(const float4* __restrict__ pos, lon
   for (int it = 0; it < KITEMS; ++it) {
     long long p = base + it * KT + threadIdx.x;
     if (p >= N) break;
-    float4 x = pos[p];
-    bool keep = x.x >= klo && x.x <= khi && x.y >= klo && x.y <= khi && x.z >= klo &&
-                x.z <= khi;
+    const float4 x = pos[p];
+    const bool keep = in_keep(x, klo, khi, kb);
     flags[p] = keep ? 1 : 0;
     keep_count += keep;
   }
@@ -450,9 +449,9 @@ __global__ void __launch_bounds__(KT) k_flag(const float4* __restrict__ pos, lon
 }
 
 void launch_flag(cudaStream_t st, const float4* pos, long long N, float klo, float khi,
-                 unsigned char* flags, unsigned int* block_keep) {
+                 unsigned char* flags, unsigned int* block_keep, KeepBall kb) {
   if (N <= 0) return;
-  k_flag<<<gkd_blocks(N), KT, 0, st>>>(pos, N, klo, khi, flags, block_keep);
+  k_flag<<<gkd_blocks(N), KT, 0, st>>>(pos, N, klo, khi, kb, flags, block_keep);
   note_launch();
 }
 
@@ -588,7 +587,7 @@ void launch_scatter(cudaStream_t st, const float4* pos, const float4* mom, long 
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(KT) k_flag_record(const float4* __restrict__ pos,
                                                     const float4* __restrict__ mom, long long N,
-                                                    float klo, float khi,
+                                                    float klo, float khi, KeepBall kb,
                                                     unsigned char* __restrict__ flags,
                                                     unsigned int* __restrict__ block_cnt) {
   const long long base = (long long)blockIdx.x * KCHUNK;
@@ -597,8 +596,7 @@ __global__ void __launch_bounds__(KT) k_flag_record(const float4* __restrict__ p
     long long p = base + it * KT + threadIdx.x;
     if (p >= N) break;
     const float4 x = pos[p];
-    const bool inside = x.x >= klo && x.x <= khi && x.y >= klo && x.y <= khi &&
-                        x.z >= klo && x.z <= khi;
+    const bool inside = in_keep(x, klo, khi, kb);
     const bool rec = !inside && mom[p].w == 0.0f;
     flags[p] = rec ? 1 : 0;
     cnt += rec ? 1u : 0u;
@@ -652,9 +650,10 @@ __global__ void __launch_bounds__(KT) k_record(const float4* __restrict__ pos,
 }
 
 void launch_flag_record(cudaStream_t st, const float4* pos, const float4* mom, long long N,
-                        float klo, float khi, unsigned char* flags, unsigned int* block_cnt) {
+                        float klo, float khi, unsigned char* flags, unsigned int* block_cnt,
+                        KeepBall kb) {
   if (N <= 0) return;
-  k_flag_record<<<gkd_blocks(N), KT, 0, st>>>(pos, mom, N, klo, khi, flags, block_cnt);
+  k_flag_record<<<gkd_blocks(N), KT, 0, st>>>(pos, mom, N, klo, khi, kb, flags, block_cnt);
   note_launch();
 }
 
@@ -676,7 +675,8 @@ __global__ void __launch_bounds__(KT) kb_gather(const GatherDesc* d, const BTabl
   if (!batch_map(d, t, (const int*)nullptr, q, bi)) return;
   const GatherDesc& e = d[q];
   d_gather_kick_drift<false>(bi, e.pos, e.mom, e.N, e.ph, e.pl, nullptr, e.n, e.lo, e.s,
-                             e.periodic, e.kick, e.c2, e.do_flag, e.klo, e.khi, e.flags,
+                             e.periodic, e.kick, e.c2, e.do_flag, e.klo, e.khi,
+                             KeepBall{0, 0.0, 0.0}, e.flags,
                              e.block_keep, e.forces, e.escaped);
 }
 __global__ void __launch_bounds__(1024) kb_scan(const ScanDesc* d, const BTable* t) {

@@ -84,7 +84,8 @@ extern "C" pm_status pm_shrink_static(const float* pos4_in, const float* mom4_in
   const int nblk = pm::gkd_blocks(n);
   // every flag, count, offset and the survivor count are written before they
   // are read, so nothing left over from an earlier call needs clearing
-  pm::launch_flag(st, (const float4*)pos4_in, n, klo, khi, flags, counts);
+  pm::launch_flag(st, (const float4*)pos4_in, n, klo, khi, flags, counts,
+                  pm::KeepBall{0, 0.0, 0.0});
   pm::launch_scan_blocks(st, counts, offs, nblk, nkeep);
   pm::launch_scatter(st, (const float4*)pos4_in, (const float4*)mom4_in, n, flags, offs,
                      (float4*)pos4_keep, (float4*)mom4_keep, (float4*)pos4_leave,

@@ -81,6 +81,23 @@ __device__ __forceinline__ df df_mul(df a, df b) {
   return fast_two_sum(p.hi, p.lo);
 }
 
+// Keep test of the lightcone shrink: the cube klo <= x_d <= khi (exact
+// float bounds of max_d |x_d - c| <= R), or with on = 1 the ball
+// ((x - c)^2 + (y - c)^2) + (z - c)^2 <= r2 in FP64 (each square exact).
+struct KeepBall {
+  int on;
+  double c, r2;
+};
+__device__ __forceinline__ bool in_keep(const float4& x, float klo, float khi,
+                                        const KeepBall& kb) {
+  if (kb.on) {
+    const double dx = (double)x.x - kb.c, dy = (double)x.y - kb.c, dz = (double)x.z - kb.c;
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)) <=
+           kb.r2;
+  }
+  return x.x >= klo && x.x <= khi && x.y >= klo && x.y <= khi && x.z >= klo && x.z <= khi;
+}
+
 // Non-negative 64-bit count -> (hi, lo) float pair, without 64-bit
 // conversions (those run on the FP64 pipe, 1/64 rate on GB300): v is split
 // into three 24-bit digits, each exact in float, and summed error-free.

@@ -20,7 +20,7 @@ void launch_drift_deposit(cudaStream_t st, int grid, float4* pos, const float4* 
                           unsigned long long* escaped);
 void launch_source(cudaStream_t st, int grid, unsigned long long* rho, int n, int lo,
                    int s, Grid fh, Grid fl, double invM, double S, const df* bgw,
-                   bool moments, double* partial_f2, void* partial_m,
+                   const float* ballw, bool moments, double* partial_f2, void* partial_m,
                    unsigned int* counter, double* out, const double* bgm, int* overflow);
 void launch_source_f64(cudaStream_t st, int grid, const double* delta, int n, Grid fh,
                        Grid fl, double S, bool moments, double* partial,
@@ -67,6 +67,13 @@ void launch_sum_phi(cudaStream_t st, Grid ph, Grid pl, double* partial, unsigned
                     double* out);
 
 // k_part.cu
+constexpr int BALL_GL = 16;  // Gauss-Legendre points per axis and quadrant
+struct BallRule {
+  float xi[BALL_GL];  // nodes on [0, 1]
+  float om[BALL_GL];  // weights on [0, 1] times the tent 1 - xi
+};
+void launch_ball_w(cudaStream_t st, float* W, int n, int lo, int s, double R,
+                   const BallRule& rule, double* partial, unsigned int* counter, double* out);
 void launch_drift_deposit_tsc(cudaStream_t st, long long N, float4* pos, const float4* mom,
                               float c0, bool drift, int n, int lo, int s, int periodic,
                               unsigned long long* rho, unsigned long long* escaped);
@@ -80,12 +87,13 @@ int gkd_blocks(long long N);
 void launch_gather_kick_drift(cudaStream_t st, float4* pos, float4* mom, long long N,
                               const float* ph, const float* pl, const float4* G, int n, int lo,
                               int s, int periodic, float kick, float c2, bool do_flag, float klo,
-                              float khi, unsigned char* flags, unsigned int* block_keep,
-                              float4* forces, unsigned long long* escaped);
+                              float khi, KeepBall kb, unsigned char* flags,
+                              unsigned int* block_keep, float4* forces,
+                              unsigned long long* escaped);
 void launch_grad(cudaStream_t st, const float* ph, const float* pl, int n, int lo, int s,
                  int periodic, float4* G);
 void launch_flag(cudaStream_t st, const float4* pos, long long N, float klo, float khi,
-                 unsigned char* flags, unsigned int* block_keep);
+                 unsigned char* flags, unsigned int* block_keep, KeepBall kb);
 void launch_scan_blocks(cudaStream_t st, const unsigned int* cnt, unsigned long long* off,
                         int nblk, unsigned long long* n_keep);
 void launch_scatter(cudaStream_t st, const float4* pos, const float4* mom, long long N,
@@ -93,7 +101,8 @@ void launch_scatter(cudaStream_t st, const float4* pos, const float4* mom, long 
                     float4* pos_out, float4* mom_out, float4* lc_pos, float4* lc_mom,
                     long long lc_base, float a_cross);
 void launch_flag_record(cudaStream_t st, const float4* pos, const float4* mom, long long N,
-                        float klo, float khi, unsigned char* flags, unsigned int* block_cnt);
+                        float klo, float khi, unsigned char* flags, unsigned int* block_cnt,
+                        KeepBall kb);
 void launch_record(cudaStream_t st, const float4* pos, float4* mom, long long N,
                    const unsigned char* flags, const unsigned long long* off, float4* lc_pos,
                    float4* lc_mom, long long lc_base, long long lc_cap, float a_cross);

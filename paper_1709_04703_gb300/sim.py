@@ -169,7 +169,7 @@ class Sim:
                  rtol=1e-7, precision="mixed", guess="warm", bc="paper",
                  shrink=True, buffer_cells=1.0, max_vcycles=50, store_forces=False,
                  omega_m=0.3, omega_l=0.7, host_init=False, gravity="poisson",
-                 c_eff_factor=0.019, assignment="cic"):
+                 c_eff_factor=0.019, assignment="cic", domain="cube"):
         lib = L.load()
         cfg = L.PmConfig()
         lib.pm_config_default(C.byref(cfg))
@@ -188,6 +188,7 @@ class Sim:
         cfg.gravity = _GRAVITY[gravity]
         cfg.c_eff_factor = float(c_eff_factor)
         cfg.assignment = {"cic": L.PM_ASSIGN_CIC, "tsc": L.PM_ASSIGN_TSC}[assignment]
+        cfg.domain = {"cube": L.PM_DOMAIN_CUBE, "sphere": L.PM_DOMAIN_SPHERE}[domain]
         self.cfg = cfg
         self.n_particles = int(len(pos))
         # the context runs on its own stream so that its V-cycle can be
