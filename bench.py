@@ -330,7 +330,7 @@ def run_batch(args):
 TABLE4 = {512.0: 1.08, 2048.0: 1.44, 8192.0: 3.02}   # Table 4, 512^3 particles
 
 
-def _timed_run(pos, mom, ids, n, box, a0, steps, rtol, gravity, shrink):
+def _timed_run(pos, mom, ids, n, box, a0, steps, rtol, gravity, shrink, domain="cube"):
     """One whole run, each step device-timed on the context stream; per-step
     active particles and milliseconds, and the run's catalogue (lightcone
     records plus the particles never recorded) for P(k).  shrink=False is
@@ -339,7 +339,7 @@ def _timed_run(pos, mom, ids, n, box, a0, steps, rtol, gravity, shrink):
     from paper_1709_04703_gb300.sim import Sim
     sim = Sim(pos, mom, ids, n, box, a0, 1.0, steps, rtol=rtol, precision="mixed",
               max_vcycles=100, gravity=gravity, bc="paper" if shrink else "periodic",
-              shrink=True if shrink else "record")
+              shrink=True if shrink else "record", domain=domain)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     n_act = []
     torch.cuda.synchronize()
@@ -388,12 +388,14 @@ def run_shrink_table(args):
     # warm-up: a few steps of each kind
     for grav in args.gravities:
         for shrink in (True, False):
-            _timed_run(pos, mom, ids, n, 8192.0, a0, max(3, args.warmup), tol, grav, shrink)
+            _timed_run(pos, mom, ids, n, 8192.0, a0, max(3, args.warmup), tol, grav, shrink,
+                       args.table_domain)
     rows = []
     for grav in args.gravities:
         for box in (512.0, 2048.0, 8192.0):
-            sh = _timed_run(pos, mom, ids, n, box, a0, steps, tol, grav, True)
-            fx = _timed_run(pos, mom, ids, n, box, a0, steps, tol, grav, False)
+            sh = _timed_run(pos, mom, ids, n, box, a0, steps, tol, grav, True, args.table_domain)
+            fx = _timed_run(pos, mom, ids, n, box, a0, steps, tol, grav, False,
+                            args.table_domain)
             q = [steps // 4, steps // 2, (3 * steps) // 4]
             # Fig. 4: P(k) of the two catalogues in the original box, k <= k_Ny/2
             _, p_sh = _catalogue_pk(sh["catalogue"], box, n)
@@ -414,7 +416,8 @@ def run_shrink_table(args):
     line = {"metric": "whole-run speed-up, shrinking vs fixed periodic box", "unit": "x",
             "higher_is_better": True, "n_gpus": 1, "steps": steps,
             "data": "synthetic (seeded Zel'dovich ICs)",
-            "config": {"workload": "shrink_table", "n_mesh": n, "n_particles": n**3,
+            "config": {"workload": "shrink_table", "domain": args.table_domain,
+                       "n_mesh": n, "n_particles": n**3,
                        "a": [a0, 1.0], "rtol": tol, "precision": "mixed"},
             "rows": rows}
     print(json.dumps(line), flush=True)
@@ -606,6 +609,8 @@ def main():
     ap.add_argument("--workload", choices=["pm256", "batch48", "shrink_table"], default="pm256")
     ap.add_argument("--table-n", type=int, default=512,
                     help="shrink_table: particles and mesh per side")
+    ap.add_argument("--table-domain", choices=["cube", "sphere"], default="cube",
+                    help="shrink_table: keep region")
     ap.add_argument("--gravities", nargs="+", default=["diffusion", "poisson"],
                     choices=["diffusion", "diffusion_ade", "poisson"],
                     help="shrink_table: gravity solvers")
