@@ -134,8 +134,8 @@ void launch_drift_deposit(cudaStream_t st, int grid, float4* pos, const float4* 
 
 // ---------------------------------------------------------------------------
 // Mean-density term of a spherical keep region (Table 1's domain): the CIC
-// image of the ball |x - c| <= R on every cell of the cube, written to the
-// full-mesh array W [z][y][x], and its moments (sum W, sum W y_a,
+// image of the ball |x - c| <= R on every cell of the (even-sided, centred)
+// cube, written to the full-mesh array W [z][y][x], and its moments (sum W, sum W y_a,
 // sum W y_a y_b, y the cell centre - c) reduced in a fixed order into
 // out[0..9] (the layout of the source kernel's background moments).  Per
 // cell: 1 when |y| + sqrt(3) <= R, 0 when |y| - sqrt(3) >= R, otherwise the
@@ -155,57 +155,77 @@ __global__ void __launch_bounds__(256) k_ball_w(float* __restrict__ W, int n, in
                                                 double R, BallRule rule,
                                                 double* __restrict__ partial,
                                                 unsigned int* counter, double* __restrict__ out) {
+  // The cube is centred on c and W is even in each coordinate, so one warp
+  // takes an x row of the octant i, j, k >= s/2 and writes each value to
+  // its eight mirror cells; a cell on the ball's surface is integrated by
+  // the whole warp (the 4 G^2 rule points split over the lanes).
+  constexpr unsigned FULL = 0xffffffffu;
+  constexpr int NQ = 4 * BALL_GL * BALL_GL;
   double m[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  const long long cells = (long long)s * s * s;
+  const int half = s / 2, lane = threadIdx.x & 31;
+  const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
   const float R2 = (float)(R * R);
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < cells;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % s), j = (int)((t / s) % s), k = (int)(t / ((long long)s * s));
-    const int gi = lo + i, gj = lo + j, gk = lo + k;
-    const double yx = gi + 0.5 - 0.5 * n, yy = gj + 0.5 - 0.5 * n, yz = gk + 0.5 - 0.5 * n;
-    const double r = sqrt(yx * yx + yy * yy + yz * yz);
-    float w;
-    if (r + 1.7320508075688772 <= R) {
-      w = 1.0f;
-    } else if (r - 1.7320508075688772 >= R) {
-      w = 0.0f;
-    } else {
-      const float ax = (float)yx, ay = (float)yy, az = (float)yz;
-      float acc = 0.0f;
-      for (int q = 0; q < 4; ++q) {
-        const float sx = (q & 1) ? 1.0f : -1.0f, sy = (q & 2) ? 1.0f : -1.0f;
-        for (int g = 0; g < BALL_GL; ++g) {
-          const float X = ax + sx * rule.xi[g];
-          float row = 0.0f;
-          for (int hh = 0; hh < BALL_GL; ++hh) {
-            const float Y = ay + sy * rule.xi[hh];
-            const float h2 = R2 - X * X - Y * Y;
-            if (h2 > 0.0f) {
-              const float h = sqrtf(h2);
-              row += rule.om[hh] * (tent_cdf(h - az) - tent_cdf(-h - az));
-            }
+  const double c = 0.5 * n;
+  for (int row = gw; row < half * half; row += nw) {
+    const int jj = half + row % half, kk = half + row / half;
+    for (int x0 = half; x0 < s; x0 += 32) {
+      const int ii = x0 + lane;
+      const bool valid = ii < s;
+      const double yx = lo + ii + 0.5 - c, yy = lo + jj + 0.5 - c, yz = lo + kk + 0.5 - c;
+      const double r = sqrt(yx * yx + yy * yy + yz * yz);
+      const int cls = !valid ? -1
+                      : (r + 1.7320508075688772 <= R ? 1
+                                                      : (r - 1.7320508075688772 >= R ? 0 : 2));
+      float w = cls == 1 ? 1.0f : 0.0f;
+      unsigned shell = __ballot_sync(FULL, cls == 2);
+      while (shell) {
+        const int src = __ffs(shell) - 1;
+        shell &= shell - 1;
+        const float ax = __shfl_sync(FULL, (float)yx, src);
+        const float ay = __shfl_sync(FULL, (float)yy, src);
+        const float az = __shfl_sync(FULL, (float)yz, src);
+        float part = 0.0f;
+        for (int e = lane; e < NQ; e += 32) {
+          const int q = e / (BALL_GL * BALL_GL), g = (e / BALL_GL) % BALL_GL,
+                    h = e % BALL_GL;
+          const float X = ax + ((q & 1) ? rule.xi[g] : -rule.xi[g]);
+          const float Y = ay + ((q & 2) ? rule.xi[h] : -rule.xi[h]);
+          const float h2 = R2 - X * X - Y * Y;
+          if (h2 > 0.0f) {
+            const float hz = sqrtf(h2);
+            part += rule.om[g] * rule.om[h] * (tent_cdf(hz - az) - tent_cdf(-hz - az));
           }
-          acc += rule.om[g] * row;
         }
+        part = warp_sumf_all(part);
+        if (lane == src) w = part;
       }
-      w = acc;
+      if (!valid) continue;
+      const double wd = (double)w;
+#pragma unroll
+      for (int mirror = 0; mirror < 8; ++mirror) {
+        const int i2 = (mirror & 1) ? s - 1 - ii : ii;
+        const int j2 = (mirror & 2) ? s - 1 - jj : jj;
+        const int k2 = (mirror & 4) ? s - 1 - kk : kk;
+        W[((long long)(lo + k2) * n + (lo + j2)) * n + (lo + i2)] = w;
+        const double px = (mirror & 1) ? -yx : yx, py = (mirror & 2) ? -yy : yy,
+                     pz = (mirror & 4) ? -yz : yz;
+        m[0] += wd;
+        m[1] += wd * px;
+        m[2] += wd * py;
+        m[3] += wd * pz;
+        m[4] += wd * px * px;
+        m[5] += wd * py * py;
+        m[6] += wd * pz * pz;
+        m[7] += wd * px * py;
+        m[8] += wd * px * pz;
+        m[9] += wd * py * pz;
+      }
     }
-    W[((long long)gk * n + gj) * n + gi] = w;
-    const double wd = (double)w;
-    m[0] += wd;
-    m[1] += wd * yx;
-    m[2] += wd * yy;
-    m[3] += wd * yz;
-    m[4] += wd * yx * yx;
-    m[5] += wd * yy * yy;
-    m[6] += wd * yz * yz;
-    m[7] += wd * yx * yy;
-    m[8] += wd * yx * yz;
-    m[9] += wd * yy * yz;
   }
   // block sums (fixed order), then the last block folds the partials in order
   __shared__ double sm[8][10];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < 10; ++q) {
     const double v = warp_sum(m[q]);
@@ -235,8 +255,9 @@ __global__ void __launch_bounds__(256) k_ball_w(float* __restrict__ W, int n, in
 
 void launch_ball_w(cudaStream_t st, float* W, int n, int lo, int s, double R,
                    const BallRule& rule, double* partial, unsigned int* counter, double* out) {
-  const long long cells = (long long)s * s * s;
-  const int g = (int)std::min<long long>((cells + 255) / 256, 1216);
+  // one warp per octant row (the cube side is even), 8 warps per block
+  const long long rows = (long long)(s / 2) * (s / 2);
+  const int g = (int)std::max<long long>(1, std::min<long long>((rows + 7) / 8, 1216));
   k_ball_w<<<g, 256, 0, st>>>(W, n, lo, s, R, rule, partial, counter, out);
   note_launch();
 }
