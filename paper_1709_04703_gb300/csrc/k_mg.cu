@@ -913,30 +913,47 @@ __device__ __forceinline__ void d_defect(const BI& bi, Grid ph, Grid pl, Grid e,
     float Hm, Lm, Hc, Lc, Hp, Lp;
     column(wrap_m(k0, s, periodic), Hm, Lm);
     column(k0, Hc, Lc);
-    for (int k = k0; k < k1; ++k) {
-      column(wrap_p(k, s, periodic), Hp, Lp);
+    const int off[4] = {xm, xp, ym * ph.sy, yp * ph.sy};
+    const int eoff[4] = {xm, xp, ym * e.sy, yp * e.sy};
+    // the in-plane neighbours (with their corrections) and f of plane k are
+    // loaded one iteration ahead, so their latency overlaps the arithmetic
+    // of the plane before (none of them is written by this kernel)
+    float nh[4], nl[4], ne[4], nfh, nfl;
+    auto load_plane = [&](int k) {
       const int c = gidx(ph, i, j, k);
-      const int off[4] = {xm, xp, ym * ph.sy, yp * ph.sy};
-      float H[7], Lo[7];
-      H[0] = Hc;
-      Lo[0] = Lc;
-      const float* h = ph.base + c;
-      const float* l = pl.base + c;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        H[q + 1] = __ldg(h + off[q]);
-        Lo[q + 1] = __ldg(l + off[q]);
+        nh[q] = __ldg(ph.base + c + off[q]);
+        nl[q] = __ldg(pl.base + c + off[q]);
+        if (CORRECT) ne[q] = __ldg(e.base + gidx(e, i, j, k) + eoff[q]);
       }
+      const int fc = gidx(fh, i, j, k);
+      nfh = __ldg(fh.base + fc);
+      nfl = __ldg(fl.base + fc);
+    };
+    load_plane(k0);
+    for (int k = k0; k < k1; ++k) {
+      float H[7], Lo[7], E[4];
+      H[0] = Hc;
+      Lo[0] = Lc;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        H[q + 1] = nh[q];
+        Lo[q + 1] = nl[q];
+        E[q] = ne[q];
+      }
+      float sacc = nfh;
+      float comp = nfl;
+      if (k + 1 < k1) load_plane(k + 1);
+      column(wrap_p(k, s, periodic), Hp, Lp);
       H[5] = Hm;
       Lo[5] = Lm;
       H[6] = Hp;
       Lo[6] = Lp;
       if (CORRECT) {
-        const float* ec = e.base + gidx(e, i, j, k);
-        const int eoff[4] = {xm, xp, ym * e.sy, yp * e.sy};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          df t = two_sum(H[q + 1], __ldg(ec + eoff[q]));
+          df t = two_sum(H[q + 1], E[q]);
           H[q + 1] = t.hi;
           Lo[q + 1] = __fadd_rn(Lo[q + 1], t.lo);
         }
@@ -945,11 +962,8 @@ __device__ __forceinline__ void d_defect(const BI& bi, Grid ph, Grid pl, Grid e,
         qh.base[qc] = n.hi;
         ql.base[qc] = n.lo;
       }
-      int fc = gidx(fh, i, j, k);
       // r = f - sum_nb + 6 phi: TwoSum cascade on the hi parts, rounding errors
       // and lo parts in a float compensation term
-      float sacc = __ldg(fh.base + fc);
-      float comp = __ldg(fl.base + fc);
       df t;
 #pragma unroll
       for (int q = 1; q < 7; ++q) {
