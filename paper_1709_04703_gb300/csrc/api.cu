@@ -26,7 +26,7 @@ namespace {
 
 constexpr double C_OVER_H0 = 2997.92458;  // Mpc/h
 constexpr int SRC_GRID = 1216;            // 152 SMs x 8 blocks
-constexpr int COARSE_SWEEPS = 12;
+constexpr int COARSE_SWEEPS = 6;
 constexpr int FUSED_MIN = 192;  // smallest level side smoothed by the fused pass
 constexpr size_t BGW_OFF = 128;  // byte offset of the background weights in bgm
 
