@@ -1707,6 +1707,8 @@ struct pm_batch {
   bool tables_stale = true;
   cudaGraphExec_t vgraph = nullptr;
   long long vgraph_kernels = 0;
+  int rb_bx = 32, rb_by = 8;  // block shape of the batched colour pass (autotuned)
+  bool rb_tuned = false;
   std::string err;
 };
 
@@ -1802,9 +1804,9 @@ void upload_vcycle_tables(pm_batch* B) {
           e.color = k & 1;
           e.periodic = c->periodic;
           e.zero_start = k == 0;  // level 0: e is not cleared; coarser: restriction zeroed it
-          set_dims(e, r, rbgs_grid(c->ls[l]));
+          set_dims(e, r, rbgs_grid(c->ls[l], B->rb_bx, B->rb_by));
           d.push_back(e);
-          bl.push_back(nblocks(rbgs_grid(c->ls[l])));
+          bl.push_back(nblocks(rbgs_grid(c->ls[l], B->rb_bx, B->rb_by)));
         }
         tab_upload(B, B->t_vc[slot_down(l, k)], d, bl);
       } else {
@@ -1878,9 +1880,9 @@ void upload_vcycle_tables(pm_batch* B) {
           e.color = (k - 1) & 1;
           e.periodic = c->periodic;
           e.zero_start = 0;
-          set_dims(e, r, rbgs_grid(c->ls[l]));
+          set_dims(e, r, rbgs_grid(c->ls[l], B->rb_bx, B->rb_by));
           d.push_back(e);
-          bl.push_back(nblocks(rbgs_grid(c->ls[l])));
+          bl.push_back(nblocks(rbgs_grid(c->ls[l], B->rb_bx, B->rb_by)));
         }
         tab_upload(B, B->t_vc[slot_up(M, l, k)], d, bl);
       }
@@ -1896,7 +1898,8 @@ void launch_vcycle_slots(pm_batch* B) {
   for (int l = 0; l < M; ++l) {
     for (int k = 0; k < 4; ++k) {
       BTab& t = B->t_vc[slot_down(l, k)];
-      launch_rbgs_b(B->st, t.grid_max, (const RbgsDesc*)t.d_desc, t.d_tab, act);
+      launch_rbgs_b(B->st, t.grid_max, (const RbgsDesc*)t.d_desc, t.d_tab, act, B->rb_bx,
+                    B->rb_by);
     }
     BTab& t = B->t_vc[slot_down(l, 4)];
     launch_restrict_b(B->st, t.grid_max, (const RestrictDesc*)t.d_desc, t.d_tab, act);
@@ -1908,9 +1911,58 @@ void launch_vcycle_slots(pm_batch* B) {
     launch_prolong_b(B->st, tp.grid_max, (const ProlongDesc*)tp.d_desc, tp.d_tab, act);
     for (int k = 1; k < 5; ++k) {
       BTab& t = B->t_vc[slot_up(M, l, k)];
-      launch_rbgs_b(B->st, t.grid_max, (const RbgsDesc*)t.d_desc, t.d_tab, act);
+      launch_rbgs_b(B->st, t.grid_max, (const RbgsDesc*)t.d_desc, t.d_tab, act, B->rb_bx,
+                    B->rb_by);
     }
   }
+}
+
+// Autotuner of the batched colour pass: before the V-cycle graph is
+// captured, the down-sweep passes of every level run with each candidate
+// block shape on the batch's own grids (they only write the levels'
+// iterates, which every V-cycle restarts from zero) and the fastest shape
+// is kept.  Every shape computes the same cells with the same arithmetic:
+// the choice changes the time, not the bits.
+pm_status tune_rbgs(pm_batch* B) {
+  static const int shapes[4][2] = {{32, 8}, {32, 4}, {16, 8}, {64, 4}};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return bfail(B, PM_ECUDA, "pm_batch: event creation failed");
+  const int M = B->maxLc;
+  float best = 1e30f;
+  int pick = 0;
+  for (int q = 0; q < 4; ++q) {
+    B->rb_bx = shapes[q][0];
+    B->rb_by = shapes[q][1];
+    upload_vcycle_tables(B);
+    float tot = 0.0f;
+    for (int rep = 0; rep < 3; ++rep) {  // the first pass warms up
+      cudaEventRecord(e0, B->st);
+      for (int l = 0; l < M; ++l)
+        for (int k = 0; k < 4; ++k) {
+          BTab& t = B->t_vc[slot_down(l, k)];
+          launch_rbgs_b(B->st, t.grid_max, (const RbgsDesc*)t.d_desc, t.d_tab, B->d_active,
+                        B->rb_bx, B->rb_by);
+        }
+      cudaEventRecord(e1, B->st);
+      cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tot += ms;
+    }
+    if (tot < best) {
+      best = tot;
+      pick = q;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  B->rb_bx = shapes[pick][0];
+  B->rb_by = shapes[pick][1];
+  upload_vcycle_tables(B);
+  B->rb_tuned = true;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? PM_OK : bfail(B, PM_ECUDA, cudaGetErrorString(e));
 }
 
 pm_status batch_vcycle(pm_batch* B) {
@@ -1919,6 +1971,10 @@ pm_status batch_vcycle(pm_batch* B) {
     B->tables_stale = false;
   }
   cudaMemcpyAsync(B->d_active, B->h_active, sizeof(int) * B->R, cudaMemcpyHostToDevice, B->st);
+  if (!B->rb_tuned) {
+    pm_status st = tune_rbgs(B);
+    if (st != PM_OK) return st;
+  }
   if (!B->vgraph) {
     // grids of the graph: the largest totals (taken from the first cubes,
     // which are the largest of the run)

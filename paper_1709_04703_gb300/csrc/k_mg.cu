@@ -1290,9 +1290,9 @@ __global__ void __launch_bounds__(256) kb_predict(const PredictDesc* d, const BT
 }
 
 void launch_rbgs_b(cudaStream_t st, int grid, const RbgsDesc* d, const BTable* t,
-                   const int* active) {
+                   const int* active, int bx, int by) {
   if (grid <= 0) return;
-  kb_rbgs<<<grid, dim3(32, 8), 0, st>>>(d, t, active);
+  kb_rbgs<<<grid, dim3(bx, by), 0, st>>>(d, t, active);
   note_launch();
 }
 void launch_restrict_b(cudaStream_t st, int grid, const RestrictDesc* d, const BTable* t,
@@ -1326,6 +1326,12 @@ void launch_predict_b(cudaStream_t st, int grid, const PredictDesc* d, const BTa
 }
 
 dim3 rbgs_grid(int s) { return grid_half(s); }
+// the colour pass with bx x by blocks: each thread takes two cells of its
+// colour in a row, so a row needs ceil(s/4) threads
+dim3 rbgs_grid(int s, int bx, int by) {
+  const int tx = ((s >> 1) + 1) / 2;
+  return dim3((unsigned)((tx + bx - 1) / bx), (unsigned)((s + by - 1) / by), (unsigned)s);
+}
 dim3 full_grid(int s) { return grid_full(s); }
 dim3 defect_grid(int s) { return grid_defect(s); }
 

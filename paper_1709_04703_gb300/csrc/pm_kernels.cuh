@@ -229,7 +229,8 @@ struct ScatterDesc {
 
 // batched launchers: `grid` blocks (the members' total, or more), tables in
 // device memory, `active` (may be NULL) masks realisations by index
-void launch_rbgs_b(cudaStream_t st, int grid, const RbgsDesc* d, const BTable* t, const int* active);
+void launch_rbgs_b(cudaStream_t st, int grid, const RbgsDesc* d, const BTable* t,
+                   const int* active, int bx, int by);
 void launch_restrict_b(cudaStream_t st, int grid, const RestrictDesc* d, const BTable* t,
                        const int* active);
 void launch_prolong_b(cudaStream_t st, int grid, const ProlongDesc* d, const BTable* t,
@@ -248,6 +249,7 @@ void launch_scatter_b(cudaStream_t st, int grid, const ScatterDesc* d, const BTa
 
 // grid shapes of the single-realisation launches (blocks per dimension)
 dim3 rbgs_grid(int s);
+dim3 rbgs_grid(int s, int bx, int by);
 dim3 full_grid(int s);
 dim3 defect_grid(int s);
 dim3 source_grid(int s);
