@@ -356,25 +356,23 @@ struct Rbgs2 {
   float* pb;
   int uoff[2], boff[2];
   unsigned rmask[2];  // bit h: the cell is updated by the stage covering tile + h
-  bool out_tile;
+  bool out0, out1;    // this thread stores cell xa / xa + 1 of the tile's planes
+  int par0;           // (y + first step) & 1: the parities below follow from it and J
+  int zst0, zst1;     // steady steps: all four stages active in z
+  // the next plane to prefetch: its index P, its z (wrapped when periodic)
+  // and its offsets in win and b; the output offset of the next step's plane
+  int iss_P, iss_z;
+  long long iss_u, iss_b, out_off;
   float R[RING], K[RING], BR[RING], BK[RING];  // plane t-4+m in slot (j + m) % 6
 
-  __device__ int zmem(int P) const {
-    if (PERIODIC) {
-      while (P < 0) P += s;
-      while (P >= s) P -= s;
-      return P;
-    }
-    return (P < -1 || P > s) ? -2 : P;
-  }
-
-  // asynchronous copy of u(P) and b(P) for this pair into prefetch slot P
-  __device__ void issue(int P) {
+  // asynchronous copy of u and b of plane iss_P for this pair into its
+  // prefetch slot, then advance to the next plane
+  __device__ void issue() {
+    const int P = iss_P;
     const int sl = P & (F2_PR - 1);
-    const int z = zmem(P);
-    const bool zok = z >= -1;
-    const float* gu = win.base - 1 - win.sy + (long long)(zok ? z : 0) * win.sz;
-    const float* gb = b.base - 1 - b.sy + (long long)(zok ? z : 0) * b.sz;
+    const bool zok = PERIODIC || (P >= -1 && P <= s);
+    const float* gu = win.base - 1 - win.sy + (zok ? iss_u : 0ll);
+    const float* gb = b.base - 1 - b.sy + (zok ? iss_b : 0ll);
     float* du = pu + sl * F2_PL + me;
     float* db = pb + sl * F2_PL + me;
 #pragma unroll
@@ -389,16 +387,24 @@ struct Rbgs2 {
       cp_async4(db + k, gb + (okb ? boff[k] : 0), okb);
     }
     cp_async_commit();
+    ++iss_P;
+    iss_u += win.sz;
+    iss_b += b.sz;
+    if (PERIODIC && ++iss_z == s) {
+      iss_z = 0;
+      iss_u = 0;
+      iss_b = 0;
+    }
   }
 
-  // the prefetched plane P (cells in x order) into colour-ordered slot Q
+  // the prefetched plane P (cells in x order) into colour-ordered slot Q;
+  // r1: (y + P) & 1
   template <int Q>
-  __device__ void take(int P) {
+  __device__ void take(int P, int r1) {
     constexpr int q = Q;
     const int sl = P & (F2_PR - 1);
     const float* du = pu + sl * F2_PL + me;
     const float* db = pb + sl * F2_PL + me;
-    const bool r1 = ((y + P) & 1) != 0;
     const float a = du[0], c = du[1], e = db[0], f = db[1];
     R[q] = r1 ? c : a;
     K[q] = r1 ? a : c;
@@ -407,30 +413,40 @@ struct Rbgs2 {
   }
 
   template <int Q>
-  __device__ void put(int p) {  // plane p (slot Q) into the shared ring
+  __device__ void put(int p, int r) {  // plane p (slot Q) into the shared ring; r: (y + p) & 1
     constexpr int q = Q;
     float* d = sp + (p & (F2_R - 1)) * F2_PL + me;
-    const int r = (y + p) & 1;
     d[r] = R[q];
     d[1 - r] = K[q];
   }
 
   template <int J>
   __device__ void step(int t) {
-    issue(t + F2_D + 1);
+    issue();  // plane t + F2_D + 1
     __syncthreads();
-    const int kc = (y + t) & 1;  // x offset of the cell updated by all four stages
-    const unsigned mask = kc ? rmask[1] : rmask[0];
+    const int kc = par0 ^ (J & 1);  // x offset of the cell updated by all four stages
     const int xo = kc ? 1 : -1;
+    // z activity of the four stages (bit 3 - st), all on in the steady steps
+    unsigned zb = 0xFu;
+    if (t < zst0 || t > zst1) {
+      zb = 0u;
+#pragma unroll
+      for (int st = 0; st < 4; ++st) {
+        const int p = t - st;
+        const bool zact =
+            (st == 0 || (st == 1 ? p >= z0 - 2 : st == 2 ? (p >= z0 - 1 && p <= z1)
+                                                          : (p >= z0 && p < z1))) &&
+            (PERIODIC || (p >= 0 && p < s));
+        zb |= (zact ? 1u : 0u) << (3 - st);
+      }
+    }
+    const unsigned act = (kc ? rmask[1] : rmask[0]) & zb;
 #pragma unroll
     for (int st = 0; st < 4; ++st) {
       const int p = t - st;
       const int m = 4 - st;
       const int q = (J + m) % RING, qm = (J + m - 1) % RING, qp = (J + m + 1) % RING;
-      const bool zact = (st == 0 || (st == 1 ? p >= z0 - 2 : st == 2 ? (p >= z0 - 1 && p <= z1)
-                                                                      : (p >= z0 && p < z1))) &&
-                        (PERIODIC || (p >= 0 && p < s));
-      if (zact && ((mask >> (3 - st)) & 1u)) {
+      if ((act >> (3 - st)) & 1u) {
         float* c = sp + (p & (F2_R - 1)) * F2_PL + me + kc;
         const float xv = c[xo], ym = c[-F2_W], yp = c[F2_W];
         float nv;
@@ -450,16 +466,17 @@ struct Rbgs2 {
         *c = nv;
       }
     }
-    if (t - 3 >= z0 && t - 3 < z1 && out_tile) {
+    if (t - 3 >= z0 && t - 3 < z1) {
       constexpr int q1 = (J + 1) % RING;  // plane t-3
-      const int r = (y + t - 3) & 1;
-      float* g = wout.base + (long long)(t - 3) * wout.sz + (xa + y * wout.sy);
-      if (xa < s && y < s) g[0] = r ? K[q1] : R[q1];
-      if (xa + 1 < s && y < s) g[1] = r ? R[q1] : K[q1];
+      const int r = kc ^ 1;               // (y + t - 3) & 1
+      float* g = wout.base + out_off;
+      if (out0) g[0] = r ? K[q1] : R[q1];
+      if (out1) g[1] = r ? R[q1] : K[q1];
     }
-    put<(J + 5) % RING>(t + 1);
+    out_off += wout.sz;
+    put<(J + 5) % RING>(t + 1, kc ^ 1);
     cp_async_wait<F2_D - 1>();
-    take<J % RING>(t + 2);  // the slot of plane t-4 takes plane t+2
+    take<J % RING>(t + 2, kc);  // the slot of plane t-4 takes plane t+2
   }
 };
 
@@ -505,16 +522,30 @@ __global__ void __launch_bounds__(F2_NT, 2) k_rbgs2(Grid win, Grid wout, Grid b,
     }
     g.rmask[k] = mk;
   }
-  g.out_tile = ly >= F2_H && ly < F2_H + F2_TY && lx0 >= F2_H && lx0 < F2_H + F2_TX;
+  const bool out_tile = ly >= F2_H && ly < F2_H + F2_TY && lx0 >= F2_H && lx0 < F2_H + F2_TX;
+  g.out0 = out_tile && g.xa < s && g.y < s;
+  g.out1 = out_tile && g.xa + 1 < s && g.y < s;
 #pragma unroll
   for (int m = 0; m < 6; ++m) g.R[m] = g.K[m] = g.BR[m] = g.BK[m] = 0.0f;
   const int tz = z0 - 3;  // first step; it needs planes tz-1 .. tz+1
-  for (int P = tz - 1; P <= tz + F2_D; ++P) g.issue(P);
+  g.par0 = (g.y + tz) & 1;
+  g.zst0 = z0 + 3;
+  g.zst1 = PERIODIC ? g.z1 + 2 : min(g.z1 + 2, s - 1);
+  g.out_off = (long long)(tz - 3) * wout.sz + (g.xa + g.y * wout.sy);
+  {
+    const int P0 = tz - 1;
+    const int zw = PERIODIC ? mc(P0) : P0;
+    g.iss_P = P0;
+    g.iss_z = zw;
+    g.iss_u = (long long)zw * win.sz;
+    g.iss_b = (long long)zw * b.sz;
+  }
+  for (int P = tz - 1; P <= tz + F2_D; ++P) g.issue();
   cp_async_wait<F2_D - 1>();  // groups tz-1 .. tz+1 have landed
-  g.template take<3>(tz - 1);
-  g.template take<4>(tz);
-  g.template take<5>(tz + 1);
-  g.template put<4>(tz);
+  g.template take<3>(tz - 1, g.par0 ^ 1);
+  g.template take<4>(tz, g.par0);
+  g.template take<5>(tz + 1, g.par0 ^ 1);
+  g.template put<4>(tz, g.par0);
   const int tend = g.z1 + 2;
   for (int t = tz; t <= tend; t += 6) {
     g.template step<0>(t);
