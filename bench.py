@@ -125,7 +125,7 @@ STRICT_RTOL = 1e-7
 # ncu dram__bytes_read.sum + dram__bytes_write.sum over the algorithmic bytes
 # of the kernel class's launches at 256^3 on the current kernels
 TRAFFIC_RATIO = {
-    "smooth0": (290.7e6 / 335.5e6, "k_rbgs2 pre + post at 256^3, "
+    "smooth0": (290.8e6 / 335.5e6, "k_rbgs2 pre + post at 256^3, "
                 "profiles/rbgs2_pm256_level0.md"),
     "defect": (328.2e6 / 335.5e6, "k_defect<0> at 256^3, "
                "profiles/defect_gather_deposit_pm256.md"),
