@@ -114,10 +114,16 @@ def _ics():
     return ics.workload_ics(WORKLOAD), ics.WORKLOADS[WORKLOAD]
 
 
+# particles reordered by cell at the start of every SORT_EVERY-th step
+# (--sort-every; 0: the initial order, compacted stably)
+SORT_EVERY = 32
+
+
 def _new_sim(pos, mom, ids, cfg, rtol, precision, guess="warm"):
     from paper_1709_04703_gb300.sim import Sim
     return Sim(pos, mom, ids, cfg["n"], cfg["box"], cfg["a_init"], cfg["a_final"],
-               cfg["steps"], rtol=rtol, precision=precision, max_vcycles=100, guess=guess)
+               cfg["steps"], rtol=rtol, precision=precision, max_vcycles=100, guess=guess,
+               sort_every=SORT_EVERY)
 
 
 STRICT_RTOL = 1e-7
@@ -158,7 +164,8 @@ def _variant(pos, mom, ids, cfg, K, rtol, precision, guess="warm", net=None,
     from paper_1709_04703_gb300.sim import Sim
     sim = Sim(pos, mom, ids, cfg["n"], cfg["box"], cfg["a_init"], cfg["a_final"],
               cfg["steps"], rtol=rtol, precision=precision, max_vcycles=100, guess=guess,
-              gravity=gravity, bc=bc, shrink=shrink, assignment=assignment)
+              gravity=gravity, bc=bc, shrink=shrink, assignment=assignment,
+              sort_every=SORT_EVERY)
     if net is not None:
         sim.set_guess(net)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -567,7 +574,8 @@ def run_ours(args):
                    "rtol_rule": "equal residual: max(1e-5, 10 x plain FP32 floor)"
                                 if args.rtol is None else "given",
                    "plain_fp32_floor": floor,
-                   "precision": args.precision, "parallelism": f"replicas x{ws}",
+                   "precision": args.precision, "sort_every": SORT_EVERY,
+                   "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (particles 537 MB, mesh 134 MB)"},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
@@ -593,6 +601,7 @@ def run_ours(args):
 
 
 def main():
+    global SORT_EVERY
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
@@ -605,6 +614,8 @@ def main():
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the plain-FP32 and learned-guess runs of the same steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sort-every", type=int, default=SORT_EVERY,
+                    help="reorder the particles by cell every k-th step (0: never)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--workload", choices=["pm256", "batch48", "shrink_table"], default="pm256")
     ap.add_argument("--table-n", type=int, default=512,
@@ -616,6 +627,7 @@ def main():
                     help="shrink_table: gravity solvers")
     args = ap.parse_args()
     args.steps_given = "--steps" in sys.argv
+    SORT_EVERY = max(0, args.sort_every)
     if args.impl == "reference":
         return run_reference(args)
     from paper_1709_04703_gb300 import build

@@ -113,6 +113,18 @@ typedef struct {
                             term is the CIC image of the ball (exact chord
                             integral, 16-point Gauss-Legendre over the tents);
                             the sphere needs PM_ASSIGN_CIC */
+  int32_t sort_every;    /* 0: the particle arrays keep their order (the
+                            initial order, compacted stably by the shrink);
+                            k > 0: at the start of every k-th step (step
+                            index a multiple of k) the active particles are
+                            reordered by the mesh cell of their CIC base
+                            node, as pm_sort_particles.  No result of a
+                            particle changes, only the order of the arrays
+                            and hence of the lightcone records; it keeps
+                            the deposit's atomics and the gather's loads
+                            coherent once clustering has scattered the
+                            initial order.  Single contexts only (a batch
+                            rejects k > 0) */
 } pm_config;
 
 /* Fill *cfg with defaults: 32^3 mesh and particles, 250 Mpc/h, Om=0.3,
@@ -241,6 +253,19 @@ pm_status pm_deposit_tsc(float* pos4_dev, const float* mom4_dev, int64_t n,
                          int32_t periodic, int64_t* rho_dev, int64_t* escaped_out,
                          void* stream);
 
+/* Reorder n particles by the mesh cell of their CIC base node: key
+ * ((k n + j) n + i) with i = floor(u_x - 1/2) mod n_mesh (likewise j, k;
+ * float32 subtraction, non-finite coordinates give 0), a stable sort (equal
+ * keys keep their input order), so the result is unique.  pos4_out and
+ * mom4_out (device, n float4 each, caller-owned, not overlapping the inputs)
+ * receive the records in that order; mom4_dev may be NULL (then mom4_out is
+ * not written).  An order of the data only: the deposit of the particles is
+ * unchanged (its integer sums do not depend on the order).  Work space is
+ * allocated and freed inside the call.  n_mesh in [1, 1024], n in
+ * [0, 2^31).  Synchronises stream. */
+pm_status pm_sort_particles(const float* pos4_dev, const float* mom4_dev, int64_t n,
+                            int32_t n_mesh, float* pos4_out, float* mom4_out, void* stream);
+
 typedef struct {
   int32_t step;          /* steps completed */
   double a;              /* current expansion factor */
@@ -308,6 +333,7 @@ enum {
   PM_PROF_COMPACT,      /* scan + stable scatter                            */
   PM_PROF_GUESS,        /* learned initial guess (network forward)          */
   PM_PROF_ADE,          /* explicit diffusion sweeps (PM_GRAVITY_DIFFUSION_ADE) */
+  PM_PROF_SORT,         /* particle order by cell (sort_every)              */
   PM_PROF_N
 };
 /* enable = 1 starts (and zeroes) the counters, 0 stops them. */

@@ -136,6 +136,22 @@ def cic_index(pos):
     return i.astype(np.int64), dq.astype(np.int64)
 
 
+def cell_order(pos, n):
+    """Permutation that orders particles by the mesh cell of their CIC base
+    node, stably (equal cells keep their input order).  Not a step of the
+    paper's method but a data layout of the library (its sort_every option):
+    key ((k n + j) n + i), i = floor(u_x - 1/2) mod n with the subtraction in
+    float32 (exact below 2^23), likewise j and k; a non-finite coordinate or
+    one beyond 1e9 counts as cell 0."""
+    u = np.asarray(pos, dtype=np.float32)
+    with np.errstate(invalid="ignore"):
+        v = np.floor(u - np.float32(0.5)).astype(np.float64)
+        ok = np.isfinite(v) & (np.abs(v) <= 1.0e9)
+    c = np.mod(np.where(ok, v, 0.0).astype(np.int64), n)
+    key = (c[:, 2] * n + c[:, 1]) * n + c[:, 0]
+    return np.argsort(key, kind="stable")
+
+
 def _valid(i, lo, s):
     return np.all((i >= lo) & (i + 1 <= lo + s - 1), axis=1)
 

@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ECUDA",
 # every entry point declared in include/pmshrink.h
 EXPORTED = [
     "pm_config_default", "pm_init", "pm_step", "pm_shrink", "pm_potential",
-    "pm_power_spectrum", "pm_power_spectrum_jing", "pm_deposit", "pm_deposit_tsc", "pm_stats", "pm_schedule",
+    "pm_power_spectrum", "pm_power_spectrum_jing", "pm_deposit", "pm_deposit_tsc", "pm_sort_particles", "pm_stats", "pm_schedule",
     "pm_get_particles", "pm_set_particles", "pm_get_lightcone", "pm_get_forces",
     "pm_get_potential", "pm_profile", "pm_profile_read", "pm_launch_count", "pm_last_error",
     "pm_destroy", "pm_shrink_static", "pm_shrink_static_error",
@@ -37,7 +37,7 @@ EXPORTED = [
     "pm_guess_last_error", "pm_guess_destroy", "pm_set_guess", "pm_capture",
 ]
 PROF_CLASSES = ["deposit", "source", "boundary", "smooth0", "transfer0", "coarse",
-                "defect", "correct", "gather", "compact", "guess", "ade"]
+                "defect", "correct", "gather", "compact", "guess", "ade", "sort"]
 
 
 class PmConfig(C.Structure):
@@ -48,7 +48,7 @@ class PmConfig(C.Structure):
         ("max_vcycles", C.c_int32), ("precision", C.c_int32), ("guess", C.c_int32),
         ("bc", C.c_int32), ("shrink", C.c_int32), ("buffer_cells", C.c_double),
         ("store_forces", C.c_int32), ("gravity", C.c_int32), ("c_eff_factor", C.c_double),
-        ("assignment", C.c_int32), ("domain", C.c_int32),
+        ("assignment", C.c_int32), ("domain", C.c_int32), ("sort_every", C.c_int32),
     ]
 
 
@@ -95,6 +95,7 @@ def load():
                                          P]),
         "pm_deposit": (I32, [P, P, I64, F, I32, I32, I32, I32, P, C.POINTER(I64), P]),
         "pm_deposit_tsc": (I32, [P, P, I64, F, I32, I32, I32, I32, P, C.POINTER(I64), P]),
+        "pm_sort_particles": (I32, [P, P, I64, I32, P, P, P]),
         "pm_stats": (I32, [P, C.POINTER(PmStats)]),
         "pm_schedule": (I32, [P, P, P, P, P]),
         "pm_get_particles": (I32, [P, P, P, I32, C.POINTER(I64)]),

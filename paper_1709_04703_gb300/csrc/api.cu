@@ -152,6 +152,7 @@ struct pm_ctx {
   double* bgm = nullptr;        // background moments (10), then at BGW_OFF the weights
   df* bgw = nullptr;            // per-axis mean-density weights w_g, g in [0, n)
   float* ballw = nullptr;       // spherical keep region: mean-density image, n^3
+  SortWork sortw{};             // particle order by cell (sort_every > 0)
   BallRule ball_rule{};         // its Gauss-Legendre rule
   std::vector<unsigned char> h_bg;  // host image of bgm + bgw
   unsigned long long* d_cnt = nullptr;  // [0] n_keep, [1] escaped
@@ -868,6 +869,8 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
   if (cfg->assignment != PM_ASSIGN_CIC &&
       (cfg->assignment != PM_ASSIGN_TSC || cfg->gravity != PM_GRAVITY_POISSON))
     return fail(nullptr, PM_EINVAL, "pm_init: assignment is CIC, or TSC with Poisson gravity");
+  if (cfg->sort_every < 0)
+    return fail(nullptr, PM_EINVAL, "pm_init: sort_every must be >= 0");
   if (cfg->gravity != PM_GRAVITY_POISSON &&
       ((cfg->gravity != PM_GRAVITY_DIFFUSION && cfg->gravity != PM_GRAVITY_DIFFUSION_ADE) ||
        !(cfg->c_eff_factor > 0) || cfg->precision != PM_MIXED ||
@@ -960,6 +963,14 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
     AL(ctx->ballw, sizeof(float) * (size_t)n * n * n);
     ctx->ball_rule = ball_rule();
   }
+  if (cfg->sort_every > 0) {
+    for (int q = 0; q < 2; ++q) {
+      AL(ctx->sortw.keys[q], sizeof(unsigned) * N);
+      AL(ctx->sortw.vals[q], sizeof(unsigned) * N);
+    }
+    AL(ctx->sortw.counts, sizeof(unsigned) * sort_counts_len(N));
+    AL(ctx->sortw.ghist, sizeof(unsigned) * sort_ghist_len());
+  }
   ctx->h_bg.assign(BGW_OFF + sizeof(df) * (size_t)n, 0);
   AL(ctx->d_cnt, sizeof(unsigned long long) * 4);
   ctx->d_overflow = (int*)(ctx->d_cnt + 3);  // read back with every sync_read
@@ -1018,6 +1029,18 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
     pm_status st = set_cube(ctx, lo, s, per, R0);
     if (st != PM_OK) return st;
     const long long N = ctx->n_active;
+    if (ctx->cfg.sort_every > 0 && k % ctx->cfg.sort_every == 0 && N > 1) {
+      // particle order by cell: keys (read x 16 B, write key + index 8 B),
+      // per pass a histogram (4 B) and a scatter (read and write key + index,
+      // 16 B), then the permutation (4 B) and both records (read and write,
+      // 64 B)
+      int es = prof_begin(ctx);
+      CK(launch_sort_particles(ctx->st, ctx->pos, ctx->mom, N, n, ctx->sortw, ctx->pos2,
+                               ctx->mom2));
+      prof_end(ctx, PM_PROF_SORT, es, (24.0 + 20.0 * sort_passes(n) + 68.0) * N);
+      std::swap(ctx->pos, ctx->pos2);
+      std::swap(ctx->mom, ctx->mom2);
+    }
     const double cells = (double)s * s * s;
     const bool diffusion = ctx->cfg.gravity != PM_GRAVITY_POISSON;
     const bool ade = ctx->cfg.gravity == PM_GRAVITY_DIFFUSION_ADE;
@@ -1330,6 +1353,51 @@ pm_status pm_deposit_tsc(float* pos4_dev, const float* mom4_dev, int64_t n, floa
                          int64_t* rho_dev, int64_t* escaped_out, void* stream) {
   return deposit_any(true, "pm_deposit_tsc", pos4_dev, mom4_dev, n, drift_coef, n_mesh, lo,
                      side, periodic, rho_dev, escaped_out, stream);
+}
+
+pm_status pm_sort_particles(const float* pos4_dev, const float* mom4_dev, int64_t n,
+                            int32_t n_mesh, float* pos4_out, float* mom4_out, void* stream) {
+  pm_ctx* ctx = nullptr;
+  if (n < 0 || n >= (1LL << 31) || n_mesh < 1 || n_mesh > 1024)
+    return fail(ctx, PM_EINVAL, "pm_sort_particles: n in [0, 2^31), n_mesh in [1, 1024]");
+  if (n == 0) return PM_OK;
+  if (!pos4_dev || !pos4_out || (mom4_dev && !mom4_out))
+    return fail(ctx, PM_EINVAL, "pm_sort_particles: NULL argument");
+  const size_t bytes = sizeof(float4) * (size_t)n;
+  auto overlap = [&](const void* a, const void* b) {
+    const char *x = (const char*)a, *y = (const char*)b;
+    return a && b && x < y + bytes && y < x + bytes;
+  };
+  if (overlap(pos4_out, pos4_dev) || overlap(pos4_out, mom4_dev) ||
+      (mom4_dev && (overlap(mom4_out, pos4_dev) || overlap(mom4_out, mom4_dev) ||
+                    overlap(mom4_out, pos4_out))))
+    return fail(ctx, PM_EINVAL, "pm_sort_particles: outputs overlap the inputs or each other");
+  cudaStream_t st = (cudaStream_t)stream;
+  SortWork w{};
+  void** bufs[] = {(void**)&w.keys[0], (void**)&w.keys[1], (void**)&w.vals[0],
+                   (void**)&w.vals[1], (void**)&w.counts, (void**)&w.ghist};
+  const size_t sizes[] = {sizeof(unsigned) * (size_t)n, sizeof(unsigned) * (size_t)n,
+                          sizeof(unsigned) * (size_t)n, sizeof(unsigned) * (size_t)n,
+                          sizeof(unsigned) * sort_counts_len(n),
+                          sizeof(unsigned) * sort_ghist_len()};
+  auto release = [&]() {
+    for (void** b : bufs)
+      if (*b) cudaFree(*b);
+  };
+  for (int q = 0; q < 6; ++q) {
+    if (cudaMalloc(bufs[q], sizes[q]) != cudaSuccess) {
+      cudaGetLastError();
+      release();
+      return fail(ctx, PM_ENOMEM, "pm_sort_particles: cudaMalloc failed");
+    }
+  }
+  cudaError_t e = launch_sort_particles(st, (const float4*)pos4_dev, (const float4*)mom4_dev, n,
+                                        n_mesh, w, (float4*)pos4_out, (float4*)mom4_out);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  release();
+  if (e != cudaSuccess)
+    return fail(ctx, PM_ECUDA, std::string("pm_sort_particles: ") + cudaGetErrorString(e));
+  return PM_OK;
 }
 
 namespace {
@@ -1657,7 +1725,8 @@ void pm_destroy(pm_ctx* ctx) {
                   ctx->f_lo, ctx->prev_hi, ctx->prev_lo,
                   ctx->partial, ctx->partial_m,
                   ctx->counter, ctx->d_scal, ctx->bgm, ctx->d_cnt, ctx->ballw,
-                  ctx->nn_in, ctx->nn_out, ctx->grad};
+                  ctx->nn_in, ctx->nn_out, ctx->grad, ctx->sortw.keys[0], ctx->sortw.keys[1],
+                  ctx->sortw.vals[0], ctx->sortw.vals[1], ctx->sortw.counts, ctx->sortw.ghist};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (float* p : ctx->lu) if (p) cudaFree(p);
@@ -2034,6 +2103,9 @@ pm_status pm_batch_init(int32_t n_real, const pm_config* cfgs, const float* cons
     if (cfgs[r].shrink == PM_SHRINK_RECORD)
       return bfail(nullptr, PM_EINVAL, "pm_batch_init: the fixed-box lightcone record runs "
                                        "per context");
+    if (cfgs[r].sort_every != 0)
+      return bfail(nullptr, PM_EINVAL, "pm_batch_init: the particle order by cell runs "
+                                       "per context (sort_every = 0)");
     if (cfgs[r].n_steps != cfgs[0].n_steps || cfgs[r].a_init != cfgs[0].a_init ||
         cfgs[r].a_final != cfgs[0].a_final)
       return bfail(nullptr, PM_EINVAL, "pm_batch_init: realisations must share the a schedule");

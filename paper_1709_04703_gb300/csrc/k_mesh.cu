@@ -12,9 +12,12 @@ namespace cg = cooperative_groups;
 namespace pm {
 
 // ---------------------------------------------------------------------------
-// K1: x += p * c0 (float32, two roundings), then 8 int64 atomics per particle.
+// K1: x += p * c0 (float32, two roundings), then the 8 int64 CIC weights.
 // Periodic: nodes wrap mod n.  Open: a particle with a node outside the cube
-// [lo, lo+s) deposits nothing and is counted as escaped.
+// [lo, lo+s) deposits nothing and is counted as escaped.  The weights of
+// lanes that share a cell, and the shared column of x-neighbouring cells,
+// are summed within the warp first (integers: the same totals), so that a
+// cell-ordered warp issues about one set of atomics per cell.
 // ---------------------------------------------------------------------------
 template <bool DRIFT>
 __device__ __forceinline__ void d_drift_deposit(const BI& bi, 
@@ -78,23 +81,51 @@ __device__ __forceinline__ void d_drift_deposit(const BI& bi,
     const unsigned long long wz0 = 65536u - dz, wz1 = dz;
     const unsigned long long a00 = wy0 * wz0, a10 = wy1 * wz0, a01 = wy0 * wz1,
                              a11 = wy1 * wz1;
-    // the x1 column of lane l is the x0 column of lane l+1 when their cells
-    // are x-neighbours: lane l+1 adds lane l's x1 weights to its own atomics
+    // contributions to the x0 column (b) and the x1 column (c) of the cell
+    unsigned long long b00 = wx0 * a00, b10 = wx0 * a10, b01 = wx0 * a01, b11 = wx0 * a11;
     unsigned long long c00 = wx1 * a00, c10 = wx1 * a10, c01 = wx1 * a01, c11 = wx1 * a11;
-    const int px1 = __shfl_up_sync(FULL, x1, 1), py0 = __shfl_up_sync(FULL, y0, 1);
-    const int pz0 = __shfl_up_sync(FULL, z0, 1);
-    const bool pact = __shfl_up_sync(FULL, act ? 1 : 0, 1) != 0;
-    const unsigned long long q00 = __shfl_up_sync(FULL, c00, 1), q10 = __shfl_up_sync(FULL, c10, 1);
-    const unsigned long long q01 = __shfl_up_sync(FULL, c01, 1), q11 = __shfl_up_sync(FULL, c11, 1);
-    const bool take = lane > 0 && act && pact && px1 == x0 && py0 == y0 && pz0 == z0;
-    const bool given = __shfl_down_sync(FULL, take ? 1 : 0, 1) != 0 && lane < 31;
-    if (act) {
+    // 1. lanes in the cell of the lane before them continue its run; each
+    // run's eight sums are reduced onto its first lane (the head), which
+    // alone issues atomics
+    const int pact = __shfl_up_sync(FULL, act ? 1 : 0, 1);
+    const int sx0 = __shfl_up_sync(FULL, x0, 1), sy0 = __shfl_up_sync(FULL, y0, 1);
+    const int sz0 = __shfl_up_sync(FULL, z0, 1);
+    const bool same = lane > 0 && act && pact != 0 && sx0 == x0 && sy0 == y0 && sz0 == z0;
+    const unsigned cont = __ballot_sync(FULL, same);
+    if (cont) {
+      // last lane of my run: the one before the next lane that does not continue
+      const unsigned brk = ~cont & (0xfffffffeu << lane);
+      const int rend = brk ? __ffs(brk) - 2 : 31;
+      for (int o = 1; o < 32; o <<= 1) {
+        const bool in = lane + o <= rend;
+        if (!__any_sync(FULL, in)) break;
+#define PM_RUN_ADD(v) { const unsigned long long t_ = __shfl_down_sync(FULL, v, o); if (in) v += t_; }
+        PM_RUN_ADD(b00) PM_RUN_ADD(b10) PM_RUN_ADD(b01) PM_RUN_ADD(b11)
+        PM_RUN_ADD(c00) PM_RUN_ADD(c10) PM_RUN_ADD(c01) PM_RUN_ADD(c11)
+#undef PM_RUN_ADD
+      }
+    }
+    // 2. the x1 column of a head is the x0 column of the next head when their
+    // cells are x-neighbours: the next head adds it to its own atomics
+    const bool head = act && !same;
+    const unsigned heads = __ballot_sync(FULL, head);
+    const unsigned below = heads & ((1u << lane) - 1u);
+    const int ph = below ? 31 - __clz(below) : lane;
+    const int px1 = __shfl_sync(FULL, x1, ph), py0 = __shfl_sync(FULL, y0, ph);
+    const int pz0 = __shfl_sync(FULL, z0, ph);
+    const unsigned long long q00 = __shfl_sync(FULL, c00, ph), q10 = __shfl_sync(FULL, c10, ph);
+    const unsigned long long q01 = __shfl_sync(FULL, c01, ph), q11 = __shfl_sync(FULL, c11, ph);
+    const bool take = head && below != 0u && px1 == x0 && py0 == y0 && pz0 == z0;
+    const unsigned takes = __ballot_sync(FULL, take);
+    const unsigned above = heads & (0xfffffffeu << lane);
+    const bool given = above != 0u && ((takes >> (__ffs(above) - 1)) & 1u);
+    if (head) {
       const long long r00 = ((long long)z0 * n + y0) * n, r10 = ((long long)z0 * n + y1) * n;
       const long long r01 = ((long long)z1 * n + y0) * n, r11 = ((long long)z1 * n + y1) * n;
-      atomicAdd(rho + r00 + x0, wx0 * a00 + (take ? q00 : 0ull));
-      atomicAdd(rho + r10 + x0, wx0 * a10 + (take ? q10 : 0ull));
-      atomicAdd(rho + r01 + x0, wx0 * a01 + (take ? q01 : 0ull));
-      atomicAdd(rho + r11 + x0, wx0 * a11 + (take ? q11 : 0ull));
+      atomicAdd(rho + r00 + x0, b00 + (take ? q00 : 0ull));
+      atomicAdd(rho + r10 + x0, b10 + (take ? q10 : 0ull));
+      atomicAdd(rho + r01 + x0, b01 + (take ? q01 : 0ull));
+      atomicAdd(rho + r11 + x0, b11 + (take ? q11 : 0ull));
       if (!given) {
         atomicAdd(rho + r00 + x1, c00);
         atomicAdd(rho + r10 + x1, c10);

@@ -13,6 +13,22 @@ void note_launch();
 double shrink_radius_cells(int n, double box, double om, double ol, double buffer, double a);
 void shrink_keep_bounds(int n, double R, float* klo, float* khi);
 
+// k_sort.cu: stable radix sort of the particles by the cell of their CIC
+// base node (keys: ((z n + y) n + x) of floor(u - 1/2) wrapped into [0, n))
+struct SortWork {
+  unsigned* keys[2];  // N each
+  unsigned* vals[2];  // N each
+  unsigned* counts;   // sort_counts_len(N)
+  unsigned* ghist;    // sort_ghist_len()
+};
+int sort_passes(int n);
+size_t sort_counts_len(long long N);
+size_t sort_ghist_len();
+// pos_out/mom_out <- pos/mom in the sorted order (must not alias them)
+cudaError_t launch_sort_particles(cudaStream_t st, const float4* pos, const float4* mom,
+                                  long long N, int n, const SortWork& w, float4* pos_out,
+                                  float4* mom_out);
+
 // k_mesh.cu
 void launch_drift_deposit(cudaStream_t st, int grid, float4* pos, const float4* mom,
                           long long N, float c0, bool drift, int n, int lo, int s,

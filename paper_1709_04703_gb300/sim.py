@@ -169,7 +169,7 @@ class Sim:
                  rtol=1e-7, precision="mixed", guess="warm", bc="paper",
                  shrink=True, buffer_cells=1.0, max_vcycles=50, store_forces=False,
                  omega_m=0.3, omega_l=0.7, host_init=False, gravity="poisson",
-                 c_eff_factor=0.019, assignment="cic", domain="cube"):
+                 c_eff_factor=0.019, assignment="cic", domain="cube", sort_every=0):
         lib = L.load()
         cfg = L.PmConfig()
         lib.pm_config_default(C.byref(cfg))
@@ -189,6 +189,7 @@ class Sim:
         cfg.c_eff_factor = float(c_eff_factor)
         cfg.assignment = {"cic": L.PM_ASSIGN_CIC, "tsc": L.PM_ASSIGN_TSC}[assignment]
         cfg.domain = {"cube": L.PM_DOMAIN_CUBE, "sphere": L.PM_DOMAIN_SPHERE}[domain]
+        cfg.sort_every = int(sort_every)
         self.cfg = cfg
         self.n_particles = int(len(pos))
         # the context runs on its own stream so that its V-cycle can be
@@ -355,6 +356,20 @@ class Sim:
                                                   C.byref(b)))
             out[name] = {"ms": t.value, "groups": g.value, "bytes": b.value}
         return out
+
+
+def sort_particles(pos4_dev, mom4_dev, n_mesh):
+    """(pos4, mom4) reordered by the mesh cell of the CIC base node (stable);
+    mom4_dev may be None."""
+    import torch
+    lib = L.load()
+    n = pos4_dev.shape[0]
+    po = torch.empty_like(pos4_dev)
+    mo = torch.empty_like(mom4_dev) if mom4_dev is not None else None
+    code = lib.pm_sort_particles(_ptr(pos4_dev), _ptr(mom4_dev), n, int(n_mesh), _ptr(po),
+                                 _ptr(mo), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    L.check(code, None)
+    return po, mo
 
 
 def power_spectrum(pos4_dev, box, n_mesh, n_bins, subtract_shot=True):

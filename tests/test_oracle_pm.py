@@ -578,3 +578,38 @@ def test_uniform_density_in_the_ball_has_zero_contrast():
     for r0 in np.arange(R - 2.0, R + 1.5, 0.5):    # shells across the surface
         sel = (r >= r0) & (r < r0 + 0.5)
         assert abs(d[sel].mean()) < 0.03, (r0, d[sel].mean())
+
+
+def test_cell_order_worked_example():
+    """A hand-sorted case: cells of the CIC base node, z slowest, x fastest,
+    ties in input order, wrap of floor(u - 1/2) = -1 to n - 1."""
+    n = 4
+    pos = np.array([[1.7, 0.5, 0.5],    # cell (1, 0, 0): key 1
+                    [0.5, 0.5, 0.5],    # (0, 0, 0): key 0
+                    [0.4, 0.5, 0.5],    # x cell -1 -> 3: key 3
+                    [1.5, 2.6, 0.5],    # (1, 2, 0): key 9
+                    [1.9, 0.6, 0.99],   # (1, 0, 0): key 1, after particle 0
+                    [0.5, 0.5, 1.5],    # (0, 0, 1): key 16
+                    [3.6, 3.6, 3.6],    # (3, 3, 3): key 63
+                    [0.5, 0.5, 0.2]])   # z cell -1 -> 3: key 48
+    np.testing.assert_array_equal(pm.cell_order(pos, n), [1, 0, 4, 2, 3, 5, 7, 6])
+
+
+def test_cell_order_is_a_stable_sort_by_cell():
+    """Keys non-decreasing along the order, input order kept among equal
+    keys, every particle once; keys read from the CIC base node."""
+    rng = np.random.default_rng(21)
+    n = 16
+    centres = rng.integers(0, n, (40, 3)) + 0.5
+    pos = (centres[rng.integers(0, 40, 3000)] + rng.uniform(-0.4, 0.4, (3000, 3))) % n
+    o = pm.cell_order(pos.astype(np.float32), n)
+    assert sorted(o.tolist()) == list(range(3000))
+    i, _ = pm.cic_index(pos.astype(np.float32))
+    i %= n
+    key = (i[:, 2] * n + i[:, 1]) * n + i[:, 0]
+    k = key[o]
+    assert np.all(np.diff(k) >= 0)
+    assert np.all(np.diff(o)[np.diff(k) == 0] > 0)
+    # non-finite coordinates count as cell 0
+    bad = np.array([[np.nan, 1.5, 1.5], [np.inf, 0.5, 0.5], [0.5, 0.5, 0.5]], np.float32)
+    assert pm.cell_order(bad, n).tolist() == [1, 2, 0]
