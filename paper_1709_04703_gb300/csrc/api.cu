@@ -21,6 +21,10 @@ std::atomic<long long> g_launches{0};
 }  // namespace
 
 void pm::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+bool pm::pdl_enabled() {
+  static const bool on = getenv("PM_NO_PDL") == nullptr;
+  return on;
+}
 
 namespace {
 

@@ -146,6 +146,8 @@ __global__ void __launch_bounds__(256) k_drift_deposit(
     float4* __restrict__ pos, const float4* __restrict__ mom, long long N,
     float c0, int n, int lo, int s, int periodic,
     unsigned long long* __restrict__ rho, unsigned long long* __restrict__ escaped) {
+  pdl_wait();
+  pdl_release();
   d_drift_deposit<DRIFT>(bi_native(), pos, mom, N, c0, n, lo, s, periodic, rho, escaped);
 }
 
@@ -155,11 +157,11 @@ void launch_drift_deposit(cudaStream_t st, int grid, float4* pos, const float4* 
                           unsigned long long* escaped) {
   if (N <= 0) return;
   if (drift)
-    k_drift_deposit<true><<<grid, 256, 0, st>>>(pos, mom, N, c0, n, lo, s, periodic, rho,
-                                                escaped);
+    launch_pdl(k_drift_deposit<true>, dim3(grid), dim3(256), 0, st, pos, mom, N, c0, n, lo, s,
+               periodic, rho, escaped);
   else
-    k_drift_deposit<false><<<grid, 256, 0, st>>>(pos, mom, N, c0, n, lo, s, periodic, rho,
-                                                 escaped);
+    launch_pdl(k_drift_deposit<false>, dim3(grid), dim3(256), 0, st, pos, mom, N, c0, n, lo, s,
+               periodic, rho, escaped);
   note_launch();
 }
 
@@ -593,6 +595,8 @@ __global__ void __launch_bounds__(256) k_source(
     double* __restrict__ partial_f2,
     __int128* __restrict__ partial_m, unsigned int* counter, double* __restrict__ out,
     const double* __restrict__ bgm, double invM2_hi, int* __restrict__ overflow) {
+  pdl_wait();
+  pdl_release();
   d_source<MOMENTS>(bi_native(), rho, n, lo, s, fh, fl, invM, S, bgw, ballw, partial_f2,
                     partial_m, counter, out, bgm, invM2_hi, overflow);
 }
@@ -612,13 +616,13 @@ void launch_source(cudaStream_t st, int grid, unsigned long long* rho, int n, in
   Sd.hi = (float)S;
   Sd.lo = (float)(S - (double)Sd.hi);
   if (moments)
-    k_source<true><<<source_grid(s), dim3(32, 8), 0, st>>>(rho, n, lo, s, fh, fl, invMd, Sd, bgw, ballw,
-                                         partial_f2, (__int128*)partial_m, counter, out,
-                                         bgm, invM, overflow);
+    launch_pdl(k_source<true>, source_grid(s), dim3(32, 8), 0, st, rho, n, lo, s, fh, fl, invMd,
+               Sd, bgw, ballw, partial_f2, (__int128*)partial_m, counter, out, bgm, invM,
+               overflow);
   else
-    k_source<false><<<source_grid(s), dim3(32, 8), 0, st>>>(rho, n, lo, s, fh, fl, invMd, Sd, bgw, ballw,
-                                          partial_f2, (__int128*)partial_m, counter, out,
-                                          bgm, invM, overflow);
+    launch_pdl(k_source<false>, source_grid(s), dim3(32, 8), 0, st, rho, n, lo, s, fh, fl, invMd,
+               Sd, bgw, ballw, partial_f2, (__int128*)partial_m, counter, out, bgm, invM,
+               overflow);
   note_launch();
 }
 

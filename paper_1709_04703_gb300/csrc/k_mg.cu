@@ -104,6 +104,8 @@ __device__ __forceinline__ void d_rbgs(const BI& bi, Grid u, Grid b, float h2, i
 
 __global__ void __launch_bounds__(256) k_rbgs(Grid u, Grid b, float h2, int color,
                                               int periodic, float gam, int zero_start, float d0) {
+  pdl_wait();
+  pdl_release();
   d_rbgs(bi_native(), u, b, h2, color, periodic, gam, zero_start, d0);
 }
 
@@ -168,6 +170,8 @@ __device__ __forceinline__ void d_resid_restrict(const BI& bi, Grid u, Grid b, f
 __global__ void __launch_bounds__(256) k_resid_restrict(Grid u, Grid b, float inv_h2,
                                                         Grid uc, Grid bc, int periodic,
                                                         float gam, float d0) {
+  pdl_wait();
+  pdl_release();
   d_resid_restrict(bi_native(), u, b, inv_h2, uc, bc, periodic, gam, d0);
 }
 
@@ -221,6 +225,8 @@ __device__ __forceinline__ void d_prolong(const BI& bi, Grid uc, Grid u, int per
 
 __global__ void __launch_bounds__(256) k_prolong(Grid uc, Grid u, int periodic,
                                                  float gam_c) {
+  pdl_wait();
+  pdl_release();
   d_prolong(bi_native(), uc, u, periodic, gam_c);
 }
 
@@ -229,6 +235,8 @@ __global__ void __launch_bounds__(256) k_prolong(Grid uc, Grid u, int periodic,
 // its 8 fine children take prolong_value's arithmetic on those values.
 __global__ void __launch_bounds__(256) k_prolong_to(Grid uc, Grid u, Grid w, int periodic,
                                                     float gam_c) {
+  pdl_wait();
+  pdl_release();
   const int sc = uc.s;
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
@@ -483,6 +491,8 @@ struct Rbgs2 {
 template <bool PERIODIC, bool SIMPLE, bool ZERO>
 __global__ void __launch_bounds__(F2_NT, 2) k_rbgs2(Grid win, Grid wout, Grid b, float h2,
                                                     float gam, float d0, int zc) {
+  pdl_wait();
+  pdl_release();
   extern __shared__ float f2_smem[];
   const int s = wout.s;
   const int ly = threadIdx.x / F2_PW, lx0 = 2 * (threadIdx.x - ly * F2_PW);
@@ -592,7 +602,7 @@ void launch_rbgs2(cudaStream_t st, Grid win, Grid wout, Grid b, float h2, int pe
             (unsigned)((wout.s + zc - 1) / zc));
   const bool simple = (periodic || gam == 0.0f) && d0 == 6.0f;
 #define PM_RBGS2(P, S, Z) \
-  k_rbgs2<P, S, Z><<<grid, F2_NT, F2_SMEM, st>>>(win, wout, b, h2, gam, d0, zc)
+  launch_pdl(k_rbgs2<P, S, Z>, grid, dim3(F2_NT), F2_SMEM, st, win, wout, b, h2, gam, d0, zc)
   if (periodic && simple) {
     if (zero_start) PM_RBGS2(true, true, true); else PM_RBGS2(true, true, false);
   } else if (periodic) {
@@ -826,6 +836,8 @@ constexpr int CMG_SMEM_FLOATS = 11776;  // 16^3 -> 8^3 -> 4^3 needs 11720
 __global__ void __launch_bounds__(1024) k_coarse_mg(Grid u, Grid b, int level, int periodic,
                                                     int coarse_sweeps, int zero_top,
                                                     float sig0) {
+  pdl_wait();
+  pdl_release();
   __shared__ float sm[CMG_SMEM_FLOATS];
   __shared__ float red[32];
   CmgArgs a{periodic, level, coarse_sweeps, sig0};
@@ -846,7 +858,8 @@ __global__ void __launch_bounds__(1024) k_coarse_mg(Grid u, Grid b, int level, i
 
 void launch_coarse_mg(cudaStream_t st, Grid u, Grid b, int level, int periodic,
                       int coarse_sweeps, bool zero_top, float sig0) {
-  k_coarse_mg<<<1, 1024, 0, st>>>(u, b, level, periodic, coarse_sweeps, zero_top ? 1 : 0, sig0);
+  launch_pdl(k_coarse_mg, dim3(1), dim3(1024), 0, st, u, b, level, periodic, coarse_sweeps,
+             zero_top ? 1 : 0, sig0);
   note_launch();
 }
 
@@ -857,14 +870,14 @@ static inline dim3 grid_full(int s) { return dim3((unsigned)((s + 31) / 32), (un
 
 void launch_rbgs(cudaStream_t st, Grid u, Grid b, float h2, int color, int periodic,
                  float gam, bool zero_start, float d0) {
-  k_rbgs<<<grid_half(u.s), dim3(32, 8), 0, st>>>(u, b, h2, color, periodic, gam,
-                                                 zero_start ? 1 : 0, d0);
+  launch_pdl(k_rbgs, grid_half(u.s), dim3(32, 8), 0, st, u, b, h2, color, periodic, gam,
+             zero_start ? 1 : 0, d0);
   note_launch();
 }
 void launch_resid_restrict(cudaStream_t st, Grid u, Grid b, float inv_h2, Grid uc, Grid bc,
                            int periodic, float gam, float d0) {
-  k_resid_restrict<<<grid_full(uc.s), dim3(32, 8), 0, st>>>(u, b, inv_h2, uc, bc, periodic,
-                                                            gam, d0);
+  launch_pdl(k_resid_restrict, grid_full(uc.s), dim3(32, 8), 0, st, u, b, inv_h2, uc, bc,
+             periodic, gam, d0);
   note_launch();
 }
 // ghost layer of src copied into d1 and d2 (same side, any layouts)
@@ -892,11 +905,11 @@ void launch_copy_ghosts(cudaStream_t st, Grid src, Grid d1, Grid d2) {
 }
 
 void launch_prolong_to(cudaStream_t st, Grid uc, Grid u, Grid w, int periodic, float gam_c) {
-  k_prolong_to<<<grid_full(uc.s), dim3(32, 8), 0, st>>>(uc, u, w, periodic, gam_c);
+  launch_pdl(k_prolong_to, grid_full(uc.s), dim3(32, 8), 0, st, uc, u, w, periodic, gam_c);
   note_launch();
 }
 void launch_prolong(cudaStream_t st, Grid uc, Grid u, int periodic, float gam_c) {
-  k_prolong<<<grid_full(u.s), dim3(32, 8), 0, st>>>(uc, u, periodic, gam_c);
+  launch_pdl(k_prolong, grid_full(u.s), dim3(32, 8), 0, st, uc, u, periodic, gam_c);
   note_launch();
 }
 
@@ -1055,6 +1068,8 @@ __global__ void __launch_bounds__(256) k_defect(Grid ph, Grid pl, Grid e, Grid q
                                                 int write_r, double* __restrict__ partial,
                                                 unsigned int* counter, double* __restrict__ out,
                                                 float d0, float d0l) {
+  pdl_wait();
+  pdl_release();
   d_defect<CORRECT>(bi_native(), ph, pl, e, qh, ql, fh, fl, rb, periodic, write_r, partial,
                     counter, out, d0, d0l);
 }
@@ -1072,18 +1087,18 @@ void launch_defect(cudaStream_t st, Grid ph, Grid pl, const Grid* e, Grid qh, Gr
                    unsigned int* counter, double* out, double d0) {
   const float d0h = (float)d0, d0l = (float)(d0 - (double)d0h);
   if (e)
-    k_defect<true><<<grid_defect(ph.s), dim3(32, 8), 0, st>>>(
-        ph, pl, *e, qh, ql, fh, fl, rb, periodic, write_r ? 1 : 0, partial, counter, out, d0h,
-        d0l);
+    launch_pdl(k_defect<true>, grid_defect(ph.s), dim3(32, 8), 0, st, ph, pl, *e, qh, ql, fh, fl,
+               rb, periodic, write_r ? 1 : 0, partial, counter, out, d0h, d0l);
   else
-    k_defect<false><<<grid_defect(ph.s), dim3(32, 8), 0, st>>>(
-        ph, pl, ph, qh, ql, fh, fl, rb, periodic, write_r ? 1 : 0, partial, counter, out, d0h,
-        d0l);
+    launch_pdl(k_defect<false>, grid_defect(ph.s), dim3(32, 8), 0, st, ph, pl, ph, qh, ql, fh,
+               fl, rb, periodic, write_r ? 1 : 0, partial, counter, out, d0h, d0l);
   note_launch();
 }
 
 // Phi (hi, lo) += e.
 __global__ void __launch_bounds__(256) k_correct(Grid ph, Grid pl, Grid e) {
+  pdl_wait();
+  pdl_release();
   const int s = ph.s;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -1096,7 +1111,7 @@ __global__ void __launch_bounds__(256) k_correct(Grid ph, Grid pl, Grid e) {
 }
 
 void launch_correct(cudaStream_t st, Grid ph, Grid pl, Grid e) {
-  k_correct<<<grid_full(ph.s), dim3(32, 8), 0, st>>>(ph, pl, e);
+  launch_pdl(k_correct, grid_full(ph.s), dim3(32, 8), 0, st, ph, pl, e);
   note_launch();
 }
 
@@ -1162,11 +1177,13 @@ __device__ __forceinline__ void d_predict(const BI& bi, Grid ph, Grid pl, Grid q
 
 __global__ void __launch_bounds__(256) k_predict(Grid ph, Grid pl, Grid qh, Grid ql, float w,
                                                  int pair) {
+  pdl_wait();
+  pdl_release();
   d_predict(bi_native(), ph, pl, qh, ql, w, pair);
 }
 
 void launch_predict(cudaStream_t st, Grid ph, Grid pl, Grid qh, Grid ql, float w, bool pair) {
-  k_predict<<<grid_full(ph.s), dim3(32, 8), 0, st>>>(ph, pl, qh, ql, w, pair ? 1 : 0);
+  launch_pdl(k_predict, grid_full(ph.s), dim3(32, 8), 0, st, ph, pl, qh, ql, w, pair ? 1 : 0);
   note_launch();
 }
 

@@ -233,6 +233,8 @@ __global__ void __launch_bounds__(KT) k_gather_kick_drift(
     int n, int lo, int s, int periodic, float kick, float c2, int do_flag, float klo, float khi,
     KeepBall kb, unsigned char* __restrict__ flags, unsigned int* __restrict__ block_keep,
     float4* __restrict__ forces, unsigned long long* __restrict__ escaped) {
+  pdl_wait();
+  pdl_release();
   d_gather_kick_drift<GF>(bi_native(), pos, mom, N, ph, pl, G, n, lo, s, periodic, kick, c2,
                           do_flag, klo, khi, kb, flags, block_keep, forces, escaped);
 }
@@ -243,6 +245,8 @@ __global__ void __launch_bounds__(KT) k_gather_kick_drift(
 __global__ void __launch_bounds__(256) k_grad(const float* __restrict__ ph,
                                               const float* __restrict__ pl, int n, int lo,
                                               int s, int periodic, float4* __restrict__ G) {
+  pdl_wait();
+  pdl_release();
   const int P = n + 2;
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
@@ -402,20 +406,20 @@ void launch_gather_kick_drift(cudaStream_t st, float4* pos, float4* mom, long lo
                               unsigned long long* escaped) {
   if (N <= 0) return;
   if (G)
-    k_gather_kick_drift<true><<<gkd_blocks(N), KT, 0, st>>>(
-        pos, mom, N, ph, pl, G, n, lo, s, periodic, kick, c2, do_flag ? 1 : 0, klo, khi, kb,
-        flags, block_keep, forces, escaped);
+    launch_pdl(k_gather_kick_drift<true>, dim3(gkd_blocks(N)), dim3(KT), 0, st, pos, mom, N, ph,
+               pl, G, n, lo, s, periodic, kick, c2, do_flag ? 1 : 0, klo, khi, kb, flags,
+               block_keep, forces, escaped);
   else
-    k_gather_kick_drift<false><<<gkd_blocks(N), KT, 0, st>>>(
-        pos, mom, N, ph, pl, G, n, lo, s, periodic, kick, c2, do_flag ? 1 : 0, klo, khi, kb,
-        flags, block_keep, forces, escaped);
+    launch_pdl(k_gather_kick_drift<false>, dim3(gkd_blocks(N)), dim3(KT), 0, st, pos, mom, N, ph,
+               pl, G, n, lo, s, periodic, kick, c2, do_flag ? 1 : 0, klo, khi, kb, flags,
+               block_keep, forces, escaped);
   note_launch();
 }
 
 void launch_grad(cudaStream_t st, const float* ph, const float* pl, int n, int lo, int s,
                  int periodic, float4* G) {
   dim3 grid((unsigned)((s + 31) / 32), (unsigned)((s + 7) / 8), (unsigned)s);
-  k_grad<<<grid, dim3(32, 8), 0, st>>>(ph, pl, n, lo, s, periodic, G);
+  launch_pdl(k_grad, grid, dim3(32, 8), 0, st, ph, pl, n, lo, s, periodic, G);
   note_launch();
 }
 

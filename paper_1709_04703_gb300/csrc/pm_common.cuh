@@ -32,6 +32,16 @@ __device__ __forceinline__ BI bi_native() {
             (int)gridDim.x, (int)gridDim.y, (int)gridDim.z};
 }
 
+// Programmatic dependent launch (the V-cycle's kernels): a kernel launched
+// with that attribute may be scheduled while its predecessor in the stream
+// still runs, so it waits for the predecessor's completion (and memory)
+// before its first memory access, then lets its own successor be scheduled.
+// Both are no-ops in a kernel launched normally.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Neighbour index along one axis: wraps when periodic, else may reach the
 // ghost at -1 / s.
 __device__ __forceinline__ int wrap_m(int i, int s, int periodic) {

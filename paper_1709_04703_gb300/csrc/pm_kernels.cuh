@@ -8,6 +8,25 @@ namespace pm {
 // Counts kernel launches made by the library (pm_launch_count).
 void note_launch();
 
+// Launch with the programmatic-stream-serialization attribute (the kernel
+// starts with pdl_wait); a normal launch when PM_NO_PDL is set.
+bool pdl_enabled();
+template <typename... Exp, typename... Act>
+void launch_pdl(void (*k)(Exp...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                Act&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, k, static_cast<Exp>(args)...);
+}
+
 // pm_shrink's keep rule: R = chi(a)/cell + buffer (cells), and the exact
 // float bounds of |x - n/2| <= R (everything kept while R > n/2 - 1).
 double shrink_radius_cells(int n, double box, double om, double ol, double buffer, double a);
