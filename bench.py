@@ -506,6 +506,11 @@ def run_ours(args):
                                                            "mixed"),
                    f"plain_fp32_rtol_{STRICT_RTOL:g}": _variant(pos, mom, ids, cfg, 1,
                                                                 STRICT_RTOL, "fp32")}
+        # FP64 everywhere: potential, source and every multigrid level in
+        # double, at the same tolerance and at 1e-7
+        compare["plain_fp64"] = _variant(pos, mom, ids, cfg, K, rtol, "fp64")
+        compare[f"plain_fp64_rtol_{STRICT_RTOL:g}"] = _variant(pos, mom, ids, cfg, K,
+                                                               STRICT_RTOL, "fp64")
         # the paper's diffusion-equation gravity (two implicit half-substeps)
         compare["diffusion_gravity"] = _variant(pos, mom, ids, cfg, K, rtol, "mixed",
                                                 gravity="diffusion")

@@ -48,7 +48,7 @@ typedef enum {
   PM_ETIMEOUT = 6    /* a bounded device-side wait gave up */
 } pm_status;
 
-enum { PM_MIXED = 0, PM_FP32_PLAIN = 1 };               /* pm_config.precision */
+enum { PM_MIXED = 0, PM_FP32_PLAIN = 1, PM_FP64_PLAIN = 2 };  /* pm_config.precision */
 enum { PM_GUESS_WARM = 0, PM_GUESS_ZERO = 1, PM_GUESS_LEARNED = 2 };  /* pm_config.guess */
 enum { PM_GRAVITY_POISSON = 0, PM_GRAVITY_DIFFUSION = 1,
        PM_GRAVITY_DIFFUSION_ADE = 2 };                                 /* pm_config.gravity */
@@ -70,7 +70,12 @@ typedef struct {
   double rtol;           /* relative residual ||f - A Phi||_2 / ||f||_2 per solve */
   int32_t max_vcycles;   /* V-cycles allowed per solve before PM_ENOCONV */
   int32_t precision;     /* PM_MIXED: FP32 V-cycles inside a double-float
-                            defect-correction loop; PM_FP32_PLAIN: FP32 only */
+                            defect-correction loop; PM_FP32_PLAIN: FP32 only;
+                            PM_FP64_PLAIN: potential, source and every
+                            multigrid level in FP64 (one-colour sweeps, a
+                            one-CTA bottom of 64 sweeps), Poisson gravity
+                            without the learned guess only: the cost of FP64
+                            on the device, for comparison */
   int32_t guess;         /* PM_GUESS_WARM: previous step's Phi; PM_GUESS_ZERO;
                             PM_GUESS_LEARNED: the warm start corrected by the
                             network attached with pm_set_guess */

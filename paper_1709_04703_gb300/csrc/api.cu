@@ -157,6 +157,10 @@ struct pm_ctx {
   df* bgw = nullptr;            // per-axis mean-density weights w_g, g in [0, n)
   float* ballw = nullptr;       // spherical keep region: mean-density image, n^3
   SortWork sortw{};             // particle order by cell (sort_every > 0)
+  // PM_FP64_PLAIN: the potential and source in double (full (n+2)^3) and
+  // the coarse levels (compact, level 0 unused)
+  double *phi64 = nullptr, *f64 = nullptr;
+  std::vector<double*> lu64, lb64;
   BallRule ball_rule{};         // its Gauss-Legendre rule
   std::vector<unsigned char> h_bg;  // host image of bgm + bgw
   unsigned long long* d_cnt = nullptr;  // [0] n_keep, [1] escaped
@@ -397,6 +401,10 @@ pm_status set_cube(pm_ctx* ctx, int lo, int s, int periodic, double R) {
     CK(cudaMemsetAsync(ctx->lu[l], 0, bytes, ctx->st));
     CK(cudaMemsetAsync(ctx->lb[l], 0, bytes, ctx->st));
     CK(cudaMemsetAsync(ctx->lu2[l], 0, bytes, ctx->st));
+    if (l > 0 && l < ctx->lu64.size() && ctx->lu64[l]) {
+      CK(cudaMemsetAsync(ctx->lu64[l], 0, 2 * bytes, ctx->st));
+      CK(cudaMemsetAsync(ctx->lb64[l], 0, 2 * bytes, ctx->st));
+    }
   }
   return PM_OK;
 }
@@ -615,7 +623,117 @@ pm_status vcycle_run(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
 // Iterate to rtol.  f2 = ||f||^2 already in d_scal[0] (read at first sync).
 // With a learned guess, the first correction comes from the network applied
 // to the residual of the start instead of from a V-cycle.
+GridD full_view64(const pm_ctx* c, double* base, int lo, int s) {
+  GridD g;
+  g.sy = c->P;
+  g.sz = c->P * c->P;
+  g.s = s;
+  g.base = base + (lo + 1) + (lo + 1) * g.sy + (lo + 1) * g.sz;
+  return g;
+}
+
+GridD compact_view64(double* base, int s) {
+  GridD g;
+  g.sy = s + 2;
+  g.sz = (s + 2) * (s + 2);
+  g.s = s;
+  g.base = base + 1 + g.sy + g.sz;
+  return g;
+}
+
+// V(2,2) in double on the level-0 grids (u0, b0): the FP32 cycle's order and
+// boundary treatment, one-colour passes on every level, 64 sweeps at the
+// coarsest level (side <= 8)
+pm_status vcycle64(pm_ctx* ctx, GridD u0, GridD b0) {
+  const int per = ctx->periodic;
+  const int L = (int)ctx->ls.size() - 1;
+  if (L >= 16) return fail(ctx, PM_EINVAL, "too many multigrid levels");
+  GridD U[16], B[16];
+  U[0] = u0;
+  B[0] = b0;
+  for (int l = 1; l <= L; ++l) {
+    U[l] = compact_view64(ctx->lu64[l], ctx->ls[l]);
+    B[l] = compact_view64(ctx->lb64[l], ctx->ls[l]);
+  }
+  auto gam = [&](int l) {
+    const double H = (double)(1 << l);
+    return per ? 0.0 : (H - 1.0) / (H + 1.0);
+  };
+  auto smooth = [&](int l, double h2) {
+    for (int sw = 0; sw < 2; ++sw) {
+      launch64_rbgs(ctx->st, U[l], B[l], h2, 0, per, gam(l));
+      launch64_rbgs(ctx->st, U[l], B[l], h2, 1, per, gam(l));
+    }
+  };
+  double h2 = 1.0;
+  for (int l = 0; l < L; ++l) {
+    smooth(l, h2);
+    launch64_resid_restrict(ctx->st, U[l], B[l], 1.0 / h2, U[l + 1], B[l + 1], per, gam(l));
+    h2 *= 4.0;
+  }
+  launch64_bottom(ctx->st, U[L], B[L], h2, per, gam(L), 64);
+  for (int l = L - 1; l >= 0; --l) {
+    h2 *= 0.25;
+    launch64_prolong(ctx->st, U[l + 1], U[l], per, gam(l + 1));
+    smooth(l, h2);
+  }
+  CKL();
+  return PM_OK;
+}
+
+// The solve with the potential, the source and every level in double
+// (PM_FP64_PLAIN): Phi (with its ghost layer, the open boundary's Dirichlet
+// values) and f widened from their double-float pairs, V-cycles on Phi
+// until ||f - A Phi|| / ||f|| <= rtol (read after each), Phi narrowed back
+// to a pair for the gradient and the next warm start.
+pm_status solve64(pm_ctx* ctx) {
+  const int lo = ctx->lo, s = ctx->s, per = ctx->periodic;
+  Grid fh = full_view(ctx, ctx->f_hi, lo, s), fl = full_view(ctx, ctx->f_lo, lo, s);
+  Grid ph = full_view(ctx, ctx->phi_h[ctx->cur], lo, s);
+  Grid pl = full_view(ctx, ctx->phi_l[ctx->cur], lo, s);
+  GridD P = full_view64(ctx, ctx->phi64, lo, s), F = full_view64(ctx, ctx->f64, lo, s);
+  if (ctx->cfg.guess == PM_GUESS_ZERO) {
+    launch_fill(ctx->st, ph, 0.0f, false);
+    launch_fill(ctx->st, pl, 0.0f, false);
+  }
+  launch64_from_pair(ctx->st, ph, pl, P, true);
+  launch64_from_pair(ctx->st, fh, fl, F, false);
+  ctx->guess_used_last = 0;
+  int it = 0;
+  double rel = 0.0;
+  for (;;) {
+    launch64_defect(ctx->st, P, F, per, ctx->partial, ctx->counter, ctx->d_scal + 11);
+    CKL();
+    pm_status st = sync_read(ctx);
+    if (st != PM_OK) return st;
+    const double f2 = ctx->h_scal[0], r2 = ctx->h_scal[11];
+    rel = f2 > 0 ? std::sqrt(r2 / f2) : 0.0;
+    if (it == 0) ctx->resid_start = ctx->resid_guess = rel;
+    if (rel <= ctx->cfg.rtol || f2 == 0.0) break;
+    if (it >= ctx->cfg.max_vcycles) {
+      ctx->vcycles_last = it;
+      ctx->vcycles_total += it;
+      ctx->resid_last = rel;
+      char buf[160];
+      snprintf(buf, sizeof buf, "solve: relative residual %.3e after %d V-cycles (rtol %.1e)",
+               rel, it, ctx->cfg.rtol);
+      return fail(ctx, PM_ENOCONV, buf);
+    }
+    st = vcycle64(ctx, P, F);
+    if (st != PM_OK) return st;
+    ++it;
+  }
+  launch64_to_pair(ctx->st, P, ph, pl);
+  CKL();
+  ctx->vcycles_last = it;
+  ctx->vcycles_total += it;
+  ctx->resid_last = rel;
+  ctx->vc_prev = it;
+  return PM_OK;
+}
+
 pm_status solve(pm_ctx* ctx) {
+  if (ctx->cfg.precision == PM_FP64_PLAIN) return solve64(ctx);
   const int lo = ctx->lo, s = ctx->s, per = ctx->periodic;
   Grid fh = full_view(ctx, ctx->f_hi, lo, s), fl = full_view(ctx, ctx->f_lo, lo, s);
   Grid e0 = compact_view(ctx->lu[0], s), r0 = compact_view(ctx->lb[0], s);
@@ -859,8 +977,13 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
       !(cfg->rtol > 0) ||
       cfg->max_vcycles < 1)
     return fail(nullptr, PM_EINVAL, "pm_init: invalid schedule, cosmology or tolerance");
-  if (cfg->precision != PM_MIXED && cfg->precision != PM_FP32_PLAIN)
+  if (cfg->precision != PM_MIXED && cfg->precision != PM_FP32_PLAIN &&
+      cfg->precision != PM_FP64_PLAIN)
     return fail(nullptr, PM_EINVAL, "pm_init: unknown precision");
+  if (cfg->precision == PM_FP64_PLAIN &&
+      (cfg->gravity != PM_GRAVITY_POISSON || cfg->guess == PM_GUESS_LEARNED))
+    return fail(nullptr, PM_EINVAL, "pm_init: PM_FP64_PLAIN solves Poisson's equation from "
+                                    "the warm or zero start");
   if (cfg->bc < PM_BC_PAPER || cfg->bc > PM_BC_PERIODIC)
     return fail(nullptr, PM_EINVAL, "pm_init: unknown bc");
   if (cfg->guess < PM_GUESS_WARM || cfg->guess > PM_GUESS_LEARNED)
@@ -954,7 +1077,20 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
     float* u2 = nullptr;
     AL(u2, bytes);
     ctx->lu2.push_back(u2);
+    if (cfg->precision == PM_FP64_PLAIN) {
+      double *u64 = nullptr, *b64 = nullptr;
+      if (ctx->lu.size() > 1) {  // level 0 is the full grid
+        AL(u64, 2 * bytes);
+        AL(b64, 2 * bytes);
+      }
+      ctx->lu64.push_back(u64);
+      ctx->lb64.push_back(b64);
+    }
     if (sl <= 4 || sl % 2) break;
+  }
+  if (cfg->precision == PM_FP64_PLAIN) {
+    AL(ctx->phi64, sizeof(double) * padded);
+    AL(ctx->f64, sizeof(double) * padded);
   }
   const int maxblk = std::max(std::max(SRC_GRID, defect_blocks(n)), 4096);
   AL(ctx->partial, sizeof(double) * 16 * maxblk);
@@ -1024,6 +1160,7 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
     return fail(ctx, PM_EINVAL, "pm_step: PM_GUESS_LEARNED without a network (pm_set_guess)");
   const int n = ctx->n;
   const bool mixed = ctx->cfg.precision == PM_MIXED;
+  const bool pair = ctx->cfg.precision != PM_FP32_PLAIN;  // Phi kept as hi + lo
   for (int q = 0; q < n_steps; ++q) {
     const int k = ctx->step;
     const double R0 = ctx->R[k], R1 = ctx->R[k + 1];
@@ -1141,7 +1278,7 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
       for (int q = 0; q < (mixed ? 2 : 1); ++q)  // both buffers carry the ghosts
         launch_boundary(ctx->st, full_view(ctx, ctx->phi_h[q ^ ctx->cur], lo, s),
                         full_view(ctx, ctx->phi_l[q ^ ctx->cur], lo, s), n, lo,
-                        ctx->d_scal + 1, S, mixed);
+                        ctx->d_scal + 1, S, pair);
       prof_end(ctx, PM_PROF_BOUNDARY, e, 8.0 * 6.0 * (s + 2.0) * (s + 2.0));
     }
     CKL();
@@ -1160,7 +1297,7 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
         launch_predict(ctx->st, full_view(ctx, ctx->phi_h[ctx->cur], lo, s),
                        full_view(ctx, ctx->phi_l[ctx->cur], lo, s),
                        full_view(ctx, ctx->prev_hi, lo, s),
-                       full_view(ctx, ctx->prev_lo, lo, s), w, mixed);
+                       full_view(ctx, ctx->prev_lo, lo, s), w, pair);
         prof_end(ctx, PM_PROF_CORRECT, e, 32.0 * cells);
       }
     }
@@ -1277,13 +1414,13 @@ pm_status pm_potential(pm_ctx* ctx, const double* delta_dev, double a, int32_t b
   ctx->field_ready = false; // a diffusion run restarts its field
   const double S = 1.5 * ctx->cfg.omega_m / a;
   Grid fh = full_view(ctx, ctx->f_hi, 0, n), fl = full_view(ctx, ctx->f_lo, 0, n);
-  const bool mixed = ctx->cfg.precision == PM_MIXED;
+  const bool pair = ctx->cfg.precision != PM_FP32_PLAIN;  // Phi kept as hi + lo
   launch_source_f64(ctx->st, SRC_GRID, delta_dev, n, fh, fl, S, !per, ctx->partial,
                     ctx->counter, ctx->d_scal);
   // launch_source_f64 writes (||f||^2, q0, d, S_ab) to d_scal[0..10]
   for (int q = 0; q < 2; ++q) {
     Grid gh = full_view(ctx, ctx->phi_h[q], 0, n), gl = full_view(ctx, ctx->phi_l[q], 0, n);
-    if (!per) launch_boundary(ctx->st, gh, gl, n, 0, ctx->d_scal + 1, S, mixed);
+    if (!per) launch_boundary(ctx->st, gh, gl, n, 0, ctx->d_scal + 1, S, pair);
     launch_fill(ctx->st, gh, 0.0f, false);
     launch_fill(ctx->st, gl, 0.0f, false);
   }
@@ -1736,6 +1873,10 @@ void pm_destroy(pm_ctx* ctx) {
   for (float* p : ctx->lu) if (p) cudaFree(p);
   for (float* p : ctx->lb) if (p) cudaFree(p);
   for (float* p : ctx->lu2) if (p) cudaFree(p);
+  for (double* p : ctx->lu64) if (p) cudaFree(p);
+  for (double* p : ctx->lb64) if (p) cudaFree(p);
+  if (ctx->phi64) cudaFree(ctx->phi64);
+  if (ctx->f64) cudaFree(ctx->f64);
   drop_graph(ctx);
   for (auto& e : ctx->ev) cudaEventDestroy(e);
   if (ctx->h_scal) cudaFreeHost(ctx->h_scal);

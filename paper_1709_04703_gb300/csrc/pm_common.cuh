@@ -22,6 +22,14 @@ __host__ __device__ inline int gidx(const Grid& g, int i, int j, int k) {
   return i + j * g.sy + k * g.sz;
 }
 
+// The same view of a double grid (the FP64 solve)
+struct GridD {
+  double* base;
+  int s;
+  int sy;
+  int sz;
+};
+
 // Block coordinates of one launch: the native blockIdx / gridDim, or those of
 // a realisation's share of a batched launch.
 struct BI {

@@ -48,6 +48,20 @@ cudaError_t launch_sort_particles(cudaStream_t st, const float4* pos, const floa
                                   long long N, int n, const SortWork& w, float4* pos_out,
                                   float4* mom_out);
 
+// k_fp64.cu: the Poisson V-cycle and defect in double (PM_FP64_PLAIN)
+void launch64_rbgs(cudaStream_t st, GridD u, GridD b, double h2, int color, int periodic,
+                   double gam);
+void launch64_resid_restrict(cudaStream_t st, GridD u, GridD b, double inv_h2, GridD uc,
+                             GridD bc, int periodic, double gam);
+void launch64_prolong(cudaStream_t st, GridD uc, GridD u, int periodic, double gam_c);
+void launch64_bottom(cudaStream_t st, GridD u, GridD b, double h2, int periodic, double gam,
+                     int sweeps);
+int defect64_blocks(int s);
+void launch64_defect(cudaStream_t st, GridD p, GridD f, int periodic, double* partial,
+                     unsigned int* counter, double* out);
+void launch64_from_pair(cudaStream_t st, Grid hi, Grid lo, GridD out, bool ghost);
+void launch64_to_pair(cudaStream_t st, GridD in, Grid hi, Grid lo);
+
 // k_mesh.cu
 void launch_drift_deposit(cudaStream_t st, int grid, float4* pos, const float4* mom,
                           long long N, float c0, bool drift, int n, int lo, int s,

@@ -7,7 +7,7 @@ import torch
 
 from . import _lib as L
 
-_PREC = {"mixed": L.PM_MIXED, "fp32": L.PM_FP32_PLAIN}
+_PREC = {"mixed": L.PM_MIXED, "fp32": L.PM_FP32_PLAIN, "fp64": L.PM_FP64_PLAIN}
 _GUESS = {"warm": L.PM_GUESS_WARM, "zero": L.PM_GUESS_ZERO, "learned": L.PM_GUESS_LEARNED}
 _BC = {"paper": L.PM_BC_PAPER, "open": L.PM_BC_OPEN, "periodic": L.PM_BC_PERIODIC}
 _GRAVITY = {"poisson": L.PM_GRAVITY_POISSON, "diffusion": L.PM_GRAVITY_DIFFUSION,
