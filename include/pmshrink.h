@@ -45,7 +45,8 @@ typedef enum {
   PM_ECUDA = 3,      /* a CUDA call or kernel launch failed */
   PM_ENOCONV = 4,    /* a Poisson solve did not reach rtol in max_vcycles */
   PM_EOVERFLOW = 5,  /* a fixed-point cell count exceeded 2^62 */
-  PM_ETIMEOUT = 6    /* a bounded device-side wait gave up */
+  PM_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
+  PM_EIO = 7         /* a checkpoint file could not be written or read */
 } pm_status;
 
 enum { PM_MIXED = 0, PM_FP32_PLAIN = 1, PM_FP64_PLAIN = 2 };  /* pm_config.precision */
@@ -138,6 +139,22 @@ typedef struct {
 void pm_config_default(pm_config* cfg);
 
 typedef struct pm_ctx pm_ctx;
+
+/* Checkpoint and resume (not in the paper).  pm_save writes, at a step
+ * boundary, everything the following steps depend on: the configuration,
+ * the step index, the active particles and the lightcone records (in array
+ * order), the potential pair and the previous solution that the warm start
+ * extrapolates from, the active cube, the solver's counters and history and
+ * the cumulative statistics.  pm_load restores that state into a context
+ * created by pm_init with the same configuration (every pm_config field
+ * equal, else PM_EINVAL); the steps after it then give the same bits as an
+ * uninterrupted run.  The file is a fixed header followed by raw
+ * little-endian arrays; it is read back only by this library.  Both calls
+ * synchronise the context's stream.  Errors: PM_EINVAL (NULL argument,
+ * another configuration, not a checkpoint of this library), PM_EIO (open,
+ * write or short read), PM_ECUDA. */
+pm_status pm_save(pm_ctx* ctx, const char* path);
+pm_status pm_load(pm_ctx* ctx, const char* path);
 
 /* Create a simulation context.  pos4/mom4 hold cfg->n_particles float4
  * records (layout above); they are copied (host_mem = 1: host pointers,

@@ -10,7 +10,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpmshrink.so")
 
-PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_ENOCONV, PM_EOVERFLOW, PM_ETIMEOUT = range(7)
+PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_ENOCONV, PM_EOVERFLOW, PM_ETIMEOUT, PM_EIO = range(8)
 PM_MIXED, PM_FP32_PLAIN, PM_FP64_PLAIN = 0, 1, 2
 PM_GUESS_WARM, PM_GUESS_ZERO, PM_GUESS_LEARNED = 0, 1, 2
 PM_GRAVITY_POISSON, PM_GRAVITY_DIFFUSION, PM_GRAVITY_DIFFUSION_ADE = 0, 1, 2
@@ -21,12 +21,12 @@ PM_DOMAIN_CUBE, PM_DOMAIN_SPHERE = 0, 1
 PM_SHRINK_STATIC_MAX_PARTICLES = 1 << 22
 
 STATUS_NAMES = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ECUDA",
-                4: "PM_ENOCONV", 5: "PM_EOVERFLOW", 6: "PM_ETIMEOUT"}
+                4: "PM_ENOCONV", 5: "PM_EOVERFLOW", 6: "PM_ETIMEOUT", 7: "PM_EIO"}
 
 # every entry point declared in include/pmshrink.h
 EXPORTED = [
     "pm_config_default", "pm_init", "pm_step", "pm_shrink", "pm_potential",
-    "pm_power_spectrum", "pm_power_spectrum_jing", "pm_deposit", "pm_deposit_tsc", "pm_sort_particles", "pm_stats", "pm_schedule",
+    "pm_power_spectrum", "pm_power_spectrum_jing", "pm_deposit", "pm_deposit_tsc", "pm_sort_particles", "pm_stats", "pm_schedule", "pm_save", "pm_load",
     "pm_get_particles", "pm_set_particles", "pm_get_lightcone", "pm_get_forces",
     "pm_get_potential", "pm_profile", "pm_profile_read", "pm_launch_count", "pm_last_error",
     "pm_destroy", "pm_shrink_static", "pm_shrink_static_error",
@@ -97,6 +97,8 @@ def load():
         "pm_deposit_tsc": (I32, [P, P, I64, F, I32, I32, I32, I32, P, C.POINTER(I64), P]),
         "pm_sort_particles": (I32, [P, P, I64, I32, P, P, P]),
         "pm_stats": (I32, [P, C.POINTER(PmStats)]),
+        "pm_save": (I32, [P, C.c_char_p]),
+        "pm_load": (I32, [P, C.c_char_p]),
         "pm_schedule": (I32, [P, P, P, P, P]),
         "pm_get_particles": (I32, [P, P, P, I32, C.POINTER(I64)]),
         "pm_set_particles": (I32, [P, P, P, I64, I32]),

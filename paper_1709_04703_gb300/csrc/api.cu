@@ -1797,6 +1797,54 @@ pm_status pm_get_forces(pm_ctx* ctx, float* f4, int32_t host_mem, int64_t* n_out
   return PM_OK;
 }
 
+namespace {
+// Checkpoint layout: this header, then pos and mom of the active particles,
+// the lightcone pos and mom, then phi_hi, phi_lo (the current buffer),
+// prev_hi, prev_lo (full (n+2)^3 arrays).
+struct CkptHeader {
+  char magic[8];
+  uint32_t version, header_bytes;
+  pm_config cfg;
+  int32_t step, cur, n_sol, field_ready, vc_prev, cube_valid, lo, s, periodic, vcycles_last;
+  int64_t n_active, n_lc, vcycles_total, particle_steps, escaped, guess_used_total;
+  double ah_hist[2], resid_last, resid_start, resid_guess;
+  uint64_t padded;
+};
+const char CKPT_MAGIC[8] = {'P', 'M', 'S', 'H', 'R', 'K', 'C', '1'};
+
+bool cfg_equal(const pm_config& a, const pm_config& b) {
+  return a.n_mesh == b.n_mesh && a.n_particles == b.n_particles && a.box_mpch == b.box_mpch &&
+         a.omega_m == b.omega_m && a.omega_l == b.omega_l && a.a_init == b.a_init &&
+         a.a_final == b.a_final && a.n_steps == b.n_steps && a.rtol == b.rtol &&
+         a.max_vcycles == b.max_vcycles && a.precision == b.precision && a.guess == b.guess &&
+         a.bc == b.bc && a.shrink == b.shrink && a.buffer_cells == b.buffer_cells &&
+         a.store_forces == b.store_forces && a.gravity == b.gravity &&
+         a.c_eff_factor == b.c_eff_factor && a.assignment == b.assignment &&
+         a.domain == b.domain && a.sort_every == b.sort_every;
+}
+
+// device <-> file through a bounded host buffer
+constexpr size_t CKPT_CHUNK = size_t(64) << 20;
+bool dev_to_file(FILE* f, const void* dev, size_t bytes, std::vector<char>& buf) {
+  for (size_t off = 0; off < bytes; off += CKPT_CHUNK) {
+    const size_t m = std::min(CKPT_CHUNK, bytes - off);
+    if (cudaMemcpy(buf.data(), (const char*)dev + off, m, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return false;
+    if (std::fwrite(buf.data(), 1, m, f) != m) return false;
+  }
+  return true;
+}
+bool file_to_dev(FILE* f, void* dev, size_t bytes, std::vector<char>& buf) {
+  for (size_t off = 0; off < bytes; off += CKPT_CHUNK) {
+    const size_t m = std::min(CKPT_CHUNK, bytes - off);
+    if (std::fread(buf.data(), 1, m, f) != m) return false;
+    if (cudaMemcpy((char*)dev + off, buf.data(), m, cudaMemcpyHostToDevice) != cudaSuccess)
+      return false;
+  }
+  return true;
+}
+}  // namespace
+
 pm_status pm_get_potential(pm_ctx* ctx, double* phi_host, int32_t* lo_out, int32_t* side_out) {
   if (!ctx) return fail(nullptr, PM_EINVAL, "pm_get_potential: NULL context");
   const int P = ctx->P, lo = ctx->lo, s = ctx->s;
@@ -1821,6 +1869,124 @@ pm_status pm_get_potential(pm_ctx* ctx, double* phi_host, int32_t* lo_out, int32
   if (lo_out) *lo_out = lo;
   if (side_out) *side_out = s;
   return PM_OK;
+}
+
+pm_status pm_save(pm_ctx* ctx, const char* path) {
+  if (!ctx || !path) return fail(ctx, PM_EINVAL, "pm_save: NULL argument");
+  pm_status st = sync_read(ctx);  // completes the stream; escaped count
+  if (st != PM_OK) return st;
+  CkptHeader h;
+  std::memset(&h, 0, sizeof h);
+  std::memcpy(h.magic, CKPT_MAGIC, 8);
+  h.version = 1;
+  h.header_bytes = (uint32_t)sizeof h;
+  h.cfg = ctx->cfg;
+  h.step = ctx->step;
+  h.cur = ctx->cur;
+  h.n_sol = ctx->n_sol;
+  h.field_ready = ctx->field_ready ? 1 : 0;
+  h.vc_prev = ctx->vc_prev;
+  h.cube_valid = ctx->cube_valid ? 1 : 0;
+  h.lo = ctx->lo;
+  h.s = ctx->s;
+  h.periodic = ctx->periodic;
+  h.vcycles_last = ctx->vcycles_last;
+  h.n_active = ctx->n_active;
+  h.n_lc = ctx->n_lc;
+  h.vcycles_total = ctx->vcycles_total;
+  h.particle_steps = ctx->particle_steps;
+  h.escaped = (int64_t)ctx->h_cnt[1];
+  h.guess_used_total = ctx->guess_used_total;
+  h.ah_hist[0] = ctx->ah_hist[0];
+  h.ah_hist[1] = ctx->ah_hist[1];
+  h.resid_last = ctx->resid_last;
+  h.resid_start = ctx->resid_start;
+  h.resid_guess = ctx->resid_guess;
+  h.padded = (uint64_t)ctx->P * ctx->P * ctx->P;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(ctx, PM_EIO, std::string("pm_save: cannot open ") + path);
+  std::vector<char> buf(CKPT_CHUNK);
+  const size_t pb = sizeof(float4), gb = sizeof(float) * (size_t)h.padded;
+  bool ok = std::fwrite(&h, sizeof h, 1, f) == 1 &&
+            dev_to_file(f, ctx->pos, pb * h.n_active, buf) &&
+            dev_to_file(f, ctx->mom, pb * h.n_active, buf) &&
+            dev_to_file(f, ctx->lc_pos, pb * h.n_lc, buf) &&
+            dev_to_file(f, ctx->lc_mom, pb * h.n_lc, buf) &&
+            dev_to_file(f, ctx->phi_h[ctx->cur], gb, buf) &&
+            dev_to_file(f, ctx->phi_l[ctx->cur], gb, buf) &&
+            dev_to_file(f, ctx->prev_hi, gb, buf) && dev_to_file(f, ctx->prev_lo, gb, buf);
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return fail(ctx, PM_EIO, std::string("pm_save: writing ") + path + " failed");
+  return PM_OK;
+}
+
+pm_status pm_load(pm_ctx* ctx, const char* path) {
+  if (!ctx || !path) return fail(ctx, PM_EINVAL, "pm_load: NULL argument");
+  CK(cudaStreamSynchronize(ctx->st));
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(ctx, PM_EIO, std::string("pm_load: cannot open ") + path);
+  CkptHeader h;
+  if (std::fread(&h, sizeof h, 1, f) != 1) {
+    std::fclose(f);
+    return fail(ctx, PM_EIO, "pm_load: short header");
+  }
+  const uint64_t padded = (uint64_t)ctx->P * ctx->P * ctx->P;
+  if (std::memcmp(h.magic, CKPT_MAGIC, 8) != 0 || h.version != 1 ||
+      h.header_bytes != sizeof h || h.padded != padded) {
+    std::fclose(f);
+    return fail(ctx, PM_EINVAL, "pm_load: not a checkpoint of this library and mesh");
+  }
+  if (!cfg_equal(h.cfg, ctx->cfg)) {
+    std::fclose(f);
+    return fail(ctx, PM_EINVAL, "pm_load: the checkpoint has another configuration");
+  }
+  if (h.step < 0 || h.step > ctx->cfg.n_steps || h.n_active < 0 || h.n_lc < 0 ||
+      h.n_active > ctx->N0 || h.n_lc > ctx->N0 ||  // the record mode keeps both
+      (ctx->cfg.shrink != PM_SHRINK_RECORD && h.n_active + h.n_lc > ctx->N0) ||
+      (h.cur != 0 && h.cur != 1)) {
+    std::fclose(f);
+    return fail(ctx, PM_EINVAL, "pm_load: inconsistent checkpoint header");
+  }
+  std::vector<char> buf(CKPT_CHUNK);
+  const size_t pb = sizeof(float4), gb = sizeof(float) * (size_t)padded;
+  bool ok = file_to_dev(f, ctx->pos, pb * h.n_active, buf) &&
+            file_to_dev(f, ctx->mom, pb * h.n_active, buf) &&
+            file_to_dev(f, ctx->lc_pos, pb * h.n_lc, buf) &&
+            file_to_dev(f, ctx->lc_mom, pb * h.n_lc, buf) &&
+            file_to_dev(f, ctx->phi_h[h.cur], gb, buf) &&
+            file_to_dev(f, ctx->phi_l[h.cur], gb, buf) &&
+            file_to_dev(f, ctx->prev_hi, gb, buf) && file_to_dev(f, ctx->prev_lo, gb, buf);
+  std::fclose(f);
+  if (!ok) return fail(ctx, PM_EIO, std::string("pm_load: reading ") + path + " failed");
+  ctx->step = h.step;
+  ctx->cur = h.cur;
+  ctx->n_sol = h.n_sol;
+  ctx->field_ready = h.field_ready != 0;
+  ctx->vc_prev = h.vc_prev;
+  ctx->vcycles_last = h.vcycles_last;
+  ctx->n_active = h.n_active;
+  ctx->n_lc = h.n_lc;
+  ctx->vcycles_total = h.vcycles_total;
+  ctx->particle_steps = h.particle_steps;
+  ctx->guess_used_total = h.guess_used_total;
+  ctx->ah_hist[0] = h.ah_hist[0];
+  ctx->ah_hist[1] = h.ah_hist[1];
+  ctx->resid_last = h.resid_last;
+  ctx->resid_start = h.resid_start;
+  ctx->resid_guess = h.resid_guess;
+  ctx->forces_valid = false;
+  drop_graph(ctx);
+  unsigned long long cnt[4] = {0ull, (unsigned long long)h.escaped, 0ull, 0ull};
+  CK(cudaMemcpy(ctx->d_cnt, cnt, sizeof cnt, cudaMemcpyHostToDevice));
+  ctx->cube_valid = false;
+  if (h.cube_valid) {
+    // the cube of the last step, its levels and mean-density term, so that
+    // the next step sees no change of boundary phase
+    pm_status st = set_cube(ctx, h.lo, h.s, h.periodic, ctx->R[ctx->step]);
+    if (st != PM_OK) return st;
+  }
+  CK(cudaStreamSynchronize(ctx->st));
+  return sync_read(ctx);
 }
 
 pm_status pm_profile(pm_ctx* ctx, int32_t enable) {

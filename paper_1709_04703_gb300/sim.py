@@ -239,6 +239,14 @@ class Sim:
         self._check(self._lib.pm_stats(self._ctx, C.byref(s)))
         return {f: getattr(s, f) for f, _ in L.PmStats._fields_}
 
+    def save(self, path):
+        """Checkpoint the run at the current step boundary (pm_save)."""
+        self._check(self._lib.pm_save(self._ctx, str(path).encode()))
+
+    def load(self, path):
+        """Resume from a checkpoint of a run with the same configuration."""
+        self._check(self._lib.pm_load(self._ctx, str(path).encode()))
+
     def schedule(self):
         m = self.cfg.n_steps + 1
         out = {k: np.zeros(m) for k in ("a", "dtau", "a_half", "chi")}

@@ -1,0 +1,87 @@
+"""Checkpoint and resume (pm_save / pm_load): a run saved at a step
+boundary and resumed in a fresh context gives the same bits as the
+uninterrupted run, through the periodic and open phases, for the static
+and diffusion gravities, with and without reordering by cell; a checkpoint
+of another configuration, or a file that is not one, is refused."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from paper_1709_04703_gb300 import ics  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1709_04703_gb300 import build
+    build.build()
+
+
+N, BOX, A0, STEPS = 32, 6000.0, 0.2, 24
+
+
+def _new(**kw):
+    from paper_1709_04703_gb300.sim import Sim
+    pos, mom, ids = ics.zeldovich(N, -1.5, 0.5, 6, A0, rms_disp=0.6)
+    return Sim(pos, mom, ids, N, BOX, A0, 1.0, STEPS, **kw)
+
+
+def _state(sim):
+    st = sim.stats()
+    p, m, i = sim.particles()
+    lp, lm, li, la = sim.lightcone()
+    return st, (p, m, i, lp, lm, li, la)
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(sort_every=5), dict(gravity="diffusion"),
+                                dict(precision="fp32", rtol=1e-4),
+                                dict(shrink="record", bc="periodic")])
+@pytest.mark.parametrize("cut", [7, 15])
+def test_resume_gives_the_same_bits(tmp_path, kw, cut):
+    ref = _new(**kw)
+    ref.step(STEPS)
+    s_ref, a_ref = _state(ref)
+    ref.close()
+    first = _new(**kw)
+    first.step(cut)
+    path = tmp_path / "run.ckpt"
+    first.save(path)
+    first.close()
+    second = _new(**kw)
+    second.load(path)
+    assert second.stats()["step"] == cut
+    second.step(STEPS - cut)
+    s_res, a_res = _state(second)
+    second.close()
+    for f in ("step", "n_active", "n_lightcone", "vcycles_total", "escaped", "particle_steps",
+              "resid_last", "cube_side", "cube_lo"):
+        assert s_res[f] == s_ref[f], f
+    for u, v in zip(a_res, a_ref):
+        np.testing.assert_array_equal(u, v)
+
+
+def test_another_configuration_is_refused(tmp_path):
+    from paper_1709_04703_gb300 import _lib as L
+    a = _new()
+    a.step(2)
+    path = tmp_path / "a.ckpt"
+    a.save(path)
+    a.close()
+    b = _new(rtol=1e-6)
+    with pytest.raises(L.PmError) as e:
+        b.load(path)
+    assert e.value.code == L.PM_EINVAL
+    junk = tmp_path / "junk.ckpt"
+    junk.write_bytes(b"not a checkpoint" * 64)
+    with pytest.raises(L.PmError) as e:
+        b.load(junk)
+    assert e.value.code in (L.PM_EINVAL, L.PM_EIO)
+    with pytest.raises(L.PmError) as e:
+        b.load(tmp_path / "missing.ckpt")
+    assert e.value.code == L.PM_EIO
+    b.step(1)   # the context is still usable
+    b.close()
