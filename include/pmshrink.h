@@ -431,6 +431,16 @@ const char* pm_shrink_static_error(void);
  * tensor memory) that maps a source to a potential guess for the solver.
  * ------------------------------------------------------------------------- */
 
+/* Failure-detection self-test of the bounded wait used by the tensor-core
+ * kernels (an mbarrier polled with an iteration limit; on giving up a
+ * kernel sets an error word that the host maps to PM_ETIMEOUT).  One warp
+ * initialises an mbarrier for one arrival; arrive = 1: a thread arrives and
+ * the wait completes (PM_OK); arrive = 0: nothing arrives and the wait gives
+ * up after `polls` polls (PM_ETIMEOUT).  Nothing asynchronous is in flight,
+ * and the context stays usable.  polls in [1, 1e9], else PM_EINVAL.
+ * Synchronises stream. */
+pm_status pm_selftest_wait(int32_t arrive, int64_t polls, void* stream);
+
 /* The multigrid smoother of the Poisson solve (Sec. 2.1, Eq. 3 as the
  * 7-point system h^-2 (sum_nb u - diag u) = b): two red-black Gauss-Seidel
  * sweeps (red = (i+j+k) even first, then black, twice), u_out = S(u_in).

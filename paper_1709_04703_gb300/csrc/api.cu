@@ -157,6 +157,7 @@ struct pm_ctx {
   df* bgw = nullptr;            // per-axis mean-density weights w_g, g in [0, n)
   float* ballw = nullptr;       // spherical keep region: mean-density image, n^3
   SortWork sortw{};             // particle order by cell (sort_every > 0)
+  long long n_allocs = 0;       // device allocations so far (fault injection)
   // PM_FP64_PLAIN: the potential and source in double (full (n+2)^3) and
   // the coarse levels (compact, level 0 unused)
   double *phi64 = nullptr, *f64 = nullptr;
@@ -908,6 +909,13 @@ pm_status record_to(pm_ctx* ctx, double R, double a_cross) {
 }
 
 pm_status alloc(pm_ctx* ctx, void** p, size_t bytes) {
+  // host-side fault injection for tests: PM_FAULT_ALLOC=k makes the k-th
+  // device allocation of a context fail as if the device were full
+  const char* fk = getenv("PM_FAULT_ALLOC");
+  if (ctx && fk && ++ctx->n_allocs == atoll(fk)) {
+    *p = nullptr;
+    return fail(ctx, PM_ENOMEM, "cudaMalloc: allocation failure injected (PM_FAULT_ALLOC)");
+  }
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     *p = nullptr;
@@ -2856,6 +2864,25 @@ extern "C" pm_status pm_mg_smooth(const float* u_in, float* u_out, const float* 
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(nullptr, PM_ECUDA, cudaGetErrorString(e));
+  return PM_OK;
+}
+
+extern "C" pm_status pm_selftest_wait(int32_t arrive, int64_t polls, void* stream) {
+  if (polls < 1 || polls > 1000000000LL)
+    return fail(nullptr, PM_EINVAL, "pm_selftest_wait: polls in [1, 1e9]");
+  cudaStream_t st = (cudaStream_t)stream;
+  int* flag = nullptr;
+  if (cudaMallocAsync((void**)&flag, sizeof(int), st) != cudaSuccess)
+    return fail(nullptr, PM_ENOMEM, "pm_selftest_wait: cudaMallocAsync");
+  cudaMemsetAsync(flag, 0, sizeof(int), st);
+  launch_wait_selftest(st, arrive ? 1 : 0, polls, flag);
+  cudaError_t e = cudaGetLastError();
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(flag, st);
+  if (e != cudaSuccess) return fail(nullptr, PM_ECUDA, cudaGetErrorString(e));
+  if (h) return fail(nullptr, PM_ETIMEOUT, "pm_selftest_wait: the bounded wait gave up");
   return PM_OK;
 }
 

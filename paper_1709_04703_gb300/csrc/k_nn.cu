@@ -145,6 +145,29 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const bf16* __restrict__ A,
   tc_end<NC>(c);
 }
 
+// Failure-detection self-test of the bounded mbarrier wait the tensor-core
+// kernels use: one warp initialises an mbarrier for one arrival; with
+// arrive = 1 a thread arrives and the wait completes, otherwise nothing
+// arrives and the wait gives up after `limit` polls, setting *gave_up.
+// Nothing asynchronous is in flight in either case.
+__global__ void k_wait_selftest(int arrive, long long limit, int* gave_up) {
+  __shared__ __align__(8) unsigned long long bar;
+  const uint32_t mbar = tc::smem_u32(&bar);
+  if (threadIdx.x == 0) tc::mbar_init(mbar, 1);
+  __syncthreads();
+  if (arrive && threadIdx.x == 0) {
+    unsigned long long state;
+    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(mbar) : "memory");
+  }
+  const bool done = tc::mbar_wait(mbar, 0u, limit);
+  if (!done && threadIdx.x == 0) atomicOr(gave_up, 1);
+}
+
+void launch_wait_selftest(cudaStream_t st, int arrive, long long limit, int* gave_up) {
+  k_wait_selftest<<<1, 32, 0, st>>>(arrive, limit, gave_up);
+  note_launch();
+}
+
 void launch_gemm_tc(cudaStream_t st, const void* A, const void* B, float* C, int M, int N,
                     int K, int* err) {
   dim3 grid(M / tc::TM);

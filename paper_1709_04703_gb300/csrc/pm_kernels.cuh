@@ -309,6 +309,7 @@ int deposit_blocks(long long N);
 
 namespace pm {
 // k_nn.cu
+void launch_wait_selftest(cudaStream_t st, int arrive, long long limit, int* gave_up);
 void launch_gemm_tc(cudaStream_t st, const void* A, const void* B, float* C, int M, int N,
                     int K, int* err);
 void launch_conv_fwd(cudaStream_t st, const void* in, int B, int D, int H, int W, int per,
