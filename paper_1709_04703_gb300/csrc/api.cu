@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pm_kernels.cuh"
 
 using namespace pm;
@@ -114,6 +116,15 @@ int mg_round_up(int m) {
 }
 
 std::string g_err;  // last error of a context-free call
+
+// NVTX range over a host scope (a step, a solve, a sort, a shrink), for
+// timeline tools; inert when no tool is attached
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 }  // namespace
 
@@ -734,6 +745,7 @@ pm_status solve64(pm_ctx* ctx) {
 }
 
 pm_status solve(pm_ctx* ctx) {
+  NvtxRange nvtx("pm solve");
   if (ctx->cfg.precision == PM_FP64_PLAIN) return solve64(ctx);
   const int lo = ctx->lo, s = ctx->s, per = ctx->periodic;
   Grid fh = full_view(ctx, ctx->f_hi, lo, s), fl = full_view(ctx, ctx->f_lo, lo, s);
@@ -855,6 +867,7 @@ pm_status solve(pm_ctx* ctx) {
 }
 
 pm_status shrink_to(pm_ctx* ctx, double R, double a_cross, bool flags_ready) {
+  NvtxRange nvtx("pm shrink");
   const double c = 0.5 * ctx->n;
   float klo, khi;
   keep_bounds(c, R, &klo, &khi);
@@ -1170,6 +1183,7 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
   const bool mixed = ctx->cfg.precision == PM_MIXED;
   const bool pair = ctx->cfg.precision != PM_FP32_PLAIN;  // Phi kept as hi + lo
   for (int q = 0; q < n_steps; ++q) {
+    NvtxRange nvtx_step("pm step");
     const int k = ctx->step;
     const double R0 = ctx->R[k], R1 = ctx->R[k + 1];
     int lo, s, per;
@@ -1183,6 +1197,7 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
       // per pass a histogram (4 B) and a scatter (read and write key + index,
       // 16 B), then the permutation (4 B) and both records (read and write,
       // 64 B)
+      NvtxRange nvtx_sort("pm sort");
       int es = prof_begin(ctx);
       CK(launch_sort_particles(ctx->st, ctx->pos, ctx->mom, N, n, ctx->sortw, ctx->pos2,
                                ctx->mom2));
