@@ -34,6 +34,7 @@ constexpr double C_OVER_H0 = 2997.92458;  // Mpc/h
 constexpr int SRC_GRID = 1216;            // 152 SMs x 8 blocks
 constexpr int COARSE_SWEEPS = 6;
 constexpr int FUSED_MIN = 192;  // smallest level side smoothed by the fused pass
+constexpr int LEVEL_SWEEPS = 2;  // pre- and post-smoothing sweeps on levels below the finest
 constexpr size_t BGW_OFF = 128;  // byte offset of the background weights in bgm
 
 // ---------------------------------------------------------------------------
@@ -486,8 +487,8 @@ pm_status sync_read(pm_ctx* ctx) {
 // Two RB-GS sweeps (red, black, red, black) on a level; zero_start when the
 // iterate is known to be zero on entry.
 void smooth2(pm_ctx* ctx, Grid u, Grid b, float h2, int per, float g, bool zero_start,
-             float d0) {
-  for (int sw = 0; sw < 2; ++sw) {
+             float d0, int sweeps = 2) {
+  for (int sw = 0; sw < sweeps; ++sw) {
     launch_rbgs(ctx->st, u, b, h2, 0, per, g, zero_start && sw == 0, d0);
     launch_rbgs(ctx->st, u, b, h2, 1, per, g, false, d0);
   }
@@ -534,7 +535,7 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
     if (fused)
       launch_rbgs2(ctx->st, U[l], Upre[l], B[l], h2, per, gam(l), zs, 0, d0);
     else
-      smooth2(ctx, U[l], B[l], h2, per, gam(l), zs, d0);
+      smooth2(ctx, U[l], B[l], h2, per, gam(l), zs, d0, l > 0 ? LEVEL_SWEEPS : 2);
     if (l == 0) {
       prof_end(ctx, PM_PROF_SMOOTH0, e, (fused ? (zs ? 8.0 : 12.0) : 32.0) * c0);
       e = prof_begin(ctx);
@@ -571,7 +572,7 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
     if (fused)
       launch_rbgs2(ctx->st, W, U[l], B[l], h2, per, gam(l), false, 0, d0);
     else
-      smooth2(ctx, U[l], B[l], h2, per, gam(l), false, d0);
+      smooth2(ctx, U[l], B[l], h2, per, gam(l), false, d0, l > 0 ? LEVEL_SWEEPS : 2);
     if (l == 0) prof_end(ctx, PM_PROF_SMOOTH0, e, (fused ? 12.0 : 32.0) * c0);
   }
   if (Lc == 0) prof_end(ctx, PM_PROF_COARSE, ec, 0.0);
