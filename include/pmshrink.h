@@ -456,6 +456,19 @@ pm_status pm_mg_smooth(const float* u_in, float* u_out, const float* b, int32_t 
                        int32_t periodic, float h2, float gam, int32_t zero_start, int32_t fused,
                        int32_t zchunk, void* stream);
 
+/* The multigrid transfers of the same solve, on padded (s+2)^3 FP32 device
+ * arrays [z][y][x] (s even, >= 4; coarse side s/2, padded likewise).
+ * pm_mg_restrict: bc = 1/8 of the sum over the 8 children of the residual
+ * b - (sum_nb u - diag u) / h2 (diag as pm_mg_smooth: 6, plus gam per ghost
+ * face when open); uc is zeroed (interiors only).  pm_mg_prolong: u += P uc,
+ * trilinear with weights 3/4 on the parent and 1/4 on the next coarse cell
+ * per axis; periodic wraps, open takes the next cell outside the coarse
+ * grid as -gam_c times the parent.  Synchronise stream. */
+pm_status pm_mg_restrict(const float* u, const float* b, int32_t s, int32_t periodic, float h2,
+                         float gam, float* uc, float* bc, void* stream);
+pm_status pm_mg_prolong(const float* uc, float* u, int32_t s, int32_t periodic, float gam_c,
+                        void* stream);
+
 /* C[M x N] (FP32, row-major) = A[M x K] B[N x K]^T with A, B row-major BF16
  * device matrices; M % 128 == 0, K % 64 == 0, N in {16, 32, 64, 128}.  The
  * tile engine under every convolution of the learned guess.  PM_ETIMEOUT if

@@ -32,7 +32,7 @@ EXPORTED = [
     "pm_destroy", "pm_shrink_static", "pm_shrink_static_error",
     "pm_batch_init", "pm_batch_step", "pm_batch_stats", "pm_batch_get_particles",
     "pm_batch_get_lightcone", "pm_batch_last_error", "pm_batch_destroy",
-    "pm_mg_smooth", "pm_selftest_wait", "pm_nn_gemm_bf16", "pm_guess_create", "pm_guess_num_params", "pm_guess_set_params",
+    "pm_mg_smooth", "pm_mg_restrict", "pm_mg_prolong", "pm_selftest_wait", "pm_nn_gemm_bf16", "pm_guess_create", "pm_guess_num_params", "pm_guess_set_params",
     "pm_guess_get_params", "pm_guess_forward", "pm_guess_loss_grad", "pm_guess_adam",
     "pm_guess_last_error", "pm_guess_destroy", "pm_set_guess", "pm_capture",
 ]
@@ -120,6 +120,8 @@ def load():
         "pm_batch_last_error": (C.c_char_p, [P]),
         "pm_batch_destroy": (None, [P]),
         "pm_selftest_wait": (I32, [I32, I64, P]),
+        "pm_mg_restrict": (I32, [P, P, I32, I32, F, F, P, P, P]),
+        "pm_mg_prolong": (I32, [P, P, I32, I32, F, P]),
         "pm_nn_gemm_bf16": (I32, [P, P, P, I32, I32, I32, P]),
         "pm_mg_smooth": (I32, [P, P, P, I32, I32, C.c_float, C.c_float, I32, I32, I32, P]),
         "pm_guess_create": (I32, [I32, P, C.POINTER(P)]),

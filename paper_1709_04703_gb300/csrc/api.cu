@@ -2846,6 +2846,42 @@ void pm_batch_destroy(pm_batch* B) {
 // ===========================================================================
 // Tensor-core building blocks of the learned guess
 // ===========================================================================
+namespace {
+Grid padded_view(const float* base, int s) {
+  Grid g;
+  g.s = s;
+  g.sy = s + 2;
+  g.sz = (s + 2) * (s + 2);
+  g.base = const_cast<float*>(base) + 1 + g.sy + g.sz;
+  return g;
+}
+pm_status finish_test_call(cudaStream_t st) {
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(nullptr, PM_ECUDA, cudaGetErrorString(e));
+  return PM_OK;
+}
+}  // namespace
+
+extern "C" pm_status pm_mg_restrict(const float* u, const float* b, int32_t s, int32_t periodic,
+                                    float h2, float gam, float* uc, float* bc, void* stream) {
+  if (!u || !b || !uc || !bc || s < 4 || (s & 1) || s > 2048 || !(h2 > 0))
+    return fail(nullptr, PM_EINVAL, "pm_mg_restrict: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  launch_resid_restrict(st, padded_view(u, s), padded_view(b, s), 1.0f / h2,
+                        padded_view(uc, s / 2), padded_view(bc, s / 2), periodic, gam);
+  return finish_test_call(st);
+}
+
+extern "C" pm_status pm_mg_prolong(const float* uc, float* u, int32_t s, int32_t periodic,
+                                   float gam_c, void* stream) {
+  if (!u || !uc || s < 4 || (s & 1) || s > 2048)
+    return fail(nullptr, PM_EINVAL, "pm_mg_prolong: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  launch_prolong(st, padded_view(uc, s / 2), padded_view(u, s), periodic, gam_c);
+  return finish_test_call(st);
+}
+
 extern "C" pm_status pm_mg_smooth(const float* u_in, float* u_out, const float* b, int32_t s,
                                   int32_t periodic, float h2, float gam, int32_t zero_start,
                                   int32_t fused, int32_t zchunk, void* stream) {

@@ -92,3 +92,86 @@ def test_fused_pass_matches_fp64_sweeps(lib, s, periodic, gam, zero):
     ref = _sweeps_fp64(u.cpu().numpy(), b.cpu().numpy(), s, periodic, 2.0, gam, zero)
     np.testing.assert_allclose(got[1:-1, 1:-1, 1:-1].cpu().numpy(), ref[1:-1, 1:-1, 1:-1],
                                rtol=1e-5, atol=1e-5 * np.abs(ref).max())
+
+
+# ------------------------------------------------------------ transfers
+
+def _restrict_fp64(u, b, s, periodic, h2, gam):
+    """1/8 of the sum over the 8 children of b - (sum_nb u - diag u)/h2, in
+    FP64 (ghosts read as stored; periodic wraps)."""
+    u = u.astype(np.float64)
+    b = b.astype(np.float64)[1:-1, 1:-1, 1:-1]
+    v = u[1:-1, 1:-1, 1:-1]
+    if periodic:
+        nb = sum(np.roll(v, sh, axis=ax) for ax in range(3) for sh in (1, -1))
+        diag = 6.0
+    else:
+        nb = (u[2:, 1:-1, 1:-1] + u[:-2, 1:-1, 1:-1] + u[1:-1, 2:, 1:-1]
+              + u[1:-1, :-2, 1:-1] + u[1:-1, 1:-1, 2:] + u[1:-1, 1:-1, :-2])
+        idx = np.arange(s)
+        Z, Y, X = np.meshgrid(idx, idx, idx, indexing="ij")
+        diag = 6.0 + gam * sum((c == e).astype(np.float64) for c in (X, Y, Z) for e in (0, s - 1))
+    r = b - (nb - diag * v) / h2
+    sc = s // 2
+    return r.reshape(sc, 2, sc, 2, sc, 2).mean(axis=(1, 3, 5))
+
+
+def _prolong_fp64(uc, u, s, periodic, gam_c):
+    """u + P uc: per axis 3/4 of the parent and 1/4 of the next coarse cell
+    (below for an even child, above for an odd one), wrapped, or (open)
+    -gam_c times the parent outside the coarse grid."""
+    sc = s // 2
+    q = uc.astype(np.float64)[1:-1, 1:-1, 1:-1]
+    i = np.arange(s)
+    par = i // 2
+    nxt = np.where(i % 2 == 1, par + 1, par - 1)
+    fac = np.ones(s)
+    if periodic:
+        nxt %= sc
+    else:
+        out = (nxt < 0) | (nxt >= sc)
+        nxt = np.where(out, par, nxt)
+        fac = np.where(out, -gam_c, 1.0)
+    terms = [(par, np.full(s, 0.75)), (nxt, 0.25 * fac)]
+    val = np.zeros((s, s, s))
+    for zi, wz in terms:
+        for yi, wy in terms:
+            for xi, wx in terms:
+                val += (wz[:, None, None] * wy[None, :, None] * wx[None, None, :]
+                        * q[np.ix_(zi, yi, xi)])
+    return u.astype(np.float64)[1:-1, 1:-1, 1:-1] + val
+
+
+TCASES = [(s, per, gam) for s in (8, 24, 64, 100) for per, gam in
+          ((1, 0.0), (0, 0.0), (0, 1.0 / 3.0), (0, 3.0 / 5.0))]
+
+
+@pytest.mark.parametrize("s,periodic,gam", TCASES)
+def test_restriction_matches_its_definition(lib, s, periodic, gam):
+    u, b = _inputs(s, 300 + s)
+    sc = s // 2
+    uc = torch.full(((sc + 2),) * 3, 7.0, device="cuda")
+    bc = torch.zeros(((sc + 2),) * 3, device="cuda")
+    h2 = 4.0 if gam else 1.0
+    code = lib.pm_mg_restrict(_p(u), _p(b), s, periodic, C.c_float(h2), C.c_float(gam), _p(uc),
+                              _p(bc), None)
+    assert code == L.PM_OK, lib.pm_last_error(None)
+    ref = _restrict_fp64(u.cpu().numpy(), b.cpu().numpy(), s, periodic, h2, gam)
+    got = bc[1:-1, 1:-1, 1:-1].cpu().numpy()
+    np.testing.assert_allclose(got, ref, rtol=0, atol=2e-6 * np.abs(ref).max() + 1e-6)
+    assert np.all(uc[1:-1, 1:-1, 1:-1].cpu().numpy() == 0.0)
+    assert np.all(uc[0].cpu().numpy() == 7.0)   # ghosts untouched
+
+
+@pytest.mark.parametrize("s,periodic,gam", TCASES)
+def test_prolongation_matches_its_definition(lib, s, periodic, gam):
+    u, _ = _inputs(s, 400 + s)
+    sc = s // 2
+    uc = torch.randn(((sc + 2),) * 3, device="cuda")
+    before = u.clone()
+    code = lib.pm_mg_prolong(_p(uc), _p(u), s, periodic, C.c_float(gam), None)
+    assert code == L.PM_OK, lib.pm_last_error(None)
+    ref = _prolong_fp64(uc.cpu().numpy(), before.cpu().numpy(), s, periodic, gam)
+    got = u[1:-1, 1:-1, 1:-1].cpu().numpy()
+    np.testing.assert_allclose(got, ref, rtol=0, atol=2e-6 * np.abs(ref).max())
+    assert torch.equal(u[0], before[0])          # ghosts untouched
