@@ -102,6 +102,21 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate_ranks(units, elapsed, device):
+    """Whole-job figures over the ranks of the default process group (one
+    replica per rank, no exchange on the data path): the sum of the units
+    processed and the slowest rank's elapsed time."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(units), float(elapsed)
+    s = torch.tensor([float(units)], device=device, dtype=torch.float64)
+    m = torch.tensor([float(elapsed)], device=device, dtype=torch.float64)
+    dist.all_reduce(s)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    return s.item(), m.item()
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -554,15 +569,13 @@ def run_ours(args):
         sim.close()
         e2e = {"value": ps / dt, "unit": UNIT, "h2d_bytes_per_step": h2d // K,
                "d2h_bytes_per_step": d2h // K}
+        e2e_units, e2e_s = ps, dt
 
     # aggregate over ranks: sum of particle-steps, max of time
-    tot_ps, max_ms = float(psteps), float(ms)
-    if ws > 1:
-        t = torch.tensor([tot_ps], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t)
-        m = torch.tensor([max_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(m, op=dist.ReduceOp.MAX)
-        tot_ps, max_ms = t.item(), m.item()
+    tot_ps, max_ms = aggregate_ranks(psteps, ms, "cuda")
+    if e2e is not None:
+        e_ps, e_s = aggregate_ranks(e2e_units, e2e_s, "cuda")
+        e2e["value"] = e_ps / e_s
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
