@@ -75,3 +75,36 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.pm_power_spectrum(None, 0, 1.0, 8, 4, 1, None, None, None, None) == L.PM_EINVAL
     assert lib.pm_deposit(None, None, 0, 0.0, 8, 0, 8, 1, None, None, None) == L.PM_EINVAL
     lib.pm_destroy(None)
+
+
+@pytest.mark.parametrize("fields", [
+    dict(precision=2, gravity=1),          # FP64 everywhere solves Poisson only
+    dict(precision=2, guess=2),            # ... from the warm or zero start
+    dict(sort_every=-1),
+    dict(assignment=1, gravity=1),         # TSC with Poisson gravity only
+    dict(domain=1, assignment=1),          # the sphere with CIC only
+    dict(gravity=1, precision=1),          # diffusion needs the mixed path
+])
+def test_init_rejects_bad_combinations_before_touching_the_gpu(lib, fields):
+    cfg = L.PmConfig()
+    lib.pm_config_default(C.byref(cfg))
+    for k, v in fields.items():
+        setattr(cfg, k, v)
+    buf = (C.c_float * 8)()
+    ctx = C.c_void_p(123)
+    code = lib.pm_init(C.byref(cfg), C.cast(buf, C.c_void_p), C.cast(buf, C.c_void_p), 1,
+                       None, C.byref(ctx))
+    assert code == L.PM_EINVAL
+    assert ctx.value is None
+
+
+def test_context_free_entries_check_arguments_before_touching_the_gpu(lib):
+    assert lib.pm_save(None, b"x") == L.PM_EINVAL
+    assert lib.pm_load(None, b"x") == L.PM_EINVAL
+    assert lib.pm_sort_particles(None, None, 0, 8, None, None, None) == L.PM_OK
+    assert lib.pm_sort_particles(None, None, 4, 0, None, None, None) == L.PM_EINVAL
+    assert lib.pm_sort_particles(None, None, 4, 8, None, None, None) == L.PM_EINVAL
+    assert lib.pm_selftest_wait(0, 0, None) == L.PM_EINVAL
+    assert lib.pm_mg_restrict(None, None, 8, 1, C.c_float(1.0), C.c_float(0.0), None, None,
+                              None) == L.PM_EINVAL
+    assert lib.pm_mg_prolong(None, None, 8, 1, C.c_float(0.0), None) == L.PM_EINVAL
