@@ -6,8 +6,11 @@ source + boundary values, multigrid Poisson solve to rtol, gradient + gather +
 kick + drift, lightcone shrink) over the active particles of one simulation.
 The workload is 256^3 particles on a 256^3 mesh, 2000 Mpc/h, Zel'dovich ICs
 from P(k) ~ k^-1.5 exp(-k^2/2k_c^2) (seed 1), steps uniform in a from 0.01 to
-1 in 200 steps; --steps K times the first K of them (default: all 200, so the
-shrinking phase is inside the timed region).
+1 in 200 steps.  --steps K times two windows of that schedule: K/2 steps from
+a = 0.01 (periodic phase, every particle active) and K/2 steps from the first
+open-phase step (a ~ 0.73: open boundaries, shrinking cube and particle set,
+the lightcone compaction), the run's own state there (the steps in between
+run untimed).
 
 Tolerance: the metric compares the plain FP32 and the mixed (FP32 V-cycles
 inside a double-float defect correction) solvers at equal residual.  The
@@ -16,7 +19,7 @@ path's measured floor on the first step) unless --rtol is given; the mixed
 path at 1e-7 is reported beside it.
 
 value  = sum over timed steps of the active particle count / device time
-         (mixed path at that tolerance)
+         (mixed path at that tolerance; "arithmetic" says which form)
 e2e    = the same through the C ABI with host buffers: each step copies the
          particles host->device, steps, and copies them back
 Multi-GPU: independent replicas (one per rank, no collective on the data
@@ -143,6 +146,16 @@ def _new_sim(pos, mom, ids, cfg, rtol, precision, guess="warm"):
 
 STRICT_RTOL = 1e-7
 
+# the arithmetic each --precision computes in
+DTYPE = {"mixed": "f32+df32", "fp32": "f32", "mixed64": "f32+f64"}
+ARITHMETIC = {
+    "mixed": "FP32 V-cycles inside a double-float (hi + lo FP32 pair, ~48-bit significand) "
+             "defect correction; FP32 particles, int64 density",
+    "fp32": "FP32 potential and V-cycles; FP32 particles, int64 density",
+    "mixed64": "FP32 V-cycles inside an FP64 defect correction (FP64 potential); FP32 "
+               "particles, int64 density",
+}
+
 # ncu dram__bytes_read.sum + dram__bytes_write.sum over the algorithmic bytes
 # of the kernel class's launches at 256^3 on the current kernels
 TRAFFIC_RATIO = {
@@ -171,10 +184,64 @@ def _plain_floor(pos, mom, ids, cfg):
     return floor
 
 
-def _variant(pos, mom, ids, cfg, K, rtol, precision, guess="warm", net=None,
-             gravity="poisson", bc="paper", shrink=True, assignment="cic"):
-    """The same K steps in another solver configuration, device-timed."""
+def _first_open_step(sim, n, box):
+    """Index of the schedule's first step whose keep cube lies inside the box
+    (open boundaries and shrinking from there on): R = chi/cell + 1 cell
+    <= n/2 - 1, the library's boundary rule."""
+    chi = sim.schedule()["chi"]
+    R = chi / (box / n) + 1.0
+    return next(k for k in range(len(chi) - 1) if R[k] <= 0.5 * n - 1.0)
+
+
+def _windows(K, k_open, steps):
+    """The timed steps: K/2 from the start of the run (periodic phase, every
+    particle active) and K/2 from the first open-phase step (shrinking
+    cube, shrinking particle set).  Returns [(first step, count), ...]."""
+    kb = min(K // 2, steps - k_open)
+    return [(0, K - kb), (k_open, kb)]
+
+
+def _run_windows(sim, windows, stream, per_window=None):
+    """Step `sim` through the windows, timing each with CUDA events on the
+    context's stream; untimed steps in between advance the run (its state
+    at the second window is the run's own, not regenerated).  Returns
+    (device ms, particle-steps, per-window records)."""
     import torch
+    out, ms_tot, ps_tot = [], 0.0, 0
+    for k0, cnt in windows:
+        if cnt <= 0:
+            continue
+        gap = k0 - sim.stats()["step"]
+        if gap > 0:
+            sim.step(gap)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ps0 = sim.stats()["particle_steps"]
+        vc0 = sim.stats()["vcycles_total"]
+        if per_window is not None:
+            per_window("start")
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        sim.step(cnt)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if per_window is not None:
+            per_window("end")
+        ms = ev0.elapsed_time(ev1)
+        st = sim.stats()
+        ps = st["particle_steps"] - ps0
+        out.append({"first_step": k0, "steps": cnt, "ms_per_step": round(ms / cnt, 4),
+                    "particle_steps": int(ps), "value": ps / (ms * 1e-3),
+                    "vcycles": int(st["vcycles_total"] - vc0),
+                    "n_active_end": int(st["n_active"]),
+                    "phase": "periodic" if k0 == 0 else "open (shrinking)"})
+        ms_tot += ms
+        ps_tot += ps
+    return ms_tot, ps_tot, out
+
+
+def _variant(pos, mom, ids, cfg, windows, rtol, precision, guess="warm", net=None,
+             gravity="poisson", bc="paper", shrink=True, assignment="cic"):
+    """The same timed windows in another solver configuration."""
     from paper_1709_04703_gb300 import _lib as L
     from paper_1709_04703_gb300.sim import Sim
     sim = Sim(pos, mom, ids, cfg["n"], cfg["box"], cfg["a_init"], cfg["a_final"],
@@ -183,99 +250,131 @@ def _variant(pos, mom, ids, cfg, K, rtol, precision, guess="warm", net=None,
               sort_every=SORT_EVERY)
     if net is not None:
         sim.set_guess(net)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ev0.record(sim.stream)
     out = {"precision": precision, "guess": guess, "rtol": rtol, "gravity": gravity,
            "assignment": assignment}
     if not shrink:
         out["box"] = "fixed periodic (no shrinking)"
     try:
-        sim.step(K)
+        ms, ps, wins = _run_windows(sim, windows, sim.stream)
     except L.PmError as e:
         st = sim.stats()
         out.update(error=str(e), steps_done=st["step"], resid_last=st["resid_last"])
         sim.close()
         return out
-    ev1.record(sim.stream)
-    torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
     st = sim.stats()
     sim.close()
-    out.update(value=st["particle_steps"] / (ms * 1e-3), ms_per_step=ms / K,
-               vcycles_total=st["vcycles_total"], guess_used=st["guess_used_total"])
+    K = sum(c for _, c in windows)
+    out.update(value=ps / (ms * 1e-3), ms_per_step=ms / K,
+               vcycles_total=sum(w["vcycles"] for w in wins),
+               guess_used=st["guess_used_total"],
+               windows=[{k: w[k] for k in ("first_step", "steps", "ms_per_step", "vcycles")}
+                        for w in wins])
     return out
 
 
-def cpu_baseline(budget_s=20.0, n_sample=128, window=5):
-    """The FP64 oracle, as it stands, on a replica of the workload at
-    n_sample^3 (same box, spectrum and seed): `window` steps from a_init
-    (periodic phase) and `window` steps from the first step of the open
-    phase (ICs regenerated at that a), each window cut short once it has
-    used half of budget_s.  particle-steps/s = sum of active particles over
-    the steps run / their time."""
+def _oracle_worker(task):
+    """One host process: the FP64 oracle, as it stands, stepping an n^3
+    replica of the workload from step k0 (ICs regenerated at that a) for up
+    to `steps` steps or `budget_s` seconds.  Returns (particle-steps, s)."""
+    import sys as _sys
+    _sys.path.insert(0, ROOT)
+    from oracle import cosmology as cz
+    from oracle import pm as opm
+    from paper_1709_04703_gb300 import ics
+    n, k0, steps, budget_s = task
+    cfg = ics.WORKLOADS[WORKLOAD]
+    sched = cz.schedule(n, cfg["box"], 0.3, 0.7, cfg["a_init"], cfg["a_final"], cfg["steps"])
+    pos, mom, _ = ics.zeldovich(n, cfg["alpha"], cfg["cutoff"], cfg["seed"], sched["a"][k0])
+    x, p = pos.astype(np.float64), mom.astype(np.float64)
+    ps = 0
+    t0 = time.perf_counter()
+    for k in range(k0, min(k0 + steps, cfg["steps"])):
+        ps += len(x)
+        x, p, info = opm.step(x, p, k, sched, n, 0.3, 1.0)
+        if not info["periodic"]:
+            keep = opm.keep_mask(x, sched["R"][k + 1], n)
+            x, p = x[keep], p[keep]
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    return ps, time.perf_counter() - t0
+
+
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_pool(n, starts, steps, budget_s):
+    """The oracle on every host core at once: one process per core (spawned,
+    so none inherits the parent's CUDA context), each a replica of the
+    workload at n^3 starting at one of `starts` in turn.  Returns
+    (particle-steps / wall s, cores, wall s, per-start particle-steps)."""
+    import multiprocessing as mp
+    cores = _host_cores()
+    tasks = [(n, starts[w % len(starts)], steps, budget_s) for w in range(cores)]
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_worker, tasks)
+    wall = time.perf_counter() - t0
+    busy = max(r[1] for r in res)
+    ps = sum(r[0] for r in res)
+    return ps / busy, cores, busy, wall
+
+
+def _k_open_oracle(n):
     from oracle import cosmology as cz
     from oracle import pm as opm
     from paper_1709_04703_gb300 import ics
     cfg = ics.WORKLOADS[WORKLOAD]
-    n = n_sample
     sched = cz.schedule(n, cfg["box"], 0.3, 0.7, cfg["a_init"], cfg["a_final"], cfg["steps"])
-    k_open = next(k for k in range(cfg["steps"]) if not opm.active_cube(sched["R"][k], n)[2])
-    ps, dt, run = 0, 0.0, []
-    for k0 in (0, k_open):
-        pos, mom, _ = ics.zeldovich(n, cfg["alpha"], cfg["cutoff"], cfg["seed"], sched["a"][k0])
-        x, p = pos.astype(np.float64), mom.astype(np.float64)
-        t0 = time.perf_counter()
-        k = k0
-        while k < min(k0 + window, cfg["steps"]):
-            ps += len(x)
-            x, p, info = opm.step(x, p, k, sched, n, 0.3, 1.0)
-            if not info["periodic"]:
-                keep = opm.keep_mask(x, sched["R"][k + 1], n)
-                x, p = x[keep], p[keep]
-            k += 1
-            if time.perf_counter() - t0 >= 0.5 * budget_s:
-                break
-        dt += time.perf_counter() - t0
-        run.append((k0, k - k0))
-    return {"value": ps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle (numpy FP64, exact FFT / DST Poisson solves) on a {n}^3-particle "
-                      f"replica of the 256^3 workload: steps {run[0][0]}-{sum(run[0]) - 1} "
-                      f"(periodic) and {run[1][0]}-{sum(run[1]) - 1} (open phase, ICs at "
-                      f"a={sched['a'][k_open]:.3f}), {dt:.1f} s"}
+    return next(k for k in range(cfg["steps"]) if not opm.active_cube(sched["R"][k], n)[2])
+
+
+def cpu_baseline(budget_s=20.0, n_sample=128, window=5):
+    """The FP64 oracle, as it stands, on all host cores: one process per
+    core, each stepping a replica of the workload at n_sample^3 (same box,
+    spectrum and seed) for `window` steps or budget_s seconds, half of them
+    from a_init (periodic phase) and half from the first open-phase step
+    (ICs regenerated at that a).  particle-steps/s = all processes' active
+    particles over the steps run / the slowest process's time.  A 128^3
+    replica: one oracle step at 256^3 takes ~1 min and ~3 GB per process."""
+    k_open = _k_open_oracle(n_sample)
+    val, cores, busy, wall = _oracle_pool(n_sample, [0, k_open], window, budget_s)
+    return {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"oracle (numpy FP64, exact FFT / DST Poisson solves) in {cores} "
+                      f"processes, one per host core, each a {n_sample}^3-particle replica of "
+                      f"the 256^3 workload (same box, spectrum, seed) for up to {window} steps "
+                      f"from step 0 (periodic; even processes) or step {k_open} (open phase, "
+                      f"ICs at that a; odd processes), {busy:.1f} s"}
 
 
 def run_reference(args):
-    """--impl reference: the oracle as the reference arm, on the host cores."""
+    """--impl reference: the oracle as the reference arm, on all host cores
+    (one process per core, spawned), on the same windows as the GPU arm:
+    K/2 steps from a_init and K/2 from the first open-phase step, each
+    process a replica of the 256^3 workload at 64^3 (ICs regenerated at the
+    window's a), every process bounded to a minute."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    # bounded sample: a 32^3 replica per step keeps K+W steps to about a minute
-    from oracle import cosmology as cz
-    from oracle import pm as opm
-    from paper_1709_04703_gb300 import ics
-    cfg = ics.WORKLOADS[WORKLOAD]
-    n = 32 if args.steps + args.warmup > 60 else 64
-    pos, mom, ids = ics.zeldovich(n, cfg["alpha"], cfg["cutoff"], cfg["seed"], cfg["a_init"])
-    sched = cz.schedule(n, cfg["box"], 0.3, 0.7, cfg["a_init"], cfg["a_final"], cfg["steps"])
-    x, p = pos.astype(np.float64), mom.astype(np.float64)
-    ksteps = min(args.steps, cfg["steps"])
-    for k in range(args.warmup):
-        opm.step(x, p, k % cfg["steps"], sched, n, 0.3, 1.0)
-    t0 = time.perf_counter()
-    for k in range(ksteps):
-        x, p, _ = opm.step(x, p, k, sched, n, 0.3, 1.0)
-    dt = time.perf_counter() - t0
-    val = n**3 * ksteps / dt
-    sample = (f"oracle (numpy FP64) steps 0..{ksteps - 1} of the 256^3 schedule on a "
-              f"{n}^3-particle replica (same box, spectrum, seed)")
+    n = 64
+    k_open = _k_open_oracle(n)
+    half = max(1, args.steps // 2)
+    val, cores, busy, wall = _oracle_pool(n, [0, k_open], half, 60.0)
+    sample = (f"oracle (numpy FP64) in {cores} processes, one per host core, each a "
+              f"{n}^3-particle replica of the 256^3 workload (same box, spectrum, seed) for up to "
+              f"{half} steps from step 0 (even processes) or step {k_open} (open phase, ICs at "
+              f"that a; odd processes), {busy:.1f} s")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
-            "n_gpus": args.gpus, "steps": ksteps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * dt / max(ksteps, 1), "higher_is_better": True,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * busy / half, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_mesh": 256, "n_particles": 256**3,
-                       "box_mpch": 2000.0, "sample_mesh": n},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                       "box_mpch": 2000.0, "sample_mesh": n, "windows": "start + open phase"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -462,110 +561,138 @@ def run_ours(args):
     # warm-up: W steps on a throw-away context (same ICs)
     sim = _new_sim(pos, mom, ids, cfg, STRICT_RTOL, args.precision)
     sim.step(min(args.warmup, cfg["steps"]))
+    k_open = _first_open_step(sim, cfg["n"], cfg["box"])
     sim.close()
     torch.cuda.synchronize()
+    windows = _windows(K, k_open, cfg["steps"])
 
     # tolerance of the plain-vs-mixed comparison: the FP32 potential stalls
     # above 1e-7, so both paths run to max(1e-5, 10 x its measured floor)
     floor = _plain_floor(pos, mom, ids, cfg)
     rtol = args.rtol if args.rtol is not None else max(1e-5, 10.0 * floor)
 
-    # timed: K steps from the ICs, device-resident inputs, no instrumentation
+    # timed: the two windows, device-resident inputs, no instrumentation;
+    # the untimed steps between them advance the same run
     sim = _new_sim(pos, mom, ids, cfg, rtol, args.precision)
     stream = sim.stream   # the stream every kernel of the context is launched on
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    l0 = lib.pm_launch_count()
-    ps0 = sim.stats()["particle_steps"]
+    launches = [0]
+
+    def count(edge):
+        launches[0] += (-1 if edge == "start" else 1) * lib.pm_launch_count()
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
-        ev0.record(stream)
-        sim.step(K)
-        ev1.record(stream)
-        torch.cuda.synchronize()
+        ms, psteps, wins = _run_windows(sim, windows, stream, count)
     if ws > 1:
         dist.barrier()
-    ms = ev0.elapsed_time(ev1)
     st = sim.stats()
-    psteps = st["particle_steps"] - ps0
-    launches = lib.pm_launch_count() - l0
     import ctypes as C
-    vstats = {"vcycles_total": st["vcycles_total"], "n_active_end": st["n_active"],
+    vstats = {"vcycles_total": sum(w["vcycles"] for w in wins), "n_active_end": st["n_active"],
               "n_lightcone": st["n_lightcone"], "escaped": st["escaped"]}
     sim.close()
 
-    # the same K steps again with CUDA events around every kernel class on
-    # the context's stream: per-class device time and algorithmic bytes (the
-    # events cost about 6 % of the step, so the headline comes from the
-    # uninstrumented run above)
+    # the same windows again, one step at a time, with CUDA events around
+    # every kernel class on the context's stream: per-class device time and
+    # algorithmic bytes (the events cost a few % of the step, so the
+    # headline comes from the uninstrumented run above), and per step the
+    # active particles N, cells C and V-cycles k for the whole-step count
     sim = _new_sim(pos, mom, ids, cfg, rtol, args.precision)
-    sim.profile(True)
-    torch.cuda.synchronize()
+    prof, per_step = None, []
     p0 = time.perf_counter()
-    sim.step(K)
+    for k0, cnt in windows:
+        gap = k0 - sim.stats()["step"]
+        if gap > 0:
+            sim.step(gap)
+        sim.profile(True)
+        for _ in range(cnt):
+            n_act = sim.stats()["n_active"]
+            sim.step(1)
+            s1 = sim.stats()
+            per_step.append((n_act, s1["cube_side"] ** 3, s1["vcycles_last"]))
+        part = sim.profile_read()
+        sim.profile(False)
+        prof = part if prof is None else {
+            c: {f: prof[c][f] + part[c][f] for f in ("ms", "groups", "bytes")} for c in prof}
     torch.cuda.synchronize()
     prof_wall_ms = (time.perf_counter() - p0) * 1e3
-    prof = sim.profile_read()
-    if sim.stats()["vcycles_total"] != st["vcycles_total"]:
+    if sum(v for _, _, v in per_step) != vstats["vcycles_total"]:
         raise RuntimeError("the instrumented repeat took a different number of V-cycles")
     sim.close()
+    # whole-step algorithmic bytes (N active particles, C active cells, k
+    # V-cycles, o = k + 1 defect evaluations in the mixed forms)
+    o_of = (lambda v: v + 1) if args.precision != "fp32" else (lambda v: 0)
+    step_bytes = sum(64.0 * N + (24.0 + 74.0 * v + 40.0 * o_of(v)) * Cc for N, Cc, v in per_step)
 
-    # the same steps with plain FP32 V-cycles at the same tolerance, with the
-    # mixed path at 1e-7 (below the plain floor), and with the learned guess
+    # the same windows with plain FP32 V-cycles at the same tolerance, the
+    # mixed path at 1e-7 (below the plain floor), FP64 forms, the other
+    # gravities and assignment, the fixed box and the learned guess
     compare = None
     if not args.no_compare:
         from paper_1709_04703_gb300 import train_guess
-        compare = {"plain_fp32": _variant(pos, mom, ids, cfg, K, rtol, "fp32"),
-                   f"mixed_rtol_{STRICT_RTOL:g}": _variant(pos, mom, ids, cfg, K, STRICT_RTOL,
-                                                           "mixed"),
-                   f"plain_fp32_rtol_{STRICT_RTOL:g}": _variant(pos, mom, ids, cfg, 1,
+        first = [(0, 1)]
+        compare = {"plain_fp32": _variant(pos, mom, ids, cfg, windows, rtol, "fp32"),
+                   f"mixed_rtol_{STRICT_RTOL:g}": _variant(pos, mom, ids, cfg, windows,
+                                                           STRICT_RTOL, "mixed"),
+                   f"plain_fp32_rtol_{STRICT_RTOL:g}": _variant(pos, mom, ids, cfg, first,
                                                                 STRICT_RTOL, "fp32")}
+        # FP32 V-cycles inside an FP64-arithmetic defect correction (FP64
+        # potential), at the same tolerance and at 1e-7
+        compare["mixed_fp64_defect"] = _variant(pos, mom, ids, cfg, windows, rtol, "mixed64")
+        compare[f"mixed_fp64_defect_rtol_{STRICT_RTOL:g}"] = _variant(
+            pos, mom, ids, cfg, windows, STRICT_RTOL, "mixed64")
         # FP64 everywhere: potential, source and every multigrid level in
         # double, at the same tolerance and at 1e-7
-        compare["plain_fp64"] = _variant(pos, mom, ids, cfg, K, rtol, "fp64")
-        compare[f"plain_fp64_rtol_{STRICT_RTOL:g}"] = _variant(pos, mom, ids, cfg, K,
+        compare["plain_fp64"] = _variant(pos, mom, ids, cfg, windows, rtol, "fp64")
+        compare[f"plain_fp64_rtol_{STRICT_RTOL:g}"] = _variant(pos, mom, ids, cfg, windows,
                                                                STRICT_RTOL, "fp64")
         # the paper's diffusion-equation gravity (two implicit half-substeps)
-        compare["diffusion_gravity"] = _variant(pos, mom, ids, cfg, K, rtol, "mixed",
+        compare["diffusion_gravity"] = _variant(pos, mom, ids, cfg, windows, rtol, "mixed",
                                                 gravity="diffusion")
         # ... and with the paper's own explicit (ADE) sweeps instead of solves
-        compare["diffusion_ade"] = _variant(pos, mom, ids, cfg, K, rtol, "mixed",
+        compare["diffusion_ade"] = _variant(pos, mom, ids, cfg, windows, rtol, "mixed",
                                             gravity="diffusion_ade")
         # TSC density assignment and force interpolation instead of CIC
-        compare["tsc"] = _variant(pos, mom, ids, cfg, K, rtol, "mixed", assignment="tsc")
+        compare["tsc"] = _variant(pos, mom, ids, cfg, windows, rtol, "mixed", assignment="tsc")
         # the same steps in the fixed periodic box (every particle, every step)
-        compare["no_shrink"] = _variant(pos, mom, ids, cfg, K, rtol, "mixed", bc="periodic",
-                                        shrink=False)
+        compare["no_shrink"] = _variant(pos, mom, ids, cfg, windows, rtol, "mixed",
+                                        bc="periodic", shrink=False)
         net = train_guess.load(train_guess.DEFAULT_WEIGHTS)
         for tol in (rtol, STRICT_RTOL):
             key = "learned_guess" + ("" if tol == rtol else f"_rtol_{tol:g}")
-            compare[key] = _variant(pos, mom, ids, cfg, K, tol, args.precision, "learned", net)
+            compare[key] = _variant(pos, mom, ids, cfg, windows, tol, args.precision, "learned",
+                                    net)
             compare[key]["weights"] = os.path.relpath(train_guess.DEFAULT_WEIGHTS, ROOT)
         net.close()
 
-    # end to end through the C ABI with host buffers (pinned)
+    # end to end through the C ABI with host buffers (pinned): every timed
+    # step copies the active particles host -> device, steps, and copies
+    # them back; the untimed steps between the windows advance the run
     e2e = None
     if not args.no_e2e:
         sim = _new_sim(pos, mom, ids, cfg, rtol, args.precision)
         p4, m4 = pack(pos, mom, ids)
         hp = torch.from_numpy(p4).pin_memory()
         hm = torch.from_numpy(m4).pin_memory()
-        n_act = len(pos)
         h2d = d2h = 0
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ps = 0
-        for _ in range(K):
-            L.check(lib.pm_set_particles(sim._ctx, C.c_void_p(hp.data_ptr()),
-                                         C.c_void_p(hm.data_ptr()), n_act, 1), sim._ctx)
-            h2d += 32 * n_act
-            ps += n_act
-            sim.step(1)
+        dt, ps = 0.0, 0
+        for k0, cnt in windows:
+            gap = k0 - sim.stats()["step"]
+            if gap > 0:
+                sim.step(gap)
             n_act = sim.get_particles_host(hp, hm)
-            d2h += 32 * n_act
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(cnt):
+                L.check(lib.pm_set_particles(sim._ctx, C.c_void_p(hp.data_ptr()),
+                                             C.c_void_p(hm.data_ptr()), n_act, 1), sim._ctx)
+                h2d += 32 * n_act
+                ps += n_act
+                sim.step(1)
+                n_act = sim.get_particles_host(hp, hm)
+                d2h += 32 * n_act
+            torch.cuda.synchronize()
+            dt += time.perf_counter() - t0
         sim.close()
         e2e = {"value": ps / dt, "unit": UNIT, "h2d_bytes_per_step": h2d // K,
                "d2h_bytes_per_step": d2h // K}
@@ -598,11 +725,15 @@ def run_ours(args):
         "metric": METRIC, "value": tot_ps / (max_ms * 1e-3), "unit": UNIT, "n_gpus": ws,
         "steps": K, "warmup": args.warmup, "ms_per_step": max_ms / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+df32" if args.precision == "mixed" else "f32",
+        "dtype": DTYPE[args.precision],
+        "arithmetic": ARITHMETIC[args.precision],
         "data": "synthetic (seeded Zel'dovich ICs)",
+        "windows": wins,
         "config": {"workload": WORKLOAD, "n_mesh": 256, "n_particles": 256**3,
                    "box_mpch": 2000.0, "a": [cfg["a_init"], cfg["a_final"]],
-                   "schedule_steps": cfg["steps"], "rtol": rtol,
+                   "schedule_steps": cfg["steps"],
+                   "timed_steps": [f"{k0}..{k0 + c - 1}" for k0, c in windows if c > 0],
+                   "rtol": rtol,
                    "rtol_rule": "equal residual: max(1e-5, 10 x plain FP32 floor)"
                                 if args.rtol is None else "given",
                    "plain_fp32_floor": floor,
@@ -615,13 +746,20 @@ def run_ours(args):
                      "traffic": round(traffic) if traffic is not None else None,
                      "algorithmic_bytes_per_launch": round(d["bytes"] / max(1, d["groups"])),
                      "traffic_source": TRAFFIC_RATIO[dom][1] if dom in TRAFFIC_RATIO else None},
+        "step_roofline": {"bound": "hbm", "bytes_per_step": round(step_bytes / K),
+                          "achieved": round(step_bytes / (ms * 1e-3) / 1e9, 1),
+                          "peak": peak, "unit": "GB/s",
+                          "frac": round(step_bytes / (ms * 1e-3) / 1e9 / peak, 4),
+                          "count": "sum over the timed steps of 64 N + (24 + 74 k + 40 o) C: N "
+                                   "active particles, C active cells, k V-cycles, o = k + 1 "
+                                   "defect evaluations (0 in plain FP32)"},
         "kernels": kernels,
         "kernels_timing": "CUDA events around each kernel class on the context stream, in an "
                           f"instrumented repeat of the same {K} steps ({prof_wall_ms / K:.3f} "
-                          "ms/step there)",
+                          "ms/step there, one step per call)",
         "solver": vstats,
         "clocks": clk.summary(),
-        "gpu_launches": int(launches),
+        "gpu_launches": int(launches[0]),
     }
     if e2e is not None:
         line["e2e"] = e2e
@@ -639,12 +777,12 @@ def main():
     global SORT_EVERY
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--rtol", type=float, default=None,
                     help="solver tolerance (default: equal-residual rule, see config)")
-    ap.add_argument("--precision", choices=["mixed", "fp32"], default="mixed")
+    ap.add_argument("--precision", choices=["mixed", "fp32", "mixed64"], default="mixed")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the plain-FP32 and learned-guess runs of the same steps")

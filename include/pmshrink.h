@@ -49,7 +49,8 @@ typedef enum {
   PM_EIO = 7         /* a checkpoint file could not be written or read */
 } pm_status;
 
-enum { PM_MIXED = 0, PM_FP32_PLAIN = 1, PM_FP64_PLAIN = 2 };  /* pm_config.precision */
+enum { PM_MIXED = 0, PM_FP32_PLAIN = 1, PM_FP64_PLAIN = 2,
+       PM_MIXED_FP64 = 3 };                          /* pm_config.precision */
 enum { PM_GUESS_WARM = 0, PM_GUESS_ZERO = 1, PM_GUESS_LEARNED = 2 };  /* pm_config.guess */
 enum { PM_GRAVITY_POISSON = 0, PM_GRAVITY_DIFFUSION = 1,
        PM_GRAVITY_DIFFUSION_ADE = 2 };                                 /* pm_config.gravity */
@@ -76,7 +77,12 @@ typedef struct {
                             multigrid level in FP64 (one-colour sweeps, a
                             one-CTA bottom of 64 sweeps), Poisson gravity
                             without the learned guess only: the cost of FP64
-                            on the device, for comparison */
+                            on the device, for comparison;
+                            PM_MIXED_FP64: the FP32 V-cycles of PM_MIXED
+                            inside a defect correction in FP64 arithmetic:
+                            the potential is FP64 for the whole run, and
+                            r = f - A Phi and Phi += e are evaluated in FP64
+                            (Poisson gravity, warm or zero start) */
   int32_t guess;         /* PM_GUESS_WARM: previous step's Phi; PM_GUESS_ZERO;
                             PM_GUESS_LEARNED: the warm start corrected by the
                             network attached with pm_set_guess */
@@ -389,6 +395,10 @@ pm_status pm_batch_get_particles(pm_batch* b, int32_t r, float* pos4, float* mom
                                  int32_t host_mem, int64_t* n_active_out);
 pm_status pm_batch_get_lightcone(pm_batch* b, int32_t r, float* pos4, float* mom4,
                                  int32_t host_mem, int64_t* n_out);
+/* grad(Phi) at each active particle of realisation r in the last batched
+ * step, as pm_get_forces (needs cfgs[r].store_forces = 1). */
+pm_status pm_batch_get_forces(pm_batch* b, int32_t r, float* f4, int32_t host_mem,
+                              int64_t* n_out);
 const char* pm_batch_last_error(const pm_batch* b);
 void pm_batch_destroy(pm_batch* b);
 
@@ -415,8 +425,10 @@ void pm_batch_destroy(pm_batch* b);
  * that array's device address (set-up), so make the first call before any
  * stream capture.  All calls on a device share the one array: calls that
  * overlap on the GPU (different streams or threads) race and must be
- * serialised by the caller.  pm_shrink_static_error() describes the last
- * failure. */
+ * serialised by the caller.  Non-finite box_mpch, omega_m, omega_l,
+ * buffer_cells or a give PM_EINVAL.  pm_shrink_static_error() describes the
+ * calling thread's last failure; the returned text stays valid until that
+ * thread's next failing call. */
 #define PM_SHRINK_STATIC_MAX_PARTICLES (1 << 22)
 pm_status pm_shrink_static(const float* pos4_in, const float* mom4_in, int64_t n,
                            int32_t n_mesh, double box_mpch, double omega_m, double omega_l,

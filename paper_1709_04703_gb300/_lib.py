@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpmshrink.so")
 
 PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_ENOCONV, PM_EOVERFLOW, PM_ETIMEOUT, PM_EIO = range(8)
-PM_MIXED, PM_FP32_PLAIN, PM_FP64_PLAIN = 0, 1, 2
+PM_MIXED, PM_FP32_PLAIN, PM_FP64_PLAIN, PM_MIXED_FP64 = 0, 1, 2, 3
 PM_GUESS_WARM, PM_GUESS_ZERO, PM_GUESS_LEARNED = 0, 1, 2
 PM_GRAVITY_POISSON, PM_GRAVITY_DIFFUSION, PM_GRAVITY_DIFFUSION_ADE = 0, 1, 2
 PM_BC_PAPER, PM_BC_OPEN, PM_BC_PERIODIC = 0, 1, 2
@@ -31,7 +31,8 @@ EXPORTED = [
     "pm_get_potential", "pm_profile", "pm_profile_read", "pm_launch_count", "pm_last_error",
     "pm_destroy", "pm_shrink_static", "pm_shrink_static_error",
     "pm_batch_init", "pm_batch_step", "pm_batch_stats", "pm_batch_get_particles",
-    "pm_batch_get_lightcone", "pm_batch_last_error", "pm_batch_destroy",
+    "pm_batch_get_lightcone", "pm_batch_get_forces", "pm_batch_last_error",
+    "pm_batch_destroy",
     "pm_mg_smooth", "pm_mg_restrict", "pm_mg_prolong", "pm_selftest_wait", "pm_nn_gemm_bf16", "pm_guess_create", "pm_guess_num_params", "pm_guess_set_params",
     "pm_guess_get_params", "pm_guess_forward", "pm_guess_loss_grad", "pm_guess_adam",
     "pm_guess_last_error", "pm_guess_destroy", "pm_set_guess", "pm_capture",
@@ -117,6 +118,7 @@ def load():
         "pm_batch_stats": (I32, [P, I32, C.POINTER(PmStats)]),
         "pm_batch_get_particles": (I32, [P, I32, P, P, I32, C.POINTER(I64)]),
         "pm_batch_get_lightcone": (I32, [P, I32, P, P, I32, C.POINTER(I64)]),
+        "pm_batch_get_forces": (I32, [P, I32, P, I32, C.POINTER(I64)]),
         "pm_batch_last_error": (C.c_char_p, [P]),
         "pm_batch_destroy": (None, [P]),
         "pm_selftest_wait": (I32, [I32, I64, P]),

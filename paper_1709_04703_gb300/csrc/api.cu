@@ -174,6 +174,10 @@ struct pm_ctx {
   // the coarse levels (compact, level 0 unused)
   double *phi64 = nullptr, *f64 = nullptr;
   std::vector<double*> lu64, lb64;
+  // PM_MIXED_FP64: phi64 is the potential of the run (full (n+2)^3, its
+  // ghost layer the open boundary's values) and prev64 the previous step's
+  // solution for the warm start; f64 the source of the current solve
+  double* prev64 = nullptr;
   BallRule ball_rule{};         // its Gauss-Legendre rule
   std::vector<unsigned char> h_bg;  // host image of bgm + bgw
   unsigned long long* d_cnt = nullptr;  // [0] n_keep, [1] escaped
@@ -736,7 +740,7 @@ pm_status solve64(pm_ctx* ctx) {
     if (st != PM_OK) return st;
     ++it;
   }
-  launch64_to_pair(ctx->st, P, ph, pl);
+  launch64_to_pair(ctx->st, P, ph, pl, false);
   CKL();
   ctx->vcycles_last = it;
   ctx->vcycles_total += it;
@@ -745,9 +749,92 @@ pm_status solve64(pm_ctx* ctx) {
   return PM_OK;
 }
 
+// PM_MIXED_FP64: FP32 V-cycles inside an FP64 defect correction.  The
+// potential is FP64 throughout; each iteration adds the last V-cycle's
+// correction to it in FP64 (k64_correct), evaluates r = f - A Phi in FP64
+// (k64m_defect, r rounded to FP32 as the next V-cycle's right-hand side) and
+// its norm; the residual is read on the host as in solve().
+pm_status solve_m64(pm_ctx* ctx) {
+  const int lo = ctx->lo, s = ctx->s, per = ctx->periodic;
+  Grid fh = full_view(ctx, ctx->f_hi, lo, s), fl = full_view(ctx, ctx->f_lo, lo, s);
+  Grid e0 = compact_view(ctx->lu[0], s), r0 = compact_view(ctx->lb[0], s);
+  GridD P = full_view64(ctx, ctx->phi64, lo, s), F = full_view64(ctx, ctx->f64, lo, s);
+  const double cells = (double)s * s * s;
+  int e = prof_begin(ctx);
+  if (ctx->cfg.guess == PM_GUESS_ZERO) launch64_fill(ctx->st, P, 0.0);
+  // the source of this solve in FP64 (hi + lo of the source kernel's pair):
+  // reads 8 B and writes 8 B per cell
+  launch64_from_pair(ctx->st, fh, fl, F, false);
+  prof_end(ctx, PM_PROF_CORRECT, e, 16.0 * cells);
+  ctx->guess_used_last = 0;
+  int it = 0;
+  bool first = true, started = false;
+  double rel = 0.0;
+  const int blind = std::min(std::max(0, ctx->vc_prev - 1), ctx->cfg.max_vcycles - 1);
+  for (;;) {
+    const int slot = first ? 13 : 11;
+    e = prof_begin(ctx);
+    // Phi += e: reads Phi (8 B) and e (4), writes Phi (8); the defect reads
+    // Phi (8) and f (8) and writes r (4)
+    if (!first) launch64_correct(ctx->st, P, e0);
+    launch64m_defect(ctx->st, P, F, r0, per, ctx->partial, ctx->counter, ctx->d_scal + slot);
+    prof_end(ctx, PM_PROF_DEFECT, e, (first ? 20.0 : 40.0) * cells);
+    first = false;
+    CKL();
+    if (it < blind) {
+      pm_status v = vcycle_run(ctx, e0, r0, true);
+      if (v != PM_OK) return v;
+      ++it;
+      continue;
+    }
+    pm_status st = sync_read(ctx);
+    if (st != PM_OK) return st;
+    const double f2 = ctx->h_scal[0], r2 = ctx->h_scal[slot];
+    rel = f2 > 0 ? std::sqrt(r2 / f2) : 0.0;
+    if (!started) {
+      started = true;
+      ctx->resid_start = f2 > 0 ? std::sqrt(ctx->h_scal[13] / f2) : 0.0;
+      ctx->resid_guess = ctx->resid_start;
+    }
+    if (rel <= ctx->cfg.rtol || f2 == 0.0) break;
+    if (it >= ctx->cfg.max_vcycles) {
+      ctx->vcycles_last = it;
+      ctx->vcycles_total += it;
+      ctx->resid_last = rel;
+      char buf[160];
+      snprintf(buf, sizeof buf, "solve: relative residual %.3e after %d V-cycles (rtol %.1e)",
+               rel, it, ctx->cfg.rtol);
+      return fail(ctx, PM_ENOCONV, buf);
+    }
+    pm_status v = vcycle_run(ctx, e0, r0, true);
+    if (v != PM_OK) return v;
+    ++it;
+  }
+  ctx->vcycles_last = it;
+  ctx->vcycles_total += it;
+  ctx->resid_last = rel;
+  ctx->vc_prev = it;
+  return PM_OK;
+}
+
+// The FP64 potential of PM_MIXED_FP64 (current and previous solution, with
+// the ghost layer) to / from the double-float pairs that pm_potential's
+// setup and outputs use.
+void m64_to_pairs(pm_ctx* ctx, int lo, int s) {
+  launch64_to_pair(ctx->st, full_view64(ctx, ctx->phi64, lo, s),
+                   full_view(ctx, ctx->phi_h[ctx->cur], lo, s),
+                   full_view(ctx, ctx->phi_l[ctx->cur], lo, s), true);
+}
+void m64_from_pairs(pm_ctx* ctx, int lo, int s) {
+  launch64_from_pair(ctx->st, full_view(ctx, ctx->phi_h[ctx->cur], lo, s),
+                     full_view(ctx, ctx->phi_l[ctx->cur], lo, s),
+                     full_view64(ctx, ctx->phi64, lo, s), true);
+}
+
 pm_status solve(pm_ctx* ctx) {
   NvtxRange nvtx("pm solve");
   if (ctx->cfg.precision == PM_FP64_PLAIN) return solve64(ctx);
+  if (ctx->cfg.precision == PM_MIXED_FP64) return solve_m64(ctx);
   const int lo = ctx->lo, s = ctx->s, per = ctx->periodic;
   Grid fh = full_view(ctx, ctx->f_hi, lo, s), fl = full_view(ctx, ctx->f_lo, lo, s);
   Grid e0 = compact_view(ctx->lu[0], s), r0 = compact_view(ctx->lb[0], s);
@@ -1000,8 +1087,12 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
       cfg->max_vcycles < 1)
     return fail(nullptr, PM_EINVAL, "pm_init: invalid schedule, cosmology or tolerance");
   if (cfg->precision != PM_MIXED && cfg->precision != PM_FP32_PLAIN &&
-      cfg->precision != PM_FP64_PLAIN)
+      cfg->precision != PM_FP64_PLAIN && cfg->precision != PM_MIXED_FP64)
     return fail(nullptr, PM_EINVAL, "pm_init: unknown precision");
+  if (cfg->precision == PM_MIXED_FP64 &&
+      (cfg->gravity != PM_GRAVITY_POISSON || cfg->guess == PM_GUESS_LEARNED))
+    return fail(nullptr, PM_EINVAL, "pm_init: PM_MIXED_FP64 solves Poisson's equation from "
+                                    "the warm or zero start");
   if (cfg->precision == PM_FP64_PLAIN &&
       (cfg->gravity != PM_GRAVITY_POISSON || cfg->guess == PM_GUESS_LEARNED))
     return fail(nullptr, PM_EINVAL, "pm_init: PM_FP64_PLAIN solves Poisson's equation from "
@@ -1110,10 +1201,11 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
     }
     if (sl <= 4 || sl % 2) break;
   }
-  if (cfg->precision == PM_FP64_PLAIN) {
+  if (cfg->precision == PM_FP64_PLAIN || cfg->precision == PM_MIXED_FP64) {
     AL(ctx->phi64, sizeof(double) * padded);
     AL(ctx->f64, sizeof(double) * padded);
   }
+  if (cfg->precision == PM_MIXED_FP64) AL(ctx->prev64, sizeof(double) * padded);
   const int maxblk = std::max(std::max(SRC_GRID, defect_blocks(n)), 4096);
   AL(ctx->partial, sizeof(double) * 16 * maxblk);
   AL(ctx->partial_m, 16 * 10 * (size_t)maxblk);
@@ -1154,6 +1246,10 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
   Z(ctx->phi_l[1], sizeof(float) * padded);
   Z(ctx->f_hi, sizeof(float) * padded);
   Z(ctx->f_lo, sizeof(float) * padded);
+  Z(ctx->prev_hi, sizeof(float) * padded);
+  Z(ctx->prev_lo, sizeof(float) * padded);
+  if (ctx->phi64) Z(ctx->phi64, sizeof(double) * padded);
+  if (ctx->prev64) Z(ctx->prev64, sizeof(double) * padded);
   Z(ctx->counter, sizeof(unsigned int) * 4);
   Z(ctx->d_scal, sizeof(double) * 16);
   Z(ctx->d_cnt, sizeof(unsigned long long) * 4);
@@ -1182,6 +1278,7 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
     return fail(ctx, PM_EINVAL, "pm_step: PM_GUESS_LEARNED without a network (pm_set_guess)");
   const int n = ctx->n;
   const bool mixed = ctx->cfg.precision == PM_MIXED;
+  const bool m64 = ctx->cfg.precision == PM_MIXED_FP64;  // Phi kept in FP64
   const bool pair = ctx->cfg.precision != PM_FP32_PLAIN;  // Phi kept as hi + lo
   for (int q = 0; q < n_steps; ++q) {
     NvtxRange nvtx_step("pm step");
@@ -1297,6 +1394,10 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
       prof_end(ctx, PM_PROF_CORRECT, e, 32.0 * cells);
       set_shift(sg);
       CKL();
+    } else if (!per && m64) {
+      e = prof_begin(ctx);
+      launch_boundary64(ctx->st, full_view64(ctx, ctx->phi64, lo, s), n, lo, ctx->d_scal + 1, S);
+      prof_end(ctx, PM_PROF_BOUNDARY, e, 8.0 * 6.0 * (s + 2.0) * (s + 2.0));
     } else if (!per) {
       e = prof_begin(ctx);
       for (int q = 0; q < (mixed ? 2 : 1); ++q)  // both buffers carry the ghosts
@@ -1318,10 +1419,20 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
           w = d0 > 0 ? (float)((ctx->a_half[k] - ctx->ah_hist[1]) / d0) : 0.0f;
         }
         e = prof_begin(ctx);
-        launch_predict(ctx->st, full_view(ctx, ctx->phi_h[ctx->cur], lo, s),
-                       full_view(ctx, ctx->phi_l[ctx->cur], lo, s),
-                       full_view(ctx, ctx->prev_hi, lo, s),
-                       full_view(ctx, ctx->prev_lo, lo, s), w, pair);
+        if (m64) {
+          double w64 = 0.0;
+          if (ctx->n_sol >= 2) {
+            double d0 = ctx->ah_hist[1] - ctx->ah_hist[0];
+            w64 = d0 > 0 ? (ctx->a_half[k] - ctx->ah_hist[1]) / d0 : 0.0;
+          }
+          launch64_predict(ctx->st, full_view64(ctx, ctx->phi64, lo, s),
+                           full_view64(ctx, ctx->prev64, lo, s), w64);
+        } else {
+          launch_predict(ctx->st, full_view(ctx, ctx->phi_h[ctx->cur], lo, s),
+                         full_view(ctx, ctx->phi_l[ctx->cur], lo, s),
+                         full_view(ctx, ctx->prev_hi, lo, s),
+                         full_view(ctx, ctx->prev_lo, lo, s), w, pair);
+        }
         prof_end(ctx, PM_PROF_CORRECT, e, 32.0 * cells);
       }
     }
@@ -1341,7 +1452,10 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
     if (do_flag) keep_bounds(0.5 * n, R1, &klo, &khi);
     e = prof_begin(ctx);
     // gradient field: read Phi hi + lo, write G (24 B/cell)
-    launch_grad(ctx->st, ctx->phi_h[ctx->cur], ctx->phi_l[ctx->cur], n, lo, s, per, ctx->grad);
+    if (m64)
+      launch64_grad(ctx->st, ctx->phi64, n, lo, s, per, ctx->grad);
+    else
+      launch_grad(ctx->st, ctx->phi_h[ctx->cur], ctx->phi_l[ctx->cur], n, lo, s, per, ctx->grad);
     if (ctx->cfg.assignment == PM_ASSIGN_TSC)
       launch_gather_tsc(ctx->st, ctx->pos, ctx->mom, N, ctx->grad, n, lo, s, per,
                         (float)(ctx->a_half[k] * ctx->dtau[k]),
@@ -1412,9 +1526,9 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
 pm_status pm_shrink(pm_ctx* ctx, double a, int64_t* n_active_out) {
   if (!ctx) return fail(nullptr, PM_EINVAL, "pm_shrink: NULL context");
   if (!(a > 0)) return fail(ctx, PM_EINVAL, "pm_shrink: a must be > 0");
-  const double om = ctx->cfg.omega_m, ol = ctx->cfg.omega_l;
-  double chi = C_OVER_H0 * (tau_of_a(1.0, om, ol) - tau_of_a(a, om, ol));
-  double R = chi / (ctx->cfg.box_mpch / ctx->n) + ctx->cfg.buffer_cells;
+  // the keep rule shared with the allocation-free compaction (noalloc.cu)
+  const double R = pm::shrink_radius_cells(ctx->n, ctx->cfg.box_mpch, ctx->cfg.omega_m,
+                                           ctx->cfg.omega_l, ctx->cfg.buffer_cells, a);
   if (is_open(ctx, R) && ctx->cfg.bc != PM_BC_PERIODIC) {
     pm_status st = shrink_to(ctx, R, a, false);
     if (st != PM_OK) return st;
@@ -1449,10 +1563,13 @@ pm_status pm_potential(pm_ctx* ctx, const double* delta_dev, double a, int32_t b
     launch_fill(ctx->st, gl, 0.0f, false);
   }
   CKL();
+  const bool m64 = ctx->cfg.precision == PM_MIXED_FP64;
+  if (m64) m64_from_pairs(ctx, 0, n);  // zero interior, boundary values
   int guess = ctx->cfg.guess;
   ctx->cfg.guess = PM_GUESS_WARM;  // already zeroed
   st = solve(ctx);
   ctx->cfg.guess = guess;
+  if (m64 && st == PM_OK) m64_to_pairs(ctx, 0, n);
   if (vcycles_out) *vcycles_out = ctx->vcycles_last;
   if (resid_out) *resid_out = ctx->resid_last;
   if (st != PM_OK) return st;
@@ -1873,13 +1990,18 @@ pm_status pm_get_potential(pm_ctx* ctx, double* phi_host, int32_t* lo_out, int32
   if (!ctx) return fail(nullptr, PM_EINVAL, "pm_get_potential: NULL context");
   const int P = ctx->P, lo = ctx->lo, s = ctx->s;
   const size_t padded = (size_t)P * P * P;
-  std::vector<float> hi(padded), lo_(padded);
-  CK(cudaMemcpyAsync(hi.data(), ctx->phi_h[ctx->cur], sizeof(float) * padded,
-                     cudaMemcpyDeviceToHost,
-                     ctx->st));
-  CK(cudaMemcpyAsync(lo_.data(), ctx->phi_l[ctx->cur], sizeof(float) * padded,
-                     cudaMemcpyDeviceToHost,
-                     ctx->st));
+  const bool m64 = ctx->cfg.precision == PM_MIXED_FP64;
+  std::vector<float> hi(m64 ? 0 : padded), lo_(m64 ? 0 : padded);
+  std::vector<double> d64(m64 ? padded : 0);
+  if (m64) {
+    CK(cudaMemcpyAsync(d64.data(), ctx->phi64, sizeof(double) * padded, cudaMemcpyDeviceToHost,
+                       ctx->st));
+  } else {
+    CK(cudaMemcpyAsync(hi.data(), ctx->phi_h[ctx->cur], sizeof(float) * padded,
+                       cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(lo_.data(), ctx->phi_l[ctx->cur], sizeof(float) * padded,
+                       cudaMemcpyDeviceToHost, ctx->st));
+  }
   CK(cudaStreamSynchronize(ctx->st));
   if (phi_host) {
     const int Q = s + 2;
@@ -1887,7 +2009,8 @@ pm_status pm_get_potential(pm_ctx* ctx, double* phi_host, int32_t* lo_out, int32
       for (int j = 0; j < Q; ++j)
         for (int i = 0; i < Q; ++i) {
           size_t src = ((size_t)(lo + k) * P + (lo + j)) * P + (lo + i);
-          phi_host[((size_t)k * Q + j) * Q + i] = (double)hi[src] + (double)lo_[src];
+          phi_host[((size_t)k * Q + j) * Q + i] =
+              m64 ? d64[src] : (double)hi[src] + (double)lo_[src];
         }
   }
   if (lo_out) *lo_out = lo;
@@ -1931,14 +2054,20 @@ pm_status pm_save(pm_ctx* ctx, const char* path) {
   if (!f) return fail(ctx, PM_EIO, std::string("pm_save: cannot open ") + path);
   std::vector<char> buf(CKPT_CHUNK);
   const size_t pb = sizeof(float4), gb = sizeof(float) * (size_t)h.padded;
+  // PM_MIXED_FP64 keeps its potential in FP64: those two arrays instead of
+  // the four pair arrays (the same byte count)
+  const bool m64 = ctx->cfg.precision == PM_MIXED_FP64;
   bool ok = std::fwrite(&h, sizeof h, 1, f) == 1 &&
             dev_to_file(f, ctx->pos, pb * h.n_active, buf) &&
             dev_to_file(f, ctx->mom, pb * h.n_active, buf) &&
             dev_to_file(f, ctx->lc_pos, pb * h.n_lc, buf) &&
             dev_to_file(f, ctx->lc_mom, pb * h.n_lc, buf) &&
-            dev_to_file(f, ctx->phi_h[ctx->cur], gb, buf) &&
-            dev_to_file(f, ctx->phi_l[ctx->cur], gb, buf) &&
-            dev_to_file(f, ctx->prev_hi, gb, buf) && dev_to_file(f, ctx->prev_lo, gb, buf);
+            (m64 ? dev_to_file(f, ctx->phi64, 2 * gb, buf) &&
+                       dev_to_file(f, ctx->prev64, 2 * gb, buf)
+                 : dev_to_file(f, ctx->phi_h[ctx->cur], gb, buf) &&
+                       dev_to_file(f, ctx->phi_l[ctx->cur], gb, buf) &&
+                       dev_to_file(f, ctx->prev_hi, gb, buf) &&
+                       dev_to_file(f, ctx->prev_lo, gb, buf));
   ok = (std::fclose(f) == 0) && ok;
   if (!ok) return fail(ctx, PM_EIO, std::string("pm_save: writing ") + path + " failed");
   return PM_OK;
@@ -1967,19 +2096,41 @@ pm_status pm_load(pm_ctx* ctx, const char* path) {
   if (h.step < 0 || h.step > ctx->cfg.n_steps || h.n_active < 0 || h.n_lc < 0 ||
       h.n_active > ctx->N0 || h.n_lc > ctx->N0 ||  // the record mode keeps both
       (ctx->cfg.shrink != PM_SHRINK_RECORD && h.n_active + h.n_lc > ctx->N0) ||
-      (h.cur != 0 && h.cur != 1)) {
+      (h.cur != 0 && h.cur != 1) || h.n_sol < 0 || h.vc_prev < 0 ||
+      h.vc_prev > ctx->cfg.max_vcycles || h.vcycles_last < 0 ||
+      (h.field_ready != 0 && h.field_ready != 1) || (h.cube_valid != 0 && h.cube_valid != 1)) {
     std::fclose(f);
     return fail(ctx, PM_EINVAL, "pm_load: inconsistent checkpoint header");
   }
+  if (h.cube_valid) {
+    // the active cube is a function of the schedule: the one of the last
+    // completed step (or of the step that stopped early); anything else
+    // would index the level arrays outside their allocations
+    bool match = false;
+    for (int k = std::max(0, h.step - 1); k <= h.step && k <= ctx->cfg.n_steps; ++k) {
+      int lo, s, per;
+      geometry(ctx, ctx->R[k], &lo, &s, &per);
+      match = match || (lo == h.lo && s == h.s && per == h.periodic);
+    }
+    if (!match) {
+      std::fclose(f);
+      return fail(ctx, PM_EINVAL, "pm_load: the checkpoint's active cube does not belong to "
+                                  "its step");
+    }
+  }
   std::vector<char> buf(CKPT_CHUNK);
   const size_t pb = sizeof(float4), gb = sizeof(float) * (size_t)padded;
+  const bool m64 = ctx->cfg.precision == PM_MIXED_FP64;
   bool ok = file_to_dev(f, ctx->pos, pb * h.n_active, buf) &&
             file_to_dev(f, ctx->mom, pb * h.n_active, buf) &&
             file_to_dev(f, ctx->lc_pos, pb * h.n_lc, buf) &&
             file_to_dev(f, ctx->lc_mom, pb * h.n_lc, buf) &&
-            file_to_dev(f, ctx->phi_h[h.cur], gb, buf) &&
-            file_to_dev(f, ctx->phi_l[h.cur], gb, buf) &&
-            file_to_dev(f, ctx->prev_hi, gb, buf) && file_to_dev(f, ctx->prev_lo, gb, buf);
+            (m64 ? file_to_dev(f, ctx->phi64, 2 * gb, buf) &&
+                       file_to_dev(f, ctx->prev64, 2 * gb, buf)
+                 : file_to_dev(f, ctx->phi_h[h.cur], gb, buf) &&
+                       file_to_dev(f, ctx->phi_l[h.cur], gb, buf) &&
+                       file_to_dev(f, ctx->prev_hi, gb, buf) &&
+                       file_to_dev(f, ctx->prev_lo, gb, buf));
   std::fclose(f);
   if (!ok) return fail(ctx, PM_EIO, std::string("pm_load: reading ") + path + " failed");
   ctx->step = h.step;
@@ -2066,6 +2217,7 @@ void pm_destroy(pm_ctx* ctx) {
   for (double* p : ctx->lu64) if (p) cudaFree(p);
   for (double* p : ctx->lb64) if (p) cudaFree(p);
   if (ctx->phi64) cudaFree(ctx->phi64);
+  if (ctx->prev64) cudaFree(ctx->prev64);
   if (ctx->f64) cudaFree(ctx->f64);
   drop_graph(ctx);
   for (auto& e : ctx->ev) cudaEventDestroy(e);
@@ -2730,8 +2882,10 @@ pm_status pm_batch_step(pm_batch* B, int32_t n_steps) {
         if (do_flag) keep_bounds(0.5 * c->n, R1, &e.klo, &e.khi);
         e.flags = c->flags;
         e.block_keep = c->block_keep;
-        e.forces = nullptr;
+        e.forces = c->forces;  // NULL unless the realisation stores forces
         e.escaped = c->d_cnt + 1;
+        c->forces_valid = c->forces != nullptr;
+        c->forces_n = c->n_active;
         int nb = gkd_blocks(c->n_active);
         set_dims(e, r, dim3(nb, 1, 1));
         d.push_back(e);
@@ -2806,6 +2960,14 @@ pm_status pm_batch_step(pm_batch* B, int32_t n_steps) {
 pm_status pm_batch_stats(pm_batch* B, int32_t r, pm_stats_t* out) {
   if (!B || r < 0 || r >= B->R) return bfail(B, PM_EINVAL, "pm_batch_stats: bad argument");
   return pm_stats(B->ctx[r], out);
+}
+
+pm_status pm_batch_get_forces(pm_batch* B, int32_t r, float* f4, int32_t host_mem,
+                              int64_t* n_out) {
+  if (!B || r < 0 || r >= B->R) return bfail(B, PM_EINVAL, "pm_batch_get_forces: bad argument");
+  pm_status st = pm_get_forces(B->ctx[r], f4, host_mem, n_out);
+  if (st != PM_OK) B->err = B->ctx[r]->err;
+  return st;
 }
 
 pm_status pm_batch_get_particles(pm_batch* B, int32_t r, float* pos4, float* mom4,

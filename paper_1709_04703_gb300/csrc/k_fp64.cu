@@ -189,16 +189,147 @@ __global__ void __launch_bounds__(256) k64_from_pair(Grid hi, Grid lo, GridD out
   out.base[gidxd(out, i, j, k)] = (double)hi.base[q] + (double)lo.base[gidx(lo, i, j, k)];
 }
 
-// hi = fl(v), lo = fl(v - hi) over the interior
-__global__ void __launch_bounds__(256) k64_to_pair(GridD in, Grid hi, Grid lo) {
-  const int s = in.s;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
-  if (i >= s || j >= s) return;
+// hi = fl(v), lo = fl(v - hi) over the interior, or also the ghost layer
+__global__ void __launch_bounds__(256) k64_to_pair(GridD in, Grid hi, Grid lo, int ghost) {
+  const int g = ghost ? 1 : 0, m = in.s + 2 * g;
+  const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y * blockDim.y + threadIdx.y;
+  if (a >= m || b >= m) return;
+  const int i = a - g, j = b - g, k = (int)blockIdx.z - g;
   const double v = in.base[gidxd(in, i, j, k)];
   const float h = (float)v;
   hi.base[gidx(hi, i, j, k)] = h;
   lo.base[gidx(lo, i, j, k)] = (float)(v - (double)h);
+}
+
+// ---------------------------------------------------------------------------
+// Mixed precision with an FP64 outer loop (PM_MIXED_FP64): the potential
+// stays in FP64 for the whole run; each V-cycle (FP32) solves A e = r for
+// the residual r of the FP64 defect below, and the correction is added to
+// the FP64 potential.
+// ---------------------------------------------------------------------------
+
+// Phi += e over the interior (e: the FP32 correction of the last V-cycle)
+__global__ void __launch_bounds__(256) k64_correct(GridD p, Grid e) {
+  pdl_wait();
+  pdl_release();
+  const int s = p.s;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= s || j >= s) return;
+  p.base[gidxd(p, i, j, k)] += (double)e.base[gidx(e, i, j, k)];
+}
+
+// r = f - (sum_nb Phi - 6 Phi) in FP64 at every interior cell (ghost layer:
+// Dirichlet data, or the grid wraps), stored rounded to FP32 in rb (the
+// V-cycle's right-hand side).  ||r||^2 of the stored values: per thread in
+// FP32 over its run of planes, then in FP64; the last block adds the block
+// sums in block order into *out.  Each thread walks a run of planes and
+// rolls its column's z neighbours through registers.
+__global__ void __launch_bounds__(256) k64m_defect(GridD p, GridD f, Grid rb, int periodic,
+                                                   double* __restrict__ partial,
+                                                   unsigned int* counter,
+                                                   double* __restrict__ out) {
+  pdl_wait();
+  pdl_release();
+  const int s = p.s;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int chunk = (s + gridDim.z - 1) / gridDim.z;
+  const int k0 = blockIdx.z * chunk, k1 = min(s, k0 + chunk);
+  float r2 = 0.0f;
+  if (i < s && j < s && k0 < k1) {
+    const double* P = p.base;
+    const long long dxm = wm(i, s, periodic) - i, dxp = wp(i, s, periodic) - i;
+    const long long dym = (long long)(wm(j, s, periodic) - j) * p.sy;
+    const long long dyp = (long long)(wp(j, s, periodic) - j) * p.sy;
+    double zm = P[gidxd(p, i, j, wm(k0, s, periodic))];
+    double zc = P[gidxd(p, i, j, k0)];
+    for (int k = k0; k < k1; ++k) {
+      const long long c = gidxd(p, i, j, k);
+      const double zp = P[gidxd(p, i, j, wp(k, s, periodic))];
+      const double nb = ((P[c + dxm] + P[c + dxp]) + (P[c + dym] + P[c + dyp])) + (zm + zp);
+      const double r = fma(6.0, zc, f.base[gidxd(f, i, j, k)]) - nb;
+      const float r32 = (float)r;
+      rb.base[gidx(rb, i, j, k)] = r32;
+      r2 = fmaf(r32, r32, r2);
+      zm = zc;
+      zc = zp;
+    }
+  }
+  __shared__ double sm[8];
+  __shared__ bool last;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double w = warp_sum((double)r2);
+  if (lane == 0) sm[warp] = w;
+  __syncthreads();
+  const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+  const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  if (tid == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += sm[q];
+    partial[bid] = t;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == nblk - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  double acc = 0.0;
+  for (unsigned q = tid; q < nblk; q += 256) acc += __ldcg(partial + q);
+  acc = warp_sum(acc);
+  __syncthreads();
+  if (lane == 0) sm[warp] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += sm[q];
+    *out = t;
+    *counter = 0u;
+  }
+}
+
+// warm start extrapolated in time, Phi <- Phi + w (Phi - Phi_prev),
+// Phi_prev <- old Phi (interior; the ghost layer keeps its boundary values)
+__global__ void __launch_bounds__(256) k64_predict(GridD p, GridD q, double w) {
+  pdl_wait();
+  pdl_release();
+  const int s = p.s;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= s || j >= s) return;
+  const long long c = gidxd(p, i, j, k);
+  const double cur = p.base[c], prev = q.base[c];
+  q.base[c] = cur;
+  p.base[c] = cur + (cur - prev) * w;
+}
+
+// the interior set to v
+__global__ void __launch_bounds__(256) k64_fill(GridD p, double v) {
+  const int s = p.s;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= s || j >= s) return;
+  p.base[gidxd(p, i, j, blockIdx.z)] = v;
+}
+
+// G(c) = (gx, gy, gz, 0): centred differences of the FP64 potential at every
+// cell of the active cube, rounded to FP32 (the gather's gradient field),
+// in the full (n+2)^3 layout
+__global__ void __launch_bounds__(256) k64_grad(const double* __restrict__ ph, int n, int lo,
+                                                int s, int periodic, float4* __restrict__ G) {
+  pdl_wait();
+  pdl_release();
+  const int P = n + 2;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= s || j >= s) return;
+  const int X = lo + i, Y = lo + j, Z = lo + k;
+  auto w = [&](int a) { return periodic ? (a < 0 ? a + n : (a >= n ? a - n : a)) : a; };
+  auto at = [&](int x, int y, int z) {
+    return __ldg(ph + ((long long)(z + 1) * P + (y + 1)) * P + (x + 1));
+  };
+  const long long c = ((long long)(Z + 1) * P + (Y + 1)) * P + (X + 1);
+  G[c] = make_float4((float)(at(w(X + 1), Y, Z) - at(w(X - 1), Y, Z)),
+                     (float)(at(X, w(Y + 1), Z) - at(X, w(Y - 1), Z)),
+                     (float)(at(X, Y, w(Z + 1)) - at(X, Y, w(Z - 1))), 0.0f);
 }
 
 namespace {
@@ -241,8 +372,34 @@ void launch64_from_pair(cudaStream_t st, Grid hi, Grid lo, GridD out, bool ghost
   k64_from_pair<<<g64_full(m), dim3(32, 8), 0, st>>>(hi, lo, out, ghost ? 1 : 0);
   note_launch();
 }
-void launch64_to_pair(cudaStream_t st, GridD in, Grid hi, Grid lo) {
-  k64_to_pair<<<g64_full(in.s), dim3(32, 8), 0, st>>>(in, hi, lo);
+void launch64_to_pair(cudaStream_t st, GridD in, Grid hi, Grid lo, bool ghost) {
+  const int m = in.s + (ghost ? 2 : 0);
+  k64_to_pair<<<g64_full(m), dim3(32, 8), 0, st>>>(in, hi, lo, ghost ? 1 : 0);
+  note_launch();
+}
+void launch64_correct(cudaStream_t st, GridD p, Grid e) {
+  launch_pdl(k64_correct, g64_full(p.s), dim3(32, 8), 0, st, p, e);
+  note_launch();
+}
+void launch64m_defect(cudaStream_t st, GridD p, GridD f, Grid rb, int periodic, double* partial,
+                      unsigned int* counter, double* out) {
+  const int s = p.s;
+  launch_pdl(k64m_defect, dim3((unsigned)((s + 31) / 32), (unsigned)((s + 7) / 8),
+                               (unsigned)(s < 16 ? s : 16)),
+             dim3(32, 8), 0, st, p, f, rb, periodic, partial, counter, out);
+  note_launch();
+}
+void launch64_predict(cudaStream_t st, GridD p, GridD q, double w) {
+  launch_pdl(k64_predict, g64_full(p.s), dim3(32, 8), 0, st, p, q, w);
+  note_launch();
+}
+void launch64_fill(cudaStream_t st, GridD p, double v) {
+  k64_fill<<<g64_full(p.s), dim3(32, 8), 0, st>>>(p, v);
+  note_launch();
+}
+void launch64_grad(cudaStream_t st, const double* ph, int n, int lo, int s, int periodic,
+                   float4* G) {
+  launch_pdl(k64_grad, g64_full(s), dim3(32, 8), 0, st, ph, n, lo, s, periodic, G);
   note_launch();
 }
 

@@ -751,24 +751,28 @@ void launch_diff_rhs(cudaStream_t st, int grid, Grid sh, Grid sl, double scale, 
 // Q_ab = 3 S_ab - delta_ab tr(S).  mom = (q0, dx, dy, dz, Sxx, Syy, Szz, Sxy,
 // Sxz, Syz).  Written to the hi/lo planes (lo = 0 when want_lo == 0).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void d_boundary(const BI& bi, Grid ph, Grid pl, int n, int lo,
-                                                  const double* __restrict__ mom,
-                                                  double S, int want_lo){
-  const int s = ph.s;
+// ghost cell t of the 6 (s+2)^2 faces of a cube of side s: its (i, j, k)
+// in cube coordinates (-1 or s on the face's axis)
+__device__ __forceinline__ bool ghost_cell(long long t, int s, int& i, int& j, int& k) {
   const int P = s + 2;
   const long long per_face = (long long)P * P;
-  long long t = bi.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= 6 * per_face) return;
+  if (t >= 6 * per_face) return false;
   int face = (int)(t / per_face);
   int rem = (int)(t % per_face);
   int u = rem % P - 1, v = rem / P - 1;
-  int i, j, k;
   int side = (face & 1) ? s : -1;
   switch (face >> 1) {
     case 0: i = side; j = u; k = v; break;
     case 1: j = side; i = u; k = v; break;
     default: k = side; i = u; j = v; break;
   }
+  return true;
+}
+
+// the multipole potential at the centre of cube cell (i, j, k) of a cube at
+// lo in an n^3 mesh
+__device__ __forceinline__ double ghost_value(int n, int lo, int i, int j, int k,
+                                              const double* __restrict__ mom, double S) {
   const double q0 = mom[0], dx = mom[1], dy = mom[2], dz = mom[3];
   const double sxx = mom[4], syy = mom[5], szz = mom[6];
   const double sxy = mom[7], sxz = mom[8], syz = mom[9];
@@ -780,8 +784,16 @@ __device__ __forceinline__ void d_boundary(const BI& bi, Grid ph, Grid pl, int n
   double r = sqrt(r2);
   double qr = qxx * x * x + qyy * y * y + qzz * z * z +
               2.0 * (qxy * x * y + qxz * x * z + qyz * y * z);
-  double phi = -(S / (4.0 * 3.14159265358979323846)) *
-               (q0 / r + (dx * x + dy * y + dz * z) / (r * r2) + 0.5 * qr / (r2 * r2 * r));
+  return -(S / (4.0 * 3.14159265358979323846)) *
+         (q0 / r + (dx * x + dy * y + dz * z) / (r * r2) + 0.5 * qr / (r2 * r2 * r));
+}
+
+__device__ __forceinline__ void d_boundary(const BI& bi, Grid ph, Grid pl, int n, int lo,
+                                                  const double* __restrict__ mom,
+                                                  double S, int want_lo){
+  int i, j, k;
+  if (!ghost_cell(bi.x * (long long)blockDim.x + threadIdx.x, ph.s, i, j, k)) return;
+  const double phi = ghost_value(n, lo, i, j, k, mom, S);
   float hi = (float)phi;
   int gi = gidx(ph, i, j, k);
   ph.base[gi] = hi;
@@ -799,6 +811,22 @@ void launch_boundary(cudaStream_t st, Grid ph, Grid pl, int n, int lo, const dou
   long long tot = 6LL * (ph.s + 2) * (ph.s + 2);
   int grid = (int)((tot + 255) / 256);
   k_boundary<<<grid, 256, 0, st>>>(ph, pl, n, lo, mom, S, want_lo ? 1 : 0);
+  note_launch();
+}
+
+// The same Dirichlet values into the ghost layer of an FP64 potential
+// (PM_MIXED_FP64).
+__global__ void __launch_bounds__(256) k_boundary64(GridD p, int n, int lo,
+                                                    const double* __restrict__ mom, double S) {
+  int i, j, k;
+  if (!ghost_cell(blockIdx.x * (long long)blockDim.x + threadIdx.x, p.s, i, j, k)) return;
+  p.base[(long long)i + (long long)j * p.sy + (long long)k * p.sz] =
+      ghost_value(n, lo, i, j, k, mom, S);
+}
+
+void launch_boundary64(cudaStream_t st, GridD p, int n, int lo, const double* mom, double S) {
+  long long tot = 6LL * (p.s + 2) * (p.s + 2);
+  k_boundary64<<<(int)((tot + 255) / 256), 256, 0, st>>>(p, n, lo, mom, S);
   note_launch();
 }
 

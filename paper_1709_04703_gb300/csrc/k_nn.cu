@@ -52,7 +52,10 @@ __device__ bool tc_mainloop(FillA fa, FillB fb, int ktiles, uint32_t taddr, uint
       }
       tc::mma_commit(mbar);
     }
-    bool done = tc::mbar_wait(mbar, phase, TC_WAIT_LIMIT);
+    // every thread polls, but the block decides together: a thread whose
+    // polls ran out just before the commit landed must not leave the loop
+    // while the others go on (mismatched barriers, a diverged tcgen05.dealloc)
+    const bool done = __syncthreads_and(tc::mbar_wait(mbar, phase, TC_WAIT_LIMIT)) != 0;
     phase ^= 1u;
     if (!done) {
       if (threadIdx.x == 0) atomicOr(err, 1);

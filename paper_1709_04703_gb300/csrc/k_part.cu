@@ -7,9 +7,7 @@
 
 namespace pm {
 
-constexpr int KT = 256;          // threads per block
-constexpr int KITEMS = 4;        // particles per thread
-constexpr int KCHUNK = KT * KITEMS;
+constexpr int KCHUNK = PART_CHUNK;  // KT threads x KITEMS particles per block
 
 // ---------------------------------------------------------------------------
 // Gradient + CIC gather + kick + drift + keep flag.  For each particle: the

@@ -3,6 +3,7 @@
 // counts and offsets, the survivor count) lives in one file-scope device
 // array sized for at most PM_SHRINK_STATIC_MAX_PARTICLES particles; every
 // GPU that loads the library holds it (about 4.1 MB) until the process exits.
+#include <cmath>
 #include <mutex>
 #include <string>
 
@@ -11,7 +12,7 @@
 namespace {
 
 constexpr long long kMaxN = PM_SHRINK_STATIC_MAX_PARTICLES;
-constexpr long long kChunk = 1024;  // particles per block of the compaction kernels
+constexpr long long kChunk = pm::PART_CHUNK;  // particles per block of the compaction kernels
 constexpr long long kMaxBlocks = (kMaxN + kChunk - 1) / kChunk;
 constexpr size_t kFlagsOff = 0;                                   // u8 per particle
 constexpr size_t kCountsOff = (size_t)kMaxN;                      // u32 per block
@@ -27,7 +28,9 @@ static __device__ __align__(256) unsigned char g_shrink_scratch[kBytes];
 constexpr int kMaxDevices = 64;
 unsigned char* g_scratch_dev[kMaxDevices] = {};
 std::mutex g_scratch_mu;
-std::string g_static_err;
+// the last failure's text, per calling thread: concurrent failing calls do
+// not overwrite each other's message
+thread_local std::string g_static_err;
 
 pm_status static_fail(pm_status code, const std::string& msg) {
   g_static_err = msg;
@@ -43,7 +46,9 @@ extern "C" pm_status pm_shrink_static(const float* pos4_in, const float* mom4_in
                                       double omega_l, double buffer_cells, double a,
                                       float* pos4_keep, float* mom4_keep, float* pos4_leave,
                                       float* mom4_leave, int64_t* n_keep_out, void* stream) {
-  if (n < 0 || n_mesh < 4 || !(box_mpch > 0) || !(omega_m > 0) || !(a > 0) || !n_keep_out)
+  if (n < 0 || n_mesh < 4 || !(box_mpch > 0) || !(omega_m > 0) || !(a > 0) || !n_keep_out ||
+      !std::isfinite(box_mpch) || !std::isfinite(omega_m) || !std::isfinite(omega_l) ||
+      !std::isfinite(buffer_cells) || !std::isfinite(a))
     return static_fail(PM_EINVAL, "pm_shrink_static: bad argument");
   if (n > kMaxN)
     return static_fail(PM_EINVAL,

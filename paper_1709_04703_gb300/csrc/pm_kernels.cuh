@@ -60,7 +60,16 @@ int defect64_blocks(int s);
 void launch64_defect(cudaStream_t st, GridD p, GridD f, int periodic, double* partial,
                      unsigned int* counter, double* out);
 void launch64_from_pair(cudaStream_t st, Grid hi, Grid lo, GridD out, bool ghost);
-void launch64_to_pair(cudaStream_t st, GridD in, Grid hi, Grid lo);
+void launch64_to_pair(cudaStream_t st, GridD in, Grid hi, Grid lo, bool ghost);
+// mixed precision with an FP64 outer loop (PM_MIXED_FP64)
+void launch64_correct(cudaStream_t st, GridD p, Grid e);
+void launch64m_defect(cudaStream_t st, GridD p, GridD f, Grid rb, int periodic, double* partial,
+                      unsigned int* counter, double* out);
+void launch64_predict(cudaStream_t st, GridD p, GridD q, double w);
+void launch64_fill(cudaStream_t st, GridD p, double v);
+void launch64_grad(cudaStream_t st, const double* ph, int n, int lo, int s, int periodic,
+                   float4* G);
+void launch_boundary64(cudaStream_t st, GridD p, int n, int lo, const double* mom, double S);
 
 // k_mesh.cu
 void launch_drift_deposit(cudaStream_t st, int grid, float4* pos, const float4* mom,
@@ -131,6 +140,12 @@ void launch_gather_tsc(cudaStream_t st, float4* pos, float4* mom, long long N,
                        float c2, int do_flag, float klo, float khi, unsigned char* flags,
                        unsigned int* block_keep, float4* forces,
                        unsigned long long* escaped);
+// Particles per block of the particle kernels (gather, keep flags, block
+// scan, stable scatter): KT threads of KITEMS particles each.  Callers that
+// size per-block scratch themselves use PART_CHUNK.
+constexpr int KT = 256;
+constexpr int KITEMS = 4;
+constexpr int PART_CHUNK = KT * KITEMS;
 int gkd_blocks(long long N);
 // G: gradient field of k_grad (NULL: differences taken from Phi directly)
 void launch_gather_kick_drift(cudaStream_t st, float4* pos, float4* mom, long long N,

@@ -7,7 +7,8 @@ import torch
 
 from . import _lib as L
 
-_PREC = {"mixed": L.PM_MIXED, "fp32": L.PM_FP32_PLAIN, "fp64": L.PM_FP64_PLAIN}
+_PREC = {"mixed": L.PM_MIXED, "fp32": L.PM_FP32_PLAIN, "fp64": L.PM_FP64_PLAIN,
+         "mixed64": L.PM_MIXED_FP64}
 _GUESS = {"warm": L.PM_GUESS_WARM, "zero": L.PM_GUESS_ZERO, "learned": L.PM_GUESS_LEARNED}
 _BC = {"paper": L.PM_BC_PAPER, "open": L.PM_BC_OPEN, "periodic": L.PM_BC_PERIODIC}
 _GRAVITY = {"poisson": L.PM_GRAVITY_POISSON, "diffusion": L.PM_GRAVITY_DIFFUSION,
@@ -90,7 +91,7 @@ class Batch:
     one kernel launch per phase over all of them."""
 
     def __init__(self, realisations, a_init, a_final, n_steps, rtol=1e-7, max_vcycles=50,
-                 buffer_cells=1.0):
+                 buffer_cells=1.0, store_forces=False):
         """realisations: list of dicts with pos, mom, ids, n_mesh, box."""
         lib = L.load()
         R = len(realisations)
@@ -104,7 +105,7 @@ class Batch:
         for r, re in enumerate(realisations):
             cfgs[r] = _config(re["n_mesh"], len(re["pos"]), re["box"], a_init, a_final,
                               n_steps, rtol=rtol, max_vcycles=max_vcycles,
-                              buffer_cells=buffer_cells)
+                              buffer_cells=buffer_cells, store_forces=store_forces)
             p4, m4 = pack(re["pos"], re["mom"], re["ids"])
             dp, dm = torch.from_numpy(p4).cuda(), torch.from_numpy(m4).cuda()
             keep += [dp, dm]
@@ -140,6 +141,14 @@ class Batch:
                                                      m4.ctypes.data, 1, C.byref(n)))
         pos, mom, ids, _ = unpack(p4[:n.value], m4[:n.value])
         return pos, mom, ids
+
+    def forces(self, r):
+        """grad(Phi) at realisation r's particles in its last step, (N, 3)."""
+        n = C.c_int64()
+        f4 = np.zeros((self.caps[r], 4), np.float32)
+        self._check(self._lib.pm_batch_get_forces(self._b, int(r), f4.ctypes.data, 1,
+                                                  C.byref(n)))
+        return f4[:n.value, :3].copy()
 
     def lightcone(self, r):
         n = C.c_int64()

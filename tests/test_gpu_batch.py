@@ -113,3 +113,71 @@ def test_fused_finest_level_matches_batched_passes():
     _compare(batch, 0, ref)
     assert ref[2]["periodic"] == 0
     batch.close()
+
+
+def _rel_rms(a, b):
+    return np.sqrt(((a - b) ** 2).sum() / (b**2).sum())
+
+
+def test_batch_against_oracle():
+    """The batched step against the FP64 oracle directly: three
+    realisations (a periodic 48^3, an open 32^3 that shrinks every step and
+    one of the 48-realisation workload's), each step's forces recomputed by
+    the oracle from the batch's own float32 particles (relative RMS <= 1e-5),
+    and each shrink reproduced bit for bit by the oracle's keep rule and
+    stable partition on the batch's float32 positions (Sec. 2.4)."""
+    from oracle import cosmology as cz
+    from oracle import pm as opm
+    from paper_1709_04703_gb300.sim import Batch
+    a0, a1, steps, rtol = 0.5, 1.0, 6, 1e-7
+    w = ics.batched_workload([101])[0]
+    reals = [_realisation(48, 1500.0, 110, a0), _realisation(32, 8000.0, 111, a0),
+             _realisation(w["n"], w["box"], w["seed"], a0)]
+    scheds = [cz.schedule(re["n_mesh"], re["box"], 0.3, 0.7, a0, a1, steps) for re in reals]
+    batch = Batch(reals, a0, a1, steps, rtol=rtol, store_forces=True)
+    phases = set()
+    shrunk = 0
+    for k in range(steps):
+        before = [batch.particles(r) for r in range(len(reals))]
+        lc0 = [batch.stats(r)["n_lightcone"] for r in range(len(reals))]
+        batch.step(1)
+        for r, re in enumerate(reals):
+            n, sched = re["n_mesh"], scheds[r]
+            p0, m0, i0 = before[r]
+            st = batch.stats(r)
+            F = batch.forces(r)
+            _, _, info = opm.step(p0.astype(np.float64), m0.astype(np.float64), k, sched, n,
+                                  0.3, 1.0, want=True, drift32=True)
+            assert (st["cube_lo"], st["cube_side"], st["periodic"]) == \
+                (info["lo"], info["s"], int(info["periodic"])), (r, k)
+            phases.add(bool(info["periodic"]))
+            ok = info["F"].any(axis=1)
+            assert _rel_rms(F[ok], info["F"][ok]) <= 1e-5, (r, k)
+            # the shrink: survivors and new records, put back in the order the
+            # step began with, must be the oracle's stable partition of them
+            p1, m1, i1 = batch.particles(r)
+            lp, lm, li, la = batch.lightcone(r)
+            lp, lm, li, la = lp[lc0[r]:], lm[lc0[r]:], li[lc0[r]:], la[lc0[r]:]
+            assert len(i1) + len(li) == len(i0)
+            where = {int(v): q for q, v in enumerate(i0)}
+            post_p = np.empty_like(p0)
+            post_m = np.empty_like(m0)
+            for arr_p, arr_m, arr_i in ((p1, m1, i1), (lp, lm, li)):
+                idx = np.array([where[int(v)] for v in arr_i], dtype=np.int64)
+                post_p[idx] = arr_p
+                post_m[idx] = arr_m
+            if opm.is_open(sched["R"][k + 1], n):
+                keep = opm.keep_mask(post_p, sched["R"][k + 1], n)
+            else:
+                keep = np.ones(len(i0), bool)
+            (sp, sm, si), (op, om_, oi) = opm.shrink([post_p, post_m, i0], keep)
+            np.testing.assert_array_equal(i1, si)
+            np.testing.assert_array_equal(p1, sp)
+            np.testing.assert_array_equal(m1, sm)
+            np.testing.assert_array_equal(li, oi)
+            np.testing.assert_array_equal(lp, op)
+            assert np.all(la == np.float32(sched["a"][k + 1])) if len(la) else True
+            shrunk += len(li) > 0
+    batch.close()
+    assert phases == {True, False}
+    assert shrunk >= 3

@@ -85,3 +85,41 @@ def test_another_configuration_is_refused(tmp_path):
     assert e.value.code == L.PM_EIO
     b.step(1)   # the context is still usable
     b.close()
+
+
+def test_corrupted_cube_is_refused(tmp_path):
+    """A header whose active cube does not belong to its step (a truncated
+    or edited file) is refused before anything is written to the device."""
+    import ctypes as C
+    from paper_1709_04703_gb300 import _lib as L
+
+    class Head(C.Structure):   # the leading fields of the checkpoint header
+        _fields_ = [("magic", C.c_char * 8), ("version", C.c_uint32),
+                    ("header_bytes", C.c_uint32), ("cfg", L.PmConfig),
+                    ("step", C.c_int32), ("cur", C.c_int32), ("n_sol", C.c_int32),
+                    ("field_ready", C.c_int32), ("vc_prev", C.c_int32),
+                    ("cube_valid", C.c_int32), ("lo", C.c_int32), ("s", C.c_int32),
+                    ("periodic", C.c_int32)]
+
+    a = _new()
+    a.step(2)
+    path = tmp_path / "a.ckpt"
+    a.save(path)
+    a.close()
+    raw = bytearray(path.read_bytes())
+    h = Head.from_buffer_copy(bytes(raw[:C.sizeof(Head)]))
+    assert h.cube_valid == 1 and h.lo == 0 and h.s == N and h.periodic == 1
+    b = _new()
+    for lo, s, per, n_sol in ((8, 2 * N, 1, h.n_sol), (N, N, 0, h.n_sol), (-1, N, 1, h.n_sol),
+                              (0, N, 7, h.n_sol), (0, N, 1, -3)):
+        bad = Head.from_buffer_copy(bytes(raw[:C.sizeof(Head)]))
+        bad.lo, bad.s, bad.periodic, bad.n_sol = lo, s, per, n_sol
+        p = tmp_path / "bad.ckpt"
+        p.write_bytes(bytes(bad) + bytes(raw[C.sizeof(Head):]))
+        with pytest.raises(L.PmError) as e:
+            b.load(p)
+        assert e.value.code == L.PM_EINVAL, (lo, s, per, n_sol)
+    b.load(path)           # the intact file still loads
+    assert b.stats()["step"] == 2
+    b.step(1)
+    b.close()

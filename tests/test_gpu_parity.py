@@ -9,6 +9,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
+import crossings  # noqa: E402
 from oracle import cosmology as cz  # noqa: E402
 from oracle import pm as opm  # noqa: E402
 from oracle.pk import power_spectrum as opk  # noqa: E402
@@ -392,8 +393,14 @@ def test_run_pm32_power_spectrum_matches_oracle():
     sim.close()
     sched = cz.schedule(n, cfg["box"], OM, OL, cfg["a_init"], cfg["a_final"], cfg["steps"])
     out = opm.run(pos, mom, ids, sched, n, OM, 1.0)
-    assert st["n_active"] == len(out["ids"]) or abs(st["n_active"] - len(out["ids"])) < 20
     assert st["n_active"] + st["n_lightcone"] == n**3
+    # the FP32 and FP64 trajectories differ by a small distance, so a particle
+    # that ends a step that close to the keep cube's face may leave one step
+    # earlier in one run; every differing crossing must be such a particle
+    a_g, x_g = crossings.table(n**3, gi, gp, ci, cp, ca)
+    a_o, x_o = crossings.table(n**3, out["ids"], out["pos"], out["lc_ids"], out["lc_pos"],
+                               out["lc_a"])
+    crossings.check_crossings(a_g, x_g, a_o, x_o, sched, n)
     allg = np.concatenate([gp, cp]).astype(np.float32) % n
     allo = np.concatenate([out["pos"], out["lc_pos"]]) % n
     p4, _ = _dev4(allg.astype(np.float32))
