@@ -135,13 +135,19 @@ def _ics():
 # particles reordered by cell at the start of every SORT_EVERY-th step
 # (--sort-every; 0: the initial order, compacted stably)
 SORT_EVERY = 32
+# FP32 V-cycles that may share one defect in the mixed forms (--inner)
+INNER = 4
+
+
+def _inner(precision):
+    return INNER if precision in ("mixed", "mixed64") else 1
 
 
 def _new_sim(pos, mom, ids, cfg, rtol, precision, guess="warm"):
     from paper_1709_04703_gb300.sim import Sim
     return Sim(pos, mom, ids, cfg["n"], cfg["box"], cfg["a_init"], cfg["a_final"],
                cfg["steps"], rtol=rtol, precision=precision, max_vcycles=100, guess=guess,
-               sort_every=SORT_EVERY)
+               sort_every=SORT_EVERY, inner_vcycles=_inner(precision))
 
 
 STRICT_RTOL = 1e-7
@@ -159,7 +165,9 @@ ARITHMETIC = {
 # ncu dram__bytes_read.sum + dram__bytes_write.sum over the algorithmic bytes
 # of the kernel class's launches at 256^3 on the current kernels
 TRAFFIC_RATIO = {
-    "smooth0": (288.7e6 / 335.5e6, "k_rbgs2 pre + post at 256^3, "
+    # the smoother's algorithmic bytes are 12 B per cell and sweep, 48 B per
+    # pre + post pair of fused passes
+    "smooth0": (288.7e6 / (48.0 * 256**3), "k_rbgs2 pre + post at 256^3, "
                 "profiles/rbgs2_pm256_level0.md"),
     "defect": ((328.7e6 + 514.2e6) / (335.5e6 + 536.9e6), "k_defect<0> + k_defect<1> at "
                "256^3, profiles/defect_gather_deposit_pm256.md"),
@@ -247,7 +255,9 @@ def _variant(pos, mom, ids, cfg, windows, rtol, precision, guess="warm", net=Non
     sim = Sim(pos, mom, ids, cfg["n"], cfg["box"], cfg["a_init"], cfg["a_final"],
               cfg["steps"], rtol=rtol, precision=precision, max_vcycles=100, guess=guess,
               gravity=gravity, bc=bc, shrink=shrink, assignment=assignment,
-              sort_every=SORT_EVERY)
+              sort_every=SORT_EVERY,
+              inner_vcycles=_inner(precision) if gravity == "poisson" and guess != "learned"
+              else 1)
     if net is not None:
         sim.set_guess(net)
     out = {"precision": precision, "guess": guess, "rtol": rtol, "gravity": gravity,
@@ -620,8 +630,8 @@ def run_ours(args):
         raise RuntimeError("the instrumented repeat took a different number of V-cycles")
     sim.close()
     # whole-step algorithmic bytes (N active particles, C active cells, k
-    # V-cycles, o = k + 1 defect evaluations in the mixed forms)
-    o_of = (lambda v: v + 1) if args.precision != "fp32" else (lambda v: 0)
+    # V-cycles, o = k outer defect-correction iterations in the mixed forms)
+    o_of = (lambda v: v) if args.precision != "fp32" else (lambda v: 0)
     step_bytes = sum(64.0 * N + (24.0 + 74.0 * v + 40.0 * o_of(v)) * Cc for N, Cc, v in per_step)
 
     # the same windows with plain FP32 V-cycles at the same tolerance, the
@@ -738,6 +748,7 @@ def run_ours(args):
                                 if args.rtol is None else "given",
                    "plain_fp32_floor": floor,
                    "precision": args.precision, "sort_every": SORT_EVERY,
+                   "inner_vcycles": _inner(args.precision),
                    "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (particles 537 MB, mesh 134 MB)"},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),
@@ -751,8 +762,8 @@ def run_ours(args):
                           "peak": peak, "unit": "GB/s",
                           "frac": round(step_bytes / (ms * 1e-3) / 1e9 / peak, 4),
                           "count": "sum over the timed steps of 64 N + (24 + 74 k + 40 o) C: N "
-                                   "active particles, C active cells, k V-cycles, o = k + 1 "
-                                   "defect evaluations (0 in plain FP32)"},
+                                   "active particles, C active cells, k V-cycles, o = k outer "
+                                   "iterations (0 in plain FP32)"},
         "kernels": kernels,
         "kernels_timing": "CUDA events around each kernel class on the context stream, in an "
                           f"instrumented repeat of the same {K} steps ({prof_wall_ms / K:.3f} "
@@ -774,7 +785,7 @@ def run_ours(args):
 
 
 def main():
-    global SORT_EVERY
+    global SORT_EVERY, INNER
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=40)
@@ -790,6 +801,8 @@ def main():
     ap.add_argument("--sort-every", type=int, default=SORT_EVERY,
                     help="reorder the particles by cell every k-th step (0: never)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--inner", type=int, default=INNER,
+                    help="FP32 V-cycles per defect in the mixed forms (1: one)")
     ap.add_argument("--workload", choices=["pm256", "batch48", "shrink_table"], default="pm256")
     ap.add_argument("--table-n", type=int, default=512,
                     help="shrink_table: particles and mesh per side")
@@ -801,6 +814,7 @@ def main():
     args = ap.parse_args()
     args.steps_given = "--steps" in sys.argv
     SORT_EVERY = max(0, args.sort_every)
+    INNER = max(1, args.inner)
     if args.impl == "reference":
         return run_reference(args)
     from paper_1709_04703_gb300 import build

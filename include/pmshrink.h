@@ -137,6 +137,16 @@ typedef struct {
                             coherent once clustering has scattered the
                             initial order.  Single contexts only (a batch
                             rejects k > 0) */
+  int32_t inner_vcycles; /* PM_MIXED / PM_MIXED_FP64: FP32 V-cycles run on one
+                            correction equation A e = r before the next
+                            defect r = f - A Phi (1, the default: a defect
+                            after every V-cycle; m > 1: while the solver runs
+                            the V-cycles it expects to need without reading
+                            the residual, up to m of them share one defect,
+                            the first from zero, the others from the
+                            iterate, driven by the V-cycle's own FP32
+                            residual).  0..16 (0 acts as 1); a batch needs
+                            <= 1 */
 } pm_config;
 
 /* Fill *cfg with defaults: 32^3 mesh and particles, 250 Mpc/h, Om=0.3,

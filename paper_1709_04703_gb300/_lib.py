@@ -50,6 +50,7 @@ class PmConfig(C.Structure):
         ("bc", C.c_int32), ("shrink", C.c_int32), ("buffer_cells", C.c_double),
         ("store_forces", C.c_int32), ("gravity", C.c_int32), ("c_eff_factor", C.c_double),
         ("assignment", C.c_int32), ("domain", C.c_int32), ("sort_every", C.c_int32),
+        ("inner_vcycles", C.c_int32),
     ]
 
 

@@ -129,6 +129,9 @@ struct NvtxRange {
 
 }  // namespace
 
+// a pair of profiling events around a launch group of one kernel class
+struct Pend { int cls, e0, e1; double bytes; };
+
 struct pm_ctx {
   pm_config cfg;
   cudaStream_t st = nullptr;
@@ -193,19 +196,23 @@ struct pm_ctx {
   bool use_graphs = false;
   bool capturing = false;
   int ev_graph_next = 0;
+  // (one graph per level-0 start: from zero, and from the iterate)
   struct VGraph {
     bool valid = false;
     int lo = 0, s = 0, per = 0, prof = 0, zero0 = 0;
     float *u0 = nullptr, *b0 = nullptr;
     cudaGraphExec_t exec = nullptr;
     long long kernels = 0;
-  } vg;
+    std::vector<struct Pend> pend;  // event pairs recorded inside the graph
+  } vg[2];
+  // the mixed forms' level-0 correction e of A e = r (compact (n+2)^3; its
+  // ghost layer stays zero: homogeneous Dirichlet for the correction)
+  float* ecorr = nullptr;
 
   // per-class event timing (pm_profile)
   bool prof_on = false;
   std::vector<cudaEvent_t> ev;
   int ev_next = 0;
-  struct Pend { int cls, e0, e1; double bytes; };
   std::vector<Pend> pend;
   std::vector<Pend> pend_graph;  // event pairs recorded inside the V-cycle graph
   double prof_ms[PM_PROF_N] = {0};
@@ -413,6 +420,9 @@ pm_status set_cube(pm_ctx* ctx, int lo, int s, int periodic, double R) {
     ctx->ls.push_back(sl);
   }
   if (sl > 8) return fail(ctx, PM_EINVAL, "cube side does not coarsen to <= 8");
+  if (ctx->ecorr)  // the correction's ghost layer (zero) moves with the side
+    CK(cudaMemsetAsync(ctx->ecorr, 0,
+                       sizeof(float) * (size_t)(s + 2) * (s + 2) * (s + 2), ctx->st));
   for (size_t l = 0; l < ctx->ls.size(); ++l) {
     size_t bytes = sizeof(float) * (size_t)(ctx->ls[l] + 2) * (ctx->ls[l] + 2) * (ctx->ls[l] + 2);
     CK(cudaMemsetAsync(ctx->lu[l], 0, bytes, ctx->st));
@@ -449,7 +459,7 @@ constexpr int EV_POOL = 1024;  // events [0, EV_POOL) eager, [EV_POOL, 2 EV_POOL
 int prof_begin(pm_ctx* ctx) {
   if (!ctx->prof_on) return -1;
   if (ctx->capturing) {
-    if (ctx->ev_graph_next + 2 > 2 * EV_POOL) return -1;
+    if ((ctx->ev_graph_next - EV_POOL) % (EV_POOL / 2) + 2 > EV_POOL / 2) return -1;
     int e = ctx->ev_graph_next++;
     // inside a capture only an external record becomes a real event node
     cudaEventRecordWithFlags(ctx->ev[e], ctx->st, cudaEventRecordExternal);
@@ -516,10 +526,12 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
     B[l] = compact_view(ctx->lb[l], ctx->ls[l]);
   }
   const double c0 = (double)ctx->s * ctx->s * ctx->s;
-  // algorithmic bytes per fine cell: pre-smoothing from zero reads b and
-  // writes u (8), otherwise reads u, b and writes u (12); residual +
-  // restriction reads u and b and writes the coarse b and u (9);
-  // prolongation reads u and the coarse u and writes u + P uc (8.5)
+  // algorithmic bytes per fine cell: a red-black Gauss-Seidel sweep reads u
+  // and b and writes u, 12 B per sweep (two sweeps per smoothing: 24; the
+  // fused pass moves 8 from a zero start and 12 otherwise, since its two
+  // sweeps share one read and one write); residual + restriction reads u
+  // and b and writes the coarse b and u (9); prolongation reads u and the
+  // coarse u and writes u + P uc (8.5)
   float h2 = 1.0f;
   int ec = -1;
   // open-boundary ghost factor of level l (spacing H = 2^l), see k_mg.cu
@@ -541,7 +553,7 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
     else
       smooth2(ctx, U[l], B[l], h2, per, gam(l), zs, d0, l > 0 ? LEVEL_SWEEPS : 2);
     if (l == 0) {
-      prof_end(ctx, PM_PROF_SMOOTH0, e, (fused ? (zs ? 8.0 : 12.0) : 32.0) * c0);
+      prof_end(ctx, PM_PROF_SMOOTH0, e, 24.0 * c0);
       e = prof_begin(ctx);
     }
     launch_resid_restrict(ctx->st, Upre[l], B[l], 1.0f / h2, U[l + 1], B[l + 1], per, gam(l),
@@ -577,7 +589,7 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
       launch_rbgs2(ctx->st, W, U[l], B[l], h2, per, gam(l), false, 0, d0);
     else
       smooth2(ctx, U[l], B[l], h2, per, gam(l), false, d0, l > 0 ? LEVEL_SWEEPS : 2);
-    if (l == 0) prof_end(ctx, PM_PROF_SMOOTH0, e, (fused ? 12.0 : 32.0) * c0);
+    if (l == 0) prof_end(ctx, PM_PROF_SMOOTH0, e, 24.0 * c0);
   }
   if (Lc == 0) prof_end(ctx, PM_PROF_COARSE, ec, 0.0);
   CKL();
@@ -585,8 +597,10 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
 }
 
 void drop_graph(pm_ctx* ctx) {
-  if (ctx->vg.exec) cudaGraphExecDestroy(ctx->vg.exec);
-  ctx->vg = pm_ctx::VGraph();
+  for (auto& g : ctx->vg) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = pm_ctx::VGraph();
+  }
 }
 
 // One V-cycle: replay of a graph captured for the current cube / grids, or
@@ -594,14 +608,15 @@ void drop_graph(pm_ctx* ctx) {
 pm_status vcycle_run(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
   // the diffusion substeps change the shift every solve: no graph for them
   if (!ctx->use_graphs || ctx->sig != 0.0f) return vcycle(ctx, u0, b0, zero0);
-  auto& g = ctx->vg;
+  auto& g = ctx->vg[zero0 ? 1 : 0];
   if (!(g.valid && g.lo == ctx->lo && g.s == ctx->s && g.per == ctx->periodic &&
         g.u0 == u0.base && g.b0 == b0.base && g.prof == (int)ctx->prof_on &&
         g.zero0 == (int)zero0)) {
-    drop_graph(ctx);
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = pm_ctx::VGraph();
     CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
     ctx->capturing = true;
-    ctx->ev_graph_next = EV_POOL;
+    ctx->ev_graph_next = EV_POOL + (zero0 ? EV_POOL / 2 : 0);
     ctx->pend_graph.clear();
     long long l0 = g_launches.load();
     pm_status st = vcycle(ctx, u0, b0, zero0);
@@ -629,11 +644,11 @@ pm_status vcycle_run(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
     g.prof = ctx->prof_on;
     g.zero0 = zero0;
     g.kernels = nk;
+    g.pend = ctx->pend_graph;
   }
   CK(cudaGraphLaunch(g.exec, ctx->st));
   g_launches.fetch_add(g.kernels);
-  if (ctx->prof_on)
-    ctx->pend.insert(ctx->pend.end(), ctx->pend_graph.begin(), ctx->pend_graph.end());
+  if (ctx->prof_on) ctx->pend.insert(ctx->pend.end(), g.pend.begin(), g.pend.end());
   return PM_OK;
 }
 
@@ -757,7 +772,7 @@ pm_status solve64(pm_ctx* ctx) {
 pm_status solve_m64(pm_ctx* ctx) {
   const int lo = ctx->lo, s = ctx->s, per = ctx->periodic;
   Grid fh = full_view(ctx, ctx->f_hi, lo, s), fl = full_view(ctx, ctx->f_lo, lo, s);
-  Grid e0 = compact_view(ctx->lu[0], s), r0 = compact_view(ctx->lb[0], s);
+  Grid e0 = compact_view(ctx->ecorr, s), r0 = compact_view(ctx->lb[0], s);
   GridD P = full_view64(ctx, ctx->phi64, lo, s), F = full_view64(ctx, ctx->f64, lo, s);
   const double cells = (double)s * s * s;
   int e = prof_begin(ctx);
@@ -771,6 +786,7 @@ pm_status solve_m64(pm_ctx* ctx) {
   bool first = true, started = false;
   double rel = 0.0;
   const int blind = std::min(std::max(0, ctx->vc_prev - 1), ctx->cfg.max_vcycles - 1);
+  const int inner = std::max(1, ctx->cfg.inner_vcycles);
   for (;;) {
     const int slot = first ? 13 : 11;
     e = prof_begin(ctx);
@@ -782,9 +798,13 @@ pm_status solve_m64(pm_ctx* ctx) {
     first = false;
     CKL();
     if (it < blind) {
-      pm_status v = vcycle_run(ctx, e0, r0, true);
-      if (v != PM_OK) return v;
-      ++it;
+      // up to `inner` FP32 V-cycles on A e = r before the next FP64 defect
+      const int m = std::min(inner, blind - it);
+      for (int q = 0; q < m; ++q) {
+        pm_status v = vcycle_run(ctx, e0, r0, q == 0);
+        if (v != PM_OK) return v;
+        ++it;
+      }
       continue;
     }
     pm_status st = sync_read(ctx);
@@ -837,8 +857,8 @@ pm_status solve(pm_ctx* ctx) {
   if (ctx->cfg.precision == PM_MIXED_FP64) return solve_m64(ctx);
   const int lo = ctx->lo, s = ctx->s, per = ctx->periodic;
   Grid fh = full_view(ctx, ctx->f_hi, lo, s), fl = full_view(ctx, ctx->f_lo, lo, s);
-  Grid e0 = compact_view(ctx->lu[0], s), r0 = compact_view(ctx->lb[0], s);
   const bool mixed = ctx->cfg.precision == PM_MIXED;
+  Grid e0 = compact_view(mixed ? ctx->ecorr : ctx->lu[0], s), r0 = compact_view(ctx->lb[0], s);
   auto ph_of = [&](int q) { return full_view(ctx, ctx->phi_h[q], lo, s); };
   auto pl_of = [&](int q) { return full_view(ctx, ctx->phi_l[q], lo, s); };
   if (ctx->cfg.guess == PM_GUESS_ZERO) {
@@ -862,10 +882,19 @@ pm_status solve(pm_ctx* ctx) {
   const int blind = (net_todo || capture)
                         ? 0
                         : std::min(std::max(0, ctx->vc_prev - 1), ctx->cfg.max_vcycles - 1);
+  const int inner = std::max(1, ctx->cfg.inner_vcycles);
   for (;;) {
-    int e = prof_begin(ctx);
     const int c0 = ctx->cur;
     slot = first ? 13 : 11;
+    // the plain path's residual norm is only needed where it is read: at the
+    // start (resid_start) and once the blind V-cycles are done
+    if (!mixed && !net_todo && !first && it < blind) {
+      pm_status v = vcycle_run(ctx, ph_of(ctx->cur), fh, false);
+      if (v != PM_OK) return v;
+      ++it;
+      continue;
+    }
+    int e = prof_begin(ctx);
     if (mixed && pending) {
       // Phi <- Phi + e, written to the other buffer; reads Phi (8 B), e (4),
       // f (8), writes Phi (8) and r (4) per cell
@@ -889,11 +918,22 @@ pm_status solve(pm_ctx* ctx) {
     first = false;
     CKL();
     if (it < blind) {
-      pm_status v = mixed ? vcycle_run(ctx, e0, r0, true)
-                          : vcycle_run(ctx, ph_of(ctx->cur), fh, false);
-      if (v != PM_OK) return v;
-      ++it;
-      pending = mixed;
+      if (mixed) {
+        // up to `inner` FP32 V-cycles on the same correction equation
+        // A e = r (the first from zero, the next from the iterate; the
+        // V-cycle's own FP32 residual drives them) before the next defect
+        const int m = std::min(inner, blind - it);
+        for (int q = 0; q < m; ++q) {
+          pm_status v = vcycle_run(ctx, e0, r0, q == 0);
+          if (v != PM_OK) return v;
+          ++it;
+        }
+        pending = true;
+      } else {
+        pm_status v = vcycle_run(ctx, ph_of(ctx->cur), fh, false);
+        if (v != PM_OK) return v;
+        ++it;
+      }
       continue;
     }
     pm_status st = sync_read(ctx);
@@ -1063,6 +1103,7 @@ void pm_config_default(pm_config* c) {
   c->shrink = 1;
   c->buffer_cells = 1.0;
   c->store_forces = 0;
+  c->inner_vcycles = 1;
   c->gravity = PM_GRAVITY_POISSON;
   c->c_eff_factor = 0.019;
   c->assignment = PM_ASSIGN_CIC;
@@ -1111,6 +1152,8 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
     return fail(nullptr, PM_EINVAL, "pm_init: assignment is CIC, or TSC with Poisson gravity");
   if (cfg->sort_every < 0)
     return fail(nullptr, PM_EINVAL, "pm_init: sort_every must be >= 0");
+  if (cfg->inner_vcycles < 0 || cfg->inner_vcycles > 16)
+    return fail(nullptr, PM_EINVAL, "pm_init: inner_vcycles must be in [0, 16]");
   if (cfg->gravity != PM_GRAVITY_POISSON &&
       ((cfg->gravity != PM_GRAVITY_DIFFUSION && cfg->gravity != PM_GRAVITY_DIFFUSION_ADE) ||
        !(cfg->c_eff_factor > 0) || cfg->precision != PM_MIXED ||
@@ -1206,6 +1249,8 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
     AL(ctx->f64, sizeof(double) * padded);
   }
   if (cfg->precision == PM_MIXED_FP64) AL(ctx->prev64, sizeof(double) * padded);
+  if (cfg->precision == PM_MIXED || cfg->precision == PM_MIXED_FP64)
+    AL(ctx->ecorr, sizeof(float) * padded);
   const int maxblk = std::max(std::max(SRC_GRID, defect_blocks(n)), 4096);
   AL(ctx->partial, sizeof(double) * 16 * maxblk);
   AL(ctx->partial_m, 16 * 10 * (size_t)maxblk);
@@ -1250,6 +1295,7 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
   Z(ctx->prev_lo, sizeof(float) * padded);
   if (ctx->phi64) Z(ctx->phi64, sizeof(double) * padded);
   if (ctx->prev64) Z(ctx->prev64, sizeof(double) * padded);
+  if (ctx->ecorr) Z(ctx->ecorr, sizeof(float) * padded);
   Z(ctx->counter, sizeof(unsigned int) * 4);
   Z(ctx->d_scal, sizeof(double) * 16);
   Z(ctx->d_cnt, sizeof(unsigned long long) * 4);
@@ -1313,10 +1359,12 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
     auto ghosts = [&](double Sb) {
       if (per) return;
       int eb = prof_begin(ctx);
-      for (int q = 0; q < 2; ++q)  // both buffers carry the ghosts
-        launch_boundary(ctx->st, full_view(ctx, ctx->phi_h[q ^ ctx->cur], lo, s),
-                        full_view(ctx, ctx->phi_l[q ^ ctx->cur], lo, s), n, lo,
-                        ctx->d_scal + 1, Sb, true);
+      // both buffers carry the ghosts
+      const Grid h2 = full_view(ctx, ctx->phi_h[ctx->cur ^ 1], lo, s);
+      const Grid l2 = full_view(ctx, ctx->phi_l[ctx->cur ^ 1], lo, s);
+      launch_boundary(ctx->st, full_view(ctx, ctx->phi_h[ctx->cur], lo, s),
+                      full_view(ctx, ctx->phi_l[ctx->cur], lo, s), n, lo, ctx->d_scal + 1, Sb,
+                      true, &h2, &l2);
       prof_end(ctx, PM_PROF_BOUNDARY, eb, 8.0 * 6.0 * (s + 2.0) * (s + 2.0));
     };
     if (diffusion && !ctx->field_ready) {
@@ -1400,10 +1448,13 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
       prof_end(ctx, PM_PROF_BOUNDARY, e, 8.0 * 6.0 * (s + 2.0) * (s + 2.0));
     } else if (!per) {
       e = prof_begin(ctx);
-      for (int q = 0; q < (mixed ? 2 : 1); ++q)  // both buffers carry the ghosts
-        launch_boundary(ctx->st, full_view(ctx, ctx->phi_h[q ^ ctx->cur], lo, s),
-                        full_view(ctx, ctx->phi_l[q ^ ctx->cur], lo, s), n, lo,
-                        ctx->d_scal + 1, S, pair);
+      // both buffers carry the ghosts in the mixed form (its defect writes
+      // Phi + e to the other buffer)
+      const Grid h2 = full_view(ctx, ctx->phi_h[ctx->cur ^ 1], lo, s);
+      const Grid l2 = full_view(ctx, ctx->phi_l[ctx->cur ^ 1], lo, s);
+      launch_boundary(ctx->st, full_view(ctx, ctx->phi_h[ctx->cur], lo, s),
+                      full_view(ctx, ctx->phi_l[ctx->cur], lo, s), n, lo, ctx->d_scal + 1, S,
+                      pair, mixed ? &h2 : nullptr, mixed ? &l2 : nullptr);
       prof_end(ctx, PM_PROF_BOUNDARY, e, 8.0 * 6.0 * (s + 2.0) * (s + 2.0));
     }
     CKL();
@@ -1961,7 +2012,8 @@ bool cfg_equal(const pm_config& a, const pm_config& b) {
          a.bc == b.bc && a.shrink == b.shrink && a.buffer_cells == b.buffer_cells &&
          a.store_forces == b.store_forces && a.gravity == b.gravity &&
          a.c_eff_factor == b.c_eff_factor && a.assignment == b.assignment &&
-         a.domain == b.domain && a.sort_every == b.sort_every;
+         a.domain == b.domain && a.sort_every == b.sort_every &&
+         a.inner_vcycles == b.inner_vcycles;
 }
 
 // device <-> file through a bounded host buffer
@@ -2218,6 +2270,7 @@ void pm_destroy(pm_ctx* ctx) {
   for (double* p : ctx->lb64) if (p) cudaFree(p);
   if (ctx->phi64) cudaFree(ctx->phi64);
   if (ctx->prev64) cudaFree(ctx->prev64);
+  if (ctx->ecorr) cudaFree(ctx->ecorr);
   if (ctx->f64) cudaFree(ctx->f64);
   drop_graph(ctx);
   for (auto& e : ctx->ev) cudaEventDestroy(e);
@@ -2590,6 +2643,9 @@ pm_status pm_batch_init(int32_t n_real, const pm_config* cfgs, const float* cons
     if (cfgs[r].shrink == PM_SHRINK_RECORD)
       return bfail(nullptr, PM_EINVAL, "pm_batch_init: the fixed-box lightcone record runs "
                                        "per context");
+    if (cfgs[r].inner_vcycles > 1)
+      return bfail(nullptr, PM_EINVAL, "pm_batch_init: batches run one V-cycle per defect "
+                                       "(inner_vcycles <= 1)");
     if (cfgs[r].sort_every != 0)
       return bfail(nullptr, PM_EINVAL, "pm_batch_init: the particle order by cell runs "
                                        "per context (sort_every = 0)");

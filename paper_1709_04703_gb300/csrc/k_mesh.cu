@@ -447,6 +447,11 @@ __device__ __forceinline__ void d_source(const BI& bi,
   __int128 acc[SRC_NV];
 #pragma unroll
   for (int q = 0; q < SRC_NV; ++q) acc[q] = 0;
+  // moments of the thread's column: sum c, c Z, c Z^2 with the count split
+  // c = c1 2^32 + c0 so that every partial sum is exact in int64 (at most
+  // 64 cells of |Z| < 2^11 per thread); the X, Y factors are constant along
+  // the column and applied once at the end in int128
+  long long m0[2] = {0, 0}, mz[2] = {0, 0}, mzz[2] = {0, 0};
   float f2 = 0.f;
   // block (32, 8) covers an x-y tile; the grid's z dimension strides over
   // planes, ZU planes per round with all loads issued before any use
@@ -486,20 +491,32 @@ __device__ __forceinline__ void d_source(const BI& bi,
     fl.base[fi] = f.lo;
     f2 = __fmaf_rn(f.hi, f.hi, f2);
     if (MOMENTS) {
-      int X = 2 * gi + 1 - n, Y = 2 * gj + 1 - n, Z = 2 * gk + 1 - n;
-      __int128 cc = (__int128)c;
-      acc[0] += cc;
-      acc[1] += cc * X;
-      acc[2] += cc * Y;
-      acc[3] += cc * Z;
-      acc[4] += cc * (long long)(X * X);
-      acc[5] += cc * (long long)(Y * Y);
-      acc[6] += cc * (long long)(Z * Z);
-      acc[7] += cc * (long long)(X * Y);
-      acc[8] += cc * (long long)(X * Z);
-      acc[9] += cc * (long long)(Y * Z);
+      const int Z = 2 * gk + 1 - n;
+      const long long c0 = (long long)(cnt & 0xffffffffull), c1 = (long long)(cnt >> 32);
+      m0[0] += c0;
+      m0[1] += c1;
+      mz[0] += c0 * Z;
+      mz[1] += c1 * Z;
+      mzz[0] += c0 * (long long)(Z * Z);
+      mzz[1] += c1 * (long long)(Z * Z);
     }
     }
+  }
+  if (MOMENTS && in_xy) {
+    const long long X = 2 * gi + 1 - n, Y = 2 * gj + 1 - n;
+    const __int128 M0 = (__int128)m0[0] + ((__int128)m0[1] << 32);
+    const __int128 MZ = (__int128)mz[0] + ((__int128)mz[1] << 32);
+    const __int128 MZZ = (__int128)mzz[0] + ((__int128)mzz[1] << 32);
+    acc[0] = M0;
+    acc[1] = M0 * X;
+    acc[2] = M0 * Y;
+    acc[3] = MZ;
+    acc[4] = M0 * (X * X);
+    acc[5] = M0 * (Y * Y);
+    acc[6] = MZZ;
+    acc[7] = M0 * (X * Y);
+    acc[8] = MZ * X;
+    acc[9] = MZ * Y;
   }
   // block reduction: ||f||^2 in double, moments in int128
   __shared__ double sf[32];
@@ -781,36 +798,48 @@ __device__ __forceinline__ double ghost_value(int n, int lo, int i, int j, int k
   const double qxy = 3 * sxy, qxz = 3 * sxz, qyz = 3 * syz;
   double x = lo + i + 0.5 - 0.5 * n, y = lo + j + 0.5 - 0.5 * n, z = lo + k + 0.5 - 0.5 * n;
   double r2 = x * x + y * y + z * z;
-  double r = sqrt(r2);
   double qr = qxx * x * x + qyy * y * y + qzz * z * z +
               2.0 * (qxy * x * y + qxz * x * z + qyz * y * z);
-  return -(S / (4.0 * 3.14159265358979323846)) *
-         (q0 / r + (dx * x + dy * y + dz * z) / (r * r2) + 0.5 * qr / (r2 * r2 * r));
+  // q0/r + d.x/r^3 + qr/(2 r^5) from one reciprocal square root (FP64
+  // divisions and square roots are long sequences on this part)
+  const double ri = rsqrt(r2), ri2 = ri * ri;
+  return -(S / (4.0 * 3.14159265358979323846)) * ri *
+         (q0 + ri2 * ((dx * x + dy * y + dz * z) + 0.5 * qr * ri2));
 }
 
+// the values into (ph, pl) and, when ph2.base is not NULL, the same into
+// (ph2, pl2) (the second buffer of the defect correction's potential)
 __device__ __forceinline__ void d_boundary(const BI& bi, Grid ph, Grid pl, int n, int lo,
                                                   const double* __restrict__ mom,
-                                                  double S, int want_lo){
+                                                  double S, int want_lo, Grid ph2, Grid pl2){
   int i, j, k;
   if (!ghost_cell(bi.x * (long long)blockDim.x + threadIdx.x, ph.s, i, j, k)) return;
   const double phi = ghost_value(n, lo, i, j, k, mom, S);
-  float hi = (float)phi;
+  const float hi = (float)phi;
+  const float lov = want_lo ? (float)(phi - (double)hi) : 0.0f;
   int gi = gidx(ph, i, j, k);
   ph.base[gi] = hi;
-  pl.base[gi] = want_lo ? (float)(phi - (double)hi) : 0.0f;
+  pl.base[gi] = lov;
+  if (ph2.base) {
+    gi = gidx(ph2, i, j, k);
+    ph2.base[gi] = hi;
+    pl2.base[gi] = lov;
+  }
 }
 
 __global__ void __launch_bounds__(256) k_boundary(Grid ph, Grid pl, int n, int lo,
                                                   const double* __restrict__ mom,
-                                                  double S, int want_lo) {
-  d_boundary(bi_native(), ph, pl, n, lo, mom, S, want_lo);
+                                                  double S, int want_lo, Grid ph2, Grid pl2) {
+  d_boundary(bi_native(), ph, pl, n, lo, mom, S, want_lo, ph2, pl2);
 }
 
 void launch_boundary(cudaStream_t st, Grid ph, Grid pl, int n, int lo, const double* mom,
-                     double S, bool want_lo) {
+                     double S, bool want_lo, const Grid* ph2, const Grid* pl2) {
   long long tot = 6LL * (ph.s + 2) * (ph.s + 2);
   int grid = (int)((tot + 255) / 256);
-  k_boundary<<<grid, 256, 0, st>>>(ph, pl, n, lo, mom, S, want_lo ? 1 : 0);
+  Grid none{};
+  k_boundary<<<grid, 256, 0, st>>>(ph, pl, n, lo, mom, S, want_lo ? 1 : 0,
+                                   ph2 ? *ph2 : none, pl2 ? *pl2 : none);
   note_launch();
 }
 
@@ -966,7 +995,7 @@ __global__ void __launch_bounds__(256) kb_boundary(const BoundaryDesc* d, const 
   BI bi;
   if (!batch_map(d, t, (const int*)nullptr, q, bi)) return;
   const BoundaryDesc& e = d[q];
-  d_boundary(bi, e.ph, e.pl, e.n, e.lo, e.mom, e.S, e.want_lo);
+  d_boundary(bi, e.ph, e.pl, e.n, e.lo, e.mom, e.S, e.want_lo, Grid{}, Grid{});
 }
 
 void launch_deposit_b(cudaStream_t st, int grid, const DepositDesc* d, const BTable* t) {

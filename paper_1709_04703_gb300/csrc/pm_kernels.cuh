@@ -88,8 +88,11 @@ cudaError_t launch_ade_sweep(cudaStream_t st, Grid ph, Grid pl, Grid fh, Grid fl
 void launch_diff_rhs(cudaStream_t st, int grid, Grid sh, Grid sl, double scale, Grid ph,
                      Grid pl, double sig, Grid gh, Grid gl, Grid qh, Grid ql, bool stash,
                      double* partial, unsigned int* counter, double* out);
+// Dirichlet ghost values of the open boundary into (ph, pl), and into
+// (*ph2, *pl2) as well when they are given
 void launch_boundary(cudaStream_t st, Grid ph, Grid pl, int n, int lo, const double* mom,
-                     double S, bool want_lo);
+                     double S, bool want_lo, const Grid* ph2 = nullptr,
+                     const Grid* pl2 = nullptr);
 
 // k_mg.cu
 // d0: base diagonal of the operator sum_nb u - d0 u (6: Poisson; 6 + sig h^2:

@@ -91,7 +91,7 @@ class Batch:
     one kernel launch per phase over all of them."""
 
     def __init__(self, realisations, a_init, a_final, n_steps, rtol=1e-7, max_vcycles=50,
-                 buffer_cells=1.0, store_forces=False):
+                 buffer_cells=1.0, store_forces=False, inner_vcycles=1):
         """realisations: list of dicts with pos, mom, ids, n_mesh, box."""
         lib = L.load()
         R = len(realisations)
@@ -106,6 +106,7 @@ class Batch:
             cfgs[r] = _config(re["n_mesh"], len(re["pos"]), re["box"], a_init, a_final,
                               n_steps, rtol=rtol, max_vcycles=max_vcycles,
                               buffer_cells=buffer_cells, store_forces=store_forces)
+            cfgs[r].inner_vcycles = int(inner_vcycles)
             p4, m4 = pack(re["pos"], re["mom"], re["ids"])
             dp, dm = torch.from_numpy(p4).cuda(), torch.from_numpy(m4).cuda()
             keep += [dp, dm]
@@ -178,7 +179,8 @@ class Sim:
                  rtol=1e-7, precision="mixed", guess="warm", bc="paper",
                  shrink=True, buffer_cells=1.0, max_vcycles=50, store_forces=False,
                  omega_m=0.3, omega_l=0.7, host_init=False, gravity="poisson",
-                 c_eff_factor=0.019, assignment="cic", domain="cube", sort_every=0):
+                 c_eff_factor=0.019, assignment="cic", domain="cube", sort_every=0,
+                 inner_vcycles=1):
         lib = L.load()
         cfg = L.PmConfig()
         lib.pm_config_default(C.byref(cfg))
@@ -199,6 +201,7 @@ class Sim:
         cfg.assignment = {"cic": L.PM_ASSIGN_CIC, "tsc": L.PM_ASSIGN_TSC}[assignment]
         cfg.domain = {"cube": L.PM_DOMAIN_CUBE, "sphere": L.PM_DOMAIN_SPHERE}[domain]
         cfg.sort_every = int(sort_every)
+        cfg.inner_vcycles = int(inner_vcycles)
         self.cfg = cfg
         self.n_particles = int(len(pos))
         # the context runs on its own stream so that its V-cycle can be
