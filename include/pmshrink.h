@@ -552,6 +552,15 @@ pm_status pm_capture(pm_ctx* ctx, float* r_dev, float* e_dev);
 /* Kernel launches made by this library in this process so far. */
 int64_t pm_launch_count(void);
 
+/* CTAs per thread-block cluster of the coarse multigrid levels (the levels
+ * of side <= 64, 32 or 16 for 16, 8 or 1 CTAs run in one cluster's
+ * distributed shared memory, Sec. 2.1's V-cycle below the launched levels),
+ * set at pm_init: 1 by default (the fastest measured), 8 or 16 when the
+ * environment variable PM_CMG_CLUSTER asks for it and the GPU can hold such
+ * a cluster, 1 whenever PM_NO_CLUSTER is set.  The results do not depend
+ * on it. */
+int32_t pm_mg_cluster_size(void);
+
 const char* pm_last_error(const pm_ctx* ctx);
 void pm_destroy(pm_ctx* ctx);
 

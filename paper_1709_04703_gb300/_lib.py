@@ -36,6 +36,7 @@ EXPORTED = [
     "pm_mg_smooth", "pm_mg_restrict", "pm_mg_prolong", "pm_selftest_wait", "pm_nn_gemm_bf16", "pm_guess_create", "pm_guess_num_params", "pm_guess_set_params",
     "pm_guess_get_params", "pm_guess_forward", "pm_guess_loss_grad", "pm_guess_adam",
     "pm_guess_last_error", "pm_guess_destroy", "pm_set_guess", "pm_capture",
+    "pm_mg_cluster_size",
 ]
 PROF_CLASSES = ["deposit", "source", "boundary", "smooth0", "transfer0", "coarse",
                 "defect", "correct", "gather", "compact", "guess", "ade", "sort"]
@@ -120,6 +121,7 @@ def load():
         "pm_batch_get_particles": (I32, [P, I32, P, P, I32, C.POINTER(I64)]),
         "pm_batch_get_lightcone": (I32, [P, I32, P, P, I32, C.POINTER(I64)]),
         "pm_batch_get_forces": (I32, [P, I32, P, I32, C.POINTER(I64)]),
+        "pm_mg_cluster_size": (I32, []),
         "pm_batch_last_error": (C.c_char_p, [P]),
         "pm_batch_destroy": (None, [P]),
         "pm_selftest_wait": (I32, [I32, I64, P]),

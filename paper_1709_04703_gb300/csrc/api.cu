@@ -536,9 +536,10 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
   int ec = -1;
   // open-boundary ghost factor of level l (spacing H = 2^l), see k_mg.cu
   auto gam = [](int l) { float H = (float)(1 << l); return (H - 1.0f) / (H + 1.0f); };
-  // levels below the first of side <= CMG_MAX_SIDE run inside one CTA
+  // the levels from the first of side <= cmg_top_side run in one
+  // thread-block cluster (k_cmg.cu)
   int Lc = 0;
-  while (Lc < L && ctx->ls[Lc] > CMG_MAX_SIDE) ++Lc;
+  while (Lc < L && ctx->ls[Lc] > cmg_top_side(cmg_cluster())) ++Lc;
   for (int l = 0; l < Lc; ++l) {
     int e = l == 0 ? prof_begin(ctx) : -1;
     // below level 0 the restriction zeroes the coarse iterate
@@ -565,7 +566,7 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
     h2 *= 4.0f;
   }
   if (Lc == 0) ec = prof_begin(ctx);
-  launch_coarse_mg(ctx->st, U[Lc], B[Lc], Lc, per, COARSE_SWEEPS, Lc == 0 ? zero0 : true,
+  launch_cmg(ctx->st, U[Lc], B[Lc], Lc, per, COARSE_SWEEPS, Lc == 0 ? zero0 : true,
                    ctx->sig);
   for (int l = Lc - 1; l >= 0; --l) {
     h2 *= 0.25f;
@@ -2246,6 +2247,8 @@ pm_status pm_profile_read(pm_ctx* ctx, int32_t cls, double* ms, int64_t* groups,
 
 int64_t pm_launch_count(void) { return g_launches.load(); }
 
+int32_t pm_mg_cluster_size(void) { return cmg_cluster(); }
+
 const char* pm_last_error(const pm_ctx* ctx) {
   return ctx ? ctx->err.c_str() : g_err.c_str();
 }
@@ -2378,7 +2381,7 @@ void set_dims(D& d, int r, dim3 g) {
 
 int first_small_level(const pm_ctx* c) {
   int L = (int)c->ls.size() - 1, Lc = 0;
-  while (Lc < L && c->ls[Lc] > CMG_MAX_SIDE) ++Lc;
+  while (Lc < L && c->ls[Lc] > cmg_top_side(cmg_cluster())) ++Lc;
   return Lc;
 }
 
@@ -2514,7 +2517,8 @@ void launch_vcycle_slots(pm_batch* B) {
     launch_restrict_b(B->st, t.grid_max, (const RestrictDesc*)t.d_desc, t.d_tab, act);
   }
   BTab& tb = B->t_vc[slot_bottom(M)];
-  launch_coarse_mg_b(B->st, tb.grid_max, (const CmgDesc*)tb.d_desc, tb.d_tab, act);
+  // one cluster per realisation, shared memory for the largest top level
+  launch_cmg_b(B->st, B->R, cmg_top_side(cmg_cluster()), (const CmgDesc*)tb.d_desc, act);
   for (int l = M - 1; l >= 0; --l) {
     BTab& tp = B->t_vc[slot_up(M, l, 0)];
     launch_prolong_b(B->st, tp.grid_max, (const ProlongDesc*)tp.d_desc, tp.d_tab, act);

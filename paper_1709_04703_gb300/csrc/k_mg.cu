@@ -3,6 +3,7 @@
 // fused residual + 8-cell restriction, trilinear prolongation + correction,
 // a single-CTA coarsest solve, and the double-float defect-correction loop
 // (residual of the double-float potential; Phi += e).
+#include "mg_arith.cuh"
 #include "pm_kernels.cuh"
 
 namespace pm {
@@ -12,53 +13,6 @@ namespace pm {
 //   u = (sum_nb u - h^2 b) / 6.
 // Thread layout: x over half a row (s even), y, z over rows.
 // ---------------------------------------------------------------------------
-// Open boundaries on coarse levels: the fine problem's error vanishes at the
-// finest ghost-cell centre, half a fine cell outside the cube face.  On level
-// l (spacing H = 2^l) the ghost centre lies H/2 outside the face, so a linear
-// profile through that point gives ghost = -gam * (adjacent interior value)
-// with gam = (H - 1) / (H + 1) (0 on the finest level, where the ghost layer
-// holds the Dirichlet data itself).  Coarse ghosts are stored as zero and the
-// -gam term is folded into the diagonal: 6 + gam * (number of ghost faces).
-__device__ __forceinline__ float bnd_diag(int i, int j, int k, int s, float gam) {
-  int nb = (i == 0) + (i == s - 1) + (j == 0) + (j == s - 1) + (k == 0) + (k == s - 1);
-  return 6.0f + gam * (float)nb;
-}
-// Diagonal with a shift: the operator sum_nb u - d0 u (d0 = 6 + sig h^2 for
-// the implicit diffusion substeps, 6 for Poisson) plus the coarse open
-// ghost term.  "simple" (d0 = 6, no ghost term) keeps the exact x(1/6) form.
-__device__ __forceinline__ float mg_diag(int i, int j, int k, int s, int periodic, float gam,
-                                         float d0) {
-  if (periodic) return d0;
-  int nb = (i == 0) + (i == s - 1) + (j == 0) + (j == s - 1) + (k == 0) + (k == s - 1);
-  return d0 + gam * (float)nb;
-}
-__device__ __forceinline__ bool mg_simple(int periodic, float gam, float d0) {
-  return (periodic || gam == 0.0f) && d0 == 6.0f;
-}
-
-// The update arithmetic of the smoother and the transfers, written with
-// explicit round-to-nearest operations so that every kernel that applies
-// them (one colour per launch, the fused two-sweep pass, the batched forms)
-// produces the same bits.
-__device__ __forceinline__ float nb6(float xm, float xp, float ym, float yp, float zm, float zp) {
-  return __fadd_rn(__fadd_rn(__fadd_rn(xm, xp), __fadd_rn(ym, yp)), __fadd_rn(zm, zp));
-}
-// Gauss-Seidel value (sum_nb u - h^2 b) / diag
-__device__ __forceinline__ float gs_value(float s0, float bv, float h2, bool simple, float diag) {
-  float t = __fsub_rn(s0, __fmul_rn(h2, bv));
-  return simple ? __fmul_rn(t, 1.0f / 6.0f) : __fdiv_rn(t, diag);
-}
-// residual b - (sum_nb u - diag u) / h^2
-__device__ __forceinline__ float resid_value(float s0, float uc, float bv, float diag,
-                                             float inv_h2) {
-  float lap = __fsub_rn(s0, __fmul_rn(diag, uc));
-  return __fsub_rn(bv, __fmul_rn(lap, inv_h2));
-}
-// trilinear weights 3/4, 1/4 per axis (x, then y, then z)
-__device__ __forceinline__ float lerp34(float a, float b) {
-  return __fadd_rn(__fmul_rn(0.75f, a), __fmul_rn(0.25f, b));
-}
-
 // zero_start (red only): the iterate is known to be zero, so the red cells
 // take (-h^2 b)/diag without reading u; the black sweep after it reads only
 // red neighbours, so u needs no clearing before a V-cycle.
@@ -200,16 +154,9 @@ __device__ __forceinline__ float prolong_value(Grid uc, int i, int j, int k, int
     if (K2 < 0 || K2 >= sc) { K2 = K; fz = -gam_c; }
   }
   const float* q = uc.base;
-  const float fxy = __fmul_rn(fx, fy), fxz = __fmul_rn(fx, fz), fyz = __fmul_rn(fy, fz);
-  const float fxyz = __fmul_rn(fxy, fz);
-  float c000 = q[gidx(uc, I, J, K)], c100 = __fmul_rn(fx, q[gidx(uc, I2, J, K)]);
-  float c010 = __fmul_rn(fy, q[gidx(uc, I, J2, K)]), c110 = __fmul_rn(fxy, q[gidx(uc, I2, J2, K)]);
-  float c001 = __fmul_rn(fz, q[gidx(uc, I, J, K2)]), c101 = __fmul_rn(fxz, q[gidx(uc, I2, J, K2)]);
-  float c011 = __fmul_rn(fyz, q[gidx(uc, I, J2, K2)]);
-  float c111 = __fmul_rn(fxyz, q[gidx(uc, I2, J2, K2)]);
-  float a0 = lerp34(c000, c100), a1 = lerp34(c010, c110);
-  float a2 = lerp34(c001, c101), a3 = lerp34(c011, c111);
-  return lerp34(lerp34(a0, a1), lerp34(a2, a3));
+  return prolong_mix(q[gidx(uc, I, J, K)], q[gidx(uc, I2, J, K)], q[gidx(uc, I, J2, K)],
+                     q[gidx(uc, I2, J2, K)], q[gidx(uc, I, J, K2)], q[gidx(uc, I2, J, K2)],
+                     q[gidx(uc, I, J2, K2)], q[gidx(uc, I2, J2, K2)], fx, fy, fz);
 }
 
 __device__ __forceinline__ void d_prolong(const BI& bi, Grid uc, Grid u, int periodic,
@@ -584,6 +531,7 @@ cudaError_t mg_prepare() {
   set(k_rbgs2<true, true, true>);
   set(k_rbgs2<true, false, false>);
   set(k_rbgs2<true, false, true>);
+  if (e == cudaSuccess) e = cmg_prepare();
   return e;
 }
 
@@ -613,253 +561,6 @@ void launch_rbgs2(cudaStream_t st, Grid win, Grid wout, Grid b, float h2, int pe
     if (zero_start) PM_RBGS2(false, false, true); else PM_RBGS2(false, false, false);
   }
 #undef PM_RBGS2
-  note_launch();
-}
-
-// ---------------------------------------------------------------------------
-// The bottom of the V-cycle in one CTA: from a level with side S <= 16 down to
-// side <= 4 (or odd) and back — V(2,2) with the same smoother, transfers and
-// boundary treatment as the multi-kernel levels — in shared memory.  The side
-// is a template parameter so that all index arithmetic uses constants.
-// ---------------------------------------------------------------------------
-namespace {
-
-template <int S>
-__device__ __forceinline__ int sui(int i, int j, int k) {
-  return ((k + 1) * (S + 2) + (j + 1)) * (S + 2) + (i + 1);
-}
-
-struct CmgArgs {
-  int periodic;
-  int level;   // multigrid level of the top grid
-  int sweeps;  // bottom sweeps
-  float sig0;  // diagonal shift per unit h^2 of level 0 (0: Poisson)
-};
-
-// base diagonal of level l: 6 + sig0 4^l
-__device__ __forceinline__ float cmg_d0(const CmgArgs& a, int l) {
-  return 6.0f + a.sig0 * (float)(1 << (2 * l));
-}
-
-__device__ __forceinline__ float cmg_gam(const CmgArgs& a, int l) {
-  float H = (float)(1 << l);
-  return a.periodic ? 0.0f : (H - 1.0f) / (H + 1.0f);
-}
-
-// one colour (or, for odd S on a periodic grid, where red-black colouring
-// does not close over the wrap, a lexicographic pass by one thread).  omega
-// != 1: over-relaxed update u + omega (gs - u) (the bottom solve).
-template <int S>
-__device__ void c_sweep(float* u, const float* b, float h2, float gam, int periodic, int color,
-                        float d0, float omega = 1.0f) {
-  constexpr int N3 = S * S * S;
-  const bool simple = periodic || gam == 0.0f;
-  auto upd = [&](int t) {
-    int i = t % S, j = (t / S) % S, k = t / (S * S);
-    int im = i == 0 ? (periodic ? S - 1 : -1) : i - 1, ip = i == S - 1 ? (periodic ? 0 : S) : i + 1;
-    int jm = j == 0 ? (periodic ? S - 1 : -1) : j - 1, jp = j == S - 1 ? (periodic ? 0 : S) : j + 1;
-    int km = k == 0 ? (periodic ? S - 1 : -1) : k - 1, kp = k == S - 1 ? (periodic ? 0 : S) : k + 1;
-    float sum = u[sui<S>(im, j, k)] + u[sui<S>(ip, j, k)] + u[sui<S>(i, jm, k)] +
-                u[sui<S>(i, jp, k)] + u[sui<S>(i, j, km)] + u[sui<S>(i, j, kp)];
-    int nb = (i == 0) + (i == S - 1) + (j == 0) + (j == S - 1) + (k == 0) + (k == S - 1);
-    const float gs = (sum - h2 * b[t]) / (simple ? d0 : d0 + gam * (float)nb);
-    float& c = u[sui<S>(i, j, k)];
-    c = omega == 1.0f ? gs : c + omega * (gs - c);
-  };
-  if ((S & 1) && periodic) {
-    if (threadIdx.x == 0)
-      for (int t = 0; t < N3; ++t) upd(t);
-  } else {
-    for (int t = threadIdx.x; t < N3; t += blockDim.x) {
-      int i = t % S, j = (t / S) % S, k = t / (S * S);
-      if (((i + j + k) & 1) == color) upd(t);
-    }
-  }
-  __syncthreads();
-}
-
-template <int S>
-__device__ void c_smooth(float* u, const float* b, float h2, float gam, int periodic, int n,
-                         float d0, float omega = 1.0f) {
-  for (int w = 0; w < n; ++w) {
-    c_sweep<S>(u, b, h2, gam, periodic, 0, d0, omega);
-    if (!((S & 1) && periodic)) c_sweep<S>(u, b, h2, gam, periodic, 1, d0, omega);
-  }
-}
-
-template <int S>
-__device__ void c_restrict(const float* u, const float* b, float* uc, float* bc, float inv_h2,
-                           float gam, int periodic, float d0) {
-  constexpr int SC = S / 2;
-  const bool simple = periodic || gam == 0.0f;
-  for (int T = threadIdx.x; T < SC * SC * SC; T += blockDim.x) {
-    int I = T % SC, J = (T / SC) % SC, K = T / (SC * SC);
-    float acc = 0.0f;
-#pragma unroll
-    for (int d = 0; d < 8; ++d) {
-      int i = 2 * I + (d & 1), j = 2 * J + ((d >> 1) & 1), k = 2 * K + (d >> 2);
-      int im = i == 0 ? (periodic ? S - 1 : -1) : i - 1, ip = i == S - 1 ? (periodic ? 0 : S) : i + 1;
-      int jm = j == 0 ? (periodic ? S - 1 : -1) : j - 1, jp = j == S - 1 ? (periodic ? 0 : S) : j + 1;
-      int km = k == 0 ? (periodic ? S - 1 : -1) : k - 1, kp = k == S - 1 ? (periodic ? 0 : S) : k + 1;
-      int nb = (i == 0) + (i == S - 1) + (j == 0) + (j == S - 1) + (k == 0) + (k == S - 1);
-      float lap = u[sui<S>(im, j, k)] + u[sui<S>(ip, j, k)] + u[sui<S>(i, jm, k)] +
-                  u[sui<S>(i, jp, k)] + u[sui<S>(i, j, km)] + u[sui<S>(i, j, kp)] -
-                  (simple ? d0 : d0 + gam * (float)nb) * u[sui<S>(i, j, k)];
-      acc += b[(k * S + j) * S + i] - lap * inv_h2;
-    }
-    bc[T] = 0.125f * acc;
-    uc[sui<SC>(I, J, K)] = 0.0f;
-  }
-  __syncthreads();
-}
-
-template <int S>
-__device__ void c_prolong(const float* uc, float* u, float gam_c, int periodic) {
-  constexpr int SC = S / 2;
-  for (int t = threadIdx.x; t < S * S * S; t += blockDim.x) {
-    int i = t % S, j = (t / S) % S, k = t / (S * S);
-    int I = i >> 1, J = j >> 1, K = k >> 1;
-    int I2 = (i & 1) ? I + 1 : I - 1, J2 = (j & 1) ? J + 1 : J - 1, K2 = (k & 1) ? K + 1 : K - 1;
-    float fx = 1.0f, fy = 1.0f, fz = 1.0f;
-    if (periodic) {
-      I2 = I2 < 0 ? SC - 1 : (I2 >= SC ? 0 : I2);
-      J2 = J2 < 0 ? SC - 1 : (J2 >= SC ? 0 : J2);
-      K2 = K2 < 0 ? SC - 1 : (K2 >= SC ? 0 : K2);
-    } else {
-      if (I2 < 0 || I2 >= SC) { I2 = I; fx = -gam_c; }
-      if (J2 < 0 || J2 >= SC) { J2 = J; fy = -gam_c; }
-      if (K2 < 0 || K2 >= SC) { K2 = K; fz = -gam_c; }
-    }
-    float c000 = uc[sui<SC>(I, J, K)], c100 = fx * uc[sui<SC>(I2, J, K)];
-    float c010 = fy * uc[sui<SC>(I, J2, K)], c110 = fx * fy * uc[sui<SC>(I2, J2, K)];
-    float c001 = fz * uc[sui<SC>(I, J, K2)], c101 = fx * fz * uc[sui<SC>(I2, J, K2)];
-    float c011 = fy * fz * uc[sui<SC>(I, J2, K2)];
-    float c111 = fx * fy * fz * uc[sui<SC>(I2, J2, K2)];
-    float a0 = 0.75f * c000 + 0.25f * c100, a1 = 0.75f * c010 + 0.25f * c110;
-    float a2 = 0.75f * c001 + 0.25f * c101, a3 = 0.75f * c011 + 0.25f * c111;
-    float b0 = 0.75f * a0 + 0.25f * a1, b1 = 0.75f * a2 + 0.25f * a3;
-    u[sui<S>(i, j, k)] += 0.75f * b0 + 0.25f * b1;
-  }
-  __syncthreads();
-}
-
-template <int S>
-__device__ float c_mean(const float* v, bool padded, float* red) {
-  float acc = 0.0f;
-  for (int t = threadIdx.x; t < S * S * S; t += blockDim.x) {
-    int i = t % S, j = (t / S) % S, k = t / (S * S);
-    acc += padded ? v[sui<S>(i, j, k)] : v[t];
-  }
-  acc = warp_sumf_all(acc);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  float m = 0.0f;
-  for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) m += red[w];
-  __syncthreads();
-  return m / (float)(S * S * S);
-}
-
-// V-cycle from side S (level l) in shared memory starting at `mem`:
-// u (padded) then b, then the next level.
-template <int S>
-__device__ void c_vcycle(float* mem, const CmgArgs& a, int l, float* red) {
-  float* u = mem;
-  float* b = mem + (S + 2) * (S + 2) * (S + 2);
-  const float H = (float)(1 << l), h2 = H * H;
-  // the periodic Poisson problem is singular: project out the mean (not
-  // needed, and wrong, with a diagonal shift)
-  const bool proj = a.periodic && a.sig0 == 0.0f;
-  if constexpr (S <= 4 || (S & 1)) {
-    if (proj) {
-      float m = c_mean<S>(b, false, red);
-      for (int t = threadIdx.x; t < S * S * S; t += blockDim.x) b[t] -= m;
-      __syncthreads();
-    }
-    // Dirichlet bottom: red-black SOR with the optimal factor of the
-    // S^3 Dirichlet Laplacian, 2 / (1 + sin(pi / (S + 1))) (Jacobi radius
-    // cos(pi / (S + 1))); periodic bottoms keep Gauss-Seidel
-    const float omega =
-        a.periodic ? 1.0f : 2.0f / (1.0f + sinf(3.14159265f / (float)(S + 1)));
-    c_smooth<S>(u, b, h2, cmg_gam(a, l), a.periodic, a.sweeps, cmg_d0(a, l), omega);
-    if (proj) {
-      float m = c_mean<S>(u, true, red);
-      for (int t = threadIdx.x; t < S * S * S; t += blockDim.x) {
-        int i = t % S, j = (t / S) % S, k = t / (S * S);
-        u[sui<S>(i, j, k)] -= m;
-      }
-      __syncthreads();
-    }
-  } else {
-    constexpr int SC = S / 2;
-    float* uc = b + S * S * S;
-    float* bc = uc + (SC + 2) * (SC + 2) * (SC + 2);
-    c_smooth<S>(u, b, h2, cmg_gam(a, l), a.periodic, 2, cmg_d0(a, l));
-    c_restrict<S>(u, b, uc, bc, 1.0f / h2, cmg_gam(a, l), a.periodic, cmg_d0(a, l));
-    c_vcycle<SC>(uc, a, l + 1, red);
-    c_prolong<S>(uc, u, cmg_gam(a, l + 1), a.periodic);
-    c_smooth<S>(u, b, h2, cmg_gam(a, l), a.periodic, 2, cmg_d0(a, l));
-  }
-}
-
-template <int S>
-__device__ void c_run(Grid u, Grid b, float* sm, const CmgArgs& a, float* red, int zero_top) {
-  constexpr int P = S + 2;
-  float* su = sm;
-  float* sb = sm + P * P * P;
-  // zero everything below the top (ghosts of coarse levels stay zero)
-  for (int t = threadIdx.x; t < 11776; t += blockDim.x) sm[t] = 0.0f;
-  __syncthreads();
-  for (int t = threadIdx.x; t < P * P * P; t += blockDim.x) {
-    int i = t % P - 1, j = (t / P) % P - 1, k = t / (P * P) - 1;
-    bool ghost = i < 0 || j < 0 || k < 0 || i >= S || j >= S || k >= S;
-    su[t] = (zero_top && !ghost) ? 0.0f : u.base[gidx(u, i, j, k)];
-  }
-  for (int t = threadIdx.x; t < S * S * S; t += blockDim.x) {
-    int i = t % S, j = (t / S) % S, k = t / (S * S);
-    sb[t] = b.base[gidx(b, i, j, k)];
-  }
-  __syncthreads();
-  c_vcycle<S>(sm, a, a.level, red);
-  for (int t = threadIdx.x; t < S * S * S; t += blockDim.x) {
-    int i = t % S, j = (t / S) % S, k = t / (S * S);
-    u.base[gidx(u, i, j, k)] = su[sui<S>(i, j, k)];
-  }
-}
-
-}  // namespace
-
-constexpr int CMG_SMEM_FLOATS = 11776;  // 16^3 -> 8^3 -> 4^3 needs 11720
-
-// level: multigrid level index of (u, b); sides 16, 14, 12, 10, 8, 7, 6, 5, 4, 3.
-// zero_top: the top level's iterate starts at zero (its interior is not read).
-__global__ void __launch_bounds__(1024) k_coarse_mg(Grid u, Grid b, int level, int periodic,
-                                                    int coarse_sweeps, int zero_top,
-                                                    float sig0) {
-  pdl_wait();
-  pdl_release();
-  __shared__ float sm[CMG_SMEM_FLOATS];
-  __shared__ float red[32];
-  CmgArgs a{periodic, level, coarse_sweeps, sig0};
-  switch (u.s) {
-    case 16: c_run<16>(u, b, sm, a, red, zero_top); break;
-    case 14: c_run<14>(u, b, sm, a, red, zero_top); break;
-    case 12: c_run<12>(u, b, sm, a, red, zero_top); break;
-    case 10: c_run<10>(u, b, sm, a, red, zero_top); break;
-    case 8: c_run<8>(u, b, sm, a, red, zero_top); break;
-    case 7: c_run<7>(u, b, sm, a, red, zero_top); break;
-    case 6: c_run<6>(u, b, sm, a, red, zero_top); break;
-    case 5: c_run<5>(u, b, sm, a, red, zero_top); break;
-    case 4: c_run<4>(u, b, sm, a, red, zero_top); break;
-    case 3: c_run<3>(u, b, sm, a, red, zero_top); break;
-    default: break;
-  }
-}
-
-void launch_coarse_mg(cudaStream_t st, Grid u, Grid b, int level, int periodic,
-                      int coarse_sweeps, bool zero_top, float sig0) {
-  launch_pdl(k_coarse_mg, dim3(1), dim3(1024), 0, st, u, b, level, periodic, coarse_sweeps,
-             zero_top ? 1 : 0, sig0);
   note_launch();
 }
 
@@ -1293,29 +994,6 @@ __global__ void __launch_bounds__(256) kb_prolong(const ProlongDesc* d, const BT
   const ProlongDesc& e = d[q];
   d_prolong(bi, e.uc, e.u, e.periodic, e.gam_c);
 }
-__global__ void __launch_bounds__(1024) kb_coarse_mg(const CmgDesc* d, const BTable* t,
-                                                     const int* active) {
-  int q;
-  BI bi;
-  if (!batch_map(d, t, active, q, bi)) return;
-  const CmgDesc& e = d[q];
-  __shared__ float sm[CMG_SMEM_FLOATS];
-  __shared__ float red[32];
-  CmgArgs a{e.periodic, e.level, e.sweeps, 0.0f};
-  switch (e.u.s) {
-    case 16: c_run<16>(e.u, e.b, sm, a, red, e.zero_top); break;
-    case 14: c_run<14>(e.u, e.b, sm, a, red, e.zero_top); break;
-    case 12: c_run<12>(e.u, e.b, sm, a, red, e.zero_top); break;
-    case 10: c_run<10>(e.u, e.b, sm, a, red, e.zero_top); break;
-    case 8: c_run<8>(e.u, e.b, sm, a, red, e.zero_top); break;
-    case 7: c_run<7>(e.u, e.b, sm, a, red, e.zero_top); break;
-    case 6: c_run<6>(e.u, e.b, sm, a, red, e.zero_top); break;
-    case 5: c_run<5>(e.u, e.b, sm, a, red, e.zero_top); break;
-    case 4: c_run<4>(e.u, e.b, sm, a, red, e.zero_top); break;
-    case 3: c_run<3>(e.u, e.b, sm, a, red, e.zero_top); break;
-    default: break;
-  }
-}
 __global__ void __launch_bounds__(256) kb_defect(const DefectDesc* d, const BTable* t,
                                                  const int* active) {
   int q;
@@ -1353,12 +1031,6 @@ void launch_prolong_b(cudaStream_t st, int grid, const ProlongDesc* d, const BTa
                       const int* active) {
   if (grid <= 0) return;
   kb_prolong<<<grid, dim3(32, 8), 0, st>>>(d, t, active);
-  note_launch();
-}
-void launch_coarse_mg_b(cudaStream_t st, int grid, const CmgDesc* d, const BTable* t,
-                        const int* active) {
-  if (grid <= 0) return;
-  kb_coarse_mg<<<grid, 1024, 0, st>>>(d, t, active);
   note_launch();
 }
 void launch_defect_b(cudaStream_t st, int grid, const DefectDesc* d, const BTable* t,

@@ -99,10 +99,15 @@ void launch_boundary(cudaStream_t st, Grid ph, Grid pl, int n, int lo, const dou
 // an implicit diffusion substep)
 void launch_rbgs(cudaStream_t st, Grid u, Grid b, float h2, int color, int periodic,
                  float gam, bool zero_start = false, float d0 = 6.0f);
-// the rest of a V-cycle from a level of side <= CMG_MAX_SIDE in one CTA
-constexpr int CMG_MAX_SIDE = 16;
-void launch_coarse_mg(cudaStream_t st, Grid u, Grid b, int level, int periodic,
-                      int coarse_sweeps, bool zero_top, float sig0 = 0.0f);
+// The rest of a V-cycle from the first level of side <= cmg_top_side(
+// cmg_cluster()) in one thread-block cluster (k_cmg.cu): cmg_prepare picks
+// the largest cluster the GPU holds (16 CTAs: levels <= 64^3; 8: <= 32^3;
+// one CTA: <= 16^3), outside any stream capture.
+cudaError_t cmg_prepare();
+int cmg_cluster();
+int cmg_top_side(int cl);
+void launch_cmg(cudaStream_t st, Grid u, Grid b, int level, int periodic, int sweeps,
+                bool zero_top, float sig0);
 void launch_resid_restrict(cudaStream_t st, Grid u, Grid b, float inv_h2, Grid uc, Grid bc,
                            int periodic, float gam, float d0 = 6.0f);
 void launch_prolong_to(cudaStream_t st, Grid uc, Grid u, Grid w, int periodic, float gam_c);
@@ -302,8 +307,11 @@ void launch_restrict_b(cudaStream_t st, int grid, const RestrictDesc* d, const B
                        const int* active);
 void launch_prolong_b(cudaStream_t st, int grid, const ProlongDesc* d, const BTable* t,
                       const int* active);
-void launch_coarse_mg_b(cudaStream_t st, int grid, const CmgDesc* d, const BTable* t,
-                        const int* active);
+// batched: cluster c solves entry c of d (n_desc entries, one per
+// realisation; entries whose realisation is inactive are skipped); shared
+// memory for tops up to max_top
+void launch_cmg_b(cudaStream_t st, int n_desc, int max_top, const CmgDesc* d,
+                  const int* active);
 void launch_defect_b(cudaStream_t st, int grid, const DefectDesc* d, const BTable* t,
                      const int* active);
 void launch_predict_b(cudaStream_t st, int grid, const PredictDesc* d, const BTable* t);
