@@ -505,6 +505,24 @@ __global__ void k_pool2_bwd(const bf16* __restrict__ dout, Vol g, int C, bf16* _
 
 // nearest upsampling by 2 into channels [c0, c0 + C) of an output with Cout
 // channels (fine shape g); optional accumulate-free backward below
+// the same with 8 channels (16 bytes) per step, 32-bit voxel arithmetic (C,
+// Cout, c0 multiples of 8; fewer than 2^31 voxels)
+__global__ void k_up2_v8(const uint4* __restrict__ in, Vol g, int C8, uint4* __restrict__ out,
+                         int Cout8, int c08) {
+  const int n = (int)(g.voxels() * C8);
+  const int W2 = g.W >> 1, H2 = g.H >> 1, D2 = g.D >> 1;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int c = t % C8, v = t / C8;
+    int r = v;
+    const int x = r % g.W; r /= g.W;
+    const int y = r % g.H; r /= g.H;
+    const int z = r % g.D;
+    const int b = r / g.D;
+    const int p = ((b * D2 + (z >> 1)) * H2 + (y >> 1)) * W2 + (x >> 1);
+    out[(long long)v * Cout8 + c08 + c] = in[(long long)p * C8 + c];
+  }
+}
+
 __global__ void k_up2(const bf16* __restrict__ in, Vol g, int C, bf16* __restrict__ out, int Cout,
                       int c0) {
   const long long n = g.voxels() * C;
@@ -548,6 +566,18 @@ __global__ void k_up2_bwd(const bf16* __restrict__ dout, Vol g, int Cout, int c0
 
 // copy channels [0, C) of a tensor into channels [c0, c0 + C) of another
 // (Cout channels); with `add` the destination is accumulated into
+// plain copy of 8-channel groups (C, Csrc, s0, Cdst, c0 multiples of 8)
+__global__ void k_chan_copy_v8(const uint4* __restrict__ src, long long nvox, int C8, int Csrc8,
+                               int s08, uint4* __restrict__ dst, int Cdst8, int c08) {
+  const long long n = nvox * C8;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(t % C8);
+    const long long v = t / C8;
+    dst[v * Cdst8 + c08 + c] = src[v * Csrc8 + s08 + c];
+  }
+}
+
 __global__ void k_chan_copy(const bf16* __restrict__ src, long long nvox, int C, int Csrc,
                             int s0, bf16* __restrict__ dst, int Cdst, int c0, int add) {
   const long long n = nvox * C;
@@ -719,7 +749,11 @@ void launch_pool2_bwd(cudaStream_t st, const void* dout, int B, int D, int H, in
 void launch_up2(cudaStream_t st, const void* in, int B, int D, int H, int W, int C, void* out,
                 int Cout, int c0) {
   Vol g{B, D, H, W};
-  k_up2<<<ew_grid(g.voxels() * C), 256, 0, st>>>((const bf16*)in, g, C, (bf16*)out, Cout, c0);
+  if (C % 8 == 0 && Cout % 8 == 0 && c0 % 8 == 0 && g.voxels() * C / 8 < (1LL << 31))
+    k_up2_v8<<<ew_grid(g.voxels() * C / 8), 256, 0, st>>>((const uint4*)in, g, C / 8,
+                                                            (uint4*)out, Cout / 8, c0 / 8);
+  else
+    k_up2<<<ew_grid(g.voxels() * C), 256, 0, st>>>((const bf16*)in, g, C, (bf16*)out, Cout, c0);
   note_launch();
 }
 void launch_up2_bwd(cudaStream_t st, const void* dout, int B, int D, int H, int W, int Cout,
@@ -731,8 +765,13 @@ void launch_up2_bwd(cudaStream_t st, const void* dout, int B, int D, int H, int 
 }
 void launch_chan_copy(cudaStream_t st, const void* src, long long nvox, int C, int Csrc, int s0,
                       void* dst, int Cdst, int c0, bool add) {
-  k_chan_copy<<<ew_grid(nvox * C), 256, 0, st>>>((const bf16*)src, nvox, C, Csrc, s0, (bf16*)dst,
-                                                 Cdst, c0, add ? 1 : 0);
+  if (!add && C % 8 == 0 && Csrc % 8 == 0 && s0 % 8 == 0 && Cdst % 8 == 0 && c0 % 8 == 0)
+    k_chan_copy_v8<<<ew_grid(nvox * C / 8), 256, 0, st>>>((const uint4*)src, nvox, C / 8,
+                                                           Csrc / 8, s0 / 8, (uint4*)dst,
+                                                           Cdst / 8, c0 / 8);
+  else
+    k_chan_copy<<<ew_grid(nvox * C), 256, 0, st>>>((const bf16*)src, nvox, C, Csrc, s0,
+                                                   (bf16*)dst, Cdst, c0, add ? 1 : 0);
   note_launch();
 }
 void launch_nn_input(cudaStream_t st, const float* f, long long vps, const float* scale, int B,

@@ -18,6 +18,7 @@
 // for the tensor cores; Adam updates the masters.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -34,6 +35,8 @@ struct ConvL {
   int nt, kpt;  // input-gradient GEMM
   long long w_off, b_off;  // offsets in the master parameter vector
   void *wp = nullptr, *wt = nullptr;  // packed BF16 operands
+  int fast_t = 0;          // output block side of the staged-input forward kernel (0: none)
+  void* wf = nullptr;      // its packed weights
 };
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
@@ -63,6 +66,7 @@ struct pm_guess {
   float* scale_in = nullptr;   // per sample s_in
   float* scale_out = nullptr;  // per sample out_scale / s_in
   float* tscale = nullptr;     // per sample s_in / out_scale (training targets)
+  double* rms_part = nullptr;  // block partial sums of the per-sample RMS
   double* loss = nullptr;
   int* err = nullptr;
   bool packed = false;
@@ -128,19 +132,35 @@ pm_status ensure_shape(pm_guess* g, int B, int S) {
 }
 
 void pack_all(pm_guess* g) {
-  for (auto& c : g->conv)
+  for (auto& c : g->conv) {
     launch_pack_w(g->st, g->w + c.w_off, c.cin, c.cout, c.wp, c.n, c.kp, c.wt, c.nt, c.kpt);
+    if (c.fast_t) launch_pack_wf(g->st, g->w + c.w_off, c.cin, c.cout, c.n, c.wf);
+  }
   g->packed = true;
 }
 
-// per-sample s_in = 1/rms(f)
-__global__ void k_rms(const float* __restrict__ f, long long vps, int B, float out_scale,
-                      float* __restrict__ sin_, float* __restrict__ sout,
-                      float* __restrict__ tsc) {
-  int b = blockIdx.x;
+// forward convolution of layer c on a B x s^3 input: the staged-input kernel
+// where it applies, else the gathered-tile one
+void conv_fwd(pm_guess* g, ConvL& c, const void* in, int B, int s, int per, int relu,
+              void* out_bf, float* out_f) {
+  if (c.fast_t && launch_conv_fast(g->st, in, B, s, per, c.cin, c.wf, c.n, c.fast_t,
+                                   g->w + c.b_off, c.cout, relu, out_bf, out_f, g->err))
+    return;
+  launch_conv_fwd(g->st, in, B, s, s, s, per, c.cin, c.wp, c.n, c.kp, g->w + c.b_off, c.cout,
+                  relu, out_bf, out_f, g->err);
+}
+
+// per-sample s_in = 1/rms(f): block partial sums of f^2 (RMS_BLOCKS per
+// sample, FP64, each over a fixed stride of the sample), then one thread per
+// sample adds them in block order
+constexpr int RMS_BLOCKS = 256;
+
+__global__ void k_rms_part(const float* __restrict__ f, long long vps, double* __restrict__ part) {
+  const int b = blockIdx.y;
   double acc = 0.0;
-  for (long long t = threadIdx.x; t < vps; t += blockDim.x) {
-    double x = f[b * vps + t];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < vps;
+       t += (long long)gridDim.x * blockDim.x) {
+    const double x = f[b * vps + t];
     acc += x * x;
   }
   __shared__ double sm[32];
@@ -150,12 +170,21 @@ __global__ void k_rms(const float* __restrict__ f, long long vps, int B, float o
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < (int)blockDim.x / 32; ++w) t += sm[w];
-    double rms = sqrt(t / (double)vps);
-    float si = rms > 0 ? (float)(1.0 / rms) : 0.0f;
-    sin_[b] = si;
-    sout[b] = rms > 0 ? (float)(rms * out_scale) : 0.0f;
-    tsc[b] = rms > 0 ? (float)(1.0 / (rms * out_scale)) : 0.0f;
+    part[(long long)b * gridDim.x + blockIdx.x] = t;
   }
+}
+
+__global__ void k_rms(const double* __restrict__ part, long long vps, int B, float out_scale,
+                      float* __restrict__ sin_, float* __restrict__ sout,
+                      float* __restrict__ tsc) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  double t = 0.0;
+  for (int q = 0; q < RMS_BLOCKS; ++q) t += part[(long long)b * RMS_BLOCKS + q];
+  const double rms = sqrt(t / (double)vps);
+  sin_[b] = rms > 0 ? (float)(1.0 / rms) : 0.0f;
+  sout[b] = rms > 0 ? (float)(rms * out_scale) : 0.0f;
+  tsc[b] = rms > 0 ? (float)(1.0 / (rms * out_scale)) : 0.0f;
 }
 
 #define GCK()                                                                          \
@@ -170,7 +199,10 @@ pm_status forward(pm_guess* g, const float* f, int B, int S, int per) {
   if (st != PM_OK) return st;
   if (!g->packed) pack_all(g);
   const long long vps = (long long)S * S * S;
-  k_rms<<<B, 256, 0, g->st>>>(f, vps, B, g->out_scale, g->scale_in, g->scale_out, g->tscale);
+  k_rms_part<<<dim3(RMS_BLOCKS, B), 256, 0, g->st>>>(f, vps, g->rms_part);
+  k_rms<<<(B + 127) / 128, 128, 0, g->st>>>(g->rms_part, vps, B, g->out_scale, g->scale_in,
+                                            g->scale_out, g->tscale);
+  note_launch();
   note_launch();
   launch_nn_input(g->st, f, vps, g->scale_in, B, g->act[SLOT_X].p);
   const int L = g->L;
@@ -185,8 +217,7 @@ pm_status forward(pm_guess* g, const float* f, int B, int S, int per) {
       in = g->act[SLOT_P + l].p;
     }
     ConvL& c = g->conv[ci++];
-    launch_conv_fwd(g->st, in, B, s, s, s, per, c.cin, c.wp, c.n, c.kp, g->w + c.b_off, c.cout, 1,
-                    g->act[SLOT_E + l].p, nullptr, g->err);
+    conv_fwd(g, c, in, B, s, per, 1, g->act[SLOT_E + l].p, nullptr);
   }
   // decoder
   for (int l = L - 2; l >= 0; --l) {
@@ -196,13 +227,11 @@ pm_status forward(pm_guess* g, const float* f, int B, int S, int per) {
     launch_chan_copy(g->st, g->act[SLOT_E + l].p, vox(B, S, l), cl, cl, 0, g->act[SLOT_C + l].p,
                      cu + cl, cu, false);
     ConvL& c = g->conv[ci++];
-    launch_conv_fwd(g->st, g->act[SLOT_C + l].p, B, s, s, s, per, c.cin, c.wp, c.n, c.kp,
-                    g->w + c.b_off, c.cout, 1, g->act[SLOT_D + l].p, nullptr, g->err);
+    conv_fwd(g, c, g->act[SLOT_C + l].p, B, s, per, 1, g->act[SLOT_D + l].p, nullptr);
   }
   ConvL& c = g->conv[ci];
   const void* d0 = L == 1 ? g->act[SLOT_E].p : g->act[SLOT_D].p;
-  launch_conv_fwd(g->st, d0, B, S, S, S, per, c.cin, c.wp, c.n, c.kp, g->w + c.b_off, c.cout, 0,
-                  nullptr, g->y, g->err);
+  conv_fwd(g, c, d0, B, S, per, 0, nullptr, g->y);
   GCK();
   return PM_OK;
 }
@@ -327,6 +356,12 @@ pm_status pm_guess_create(int32_t levels, void* stream, pm_guess** out) {
   for (auto& c : g->conv) {
     ok = ok && cudaMalloc(&c.wp, (size_t)c.n * c.kp * 2) == cudaSuccess;
     ok = ok && cudaMalloc(&c.wt, (size_t)c.nt * c.kpt * 2) == cudaSuccess;
+    // the staged-input kernel wherever its block and weights fit (forward at
+    // 256^3: 8.7 ms against 12.4 ms with every layer on the gathered tile);
+    // PM_NN_GATHER keeps the gathered tile everywhere
+    c.fast_t = getenv("PM_NN_GATHER") ? 0 : conv_fast_side(c.cin, c.cout);
+    if (c.fast_t)
+      ok = ok && cudaMalloc(&c.wf, (size_t)c.n * conv_fast_kf(c.cin) * 2) == cudaSuccess;
   }
   size_t pb = sizeof(float) * g->n_params;
   ok = ok && cudaMalloc((void**)&g->w, pb) == cudaSuccess &&
@@ -336,6 +371,7 @@ pm_status pm_guess_create(int32_t levels, void* stream, pm_guess** out) {
        cudaMalloc((void**)&g->scale_in, sizeof(float) * 4096) == cudaSuccess &&
        cudaMalloc((void**)&g->scale_out, sizeof(float) * 4096) == cudaSuccess &&
        cudaMalloc((void**)&g->tscale, sizeof(float) * 4096) == cudaSuccess &&
+       cudaMalloc((void**)&g->rms_part, sizeof(double) * 4096 * RMS_BLOCKS) == cudaSuccess &&
        cudaMalloc((void**)&g->loss, sizeof(double)) == cudaSuccess &&
        cudaMalloc((void**)&g->err, sizeof(int)) == cudaSuccess;
   if (!ok) {
@@ -428,10 +464,12 @@ void pm_guess_destroy(pm_guess* g) {
   for (auto& c : g->conv) {
     if (c.wp) cudaFree(c.wp);
     if (c.wt) cudaFree(c.wt);
+    if (c.wf) cudaFree(c.wf);
   }
   for (auto& b : g->act)
     if (b.p) cudaFree(b.p);
-  void* ps[] = {g->y, g->ld, g->lq, g->w, g->g, g->m, g->v, g->scale_in, g->scale_out, g->tscale, g->loss, g->err};
+  void* ps[] = {g->y, g->ld, g->lq, g->w, g->g, g->m, g->v, g->scale_in, g->scale_out,
+                g->tscale, g->rms_part, g->loss, g->err};
   for (void* p : ps)
     if (p) cudaFree(p);
   delete g;

@@ -154,6 +154,17 @@ void launch_gather_tsc(cudaStream_t st, float4* pos, float4* mom, long long N,
 constexpr int KT = 256;
 constexpr int KITEMS = 4;
 constexpr int PART_CHUNK = KT * KITEMS;
+// Learned guess: the forward 3x3x3 convolution as a tensor-core implicit
+// GEMM read straight from a staged input block (k_conv.cu).  conv_fast_side
+// gives the output block side for a layer (0: not applicable), wf the
+// weights packed by launch_pack_wf ([n][conv_fast_kf(cin)] BF16);
+// launch_conv_fast returns false if the kernel could not be configured.
+int conv_fast_side(int cin, int cout);
+int conv_fast_kf(int cin);
+void launch_pack_wf(cudaStream_t st, const float* w, int cin, int cout, int n, void* wf);
+bool launch_conv_fast(cudaStream_t st, const void* in, int B, int S, int per, int cin,
+                      const void* wf, int n, int T, const float* bias, int cout, int relu,
+                      void* out_bf, float* out_f, int* err);
 int gkd_blocks(long long N);
 // G: gradient field of k_grad (NULL: differences taken from Phi directly)
 void launch_gather_kick_drift(cudaStream_t st, float4* pos, float4* mom, long long N,
