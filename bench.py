@@ -458,6 +458,37 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
     return 0
 
+def run_guess512(args):
+    """--workload guess512: the learned initial guess on the 512^3 workload
+    (512^3 particles and mesh, 3000 Mpc/h, 100 steps from a = 0.02, mixed
+    precision to a relative residual of 1e-7): the same steps solved from
+    the warm start alone (the method without the network) and from the
+    network's correction of it; V-cycles saved, the network's time and the
+    particle-steps/s of each."""
+    import torch
+    from paper_1709_04703_gb300 import train_guess
+    torch.cuda.set_device(0)
+    steps = args.steps if args.steps_given else None
+    with Clocks(0) as clk:
+        out = train_guess.compare("pm512", args.weights, ("warm", "learned"), steps)
+    w, l = out["warm"], out["learned"]
+    z = np.load(args.weights)
+    meta = json.loads(str(z["meta"])) if "meta" in z.files else {}
+    line = {"metric": "particle-steps/s, PM step at 512^3, learned initial guess against the "
+                      "warm start, rtol 1e-7",
+            "value": l["particle_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": l["steps"], "higher_is_better": True, "dtype": "bf16 network, f32+df32 "
+            "solve", "data": "synthetic (seeded Zel'dovich ICs)",
+            "config": {"workload": "guess512", "n_mesh": 512, "n_particles": 512**3,
+                       "box_mpch": 3000.0, "rtol": 1e-7,
+                       "weights": os.path.relpath(args.weights, ROOT),
+                       "trained_pairs": meta.get("pairs"), "trained_on": meta.get("workload")},
+            "warm": w, "learned": l, "vcycles_saved": out["vcycles_saved"],
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 TABLE4 = {512.0: 1.08, 2048.0: 1.44, 8192.0: 3.02}   # Table 4, 512^3 particles
 
 
@@ -803,7 +834,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--inner", type=int, default=INNER,
                     help="FP32 V-cycles per defect in the mixed forms (1: one)")
-    ap.add_argument("--workload", choices=["pm256", "batch48", "shrink_table"], default="pm256")
+    ap.add_argument("--workload", choices=["pm256", "batch48", "shrink_table", "guess512"],
+                    default="pm256")
+    ap.add_argument("--weights", default=None,
+                    help="guess512: network weights (default: the committed ones)")
     ap.add_argument("--table-n", type=int, default=512,
                     help="shrink_table: particles and mesh per side")
     ap.add_argument("--table-domain", choices=["cube", "sphere"], default="cube",
@@ -823,6 +857,11 @@ def main():
         return run_batch(args)
     if args.workload == "shrink_table":
         return run_shrink_table(args)
+    if args.workload == "guess512":
+        if args.weights is None:
+            from paper_1709_04703_gb300 import train_guess
+            args.weights = train_guess.DEFAULT_WEIGHTS
+        return run_guess512(args)
     return run_ours(args)
 
 

@@ -25,16 +25,24 @@ from . import ics
 from .guess import GuessNet
 from .sim import Sim
 
-# trained by: python -m paper_1709_04703_gb300.train_guess --workload pm256 \
-#     --seeds 2 3 4 5 --epochs 2 --out <this file>
+# trained by (9753 pairs: the 18-minute limit ended the run before 20000):
+#   python -m paper_1709_04703_gb300.train_guess --workload pm256 \
+#     --seeds 2 3 4 5 6 7 8 9 10 11 12 13 --pairs 20000 --max-seconds 1080 --out <this file>
 DEFAULT_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
-                               "guess_l4_pm256.npz")
+                               "guess_l4_pm256_10k.npz")
 
 
-def run_pairs(cfg, steps=None, on_pair=None):
+_IC_CACHE = {}
+
+
+def run_pairs(cfg, steps=None, on_pair=None, stop=None):
     """Run one realisation with capture armed; on_pair(k, r, e, side,
-    periodic, stats) for every solve (r, e: CUDA views [1, s, s, s])."""
-    pos, mom, ids = ics.workload_ics(cfg)
+    periodic, stats) for every solve (r, e: CUDA views [1, s, s, s]); the
+    run ends early once stop() is true."""
+    key = (cfg["n"], cfg["alpha"], cfg["cutoff"], cfg["seed"], cfg["a_init"])
+    if key not in _IC_CACHE:  # a pass over the seeds regenerates no initial conditions
+        _IC_CACHE[key] = ics.workload_ics(cfg)
+    pos, mom, ids = _IC_CACHE[key]
     n = cfg["n"]
     sim = Sim(pos, mom, ids, n, cfg["box"], cfg["a_init"], cfg["a_final"], cfg["steps"],
               rtol=cfg["rtol"])
@@ -42,6 +50,8 @@ def run_pairs(cfg, steps=None, on_pair=None):
     e = torch.zeros(n ** 3, device="cuda")
     sim.capture(r, e)
     for k in range(cfg["steps"] if steps is None else steps):
+        if stop is not None and stop():
+            break
         sim.step(1)
         st = sim.stats()
         s = st["cube_side"]
@@ -52,25 +62,36 @@ def run_pairs(cfg, steps=None, on_pair=None):
     sim.close()
 
 
-def train(net, cfgs, lr=1e-3, epochs=1, steps=None, log=None):
+def train(net, cfgs, lr=1e-3, epochs=1, steps=None, log=None, pairs=None, max_seconds=None):
     """Online Adam on the pairs of every configuration in cfgs (epochs
-    passes).  Returns the history [(epoch, seed, step, side, periodic,
-    loss)]."""
+    passes, or as many as it takes to reach `pairs` pairs when given; no
+    further pair after max_seconds).  Returns the history [(epoch, seed,
+    step, side, periodic, loss)]."""
     hist = []
     fits = lambda s: s >= 16 and s % (1 << (net.levels - 1)) == 0  # noqa: E731
+    t_end = None if max_seconds is None else time.time() + max_seconds
+    done = lambda: ((pairs is not None and len(hist) >= pairs) or  # noqa: E731
+                    (t_end is not None and time.time() >= t_end))
 
-    for ep in range(epochs):
+    ep = 0
+    while ep < epochs or (pairs is not None and not done()):
         for cfg in cfgs:
+            if done():
+                break
+
             def on_pair(k, r, e, s, per, st):
-                if not fits(s):
+                if not fits(s) or done():
                     return
                 loss = net.loss_grad(r, e, per, 1)
                 net.adam(lr)
                 hist.append((ep, cfg["seed"], k, s, int(per), loss))
-                if log is not None:
-                    log(f"epoch {ep} seed {cfg['seed']} step {k} side {s} "
+                if log is not None and len(hist) % 100 == 0:
+                    log(f"pair {len(hist)} epoch {ep} seed {cfg['seed']} step {k} side {s} "
                         f"periodic {int(per)} |r_after|/|r| {np.sqrt(loss):.4f}")
-            run_pairs(cfg, steps, on_pair)
+            run_pairs(cfg, steps, on_pair, done)
+        ep += 1
+        if (pairs is None and ep >= epochs) or (t_end is not None and time.time() >= t_end):
+            break
     return hist
 
 
@@ -154,6 +175,10 @@ def main(argv=None):
     ap.add_argument("--workload", default="pm256")
     ap.add_argument("--seeds", type=int, nargs="+", default=[1])
     ap.add_argument("--epochs", type=int, default=1)
+    ap.add_argument("--pairs", type=int, default=None,
+                    help="train until this many pairs (passes over the seeds as needed)")
+    ap.add_argument("--max-seconds", type=float, default=None,
+                    help="take no further pair after this long")
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--levels", type=int, default=4)
     ap.add_argument("--lr", type=float, default=1e-3)
@@ -179,9 +204,10 @@ def main(argv=None):
         cfgs.append(c)
     t0 = time.time()
     hist = train(net, cfgs, a.lr, a.epochs, a.steps,
-                 log=lambda m: print(m, file=sys.stderr, flush=True))
+                 log=lambda m: print(m, file=sys.stderr, flush=True), pairs=a.pairs,
+                 max_seconds=a.max_seconds)
     save(a.out, net, hist, dict(workload=a.workload, seeds=a.seeds, epochs=a.epochs,
-                                lr=a.lr, seconds=time.time() - t0))
+                                pairs=len(hist), lr=a.lr, seconds=time.time() - t0))
     print(json.dumps(dict(pairs=len(hist), seconds=round(time.time() - t0, 1),
                           last_ratio=float(np.sqrt(hist[-1][-1])) if hist else None)))
     return 0
