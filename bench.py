@@ -392,26 +392,27 @@ def run_reference(args):
     return 0
 
 
-def run_batch(args):
-    """--workload batch48: 48 independent realisations (mesh 32..128^3, boxes
-    200-1500 Mpc/h, seeds 100-147, 50 steps from a=0.02) advanced by the
-    batched step; compared with the same realisations run one context after
-    another."""
+def _batch48(steps, warmup, sequential="all"):
+    """The 48-realisation batched workload (mesh 32..128^3, boxes 200-1500
+    Mpc/h, seeds 100-147, 50 steps from a = 0.02): the batched step over
+    `steps` steps after `warmup` untimed ones on a separate batch, and the
+    same realisations as separate contexts (sequential = "all": every one of
+    them, one after another; "128": the 128^3 ones, for the per-particle rate
+    of a single context at that size)."""
     import torch
     from paper_1709_04703_gb300 import _lib as L
     from paper_1709_04703_gb300 import ics
     from paper_1709_04703_gb300.sim import Batch, Sim
-    torch.cuda.set_device(0)
     cfgs = ics.batched_workload(range(100, 148))
     a0, a1, nsteps, rtol = cfgs[0]["a_init"], cfgs[0]["a_final"], cfgs[0]["steps"], cfgs[0]["rtol"]
-    K = min(args.steps, nsteps)
+    K = min(steps, nsteps)
     reals = []
     for c in cfgs:
         pos, mom, ids = ics.zeldovich(c["n"], c["alpha"], c["cutoff"], c["seed"], a0)
         reals.append(dict(pos=pos, mom=mom, ids=ids, n_mesh=c["n"], box=c["box"]))
     lib = L.load()
     warm = Batch(reals, a0, a1, nsteps, rtol=rtol)
-    warm.step(min(args.warmup, nsteps))
+    warm.step(min(warmup, nsteps))
     warm.close()
     batch = Batch(reals, a0, a1, nsteps, rtol=rtol)
     ps0 = sum(batch.stats(r)["particle_steps"] for r in range(len(reals)))
@@ -428,9 +429,11 @@ def run_batch(args):
     ps = sum(batch.stats(r)["particle_steps"] for r in range(len(reals))) - ps0
     vc = sum(batch.stats(r)["vcycles_total"] for r in range(len(reals)))
     batch.close()
-    # the same realisations, one context after another
     seq_ms, seq_ps = 0.0, 0
-    for re in reals:
+    pick = range(len(reals)) if sequential == "all" else \
+        [r for r, c in enumerate(cfgs) if c["n"] == 128]
+    for r in pick:
+        re = reals[r]
         sim = Sim(re["pos"], re["mom"], re["ids"], re["n_mesh"], re["box"], a0, a1, nsteps,
                   rtol=rtol)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -442,18 +445,37 @@ def run_batch(args):
         seq_ms += e0.elapsed_time(e1)
         seq_ps += sim.stats()["particle_steps"]
         sim.close()
+    return {"value": ps / (ms * 1e-3), "unit": UNIT, "steps": K, "warmup": warmup,
+            "ms_per_step": ms / K, "launches_per_step": launches / K,
+            "solve": "persistent (one cooperative launch per solve, decided on the device)",
+            "realisations": len(reals), "mesh_sizes": sorted({c["n"] for c in cfgs}),
+            "particles": int(sum(len(r["pos"]) for r in reals)), "rtol": rtol,
+            "vcycles_total": int(vc),
+            ("sequential_contexts" if sequential == "all" else "single_context_128"):
+                {"value": seq_ps / (seq_ms * 1e-3), "realisations": len(pick),
+                 "ms_per_step": seq_ms / K},
+            "clocks": clk.summary(), "gpu_launches": int(launches)}
+
+
+def run_batch(args):
+    """--workload batch48: the 48-realisation batched workload, compared with
+    the same realisations run one context after another."""
+    import torch
+    torch.cuda.set_device(0)
+    out = _batch48(args.steps, args.warmup, "all")
     line = {
         "metric": "particle-steps/s, batched PM step, 48 realisations",
-        "value": ps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": K,
-        "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True,
+        "value": out["value"], "unit": UNIT, "n_gpus": 1, "steps": out["steps"],
+        "warmup": args.warmup, "ms_per_step": out["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+df32",
         "data": "synthetic (seeded Zel'dovich ICs)",
-        "config": {"workload": "batch48", "realisations": len(reals),
-                   "mesh_sizes": sorted({c["n"] for c in cfgs}),
-                   "particles": int(sum(len(r["pos"]) for r in reals)), "rtol": rtol,
-                   "vcycles_total": int(vc)},
-        "sequential_contexts": {"value": seq_ps / (seq_ms * 1e-3), "ms_per_step": seq_ms / K},
-        "clocks": clk.summary(), "gpu_launches": int(launches),
+        "config": {"workload": "batch48", "realisations": out["realisations"],
+                   "mesh_sizes": out["mesh_sizes"], "particles": out["particles"],
+                   "rtol": out["rtol"], "vcycles_total": out["vcycles_total"],
+                   "solve": out["solve"]},
+        "sequential_contexts": out["sequential_contexts"],
+        "launches_per_step": out["launches_per_step"],
+        "clocks": out["clocks"], "gpu_launches": out["gpu_launches"],
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -705,6 +727,9 @@ def run_ours(args):
                                     net)
             compare[key]["weights"] = os.path.relpath(train_guess.DEFAULT_WEIGHTS, ROOT)
         net.close()
+        # the 48-realisation batched step (10 steps), with the 128^3 single
+        # context's rate per particle beside it
+        compare["batch48"] = _batch48(10, 3, "128")
 
     # end to end through the C ABI with host buffers (pinned): every timed
     # step copies the active particles host -> device, steps, and copies

@@ -385,10 +385,13 @@ pm_status pm_profile_read(pm_ctx* ctx, int32_t cls, double* ms, int64_t* groups,
  * Batched step: many independent realisations (each its own configuration,
  * mesh size, particles and lightcone schedule; Sec. 2.4 applied to each)
  * advance together.  Every phase of pm_step runs as one kernel launch over
- * all realisations (a device table maps each block to a realisation), and
- * one CUDA graph per batch holds the V-cycle of every realisation; a
- * realisation whose solve has converged is masked out of further V-cycles.
- * Results equal those of separate contexts bit for bit.
+ * all realisations (a device table maps each block to a realisation).  The
+ * solve (Sec. 2.1: defect, convergence test, V-cycle, repeated) is one
+ * persistent cooperative launch: its passes are separated by a grid-wide
+ * barrier, every block takes the convergence decisions from the residual
+ * norms on the device, a realisation that has converged is masked out of
+ * further passes, and the host reads nothing until the step ends.  Results
+ * equal those of separate contexts bit for bit.
  * Requirements: 1 <= n_real <= 64, precision PM_MIXED, all realisations on
  * the same number of steps and a_init/a_final (one schedule of a, each with
  * its own chi(a)/cell), stream not NULL.
@@ -409,6 +412,19 @@ pm_status pm_batch_get_lightcone(pm_batch* b, int32_t r, float* pos4, float* mom
  * step, as pm_get_forces (needs cfgs[r].store_forces = 1). */
 pm_status pm_batch_get_forces(pm_batch* b, int32_t r, float* f4, int32_t host_mem,
                               int64_t* n_out);
+/* How a batch solves.  persistent = 1 (the default where the GPU holds the
+ * kernel's grid): the persistent launch above.  persistent = 0: one CUDA
+ * graph holds the V-cycle of every realisation and the host reads the
+ * residual norms after each defect to decide (the two give the same bits).
+ * wait_seconds (> 0, finite; default 2): the longest wait at one grid
+ * barrier; when it runs out the kernel sets an error word, every block
+ * leaves, and pm_batch_step returns PM_ETIMEOUT (the batch's state is then
+ * undefined: destroy it).  extra_arrivals: 0; a value > 0 makes every
+ * barrier wait for arrivals that never come, which tests the time limit.
+ * PM_EINVAL on bad arguments, or persistent = 1 where the kernel's grid
+ * cannot be resident. */
+pm_status pm_batch_set_solve(pm_batch* b, int32_t persistent, double wait_seconds,
+                             int32_t extra_arrivals);
 const char* pm_batch_last_error(const pm_batch* b);
 void pm_batch_destroy(pm_batch* b);
 

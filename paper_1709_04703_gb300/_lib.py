@@ -31,8 +31,8 @@ EXPORTED = [
     "pm_get_potential", "pm_profile", "pm_profile_read", "pm_launch_count", "pm_last_error",
     "pm_destroy", "pm_shrink_static", "pm_shrink_static_error",
     "pm_batch_init", "pm_batch_step", "pm_batch_stats", "pm_batch_get_particles",
-    "pm_batch_get_lightcone", "pm_batch_get_forces", "pm_batch_last_error",
-    "pm_batch_destroy",
+    "pm_batch_get_lightcone", "pm_batch_get_forces", "pm_batch_set_solve",
+    "pm_batch_last_error", "pm_batch_destroy",
     "pm_mg_smooth", "pm_mg_restrict", "pm_mg_prolong", "pm_selftest_wait", "pm_nn_gemm_bf16", "pm_guess_create", "pm_guess_num_params", "pm_guess_set_params",
     "pm_guess_get_params", "pm_guess_forward", "pm_guess_loss_grad", "pm_guess_adam",
     "pm_guess_last_error", "pm_guess_destroy", "pm_set_guess", "pm_capture",
@@ -121,6 +121,7 @@ def load():
         "pm_batch_get_particles": (I32, [P, I32, P, P, I32, C.POINTER(I64)]),
         "pm_batch_get_lightcone": (I32, [P, I32, P, P, I32, C.POINTER(I64)]),
         "pm_batch_get_forces": (I32, [P, I32, P, I32, C.POINTER(I64)]),
+        "pm_batch_set_solve": (I32, [P, I32, C.c_double, I32]),
         "pm_mg_cluster_size": (I32, []),
         "pm_batch_last_error": (C.c_char_p, [P]),
         "pm_batch_destroy": (None, [P]),

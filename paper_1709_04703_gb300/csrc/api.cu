@@ -2313,7 +2313,7 @@ struct pm_batch {
   unsigned long long* d_cnt = nullptr;  // 4 per realisation: [0] survivors
   unsigned long long* h_cnt = nullptr;
   int* d_ovf = nullptr;
-  BTab t_dep, t_src, t_bnd, t_pred, t_def, t_gat, t_scan, t_scat;
+  BTab t_dep, t_src, t_bnd, t_pred, t_def, t_grad, t_gat, t_scan, t_scat;
   std::vector<BTab> t_vc;  // V-cycle launch slots
   int maxLc = 0;
   bool tables_stale = true;
@@ -2321,6 +2321,20 @@ struct pm_batch {
   long long vgraph_kernels = 0;
   int rb_bx = 32, rb_by = 8;  // block shape of the batched colour pass (autotuned)
   bool rb_tuned = false;
+  // the persistent solve: one cooperative launch per solve
+  bool persistent = false;
+  double wait_s = 2.0;         // longest wait at one grid barrier
+  int extra = 0;               // barrier arrivals that never come (tests the wait limit)
+  GridBar* d_bar = nullptr;
+  GridBar* h_bar = nullptr;
+  int* d_iters = nullptr;      // [0, MAX_REAL): V-cycles, [MAX_REAL, 2 MAX_REAL): failed
+  int* h_iters = nullptr;
+  double* d_rel = nullptr;     // [0, MAX_REAL): last relative residual, then rtol
+  double* h_rel = nullptr;
+  int* d_maxv = nullptr;
+  SolveSlot* d_slots = nullptr;
+  int n_slots_dev = 0;
+  bool solved_on_device = false;  // this step's solve awaits its read-back
   std::string err;
 };
 
@@ -2610,7 +2624,133 @@ pm_status batch_vcycle(pm_batch* B) {
   return PM_OK;
 }
 
+// The V-cycle slots in launch order, for the persistent solve.
+pm_status upload_solve_slots(pm_batch* B) {
+  const int M = B->maxLc, n = n_slots(M);
+  if (B->d_slots && B->n_slots_dev != n) {
+    cudaFree(B->d_slots);
+    B->d_slots = nullptr;
+  }
+  if (!B->d_slots && cudaMalloc((void**)&B->d_slots, sizeof(SolveSlot) * n) != cudaSuccess)
+    return bfail(B, PM_ENOMEM, "pm_batch: solve slot allocation failed");
+  B->n_slots_dev = n;
+  std::vector<SolveSlot> v;
+  auto add = [&](int kind, int slot, int cnt) {
+    v.push_back(SolveSlot{kind, cnt, B->t_vc[slot].d_desc, B->t_vc[slot].d_tab});
+  };
+  for (int l = 0; l < M; ++l) {
+    for (int k = 0; k < 4; ++k) add(SLOT_RBGS, slot_down(l, k), 0);
+    add(SLOT_RESTRICT, slot_down(l, 4), 0);
+  }
+  add(SLOT_CMG, slot_bottom(M), B->R);
+  for (int l = M - 1; l >= 0; --l) {
+    add(SLOT_PROLONG, slot_up(M, l, 0), 0);
+    for (int k = 1; k < 5; ++k) add(SLOT_RBGS, slot_up(M, l, k), 0);
+  }
+  // synchronous: the slots change only with the V-cycle depth
+  if (cudaMemcpy(B->d_slots, v.data(), sizeof(SolveSlot) * v.size(), cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return bfail(B, PM_ECUDA, "pm_batch: solve slot upload failed");
+  return PM_OK;
+}
+
+// The gradient-field table: every realisation's potential in buffer cur
+// (alt: the other buffer, taken by the persistent solve after an odd number
+// of V-cycles).
+void upload_grad_table(pm_batch* B) {
+  std::vector<GradDesc> d;
+  std::vector<int> bl;
+  for (int r = 0; r < B->R; ++r) {
+    pm_ctx* c = B->ctx[r];
+    if (c->n_active <= 0) continue;
+    GradDesc e{};
+    e.ph = c->phi_h[c->cur];
+    e.pl = c->phi_l[c->cur];
+    e.ph_alt = c->phi_h[c->cur ^ 1];
+    e.pl_alt = c->phi_l[c->cur ^ 1];
+    e.n = c->n;
+    e.lo = c->lo;
+    e.s = c->s;
+    e.periodic = c->periodic;
+    e.G = c->grad;
+    set_dims(e, r, dim3((unsigned)((c->s + 31) / 32), (unsigned)((c->s + 7) / 8), (unsigned)c->s));
+    d.push_back(e);
+    bl.push_back(nblocks(dim3((unsigned)((c->s + 31) / 32), (unsigned)((c->s + 7) / 8),
+                              (unsigned)c->s)));
+  }
+  tab_upload(B, B->t_grad, d, bl);
+}
+
+// One persistent launch solves every realisation from its current buffer to
+// its tolerance; V-cycle counts, failures and residuals are read back when
+// the step ends (batch_solve_done).
+pm_status batch_solve_persistent(pm_batch* B) {
+  const int R = B->R;
+  if (B->tables_stale) {
+    upload_vcycle_tables(B);
+    B->tables_stale = false;
+  }
+  if (!B->d_slots || B->n_slots_dev != n_slots(B->maxLc)) {
+    pm_status st = upload_solve_slots(B);
+    if (st != PM_OK) return st;
+  }
+  std::vector<DefectDesc> d;
+  std::vector<int> bl;
+  for (int r = 0; r < R; ++r) {
+    pm_ctx* c = B->ctx[r];
+    const int lo = c->lo, s = c->s, c0 = c->cur;
+    DefectDesc e{};
+    e.ph = full_view(c, c->phi_h[c0], lo, s);
+    e.pl = full_view(c, c->phi_l[c0], lo, s);
+    e.qh = full_view(c, c->phi_h[c0 ^ 1], lo, s);
+    e.ql = full_view(c, c->phi_l[c0 ^ 1], lo, s);
+    e.e = compact_view(c->lu[0], s);
+    e.fh = full_view(c, c->f_hi, lo, s);
+    e.fl = full_view(c, c->f_lo, lo, s);
+    e.rb = compact_view(c->lb[0], s);
+    e.periodic = c->periodic;
+    e.write_r = 1;
+    e.partial = c->partial;
+    e.counter = c->counter;
+    e.out = B->d_scal + 16 * r + 11;
+    set_dims(e, r, defect_grid(s));
+    d.push_back(e);
+    bl.push_back(nblocks(defect_grid(s)));
+  }
+  tab_upload(B, B->t_def, d, bl);
+  upload_grad_table(B);
+  cudaMemsetAsync(B->d_bar, 0, sizeof(GridBar), B->st);
+  cudaMemsetAsync(B->d_iters + MAX_REAL, 0, sizeof(int) * R, B->st);
+  SolveArgs a{};
+  a.grad = (const GradDesc*)B->t_grad.d_desc;
+  a.grad_t = B->t_grad.d_tab;
+  a.def = (const DefectDesc*)B->t_def.d_desc;
+  a.def_t = B->t_def.d_tab;
+  a.slots = B->d_slots;
+  a.n_slots = B->n_slots_dev;
+  a.R = R;
+  a.scal = B->d_scal;
+  a.rtol = B->d_rel + MAX_REAL;
+  a.maxv = B->d_maxv;
+  a.iters = B->d_iters;
+  a.failed = B->d_iters + MAX_REAL;
+  a.rel = B->d_rel;
+  a.bar = B->d_bar;
+  a.limit_ns = (unsigned long long)(B->wait_s * 1e9);
+  a.extra = B->extra;
+  cudaError_t e = launch_solve_b(B->st, a);
+  if (e != cudaSuccess) return bfail(B, PM_ECUDA, cudaGetErrorString(e));
+  B->solved_on_device = true;
+  return PM_OK;
+}
+
 pm_status batch_sync(pm_batch* B) {
+  if (B->solved_on_device) {
+    cudaMemcpyAsync(B->h_iters, B->d_iters, sizeof(int) * 2 * MAX_REAL, cudaMemcpyDeviceToHost,
+                    B->st);
+    cudaMemcpyAsync(B->h_rel, B->d_rel, sizeof(double) * B->R, cudaMemcpyDeviceToHost, B->st);
+    cudaMemcpyAsync(B->h_bar, B->d_bar, sizeof(GridBar), cudaMemcpyDeviceToHost, B->st);
+  }
   cudaMemcpyAsync(B->h_scal, B->d_scal, sizeof(double) * 16 * B->R, cudaMemcpyDeviceToHost,
                   B->st);
   cudaMemcpyAsync(B->h_cnt, B->d_cnt, sizeof(unsigned long long) * 4 * B->R,
@@ -2619,6 +2759,37 @@ pm_status batch_sync(pm_batch* B) {
   if (e != cudaSuccess) return bfail(B, PM_ECUDA, cudaGetErrorString(e));
   e = cudaGetLastError();
   if (e != cudaSuccess) return bfail(B, PM_ECUDA, cudaGetErrorString(e));
+  return PM_OK;
+}
+
+// After the step's sync: the outcome of a persistent solve per realisation
+// (its potential ends in the buffer of parity iters relative to the start).
+pm_status batch_solve_done(pm_batch* B) {
+  if (!B->solved_on_device) return PM_OK;
+  B->solved_on_device = false;
+  if (B->h_bar->err) {
+    char buf[200];
+    snprintf(buf, sizeof buf,
+             "pm_batch_step: a grid barrier of the persistent solve waited longer than %.3g s "
+             "(pass %d); the batch must be destroyed",
+             B->wait_s, B->h_bar->where);
+    return bfail(B, PM_ETIMEOUT, buf);
+  }
+  for (int r = 0; r < B->R; ++r) {
+    pm_ctx* c = B->ctx[r];
+    const int it = B->h_iters[r];
+    if (B->h_iters[MAX_REAL + r]) {
+      char buf[200];
+      snprintf(buf, sizeof buf,
+               "realisation %d: relative residual %.3e after %d V-cycles (rtol %.1e)", r,
+               B->h_rel[r], it, c->cfg.rtol);
+      return bfail(B, PM_ENOCONV, buf);
+    }
+    c->cur ^= it & 1;
+    c->vcycles_last = it;
+    c->vcycles_total += it;
+    c->resid_last = B->h_rel[r];
+  }
   return PM_OK;
 }
 
@@ -2680,13 +2851,42 @@ pm_status pm_batch_init(int32_t n_real, const pm_config* cfgs, const float* cons
       cudaMalloc((void**)&B->d_cnt, sizeof(unsigned long long) * 4 * MAX_REAL) != cudaSuccess ||
       cudaMallocHost((void**)&B->h_cnt, sizeof(unsigned long long) * 4 * MAX_REAL) !=
           cudaSuccess ||
-      cudaMalloc((void**)&B->d_ovf, sizeof(int) * MAX_REAL) != cudaSuccess)
+      cudaMalloc((void**)&B->d_ovf, sizeof(int) * MAX_REAL) != cudaSuccess ||
+      cudaMalloc((void**)&B->d_bar, sizeof(GridBar)) != cudaSuccess ||
+      cudaMallocHost((void**)&B->h_bar, sizeof(GridBar)) != cudaSuccess ||
+      cudaMalloc((void**)&B->d_iters, sizeof(int) * 2 * MAX_REAL) != cudaSuccess ||
+      cudaMallocHost((void**)&B->h_iters, sizeof(int) * 2 * MAX_REAL) != cudaSuccess ||
+      cudaMalloc((void**)&B->d_rel, sizeof(double) * 2 * MAX_REAL) != cudaSuccess ||
+      cudaMallocHost((void**)&B->h_rel, sizeof(double) * MAX_REAL) != cudaSuccess ||
+      cudaMalloc((void**)&B->d_maxv, sizeof(int) * MAX_REAL) != cudaSuccess)
     st = bfail(B, PM_ENOMEM, "pm_batch_init: allocation failed");
+  if (st == PM_OK) {
+    // per-realisation tolerances of the persistent solve (fixed for the run)
+    double tol[MAX_REAL];
+    int mv[MAX_REAL];
+    for (int r = 0; r < n_real; ++r) {
+      tol[r] = cfgs[r].rtol;
+      mv[r] = cfgs[r].max_vcycles;
+    }
+    if (cudaMemcpy(B->d_rel + MAX_REAL, tol, sizeof(double) * n_real, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(B->d_maxv, mv, sizeof(int) * n_real, cudaMemcpyHostToDevice) != cudaSuccess)
+      st = bfail(B, PM_ECUDA, "pm_batch_init: tolerance upload failed");
+    // the persistent solve takes the one-CTA coarse levels (tops <= 16^3)
+    // and needs its whole grid resident; the graph path otherwise
+    B->persistent = cmg_cluster() == 1 && solve_grid_b() > 0;
+    if (B->persistent) {
+      B->rb_bx = 32;  // the persistent kernel's block
+      B->rb_by = 8;
+      B->rb_tuned = true;
+    }
+  }
   if (st == PM_OK) st = tab_alloc(B, B->t_dep, sizeof(DepositDesc));
   if (st == PM_OK) st = tab_alloc(B, B->t_src, sizeof(SourceDesc));
   if (st == PM_OK) st = tab_alloc(B, B->t_bnd, sizeof(BoundaryDesc));
   if (st == PM_OK) st = tab_alloc(B, B->t_pred, sizeof(PredictDesc));
   if (st == PM_OK) st = tab_alloc(B, B->t_def, sizeof(DefectDesc));
+  if (st == PM_OK) st = tab_alloc(B, B->t_grad, sizeof(GradDesc));
   if (st == PM_OK) st = tab_alloc(B, B->t_gat, sizeof(GatherDesc));
   if (st == PM_OK) st = tab_alloc(B, B->t_scan, sizeof(ScanDesc));
   if (st == PM_OK) st = tab_alloc(B, B->t_scat, sizeof(ScatterDesc));
@@ -2697,6 +2897,7 @@ pm_status pm_batch_init(int32_t n_real, const pm_config* cfgs, const float* cons
   cudaMemsetAsync(B->d_scal, 0, sizeof(double) * 16 * MAX_REAL, B->st);
   cudaMemsetAsync(B->d_cnt, 0, sizeof(unsigned long long) * 4 * MAX_REAL, B->st);
   cudaMemsetAsync(B->d_ovf, 0, sizeof(int) * MAX_REAL, B->st);
+  cudaMemsetAsync(B->d_iters, 0, sizeof(int) * 2 * MAX_REAL, B->st);
   *out = B;
   return PM_OK;
 }
@@ -2719,7 +2920,7 @@ pm_status pm_batch_step(pm_batch* B, int32_t n_steps) {
       if (st != PM_OK) return bfail(B, st, c->err);
       if (changed) B->tables_stale = true;
     }
-    if (B->tables_stale && !B->vgraph) {
+    if (B->t_vc.empty()) {
       // the first configuration fixes the V-cycle depth (cubes only shrink)
       int M = 0;
       for (int r = 0; r < R; ++r) M = std::max(M, first_small_level(B->ctx[r]));
@@ -2847,9 +3048,13 @@ pm_status pm_batch_step(pm_batch* B, int32_t n_steps) {
       launch_predict_b(B->st, g, (const PredictDesc*)B->t_pred.d_desc, B->t_pred.d_tab);
     }
     // 4. solve every realisation to its rtol
+    if (B->persistent) {
+      pm_status st = batch_solve_persistent(B);
+      if (st != PM_OK) return st;
+    }
     std::vector<int> it(R, 0);
-    for (int r = 0; r < R; ++r) B->h_active[r] = 1;
-    for (;;) {
+    for (int r = 0; r < R; ++r) B->h_active[r] = B->persistent ? 0 : 1;
+    while (!B->persistent) {
       std::vector<DefectDesc> d;
       std::vector<int> bl, swapped;
       for (int r = 0; r < R; ++r) {
@@ -2914,7 +3119,13 @@ pm_status pm_batch_step(pm_batch* B, int32_t n_steps) {
       c->ah_hist[1] = c->a_half[k];
       c->n_sol++;
     }
-    // 5-6. gather + kick + drift (+ keep flags)
+    // 5-6. gradient field (the persistent solve wrote it), gather + kick +
+    // drift (+ keep flags)
+    if (!B->persistent) {
+      upload_grad_table(B);
+      launch_grad_b(B->st, B->t_grad.h_tab->off[B->t_grad.h_tab->m],
+                    (const GradDesc*)B->t_grad.d_desc, B->t_grad.d_tab);
+    }
     bool any_flag = false;
     std::vector<int> flagged(R, 0);
     {
@@ -2930,8 +3141,7 @@ pm_status pm_batch_step(pm_batch* B, int32_t n_steps) {
         e.pos = c->pos;
         e.mom = c->mom;
         e.N = c->n_active;
-        e.ph = c->phi_h[c->cur];
-        e.pl = c->phi_l[c->cur];
+        e.G = c->grad;
         e.n = c->n;
         e.lo = c->lo;
         e.s = c->s;
@@ -2996,6 +3206,8 @@ pm_status pm_batch_step(pm_batch* B, int32_t n_steps) {
     }
     pm_status st = batch_sync(B);
     if (st != PM_OK) return st;
+    st = batch_solve_done(B);
+    if (st != PM_OK) return st;
     for (int r = 0; r < R; ++r) {
       pm_ctx* c = B->ctx[r];
       c->particle_steps += c->n_active;
@@ -3042,6 +3254,33 @@ pm_status pm_batch_get_lightcone(pm_batch* B, int32_t r, float* pos4, float* mom
   return pm_get_lightcone(B->ctx[r], pos4, mom4, host_mem, n_out);
 }
 
+pm_status pm_batch_set_solve(pm_batch* B, int32_t persistent, double wait_seconds,
+                             int32_t extra_arrivals) {
+  if (!B) return bfail(nullptr, PM_EINVAL, "pm_batch_set_solve: NULL batch");
+  if (!(wait_seconds > 0.0) || !std::isfinite(wait_seconds) || wait_seconds > 3600.0 ||
+      extra_arrivals < 0 || (persistent != 0 && persistent != 1))
+    return bfail(B, PM_EINVAL, "pm_batch_set_solve: bad argument");
+  if (persistent && !(cmg_cluster() == 1 && solve_grid_b() > 0))
+    return bfail(B, PM_EINVAL, "pm_batch_set_solve: the persistent solve cannot run here "
+                               "(coarse levels in a cluster, or grid not resident)");
+  if (persistent != (int)B->persistent) {
+    B->persistent = persistent != 0;
+    // block shape of the colour pass: the persistent kernel's, or autotuned
+    B->rb_bx = 32;
+    B->rb_by = 8;
+    B->rb_tuned = B->persistent;
+    B->tables_stale = true;
+    if (B->vgraph) {
+      cudaStreamSynchronize(B->st);
+      cudaGraphExecDestroy(B->vgraph);
+      B->vgraph = nullptr;
+    }
+  }
+  B->wait_s = wait_seconds;
+  B->extra = extra_arrivals;
+  return PM_OK;
+}
+
 const char* pm_batch_last_error(const pm_batch* B) { return B ? B->err.c_str() : g_err.c_str(); }
 
 void pm_batch_destroy(pm_batch* B) {
@@ -3049,12 +3288,20 @@ void pm_batch_destroy(pm_batch* B) {
   if (B->st) cudaStreamSynchronize(B->st);
   if (B->vgraph) cudaGraphExecDestroy(B->vgraph);
   for (pm_ctx* c : B->ctx) pm_destroy(c);
-  for (BTab* t : {&B->t_dep, &B->t_src, &B->t_bnd, &B->t_pred, &B->t_def, &B->t_gat,
-                  &B->t_scan, &B->t_scat})
+  for (BTab* t : {&B->t_dep, &B->t_src, &B->t_bnd, &B->t_pred, &B->t_def, &B->t_grad,
+                  &B->t_gat, &B->t_scan, &B->t_scat})
     tab_free(*t);
   for (auto& t : B->t_vc) tab_free(t);
   if (B->d_active) cudaFree(B->d_active);
   if (B->h_active) cudaFreeHost(B->h_active);
+  if (B->d_bar) cudaFree(B->d_bar);
+  if (B->h_bar) cudaFreeHost(B->h_bar);
+  if (B->d_iters) cudaFree(B->d_iters);
+  if (B->h_iters) cudaFreeHost(B->h_iters);
+  if (B->d_rel) cudaFree(B->d_rel);
+  if (B->h_rel) cudaFreeHost(B->h_rel);
+  if (B->d_maxv) cudaFree(B->d_maxv);
+  if (B->d_slots) cudaFree(B->d_slots);
   if (B->d_scal) cudaFree(B->d_scal);
   if (B->h_scal) cudaFreeHost(B->h_scal);
   if (B->d_cnt) cudaFree(B->d_cnt);

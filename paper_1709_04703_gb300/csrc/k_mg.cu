@@ -3,6 +3,9 @@
 // fused residual + 8-cell restriction, trilinear prolongation + correction,
 // a single-CTA coarsest solve, and the double-float defect-correction loop
 // (residual of the double-float potential; Phi += e).
+#include <cstdlib>
+
+#include "cmg_dev.cuh"
 #include "mg_arith.cuh"
 #include "pm_kernels.cuh"
 
@@ -626,8 +629,16 @@ void launch_prolong(cudaStream_t st, Grid uc, Grid u, int periodic, float gam_c)
 // With CORRECT the potential is first advanced by the V-cycle's correction,
 // Phi' = Phi + e (the e grid has zero ghosts / the same wrap), evaluated on
 // the fly at all 7 stencil points; Phi' is written out of place to (qh, ql)
-// and the residual is that of Phi'.
-template <bool CORRECT>
+// and the residual is that of Phi'.  NC: the grids are read through the
+// non-coherent cache (they do not change during the launch); the persistent
+// solve, which rewrites them between its phases, reads them from L2.
+template <bool NC>
+__device__ __forceinline__ float ldx(const float* p) {
+  if (NC) return __ldg(p);
+  return __ldcg(p);
+}
+
+template <bool CORRECT, bool NC = true>
 __device__ __forceinline__ void d_defect(const BI& bi, Grid ph, Grid pl, Grid e, Grid qh, Grid ql,
                                                 Grid fh, Grid fl, Grid rb, int periodic,
                                                 int write_r, double* __restrict__ partial,
@@ -647,10 +658,10 @@ __device__ __forceinline__ void d_defect(const BI& bi, Grid ph, Grid pl, Grid e,
     // the corrected double-float value of Phi at (i, j, kk)
     auto column = [&](int kk, float& H, float& L) {
       const int c = gidx(ph, i, j, kk);
-      H = __ldg(ph.base + c);
-      L = __ldg(pl.base + c);
+      H = ldx<NC>(ph.base + c);
+      L = ldx<NC>(pl.base + c);
       if (CORRECT) {
-        df t = two_sum(H, __ldg(e.base + gidx(e, i, j, kk)));
+        df t = two_sum(H, ldx<NC>(e.base + gidx(e, i, j, kk)));
         H = t.hi;
         L = __fadd_rn(L, t.lo);
       }
@@ -668,13 +679,13 @@ __device__ __forceinline__ void d_defect(const BI& bi, Grid ph, Grid pl, Grid e,
       const int c = gidx(ph, i, j, k);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        nh[q] = __ldg(ph.base + c + off[q]);
-        nl[q] = __ldg(pl.base + c + off[q]);
-        if (CORRECT) ne[q] = __ldg(e.base + gidx(e, i, j, k) + eoff[q]);
+        nh[q] = ldx<NC>(ph.base + c + off[q]);
+        nl[q] = ldx<NC>(pl.base + c + off[q]);
+        if (CORRECT) ne[q] = ldx<NC>(e.base + gidx(e, i, j, k) + eoff[q]);
       }
       const int fc = gidx(fh, i, j, k);
-      nfh = __ldg(fh.base + fc);
-      nfl = __ldg(fl.base + fc);
+      nfh = ldx<NC>(fh.base + fc);
+      nfl = ldx<NC>(fl.base + fc);
     };
     load_plane(k0);
     for (int k = k0; k < k1; ++k) {
@@ -1054,5 +1065,268 @@ dim3 rbgs_grid(int s, int bx, int by) {
 }
 dim3 full_grid(int s) { return grid_full(s); }
 dim3 defect_grid(int s) { return grid_defect(s); }
+
+// ---------------------------------------------------------------------------
+// Persistent batched solve.  One cooperative launch (all blocks resident)
+// takes every realisation of a batch from its starting potential to its
+// tolerance: defect (with the V-cycle's correction applied), the
+// convergence test, and the V-cycle's passes, each pass over all still
+// active realisations, separated by a grid-wide barrier.  The decisions are
+// those of a single context's host loop (Sec. 2.1 solve; stop once
+// ||f - A Phi|| / ||f|| <= rtol), taken by every block alike from the same
+// residual norms, so no host read happens inside a solve.
+// ---------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
+               : "=r"(old)
+               : "l"(p), "r"(v)
+               : "memory");
+  return old;
+}
+__device__ __forceinline__ int ld_volatile_i32(const int* p) {
+  return *(const volatile int*)p;
+}
+
+// Grid-wide barrier with a bounded wait.  Thread 0 of each block reads the
+// generation, arrives, and either (last arrival) resets the count and
+// publishes the next generation, or polls the generation until it changes,
+// the barrier's error word is set, or limit_ns has passed (then it sets the
+// error word and the phase).  Returns false, in every thread of the block,
+// once the barrier has failed: the caller leaves the kernel.
+__device__ bool grid_barrier(GridBar* g, unsigned expected, unsigned long long limit_ns,
+                             int phase) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    int good = ld_volatile_i32(&g->err) == 0;
+    if (good) {
+      __threadfence();
+      const unsigned gen = ld_acquire_u32(&g->gen);
+      const unsigned arrived = atom_add_acq_rel_u32(&g->count, 1u) + 1u;
+      if (arrived == expected) {
+        g->count = 0u;
+        st_release_u32(&g->gen, gen + 1u);
+      } else {
+        const unsigned long long t0 = global_ns();
+        while (ld_acquire_u32(&g->gen) == gen) {
+          if (ld_volatile_i32(&g->err)) {
+            good = 0;
+            break;
+          }
+          if (global_ns() - t0 > limit_ns) {
+            if (atomicCAS(&g->err, 0, 1) == 0) atomicExch(&g->where, phase);
+            good = 0;
+            break;
+          }
+          __nanosleep(100);
+        }
+      }
+      __threadfence();
+    }
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+constexpr int SOLVE_NT = 256;  // 32 x 8 threads: the block of every batched mesh pass
+
+// The blocks of table t, taken by the blocks of the grid in turn: block
+// blockIdx.x takes blocks blockIdx.x, blockIdx.x + gridDim.x, ...  The table's
+// block offsets are staged in shared memory (s_off, MAX_MEMBERS + 1 ints) and
+// the member is found by walking forward (members are in block order), so a
+// block costs no dependent global loads beyond its descriptor; the blocks of
+// inactive realisations are skipped member by member.
+template <class D, class F>
+__device__ __forceinline__ void each_block(const D* d, const BTable* t, const int* act,
+                                           int* s_off, F&& f) {
+  const int tid = (int)(threadIdx.x + threadIdx.y * blockDim.x);
+  __syncthreads();  // the previous phase's readers of s_off are done
+  const int m = t->m;
+  for (int i = tid; i <= m; i += (int)(blockDim.x * blockDim.y)) s_off[i] = t->off[i];
+  __syncthreads();
+  if (m <= 0) return;
+  const int tot = s_off[m], G = (int)gridDim.x;
+  int q = 0;
+  int b = (int)blockIdx.x;
+  while (b < tot) {
+    while (s_off[q + 1] <= b) ++q;
+    const D& e = d[q];
+    if (act && !act[e.r]) {
+      // the first block of this grid block's sequence past member q
+      const int next = s_off[q + 1];
+      b = next + ((((int)blockIdx.x - next) % G) + G) % G;
+      continue;
+    }
+    const int lb = b - s_off[q];
+    const BI bi{lb % e.gx, (lb / e.gx) % e.gy, lb / (e.gx * e.gy), e.gx, e.gy, e.gz};
+    f(e, bi);
+    __syncthreads();  // the passes' shared reduction words are reused
+    b += G;
+  }
+}
+
+template <int MINB>
+__global__ void __launch_bounds__(SOLVE_NT, MINB) kb_solve(SolveArgs a) {
+  extern __shared__ float cc_sm[];
+  __shared__ int act[MAX_REAL], it[MAX_REAL];
+  __shared__ float red[CC_NT / 32];
+  __shared__ CcLevel lev[CC_MAXL];
+  __shared__ int nlev;
+  __shared__ int s_off[MAX_MEMBERS + 1];
+  const int tid = (int)(threadIdx.x + threadIdx.y * blockDim.x);
+  const unsigned expected = gridDim.x + (unsigned)a.extra;
+  for (int r = tid; r < a.R; r += SOLVE_NT) {
+    act[r] = 1;
+    it[r] = 0;
+  }
+  __syncthreads();
+  int phase = 0;
+  for (;;) {
+    // defect: after V-cycle k >= 1 the correction e moves the potential from
+    // the buffer of parity k - 1 into that of parity k (k = 0: no correction)
+    each_block(a.def, a.def_t, act, s_off, [&](const DefectDesc& e, const BI& bi) {
+      const int k = it[e.r];
+      if (k == 0)
+        d_defect<false, false>(bi, e.ph, e.pl, e.e, e.ph, e.pl, e.fh, e.fl, e.rb, e.periodic,
+                               e.write_r, e.partial, e.counter, e.out, 6.0f, 0.0f);
+      else if (((k - 1) & 1) == 0)
+        d_defect<true, false>(bi, e.ph, e.pl, e.e, e.qh, e.ql, e.fh, e.fl, e.rb, e.periodic,
+                              e.write_r, e.partial, e.counter, e.out, 6.0f, 0.0f);
+      else
+        d_defect<true, false>(bi, e.qh, e.ql, e.e, e.ph, e.pl, e.fh, e.fl, e.rb, e.periodic,
+                              e.write_r, e.partial, e.counter, e.out, 6.0f, 0.0f);
+    });
+    if (!grid_barrier(a.bar, expected, a.limit_ns, phase++)) return;
+    // convergence test of every active realisation, the same in every block
+    if (tid < a.R && act[tid]) {
+      const int r = tid;
+      const double f2 = __ldcg(a.scal + 16 * r), r2 = __ldcg(a.scal + 16 * r + 11);
+      const double v = f2 > 0.0 ? sqrt(r2 / f2) : 0.0;
+      if (blockIdx.x == 0) a.rel[r] = v;
+      if (v <= a.rtol[r] || f2 == 0.0) {
+        act[r] = 0;
+      } else if (it[r] >= a.maxv[r]) {
+        act[r] = 0;
+        if (blockIdx.x == 0) a.failed[r] = 1;
+      } else {
+        it[r] += 1;
+      }
+    }
+    if (!__syncthreads_or(tid < a.R && act[tid])) break;
+    // one V(2,2) cycle of every active realisation, pass by pass
+    for (int sl = 0; sl < a.n_slots; ++sl) {
+      const SolveSlot S = a.slots[sl];
+      if (S.kind == SLOT_RBGS) {
+        each_block((const RbgsDesc*)S.d, S.t, act, s_off,
+                   [&](const RbgsDesc& e, const BI& bi) {
+                     d_rbgs(bi, e.u, e.b, e.h2, e.color, e.periodic, e.gam, e.zero_start, 6.0f);
+                   });
+      } else if (S.kind == SLOT_RESTRICT) {
+        each_block((const RestrictDesc*)S.d, S.t, act, s_off,
+                   [&](const RestrictDesc& e, const BI& bi) {
+                     d_resid_restrict(bi, e.u, e.b, e.inv_h2, e.uc, e.bc, e.periodic, e.gam,
+                                      6.0f);
+                   });
+      } else if (S.kind == SLOT_PROLONG) {
+        each_block((const ProlongDesc*)S.d, S.t, act, s_off,
+                   [&](const ProlongDesc& e, const BI& bi) {
+                     d_prolong(bi, e.uc, e.u, e.periodic, e.gam_c);
+                   });
+      } else {  // SLOT_CMG: the coarse levels of one realisation per block
+        const CmgDesc* cd = (const CmgDesc*)S.d;
+        for (int q = (int)blockIdx.x; q < S.n; q += (int)gridDim.x) {
+          const CmgDesc& e = cd[q];
+          if (!act[e.r]) continue;
+          if (tid == 0) Cc<1, SOLVE_NT>::init_levels(lev, nlev, e.u.s, e.level, e.periodic, 0.0f);
+          __syncthreads();
+          Cc<1, SOLVE_NT> c;
+          c.sm = cc_sm;
+          c.my = 0;
+          c.periodic = e.periodic;
+          c.sweeps = e.sweeps;
+          c.nlev = nlev;
+          c.sig0 = 0.0f;
+          c.gu = e.u;
+          c.gb = e.b;
+          c.V = lev;
+          c.init_pointers(lev);
+          __syncthreads();
+          c.run(e.zero_top, red);
+          __syncthreads();
+        }
+      }
+      if (!grid_barrier(a.bar, expected, a.limit_ns, phase++)) return;
+    }
+  }
+  if (blockIdx.x == 0)
+    for (int r = tid; r < a.R; r += SOLVE_NT) a.iters[r] = it[r];
+  // the gradient field of each final potential (in the start buffer after an
+  // even number of V-cycles, in the other one after an odd number)
+  each_block(a.grad, a.grad_t, (const int*)nullptr, s_off, [&](const GradDesc& e, const BI& bi) {
+    const bool odd = (it[e.r] & 1) != 0;
+    d_grad(bi, odd ? e.ph_alt : e.ph, odd ? e.pl_alt : e.pl, e.n, e.lo, e.s, e.periodic, e.G);
+  });
+}
+
+int solve_smem() { return (int)sizeof(float) * cc_layout(cmg_top_side(1), 1).floats; }
+
+// blocks per SM the kernel is compiled for: 2 (no register spill) by
+// default, 4 with PM_SOLVE_MINB=4
+int solve_minb() {
+  const char* v = getenv("PM_SOLVE_MINB");
+  return v && atoi(v) == 4 ? 4 : 2;
+}
+
+template <int MINB>
+int solve_grid_t() {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaFuncSetAttribute(kb_solve<MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           solve_smem()) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kb_solve<MINB>, SOLVE_NT,
+                                                    solve_smem()) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per * sms;
+}
+
+}  // namespace
+
+int solve_grid_b() {
+  static int grid = -1;
+  if (grid < 0) grid = solve_minb() == 4 ? solve_grid_t<4>() : solve_grid_t<2>();
+  return grid;
+}
+
+cudaError_t launch_solve_b(cudaStream_t st, const SolveArgs& a) {
+  const int grid = solve_grid_b();
+  if (grid <= 0) return cudaErrorLaunchOutOfResources;
+  SolveArgs arg = a;
+  void* params[] = {(void*)&arg};
+  const void* fn = solve_minb() == 4 ? (const void*)kb_solve<4> : (const void*)kb_solve<2>;
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(32, 8), params,
+                                              (size_t)solve_smem(), st);
+  note_launch();
+  return e;
+}
 
 }  // namespace pm

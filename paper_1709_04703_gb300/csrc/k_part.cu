@@ -3,6 +3,7 @@
 // uses the deposit's CIC weights), and the order-preserving compaction that
 // drops particles leaving the lightcone (Sec. 2.4: active particles are
 // recomputed at the end of every step; Table 2, last row).
+#include "mg_arith.cuh"
 #include "pm_kernels.cuh"
 
 namespace pm {
@@ -23,9 +24,6 @@ constexpr int KCHUNK = PART_CHUNK;  // KT threads x KITEMS particles per block
 // points, hi and lo: 64 loads).  Both forms apply the same operations in the
 // same order, so they give the same bits.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float gdiff(float hp, float hm, float lp, float lm) {
-  return __fadd_rn(__fsub_rn(hp, hm), __fsub_rn(lp, lm));
-}
 // F += wa wb (w0 g0 + w1 g1)
 __device__ __forceinline__ float cic_acc(float F, float wa, float wb, float w0, float g0,
                                          float w1, float g1) {
@@ -245,21 +243,7 @@ __global__ void __launch_bounds__(256) k_grad(const float* __restrict__ ph,
                                               int s, int periodic, float4* __restrict__ G) {
   pdl_wait();
   pdl_release();
-  const int P = n + 2;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
-  if (i >= s || j >= s) return;
-  const int X = lo + i, Y = lo + j, Z = lo + k;
-  auto w = [&](int a) { return periodic ? (a < 0 ? a + n : (a >= n ? a - n : a)) : a; };
-  const long long c = ((long long)(Z + 1) * P + (Y + 1)) * P + (X + 1);
-  const long long xm = ((long long)(Z + 1) * P + (Y + 1)) * P + (w(X - 1) + 1);
-  const long long xp = ((long long)(Z + 1) * P + (Y + 1)) * P + (w(X + 1) + 1);
-  const long long ym = ((long long)(Z + 1) * P + (w(Y - 1) + 1)) * P + (X + 1);
-  const long long yp = ((long long)(Z + 1) * P + (w(Y + 1) + 1)) * P + (X + 1);
-  const long long zm = ((long long)(w(Z - 1) + 1) * P + (Y + 1)) * P + (X + 1);
-  const long long zp = ((long long)(w(Z + 1) + 1) * P + (Y + 1)) * P + (X + 1);
-  G[c] = make_float4(gdiff(ph[xp], ph[xm], pl[xp], pl[xm]), gdiff(ph[yp], ph[ym], pl[yp], pl[ym]),
-                     gdiff(ph[zp], ph[zm], pl[zp], pl[zm]), 0.0f);
+  d_grad(bi_native(), ph, pl, n, lo, s, periodic, G);
 }
 
 // ---------------------------------------------------------------------------
@@ -671,12 +655,19 @@ void launch_record(cudaStream_t st, const float4* pos, float4* mom, long long N,
 // ---------------------------------------------------------------------------
 // Batched forms.
 // ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) kb_grad(const GradDesc* d, const BTable* t) {
+  int q;
+  BI bi;
+  if (!batch_map(d, t, (const int*)nullptr, q, bi)) return;
+  const GradDesc& e = d[q];
+  d_grad(bi, e.ph, e.pl, e.n, e.lo, e.s, e.periodic, e.G);
+}
 __global__ void __launch_bounds__(KT) kb_gather(const GatherDesc* d, const BTable* t) {
   int q;
   BI bi;
   if (!batch_map(d, t, (const int*)nullptr, q, bi)) return;
   const GatherDesc& e = d[q];
-  d_gather_kick_drift<false>(bi, e.pos, e.mom, e.N, e.ph, e.pl, nullptr, e.n, e.lo, e.s,
+  d_gather_kick_drift<true>(bi, e.pos, e.mom, e.N, nullptr, nullptr, e.G, e.n, e.lo, e.s,
                              e.periodic, e.kick, e.c2, e.do_flag, e.klo, e.khi,
                              KeepBall{0, 0.0, 0.0}, e.flags,
                              e.block_keep, e.forces, e.escaped);
@@ -697,6 +688,11 @@ __global__ void __launch_bounds__(KT) kb_scatter(const ScatterDesc* d, const BTa
             e.lc_mom, e.lc_base, e.a_cross);
 }
 
+void launch_grad_b(cudaStream_t st, int grid, const GradDesc* d, const BTable* t) {
+  if (grid <= 0) return;
+  kb_grad<<<grid, dim3(32, 8), 0, st>>>(d, t);
+  note_launch();
+}
 void launch_gather_b(cudaStream_t st, int grid, const GatherDesc* d, const BTable* t) {
   if (grid <= 0) return;
   kb_gather<<<grid, KT, 0, st>>>(d, t);

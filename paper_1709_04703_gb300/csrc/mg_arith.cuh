@@ -75,4 +75,32 @@ __device__ __forceinline__ float prolong_mix(float q000, float q100, float q010,
   return lerp34(lerp34(a0, a1), lerp34(a2, a3));
 }
 
+// Centred difference of the double-float potential (hi + lo pairs) between
+// mesh points p and m: (hp - hm) + (lp - lm), as the gather's force uses it.
+__device__ __forceinline__ float gdiff(float hp, float hm, float lp, float lm) {
+  return __fadd_rn(__fsub_rn(hp, hm), __fsub_rn(lp, lm));
+}
+
+// The gradient field of the potential at cell (i, j, k) of the active cube
+// (lo, side s) on the padded (n + 2)^3 mesh: G = the centred differences
+// along x, y, z (wrapped when periodic), one float4 per cell.
+__device__ __forceinline__ void d_grad(const BI& bi, const float* ph, const float* pl, int n,
+                                       int lo, int s, int periodic, float4* G) {
+  const int P = n + 2;
+  const int i = bi.x * blockDim.x + threadIdx.x, j = bi.y * blockDim.y + threadIdx.y;
+  const int k = bi.z;
+  if (i >= s || j >= s) return;
+  const int X = lo + i, Y = lo + j, Z = lo + k;
+  auto w = [&](int a) { return periodic ? (a < 0 ? a + n : (a >= n ? a - n : a)) : a; };
+  const long long c = ((long long)(Z + 1) * P + (Y + 1)) * P + (X + 1);
+  const long long xm = ((long long)(Z + 1) * P + (Y + 1)) * P + (w(X - 1) + 1);
+  const long long xp = ((long long)(Z + 1) * P + (Y + 1)) * P + (w(X + 1) + 1);
+  const long long ym = ((long long)(Z + 1) * P + (w(Y - 1) + 1)) * P + (X + 1);
+  const long long yp = ((long long)(Z + 1) * P + (w(Y + 1) + 1)) * P + (X + 1);
+  const long long zm = ((long long)(w(Z - 1) + 1) * P + (Y + 1)) * P + (X + 1);
+  const long long zp = ((long long)(w(Z + 1) + 1) * P + (Y + 1)) * P + (X + 1);
+  G[c] = make_float4(gdiff(ph[xp], ph[xm], pl[xp], pl[xm]), gdiff(ph[yp], ph[ym], pl[yp], pl[ym]),
+                     gdiff(ph[zp], ph[zm], pl[zp], pl[zm]), 0.0f);
+}
+
 }  // namespace pm

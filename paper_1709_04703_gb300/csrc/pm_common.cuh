@@ -197,21 +197,30 @@ struct BTable {
   int off[MAX_MEMBERS + 1];    // cumulative block counts
 };
 
+// The block of a batched launch -> member q of the table and its block
+// coordinates (false: past the table's blocks, or an inactive realisation).
+// The table's offsets are staged in shared memory by the whole block (one
+// coalesced load) and searched there; every thread of the block must call.
 template <class D>
 __device__ __forceinline__ bool batch_map(const D* d, const BTable* t, const int* active, int& q,
                                           BI& bi) {
-  const int b = (int)blockIdx.x;
+  __shared__ int s_off[MAX_MEMBERS + 1];
+  const int tid = (int)(threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z));
+  const int nth = (int)(blockDim.x * blockDim.y * blockDim.z);
   const int m = t->m;
-  if (m <= 0 || b >= t->off[m]) return false;
+  for (int i = tid; i <= m; i += nth) s_off[i] = t->off[i];
+  __syncthreads();
+  const int b = (int)blockIdx.x;
+  if (m <= 0 || b >= s_off[m]) return false;
   int lo = 0, hi = m - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
-    if (t->off[mid] <= b) lo = mid; else hi = mid - 1;
+    if (s_off[mid] <= b) lo = mid; else hi = mid - 1;
   }
   q = lo;
   const D& e = d[lo];
   if (active && !active[e.r]) return false;
-  const int lb = b - t->off[lo];
+  const int lb = b - s_off[lo];
   bi = BI{lb % e.gx, (lb / e.gx) % e.gy, lb / (e.gx * e.gy), e.gx, e.gy, e.gz};
   return true;
 }

@@ -278,10 +278,19 @@ struct BoundaryDesc {
   int want_lo;
   int r, gx, gy, gz;
 };
+// the gradient field of a realisation's potential (ph, pl: the padded mesh;
+// the persistent solve takes (ph_alt, pl_alt) instead when the V-cycles it
+// ran are odd in number)
+struct GradDesc {
+  const float *ph, *pl, *ph_alt, *pl_alt;
+  int n, lo, s, periodic;
+  float4* G;
+  int r, gx, gy, gz;
+};
 struct GatherDesc {
   float4 *pos, *mom;
   long long N;
-  const float *ph, *pl;
+  const float4* G;  // the gradient field, (n + 2)^3
   int n, lo, s, periodic;
   float kick, c2;
   int do_flag;
@@ -323,12 +332,55 @@ void launch_prolong_b(cudaStream_t st, int grid, const ProlongDesc* d, const BTa
 // memory for tops up to max_top
 void launch_cmg_b(cudaStream_t st, int n_desc, int max_top, const CmgDesc* d,
                   const int* active);
+// ---------------------------------------------------------------------------
+// Persistent batched solve: one cooperative launch runs defect, convergence
+// test and V-cycle of every realisation until all have converged (or reached
+// their V-cycle limit); phases are separated by a grid-wide barrier whose
+// waits end after a time limit.
+// ---------------------------------------------------------------------------
+// barrier state (zeroed before a launch): arrivals, generation, and the error
+// (1 = a wait ran out; every later wait then ends at once) with the phase it
+// ran out in
+struct GridBar {
+  unsigned count, gen;
+  int err, where;
+};
+enum { SLOT_RBGS = 0, SLOT_RESTRICT = 1, SLOT_PROLONG = 2, SLOT_CMG = 3 };
+struct SolveSlot {
+  int kind;          // SLOT_*
+  int n;             // SLOT_CMG: descriptors
+  const void* d;     // RbgsDesc / RestrictDesc / ProlongDesc / CmgDesc array
+  const BTable* t;   // block table (unused for SLOT_CMG)
+};
+struct SolveArgs {
+  const GradDesc* grad;   // per realisation: the gradient field of the final potential,
+  const BTable* grad_t;   // written once every realisation has converged
+  const DefectDesc* def;  // per realisation: the buffer it starts in (ph, pl), the other
+  const BTable* def_t;    // one (qh, ql); defect after V-cycle it applies e into
+  const SolveSlot* slots; // buffer it & 1 (relative to the start) from the other
+  int n_slots;            // the V-cycle, in launch order
+  int R;
+  const double* scal;     // 16 per realisation: [0] ||f||^2, [11] ||r||^2 (written here)
+  const double* rtol;     // R each
+  const int* maxv;
+  int* iters;             // out: V-cycles run
+  int* failed;            // out: 1 where max_vcycles was reached first
+  double* rel;            // out: the last relative residual
+  GridBar* bar;
+  unsigned long long limit_ns;  // longest wait at one barrier
+  int extra;              // arrivals a barrier waits for beyond the grid (0; > 0 only to
+                          // test the time limit: no barrier then completes)
+};
+// blocks of one persistent solve launch (all co-resident), and its launch
+int solve_grid_b();
+cudaError_t launch_solve_b(cudaStream_t st, const SolveArgs& a);
 void launch_defect_b(cudaStream_t st, int grid, const DefectDesc* d, const BTable* t,
                      const int* active);
 void launch_predict_b(cudaStream_t st, int grid, const PredictDesc* d, const BTable* t);
 void launch_deposit_b(cudaStream_t st, int grid, const DepositDesc* d, const BTable* t);
 void launch_source_b(cudaStream_t st, int grid, const SourceDesc* d, const BTable* t);
 void launch_boundary_b(cudaStream_t st, int grid, const BoundaryDesc* d, const BTable* t);
+void launch_grad_b(cudaStream_t st, int grid, const GradDesc* d, const BTable* t);
 void launch_gather_b(cudaStream_t st, int grid, const GatherDesc* d, const BTable* t);
 void launch_scan_b(cudaStream_t st, int grid, const ScanDesc* d, const BTable* t);
 void launch_scatter_b(cudaStream_t st, int grid, const ScatterDesc* d, const BTable* t);

@@ -128,6 +128,14 @@ class Batch:
     def step(self, k=1):
         self._check(self._lib.pm_batch_step(self._b, int(k)))
 
+    def set_solve(self, persistent=True, wait_seconds=2.0, extra_arrivals=0):
+        """persistent: one cooperative launch per solve, decided on the
+        device (else a V-cycle graph with host decisions); wait_seconds: the
+        longest wait at one of its grid barriers; extra_arrivals > 0 only to
+        test that limit (every barrier then runs out: PM_ETIMEOUT)."""
+        self._check(self._lib.pm_batch_set_solve(self._b, int(bool(persistent)),
+                                                 float(wait_seconds), int(extra_arrivals)))
+
     def stats(self, r):
         s = L.PmStats()
         self._check(self._lib.pm_batch_stats(self._b, int(r), C.byref(s)))

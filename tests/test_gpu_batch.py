@@ -181,3 +181,62 @@ def test_batch_against_oracle():
     batch.close()
     assert phases == {True, False}
     assert shrunk >= 3
+
+
+def test_persistent_solve_matches_graph_solve():
+    """The persistent solve (one cooperative launch per solve, convergence
+    decided on the device) and the V-cycle graph with the host's decisions
+    give the same bits and V-cycle counts, in both phases; the persistent
+    step makes at most 8 launches (deposit, source, boundary, predict,
+    solve, gather, scan, scatter)."""
+    from paper_1709_04703_gb300 import _lib as L
+    from paper_1709_04703_gb300.sim import Batch
+    a0, a1, steps, rtol = 0.02, 1.0, 6, 1e-7
+    reals = [_realisation(32, 8000.0, 120, a0), _realisation(48, 1000.0, 121, a0),
+             _realisation(64, 12000.0, 122, a0)]
+    lib = L.load()
+    per = Batch(reals, a0, a1, steps, rtol=rtol)
+    counts, phases = [], set()
+    for _ in range(steps):
+        l0 = lib.pm_launch_count()
+        per.step(1)
+        counts.append(lib.pm_launch_count() - l0)
+        phases |= {per.stats(r)["periodic"] for r in range(len(reals))}
+    gra = Batch(reals, a0, a1, steps, rtol=rtol)
+    gra.set_solve(persistent=False)
+    g0 = lib.pm_launch_count()
+    gra.step(steps)
+    g_launches = lib.pm_launch_count() - g0
+    for r in range(len(reals)):
+        ref = gra.particles(r), gra.lightcone(r), gra.stats(r)
+        _compare(per, r, ref)
+        assert per.stats(r)["vcycles_total"] == ref[2]["vcycles_total"]
+    assert phases == {0, 1}
+    assert max(counts) <= 8, counts
+    assert g_launches > sum(counts)
+    per.close()
+    gra.close()
+
+
+def test_persistent_barrier_wait_runs_out():
+    """A grid barrier that waits for an arrival that never comes gives up
+    after its limit: the step returns PM_ETIMEOUT after about that long, and
+    the GPU stays usable (a new batch then steps as a separate context)."""
+    import time
+    from paper_1709_04703_gb300 import _lib as L
+    from paper_1709_04703_gb300.sim import Batch
+    a0, a1, steps, rtol = 0.02, 1.0, 6, 1e-7
+    reals = [_realisation(16, 4000.0, 100, a0), _realisation(32, 8000.0, 101, a0)]
+    b = Batch(reals, a0, a1, steps, rtol=rtol)
+    b.set_solve(persistent=True, wait_seconds=0.25, extra_arrivals=1)
+    t0 = time.time()
+    with pytest.raises(L.PmError) as ei:
+        b.step(1)
+    dt = time.time() - t0
+    assert ei.value.code == L.PM_ETIMEOUT, ei.value
+    assert 0.2 <= dt < 20.0, dt
+    b.close()
+    b = Batch(reals, a0, a1, steps, rtol=rtol)
+    b.step(2)
+    _compare(b, 1, _single(reals[1], a0, a1, steps, rtol, 2))
+    b.close()
