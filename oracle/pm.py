@@ -31,7 +31,14 @@ library, which implements them independently):
   R = chi(a)/cell + buffer (1 cell).  Keep iff max_d |x_d - c| <= R.  The
   sphere of Table 1 is the variant domain="sphere": keep iff |x - c| <= R,
   solved on the same cube, its mean-density term the CIC image of the ball
-  (background_ball).
+  (background_ball).  domain="ball" keeps and weighs as "sphere" but solves
+  only on the ball's cells: the unknowns are the cells whose centre lies
+  within R + 2 of c (the CIC support of every kept particle and of the ball
+  image lies inside), every other cell of the cube and its ghost layer
+  takes the multipole value (the ones next to the mask are its Dirichlet
+  ghosts; the rest give the force of particles beyond the mask in the step
+  before they leave), and the cube reaches 3 cells beyond R so that the
+  mask lies in the cube's interior.
 * Boundary conditions: periodic until the lightcone reaches the box border
   (Sec. 3), read as R > n/2 - 1; afterwards open (Table 1) with Dirichlet
   values from a monopole + dipole + quadrupole expansion of the source about
@@ -225,7 +232,7 @@ def delta_cube(rho, n, lo, s, nbar, R, periodic, assign="cic", domain="cube"):
     """Density contrast on the active cube [z,y,x] (s^3, float64)."""
     sub = rho[lo:lo + s, lo:lo + s, lo:lo + s].astype(np.float64)
     d = sub / (MASS_UNIT * nbar)
-    if domain == "sphere" and not periodic:
+    if domain in ("sphere", "ball") and not periodic:
         return d - background_ball(R, n, lo, s)
     w = background_weights(R, n, lo, s, periodic, assign)
     return d - w[:, None, None] * w[None, :, None] * w[None, None, :]
@@ -261,8 +268,9 @@ def multipole_potential(points, S, q0, dip, quad):
     return -(S / (4 * math.pi)) * (q0 / r + dr / (r * r2) + 0.5 * qr / (r2 * r2 * r))
 
 
-def open_ghost_potential(f_cube, S, lo, n):
-    """Padded (s+2)^3 array whose ghost layer holds the Dirichlet values."""
+def open_ghost_potential(f_cube, S, lo, n, full=False):
+    """Padded (s+2)^3 array whose ghost layer holds the Dirichlet values
+    (full: the multipole potential at every cell of the padded cube)."""
     s = f_cube.shape[0]
     delta = f_cube / S
     q0, dip, quad = multipoles(delta, lo, n)
@@ -270,7 +278,8 @@ def open_ghost_potential(f_cube, S, lo, n):
     coords = np.arange(lo - 1, lo + s + 1) + 0.5 - n / 2
     Z, Y, X = np.meshgrid(coords, coords, coords, indexing="ij")
     ghost = np.ones((s + 2,) * 3, dtype=bool)
-    ghost[1:-1, 1:-1, 1:-1] = False
+    if not full:
+        ghost[1:-1, 1:-1, 1:-1] = False
     pts = np.stack([X[ghost], Y[ghost], Z[ghost]], axis=1)
     g[ghost] = multipole_potential(pts, S, q0, dip, quad)
     return g
@@ -327,6 +336,77 @@ def solve_open(f, ghost):
     return out
 
 
+BALL_MARGIN = 2.0   # mask radius R + 2: beyond the CIC reach (sqrt 3) of every kept particle
+BALL_REACH = 3      # the ball's cube reaches ceil(R) + 3 cells
+DIRECT_MAX = 20000  # unknowns up to which solve_ball factorises the system
+
+
+def ball_mask(R, n, lo, s):
+    """The unknowns of the ball solve: cells of [lo, lo+s)^3 ([z,y,x] bool)
+    whose centre lies within R + BALL_MARGIN of c = n/2 (FP64; the squared
+    distances of cell centres are exact)."""
+    a = np.arange(lo, lo + s) + 0.5 - n / 2
+    d2 = (a[:, None, None] ** 2 + a[None, :, None] ** 2) + a[None, None, :] ** 2
+    return d2 <= (R + BALL_MARGIN) ** 2
+
+
+def ball_ghosts(mask):
+    """Padded (s+2)^3 bool array of the ghost cells: outside the mask, next
+    (along an axis) to a cell of it."""
+    s = mask.shape[0]
+    pm = np.zeros((s + 2,) * 3, dtype=bool)
+    pm[1:-1, 1:-1, 1:-1] = mask
+    near = np.zeros_like(pm)
+    for ax in range(3):
+        for sh in (1, -1):
+            near |= np.roll(pm, sh, axis=ax)   # the padding keeps rolls from wrapping mask cells
+    return near & ~pm
+
+
+def solve_ball(f, ghost, mask):
+    """sum_nb Phi - 6 Phi = f on the cells of `mask` (s^3), with Dirichlet
+    values at the ghost cells (ghost: padded (s+2)^3, read where
+    ball_ghosts is true).  The masked 7-point system is solved directly
+    (sparse LU) up to DIRECT_MAX unknowns, by conjugate gradients on its
+    negative (symmetric positive definite) to a relative residual of 1e-13
+    above.  Returns the padded potential: the solution on the mask, `ghost`
+    everywhere else (outside the mask the potential is the multipole field,
+    felt by particles beyond the mask before they leave)."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.linalg import cg, spsolve
+    s = f.shape[0]
+    gmask = ball_ghosts(mask)
+    pm = np.zeros((s + 2,) * 3, dtype=bool)
+    pm[1:-1, 1:-1, 1:-1] = mask
+    cells = np.argwhere(pm)                 # padded coordinates of the unknowns
+    idx = -np.ones((s + 2,) * 3, dtype=np.int64)
+    idx[tuple(cells.T)] = np.arange(len(cells))
+    rows, cols, vals = [np.arange(len(cells))], [np.arange(len(cells))], [np.full(len(cells), -6.0)]
+    rhs = f[mask].astype(np.float64).copy()   # argwhere and boolean indexing share C order
+    for ax in range(3):
+        for sh in (1, -1):
+            nb = cells.copy()
+            nb[:, ax] += sh
+            t = tuple(nb.T)
+            inside = pm[t]
+            rows.append(np.nonzero(inside)[0])
+            cols.append(idx[t][inside])
+            vals.append(np.ones(int(inside.sum())))
+            g = gmask[t]
+            rhs[g] -= ghost[t][g]
+    A = coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                   shape=(len(cells), len(cells))).tocsc()
+    if len(cells) <= DIRECT_MAX:
+        u = spsolve(A, rhs)
+    else:
+        u, info = cg(-A, -rhs, rtol=1e-13, atol=0.0, maxiter=100000)
+        if info != 0 or np.linalg.norm(A @ u - rhs) > 1e-12 * max(np.linalg.norm(rhs), 1e-300):
+            raise RuntimeError("solve_ball: conjugate gradients did not converge")
+    out = np.array(ghost, dtype=np.float64, copy=True)
+    out[tuple(cells.T)] = u
+    return out
+
+
 def apply_laplacian_padded(phi_pad):
     """7-point operator on the interior of a padded array (h = 1)."""
     p = phi_pad
@@ -349,6 +429,9 @@ def solve_step_potential(rho, n, lo, s, periodic, nbar, R, a_half, om, assign="c
     f = S * delta_cube(rho, n, lo, s, nbar, R, periodic, assign, domain)
     if periodic:
         return f, solve_periodic(f)
+    if domain == "ball":
+        return f, solve_ball(f, open_ghost_potential(f, S, lo, n, full=True),
+                             ball_mask(R, n, lo, s))
     return f, solve_open(f, open_ghost_potential(f, S, lo, n))
 
 
@@ -498,7 +581,7 @@ def keep_mask(pos, R, n, domain="cube"):
     ((x - c)^2 + (y - c)^2) + (z - c)^2 <= R^2 (sphere), in FP64 on the
     position (Sec. 2.4 / Table 1)."""
     d = np.asarray(pos, dtype=np.float64) - n / 2
-    if domain == "sphere":
+    if domain in ("sphere", "ball"):
         return (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2] <= R * R
     return np.abs(d).max(axis=1) <= R
 
@@ -523,12 +606,14 @@ def step(pos, mom, k, sched, n, om, nbar, want=False, drift32=False, fixed_box=F
     positions; everything after it stays FP64.  fixed_box=True solves on the
     whole periodic box at every step (the run without shrinking).  assign:
     "cic" or "tsc" (density assignment and force interpolation alike).
-    domain: "cube" or "sphere" keep region (its mean-density term)."""
+    domain: "cube" or "sphere" keep region (its mean-density term), or
+    "ball": the sphere solved on the ball's cells only (solve_ball)."""
     a0, a1 = sched["a"][k], sched["a"][k + 1]
     dtau, ah = sched["dtau"][k], sched["a_half"][k]
     R0 = sched["R"][k]
     tsc = assign == "tsc"
-    lo, s, periodic = (0, n, True) if fixed_box else active_cube(R0, n, 2 if tsc else 1)
+    reach = BALL_REACH if domain == "ball" else (2 if tsc else 1)
+    lo, s, periodic = (0, n, True) if fixed_box else active_cube(R0, n, reach)
     if drift32:
         pos = drift_fp32(np.asarray(pos, np.float32), np.asarray(mom, np.float32),
                          dtau / (2 * a0), n, periodic).astype(np.float64)
