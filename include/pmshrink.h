@@ -57,7 +57,7 @@ enum { PM_GRAVITY_POISSON = 0, PM_GRAVITY_DIFFUSION = 1,
 enum { PM_BC_PAPER = 0, PM_BC_OPEN = 1, PM_BC_PERIODIC = 2 };  /* pm_config.bc */
 enum { PM_SHRINK_OFF = 0, PM_SHRINK_ON = 1, PM_SHRINK_RECORD = 2 };  /* pm_config.shrink */
 enum { PM_ASSIGN_CIC = 0, PM_ASSIGN_TSC = 1 };                  /* pm_config.assignment */
-enum { PM_DOMAIN_CUBE = 0, PM_DOMAIN_SPHERE = 1 };                  /* pm_config.domain */
+enum { PM_DOMAIN_CUBE = 0, PM_DOMAIN_SPHERE = 1, PM_DOMAIN_BALL = 2 };  /* pm_config.domain */
 
 typedef struct {
   int32_t n_mesh;        /* cells per side, of the form 2^j or 3*2^j, 4..1024 */
@@ -124,7 +124,18 @@ typedef struct {
                             stays on the cube; with the sphere the mean-density
                             term is the CIC image of the ball (exact chord
                             integral, 16-point Gauss-Legendre over the tents);
-                            the sphere needs PM_ASSIGN_CIC */
+                            the sphere needs PM_ASSIGN_CIC.  PM_DOMAIN_BALL:
+                            the sphere's keep rule and mean-density term; in
+                            the open phase the solve runs only on the cells
+                            whose centre lies within R + 2 of c (the cube
+                            reaches ceil(R) + 3).  Every
+                            smoothing, restriction, prolongation and defect
+                            pass skips the other cells, which take the
+                            multipole values (Dirichlet ghosts next to the
+                            ball); coarse levels keep the cells whose centre
+                            lies in the ball, with the finest level's
+                            boundary.  Needs PM_ASSIGN_CIC, PM_MIXED, Poisson
+                            gravity and the warm or zero start */
   int32_t sort_every;    /* 0: the particle arrays keep their order (the
                             initial order, compacted stably by the shrink);
                             k > 0: at the start of every k-th step (step
@@ -386,12 +397,13 @@ pm_status pm_profile_read(pm_ctx* ctx, int32_t cls, double* ms, int64_t* groups,
  * mesh size, particles and lightcone schedule; Sec. 2.4 applied to each)
  * advance together.  Every phase of pm_step runs as one kernel launch over
  * all realisations (a device table maps each block to a realisation).  The
- * solve (Sec. 2.1: defect, convergence test, V-cycle, repeated) is one
- * persistent cooperative launch: its passes are separated by a grid-wide
- * barrier, every block takes the convergence decisions from the residual
- * norms on the device, a realisation that has converged is masked out of
- * further passes, and the host reads nothing until the step ends.  Results
- * equal those of separate contexts bit for bit.
+ * solve (Sec. 2.1: defect, convergence test, V-cycle, repeated) is decided
+ * on the device: the convergence test runs in a kernel after each batched
+ * defect, a realisation that has converged is masked out of further passes,
+ * and the host reads nothing until the step ends.  By default the solve is
+ * one CUDA graph whose V-cycle loop is a conditional while node; a
+ * persistent cooperative kernel is the other form (pm_batch_set_solve).
+ * Results equal those of separate contexts bit for bit.
  * Requirements: 1 <= n_real <= 64, precision PM_MIXED, all realisations on
  * the same number of steps and a_init/a_final (one schedule of a, each with
  * its own chi(a)/cell), stream not NULL.
@@ -412,10 +424,10 @@ pm_status pm_batch_get_lightcone(pm_batch* b, int32_t r, float* pos4, float* mom
  * step, as pm_get_forces (needs cfgs[r].store_forces = 1). */
 pm_status pm_batch_get_forces(pm_batch* b, int32_t r, float* f4, int32_t host_mem,
                               int64_t* n_out);
-/* How a batch solves.  persistent = 1 (the default where the GPU holds the
- * kernel's grid): the persistent launch above.  persistent = 0: one CUDA
- * graph holds the V-cycle of every realisation and the host reads the
- * residual norms after each defect to decide (the two give the same bits).
+/* How a batch solves.  persistent = 0 (the default): the graph above.
+ * persistent = 1: one persistent cooperative launch per solve, its passes
+ * separated by a grid-wide barrier, every block taking the same convergence
+ * decisions from the residual norms (the two give the same bits).
  * wait_seconds (> 0, finite; default 2): the longest wait at one grid
  * barrier; when it runs out the kernel sets an error word, every block
  * leaves, and pm_batch_step returns PM_ETIMEOUT (the batch's state is then

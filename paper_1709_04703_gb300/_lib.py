@@ -17,7 +17,7 @@ PM_GRAVITY_POISSON, PM_GRAVITY_DIFFUSION, PM_GRAVITY_DIFFUSION_ADE = 0, 1, 2
 PM_BC_PAPER, PM_BC_OPEN, PM_BC_PERIODIC = 0, 1, 2
 PM_SHRINK_OFF, PM_SHRINK_ON, PM_SHRINK_RECORD = 0, 1, 2
 PM_ASSIGN_CIC, PM_ASSIGN_TSC = 0, 1
-PM_DOMAIN_CUBE, PM_DOMAIN_SPHERE = 0, 1
+PM_DOMAIN_CUBE, PM_DOMAIN_SPHERE, PM_DOMAIN_BALL = 0, 1, 2
 PM_SHRINK_STATIC_MAX_PARTICLES = 1 << 22
 
 STATUS_NAMES = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ECUDA",

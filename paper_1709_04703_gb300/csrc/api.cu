@@ -190,6 +190,10 @@ struct pm_ctx {
 
   int lo = 0, s = 0, periodic = 1;
   bool cube_valid = false;
+  // PM_DOMAIN_BALL in the open phase: the mask of the current cube (Grid's
+  // mask fields; mbase = 0: no mask)
+  int mbase = 0, mr = 0;
+  double ball_rm = 0.0;  // its radius R + 2 (cells)
 
   // CUDA graph of one V-cycle for the current cube and level-0 grids (needs a
   // non-default stream to capture on)
@@ -199,7 +203,7 @@ struct pm_ctx {
   // (one graph per level-0 start: from zero, and from the iterate)
   struct VGraph {
     bool valid = false;
-    int lo = 0, s = 0, per = 0, prof = 0, zero0 = 0;
+    int lo = 0, s = 0, per = 0, prof = 0, zero0 = 0, mr = 0;
     float *u0 = nullptr, *b0 = nullptr;
     cudaGraphExec_t exec = nullptr;
     long long kernels = 0;
@@ -265,7 +269,7 @@ pm_status fail(pm_ctx* c, pm_status code, const std::string& msg) {
   } while (0)
 
 Grid full_view(const pm_ctx* c, float* base, int lo, int s) {
-  Grid g;
+  Grid g{};
   g.sy = c->P;
   g.sz = c->P * c->P;
   g.s = s;
@@ -274,11 +278,23 @@ Grid full_view(const pm_ctx* c, float* base, int lo, int s) {
 }
 
 Grid compact_view(float* base, int s) {
-  Grid g;
+  Grid g{};
   g.sy = s + 2;
   g.sz = (s + 2) * (s + 2);
   g.s = s;
   g.base = base + 1 + g.sy + g.sz;
+  return g;
+}
+
+// g with the ball solve's mask of level l of the current cube (if any)
+Grid masked(const pm_ctx* c, Grid g, int l) {
+  if (c->mbase) {
+    g.mbase = c->mbase;
+    g.mstep = 2 << l;
+    g.mr = c->mr;
+    g.mrm2 = (float)(c->ball_rm * c->ball_rm);
+    g.mrb2 = (float)((c->ball_rm + 0.5) * (c->ball_rm + 0.5));
+  }
   return g;
 }
 
@@ -290,7 +306,7 @@ bool is_open(const pm_ctx* c, double R) {
 
 // Keep test of radius R (the cube's float bounds are passed separately).
 KeepBall keep_ball(const pm_ctx* c, double R) {
-  return KeepBall{c->cfg.domain == PM_DOMAIN_SPHERE ? 1 : 0, 0.5 * c->n, R * R};
+  return KeepBall{c->cfg.domain != PM_DOMAIN_CUBE ? 1 : 0, 0.5 * c->n, R * R};
 }
 
 // m-point Gauss-Legendre rule on [0, 1] (Newton on the Legendre recurrence)
@@ -333,8 +349,11 @@ void geometry(const pm_ctx* c, double R, int* lo, int* s, int* periodic) {
   if (!is_open(c, R)) { *lo = 0; *s = n; *periodic = 1; return; }
   *periodic = 0;
   if (R > 0.5 * n - 1.0) { *lo = 0; *s = n; return; }
-  // the assignment reaches one cell (CIC) or two (TSC) beyond the keep cube
-  int m = (int)std::ceil(R) + (c->cfg.assignment == PM_ASSIGN_TSC ? 2 : 1);
+  // the assignment reaches one cell (CIC) or two (TSC) beyond the keep cube;
+  // the ball solve's mask two beyond the keep radius and its ghosts one more
+  const int reach = c->cfg.domain == PM_DOMAIN_BALL ? 3
+                    : c->cfg.assignment == PM_ASSIGN_TSC ? 2 : 1;
+  int m = (int)std::ceil(R) + reach;
   int side = std::min(mg_round_up(2 * m), n);
   *s = side;
   *lo = n / 2 - side / 2;
@@ -376,6 +395,23 @@ pm_status set_cube(pm_ctx* ctx, int lo, int s, int periodic, double R) {
   ctx->s = s;
   ctx->periodic = periodic;
   ctx->cube_valid = true;
+  // the ball solve's mask: cell centres within R + 2 of c; twice a centre's
+  // offset from c along an axis is the odd integer 2 (lo + i) + 1 - n, and
+  // the mask holds the squares' sum up to floor(4 (R + 2)^2)
+  const int mbase0 = ctx->mbase, mr0 = ctx->mr;
+  ctx->mbase = 0;
+  ctx->mr = 0;
+  if (ctx->cfg.domain == PM_DOMAIN_BALL && !periodic && R < (double)ctx->n) {
+    const double rm = R + 2.0;
+    ctx->mbase = 2 * lo + 1 - ctx->n;
+    ctx->mr = (int)std::floor(rm * rm * 4.0);
+    ctx->ball_rm = rm;
+  }
+  // the correction is zero outside the mask (the masked passes never write
+  // there, and the defect adds it everywhere): cleared when the mask moves
+  if (same && ctx->ecorr && (ctx->mbase != mbase0 || ctx->mr != mr0))
+    CK(cudaMemsetAsync(ctx->ecorr, 0, sizeof(float) * (size_t)(s + 2) * (s + 2) * (s + 2),
+                       ctx->st));
   // mean-density term of delta: per axis the image of the keep interval
   // [c - R, c + R] under the assignment kernel (CIC tent or TSC),
   // w_g = T(c + R - x_g) - T(c - R - x_g) at x_g = g + 1/2 with T the
@@ -519,11 +555,13 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
   const int L = (int)ctx->ls.size() - 1;
   Grid U[16], B[16], Upre[16];
   if (L >= 16) return fail(ctx, PM_EINVAL, "too many multigrid levels");
-  U[0] = u0;
-  B[0] = b0;
+  // the ball solve: every level masked, homogeneous coarse ghosts (gam 0)
+  const bool ball = ctx->mbase != 0;
+  U[0] = masked(ctx, u0, 0);
+  B[0] = masked(ctx, b0, 0);  // (the fused smoother reads the mask from b)
   for (int l = 1; l <= L; ++l) {
-    U[l] = compact_view(ctx->lu[l], ctx->ls[l]);
-    B[l] = compact_view(ctx->lb[l], ctx->ls[l]);
+    U[l] = masked(ctx, compact_view(ctx->lu[l], ctx->ls[l]), l);
+    B[l] = masked(ctx, compact_view(ctx->lb[l], ctx->ls[l]), l);
   }
   const double c0 = (double)ctx->s * ctx->s * ctx->s;
   // algorithmic bytes per fine cell: a red-black Gauss-Seidel sweep reads u
@@ -535,16 +573,19 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
   float h2 = 1.0f;
   int ec = -1;
   // open-boundary ghost factor of level l (spacing H = 2^l), see k_mg.cu
-  auto gam = [](int l) { float H = (float)(1 << l); return (H - 1.0f) / (H + 1.0f); };
+  auto gam = [&](int l) {
+    float H = (float)(1 << l);
+    return ball ? 0.0f : (H - 1.0f) / (H + 1.0f);
+  };
   // the levels from the first of side <= cmg_top_side run in one
   // thread-block cluster (k_cmg.cu)
   int Lc = 0;
-  while (Lc < L && ctx->ls[Lc] > cmg_top_side(cmg_cluster())) ++Lc;
+  while (Lc < L && ctx->ls[Lc] > cmg_top_side(ball ? 1 : cmg_cluster())) ++Lc;
   for (int l = 0; l < Lc; ++l) {
     int e = l == 0 ? prof_begin(ctx) : -1;
     // below level 0 the restriction zeroes the coarse iterate
     const bool zs = l == 0 ? zero0 : true;
-    const bool fused = ctx->ls[l] >= FUSED_MIN;
+    const bool fused = ctx->ls[l] >= FUSED_MIN && (!ball || l == 0);
     const float d0 = 6.0f + ctx->sig * h2;  // h2 = 4^l
     Upre[l] = (zs || !fused) ? U[l] : compact_view(ctx->lu[0], ctx->ls[0]);
     if (fused && !zs && !per)  // the scratch grids take u0's Dirichlet ghost values
@@ -575,7 +616,7 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
       prof_end(ctx, PM_PROF_COARSE, ec, (Lc > 0 ? 8.0 / 7.0 * 81.0 * c0 / 8.0 : 0.0));
       e = prof_begin(ctx);
     }
-    const bool fused = ctx->ls[l] >= FUSED_MIN;
+    const bool fused = ctx->ls[l] >= FUSED_MIN && (!ball || l == 0);
     const float d0 = 6.0f + ctx->sig * h2;
     Grid W = compact_view(ctx->lu2[l], ctx->ls[l]);
     if (fused)
@@ -612,7 +653,7 @@ pm_status vcycle_run(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
   auto& g = ctx->vg[zero0 ? 1 : 0];
   if (!(g.valid && g.lo == ctx->lo && g.s == ctx->s && g.per == ctx->periodic &&
         g.u0 == u0.base && g.b0 == b0.base && g.prof == (int)ctx->prof_on &&
-        g.zero0 == (int)zero0)) {
+        g.zero0 == (int)zero0 && g.mr == ctx->mr)) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
     g = pm_ctx::VGraph();
     CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
@@ -644,6 +685,7 @@ pm_status vcycle_run(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
     g.b0 = b0.base;
     g.prof = ctx->prof_on;
     g.zero0 = zero0;
+    g.mr = ctx->mr;  // the ball's mask radius (captured in the kernels' grids)
     g.kernels = nk;
     g.pend = ctx->pend_graph;
   }
@@ -860,7 +902,8 @@ pm_status solve(pm_ctx* ctx) {
   Grid fh = full_view(ctx, ctx->f_hi, lo, s), fl = full_view(ctx, ctx->f_lo, lo, s);
   const bool mixed = ctx->cfg.precision == PM_MIXED;
   Grid e0 = compact_view(mixed ? ctx->ecorr : ctx->lu[0], s), r0 = compact_view(ctx->lb[0], s);
-  auto ph_of = [&](int q) { return full_view(ctx, ctx->phi_h[q], lo, s); };
+  // (the ball solve's defect leaves the cells outside its mask out)
+  auto ph_of = [&](int q) { return masked(ctx, full_view(ctx, ctx->phi_h[q], lo, s), 0); };
   auto pl_of = [&](int q) { return full_view(ctx, ctx->phi_l[q], lo, s); };
   if (ctx->cfg.guess == PM_GUESS_ZERO) {
     launch_fill(ctx->st, ph_of(ctx->cur), 0.0f, false);
@@ -1146,8 +1189,14 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
   if (cfg->shrink < PM_SHRINK_OFF || cfg->shrink > PM_SHRINK_RECORD)
     return fail(nullptr, PM_EINVAL, "pm_init: unknown shrink mode");
   if (cfg->domain != PM_DOMAIN_CUBE &&
-      (cfg->domain != PM_DOMAIN_SPHERE || cfg->assignment != PM_ASSIGN_CIC))
-    return fail(nullptr, PM_EINVAL, "pm_init: domain is the cube, or the sphere with CIC");
+      ((cfg->domain != PM_DOMAIN_SPHERE && cfg->domain != PM_DOMAIN_BALL) ||
+       cfg->assignment != PM_ASSIGN_CIC))
+    return fail(nullptr, PM_EINVAL, "pm_init: domain is the cube, or the sphere or ball with CIC");
+  if (cfg->domain == PM_DOMAIN_BALL &&
+      (cfg->precision != PM_MIXED || cfg->gravity != PM_GRAVITY_POISSON ||
+       cfg->guess == PM_GUESS_LEARNED))
+    return fail(nullptr, PM_EINVAL, "pm_init: the ball solve needs PM_MIXED, Poisson gravity "
+                                    "and the warm or zero start");
   if (cfg->assignment != PM_ASSIGN_CIC &&
       (cfg->assignment != PM_ASSIGN_TSC || cfg->gravity != PM_GRAVITY_POISSON))
     return fail(nullptr, PM_EINVAL, "pm_init: assignment is CIC, or TSC with Poisson gravity");
@@ -1259,7 +1308,7 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
   AL(ctx->d_scal, sizeof(double) * 16);
   AL(ctx->bgm, BGW_OFF + sizeof(df) * (size_t)n);
   ctx->bgw = (df*)((char*)ctx->bgm + BGW_OFF);
-  if (cfg->domain == PM_DOMAIN_SPHERE) {
+  if (cfg->domain != PM_DOMAIN_CUBE) {
     AL(ctx->ballw, sizeof(float) * (size_t)n * n * n);
     ctx->ball_rule = ball_rule();
   }
@@ -1447,7 +1496,7 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
       e = prof_begin(ctx);
       launch_boundary64(ctx->st, full_view64(ctx, ctx->phi64, lo, s), n, lo, ctx->d_scal + 1, S);
       prof_end(ctx, PM_PROF_BOUNDARY, e, 8.0 * 6.0 * (s + 2.0) * (s + 2.0));
-    } else if (!per) {
+    } else if (!per && !ctx->mbase) {
       e = prof_begin(ctx);
       // both buffers carry the ghosts in the mixed form (its defect writes
       // Phi + e to the other buffer)
@@ -1487,6 +1536,19 @@ pm_status pm_step(pm_ctx* ctx, int32_t n_steps) {
         }
         prof_end(ctx, PM_PROF_CORRECT, e, 32.0 * cells);
       }
+    }
+    if (ctx->mbase) {
+      // the ball solve's Dirichlet values, after the prediction (its ghost
+      // cells lie inside the cube, where the prediction extrapolates)
+      e = prof_begin(ctx);
+      launch_ball_ghosts(ctx->st, masked(ctx, full_view(ctx, ctx->phi_h[ctx->cur], lo, s), 0),
+                         full_view(ctx, ctx->phi_l[ctx->cur], lo, s),
+                         full_view(ctx, ctx->phi_h[ctx->cur ^ 1], lo, s),
+                         full_view(ctx, ctx->phi_l[ctx->cur ^ 1], lo, s), n, lo,
+                         ctx->d_scal + 1, S);
+      // 16 B per cell outside the ball's mask (about half the cube)
+      prof_end(ctx, PM_PROF_BOUNDARY, e, 8.0 * (s + 2.0) * (s + 2.0) * (s + 2.0));
+      CKL();
     }
     if (!ade) {
       st = solve(ctx);
@@ -2306,8 +2368,7 @@ struct pm_batch {
   int R = 0;
   cudaStream_t st = nullptr;
   std::vector<pm_ctx*> ctx;
-  int* d_active = nullptr;
-  int* h_active = nullptr;
+  int* d_active = nullptr;  // the graph solve's per-realisation activity
   double* d_scal = nullptr;  // 16 per realisation: [0] ||f||^2, [1..10] moments, [11] ||r||^2
   double* h_scal = nullptr;
   unsigned long long* d_cnt = nullptr;  // 4 per realisation: [0] survivors
@@ -2317,8 +2378,11 @@ struct pm_batch {
   std::vector<BTab> t_vc;  // V-cycle launch slots
   int maxLc = 0;
   bool tables_stale = true;
-  cudaGraphExec_t vgraph = nullptr;
-  long long vgraph_kernels = 0;
+  // the graph solve: init, defect, decision, a conditional while loop over
+  // (V-cycle, defect, decision), the gradient field; one launch per solve
+  cudaGraphExec_t sgraph = nullptr;
+  cudaStream_t st2 = nullptr;  // captures the loop's body
+  long long loop_kernels = 0;  // kernels of one pass of the loop body
   int rb_bx = 32, rb_by = 8;  // block shape of the batched colour pass (autotuned)
   bool rb_tuned = false;
   // the persistent solve: one cooperative launch per solve
@@ -2430,9 +2494,9 @@ void upload_vcycle_tables(pm_batch* B) {
           e.color = k & 1;
           e.periodic = c->periodic;
           e.zero_start = k == 0;  // level 0: e is not cleared; coarser: restriction zeroed it
-          set_dims(e, r, rbgs_grid(c->ls[l], B->rb_bx, B->rb_by));
+          set_dims(e, r, rbgs_grid_b(c->ls[l], B->rb_bx, B->rb_by));
           d.push_back(e);
-          bl.push_back(nblocks(rbgs_grid(c->ls[l], B->rb_bx, B->rb_by)));
+          bl.push_back(nblocks(rbgs_grid_b(c->ls[l], B->rb_bx, B->rb_by)));
         }
         tab_upload(B, B->t_vc[slot_down(l, k)], d, bl);
       } else {
@@ -2448,9 +2512,9 @@ void upload_vcycle_tables(pm_batch* B) {
           e.inv_h2 = 1.0f / (float)(1 << (2 * l));
           e.gam = level_gam(l);
           e.periodic = c->periodic;
-          set_dims(e, r, full_grid(c->ls[l + 1]));
+          set_dims(e, r, full_grid_b(c->ls[l + 1]));
           d.push_back(e);
-          bl.push_back(nblocks(full_grid(c->ls[l + 1])));
+          bl.push_back(nblocks(full_grid_b(c->ls[l + 1])));
         }
         tab_upload(B, B->t_vc[slot_down(l, k)], d, bl);
       }
@@ -2488,9 +2552,9 @@ void upload_vcycle_tables(pm_batch* B) {
           e.u = compact_view(c->lu[l], c->ls[l]);
           e.gam_c = level_gam(l + 1);
           e.periodic = c->periodic;
-          set_dims(e, r, full_grid(c->ls[l]));
+          set_dims(e, r, full_grid_b(c->ls[l]));
           d.push_back(e);
-          bl.push_back(nblocks(full_grid(c->ls[l])));
+          bl.push_back(nblocks(full_grid_b(c->ls[l])));
         }
         tab_upload(B, B->t_vc[slot_up(M, l, k)], d, bl);
       } else {
@@ -2506,9 +2570,9 @@ void upload_vcycle_tables(pm_batch* B) {
           e.color = (k - 1) & 1;
           e.periodic = c->periodic;
           e.zero_start = 0;
-          set_dims(e, r, rbgs_grid(c->ls[l], B->rb_bx, B->rb_by));
+          set_dims(e, r, rbgs_grid_b(c->ls[l], B->rb_bx, B->rb_by));
           d.push_back(e);
-          bl.push_back(nblocks(rbgs_grid(c->ls[l], B->rb_bx, B->rb_by)));
+          bl.push_back(nblocks(rbgs_grid_b(c->ls[l], B->rb_bx, B->rb_by)));
         }
         tab_upload(B, B->t_vc[slot_up(M, l, k)], d, bl);
       }
@@ -2518,27 +2582,27 @@ void upload_vcycle_tables(pm_batch* B) {
 
 // Launch the V-cycle slots (captured once into a graph, grids at their
 // largest; members and their grids come from the tables).
-void launch_vcycle_slots(pm_batch* B) {
+void launch_vcycle_slots(pm_batch* B, cudaStream_t st) {
   const int M = B->maxLc;
   const int* act = B->d_active;
   for (int l = 0; l < M; ++l) {
     for (int k = 0; k < 4; ++k) {
       BTab& t = B->t_vc[slot_down(l, k)];
-      launch_rbgs_b(B->st, t.grid_max, (const RbgsDesc*)t.d_desc, t.d_tab, act, B->rb_bx,
+      launch_rbgs_b(st, t.grid_max, (const RbgsDesc*)t.d_desc, t.d_tab, act, B->rb_bx,
                     B->rb_by);
     }
     BTab& t = B->t_vc[slot_down(l, 4)];
-    launch_restrict_b(B->st, t.grid_max, (const RestrictDesc*)t.d_desc, t.d_tab, act);
+    launch_restrict_b(st, t.grid_max, (const RestrictDesc*)t.d_desc, t.d_tab, act);
   }
   BTab& tb = B->t_vc[slot_bottom(M)];
   // one cluster per realisation, shared memory for the largest top level
-  launch_cmg_b(B->st, B->R, cmg_top_side(cmg_cluster()), (const CmgDesc*)tb.d_desc, act);
+  launch_cmg_b(st, B->R, cmg_top_side(cmg_cluster()), (const CmgDesc*)tb.d_desc, act);
   for (int l = M - 1; l >= 0; --l) {
     BTab& tp = B->t_vc[slot_up(M, l, 0)];
-    launch_prolong_b(B->st, tp.grid_max, (const ProlongDesc*)tp.d_desc, tp.d_tab, act);
+    launch_prolong_b(st, tp.grid_max, (const ProlongDesc*)tp.d_desc, tp.d_tab, act);
     for (int k = 1; k < 5; ++k) {
       BTab& t = B->t_vc[slot_up(M, l, k)];
-      launch_rbgs_b(B->st, t.grid_max, (const RbgsDesc*)t.d_desc, t.d_tab, act, B->rb_bx,
+      launch_rbgs_b(st, t.grid_max, (const RbgsDesc*)t.d_desc, t.d_tab, act, B->rb_bx,
                     B->rb_by);
     }
   }
@@ -2568,7 +2632,7 @@ pm_status tune_rbgs(pm_batch* B) {
       for (int l = 0; l < M; ++l)
         for (int k = 0; k < 4; ++k) {
           BTab& t = B->t_vc[slot_down(l, k)];
-          launch_rbgs_b(B->st, t.grid_max, (const RbgsDesc*)t.d_desc, t.d_tab, B->d_active,
+          launch_rbgs_b(B->st, t.grid_max, (const RbgsDesc*)t.d_desc, t.d_tab, nullptr,
                         B->rb_bx, B->rb_by);
         }
       cudaEventRecord(e1, B->st);
@@ -2592,35 +2656,74 @@ pm_status tune_rbgs(pm_batch* B) {
   return e == cudaSuccess ? PM_OK : bfail(B, PM_ECUDA, cudaGetErrorString(e));
 }
 
-pm_status batch_vcycle(pm_batch* B) {
-  if (B->tables_stale) {
-    upload_vcycle_tables(B);
-    B->tables_stale = false;
-  }
-  cudaMemcpyAsync(B->d_active, B->h_active, sizeof(int) * B->R, cudaMemcpyHostToDevice, B->st);
-  if (!B->rb_tuned) {
-    pm_status st = tune_rbgs(B);
-    if (st != PM_OK) return st;
-  }
-  if (!B->vgraph) {
-    // grids of the graph: the largest totals (taken from the first cubes,
-    // which are the largest of the run)
-    cudaError_t e = cudaStreamBeginCapture(B->st, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return bfail(B, PM_ECUDA, cudaGetErrorString(e));
-    long long l0 = g_launches.load();
-    launch_vcycle_slots(B);
-    cudaGraph_t g = nullptr;
-    e = cudaStreamEndCapture(B->st, &g);
-    B->vgraph_kernels = g_launches.load() - l0;
-    g_launches.fetch_sub(B->vgraph_kernels);
-    if (e != cudaSuccess) return bfail(B, PM_ECUDA, cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&B->vgraph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return bfail(B, PM_ECUDA, cudaGetErrorString(e));
-  }
-  cudaError_t e = cudaGraphLaunch(B->vgraph, B->st);
+// Capture the graph solve once (grids at their largest: the first cubes,
+// which are the largest of the run): init; defect; decision; while any
+// realisation is active: its V-cycle, defect and decision; the gradient
+// field of each final potential.  The decision kernel sets the loop's
+// condition, so no host read happens inside the solve.
+pm_status build_solve_graph(pm_batch* B) {
+  const int R = B->R;
+  cudaError_t e = cudaSuccess;
+  if (!B->st2 && (e = cudaStreamCreateWithFlags(&B->st2, cudaStreamNonBlocking)) != cudaSuccess)
+    return bfail(B, PM_ECUDA, cudaGetErrorString(e));
+  e = cudaStreamBeginCapture(B->st, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return bfail(B, PM_ECUDA, cudaGetErrorString(e));
-  g_launches.fetch_add(B->vgraph_kernels);
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  cudaGraphConditionalHandle loop = 0;
+  const long long l0 = g_launches.load();
+  e = cudaStreamGetCaptureInfo(B->st, &cs, nullptr, &g);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&loop, g, 0, 0);
+  auto decide = [&](cudaStream_t st) {
+    launch_defect_b(st, B->t_def.grid_max, (const DefectDesc*)B->t_def.d_desc, B->t_def.d_tab,
+                    B->d_active);
+    launch_converged_b(st, R, B->d_scal, B->d_rel + MAX_REAL, B->d_maxv, B->d_active,
+                       B->d_iters, B->d_iters + MAX_REAL, B->d_rel, loop);
+  };
+  cudaGraphNode_t wnode = nullptr;
+  long long lb0 = 0, lb1 = 0;
+  if (e == cudaSuccess) {
+    launch_solve_init_b(B->st, R, B->d_active, B->d_iters, B->d_iters + MAX_REAL);
+    decide(B->st);
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    e = cudaStreamGetCaptureInfo(B->st, &cs, nullptr, &g, &deps, nullptr, &nd);
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = loop;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&wnode, g, deps, nullptr, nd, &p);
+    if (e == cudaSuccess)
+      e = cudaStreamUpdateCaptureDependencies(B->st, &wnode, nullptr, 1,
+                                              cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) {
+      cudaGraph_t body = p.conditional.phGraph_out[0];
+      e = cudaStreamBeginCaptureToGraph(B->st2, body, nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        lb0 = g_launches.load();
+        launch_vcycle_slots(B, B->st2);
+        decide(B->st2);
+        lb1 = g_launches.load();
+        e = cudaStreamEndCapture(B->st2, &body);
+      }
+    }
+    launch_grad_b(B->st, B->t_grad.grid_max, (const GradDesc*)B->t_grad.d_desc,
+                  B->t_grad.d_tab);
+  }
+  cudaGraph_t done = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(B->st, &done);
+  // the launches counted here run when the graph does (batch_solve_done)
+  g_launches.fetch_sub(g_launches.load() - l0);
+  B->loop_kernels = lb1 - lb0;
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&B->sgraph, done, 0);
+  if (done) cudaGraphDestroy(done);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return bfail(B, PM_ECUDA, std::string("pm_batch: solve graph: ") + cudaGetErrorString(e));
+  }
   return PM_OK;
 }
 
@@ -2657,7 +2760,7 @@ pm_status upload_solve_slots(pm_batch* B) {
 // The gradient-field table: every realisation's potential in buffer cur
 // (alt: the other buffer, taken by the persistent solve after an odd number
 // of V-cycles).
-void upload_grad_table(pm_batch* B) {
+void upload_grad_table(pm_batch* B, const int* flip) {
   std::vector<GradDesc> d;
   std::vector<int> bl;
   for (int r = 0; r < B->R; ++r) {
@@ -2668,6 +2771,7 @@ void upload_grad_table(pm_batch* B) {
     e.pl = c->phi_l[c->cur];
     e.ph_alt = c->phi_h[c->cur ^ 1];
     e.pl_alt = c->phi_l[c->cur ^ 1];
+    e.flip = flip;
     e.n = c->n;
     e.lo = c->lo;
     e.s = c->s;
@@ -2681,19 +2785,11 @@ void upload_grad_table(pm_batch* B) {
   tab_upload(B, B->t_grad, d, bl);
 }
 
-// One persistent launch solves every realisation from its current buffer to
-// its tolerance; V-cycle counts, failures and residuals are read back when
-// the step ends (batch_solve_done).
-pm_status batch_solve_persistent(pm_batch* B) {
+// The defect table of a device-decided solve: every realisation, from the
+// buffer it starts in (iters: the V-cycle counts that pick the buffers in
+// the graph solve; NULL for the persistent one, which keeps its own).
+void upload_defect_table(pm_batch* B, const int* iters) {
   const int R = B->R;
-  if (B->tables_stale) {
-    upload_vcycle_tables(B);
-    B->tables_stale = false;
-  }
-  if (!B->d_slots || B->n_slots_dev != n_slots(B->maxLc)) {
-    pm_status st = upload_solve_slots(B);
-    if (st != PM_OK) return st;
-  }
   std::vector<DefectDesc> d;
   std::vector<int> bl;
   for (int r = 0; r < R; ++r) {
@@ -2713,12 +2809,29 @@ pm_status batch_solve_persistent(pm_batch* B) {
     e.partial = c->partial;
     e.counter = c->counter;
     e.out = B->d_scal + 16 * r + 11;
+    e.iters = iters;
     set_dims(e, r, defect_grid(s));
     d.push_back(e);
     bl.push_back(nblocks(defect_grid(s)));
   }
   tab_upload(B, B->t_def, d, bl);
-  upload_grad_table(B);
+}
+
+// One persistent launch solves every realisation from its current buffer to
+// its tolerance; V-cycle counts, failures and residuals are read back when
+// the step ends (batch_solve_done).
+pm_status batch_solve_persistent(pm_batch* B) {
+  const int R = B->R;
+  if (B->tables_stale) {
+    upload_vcycle_tables(B);
+    B->tables_stale = false;
+  }
+  if (!B->d_slots || B->n_slots_dev != n_slots(B->maxLc)) {
+    pm_status st = upload_solve_slots(B);
+    if (st != PM_OK) return st;
+  }
+  upload_defect_table(B, nullptr);
+  upload_grad_table(B, nullptr);
   cudaMemsetAsync(B->d_bar, 0, sizeof(GridBar), B->st);
   cudaMemsetAsync(B->d_iters + MAX_REAL, 0, sizeof(int) * R, B->st);
   SolveArgs a{};
@@ -2738,7 +2851,30 @@ pm_status batch_solve_persistent(pm_batch* B) {
   a.bar = B->d_bar;
   a.limit_ns = (unsigned long long)(B->wait_s * 1e9);
   a.extra = B->extra;
+  a.fast_coarse = cmg_fast();
   cudaError_t e = launch_solve_b(B->st, a);
+  if (e != cudaSuccess) return bfail(B, PM_ECUDA, cudaGetErrorString(e));
+  B->solved_on_device = true;
+  return PM_OK;
+}
+
+// One launch of the solve graph (captured at the first solve).
+pm_status batch_solve_graph(pm_batch* B) {
+  if (B->tables_stale) {
+    upload_vcycle_tables(B);
+    B->tables_stale = false;
+  }
+  if (!B->rb_tuned) {
+    pm_status st = tune_rbgs(B);
+    if (st != PM_OK) return st;
+  }
+  upload_defect_table(B, B->d_iters);
+  upload_grad_table(B, B->d_iters);
+  if (!B->sgraph) {
+    pm_status st = build_solve_graph(B);
+    if (st != PM_OK) return st;
+  }
+  cudaError_t e = cudaGraphLaunch(B->sgraph, B->st);
   if (e != cudaSuccess) return bfail(B, PM_ECUDA, cudaGetErrorString(e));
   B->solved_on_device = true;
   return PM_OK;
@@ -2774,6 +2910,13 @@ pm_status batch_solve_done(pm_batch* B) {
              "(pass %d); the batch must be destroyed",
              B->wait_s, B->h_bar->where);
     return bfail(B, PM_ETIMEOUT, buf);
+  }
+  if (!B->persistent) {
+    // the graph's kernels: init, defect, decision, gradient, and the loop's
+    // body once per V-cycle of the realisation that took the most
+    int most = 0;
+    for (int r = 0; r < B->R; ++r) most = std::max(most, B->h_iters[r]);
+    g_launches.fetch_add(4 + (long long)most * B->loop_kernels);
   }
   for (int r = 0; r < B->R; ++r) {
     pm_ctx* c = B->ctx[r];
@@ -2845,7 +2988,6 @@ pm_status pm_batch_init(int32_t n_real, const pm_config* cfgs, const float* cons
   }
   pm_status st = PM_OK;
   if (cudaMalloc((void**)&B->d_active, sizeof(int) * MAX_REAL) != cudaSuccess ||
-      cudaMallocHost((void**)&B->h_active, sizeof(int) * MAX_REAL) != cudaSuccess ||
       cudaMalloc((void**)&B->d_scal, sizeof(double) * 16 * MAX_REAL) != cudaSuccess ||
       cudaMallocHost((void**)&B->h_scal, sizeof(double) * 16 * MAX_REAL) != cudaSuccess ||
       cudaMalloc((void**)&B->d_cnt, sizeof(unsigned long long) * 4 * MAX_REAL) != cudaSuccess ||
@@ -2872,14 +3014,9 @@ pm_status pm_batch_init(int32_t n_real, const pm_config* cfgs, const float* cons
             cudaSuccess ||
         cudaMemcpy(B->d_maxv, mv, sizeof(int) * n_real, cudaMemcpyHostToDevice) != cudaSuccess)
       st = bfail(B, PM_ECUDA, "pm_batch_init: tolerance upload failed");
-    // the persistent solve takes the one-CTA coarse levels (tops <= 16^3)
-    // and needs its whole grid resident; the graph path otherwise
-    B->persistent = cmg_cluster() == 1 && solve_grid_b() > 0;
-    if (B->persistent) {
-      B->rb_bx = 32;  // the persistent kernel's block
-      B->rb_by = 8;
-      B->rb_tuned = true;
-    }
+    // the graph solve by default (measured faster than the persistent
+    // kernel, whose register budget is that of its heaviest phase)
+    B->persistent = false;
   }
   if (st == PM_OK) st = tab_alloc(B, B->t_dep, sizeof(DepositDesc));
   if (st == PM_OK) st = tab_alloc(B, B->t_src, sizeof(SourceDesc));
@@ -3040,78 +3177,17 @@ pm_status pm_batch_step(pm_batch* B, int32_t n_steps) {
         e.ql = full_view(c, c->prev_lo, c->lo, c->s);
         e.w = w;
         e.pair = 1;
-        set_dims(e, r, full_grid(c->s));
+        set_dims(e, r, full_grid_b(c->s));
         d.push_back(e);
-        bl.push_back(nblocks(full_grid(c->s)));
+        bl.push_back(nblocks(full_grid_b(c->s)));
       }
       int g = tab_upload(B, B->t_pred, d, bl);
       launch_predict_b(B->st, g, (const PredictDesc*)B->t_pred.d_desc, B->t_pred.d_tab);
     }
-    // 4. solve every realisation to its rtol
-    if (B->persistent) {
-      pm_status st = batch_solve_persistent(B);
+    // 4. solve every realisation to its rtol, decided on the device
+    {
+      pm_status st = B->persistent ? batch_solve_persistent(B) : batch_solve_graph(B);
       if (st != PM_OK) return st;
-    }
-    std::vector<int> it(R, 0);
-    for (int r = 0; r < R; ++r) B->h_active[r] = B->persistent ? 0 : 1;
-    while (!B->persistent) {
-      std::vector<DefectDesc> d;
-      std::vector<int> bl, swapped;
-      for (int r = 0; r < R; ++r) {
-        if (!B->h_active[r]) continue;
-        pm_ctx* c = B->ctx[r];
-        const int lo = c->lo, s = c->s, c0 = c->cur;
-        DefectDesc e{};
-        e.ph = full_view(c, c->phi_h[c0], lo, s);
-        e.pl = full_view(c, c->phi_l[c0], lo, s);
-        e.e = compact_view(c->lu[0], s);
-        e.correct = it[r] > 0;
-        e.qh = full_view(c, c->phi_h[e.correct ? c0 ^ 1 : c0], lo, s);
-        e.ql = full_view(c, c->phi_l[e.correct ? c0 ^ 1 : c0], lo, s);
-        e.fh = full_view(c, c->f_hi, lo, s);
-        e.fl = full_view(c, c->f_lo, lo, s);
-        e.rb = compact_view(c->lb[0], s);
-        e.periodic = c->periodic;
-        e.write_r = 1;
-        e.partial = c->partial;
-        e.counter = c->counter;
-        e.out = B->d_scal + 16 * r + 11;
-        set_dims(e, r, defect_grid(s));
-        d.push_back(e);
-        bl.push_back(nblocks(defect_grid(s)));
-        if (e.correct) c->cur ^= 1;
-      }
-      int g = tab_upload(B, B->t_def, d, bl);
-      launch_defect_b(B->st, g, (const DefectDesc*)B->t_def.d_desc, B->t_def.d_tab, nullptr);
-      pm_status st = batch_sync(B);
-      if (st != PM_OK) return st;
-      int n_act = 0;
-      for (int r = 0; r < R; ++r) {
-        if (!B->h_active[r]) continue;
-        pm_ctx* c = B->ctx[r];
-        double f2 = B->h_scal[16 * r], r2 = B->h_scal[16 * r + 11];
-        double rel = f2 > 0 ? std::sqrt(r2 / f2) : 0.0;
-        if (rel <= c->cfg.rtol || f2 == 0.0) {
-          B->h_active[r] = 0;
-          c->vcycles_last = it[r];
-          c->vcycles_total += it[r];
-          c->resid_last = rel;
-          continue;
-        }
-        if (it[r] >= c->cfg.max_vcycles) {
-          char buf[200];
-          snprintf(buf, sizeof buf,
-                   "realisation %d: relative residual %.3e after %d V-cycles (rtol %.1e)", r,
-                   rel, it[r], c->cfg.rtol);
-          return bfail(B, PM_ENOCONV, buf);
-        }
-        ++n_act;
-      }
-      if (n_act == 0) break;
-      st = batch_vcycle(B);
-      if (st != PM_OK) return st;
-      for (int r = 0; r < R; ++r)
-        if (B->h_active[r]) ++it[r];
     }
     for (int r = 0; r < R; ++r) {
       pm_ctx* c = B->ctx[r];
@@ -3119,13 +3195,8 @@ pm_status pm_batch_step(pm_batch* B, int32_t n_steps) {
       c->ah_hist[1] = c->a_half[k];
       c->n_sol++;
     }
-    // 5-6. gradient field (the persistent solve wrote it), gather + kick +
-    // drift (+ keep flags)
-    if (!B->persistent) {
-      upload_grad_table(B);
-      launch_grad_b(B->st, B->t_grad.h_tab->off[B->t_grad.h_tab->m],
-                    (const GradDesc*)B->t_grad.d_desc, B->t_grad.d_tab);
-    }
+    // 5-6. gather + kick + drift (+ keep flags) from the gradient field the
+    // solve wrote
     bool any_flag = false;
     std::vector<int> flagged(R, 0);
     {
@@ -3270,10 +3341,10 @@ pm_status pm_batch_set_solve(pm_batch* B, int32_t persistent, double wait_second
     B->rb_by = 8;
     B->rb_tuned = B->persistent;
     B->tables_stale = true;
-    if (B->vgraph) {
+    if (B->sgraph) {
       cudaStreamSynchronize(B->st);
-      cudaGraphExecDestroy(B->vgraph);
-      B->vgraph = nullptr;
+      cudaGraphExecDestroy(B->sgraph);
+      B->sgraph = nullptr;
     }
   }
   B->wait_s = wait_seconds;
@@ -3286,14 +3357,14 @@ const char* pm_batch_last_error(const pm_batch* B) { return B ? B->err.c_str() :
 void pm_batch_destroy(pm_batch* B) {
   if (!B) return;
   if (B->st) cudaStreamSynchronize(B->st);
-  if (B->vgraph) cudaGraphExecDestroy(B->vgraph);
+  if (B->sgraph) cudaGraphExecDestroy(B->sgraph);
+  if (B->st2) cudaStreamDestroy(B->st2);
   for (pm_ctx* c : B->ctx) pm_destroy(c);
   for (BTab* t : {&B->t_dep, &B->t_src, &B->t_bnd, &B->t_pred, &B->t_def, &B->t_grad,
                   &B->t_gat, &B->t_scan, &B->t_scat})
     tab_free(*t);
   for (auto& t : B->t_vc) tab_free(t);
   if (B->d_active) cudaFree(B->d_active);
-  if (B->h_active) cudaFreeHost(B->h_active);
   if (B->d_bar) cudaFree(B->d_bar);
   if (B->h_bar) cudaFreeHost(B->h_bar);
   if (B->d_iters) cudaFree(B->d_iters);
@@ -3317,7 +3388,7 @@ void pm_batch_destroy(pm_batch* B) {
 // ===========================================================================
 namespace {
 Grid padded_view(const float* base, int s) {
-  Grid g;
+  Grid g{};
   g.s = s;
   g.sy = s + 2;
   g.sz = (s + 2) * (s + 2);
@@ -3360,7 +3431,7 @@ extern "C" pm_status pm_mg_smooth(const float* u_in, float* u_out, const float* 
   cudaStream_t st = (cudaStream_t)stream;
   if (mg_prepare() != cudaSuccess) return fail(nullptr, PM_ECUDA, "pm_mg_smooth: attributes");
   auto view = [&](const float* base) {
-    Grid g;
+    Grid g{};
     g.s = s;
     g.sy = s + 2;
     g.sz = (s + 2) * (s + 2);

@@ -10,6 +10,7 @@
 #include <utility>
 
 #include "cmg_dev.cuh"
+#include "cmg_fast.cuh"
 
 namespace pm {
 
@@ -17,11 +18,17 @@ namespace {
 
 template <int CL>
 __global__ void __launch_bounds__(CC_NT, 1) k_cmg(Grid u, Grid b, int level, int periodic,
-                                                  int sweeps, int zero_top, float sig0) {
+                                                  int sweeps, int zero_top, float sig0,
+                                                  int fast) {
   pdl_wait();
   pdl_release();
   extern __shared__ float cc_sm[];
   __shared__ float red[CC_NT / 32];
+  if (CL == 1 && (fast || u.mbase) && fc_supported(u.s)) {
+    fc_vcycle<CC_NT>(cc_sm, red, u, b, level, periodic, sweeps, zero_top, sig0);
+    return;
+  }
+  if (u.mbase) return;  // not reached: masked tops (q 2^j <= 16) are all supported
   __shared__ CcLevel lev[CC_MAXL];
   __shared__ int nlev;
   if (threadIdx.x == 0) Cc<CL>::init_levels(lev, nlev, u.s, level, periodic, sig0);
@@ -45,13 +52,17 @@ __global__ void __launch_bounds__(CC_NT, 1) k_cmg(Grid u, Grid b, int level, int
 // (realisations whose solve has converged are skipped, by whole clusters)
 template <int CL>
 __global__ void __launch_bounds__(CC_NT, 1) kb_cmg(const CmgDesc* d, int n_desc,
-                                                   const int* active) {
+                                                   const int* active, int fast) {
   extern __shared__ float cc_sm[];
   __shared__ float red[CC_NT / 32];
   const int q = blockIdx.x / CL;
   if (q >= n_desc) return;
   const CmgDesc& e = d[q];
   if (active && !active[e.r]) return;
+  if (CL == 1 && fast && fc_supported(e.u.s)) {
+    fc_vcycle<CC_NT>(cc_sm, red, e.u, e.b, e.level, e.periodic, e.sweeps, e.zero_top, 0.0f);
+    return;
+  }
   __shared__ CcLevel lev[CC_MAXL];
   __shared__ int nlev;
   if (threadIdx.x == 0) Cc<CL>::init_levels(lev, nlev, e.u.s, e.level, e.periodic, 0.0f);
@@ -72,10 +83,18 @@ __global__ void __launch_bounds__(CC_NT, 1) kb_cmg(const CmgDesc* d, int n_desc,
 }
 
 int g_cmg_cl = 1;  // CTAs per cluster of this process's launches (set by cmg_prepare)
+int g_cmg_fast = 1;  // one-CTA tops <= 16 take the constant-side form (cmg_fast.cuh)
+
+// dynamic shared memory of a coarse-level launch from tops up to `top`
+int cmg_smem(int top, int CL) {
+  int f = cc_layout(top, CL).floats;
+  if (CL == 1 && fc_floats(FC_MAX_TOP) > f) f = fc_floats(FC_MAX_TOP);
+  return (int)sizeof(float) * f;
+}
 
 template <int CL>
 cudaError_t cmg_attrs() {
-  const int smem = (int)sizeof(float) * cc_layout(cmg_top_side(CL), CL).floats;
+  const int smem = cmg_smem(cmg_top_side(CL), CL);
   cudaError_t e = cudaFuncSetAttribute(k_cmg<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        smem);
   if (e == cudaSuccess)
@@ -98,7 +117,7 @@ bool cmg_fits() {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(CL);
   cfg.blockDim = dim3(CC_NT);
-  cfg.dynamicSmemBytes = sizeof(float) * cc_layout(cmg_top_side(CL), CL).floats;
+  cfg.dynamicSmemBytes = cmg_smem(cmg_top_side(CL), CL);
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = CL;
@@ -119,7 +138,7 @@ void cmg_launch(K kernel, int clusters, int top, cudaStream_t st, Act&&... args)
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(CL * clusters);
   cfg.blockDim = dim3(CC_NT);
-  cfg.dynamicSmemBytes = sizeof(float) * cc_layout(top, CL).floats;
+  cfg.dynamicSmemBytes = cmg_smem(top, CL);
   cfg.stream = st;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -143,6 +162,8 @@ cudaError_t cmg_prepare() {
   cudaError_t e = cmg_attrs<1>();
   if (e != cudaSuccess) return e;
   g_cmg_cl = 1;
+  // PM_CMG_GENERIC: the generic one-CTA form for every top (the same bits)
+  g_cmg_fast = getenv("PM_CMG_GENERIC") ? 0 : 1;
   if (getenv("PM_NO_CLUSTER")) return cudaSuccess;
   // PM_CMG_CLUSTER = 8 or 16 asks for a cluster.  One CTA is the default:
   // measured on the 256^3 workload (20 steps, both phases), the coarse
@@ -158,24 +179,35 @@ cudaError_t cmg_prepare() {
   return cudaSuccess;
 }
 
-int cmg_smem_bytes(int top) { return (int)sizeof(float) * cc_layout(top, g_cmg_cl).floats; }
+int cmg_smem_bytes(int top) { return cmg_smem(top, g_cmg_cl); }
+
+int cmg_fast() { return g_cmg_fast; }
 
 void launch_cmg(cudaStream_t st, Grid u, Grid b, int level, int periodic, int sweeps,
                 bool zero_top, float sig0) {
   const int z = zero_top ? 1 : 0;
-  switch (g_cmg_cl) {
-    case 16: cmg_launch<16>(k_cmg<16>, 1, u.s, st, u, b, level, periodic, sweeps, z, sig0); break;
-    case 8: cmg_launch<8>(k_cmg<8>, 1, u.s, st, u, b, level, periodic, sweeps, z, sig0); break;
-    default: cmg_launch<1>(k_cmg<1>, 1, u.s, st, u, b, level, periodic, sweeps, z, sig0); break;
+  // the ball solve's masked levels take the one-CTA constant-side form
+  switch (u.mbase ? 1 : g_cmg_cl) {
+    case 16:
+      cmg_launch<16>(k_cmg<16>, 1, u.s, st, u, b, level, periodic, sweeps, z, sig0, 0);
+      break;
+    case 8:
+      cmg_launch<8>(k_cmg<8>, 1, u.s, st, u, b, level, periodic, sweeps, z, sig0, 0);
+      break;
+    default:
+      cmg_launch<1>(k_cmg<1>, 1, u.s, st, u, b, level, periodic, sweeps, z, sig0, g_cmg_fast);
+      break;
   }
   note_launch();
 }
 
 void launch_cmg_b(cudaStream_t st, int n_desc, int max_top, const CmgDesc* d, const int* active) {
   switch (g_cmg_cl) {
-    case 16: cmg_launch<16>(kb_cmg<16>, n_desc, max_top, st, d, n_desc, active); break;
-    case 8: cmg_launch<8>(kb_cmg<8>, n_desc, max_top, st, d, n_desc, active); break;
-    default: cmg_launch<1>(kb_cmg<1>, n_desc, max_top, st, d, n_desc, active); break;
+    case 16: cmg_launch<16>(kb_cmg<16>, n_desc, max_top, st, d, n_desc, active, 0); break;
+    case 8: cmg_launch<8>(kb_cmg<8>, n_desc, max_top, st, d, n_desc, active, 0); break;
+    default:
+      cmg_launch<1>(kb_cmg<1>, n_desc, max_top, st, d, n_desc, active, g_cmg_fast);
+      break;
   }
   note_launch();
 }

@@ -800,11 +800,36 @@ __device__ __forceinline__ double ghost_value(int n, int lo, int i, int j, int k
   double r2 = x * x + y * y + z * z;
   double qr = qxx * x * x + qyy * y * y + qzz * z * z +
               2.0 * (qxy * x * y + qxz * x * z + qyz * y * z);
-  // q0/r + d.x/r^3 + qr/(2 r^5) from one reciprocal square root (FP64
-  // divisions and square roots are long sequences on this part)
-  const double ri = rsqrt(r2), ri2 = ri * ri;
+  // q0/r + d.x/r^3 + qr/(2 r^5) from one reciprocal square root: the float
+  // estimate refined by two Newton steps in FP64, ri <- ri (3 - r2 ri^2) / 2,
+  // each squaring the relative error (1e-7 -> 1e-14 -> double rounding);
+  // FP64 divisions and square roots are long sequences on this part
+  double ri = (double)rsqrtf((float)r2);
+  ri = ri * (1.5 - 0.5 * r2 * ri * ri);
+  ri = ri * (1.5 - 0.5 * r2 * ri * ri);
+  const double ri2 = ri * ri;
   return -(S / (4.0 * 3.14159265358979323846)) * ri *
          (q0 + ri2 * ((dx * x + dy * y + dz * z) + 0.5 * qr * ri2));
+}
+
+// The same multipole value in FP32 throughout
+__device__ __forceinline__ float ghost_value_f(int n, int lo, int i, int j, int k,
+                                               const double* __restrict__ mom, float S) {
+  const float q0 = (float)mom[0], dx = (float)mom[1], dy = (float)mom[2], dz = (float)mom[3];
+  const float sxx = (float)mom[4], syy = (float)mom[5], szz = (float)mom[6];
+  const float sxy = (float)mom[7], sxz = (float)mom[8], syz = (float)mom[9];
+  const float tr = sxx + syy + szz;
+  const float qxx = 3.0f * sxx - tr, qyy = 3.0f * syy - tr, qzz = 3.0f * szz - tr;
+  const float qxy = 3.0f * sxy, qxz = 3.0f * sxz, qyz = 3.0f * syz;
+  const float h = 0.5f * (float)n;
+  const float x = (float)(lo + i) + 0.5f - h, y = (float)(lo + j) + 0.5f - h;
+  const float z = (float)(lo + k) + 0.5f - h;
+  const float r2 = x * x + y * y + z * z;
+  const float qr = qxx * x * x + qyy * y * y + qzz * z * z +
+                   2.0f * (qxy * x * y + qxz * x * z + qyz * y * z);
+  const float ri = rsqrtf(r2), ri2 = ri * ri;
+  return -(S / (4.0f * 3.14159265f)) * ri *
+         (q0 + ri2 * ((dx * x + dy * y + dz * z) + 0.5f * qr * ri2));
 }
 
 // the values into (ph, pl) and, when ph2.base is not NULL, the same into
@@ -840,6 +865,49 @@ void launch_boundary(cudaStream_t st, Grid ph, Grid pl, int n, int lo, const dou
   Grid none{};
   k_boundary<<<grid, 256, 0, st>>>(ph, pl, n, lo, mom, S, want_lo ? 1 : 0,
                                    ph2 ? *ph2 : none, pl2 ? *pl2 : none);
+  note_launch();
+}
+
+// The ball solve's boundary values: every cell of the padded cube outside
+// the mask (ph's mask fields) takes the multipole value, in (ph, pl) and
+// (ph2, pl2): the cells next to the mask are its Dirichlet ghosts, the rest
+// give the force of particles beyond the mask in the step before they leave.
+__global__ void __launch_bounds__(256) k_ball_ghosts(Grid ph, Grid pl, Grid ph2, Grid pl2,
+                                                     int n, int lo,
+                                                     const double* __restrict__ mom,
+                                                     double S) {
+  const int s = ph.s, P = s + 2;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)P * P * P) return;
+  const int i = (int)(t % P) - 1, j = (int)((t / P) % P) - 1, k = (int)(t / ((long long)P * P)) - 1;
+  auto in = [&](int a, int b, int c) {
+    return a >= 0 && b >= 0 && c >= 0 && a < s && b < s && c < s && g_in(ph, a, b, c);
+  };
+  if (in(i, j, k)) return;
+  // the Dirichlet ghosts (next to the mask) in FP64 as a hi + lo pair; the
+  // cells beyond, read only by the gather of particles beyond the mask, in
+  // FP32 (FP64 arithmetic is slow on this part)
+  const bool ghost = in(i - 1, j, k) || in(i + 1, j, k) || in(i, j - 1, k) ||
+                     in(i, j + 1, k) || in(i, j, k - 1) || in(i, j, k + 1);
+  float hi, lov;
+  if (ghost) {
+    const double phi = ghost_value(n, lo, i, j, k, mom, S);
+    hi = (float)phi;
+    lov = (float)(phi - (double)hi);
+  } else {
+    hi = ghost_value_f(n, lo, i, j, k, mom, (float)S);
+    lov = 0.0f;
+  }
+  ph.base[gidx(ph, i, j, k)] = hi;
+  pl.base[gidx(pl, i, j, k)] = lov;
+  ph2.base[gidx(ph2, i, j, k)] = hi;
+  pl2.base[gidx(pl2, i, j, k)] = lov;
+}
+
+void launch_ball_ghosts(cudaStream_t st, Grid ph, Grid pl, Grid ph2, Grid pl2, int n, int lo,
+                        const double* mom, double S) {
+  const long long P = ph.s + 2, tot = P * P * P;
+  k_ball_ghosts<<<(int)((tot + 255) / 256), 256, 0, st>>>(ph, pl, ph2, pl2, n, lo, mom, S);
   note_launch();
 }
 

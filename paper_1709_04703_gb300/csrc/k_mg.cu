@@ -6,6 +6,7 @@
 #include <cstdlib>
 
 #include "cmg_dev.cuh"
+#include "cmg_fast.cuh"
 #include "mg_arith.cuh"
 #include "pm_kernels.cuh"
 
@@ -32,9 +33,14 @@ __device__ __forceinline__ void d_rbgs(const BI& bi, Grid u, Grid b, float h2, i
   if (2 * t >= half || j >= s) return;
   const int i0 = 4 * t + ((j + k + color) & 1);
   const bool two = 2 * t + 1 < half;
+  // the ball solve updates only the cells of its mask
+  const bool in0 = g_in(u, i0, j, k), in1 = two && g_in(u, i0 + 2, j, k);
+  if (!in0 && !in1) return;
   const int ym = (wrap_m(j, s, periodic) - j) * u.sy, yp = (wrap_p(j, s, periodic) - j) * u.sy;
   const int zm = (wrap_m(k, s, periodic) - k) * u.sz, zp = (wrap_p(k, s, periodic) - k) * u.sz;
-  const bool simple = mg_simple(periodic, gam, d0);
+  // masked coarse levels of the ball solve: their own diagonal
+  const bool ballc = ball_coarse(u);
+  const bool simple = mg_simple(periodic, gam, d0) && !ballc;
   const int c0 = gidx(u, i0, j, k);
   const int bc0 = gidx(b, i0, j, k);
   float* p0 = u.base + c0;
@@ -53,10 +59,11 @@ __device__ __forceinline__ void d_rbgs(const BI& bi, Grid u, Grid b, float h2, i
       s1 = nb6(xmid, p1[xp1], p1[ym], p1[yp], p1[zm], p1[zp]);
     }
   }
-  p0[0] = gs_value(s0, b0v, h2, simple, simple ? 6.0f : mg_diag(i0, j, k, s, periodic, gam, d0));
-  if (two)
-    p0[2] = gs_value(s1, b1v, h2, simple,
-                     simple ? 6.0f : mg_diag(i0 + 2, j, k, s, periodic, gam, d0));
+  auto dg = [&](int i) {
+    return simple ? 6.0f : (ballc ? ball_diag(u, i, j, k) : mg_diag(i, j, k, s, periodic, gam, d0));
+  };
+  if (in0) p0[0] = gs_value(s0, b0v, h2, simple, dg(i0));
+  if (in1) p0[2] = gs_value(s1, b1v, h2, simple, dg(i0 + 2));
 }
 
 __global__ void __launch_bounds__(256) k_rbgs(Grid u, Grid b, float h2, int color,
@@ -114,10 +121,14 @@ __device__ __forceinline__ void d_resid_restrict(const BI& bi, Grid u, Grid b, f
         const float xm = dx ? V[dz][dy][0] : XM[dz][dy], xp = dx ? XP[dz][dy] : V[dz][dy][1];
         const float ym = dy ? V[dz][0][dx] : YM[dz][dx], yp = dy ? YP[dz][dx] : V[dz][1][dx];
         const float zm = dz ? V[0][dy][dx] : ZM[dy][dx], zp = dz ? ZP[dy][dx] : V[1][dy][dx];
-        float diag = mg_simple(periodic, gam, d0) ? 6.0f : mg_diag(i, j, k, s, periodic, gam, d0);
+        float diag = ball_coarse(u) ? ball_diag(u, i, j, k)
+                     : mg_simple(periodic, gam, d0) ? 6.0f
+                                                    : mg_diag(i, j, k, s, periodic, gam, d0);
         float s0 = nb6(xm, xp, ym, yp, zm, zp);
-        acc = __fadd_rn(acc, resid_value(s0, V[dz][dy][dx], b.base[gidx(b, i, j, k)], diag,
-                                         inv_h2));
+        // children outside the ball solve's mask carry no residual
+        if (g_in(u, i, j, k))
+          acc = __fadd_rn(acc, resid_value(s0, V[dz][dy][dx], b.base[gidx(b, i, j, k)], diag,
+                                           inv_h2));
       }
   int cc = gidx(uc, I, J, K);
   bc.base[cc] = __fmul_rn(0.125f, acc);
@@ -162,14 +173,38 @@ __device__ __forceinline__ float prolong_value(Grid uc, int i, int j, int k, int
                      q[gidx(uc, I, J2, K2)], q[gidx(uc, I2, J2, K2)], fx, fy, fz);
 }
 
+// The ball solve's prolongation value v: as prolong_value, with the masked
+// coarse level's own boundary (a second coarse cell outside the mask is the
+// parent times -ball_gam); false (no correction) where the parent itself is
+// outside the coarse mask.
+__device__ __forceinline__ bool prolong_value_ball(Grid uc, int i, int j, int k, float& v) {
+  const int I = i >> 1, J = j >> 1, K = k >> 1;
+  if (!g_in(uc, I, J, K)) return false;
+  int I2 = (i & 1) ? I + 1 : I - 1, J2 = (j & 1) ? J + 1 : J - 1, K2 = (k & 1) ? K + 1 : K - 1;
+  float fx = 1.0f, fy = 1.0f, fz = 1.0f;
+  if (!g_in(uc, I2, J, K)) { fx = -ball_gam(uc, I, J, K, 0, I2 > I ? 1 : -1); I2 = I; }
+  if (!g_in(uc, I, J2, K)) { fy = -ball_gam(uc, I, J, K, 1, J2 > J ? 1 : -1); J2 = J; }
+  if (!g_in(uc, I, J, K2)) { fz = -ball_gam(uc, I, J, K, 2, K2 > K ? 1 : -1); K2 = K; }
+  const float* q = uc.base;
+  v = prolong_mix(q[gidx(uc, I, J, K)], q[gidx(uc, I2, J, K)], q[gidx(uc, I, J2, K)],
+                  q[gidx(uc, I2, J2, K)], q[gidx(uc, I, J, K2)], q[gidx(uc, I2, J, K2)],
+                  q[gidx(uc, I, J2, K2)], q[gidx(uc, I2, J2, K2)], fx, fy, fz);
+  return true;
+}
+
 __device__ __forceinline__ void d_prolong(const BI& bi, Grid uc, Grid u, int periodic,
                                                  float gam_c){
   const int s = u.s;
   int i = bi.x * blockDim.x + threadIdx.x;
   int j = bi.y * blockDim.y + threadIdx.y;
   int k = bi.z;
-  if (i >= s || j >= s) return;
+  if (i >= s || j >= s || !g_in(u, i, j, k)) return;
   float* p = u.base + gidx(u, i, j, k);
+  if (uc.mbase) {
+    float v;
+    if (prolong_value_ball(uc, i, j, k, v)) *p = __fadd_rn(*p, v);
+    return;
+  }
   *p = __fadd_rn(*p, prolong_value(uc, i, j, k, periodic, gam_c));
 }
 
@@ -192,6 +227,16 @@ __global__ void __launch_bounds__(256) k_prolong_to(Grid uc, Grid u, Grid w, int
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   const int K = blockIdx.z;
   if (I >= sc || J >= sc) return;
+  if (uc.mbase) {  // the ball solve: its children one by one (mask of u)
+#pragma unroll 1
+    for (int c = 0; c < 8; ++c) {
+      const int i = 2 * I + (c & 1), j = 2 * J + ((c >> 1) & 1), k = 2 * K + (c >> 2);
+      float uv = u.base[gidx(u, i, j, k)], v;
+      if (g_in(u, i, j, k) && prolong_value_ball(uc, i, j, k, v)) uv = __fadd_rn(uv, v);
+      w.base[gidx(w, i, j, k)] = uv;
+    }
+    return;
+  }
   // coarse index of offset o in {-1, 0, +1} along an axis: wrapped, or (open)
   // the cell itself when outside, with factor -gam_c applied below
   auto idx = [&](int c, int o) {
@@ -404,7 +449,8 @@ struct Rbgs2 {
       const int p = t - st;
       const int m = 4 - st;
       const int q = (J + m) % RING, qm = (J + m - 1) % RING, qp = (J + m + 1) % RING;
-      if ((act >> (3 - st)) & 1u) {
+      // (the ball solve updates only the cells of its mask, carried by b)
+      if (((act >> (3 - st)) & 1u) && (b.mbase == 0 || g_in(b, xa + kc, y, p))) {
         float* c = sp + (p & (F2_R - 1)) * F2_PL + me + kc;
         const float xv = c[xo], ym = c[-F2_W], yp = c[F2_W];
         float nv;
@@ -447,6 +493,16 @@ __global__ void __launch_bounds__(F2_NT, 2) k_rbgs2(Grid win, Grid wout, Grid b,
   const int s = wout.s;
   const int ly = threadIdx.x / F2_PW, lx0 = 2 * (threadIdx.x - ly * F2_PW);
   const int x0 = blockIdx.x * F2_TX, y0 = blockIdx.y * F2_TY, z0 = blockIdx.z * zc;
+  if (b.mbase) {
+    // the ball solve (level 0): a tile without a mask cell has nothing to
+    // update, and the iterate is zero outside the mask in every buffer
+    auto lo2 = [&](int a, int n) {  // smallest |offset| over cells a .. a + n - 1
+      const int a0 = b.mbase + 2 * a, a1 = b.mbase + 2 * (a + n - 1);
+      return a0 > 0 ? a0 : (a1 < 0 ? -a1 : 1);
+    };
+    const int dx = lo2(x0, F2_TX), dy = lo2(y0, F2_TY), dz = lo2(z0, zc);
+    if (dx * dx + dy * dy + dz * dz > b.mr) return;
+  }
   Rbgs2<PERIODIC, SIMPLE, ZERO> g{win, wout, b, h2, gam, d0, s, x0, y0, z0, min(z0 + zc, s), ly,
                                   lx0, y0 - F2_H + ly, x0 - F2_H + lx0, ly * F2_W + lx0};
   g.sp = f2_smem;
@@ -651,7 +707,15 @@ __device__ __forceinline__ void d_defect(const BI& bi, Grid ph, Grid pl, Grid e,
   // a contiguous run of planes per thread; the (i, j) column's values at
   // k-1, k, k+1 (with the correction added) roll through registers
   const int chunk = (s + bi.gz - 1) / bi.gz;
-  const int k0 = bi.z * chunk, k1 = min(s, k0 + chunk);
+  int k0 = bi.z * chunk, k1 = min(s, k0 + chunk);
+  if (ph.mbase && i < s && j < s) {
+    // the ball solve: only the column's mask cells (outside, both potential
+    // buffers hold the same boundary values, and no pass reads r there)
+    int m0, m1;
+    mask_column(ph, i, j, m0, m1);
+    k0 = max(k0, m0);
+    k1 = min(k1, m1);
+  }
   if (i < s && j < s && k0 < k1) {
     const int xm = wrap_m(i, s, periodic) - i, xp = wrap_p(i, s, periodic) - i;
     const int ym = wrap_m(j, s, periodic) - j, yp = wrap_p(j, s, periodic) - j;
@@ -987,7 +1051,9 @@ __global__ void __launch_bounds__(256) kb_rbgs(const RbgsDesc* d, const BTable* 
   BI bi;
   if (!batch_map(d, t, active, q, bi)) return;
   const RbgsDesc& e = d[q];
-  d_rbgs(bi, e.u, e.b, e.h2, e.color, e.periodic, e.gam, e.zero_start, 6.0f);
+  each_plane(bi, e.u.s, [&](const BI& b) {
+    d_rbgs(b, e.u, e.b, e.h2, e.color, e.periodic, e.gam, e.zero_start, 6.0f);
+  });
 }
 __global__ void __launch_bounds__(256) kb_restrict(const RestrictDesc* d, const BTable* t,
                                                    const int* active) {
@@ -995,7 +1061,9 @@ __global__ void __launch_bounds__(256) kb_restrict(const RestrictDesc* d, const 
   BI bi;
   if (!batch_map(d, t, active, q, bi)) return;
   const RestrictDesc& e = d[q];
-  d_resid_restrict(bi, e.u, e.b, e.inv_h2, e.uc, e.bc, e.periodic, e.gam, 6.0f);
+  each_plane(bi, e.uc.s, [&](const BI& b) {
+    d_resid_restrict(b, e.u, e.b, e.inv_h2, e.uc, e.bc, e.periodic, e.gam, 6.0f);
+  });
 }
 __global__ void __launch_bounds__(256) kb_prolong(const ProlongDesc* d, const BTable* t,
                                                   const int* active) {
@@ -1003,14 +1071,27 @@ __global__ void __launch_bounds__(256) kb_prolong(const ProlongDesc* d, const BT
   BI bi;
   if (!batch_map(d, t, active, q, bi)) return;
   const ProlongDesc& e = d[q];
-  d_prolong(bi, e.uc, e.u, e.periodic, e.gam_c);
+  each_plane(bi, e.u.s, [&](const BI& b) { d_prolong(b, e.uc, e.u, e.periodic, e.gam_c); });
 }
-__global__ void __launch_bounds__(256) kb_defect(const DefectDesc* d, const BTable* t,
+__global__ void __launch_bounds__(256, 4) kb_defect(const DefectDesc* d, const BTable* t,
                                                  const int* active) {
   int q;
   BI bi;
   if (!batch_map(d, t, active, q, bi)) return;
   const DefectDesc& e = d[q];
+  if (e.iters) {
+    const int k = e.iters[e.r];
+    if (k == 0)
+      d_defect<false>(bi, e.ph, e.pl, e.e, e.ph, e.pl, e.fh, e.fl, e.rb, e.periodic, e.write_r,
+                      e.partial, e.counter, e.out, 6.0f, 0.0f);
+    else if (((k - 1) & 1) == 0)
+      d_defect<true>(bi, e.ph, e.pl, e.e, e.qh, e.ql, e.fh, e.fl, e.rb, e.periodic, e.write_r,
+                     e.partial, e.counter, e.out, 6.0f, 0.0f);
+    else
+      d_defect<true>(bi, e.qh, e.ql, e.e, e.ph, e.pl, e.fh, e.fl, e.rb, e.periodic, e.write_r,
+                     e.partial, e.counter, e.out, 6.0f, 0.0f);
+    return;
+  }
   if (e.correct)
     d_defect<true>(bi, e.ph, e.pl, e.e, e.qh, e.ql, e.fh, e.fl, e.rb, e.periodic, e.write_r,
                    e.partial, e.counter, e.out, 6.0f, 0.0f);
@@ -1018,12 +1099,53 @@ __global__ void __launch_bounds__(256) kb_defect(const DefectDesc* d, const BTab
     d_defect<false>(bi, e.ph, e.pl, e.e, e.qh, e.ql, e.fh, e.fl, e.rb, e.periodic, e.write_r,
                     e.partial, e.counter, e.out, 6.0f, 0.0f);
 }
+__global__ void kb_solve_init(int R, int* active, int* iters, int* failed) {
+  const int r = (int)threadIdx.x;
+  if (r < R) {
+    active[r] = 1;
+    iters[r] = 0;
+    failed[r] = 0;
+  }
+}
+__global__ void kb_converged(int R, const double* __restrict__ scal,
+                             const double* __restrict__ rtol, const int* __restrict__ maxv,
+                             int* active, int* iters, int* failed, double* rel,
+                             cudaGraphConditionalHandle loop) {
+  const int r = (int)threadIdx.x;
+  int on = 0;
+  if (r < R && active[r]) {
+    const double f2 = scal[16 * r], r2 = scal[16 * r + 11];
+    const double v = f2 > 0.0 ? sqrt(r2 / f2) : 0.0;
+    rel[r] = v;
+    if (v <= rtol[r] || f2 == 0.0) {
+      active[r] = 0;
+    } else if (iters[r] >= maxv[r]) {
+      active[r] = 0;
+      failed[r] = 1;
+    } else {
+      iters[r] += 1;
+      on = 1;
+    }
+  }
+  const int any = __syncthreads_or(on);
+  if (r == 0) cudaGraphSetConditional(loop, any ? 1u : 0u);
+}
+void launch_solve_init_b(cudaStream_t st, int R, int* active, int* iters, int* failed) {
+  kb_solve_init<<<1, MAX_REAL, 0, st>>>(R, active, iters, failed);
+  note_launch();
+}
+void launch_converged_b(cudaStream_t st, int R, const double* scal, const double* rtol,
+                        const int* maxv, int* active, int* iters, int* failed, double* rel,
+                        cudaGraphConditionalHandle loop) {
+  kb_converged<<<1, MAX_REAL, 0, st>>>(R, scal, rtol, maxv, active, iters, failed, rel, loop);
+  note_launch();
+}
 __global__ void __launch_bounds__(256) kb_predict(const PredictDesc* d, const BTable* t) {
   int q;
   BI bi;
   if (!batch_map(d, t, (const int*)nullptr, q, bi)) return;
   const PredictDesc& e = d[q];
-  d_predict(bi, e.ph, e.pl, e.qh, e.ql, e.w, e.pair);
+  each_plane(bi, e.ph.s, [&](const BI& b) { d_predict(b, e.ph, e.pl, e.qh, e.ql, e.w, e.pair); });
 }
 
 void launch_rbgs_b(cudaStream_t st, int grid, const RbgsDesc* d, const BTable* t,
@@ -1056,6 +1178,9 @@ void launch_predict_b(cudaStream_t st, int grid, const PredictDesc* d, const BTa
   note_launch();
 }
 
+// the grid of a batched pass over s planes: BZ planes per block
+static inline dim3 zchunk(dim3 g) { return dim3(g.x, g.y, (g.z + BZ - 1) / BZ); }
+
 dim3 rbgs_grid(int s) { return grid_half(s); }
 // the colour pass with bx x by blocks: each thread takes two cells of its
 // colour in a row, so a row needs ceil(s/4) threads
@@ -1065,6 +1190,8 @@ dim3 rbgs_grid(int s, int bx, int by) {
 }
 dim3 full_grid(int s) { return grid_full(s); }
 dim3 defect_grid(int s) { return grid_defect(s); }
+dim3 rbgs_grid_b(int s, int bx, int by) { return zchunk(rbgs_grid(s, bx, by)); }
+dim3 full_grid_b(int s) { return zchunk(grid_full(s)); }
 
 // ---------------------------------------------------------------------------
 // Persistent batched solve.  One cooperative launch (all blocks resident)
@@ -1236,24 +1363,34 @@ __global__ void __launch_bounds__(SOLVE_NT, MINB) kb_solve(SolveArgs a) {
       if (S.kind == SLOT_RBGS) {
         each_block((const RbgsDesc*)S.d, S.t, act, s_off,
                    [&](const RbgsDesc& e, const BI& bi) {
-                     d_rbgs(bi, e.u, e.b, e.h2, e.color, e.periodic, e.gam, e.zero_start, 6.0f);
+                     each_plane(bi, e.u.s, [&](const BI& b) {
+                       d_rbgs(b, e.u, e.b, e.h2, e.color, e.periodic, e.gam, e.zero_start, 6.0f);
+                     });
                    });
       } else if (S.kind == SLOT_RESTRICT) {
         each_block((const RestrictDesc*)S.d, S.t, act, s_off,
                    [&](const RestrictDesc& e, const BI& bi) {
-                     d_resid_restrict(bi, e.u, e.b, e.inv_h2, e.uc, e.bc, e.periodic, e.gam,
-                                      6.0f);
+                     each_plane(bi, e.uc.s, [&](const BI& b) {
+                       d_resid_restrict(b, e.u, e.b, e.inv_h2, e.uc, e.bc, e.periodic, e.gam,
+                                        6.0f);
+                     });
                    });
       } else if (S.kind == SLOT_PROLONG) {
         each_block((const ProlongDesc*)S.d, S.t, act, s_off,
                    [&](const ProlongDesc& e, const BI& bi) {
-                     d_prolong(bi, e.uc, e.u, e.periodic, e.gam_c);
+                     each_plane(bi, e.u.s,
+                                [&](const BI& b) { d_prolong(b, e.uc, e.u, e.periodic, e.gam_c); });
                    });
       } else {  // SLOT_CMG: the coarse levels of one realisation per block
         const CmgDesc* cd = (const CmgDesc*)S.d;
         for (int q = (int)blockIdx.x; q < S.n; q += (int)gridDim.x) {
           const CmgDesc& e = cd[q];
           if (!act[e.r]) continue;
+          if (a.fast_coarse && fc_supported(e.u.s)) {
+            fc_vcycle<SOLVE_NT>(cc_sm, red, e.u, e.b, e.level, e.periodic, e.sweeps, e.zero_top,
+                                0.0f);
+            continue;
+          }
           if (tid == 0) Cc<1, SOLVE_NT>::init_levels(lev, nlev, e.u.s, e.level, e.periodic, 0.0f);
           __syncthreads();
           Cc<1, SOLVE_NT> c;
@@ -1285,7 +1422,7 @@ __global__ void __launch_bounds__(SOLVE_NT, MINB) kb_solve(SolveArgs a) {
   });
 }
 
-int solve_smem() { return (int)sizeof(float) * cc_layout(cmg_top_side(1), 1).floats; }
+int solve_smem() { return cmg_smem_bytes(cmg_top_side(1)); }
 
 // blocks per SM the kernel is compiled for: 2 (no register spill) by
 // default, 4 with PM_SOLVE_MINB=4

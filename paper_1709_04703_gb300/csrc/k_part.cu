@@ -660,7 +660,8 @@ __global__ void __launch_bounds__(256) kb_grad(const GradDesc* d, const BTable* 
   BI bi;
   if (!batch_map(d, t, (const int*)nullptr, q, bi)) return;
   const GradDesc& e = d[q];
-  d_grad(bi, e.ph, e.pl, e.n, e.lo, e.s, e.periodic, e.G);
+  const bool alt = e.flip && (e.flip[e.r] & 1);
+  d_grad(bi, alt ? e.ph_alt : e.ph, alt ? e.pl_alt : e.pl, e.n, e.lo, e.s, e.periodic, e.G);
 }
 __global__ void __launch_bounds__(KT) kb_gather(const GatherDesc* d, const BTable* t) {
   int q;

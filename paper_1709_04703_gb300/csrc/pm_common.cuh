@@ -11,16 +11,113 @@ namespace pm {
 // A cubic grid level: `base` points at interior cell (0,0,0); neighbours are
 // at +-1 (x), +-sy (y), +-sz (z).  Cells -1 and s along each axis are the
 // ghost layer (open boundaries) and always exist in memory.
+//
+// The ball solve's mask (mbase != 0).  Level 0 (mstep = 2): the unknowns are
+// the cells whose centre lies within R_M of the ball's centre c; twice a
+// centre's offset from c along an axis is the odd integer mbase + 2 i
+// (mbase = 2 lo + 1 - n for the cube's origin lo on the n^3 mesh), and the
+// cell is in the mask iff the three squares sum to at most mr = floor(4
+// R_M^2).  Coarse level l (mstep = 2^(l+1)): the cells whose centre lies
+// within R_M (mrm2 = R_M^2, fine-cell units); their boundary conditions put
+// the correction's zero where the finest level has it, on the sphere of
+// radius R_M + 1/2 (mrb2) or the cube's ghost plane (ball_gam).
 struct Grid {
   float* base;
   int s;
   int sy;
   int sz;
+  int mbase, mstep, mr;
+  float mrm2, mrb2;
 };
 
 __host__ __device__ inline int gidx(const Grid& g, int i, int j, int k) {
   return i + j * g.sy + k * g.sz;
 }
+
+__host__ __device__ inline int mask_axis(int mbase, int mstep, int i) {
+  const int a0 = mbase + i * mstep, a1 = a0 + mstep - 2;
+  return a0 > 0 ? a0 : (a1 < 0 ? -a1 : 1);
+}
+// centre of cell i of a masked level along an axis, fine-cell units from c
+__host__ __device__ inline float mask_centre(const Grid& g, int i) {
+  return 0.5f * (float)(g.mbase + i * g.mstep + (g.mstep >> 1) - 1);
+}
+// cell (i, j, k) is an unknown: always without a mask; outside the level's
+// cube never
+__host__ __device__ inline bool g_in(const Grid& g, int i, int j, int k) {
+  if (g.mbase == 0) return true;
+  if (i < 0 || j < 0 || k < 0 || i >= g.s || j >= g.s || k >= g.s) return false;
+  if (g.mstep == 2) {
+    const int x = mask_axis(g.mbase, 2, i), y = mask_axis(g.mbase, 2, j);
+    const int z = mask_axis(g.mbase, 2, k);
+    return x * x + y * y + z * z <= g.mr;
+  }
+  const float x = mask_centre(g, i), y = mask_centre(g, j), z = mask_centre(g, k);
+  return x * x + y * y + z * z <= g.mrm2;
+}
+// Coarse ghost factor of mask cell (i, j, k) toward its neighbour along
+// `axis` (0 x, 1 y, 2 z) on side sgn (+-1) when that neighbour is outside the
+// mask: the ghost holds -gam times the cell's value, so that the linear
+// profile through the cell centre vanishes at distance t, where the finest
+// level's boundary lies (the sphere of radius R_M + 1/2, or the cube's ghost
+// plane): gam = H / t - 1 for spacing H, at least 0.  On a cube face without
+// a ball this is the cube's (H - 1) / (H + 1).
+__host__ __device__ inline float ball_gam(const Grid& g, int i, int j, int k, int axis, int sgn) {
+  const float H = (float)(g.mstep >> 1);
+  const float cx = mask_centre(g, i), cy = mask_centre(g, j), cz = mask_centre(g, k);
+  const float ca = axis == 0 ? cx : (axis == 1 ? cy : cz);
+  const float o1 = axis == 0 ? cy : cx, o2 = axis == 2 ? cy : cz;
+  const float ts = sqrtf(fmaxf(g.mrb2 - o1 * o1 - o2 * o2, 0.0f)) - (float)sgn * ca;
+  const float lo_plane = 0.5f * (float)(g.mbase - 2);
+  const float hi_plane = 0.5f * (float)(g.mbase + 2 * g.s * (g.mstep >> 1));
+  const float tc = sgn > 0 ? hi_plane - ca : ca - lo_plane;
+  const float t = fminf(ts, tc);
+  return t > 0.0f ? fmaxf(H / t - 1.0f, 0.0f) : 0.0f;
+}
+// the diagonal of a coarse mask cell: 6 plus the ghost factors of its
+// neighbours outside the mask
+__host__ __device__ inline float ball_diag(const Grid& g, int i, int j, int k) {
+  // a cell more than one spacing inside the ball has its neighbours inside
+  {
+    const float H = (float)(g.mstep >> 1);
+    const float x = mask_centre(g, i), y = mask_centre(g, j), z = mask_centre(g, k);
+    const float rin = sqrtf(g.mrm2) - H;
+    const float lo_plane = 0.5f * (float)(g.mbase - 2);
+    const float hi_plane = 0.5f * (float)(g.mbase + 2 * g.s * (g.mstep >> 1));
+    if (rin > 0.0f && x * x + y * y + z * z < rin * rin && fminf(fminf(x, y), z) - H > lo_plane &&
+        fmaxf(fmaxf(x, y), z) + H < hi_plane)
+      return 6.0f;
+  }
+  float d = 6.0f;
+  if (!g_in(g, i - 1, j, k)) d += ball_gam(g, i, j, k, 0, -1);
+  if (!g_in(g, i + 1, j, k)) d += ball_gam(g, i, j, k, 0, 1);
+  if (!g_in(g, i, j - 1, k)) d += ball_gam(g, i, j, k, 1, -1);
+  if (!g_in(g, i, j + 1, k)) d += ball_gam(g, i, j, k, 1, 1);
+  if (!g_in(g, i, j, k - 1)) d += ball_gam(g, i, j, k, 2, -1);
+  if (!g_in(g, i, j, k + 1)) d += ball_gam(g, i, j, k, 2, 1);
+  return d;
+}
+// The planes [k0, k1) of column (i, j) of a masked level-0 grid that hold
+// mask cells (k0 >= k1: none): |mbase + 2 k| <= A, A the largest odd
+// integer whose square is at most mr minus the column's x and y squares.
+__host__ __device__ inline void mask_column(const Grid& g, int i, int j, int& k0, int& k1) {
+  const int x = mask_axis(g.mbase, 2, i), y = mask_axis(g.mbase, 2, j);
+  const int rem = g.mr - x * x - y * y;
+  if (rem < 1) {
+    k0 = 0;
+    k1 = 0;
+    return;
+  }
+  int A = (int)sqrtf((float)rem);
+  while (A * A > rem) --A;
+  while ((A + 1) * (A + 1) <= rem) ++A;
+  if (!(A & 1)) --A;  // offsets are odd
+  // mbase + 2 k in [-A, A]; mbase and A are odd, so both ends are exact
+  k0 = (-A - g.mbase) / 2;
+  k1 = (A - g.mbase) / 2 + 1;
+}
+// a masked coarse level (its cells' diagonal is ball_diag)
+__host__ __device__ inline bool ball_coarse(const Grid& g) { return g.mbase != 0 && g.mstep > 2; }
 
 // The same view of a double grid (the FP64 solve)
 struct GridD {
@@ -196,6 +293,21 @@ struct BTable {
   int m;                       // members
   int off[MAX_MEMBERS + 1];    // cumulative block counts
 };
+
+// Planes per block of the batched mesh passes (colour pass, restriction,
+// prolongation, warm-start prediction): a block's table lookup is shared by
+// BZ planes of its (x, y) tile.
+constexpr int BZ = 4;
+template <class F>
+__device__ __forceinline__ void each_plane(const BI& bi, int nz, F&& f) {
+#pragma unroll 1
+  for (int kk = 0; kk < BZ; ++kk) {
+    BI b = bi;
+    b.z = bi.z * BZ + kk;
+    if (b.z >= nz) break;
+    f(b);
+  }
+}
 
 // The block of a batched launch -> member q of the table and its block
 // coordinates (false: past the table's blocks, or an inactive realisation).

@@ -90,6 +90,11 @@ void launch_diff_rhs(cudaStream_t st, int grid, Grid sh, Grid sl, double scale, 
                      double* partial, unsigned int* counter, double* out);
 // Dirichlet ghost values of the open boundary into (ph, pl), and into
 // (*ph2, *pl2) as well when they are given
+// The ball solve's boundary values (multipoles mom, source factor S) at the
+// cells of the padded cube outside the mask of ph (its mask fields), in both
+// potential buffers.
+void launch_ball_ghosts(cudaStream_t st, Grid ph, Grid pl, Grid ph2, Grid pl2, int n, int lo,
+                        const double* mom, double S);
 void launch_boundary(cudaStream_t st, Grid ph, Grid pl, int n, int lo, const double* mom,
                      double S, bool want_lo, const Grid* ph2 = nullptr,
                      const Grid* pl2 = nullptr);
@@ -106,6 +111,11 @@ void launch_rbgs(cudaStream_t st, Grid u, Grid b, float h2, int color, int perio
 cudaError_t cmg_prepare();
 int cmg_cluster();
 int cmg_top_side(int cl);
+// dynamic shared memory of a coarse-level launch from tops up to `top`, and
+// whether one-CTA tops <= 16 take the constant-side form (cmg_fast.cuh; 0
+// with PM_CMG_GENERIC set: the generic form, the same bits)
+int cmg_smem_bytes(int top);
+int cmg_fast();
 void launch_cmg(cudaStream_t st, Grid u, Grid b, int level, int periodic, int sweeps,
                 bool zero_top, float sig0);
 void launch_resid_restrict(cudaStream_t st, Grid u, Grid b, float inv_h2, Grid uc, Grid bc,
@@ -236,6 +246,11 @@ struct DefectDesc {
   double* partial;
   unsigned int* counter;
   double* out;
+  // a solve decided on the device: ph/pl the buffer it started in, qh/ql the
+  // other, iters[r] the V-cycles run so far; after V-cycle k >= 1 the
+  // correction moves the potential from the buffer of parity k - 1 into that
+  // of parity k (iters NULL: `correct` decides)
+  const int* iters;
   int r, gx, gy, gz;
 };
 struct PredictDesc {
@@ -283,6 +298,7 @@ struct BoundaryDesc {
 // ran are odd in number)
 struct GradDesc {
   const float *ph, *pl, *ph_alt, *pl_alt;
+  const int* flip;  // the graph solve: (ph_alt, pl_alt) where flip[r] is odd
   int n, lo, s, periodic;
   float4* G;
   int r, gx, gy, gz;
@@ -370,7 +386,18 @@ struct SolveArgs {
   unsigned long long limit_ns;  // longest wait at one barrier
   int extra;              // arrivals a barrier waits for beyond the grid (0; > 0 only to
                           // test the time limit: no barrier then completes)
+  int fast_coarse;        // cmg_fast()
 };
+// The graph form of a device-decided batched solve: kb_solve_init marks the
+// R realisations active with no V-cycles run; kb_converged (after each
+// batched defect) takes each active realisation's decision as a single
+// context's host loop does (stop at ||r|| / ||f|| <= rtol or f = 0, fail at
+// max_vcycles, else count the next V-cycle) and sets the conditional handle
+// of the graph's while loop to whether any realisation is still active.
+void launch_solve_init_b(cudaStream_t st, int R, int* active, int* iters, int* failed);
+void launch_converged_b(cudaStream_t st, int R, const double* scal, const double* rtol,
+                        const int* maxv, int* active, int* iters, int* failed, double* rel,
+                        cudaGraphConditionalHandle loop);
 // blocks of one persistent solve launch (all co-resident), and its launch
 int solve_grid_b();
 cudaError_t launch_solve_b(cudaStream_t st, const SolveArgs& a);
@@ -390,6 +417,10 @@ dim3 rbgs_grid(int s);
 dim3 rbgs_grid(int s, int bx, int by);
 dim3 full_grid(int s);
 dim3 defect_grid(int s);
+// grids of the batched colour pass, restriction, prolongation and
+// prediction tables (BZ planes per block)
+dim3 rbgs_grid_b(int s, int bx, int by);
+dim3 full_grid_b(int s);
 dim3 source_grid(int s);
 int boundary_blocks(int s);
 int deposit_blocks(long long N);

@@ -207,7 +207,8 @@ class Sim:
         cfg.gravity = _GRAVITY[gravity]
         cfg.c_eff_factor = float(c_eff_factor)
         cfg.assignment = {"cic": L.PM_ASSIGN_CIC, "tsc": L.PM_ASSIGN_TSC}[assignment]
-        cfg.domain = {"cube": L.PM_DOMAIN_CUBE, "sphere": L.PM_DOMAIN_SPHERE}[domain]
+        cfg.domain = {"cube": L.PM_DOMAIN_CUBE, "sphere": L.PM_DOMAIN_SPHERE,
+                      "ball": L.PM_DOMAIN_BALL}[domain]
         cfg.sort_every = int(sort_every)
         cfg.inner_vcycles = int(inner_vcycles)
         self.cfg = cfg

@@ -184,11 +184,11 @@ def test_batch_against_oracle():
 
 
 def test_persistent_solve_matches_graph_solve():
-    """The persistent solve (one cooperative launch per solve, convergence
-    decided on the device) and the V-cycle graph with the host's decisions
-    give the same bits and V-cycle counts, in both phases; the persistent
-    step makes at most 8 launches (deposit, source, boundary, predict,
-    solve, gather, scan, scatter)."""
+    """The two device-decided solves, the persistent cooperative kernel and
+    the graph whose V-cycle loop is a conditional while node, give the same
+    bits and V-cycle counts, in both phases; the persistent step makes at
+    most 8 launches (deposit, source, boundary, predict, solve, gather,
+    scan, scatter)."""
     from paper_1709_04703_gb300 import _lib as L
     from paper_1709_04703_gb300.sim import Batch
     a0, a1, steps, rtol = 0.02, 1.0, 6, 1e-7
@@ -196,6 +196,7 @@ def test_persistent_solve_matches_graph_solve():
              _realisation(64, 12000.0, 122, a0)]
     lib = L.load()
     per = Batch(reals, a0, a1, steps, rtol=rtol)
+    per.set_solve(persistent=True)
     counts, phases = [], set()
     for _ in range(steps):
         l0 = lib.pm_launch_count()
@@ -203,7 +204,6 @@ def test_persistent_solve_matches_graph_solve():
         counts.append(lib.pm_launch_count() - l0)
         phases |= {per.stats(r)["periodic"] for r in range(len(reals))}
     gra = Batch(reals, a0, a1, steps, rtol=rtol)
-    gra.set_solve(persistent=False)
     g0 = lib.pm_launch_count()
     gra.step(steps)
     g_launches = lib.pm_launch_count() - g0

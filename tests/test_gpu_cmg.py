@@ -107,3 +107,53 @@ def test_cluster_run_is_bitwise():
     b = _with_cluster(False, run)
     for u, v in zip(a, b):
         np.testing.assert_array_equal(u, v)
+
+
+def _with_generic(on, fn):
+    old = os.environ.pop("PM_CMG_GENERIC", None)
+    if on:
+        os.environ["PM_CMG_GENERIC"] = "1"
+    try:
+        return fn()
+    finally:
+        os.environ.pop("PM_CMG_GENERIC", None)
+        if old is not None:
+            os.environ["PM_CMG_GENERIC"] = old
+
+
+@pytest.mark.parametrize("n,bc", [(64, "periodic"), (64, "open"), (96, "periodic"),
+                                  (96, "open"), (48, "open"), (24, "periodic"),
+                                  (16, "open"), (16, "periodic"), (12, "open"),
+                                  (12, "periodic"), (8, "open"), (6, "periodic"),
+                                  (4, "open"), (4, "periodic")])
+def test_constant_side_coarse_form_is_bitwise(n, bc):
+    """The one-CTA coarse levels with compile-time sides and ghost halos
+    (cmg_fast.cuh) against the generic one-CTA form (PM_CMG_GENERIC): tops
+    16, 12, 8, 6 and 4, bottoms 4 and 3, the top as the whole mesh (n <= 16:
+    the Dirichlet data in the top's halo) or a coarse level."""
+    a, va, ra, _ = _with_cluster(False, lambda: _with_generic(False,
+                                                              lambda: _potential(n, bc, n)))
+    b, vb, rb, _ = _with_cluster(False, lambda: _with_generic(True,
+                                                              lambda: _potential(n, bc, n)))
+    assert va == vb and ra == rb
+    np.testing.assert_array_equal(a.view(np.uint64), b.view(np.uint64))
+
+
+def test_constant_side_coarse_form_run_is_bitwise():
+    """A 64^3 run through the periodic phase into shrinking open cubes whose
+    coarse tops include 14 and 10 (bottoms 7 and 5): the same particles,
+    lightcone and V-cycle counts with either one-CTA form."""
+    from paper_1709_04703_gb300.sim import Sim
+    n = 64
+    pos, mom, ids = ics.zeldovich(n, -1.5, 0.5, 9, 0.35, rms_disp=0.5)
+
+    def run():
+        sim = Sim(pos, mom, ids, n, 7000.0, 0.35, 1.0, 14, rtol=1e-7)
+        sim.step(14)
+        out = sim.particles() + sim.lightcone()[:3] + (sim.stats()["vcycles_total"],)
+        sim.close()
+        return out
+    a = _with_cluster(False, lambda: _with_generic(False, run))
+    b = _with_cluster(False, lambda: _with_generic(True, run))
+    for u, v in zip(a, b):
+        np.testing.assert_array_equal(u, v)
