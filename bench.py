@@ -540,9 +540,11 @@ def _timed_run(pos, mom, ids, n, box, a0, steps, rtol, gravity, shrink, domain="
     the fixed periodic box with the lightcone recorded (PM_SHRINK_RECORD)."""
     import torch
     from paper_1709_04703_gb300.sim import Sim
+    # (the headline's solver: INNER FP32 V-cycles per defect, as --inner sets)
+    inner = INNER if gravity == "poisson" and domain != "ball" else 1
     sim = Sim(pos, mom, ids, n, box, a0, 1.0, steps, rtol=rtol, precision="mixed",
               max_vcycles=100, gravity=gravity, bc="paper" if shrink else "periodic",
-              shrink=True if shrink else "record", domain=domain)
+              shrink=True if shrink else "record", domain=domain, inner_vcycles=inner)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     n_act = []
     torch.cuda.synchronize()
@@ -682,16 +684,23 @@ def run_ours(args):
     sim = _new_sim(pos, mom, ids, cfg, rtol, args.precision)
     prof, per_step = None, []
     p0 = time.perf_counter()
+    lib = L.load()
     for k0, cnt in windows:
         gap = k0 - sim.stats()["step"]
         if gap > 0:
             sim.step(gap)
         sim.profile(True)
+        torch.cuda.synchronize()
+        l_start = lib.pm_launch_count()
         for _ in range(cnt):
             n_act = sim.stats()["n_active"]
             sim.step(1)
             s1 = sim.stats()
             per_step.append((n_act, s1["cube_side"] ** 3, s1["vcycles_last"]))
+        # the library's kernel launches of this window (for a launch list
+        # of exactly these steps: ncu -k regex:^k_ -s <start> -c <count>)
+        print(f"instrumented window from step {k0}: library launches {l_start} .. "
+              f"{lib.pm_launch_count() - 1}", file=sys.stderr, flush=True)
         part = sim.profile_read()
         sim.profile(False)
         prof = part if prof is None else {

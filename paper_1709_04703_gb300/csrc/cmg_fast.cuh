@@ -45,7 +45,8 @@ struct FcLev {
   bool simple;
 };
 
-template <int NT>
+// MASK: the ball solve's masked levels (compiled out of the unmasked form)
+template <int NT, bool MASK>
 struct Fc {
   int periodic, sweeps, lev0;
   float sig0;
@@ -62,7 +63,7 @@ struct Fc {
   }
   template <int S>
   __device__ bool in(int q, int i, int j, int k) const {
-    return gu.mbase == 0 || g_in(lvl(q, S), i, j, k);
+    return !MASK || g_in(lvl(q, S), i, j, k);
   }
 
   __device__ static int lt() { return (int)(threadIdx.x + threadIdx.y * blockDim.x); }
@@ -72,7 +73,7 @@ struct Fc {
     const float H = (float)(1 << (lev0 + q));
     v.h2 = H * H;
     v.inv_h2 = 1.0f / v.h2;
-    v.gam = gu.mbase ? 0.0f : (H - 1.0f) / (H + 1.0f);
+    v.gam = MASK ? 0.0f : (H - 1.0f) / (H + 1.0f);
     v.d0 = 6.0f + sig0 * v.h2;
     v.simple = mg_simple(periodic, v.gam, v.d0);
     return v;
@@ -96,12 +97,12 @@ struct Fc {
 
   template <int S>
   __device__ __forceinline__ float diag(const FcLev& L, int i, int j, int k, int q) const {
-    if (gu.mbase && (gu.mstep << q) > 2) return ball_diag(lvl(q, S), i, j, k);
+    if (MASK && (gu.mstep << q) > 2) return ball_diag(lvl(q, S), i, j, k);
     return L.simple ? 6.0f : mg_diag(i, j, k, S, periodic, L.gam, L.d0);
   }
   // the Gauss-Seidel value's form: exact x(1/6) only without a coarse mask
   __device__ bool simple(const FcLev& L, int q) const {
-    return L.simple && !(gu.mbase && (gu.mstep << q) > 2);
+    return L.simple && !(MASK && (gu.mstep << q) > 2);
   }
 
   // one colour of red-black Gauss-Seidel on an even level, two cells per
@@ -176,7 +177,7 @@ struct Fc {
       int I2 = (i & 1) ? I + 1 : I - 1, J2 = (j & 1) ? J + 1 : J - 1;
       int K2 = (k & 1) ? K + 1 : K - 1;
       float fx = 1.0f, fy = 1.0f, fz = 1.0f;
-      if (gu.mbase) {
+      if (MASK) {
         // the masked coarse level's own boundary; no correction where the
         // parent is outside its mask
         const Grid cg = lvl(q + 1, C);
@@ -346,10 +347,10 @@ struct Fc {
 
 // the V-cycle from a top of side S0 (fc_supported(S0)) in one CTA of NT
 // threads; sm holds fc_floats(FC_MAX_TOP) floats, red CC_NT / 32
-template <int NT>
+template <int NT, bool MASK>
 __device__ void fc_vcycle(float* sm, float* red, Grid u, Grid b, int level, int periodic,
                           int sweeps, int zero_top, float sig0) {
-  Fc<NT> f;
+  Fc<NT, MASK> f;
   f.periodic = periodic;
   f.sweeps = sweeps;
   f.lev0 = level;

@@ -25,7 +25,10 @@ __global__ void __launch_bounds__(CC_NT, 1) k_cmg(Grid u, Grid b, int level, int
   extern __shared__ float cc_sm[];
   __shared__ float red[CC_NT / 32];
   if (CL == 1 && (fast || u.mbase) && fc_supported(u.s)) {
-    fc_vcycle<CC_NT>(cc_sm, red, u, b, level, periodic, sweeps, zero_top, sig0);
+    if (u.mbase)
+      fc_vcycle<CC_NT, true>(cc_sm, red, u, b, level, periodic, sweeps, zero_top, sig0);
+    else
+      fc_vcycle<CC_NT, false>(cc_sm, red, u, b, level, periodic, sweeps, zero_top, sig0);
     return;
   }
   if (u.mbase) return;  // not reached: masked tops (q 2^j <= 16) are all supported
@@ -60,7 +63,8 @@ __global__ void __launch_bounds__(CC_NT, 1) kb_cmg(const CmgDesc* d, int n_desc,
   const CmgDesc& e = d[q];
   if (active && !active[e.r]) return;
   if (CL == 1 && fast && fc_supported(e.u.s)) {
-    fc_vcycle<CC_NT>(cc_sm, red, e.u, e.b, e.level, e.periodic, e.sweeps, e.zero_top, 0.0f);
+    fc_vcycle<CC_NT, false>(cc_sm, red, e.u, e.b, e.level, e.periodic, e.sweeps, e.zero_top,
+                            0.0f);
     return;
   }
   __shared__ CcLevel lev[CC_MAXL];

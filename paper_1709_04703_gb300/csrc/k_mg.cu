@@ -20,6 +20,8 @@ namespace pm {
 // zero_start (red only): the iterate is known to be zero, so the red cells
 // take (-h^2 b)/diag without reading u; the black sweep after it reads only
 // red neighbours, so u needs no clearing before a V-cycle.
+// MASK: the ball solve's masked grids (compiled out of the unmasked form)
+template <bool MASK>
 __device__ __forceinline__ void d_rbgs(const BI& bi, Grid u, Grid b, float h2, int color,
                                               int periodic, float gam, int zero_start,
                                               float d0){
@@ -34,12 +36,12 @@ __device__ __forceinline__ void d_rbgs(const BI& bi, Grid u, Grid b, float h2, i
   const int i0 = 4 * t + ((j + k + color) & 1);
   const bool two = 2 * t + 1 < half;
   // the ball solve updates only the cells of its mask
-  const bool in0 = g_in(u, i0, j, k), in1 = two && g_in(u, i0 + 2, j, k);
-  if (!in0 && !in1) return;
+  const bool in0 = !MASK || g_in(u, i0, j, k), in1 = two && (!MASK || g_in(u, i0 + 2, j, k));
+  if (MASK && !in0 && !in1) return;
   const int ym = (wrap_m(j, s, periodic) - j) * u.sy, yp = (wrap_p(j, s, periodic) - j) * u.sy;
   const int zm = (wrap_m(k, s, periodic) - k) * u.sz, zp = (wrap_p(k, s, periodic) - k) * u.sz;
   // masked coarse levels of the ball solve: their own diagonal
-  const bool ballc = ball_coarse(u);
+  const bool ballc = MASK && ball_coarse(u);
   const bool simple = mg_simple(periodic, gam, d0) && !ballc;
   const int c0 = gidx(u, i0, j, k);
   const int bc0 = gidx(b, i0, j, k);
@@ -66,17 +68,19 @@ __device__ __forceinline__ void d_rbgs(const BI& bi, Grid u, Grid b, float h2, i
   if (in1) p0[2] = gs_value(s1, b1v, h2, simple, dg(i0 + 2));
 }
 
+template <bool MASK>
 __global__ void __launch_bounds__(256) k_rbgs(Grid u, Grid b, float h2, int color,
                                               int periodic, float gam, int zero_start, float d0) {
   pdl_wait();
   pdl_release();
-  d_rbgs(bi_native(), u, b, h2, color, periodic, gam, zero_start, d0);
+  d_rbgs<MASK>(bi_native(), u, b, h2, color, periodic, gam, zero_start, d0);
 }
 
 // ---------------------------------------------------------------------------
 // Residual r = b - (sum_nb u - 6u)/h^2 on the 8 children of each coarse cell,
 // averaged into the coarse right-hand side; the coarse unknown is zeroed.
 // ---------------------------------------------------------------------------
+template <bool MASK>
 __device__ __forceinline__ void d_resid_restrict(const BI& bi, Grid u, Grid b, float inv_h2,
                                                         Grid uc, Grid bc, int periodic,
                                                         float gam, float d0){
@@ -121,12 +125,12 @@ __device__ __forceinline__ void d_resid_restrict(const BI& bi, Grid u, Grid b, f
         const float xm = dx ? V[dz][dy][0] : XM[dz][dy], xp = dx ? XP[dz][dy] : V[dz][dy][1];
         const float ym = dy ? V[dz][0][dx] : YM[dz][dx], yp = dy ? YP[dz][dx] : V[dz][1][dx];
         const float zm = dz ? V[0][dy][dx] : ZM[dy][dx], zp = dz ? ZP[dy][dx] : V[1][dy][dx];
-        float diag = ball_coarse(u) ? ball_diag(u, i, j, k)
+        float diag = (MASK && ball_coarse(u)) ? ball_diag(u, i, j, k)
                      : mg_simple(periodic, gam, d0) ? 6.0f
                                                     : mg_diag(i, j, k, s, periodic, gam, d0);
         float s0 = nb6(xm, xp, ym, yp, zm, zp);
         // children outside the ball solve's mask carry no residual
-        if (g_in(u, i, j, k))
+        if (!MASK || g_in(u, i, j, k))
           acc = __fadd_rn(acc, resid_value(s0, V[dz][dy][dx], b.base[gidx(b, i, j, k)], diag,
                                            inv_h2));
       }
@@ -135,12 +139,13 @@ __device__ __forceinline__ void d_resid_restrict(const BI& bi, Grid u, Grid b, f
   uc.base[cc] = 0.0f;
 }
 
+template <bool MASK>
 __global__ void __launch_bounds__(256) k_resid_restrict(Grid u, Grid b, float inv_h2,
                                                         Grid uc, Grid bc, int periodic,
                                                         float gam, float d0) {
   pdl_wait();
   pdl_release();
-  d_resid_restrict(bi_native(), u, b, inv_h2, uc, bc, periodic, gam, d0);
+  d_resid_restrict<MASK>(bi_native(), u, b, inv_h2, uc, bc, periodic, gam, d0);
 }
 
 // ---------------------------------------------------------------------------
@@ -192,15 +197,16 @@ __device__ __forceinline__ bool prolong_value_ball(Grid uc, int i, int j, int k,
   return true;
 }
 
+template <bool MASK>
 __device__ __forceinline__ void d_prolong(const BI& bi, Grid uc, Grid u, int periodic,
                                                  float gam_c){
   const int s = u.s;
   int i = bi.x * blockDim.x + threadIdx.x;
   int j = bi.y * blockDim.y + threadIdx.y;
   int k = bi.z;
-  if (i >= s || j >= s || !g_in(u, i, j, k)) return;
+  if (i >= s || j >= s || (MASK && !g_in(u, i, j, k))) return;
   float* p = u.base + gidx(u, i, j, k);
-  if (uc.mbase) {
+  if (MASK && uc.mbase) {
     float v;
     if (prolong_value_ball(uc, i, j, k, v)) *p = __fadd_rn(*p, v);
     return;
@@ -208,11 +214,12 @@ __device__ __forceinline__ void d_prolong(const BI& bi, Grid uc, Grid u, int per
   *p = __fadd_rn(*p, prolong_value(uc, i, j, k, periodic, gam_c));
 }
 
+template <bool MASK>
 __global__ void __launch_bounds__(256) k_prolong(Grid uc, Grid u, int periodic,
                                                  float gam_c) {
   pdl_wait();
   pdl_release();
-  d_prolong(bi_native(), uc, u, periodic, gam_c);
+  d_prolong<MASK>(bi_native(), uc, u, periodic, gam_c);
 }
 
 // out-of-place form: w = u + P uc (w and u may be different layouts).  One
@@ -348,7 +355,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // four stages of step t all update the cell at offset r(t) (the colours
 // alternate along z), and the register ring of six planes is renamed
 // statically by unrolling the step loop six times.
-template <bool PERIODIC, bool SIMPLE, bool ZERO>
+template <bool PERIODIC, bool SIMPLE, bool ZERO, bool MASK>
 struct Rbgs2 {
   static constexpr int RING = 6;
   const Grid win, wout, b;
@@ -450,7 +457,7 @@ struct Rbgs2 {
       const int m = 4 - st;
       const int q = (J + m) % RING, qm = (J + m - 1) % RING, qp = (J + m + 1) % RING;
       // (the ball solve updates only the cells of its mask, carried by b)
-      if (((act >> (3 - st)) & 1u) && (b.mbase == 0 || g_in(b, xa + kc, y, p))) {
+      if (((act >> (3 - st)) & 1u) && (!MASK || g_in(b, xa + kc, y, p))) {
         float* c = sp + (p & (F2_R - 1)) * F2_PL + me + kc;
         const float xv = c[xo], ym = c[-F2_W], yp = c[F2_W];
         float nv;
@@ -484,7 +491,7 @@ struct Rbgs2 {
   }
 };
 
-template <bool PERIODIC, bool SIMPLE, bool ZERO>
+template <bool PERIODIC, bool SIMPLE, bool ZERO, bool MASK>
 __global__ void __launch_bounds__(F2_NT, 2) k_rbgs2(Grid win, Grid wout, Grid b, float h2,
                                                     float gam, float d0, int zc) {
   pdl_wait();
@@ -493,7 +500,7 @@ __global__ void __launch_bounds__(F2_NT, 2) k_rbgs2(Grid win, Grid wout, Grid b,
   const int s = wout.s;
   const int ly = threadIdx.x / F2_PW, lx0 = 2 * (threadIdx.x - ly * F2_PW);
   const int x0 = blockIdx.x * F2_TX, y0 = blockIdx.y * F2_TY, z0 = blockIdx.z * zc;
-  if (b.mbase) {
+  if (MASK) {
     // the ball solve (level 0): a tile without a mask cell has nothing to
     // update, and the iterate is zero outside the mask in every buffer
     auto lo2 = [&](int a, int n) {  // smallest |offset| over cells a .. a + n - 1
@@ -503,7 +510,7 @@ __global__ void __launch_bounds__(F2_NT, 2) k_rbgs2(Grid win, Grid wout, Grid b,
     const int dx = lo2(x0, F2_TX), dy = lo2(y0, F2_TY), dz = lo2(z0, zc);
     if (dx * dx + dy * dy + dz * dz > b.mr) return;
   }
-  Rbgs2<PERIODIC, SIMPLE, ZERO> g{win, wout, b, h2, gam, d0, s, x0, y0, z0, min(z0 + zc, s), ly,
+  Rbgs2<PERIODIC, SIMPLE, ZERO, MASK> g{win, wout, b, h2, gam, d0, s, x0, y0, z0, min(z0 + zc, s), ly,
                                   lx0, y0 - F2_H + ly, x0 - F2_H + lx0, ly * F2_W + lx0};
   g.sp = f2_smem;
   g.pu = g.sp + F2_R * F2_PL;
@@ -582,14 +589,16 @@ cudaError_t mg_prepare() {
                                          (int)F2_SMEM);
     if (r != cudaSuccess) e = r;
   };
-  set(k_rbgs2<false, false, false>);
-  set(k_rbgs2<false, false, true>);
-  set(k_rbgs2<false, true, false>);
-  set(k_rbgs2<false, true, true>);
-  set(k_rbgs2<true, true, false>);
-  set(k_rbgs2<true, true, true>);
-  set(k_rbgs2<true, false, false>);
-  set(k_rbgs2<true, false, true>);
+  set(k_rbgs2<false, false, false, false>);
+  set(k_rbgs2<false, false, true, false>);
+  set(k_rbgs2<false, true, false, false>);
+  set(k_rbgs2<false, true, true, false>);
+  set(k_rbgs2<true, true, false, false>);
+  set(k_rbgs2<true, true, true, false>);
+  set(k_rbgs2<true, false, false, false>);
+  set(k_rbgs2<true, false, true, false>);
+  set(k_rbgs2<false, true, false, true>);  // the ball solve's level 0
+  set(k_rbgs2<false, true, true, true>);
   if (e == cudaSuccess) e = cmg_prepare();
   return e;
 }
@@ -609,8 +618,15 @@ void launch_rbgs2(cudaStream_t st, Grid win, Grid wout, Grid b, float h2, int pe
             (unsigned)((wout.s + zc - 1) / zc));
   const bool simple = (periodic || gam == 0.0f) && d0 == 6.0f;
 #define PM_RBGS2(P, S, Z) \
-  launch_pdl(k_rbgs2<P, S, Z>, grid, dim3(F2_NT), F2_SMEM, st, win, wout, b, h2, gam, d0, zc)
-  if (periodic && simple) {
+  launch_pdl(k_rbgs2<P, S, Z, false>, grid, dim3(F2_NT), F2_SMEM, st, win, wout, b, h2, gam, d0, zc)
+  if (b.mbase) {  // the ball solve's level 0 (open, diagonal 6); the mask comes with b
+    if (zero_start)
+      launch_pdl(k_rbgs2<false, true, true, true>, grid, dim3(F2_NT), F2_SMEM, st, win, wout, b, h2,
+                 gam, d0, zc);
+    else
+      launch_pdl(k_rbgs2<false, true, false, true>, grid, dim3(F2_NT), F2_SMEM, st, win, wout, b,
+                 h2, gam, d0, zc);
+  } else if (periodic && simple) {
     if (zero_start) PM_RBGS2(true, true, true); else PM_RBGS2(true, true, false);
   } else if (periodic) {
     if (zero_start) PM_RBGS2(true, false, true); else PM_RBGS2(true, false, false);
@@ -630,14 +646,22 @@ static inline dim3 grid_full(int s) { return dim3((unsigned)((s + 31) / 32), (un
 
 void launch_rbgs(cudaStream_t st, Grid u, Grid b, float h2, int color, int periodic,
                  float gam, bool zero_start, float d0) {
-  launch_pdl(k_rbgs, grid_half(u.s), dim3(32, 8), 0, st, u, b, h2, color, periodic, gam,
-             zero_start ? 1 : 0, d0);
+  if (u.mbase)
+    launch_pdl(k_rbgs<true>, grid_half(u.s), dim3(32, 8), 0, st, u, b, h2, color, periodic, gam,
+               zero_start ? 1 : 0, d0);
+  else
+    launch_pdl(k_rbgs<false>, grid_half(u.s), dim3(32, 8), 0, st, u, b, h2, color, periodic,
+               gam, zero_start ? 1 : 0, d0);
   note_launch();
 }
 void launch_resid_restrict(cudaStream_t st, Grid u, Grid b, float inv_h2, Grid uc, Grid bc,
                            int periodic, float gam, float d0) {
-  launch_pdl(k_resid_restrict, grid_full(uc.s), dim3(32, 8), 0, st, u, b, inv_h2, uc, bc,
-             periodic, gam, d0);
+  if (u.mbase)
+    launch_pdl(k_resid_restrict<true>, grid_full(uc.s), dim3(32, 8), 0, st, u, b, inv_h2, uc, bc,
+               periodic, gam, d0);
+  else
+    launch_pdl(k_resid_restrict<false>, grid_full(uc.s), dim3(32, 8), 0, st, u, b, inv_h2, uc,
+               bc, periodic, gam, d0);
   note_launch();
 }
 // ghost layer of src copied into d1 and d2 (same side, any layouts)
@@ -669,7 +693,10 @@ void launch_prolong_to(cudaStream_t st, Grid uc, Grid u, Grid w, int periodic, f
   note_launch();
 }
 void launch_prolong(cudaStream_t st, Grid uc, Grid u, int periodic, float gam_c) {
-  launch_pdl(k_prolong, grid_full(u.s), dim3(32, 8), 0, st, uc, u, periodic, gam_c);
+  if (u.mbase)
+    launch_pdl(k_prolong<true>, grid_full(u.s), dim3(32, 8), 0, st, uc, u, periodic, gam_c);
+  else
+    launch_pdl(k_prolong<false>, grid_full(u.s), dim3(32, 8), 0, st, uc, u, periodic, gam_c);
   note_launch();
 }
 
@@ -694,7 +721,7 @@ __device__ __forceinline__ float ldx(const float* p) {
   return __ldcg(p);
 }
 
-template <bool CORRECT, bool NC = true>
+template <bool CORRECT, bool NC = true, bool MASK = false>
 __device__ __forceinline__ void d_defect(const BI& bi, Grid ph, Grid pl, Grid e, Grid qh, Grid ql,
                                                 Grid fh, Grid fl, Grid rb, int periodic,
                                                 int write_r, double* __restrict__ partial,
@@ -708,7 +735,7 @@ __device__ __forceinline__ void d_defect(const BI& bi, Grid ph, Grid pl, Grid e,
   // k-1, k, k+1 (with the correction added) roll through registers
   const int chunk = (s + bi.gz - 1) / bi.gz;
   int k0 = bi.z * chunk, k1 = min(s, k0 + chunk);
-  if (ph.mbase && i < s && j < s) {
+  if (MASK && i < s && j < s) {
     // the ball solve: only the column's mask cells (outside, both potential
     // buffers hold the same boundary values, and no pass reads r there)
     int m0, m1;
@@ -838,7 +865,7 @@ __device__ __forceinline__ void d_defect(const BI& bi, Grid ph, Grid pl, Grid e,
   }
 }
 
-template <bool CORRECT>
+template <bool CORRECT, bool MASK>
 __global__ void __launch_bounds__(256) k_defect(Grid ph, Grid pl, Grid e, Grid qh, Grid ql,
                                                 Grid fh, Grid fl, Grid rb, int periodic,
                                                 int write_r, double* __restrict__ partial,
@@ -846,8 +873,8 @@ __global__ void __launch_bounds__(256) k_defect(Grid ph, Grid pl, Grid e, Grid q
                                                 float d0, float d0l) {
   pdl_wait();
   pdl_release();
-  d_defect<CORRECT>(bi_native(), ph, pl, e, qh, ql, fh, fl, rb, periodic, write_r, partial,
-                    counter, out, d0, d0l);
+  d_defect<CORRECT, true, MASK>(bi_native(), ph, pl, e, qh, ql, fh, fl, rb, periodic, write_r,
+                                partial, counter, out, d0, d0l);
 }
 
 static inline dim3 grid_defect(int s) {
@@ -862,12 +889,20 @@ void launch_defect(cudaStream_t st, Grid ph, Grid pl, const Grid* e, Grid qh, Gr
                    Grid fh, Grid fl, Grid rb, int periodic, bool write_r, double* partial,
                    unsigned int* counter, double* out, double d0) {
   const float d0h = (float)d0, d0l = (float)(d0 - (double)d0h);
-  if (e)
-    launch_pdl(k_defect<true>, grid_defect(ph.s), dim3(32, 8), 0, st, ph, pl, *e, qh, ql, fh, fl,
-               rb, periodic, write_r ? 1 : 0, partial, counter, out, d0h, d0l);
+  const int w = write_r ? 1 : 0;
+  const dim3 g = grid_defect(ph.s), blk(32, 8);
+  if (e && ph.mbase)
+    launch_pdl(k_defect<true, true>, g, blk, 0, st, ph, pl, *e, qh, ql, fh, fl, rb, periodic, w,
+               partial, counter, out, d0h, d0l);
+  else if (e)
+    launch_pdl(k_defect<true, false>, g, blk, 0, st, ph, pl, *e, qh, ql, fh, fl, rb, periodic, w,
+               partial, counter, out, d0h, d0l);
+  else if (ph.mbase)
+    launch_pdl(k_defect<false, true>, g, blk, 0, st, ph, pl, ph, qh, ql, fh, fl, rb, periodic, w,
+               partial, counter, out, d0h, d0l);
   else
-    launch_pdl(k_defect<false>, grid_defect(ph.s), dim3(32, 8), 0, st, ph, pl, ph, qh, ql, fh,
-               fl, rb, periodic, write_r ? 1 : 0, partial, counter, out, d0h, d0l);
+    launch_pdl(k_defect<false, false>, g, blk, 0, st, ph, pl, ph, qh, ql, fh, fl, rb, periodic, w,
+               partial, counter, out, d0h, d0l);
   note_launch();
 }
 
@@ -1052,7 +1087,7 @@ __global__ void __launch_bounds__(256) kb_rbgs(const RbgsDesc* d, const BTable* 
   if (!batch_map(d, t, active, q, bi)) return;
   const RbgsDesc& e = d[q];
   each_plane(bi, e.u.s, [&](const BI& b) {
-    d_rbgs(b, e.u, e.b, e.h2, e.color, e.periodic, e.gam, e.zero_start, 6.0f);
+    d_rbgs<false>(b, e.u, e.b, e.h2, e.color, e.periodic, e.gam, e.zero_start, 6.0f);
   });
 }
 __global__ void __launch_bounds__(256) kb_restrict(const RestrictDesc* d, const BTable* t,
@@ -1062,7 +1097,7 @@ __global__ void __launch_bounds__(256) kb_restrict(const RestrictDesc* d, const 
   if (!batch_map(d, t, active, q, bi)) return;
   const RestrictDesc& e = d[q];
   each_plane(bi, e.uc.s, [&](const BI& b) {
-    d_resid_restrict(b, e.u, e.b, e.inv_h2, e.uc, e.bc, e.periodic, e.gam, 6.0f);
+    d_resid_restrict<false>(b, e.u, e.b, e.inv_h2, e.uc, e.bc, e.periodic, e.gam, 6.0f);
   });
 }
 __global__ void __launch_bounds__(256) kb_prolong(const ProlongDesc* d, const BTable* t,
@@ -1071,7 +1106,8 @@ __global__ void __launch_bounds__(256) kb_prolong(const ProlongDesc* d, const BT
   BI bi;
   if (!batch_map(d, t, active, q, bi)) return;
   const ProlongDesc& e = d[q];
-  each_plane(bi, e.u.s, [&](const BI& b) { d_prolong(b, e.uc, e.u, e.periodic, e.gam_c); });
+  each_plane(bi, e.u.s,
+             [&](const BI& b) { d_prolong<false>(b, e.uc, e.u, e.periodic, e.gam_c); });
 }
 __global__ void __launch_bounds__(256, 4) kb_defect(const DefectDesc* d, const BTable* t,
                                                  const int* active) {
@@ -1364,14 +1400,15 @@ __global__ void __launch_bounds__(SOLVE_NT, MINB) kb_solve(SolveArgs a) {
         each_block((const RbgsDesc*)S.d, S.t, act, s_off,
                    [&](const RbgsDesc& e, const BI& bi) {
                      each_plane(bi, e.u.s, [&](const BI& b) {
-                       d_rbgs(b, e.u, e.b, e.h2, e.color, e.periodic, e.gam, e.zero_start, 6.0f);
+                       d_rbgs<false>(b, e.u, e.b, e.h2, e.color, e.periodic, e.gam,
+                                     e.zero_start, 6.0f);
                      });
                    });
       } else if (S.kind == SLOT_RESTRICT) {
         each_block((const RestrictDesc*)S.d, S.t, act, s_off,
                    [&](const RestrictDesc& e, const BI& bi) {
                      each_plane(bi, e.uc.s, [&](const BI& b) {
-                       d_resid_restrict(b, e.u, e.b, e.inv_h2, e.uc, e.bc, e.periodic, e.gam,
+                       d_resid_restrict<false>(b, e.u, e.b, e.inv_h2, e.uc, e.bc, e.periodic, e.gam,
                                         6.0f);
                      });
                    });
@@ -1379,7 +1416,9 @@ __global__ void __launch_bounds__(SOLVE_NT, MINB) kb_solve(SolveArgs a) {
         each_block((const ProlongDesc*)S.d, S.t, act, s_off,
                    [&](const ProlongDesc& e, const BI& bi) {
                      each_plane(bi, e.u.s,
-                                [&](const BI& b) { d_prolong(b, e.uc, e.u, e.periodic, e.gam_c); });
+                                [&](const BI& b) {
+                                  d_prolong<false>(b, e.uc, e.u, e.periodic, e.gam_c);
+                                });
                    });
       } else {  // SLOT_CMG: the coarse levels of one realisation per block
         const CmgDesc* cd = (const CmgDesc*)S.d;
@@ -1387,8 +1426,8 @@ __global__ void __launch_bounds__(SOLVE_NT, MINB) kb_solve(SolveArgs a) {
           const CmgDesc& e = cd[q];
           if (!act[e.r]) continue;
           if (a.fast_coarse && fc_supported(e.u.s)) {
-            fc_vcycle<SOLVE_NT>(cc_sm, red, e.u, e.b, e.level, e.periodic, e.sweeps, e.zero_top,
-                                0.0f);
+            fc_vcycle<SOLVE_NT, false>(cc_sm, red, e.u, e.b, e.level, e.periodic, e.sweeps,
+                                       e.zero_top, 0.0f);
             continue;
           }
           if (tid == 0) Cc<1, SOLVE_NT>::init_levels(lev, nlev, e.u.s, e.level, e.periodic, 0.0f);
