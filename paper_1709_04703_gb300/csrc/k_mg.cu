@@ -1463,11 +1463,12 @@ __global__ void __launch_bounds__(SOLVE_NT, MINB) kb_solve(SolveArgs a) {
 
 int solve_smem() { return cmg_smem_bytes(cmg_top_side(1)); }
 
-// blocks per SM the kernel is compiled for: 2 (no register spill) by
-// default, 4 with PM_SOLVE_MINB=4
+// blocks per SM the kernel is compiled for: 4 by default (64 registers,
+// small spills; measured 14.2 ms per batch48 step), 2 with PM_SOLVE_MINB=2
+// (no spill, half the occupancy; 15.4 ms)
 int solve_minb() {
   const char* v = getenv("PM_SOLVE_MINB");
-  return v && atoi(v) == 4 ? 4 : 2;
+  return v && atoi(v) == 2 ? 2 : 4;
 }
 
 template <int MINB>
