@@ -244,9 +244,12 @@ __global__ void __launch_bounds__(256) k64m_defect(GridD p, GridD f, Grid rb, in
     const long long dyp = (long long)(wp(j, s, periodic) - j) * p.sy;
     double zm = P[gidxd(p, i, j, wm(k0, s, periodic))];
     double zc = P[gidxd(p, i, j, k0)];
+    // the z+ neighbour is loaded one plane ahead of its use
+    double zp = P[gidxd(p, i, j, wp(k0, s, periodic))];
     for (int k = k0; k < k1; ++k) {
       const long long c = gidxd(p, i, j, k);
-      const double zp = P[gidxd(p, i, j, wp(k, s, periodic))];
+      double zn = 0.0;
+      if (k + 1 < k1) zn = P[gidxd(p, i, j, wp(k + 1, s, periodic))];  // plane k + 2 <= k1 <= s
       const double nb = ((P[c + dxm] + P[c + dxp]) + (P[c + dym] + P[c + dyp])) + (zm + zp);
       const double r = fma(6.0, zc, f.base[gidxd(f, i, j, k)]) - nb;
       const float r32 = (float)r;
@@ -254,6 +257,7 @@ __global__ void __launch_bounds__(256) k64m_defect(GridD p, GridD f, Grid rb, in
       r2 = fmaf(r32, r32, r2);
       zm = zc;
       zc = zp;
+      zp = zn;
     }
   }
   __shared__ double sm[8];

@@ -746,20 +746,32 @@ __device__ __forceinline__ void d_defect(const BI& bi, Grid ph, Grid pl, Grid e,
   if (i < s && j < s && k0 < k1) {
     const int xm = wrap_m(i, s, periodic) - i, xp = wrap_p(i, s, periodic) - i;
     const int ym = wrap_m(j, s, periodic) - j, yp = wrap_p(j, s, periodic) - j;
-    // the corrected double-float value of Phi at (i, j, kk)
-    auto column = [&](int kk, float& H, float& L) {
+    // the column's raw values at plane kk (hi, lo and, with CORRECT, e),
+    // then the corrected double-float value of Phi from them
+    float cH, cL, cE = 0.0f;
+    auto column_load = [&](int kk) {
       const int c = gidx(ph, i, j, kk);
-      H = ldx<NC>(ph.base + c);
-      L = ldx<NC>(pl.base + c);
+      cH = ldx<NC>(ph.base + c);
+      cL = ldx<NC>(pl.base + c);
+      if (CORRECT) cE = ldx<NC>(e.base + gidx(e, i, j, kk));
+    };
+    auto column_value = [&](float& H, float& L) {
+      H = cH;
+      L = cL;
       if (CORRECT) {
-        df t = two_sum(H, ldx<NC>(e.base + gidx(e, i, j, kk)));
+        df t = two_sum(H, cE);
         H = t.hi;
         L = __fadd_rn(L, t.lo);
       }
     };
     float Hm, Lm, Hc, Lc, Hp, Lp;
-    column(wrap_m(k0, s, periodic), Hm, Lm);
-    column(k0, Hc, Lc);
+    column_load(wrap_m(k0, s, periodic));
+    column_value(Hm, Lm);
+    column_load(k0);
+    column_value(Hc, Lc);
+    // the column at k + 1 (the z+ neighbour of plane k) is loaded one plane
+    // ahead of its use: in the iteration of plane k - 1 (k0 - 1: here)
+    column_load(wrap_p(k0, s, periodic));
     const int off[4] = {xm, xp, ym * ph.sy, yp * ph.sy};
     const int eoff[4] = {xm, xp, ym * e.sy, yp * e.sy};
     // the in-plane neighbours (with their corrections) and f of plane k are
@@ -791,8 +803,11 @@ __device__ __forceinline__ void d_defect(const BI& bi, Grid ph, Grid pl, Grid e,
       }
       float sacc = nfh;
       float comp = nfl;
-      if (k + 1 < k1) load_plane(k + 1);
-      column(wrap_p(k, s, periodic), Hp, Lp);
+      column_value(Hp, Lp);
+      if (k + 1 < k1) {
+        column_load(wrap_p(k + 1, s, periodic));  // plane k + 2 <= k1 <= s
+        load_plane(k + 1);
+      }
       H[5] = Hm;
       Lo[5] = Lm;
       H[6] = Hp;
