@@ -166,11 +166,11 @@ ARITHMETIC = {
 # of the kernel class's launches at 256^3 on the current kernels
 TRAFFIC_RATIO = {
     # the smoother's algorithmic bytes are 12 B per cell and sweep, 48 B per
-    # pre + post pair of fused passes
-    "smooth0": (288.7e6 / (48.0 * 256**3), "k_rbgs2 pre + post at 256^3, "
+    # pre + post pair of fused passes (the 256^3 level: 32 x 32 tiles)
+    "smooth0": ((93512704 + 187618048) / (48.0 * 256**3), "k_rbgs2<32> pre + post at 256^3, "
                 "profiles/rbgs2_pm256_level0.md"),
-    "defect": ((328.7e6 + 514.2e6) / (335.5e6 + 536.9e6), "k_defect<0> + k_defect<1> at "
-               "256^3, profiles/defect_gather_deposit_pm256.md"),
+    "defect": ((328087808 + 515491584) / (335.5e6 + 536.9e6), "k_defect<0> + k_defect<1> at "
+               "256^3, profiles/rbgs2_pm256_level0.md"),
     "deposit": (1127.8e6 / 1073.7e6, "k_drift_deposit at 256^3, "
                 "profiles/defect_gather_deposit_pm256.md"),
     "gather": (1294.6e6 / 1342.2e6, "k_gather_kick_drift at 256^3, "
@@ -659,10 +659,20 @@ def run_ours(args):
     # the untimed steps between them advance the same run
     sim = _new_sim(pos, mom, ids, cfg, rtol, args.precision)
     stream = sim.stream   # the stream every kernel of the context is launched on
-    launches = [0]
+    tiles = {str(side): f"32x{ty} tiles, {zc} planes per CTA"
+             for side, (ty, zc) in sorted(sim.smoother_tiles().items(), reverse=True)}
+    launches, marks = [0], []
 
     def count(edge):
-        launches[0] += (-1 if edge == "start" else 1) * lib.pm_launch_count()
+        c = lib.pm_launch_count()
+        launches[0] += (-1 if edge == "start" else 1) * c
+        if edge == "start":
+            marks.append(c)
+        else:
+            # for a launch list of exactly this window's kernels:
+            # ncu -k regex:^k -s <start> -c <count>
+            print(f"timed window {len(marks) - 1}: library launches {marks[-1]} .. {c - 1}",
+                  file=sys.stderr, flush=True)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -833,6 +843,7 @@ def run_ours(args):
                    "plain_fp32_floor": floor,
                    "precision": args.precision, "sort_every": SORT_EVERY,
                    "inner_vcycles": _inner(args.precision),
+                   "smoother_tiles": tiles,
                    "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (particles 537 MB, mesh 134 MB)"},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),

@@ -337,6 +337,16 @@ typedef struct {
 
 pm_status pm_stats(pm_ctx* ctx, pm_stats_t* out);
 
+/* The fused smoother's launch shape per level side, as pm_init picked it by
+ * timing (Sec. 2.1's red-black Gauss-Seidel smoothing, two sweeps in one
+ * pass; every shape gives the same bits).  Host arrays of cap entries each
+ * (any may be NULL): sides[i], the CTA tile height (16, 24 or 32) and the
+ * planes per CTA.  *count (required) = the number of sides tuned (0: all
+ * levels smaller than 192, or the ball solve, which keeps height 16); at
+ * most cap entries are written.  NULL ctx or count, cap < 0: PM_EINVAL. */
+pm_status pm_smoother_tiles(pm_ctx* ctx, int32_t* sides, int32_t* tile_height,
+                            int32_t* z_chunk, int32_t cap, int32_t* count);
+
 /* Copy the schedule (n_steps + 1 entries each, host arrays, any may be NULL):
  * a_k, dtau_k (conformal step k -> k+1, last entry 0), a_half_k (a at the
  * conformal midpoint of step k, last entry 0), chi_k (Mpc/h). */
@@ -499,9 +509,11 @@ pm_status pm_selftest_wait(int32_t arrive, int64_t polls, void* stream);
  * ghost face to the diagonal 6 (the coarse-level open boundary).
  * zero_start: u_in is taken as zero (ghosts included) and not read.
  * fused = 1: one pass over the grid (u_in and u_out distinct unless
- * zero_start); fused = 0: four one-colour passes in place on u_out after
- * copying u_in.  Both give the same bits.  zchunk: planes per CTA of the
- * fused pass (0 = default).  s even, >= 4.  Synchronises stream. */
+ * zero_start) in 32 x 16 tiles; fused = 16, 24 or 32: the same pass in
+ * 32 x fused tiles; fused = 0: four one-colour passes in place on u_out
+ * after copying u_in.  All give the same bits.  zchunk: planes per CTA of
+ * the fused pass (0 = default).  s even, >= 4.  Other values of fused:
+ * PM_EINVAL.  Synchronises stream. */
 pm_status pm_mg_smooth(const float* u_in, float* u_out, const float* b, int32_t s,
                        int32_t periodic, float h2, float gam, int32_t zero_start, int32_t fused,
                        int32_t zchunk, void* stream);

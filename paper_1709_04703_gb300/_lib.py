@@ -36,7 +36,7 @@ EXPORTED = [
     "pm_mg_smooth", "pm_mg_restrict", "pm_mg_prolong", "pm_selftest_wait", "pm_nn_gemm_bf16", "pm_guess_create", "pm_guess_num_params", "pm_guess_set_params",
     "pm_guess_get_params", "pm_guess_forward", "pm_guess_loss_grad", "pm_guess_adam",
     "pm_guess_last_error", "pm_guess_destroy", "pm_set_guess", "pm_capture",
-    "pm_mg_cluster_size",
+    "pm_mg_cluster_size", "pm_smoother_tiles",
 ]
 PROF_CLASSES = ["deposit", "source", "boundary", "smooth0", "transfer0", "coarse",
                 "defect", "correct", "gather", "compact", "guess", "ade", "sort"]
@@ -111,6 +111,7 @@ def load():
         "pm_profile": (I32, [P, I32]),
         "pm_profile_read": (I32, [P, I32, C.POINTER(D), C.POINTER(I64), C.POINTER(D)]),
         "pm_launch_count": (I64, []),
+        "pm_smoother_tiles": (I32, [P, P, P, P, I32, C.POINTER(I32)]),
         "pm_shrink_static": (I32, [P, P, I64, I32, D, D, D, D, D, P, P, P, P,
                                    C.POINTER(I64), P]),
         "pm_shrink_static_error": (C.c_char_p, []),

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpmshrink.so")
-SOURCES = ["api.cu", "k_mesh.cu", "k_mg.cu", "k_part.cu", "k_sort.cu", "k_fp64.cu", "k_pk.cu", "k_nn.cu", "nn_net.cu", "noalloc.cu", "k_cmg.cu", "k_conv.cu"]
+SOURCES = ["api.cu", "k_mesh.cu", "k_mg.cu", "k_rbgs2.cu", "k_part.cu", "k_sort.cu", "k_fp64.cu", "k_pk.cu", "k_nn.cu", "nn_net.cu", "noalloc.cu", "k_cmg.cu", "k_conv.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-fmad=true",
          "-Xptxas", "-O3"]

@@ -209,6 +209,11 @@ struct pm_ctx {
     long long kernels = 0;
     std::vector<struct Pend> pend;  // event pairs recorded inside the graph
   } vg[2];
+  // the fused smoother's tile height and z chunk per level side (tune_fused)
+  struct F2Pick {
+    int s, ty, zc;
+  };
+  std::vector<F2Pick> f2_pick;
   // the mixed forms' level-0 correction e of A e = r (compact (n+2)^3; its
   // ghost layer stays zero: homogeneous Dirichlet for the correction)
   float* ecorr = nullptr;
@@ -357,6 +362,82 @@ void geometry(const pm_ctx* c, double R, int* lo, int* s, int* periodic) {
   int side = std::min(mg_round_up(2 * m), n);
   *s = side;
   *lo = n / 2 - side / 2;
+}
+
+// The fused smoother's launch shape for a level of side s: the tuned pick,
+// else tile height 16 with the default z chunk.
+void f2_choice(const pm_ctx* c, int s, int* ty, int* zc) {
+  *ty = 16;
+  *zc = 0;
+  for (const auto& p : c->f2_pick)
+    if (p.s == s) {
+      *ty = p.ty;
+      *zc = p.zc;
+    }
+}
+
+// Time the fused smoother's launch shapes (tile height 16, 24, 32; z chunk
+// by rule, 64, 128) on every level side >= FUSED_MIN that the run's cubes
+// give, and keep the fastest per side.  All shapes give the same bits, so
+// the pick changes the speed only.  The run's cubes follow from the
+// schedule alone (geometry), so this runs once, at init, on the level-0
+// scratch grids (cleared here; set_cube clears them again).  The ball
+// solve keeps tile height 16; FP64 everywhere has no fused pass.
+cudaError_t tune_fused(pm_ctx* ctx) {
+  ctx->f2_pick.clear();
+  if (ctx->cfg.domain == PM_DOMAIN_BALL || ctx->cfg.precision == PM_FP64_PLAIN ||
+      ctx->lu.empty())
+    return cudaSuccess;
+  std::vector<int> sides;
+  for (size_t k = 0; k < ctx->R.size(); ++k) {
+    int lo, s, per;
+    geometry(ctx, ctx->R[k], &lo, &s, &per);
+    for (int l = s; l >= FUSED_MIN && l % 2 == 0; l /= 2)
+      if (std::find(sides.begin(), sides.end(), l) == sides.end()) sides.push_back(l);
+  }
+  if (sides.empty()) return cudaSuccess;
+  const size_t bytes = sizeof(float) * (size_t)(ctx->n + 2) * (ctx->n + 2) * (ctx->n + 2);
+  cudaError_t e = cudaSuccess;
+  for (float* p : {ctx->lu[0], ctx->lu2[0], ctx->lb[0]})
+    if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, bytes, ctx->st);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return e;
+  }
+  for (int s : sides) {
+    const Grid u = compact_view(ctx->lu[0], s), w = compact_view(ctx->lu2[0], s);
+    const Grid b = compact_view(ctx->lb[0], s);
+    float best = 1e30f;
+    pm_ctx::F2Pick pick{s, 16, 0};
+    for (int ty : {16, 24, 32})
+      for (int zq : {0, 64, 128}) {
+        const int zc = zq > 0 ? zq : rbgs2_zchunk(s, ty);
+        if (zq > 0 && (zc >= s || zc == rbgs2_zchunk(s, ty))) continue;
+        // one pass from the iterate (u -> w), as the post-smoothing runs:
+        // one to warm up, three timed
+        launch_rbgs2(ctx->st, u, w, b, 1.0f, 0, 0.0f, false, zc, 6.0f, ty);
+        cudaEventRecord(e0, ctx->st);
+        for (int r = 0; r < 3; ++r)
+          launch_rbgs2(ctx->st, u, w, b, 1.0f, 0, 0.0f, false, zc, 6.0f, ty);
+        cudaEventRecord(e1, ctx->st);
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+          best = ms;
+          pick = {s, ty, zc};
+        }
+      }
+    if (e != cudaSuccess) break;
+    ctx->f2_pick.push_back(pick);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return e;
 }
 
 // Exact float bounds [klo, khi] with x in it  <=>  |(double)x - c| <= R.
@@ -590,8 +671,10 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
     Upre[l] = (zs || !fused) ? U[l] : compact_view(ctx->lu[0], ctx->ls[0]);
     if (fused && !zs && !per)  // the scratch grids take u0's Dirichlet ghost values
       launch_copy_ghosts(ctx->st, U[0], Upre[0], compact_view(ctx->lu2[0], ctx->ls[0]));
+    int f2_ty = 16, f2_zc = 0;
+    f2_choice(ctx, ctx->ls[l], &f2_ty, &f2_zc);
     if (fused)
-      launch_rbgs2(ctx->st, U[l], Upre[l], B[l], h2, per, gam(l), zs, 0, d0);
+      launch_rbgs2(ctx->st, U[l], Upre[l], B[l], h2, per, gam(l), zs, f2_zc, d0, f2_ty);
     else
       smooth2(ctx, U[l], B[l], h2, per, gam(l), zs, d0, l > 0 ? LEVEL_SWEEPS : 2);
     if (l == 0) {
@@ -627,8 +710,10 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
       prof_end(ctx, PM_PROF_TRANSFER0, e, 8.5 * c0);
       e = prof_begin(ctx);
     }
+    int f2_ty = 16, f2_zc = 0;
+    f2_choice(ctx, ctx->ls[l], &f2_ty, &f2_zc);
     if (fused)
-      launch_rbgs2(ctx->st, W, U[l], B[l], h2, per, gam(l), false, 0, d0);
+      launch_rbgs2(ctx->st, W, U[l], B[l], h2, per, gam(l), false, f2_zc, d0, f2_ty);
     else
       smooth2(ctx, U[l], B[l], h2, per, gam(l), false, d0, l > 0 ? LEVEL_SWEEPS : 2);
     if (l == 0) prof_end(ctx, PM_PROF_SMOOTH0, e, 24.0 * c0);
@@ -1350,6 +1435,11 @@ pm_status pm_init(const pm_config* cfg, const float* pos4, const float* mom4,
   Z(ctx->d_scal, sizeof(double) * 16);
   Z(ctx->d_cnt, sizeof(unsigned long long) * 4);
 #undef Z
+  if (tune_fused(ctx) != cudaSuccess) {
+    g_err = "pm_init: timing the fused smoother failed";
+    pm_destroy(ctx);
+    return PM_ECUDA;
+  }
   cudaMemcpyKind kind = host_mem ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   if (cudaMemcpyAsync(ctx->pos, pos4, sizeof(float4) * N, kind, s0) != cudaSuccess ||
       cudaMemcpyAsync(ctx->mom, mom4, sizeof(float4) * N, kind, s0) != cudaSuccess ||
@@ -2308,6 +2398,19 @@ pm_status pm_profile_read(pm_ctx* ctx, int32_t cls, double* ms, int64_t* groups,
 }
 
 int64_t pm_launch_count(void) { return g_launches.load(); }
+
+pm_status pm_smoother_tiles(pm_ctx* ctx, int32_t* sides, int32_t* tile_height,
+                            int32_t* z_chunk, int32_t cap, int32_t* count) {
+  if (!ctx || !count || cap < 0) return fail(ctx, PM_EINVAL, "pm_smoother_tiles: bad argument");
+  const int m = (int)ctx->f2_pick.size();
+  for (int i = 0; i < m && i < cap; ++i) {
+    if (sides) sides[i] = ctx->f2_pick[i].s;
+    if (tile_height) tile_height[i] = ctx->f2_pick[i].ty;
+    if (z_chunk) z_chunk[i] = ctx->f2_pick[i].zc;
+  }
+  *count = m;
+  return PM_OK;
+}
 
 int32_t pm_mg_cluster_size(void) { return cmg_cluster(); }
 
@@ -3426,6 +3529,7 @@ extern "C" pm_status pm_mg_smooth(const float* u_in, float* u_out, const float* 
                                   int32_t periodic, float h2, float gam, int32_t zero_start,
                                   int32_t fused, int32_t zchunk, void* stream) {
   if (!u_out || !b || (!u_in && !zero_start) || s < 4 || (s & 1) || s > 2048 || zchunk < 0 ||
+      (fused != 0 && fused != 1 && !rbgs2_tile_ok(fused)) ||
       (fused && !zero_start && u_in == u_out))
     return fail(nullptr, PM_EINVAL, "pm_mg_smooth: bad argument");
   cudaStream_t st = (cudaStream_t)stream;
@@ -3440,7 +3544,8 @@ extern "C" pm_status pm_mg_smooth(const float* u_in, float* u_out, const float* 
   };
   Grid wi = view(u_in ? u_in : u_out), wo = view(u_out), gb = view(b);
   if (fused) {
-    launch_rbgs2(st, wi, wo, gb, h2, periodic, gam, zero_start != 0, zchunk);
+    launch_rbgs2(st, wi, wo, gb, h2, periodic, gam, zero_start != 0, zchunk, 6.0f,
+                 fused == 1 ? 16 : fused);
   } else {
     const size_t bytes = sizeof(float) * (size_t)(s + 2) * (s + 2) * (s + 2);
     if (zero_start && cudaMemsetAsync(u_out, 0, bytes, st) != cudaSuccess)

@@ -122,9 +122,12 @@ void launch_resid_restrict(cudaStream_t st, Grid u, Grid b, float inv_h2, Grid u
                            int periodic, float gam, float d0 = 6.0f);
 void launch_prolong_to(cudaStream_t st, Grid uc, Grid u, Grid w, int periodic, float gam_c);
 void launch_copy_ghosts(cudaStream_t st, Grid src, Grid d1, Grid d2);
+// the fused two-sweep smoother (k_rbgs2.cu): tile height ty 16, 24 or 32
+// (the ball solve's masked grids: 16), zc planes per CTA (0: by rbgs2_zchunk)
 void launch_rbgs2(cudaStream_t st, Grid win, Grid wout, Grid b, float h2, int periodic, float gam,
-                  bool zero_start, int zc = 0, float d0 = 6.0f);
-int rbgs2_zchunk(int s);
+                  bool zero_start, int zc = 0, float d0 = 6.0f, int ty = 16);
+int rbgs2_zchunk(int s, int ty = 16);
+bool rbgs2_tile_ok(int ty);
 cudaError_t mg_prepare();
 void launch_prolong(cudaStream_t st, Grid uc, Grid u, int periodic, float gam_c);
 // residual of Phi (e == NULL) or of Phi + e written to (qh, ql) (e != NULL)

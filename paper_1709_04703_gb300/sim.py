@@ -260,6 +260,17 @@ class Sim:
         self._check(self._lib.pm_stats(self._ctx, C.byref(s)))
         return {f: getattr(s, f) for f, _ in L.PmStats._fields_}
 
+    def smoother_tiles(self):
+        """The fused smoother's launch shape per level side, as pm_init
+        picked it: {side: (tile height, planes per CTA)}."""
+        cnt = C.c_int32(0)
+        self._check(self._lib.pm_smoother_tiles(self._ctx, None, None, None, 0, C.byref(cnt)))
+        m = cnt.value
+        sides, ty, zc = (C.c_int32 * max(m, 1))(), (C.c_int32 * max(m, 1))(), \
+            (C.c_int32 * max(m, 1))()
+        self._check(self._lib.pm_smoother_tiles(self._ctx, sides, ty, zc, m, C.byref(cnt)))
+        return {sides[i]: (ty[i], zc[i]) for i in range(m)}
+
     def save(self, path):
         """Checkpoint the run at the current step boundary (pm_save)."""
         self._check(self._lib.pm_save(self._ctx, str(path).encode()))

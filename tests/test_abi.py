@@ -72,6 +72,8 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.pm_step(None, 1) == L.PM_EINVAL
     assert lib.pm_shrink(None, 0.5, None) == L.PM_EINVAL
     assert lib.pm_stats(None, None) == L.PM_EINVAL
+    n = C.c_int32(-1)
+    assert lib.pm_smoother_tiles(None, None, None, None, 0, C.byref(n)) == L.PM_EINVAL
     assert lib.pm_power_spectrum(None, 0, 1.0, 8, 4, 1, None, None, None, None) == L.PM_EINVAL
     assert lib.pm_deposit(None, None, 0, 0.0, 8, 0, 8, 1, None, None, None) == L.PM_EINVAL
     lib.pm_destroy(None)

@@ -49,12 +49,15 @@ CASES = [(s, per, gam) for s in (8, 24, 32, 48, 64, 100) for per, gam in
 
 @pytest.mark.parametrize("s,periodic,gam", CASES)
 @pytest.mark.parametrize("zero", [0, 1])
-def test_fused_pass_gives_the_same_bits(lib, s, periodic, gam, zero):
+@pytest.mark.parametrize("tile", [1, 24, 32])
+def test_fused_pass_gives_the_same_bits(lib, s, periodic, gam, zero, tile):
+    """Every tile height (1: the default 16) against the one-colour passes;
+    the sides span several tiles and ragged last tiles in x, y and z."""
     u, b = _inputs(s, 10 * s + periodic + zero)
     h2 = 4.0 if gam else 1.0
     ref = _smooth(lib, u, b, s, periodic, h2, gam, zero, fused=0)
     for zc in (0, 5, 16):
-        got = _smooth(lib, u, b, s, periodic, h2, gam, zero, fused=1, zchunk=zc)
+        got = _smooth(lib, u, b, s, periodic, h2, gam, zero, fused=tile, zchunk=zc)
         a = got[1:-1, 1:-1, 1:-1].cpu().numpy()
         r = ref[1:-1, 1:-1, 1:-1].cpu().numpy()
         assert np.array_equal(a.view(np.uint32), r.view(np.uint32)), (zc, np.abs(a - r).max())
@@ -175,3 +178,45 @@ def test_prolongation_matches_its_definition(lib, s, periodic, gam):
     got = u[1:-1, 1:-1, 1:-1].cpu().numpy()
     np.testing.assert_allclose(got, ref, rtol=0, atol=2e-6 * np.abs(ref).max())
     assert torch.equal(u[0], before[0])          # ghosts untouched
+
+
+def test_fused_pass_rejects_other_tile_heights(lib):
+    u, b = _inputs(8, 1)
+    out = u.clone()
+    for fused in (2, 8, 48, -1):
+        code = lib.pm_mg_smooth(_p(u), _p(out), _p(b), 8, 0, C.c_float(1.0), C.c_float(0.0), 0,
+                                fused, 0, None)
+        assert code == L.PM_EINVAL
+
+
+@pytest.mark.parametrize("domain", ["cube", "ball"])
+def test_smoother_tiles_tuned_per_level_side(lib, domain):
+    """pm_init times the fused pass's launch shapes on every level side of at
+    least 192 that the run's cubes give (the 256^3 schedule: 256 periodic,
+    then shrinking open cubes); the ball solve keeps tile height 16."""
+    from paper_1709_04703_gb300 import ics
+    from paper_1709_04703_gb300.sim import Sim
+    n = 256
+    pos, mom, ids = ics.random_particles(8, n, 0)
+    kw = dict(domain="ball", precision="mixed") if domain == "ball" else {}
+    sim = Sim(pos, mom, ids, n, 2000.0, 0.01, 1.0, 200, **kw)
+    try:
+        cnt = C.c_int32(-1)
+        assert lib.pm_smoother_tiles(sim._ctx, None, None, None, 0, C.byref(cnt)) == L.PM_OK
+        m = cnt.value
+        if domain == "ball":
+            assert m == 0
+            return
+        assert m >= 1
+        sides = (C.c_int32 * m)()
+        ty = (C.c_int32 * m)()
+        zc = (C.c_int32 * m)()
+        assert lib.pm_smoother_tiles(sim._ctx, sides, ty, zc, m, C.byref(cnt)) == L.PM_OK
+        assert 256 in list(sides)
+        assert len(set(sides)) == m
+        for i in range(m):
+            assert 192 <= sides[i] <= n and sides[i] % 2 == 0
+            assert ty[i] in (16, 24, 32)
+            assert 1 <= zc[i] <= 128
+    finally:
+        sim.close()
