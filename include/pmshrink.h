@@ -502,18 +502,25 @@ const char* pm_shrink_static_error(void);
 pm_status pm_selftest_wait(int32_t arrive, int64_t polls, void* stream);
 
 /* The multigrid smoother of the Poisson solve (Sec. 2.1, Eq. 3 as the
- * 7-point system h^-2 (sum_nb u - diag u) = b): two red-black Gauss-Seidel
- * sweeps (red = (i+j+k) even first, then black, twice), u_out = S(u_in).
+ * 7-point system h^-2 (sum_nb u - diag u) = b): two red-black SOR sweeps
+ * (red = (i+j+k) even first, then black, twice), u_out = S(u_in).
  * Arrays are padded (s+2)^3 FP32 device arrays, [z][y][x], one ghost layer
  * (read, never written).  periodic = 1 wraps instead; gam > 0 adds gam per
  * ghost face to the diagonal 6 (the coarse-level open boundary).
  * zero_start: u_in is taken as zero (ghosts included) and not read.
+ * Each update is red-black SOR: the cell moves from its old value u_old
+ * towards the Gauss-Seidel value g = (sum_nb u - h2 b) / diag by the factor
+ * PM_MG_OMEGA, u = u_old + PM_MG_OMEGA (g - u_old) (one fused multiply-add
+ * in FP32); every multigrid smoothing pass of the solver does the same.
  * fused = 1: one pass over the grid (u_in and u_out distinct unless
  * zero_start) in 32 x 16 tiles; fused = 16, 24 or 32: the same pass in
  * 32 x fused tiles; fused = 0: four one-colour passes in place on u_out
  * after copying u_in.  All give the same bits.  zchunk: planes per CTA of
  * the fused pass (0 = default).  s even, >= 4.  Other values of fused:
  * PM_EINVAL.  Synchronises stream. */
+/* The smoother's over-relaxation factor (1 would be Gauss-Seidel). */
+#define PM_MG_OMEGA 1.25f
+
 pm_status pm_mg_smooth(const float* u_in, float* u_out, const float* b, int32_t s,
                        int32_t periodic, float h2, float gam, int32_t zero_start, int32_t fused,
                        int32_t zchunk, void* stream);

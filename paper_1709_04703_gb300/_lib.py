@@ -19,6 +19,7 @@ PM_SHRINK_OFF, PM_SHRINK_ON, PM_SHRINK_RECORD = 0, 1, 2
 PM_ASSIGN_CIC, PM_ASSIGN_TSC = 0, 1
 PM_DOMAIN_CUBE, PM_DOMAIN_SPHERE, PM_DOMAIN_BALL = 0, 1, 2
 PM_SHRINK_STATIC_MAX_PARTICLES = 1 << 22
+PM_MG_OMEGA = 1.25  # the multigrid smoother's SOR factor (include/pmshrink.h)
 
 STATUS_NAMES = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ECUDA",
                 4: "PM_ENOCONV", 5: "PM_EOVERFLOW", 6: "PM_ETIMEOUT", 7: "PM_EIO"}

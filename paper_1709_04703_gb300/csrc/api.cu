@@ -615,13 +615,13 @@ pm_status sync_read(pm_ctx* ctx) {
 }
 
 // V(2,2) cycle on level 0 grids (u0, b0) of the current cube.
-// Two RB-GS sweeps (red, black, red, black) on a level; zero_start when the
-// iterate is known to be zero on entry.
+// Two red-black SOR sweeps (red, black, red, black) on a level; zero_start
+// when the iterate is known to be zero on entry (not necessarily stored).
 void smooth2(pm_ctx* ctx, Grid u, Grid b, float h2, int per, float g, bool zero_start,
              float d0, int sweeps = 2) {
   for (int sw = 0; sw < sweeps; ++sw) {
-    launch_rbgs(ctx->st, u, b, h2, 0, per, g, zero_start && sw == 0, d0);
-    launch_rbgs(ctx->st, u, b, h2, 1, per, g, false, d0);
+    launch_rbgs(ctx->st, u, b, h2, 0, per, g, zero_start && sw == 0 ? 1 : 0, d0);
+    launch_rbgs(ctx->st, u, b, h2, 1, per, g, zero_start && sw == 0 ? 2 : 0, d0);
   }
 }
 
@@ -2596,7 +2596,10 @@ void upload_vcycle_tables(pm_batch* B) {
           e.gam = level_gam(l);
           e.color = k & 1;
           e.periodic = c->periodic;
-          e.zero_start = k == 0;  // level 0: e is not cleared; coarser: restriction zeroed it
+          // level 0: e is not cleared (the first red sweep takes it as zero,
+          // the black one after it its own cells); coarser: the restriction
+          // zeroed it
+          e.zero_start = k == 0 ? 1 : (k == 1 ? 2 : 0);
           set_dims(e, r, rbgs_grid_b(c->ls[l], B->rb_bx, B->rb_by));
           d.push_back(e);
           bl.push_back(nblocks(rbgs_grid_b(c->ls[l], B->rb_bx, B->rb_by)));
@@ -3554,8 +3557,8 @@ extern "C" pm_status pm_mg_smooth(const float* u_in, float* u_out, const float* 
         cudaMemcpyAsync(u_out, u_in, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
       return fail(nullptr, PM_ECUDA, "pm_mg_smooth: copy");
     for (int sw = 0; sw < 2; ++sw) {
-      launch_rbgs(st, wo, gb, h2, 0, periodic, gam, zero_start && sw == 0);
-      launch_rbgs(st, wo, gb, h2, 1, periodic, gam, false);
+      launch_rbgs(st, wo, gb, h2, 0, periodic, gam, zero_start && sw == 0 ? 1 : 0);
+      launch_rbgs(st, wo, gb, h2, 1, periodic, gam, zero_start && sw == 0 ? 2 : 0);
     }
   }
   cudaError_t e = cudaGetLastError();

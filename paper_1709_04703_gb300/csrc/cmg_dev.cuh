@@ -397,7 +397,7 @@ struct Cc {
     const int nb = nlev - 1;  // the bottom level
     for (int q = 0; q < nb; ++q) {
       for (int p = 0; p < 4; ++p) {
-        smooth_pass(q, p & 1);
+        smooth_pass(q, p & 1, MG_OMEGA);
         sync(q);
       }
       restrict_to(q);
@@ -412,7 +412,7 @@ struct Cc {
       prolong_from(q);
       sync(q);
       for (int p = 0; p < 4; ++p) {
-        smooth_pass(q, p & 1);
+        smooth_pass(q, p & 1, MG_OMEGA);
         sync(q);
       }
     }

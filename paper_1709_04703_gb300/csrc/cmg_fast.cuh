@@ -105,7 +105,7 @@ struct Fc {
     return L.simple && !(MASK && (gu.mstep << q) > 2);
   }
 
-  // one colour of red-black Gauss-Seidel on an even level, two cells per
+  // one colour of red-black SOR (sor_value) on an even level, two cells per
   // thread at a time (loads of both before either store: cells of one
   // colour never neighbour each other)
   template <int S>
@@ -133,9 +133,13 @@ struct Fc {
         b2 = b[fc_d<S>(i2, j2, k2)];
       }
       const bool sp = simple(L, q);
-      if (in<S>(q, i1, j1, k1)) u[p1] = gs_value(s1, b1, L.h2, sp, diag<S>(L, i1, j1, k1, q));
+      // (the iterate is zeroed in shared memory before a level's first
+      // sweep, so the old values are always stored ones)
+      const float o1 = u[p1], o2 = c2 < N ? u[p2] : 0.0f;
+      if (in<S>(q, i1, j1, k1))
+        u[p1] = sor_value(o1, gs_value(s1, b1, L.h2, sp, diag<S>(L, i1, j1, k1, q)));
       if (c2 < N && in<S>(q, i2, j2, k2))
-        u[p2] = gs_value(s2, b2, L.h2, sp, diag<S>(L, i2, j2, k2, q));
+        u[p2] = sor_value(o2, gs_value(s2, b2, L.h2, sp, diag<S>(L, i2, j2, k2, q)));
     }
   }
 

@@ -35,7 +35,8 @@ __device__ __forceinline__ double nbsum64(const GridD& u, int i, int j, int k, i
 }
 }  // namespace
 
-// one colour of RB-GS, u = (sum_nb u - h^2 b) / diag, cells (i+j+k) % 2 == color
+// one colour of red-black SOR, u = u + omega ((sum_nb u - h^2 b) / diag - u),
+// cells (i+j+k) % 2 == color, omega = MG_OMEGA as in the FP32 forms
 __global__ void __launch_bounds__(256) k64_rbgs(GridD u, GridD b, double h2, int color,
                                                 int periodic, double gam) {
   const int s = u.s;
@@ -44,9 +45,10 @@ __global__ void __launch_bounds__(256) k64_rbgs(GridD u, GridD b, double h2, int
   if (j >= s) return;
   const int i = 2 * t + ((j + k + color) & 1);
   if (i >= s) return;
-  const double v = (nbsum64(u, i, j, k, periodic) - h2 * b.base[gidxd(b, i, j, k)]) /
-                   diag64(i, j, k, s, periodic, gam);
-  u.base[gidxd(u, i, j, k)] = v;
+  const double gs = (nbsum64(u, i, j, k, periodic) - h2 * b.base[gidxd(b, i, j, k)]) /
+                    diag64(i, j, k, s, periodic, gam);
+  double* c = u.base + gidxd(u, i, j, k);
+  *c = *c + (double)MG_OMEGA * (gs - *c);
 }
 
 // coarse b = average over the 8 children of r = b - (sum_nb u - diag u) / h^2;

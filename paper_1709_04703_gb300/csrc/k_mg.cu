@@ -13,13 +13,14 @@
 namespace pm {
 
 // ---------------------------------------------------------------------------
-// One colour of RB-GS: cells with (i+j+k) % 2 == color,
-//   u = (sum_nb u - h^2 b) / 6.
+// One colour of red-black SOR: cells with (i+j+k) % 2 == color,
+//   u = u + MG_OMEGA ((sum_nb u - h^2 b) / 6 - u).
 // Thread layout: x over half a row (s even), y, z over rows.
 // ---------------------------------------------------------------------------
-// zero_start (red only): the iterate is known to be zero, so the red cells
-// take (-h^2 b)/diag without reading u; the black sweep after it reads only
-// red neighbours, so u needs no clearing before a V-cycle.
+// zero_start 1 (the first red sweep): the iterate is known to be zero, so
+// the red cells take MG_OMEGA (-h^2 b)/diag without reading u; 2 (the black
+// sweep after it): the black cells' own values are known to be zero (it
+// reads only red neighbours), so u needs no clearing before a V-cycle.
 // MASK: the ball solve's masked grids (compiled out of the unmasked form)
 template <bool MASK>
 __device__ __forceinline__ void d_rbgs(const BI& bi, Grid u, Grid b, float h2, int color,
@@ -49,7 +50,12 @@ __device__ __forceinline__ void d_rbgs(const BI& bi, Grid u, Grid b, float h2, i
   const float* bb = b.base + bc0;
   float b0v = bb[0], b1v = two ? bb[2] : 0.0f;
   float s0 = 0.0f, s1 = 0.0f;
-  if (!zero_start) {
+  float o0 = 0.0f, o1 = 0.0f;  // the cells' old values (zero unless zero_start == 0)
+  if (zero_start == 0) {
+    o0 = p0[0];
+    if (two) o1 = p0[2];
+  }
+  if (zero_start != 1) {  // (1: the neighbours are zero too)
     const int xm = wrap_m(i0, s, periodic) - i0;
     const int xp = wrap_p(i0, s, periodic) - i0;  // 1 unless i0 = s - 1 (then no i0 + 2)
     float xmid = p0[xp];  // right neighbour of i0, left of i0 + 2
@@ -64,8 +70,8 @@ __device__ __forceinline__ void d_rbgs(const BI& bi, Grid u, Grid b, float h2, i
   auto dg = [&](int i) {
     return simple ? 6.0f : (ballc ? ball_diag(u, i, j, k) : mg_diag(i, j, k, s, periodic, gam, d0));
   };
-  if (in0) p0[0] = gs_value(s0, b0v, h2, simple, dg(i0));
-  if (in1) p0[2] = gs_value(s1, b1v, h2, simple, dg(i0 + 2));
+  if (in0) p0[0] = sor_value(o0, gs_value(s0, b0v, h2, simple, dg(i0)));
+  if (in1) p0[2] = sor_value(o1, gs_value(s1, b1v, h2, simple, dg(i0 + 2)));
 }
 
 template <bool MASK>
@@ -305,13 +311,13 @@ static inline dim3 grid_half(int s) {
 static inline dim3 grid_full(int s) { return dim3((unsigned)((s + 31) / 32), (unsigned)((s + 7) / 8), (unsigned)s); }
 
 void launch_rbgs(cudaStream_t st, Grid u, Grid b, float h2, int color, int periodic,
-                 float gam, bool zero_start, float d0) {
+                 float gam, int zero_start, float d0) {
   if (u.mbase)
     launch_pdl(k_rbgs<true>, grid_half(u.s), dim3(32, 8), 0, st, u, b, h2, color, periodic, gam,
-               zero_start ? 1 : 0, d0);
+               zero_start, d0);
   else
     launch_pdl(k_rbgs<false>, grid_half(u.s), dim3(32, 8), 0, st, u, b, h2, color, periodic,
-               gam, zero_start ? 1 : 0, d0);
+               gam, zero_start, d0);
   note_launch();
 }
 void launch_resid_restrict(cudaStream_t st, Grid u, Grid b, float inv_h2, Grid uc, Grid bc,

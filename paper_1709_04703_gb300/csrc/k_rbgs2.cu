@@ -24,8 +24,8 @@ namespace pm {
 // Within a step no stage reads a shared-memory value written in the same
 // step (x/y neighbours live on the stage's own plane, written one step
 // earlier; z neighbours are the thread's own registers), so one barrier per
-// step suffices.  Every update applies gs_value to the values the four
-// one-colour launches would give it: the same bits.  win and wout must be
+// step suffices.  Every update applies sor_value(old, gs_value(..)) to the
+// values the four one-colour launches would give it: the same bits.  win and wout must be
 // different arrays unless zero_start (win is then not read: the iterate
 // starts at zero, ghosts included).  Open boundaries: ghost cells are read,
 // never updated; periodic: coordinates wrap.  Needs s even.
@@ -179,15 +179,15 @@ struct Rbgs2 {
         float nv;
         if ((st & 1) == 0) {  // red: partner and z neighbours are black
           const float s0 = nb6(xv, K[q], ym, yp, K[qm], K[qp]);
-          nv = SIMPLE ? gs_value(s0, BR[q], h2, true, 6.0f)
-                      : gs_value(s0, BR[q], h2, false,
-                                 mg_diag(xa + kc, y, p, s, PERIODIC, gam, d0));
+          nv = sor_value(R[q], SIMPLE ? gs_value(s0, BR[q], h2, true, 6.0f)
+                                      : gs_value(s0, BR[q], h2, false,
+                                                 mg_diag(xa + kc, y, p, s, PERIODIC, gam, d0)));
           R[q] = nv;
         } else {              // black: partner and z neighbours are red
           const float s0 = nb6(xv, R[q], ym, yp, R[qm], R[qp]);
-          nv = SIMPLE ? gs_value(s0, BK[q], h2, true, 6.0f)
-                      : gs_value(s0, BK[q], h2, false,
-                                 mg_diag(xa + kc, y, p, s, PERIODIC, gam, d0));
+          nv = sor_value(K[q], SIMPLE ? gs_value(s0, BK[q], h2, true, 6.0f)
+                                      : gs_value(s0, BK[q], h2, false,
+                                                 mg_diag(xa + kc, y, p, s, PERIODIC, gam, d0)));
           K[q] = nv;
         }
         *c = nv;

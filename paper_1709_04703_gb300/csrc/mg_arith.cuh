@@ -46,6 +46,14 @@ __device__ __forceinline__ float gs_value(float s0, float bv, float h2, bool sim
   float t = __fsub_rn(s0, __fmul_rn(h2, bv));
   return simple ? __fmul_rn(t, 1.0f / 6.0f) : __fdiv_rn(t, diag);
 }
+// Red-black SOR (MG_OMEGA, pm_common.cuh): a smoothing update moves the cell
+// from its old value towards the Gauss-Seidel value by MG_OMEGA; every
+// smoothing pass of every FP32 form applies it, so they all keep giving the
+// same bits.  A zero old value may be read or assumed: the result is the
+// same.
+__device__ __forceinline__ float sor_value(float old, float gs) {
+  return MG_OMEGA == 1.0f ? gs : __fmaf_rn(MG_OMEGA, __fsub_rn(gs, old), old);
+}
 // residual b - (sum_nb u - diag u) / h^2
 __device__ __forceinline__ float resid_value(float s0, float uc, float bv, float diag,
                                              float inv_h2) {

@@ -277,6 +277,13 @@ __device__ inline void block_sum(double (&v)[NV], double* smem /* 32*NV */) {
 
 namespace pm {
 
+// The multigrid smoother's over-relaxation factor (red-black SOR; 1 would
+// be Gauss-Seidel).  Over-relaxation speeds up the V-cycle's smoothing of
+// the 7-point operator: on a cell-centred periodic model of this V(2,2)
+// cycle (the same transfers) the residual falls by 0.097 per cycle with
+// Gauss-Seidel and 0.030 with 1.25 at 64^3.
+constexpr float MG_OMEGA = PM_MG_OMEGA;
+
 // ---------------------------------------------------------------------------
 // Batched launches: one launch covers the blocks of several realisations.
 // A table in device memory lists the member realisations' cumulative block

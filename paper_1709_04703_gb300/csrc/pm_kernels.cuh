@@ -102,8 +102,10 @@ void launch_boundary(cudaStream_t st, Grid ph, Grid pl, int n, int lo, const dou
 // k_mg.cu
 // d0: base diagonal of the operator sum_nb u - d0 u (6: Poisson; 6 + sig h^2:
 // an implicit diffusion substep)
+// zero_start: 0, or 1 for a first red sweep from a zero iterate, 2 for the
+// black sweep right after it (its cells' own values are taken as zero)
 void launch_rbgs(cudaStream_t st, Grid u, Grid b, float h2, int color, int periodic,
-                 float gam, bool zero_start = false, float d0 = 6.0f);
+                 float gam, int zero_start = 0, float d0 = 6.0f);
 // The rest of a V-cycle from the first level of side <= cmg_top_side(
 // cmg_cluster()) in one thread-block cluster (k_cmg.cu): cmg_prepare picks
 // the largest cluster the GPU holds (16 CTAs: levels <= 64^3; 8: <= 32^3;

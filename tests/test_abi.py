@@ -33,6 +33,14 @@ def test_header_declares_the_boundary():
     assert set(names) == set(L.EXPORTED)
 
 
+def test_header_constants_match_the_binding():
+    text = open(HEADER).read()
+    om = re.search(r"#define PM_MG_OMEGA ([0-9.]+)f", text)
+    assert om and float(om.group(1)) == L.PM_MG_OMEGA
+    mx = re.search(r"#define PM_SHRINK_STATIC_MAX_PARTICLES \(1 << (\d+)\)", text)
+    assert mx and (1 << int(mx.group(1))) == L.PM_SHRINK_STATIC_MAX_PARTICLES
+
+
 def test_library_exports_every_declared_symbol(lib):
     out = subprocess.run(["nm", "-D", "--defined-only", L.LIB_PATH],
                          capture_output=True, text=True, check=True).stdout

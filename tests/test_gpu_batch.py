@@ -45,8 +45,14 @@ def _compare(batch, r, ref):
     np.testing.assert_array_equal(cp, lp)
     np.testing.assert_array_equal(ca, la)
     bs = batch.stats(r)
-    for key in ("n_active", "n_lightcone", "vcycles_total", "cube_side", "periodic"):
+    for key in ("n_active", "n_lightcone", "cube_side", "periodic"):
         assert bs[key] == st[key], (key, bs[key], st[key])
+    # the batch decides convergence on the device after every V-cycle; a
+    # single context first runs one V-cycle fewer than its previous solve
+    # took before it reads a residual, so it may run one more per step (a
+    # correction far below what the FP32 particles resolve: same bits)
+    extra = st["vcycles_total"] - bs["vcycles_total"]
+    assert 0 <= extra <= st["step"], (bs["vcycles_total"], st["vcycles_total"])
 
 
 def test_batch_matches_separate_contexts_bitwise():

@@ -1,6 +1,7 @@
-"""The multigrid smoother (two red-black Gauss-Seidel sweeps of the 7-point
-system of Eq. 3): the fused one-pass kernel against the four one-colour
-passes (same bits) and against an FP64 statement of the sweeps."""
+"""The multigrid smoother (two red-black SOR sweeps, factor PM_MG_OMEGA, of
+the 7-point system of Eq. 3): the fused one-pass kernel against the four
+one-colour passes (same bits) and against an FP64 statement of the
+sweeps."""
 import ctypes as C
 
 import numpy as np
@@ -64,7 +65,9 @@ def test_fused_pass_gives_the_same_bits(lib, s, periodic, gam, zero, tile):
 
 
 def _sweeps_fp64(u, b, s, periodic, h2, gam, zero):
-    """Red then black, twice, in FP64 (ghosts read as stored; periodic wraps)."""
+    """Red then black, twice, in FP64 (ghosts read as stored; periodic
+    wraps): each cell moves from its old value towards the Gauss-Seidel
+    value by the factor PM_MG_OMEGA."""
     u = np.zeros_like(u, dtype=np.float64) if zero else u.astype(np.float64)
     b = b.astype(np.float64)
     idx = np.arange(s)
@@ -81,7 +84,7 @@ def _sweeps_fp64(u, b, s, periodic, h2, gam, zero):
                       + u[1:-1, :-2, 1:-1] + u[1:-1, 1:-1, 2:] + u[1:-1, 1:-1, :-2])
             new = (nb - h2 * b[1:-1, 1:-1, 1:-1]) / diag
             m = (X + Y + Z) % 2 == colour
-            v[m] = new[m]
+            v[m] = v[m] + L.PM_MG_OMEGA * (new[m] - v[m])
     return u
 
 
