@@ -167,9 +167,9 @@ ARITHMETIC = {
 TRAFFIC_RATIO = {
     # the smoother's algorithmic bytes are 12 B per cell and sweep, 48 B per
     # pre + post pair of fused passes (the 256^3 level: 32 x 32 tiles)
-    "smooth0": ((93512704 + 187618048) / (48.0 * 256**3), "k_rbgs2<32> pre + post at 256^3, "
+    "smooth0": ((93332224 + 187955712) / (48.0 * 256**3), "k_rbgs2<32> pre + post at 256^3, "
                 "profiles/rbgs2_pm256_level0.md"),
-    "defect": ((328087808 + 515491584) / (335.5e6 + 536.9e6), "k_defect<0> + k_defect<1> at "
+    "defect": ((327600640 + 515282176) / (335.5e6 + 536.9e6), "k_defect<0> + k_defect<1> at "
                "256^3, profiles/rbgs2_pm256_level0.md"),
     "deposit": (1127.8e6 / 1073.7e6, "k_drift_deposit at 256^3, "
                 "profiles/defect_gather_deposit_pm256.md"),
