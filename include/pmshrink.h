@@ -338,7 +338,7 @@ typedef struct {
 pm_status pm_stats(pm_ctx* ctx, pm_stats_t* out);
 
 /* The fused smoother's launch shape per level side, as pm_init picked it by
- * timing (Sec. 2.1's red-black Gauss-Seidel smoothing, two sweeps in one
+ * timing (the multigrid solve's red-black smoothing, two sweeps in one
  * pass; every shape gives the same bits).  Host arrays of cap entries each
  * (any may be NULL): sides[i], the CTA tile height (16, 24 or 32) and the
  * planes per CTA.  *count (required) = the number of sides tuned (0: all
@@ -383,7 +383,7 @@ enum {
   PM_PROF_DEPOSIT = 0,  /* half drift + CIC deposit                         */
   PM_PROF_SOURCE,       /* counts -> double-float source (+ moments)        */
   PM_PROF_BOUNDARY,     /* open-boundary ghost layer                        */
-  PM_PROF_SMOOTH0,      /* RB-GS sweeps on the finest level                 */
+  PM_PROF_SMOOTH0,      /* red-black sweeps on the finest level             */
   PM_PROF_TRANSFER0,    /* finest-level residual+restriction, prolongation  */
   PM_PROF_COARSE,       /* everything on levels >= 1                        */
   PM_PROF_DEFECT,       /* double-float residual + norm                     */

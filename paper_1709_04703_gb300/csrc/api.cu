@@ -645,7 +645,7 @@ pm_status vcycle(pm_ctx* ctx, Grid u0, Grid b0, bool zero0) {
     B[l] = masked(ctx, compact_view(ctx->lb[l], ctx->ls[l]), l);
   }
   const double c0 = (double)ctx->s * ctx->s * ctx->s;
-  // algorithmic bytes per fine cell: a red-black Gauss-Seidel sweep reads u
+  // algorithmic bytes per fine cell: a red-black SOR sweep reads u
   // and b and writes u, 12 B per sweep (two sweeps per smoothing: 24; the
   // fused pass moves 8 from a zero start and 12 otherwise, since its two
   // sweeps share one read and one write); residual + restriction reads u

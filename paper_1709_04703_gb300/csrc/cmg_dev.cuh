@@ -210,7 +210,7 @@ struct Cc {
     i = 2 * m + ((j + k + colour) & 1);
   }
 
-  // one colour of red-black Gauss-Seidel on an even level: cells (i+j+k) % 2
+  // one colour of red-black SOR on an even level: cells (i+j+k) % 2
   // == colour of this CTA's planes, two per thread at a time (their loads
   // issued before either store; cells of one colour never neighbour each
   // other)

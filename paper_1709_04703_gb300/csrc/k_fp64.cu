@@ -1,6 +1,6 @@
 // FP64 everywhere (precision PM_FP64_PLAIN): the Poisson solve of Eq. 3
 // with the potential, the source and every multigrid level in double, the
-// same V(2,2) cycle as the FP32 path (red-black Gauss-Seidel, 8-cell
+// same V(2,2) cycle as the FP32 path (red-black SOR, 8-cell
 // average restriction of the residual, trilinear prolongation, the
 // coarse-level open-boundary factor folded into the diagonal) and a one-CTA
 // bottom.  It exists to measure what FP64 costs on this GPU against the

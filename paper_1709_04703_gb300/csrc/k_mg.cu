@@ -1,5 +1,5 @@
 // Geometric multigrid for the 7-point Poisson operator (Sec. 2.1, Eq. 3,
-// cell units, h_l = 2^l on level l): red-black Gauss-Seidel smoothing,
+// cell units, h_l = 2^l on level l): red-black SOR smoothing,
 // fused residual + 8-cell restriction, trilinear prolongation + correction,
 // a single-CTA coarsest solve, and the double-float defect-correction loop
 // (residual of the double-float potential; Phi += e).

@@ -1,4 +1,4 @@
-// The fused two-sweep red-black Gauss-Seidel smoother of the multigrid
+// The fused two-sweep red-black SOR smoother of the multigrid
 // solve (Sec. 2.1, Eq. 3, cell units) for the large levels: one pass over
 // the grid does red, black, red, black.  Tile heights 16, 24 and 32 give the
 // same bits; the solve picks the fastest for each level-0 side.
@@ -8,7 +8,7 @@
 namespace pm {
 
 // ---------------------------------------------------------------------------
-// Two RB-GS sweeps (red, black, red, black) in one pass: win -> wout.
+// Two red-black SOR sweeps (red, black, red, black) in one pass: win -> wout.
 //
 // A CTA owns a 32 x TY tile of (x, y) (TY = 16, 24 or 32) and a chunk of zc
 // planes and marches z.  Each of its 20 (TY + 8) threads (480, 640, 800) owns
