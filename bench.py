@@ -843,6 +843,7 @@ def run_ours(args):
                    "plain_fp32_floor": floor,
                    "precision": args.precision, "sort_every": SORT_EVERY,
                    "inner_vcycles": _inner(args.precision),
+                   "smoother": f"red-black SOR, factor {L.PM_MG_OMEGA}, V(2,2)",
                    "smoother_tiles": tiles,
                    "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (particles 537 MB, mesh 134 MB)"},
